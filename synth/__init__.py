@@ -1,0 +1,20 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle.
+
+This package holds *inputs only*: the model specifications of the five workloads
+(structure, parameter truth values, observable ranges, kinematic masses) and
+numpy-PCG64 generators of event samples.  It contains none of the fitting
+method's arithmetic -- no density evaluation, no normalisation, no likelihood.
+Samples are drawn with numpy's own distribution samplers plus range rejection;
+where a sampler needs a density for accept--reject (the Dalitz model), the
+caller passes that density in as a function.
+"""
+from .specs import (c1_spec, c2_spec, c3_spec, c4_spec, dalitz_resonances, DALITZ_MASSES,
+                    param_names, param_values, observable_names)
+from .gen import (gen_c1, gen_c2, dalitz_box, dalitz_candidates, accept_reject, round_to_f32,
+                  toy_sizes, gen_c4_candidates)
+
+__all__ = [
+    "c1_spec", "c2_spec", "c3_spec", "c4_spec", "dalitz_resonances", "DALITZ_MASSES",
+    "param_names", "param_values", "observable_names", "gen_c1", "gen_c2", "dalitz_box",
+    "dalitz_candidates", "accept_reject", "round_to_f32", "toy_sizes", "gen_c4_candidates",
+]

@@ -1,0 +1,117 @@
+"""Model specifications (plain data) for the five synthetic workloads.
+
+A spec is a dict:
+  name         workload name
+  observables  [(name, lo, hi), ...]           event columns, in column order
+  params       [(name, value, fixed, step), ...] parameter vector theta, in order
+  pdf          expression tree (tuples, see below)
+  norm         ("analytic",) | ("grid", [bins per observable]) | ("mc", n_points, seed)
+
+Tree nodes (parameter and observable references are names):
+  ("gauss", obs, mu, sigma)        ("expo", obs, lam)
+  ("poly2", obs, a1, a2)           ("argus", obs, m0, c, p)
+  ("prod", [child, ...])           ("add", [frac, ...], [child, ...])   K children, K-1 fractions
+  ("coherent", kin, [amp, ...])    kin = dict(M, m1, m2, m3, r_res, r_par)
+      amp = ("bw", pair, spin, m0, width, re, im) | ("nr", re, im);  pair in {"12","13","23"}
+
+The paper (GooFit 2.0, Fig. 1 and Sec. 1) describes models built from basic PDFs combined
+by sum and product combination PDFs and amplitude PDFs for three-body decays (Sec. 1,
+Sec. 6); it prints no formulas, so the meaning of each node is fixed by the oracle.
+"""
+
+# Parent and daughter masses (GeV) of the D -> K pi pi0 - like three-body model.
+DALITZ_MASSES = dict(M=1.865, m1=0.494, m2=0.140, m3=0.135)
+
+
+def c1_spec():
+    """1D: 0.3 Gauss(5.0, 0.4) + 0.7 Exp(-0.3) on x in [0, 10], analytic normalisation."""
+    return dict(
+        name="c1_1d",
+        observables=[("x", 0.0, 10.0)],
+        params=[("mu", 5.0, False, 0.01), ("sigma", 0.4, False, 0.01),
+                ("lam", -0.3, False, 0.005), ("frac", 0.3, False, 0.005)],
+        pdf=("add", ["frac"], [("gauss", "x", "mu", "sigma"), ("expo", "x", "lam")]),
+        norm=("analytic",),
+    )
+
+
+def c2_spec(bins=128):
+    """3D: 0.2 [Gauss(m) Gauss(dE) Exp(t)] + 0.8 [Argus(m) Poly2(dE) Exp(t)], grid normalisation."""
+    return dict(
+        name="c2_3d",
+        observables=[("m", 5.2, 5.3), ("dE", -0.2, 0.2), ("t", 0.0, 10.0)],
+        params=[("mu_m", 5.279, False, 1e-4), ("sig_m", 0.003, False, 1e-4),
+                ("mu_de", 0.0, False, 1e-3), ("sig_de", 0.02, False, 1e-3),
+                ("lam_s", -1.0 / 1.5, False, 1e-2),
+                ("m0", 5.29, False, 1e-4), ("c", -20.0, False, 0.5), ("p", 0.5, False, 0.02),
+                ("a1", -1.0, False, 0.05), ("a2", 0.5, False, 0.2),
+                ("lam_b", -1.0 / 0.8, False, 1e-2), ("frac", 0.2, False, 1e-3)],
+        pdf=("add", ["frac"], [
+            ("prod", [("gauss", "m", "mu_m", "sig_m"), ("gauss", "dE", "mu_de", "sig_de"),
+                      ("expo", "t", "lam_s")]),
+            ("prod", [("argus", "m", "m0", "c", "p"), ("poly2", "dE", "a1", "a2"),
+                      ("expo", "t", "lam_b")]),
+        ]),
+        norm=("grid", [bins, bins, bins]),
+    )
+
+
+def dalitz_resonances():
+    """The eight resonances of the three-body model: (name, pair, spin, m0, width).
+
+    Particle labels: 1 = K, 2 = pi, 3 = pi0.  Masses and widths are PDG-like round values.
+    """
+    return [
+        ("Kst892_12", "12", 1, 0.8955, 0.0473),
+        ("Kst892_13", "13", 1, 0.8955, 0.0473),
+        ("rho770_23", "23", 1, 0.7753, 0.1491),
+        ("K0st1430_12", "12", 0, 1.425, 0.270),
+        ("K0st1430_13", "13", 0, 1.425, 0.270),
+        ("K2st1430_12", "12", 2, 1.4324, 0.109),
+        ("Kst1680_12", "12", 1, 1.718, 0.322),
+        ("rho1450_23", "23", 1, 1.465, 0.400),
+    ]
+
+
+# Truth coefficients (Re, Im) of the eight resonant amplitudes; the non-resonant
+# amplitude is the fixed reference c = (1, 0).
+DALITZ_TRUTH = [
+    (0.913, 0.303), (-0.456, 0.580), (0.999, -0.447), (0.585, 0.400),
+    (-0.411, 0.366), (1.252, -0.293), (1.726, 1.725), (-0.918, 1.725),
+]
+
+
+def c3_spec(n_mc=1_000_000, mc_seed=1710013):
+    """Three-body Dalitz model: 8 Breit--Wigner resonances + constant NR, 16 free coefficients."""
+    kin = dict(DALITZ_MASSES, r_res=1.5, r_par=5.0)
+    M, m1, m2, m3 = kin["M"], kin["m1"], kin["m2"], kin["m3"]
+    params, amps = [], []
+    for (name, pair, spin, m0, w), (re, im) in zip(dalitz_resonances(), DALITZ_TRUTH):
+        params += [(f"m0_{name}", m0, True, 0.0), (f"w_{name}", w, True, 0.0),
+                   (f"re_{name}", re, False, 0.02), (f"im_{name}", im, False, 0.02)]
+        amps.append(("bw", pair, spin, f"m0_{name}", f"w_{name}", f"re_{name}", f"im_{name}"))
+    params += [("re_NR", 1.0, True, 0.0), ("im_NR", 0.0, True, 0.0)]
+    amps.append(("nr", "re_NR", "im_NR"))
+    return dict(
+        name="c3_dalitz",
+        observables=[("s12", (m1 + m2) ** 2, (M - m3) ** 2), ("s13", (m1 + m3) ** 2, (M - m2) ** 2)],
+        params=params,
+        pdf=("coherent", kin, amps),
+        norm=("mc", n_mc, mc_seed),
+    )
+
+
+def c4_spec():
+    raise NotImplementedError("time-dependent four-body model spec")
+
+
+def param_names(spec):
+    return [p[0] for p in spec["params"]]
+
+
+def param_values(spec):
+    return [float(p[1]) for p in spec["params"]]
+
+
+def observable_names(spec):
+    return [o[0] for o in spec["observables"]]
