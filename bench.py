@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of the unbinned-likelihood hot path on GB300.
+
+Workload (default): the 3D product model -- 10,000,000 events over (m, dE, t), signal
+Gauss x Gauss x Exp plus background Argus x Poly2 x Exp, 12 free parameters, 128^3 midpoint
+grid normalisation.  One step is one pass of the whole hot path: parameter upload, grid
+normalisation, per-event evaluation, log, accumulation, adjoint gradient and the final
+reduction, through goo_nll_grad with FP32 per-event arithmetic and compensated accumulation.
+The FP64 plain form (goo_nll in float64) is timed beside it.
+
+Prints ONE JSON line on rank 0.  With --impl reference it times the FP64 CPU oracle on
+the host cores instead (bounded samples of the same workload).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_EVENTS = 10_000_000
+GRID = 128
+METRIC = "NLL evals/s (events/s) FP64 plain vs FP32+grad; toy fits/s, p50/p99 latency"
+UNIT = "events/s"
+BYTES_PER_EVENT_F32 = 12   # three float32 columns
+BYTES_PER_EVENT_F64 = 24
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--events", type=int, default=N_EVENTS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=1_000_000)
+    ap.add_argument("--ref-sample", type=int, default=250_000)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+# ---------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on the host cores, on a bounded sample
+# ---------------------------------------------------------------------------------------
+def oracle_rate(cols, n_sample, min_seconds=10.0, max_evals=20):
+    import torch
+
+    import synth
+    from oracle import model as om
+    spec = synth.c2_spec(bins=GRID)
+    sample = {k: v[:n_sample] for k, v in cols.items()}
+    m = om.TreeModel(spec)
+    theta = synth.param_values(spec)
+    m.nll_grad(sample, theta)  # warm
+    t0 = time.perf_counter()
+    evals = 0
+    while evals < max_evals:
+        m.nll_grad(sample, theta)
+        evals += 1
+        if time.perf_counter() - t0 >= min_seconds:
+            break
+    dt = (time.perf_counter() - t0) / evals
+    return {"value": n_sample / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"first {n_sample:,} of {len(cols['m']):,} events of the 3D workload, FP64 NLL + autograd "
+                      f"gradient incl. the {GRID}^3 grid normalisation, {evals} evaluations, "
+                      f"{dt * 1e3:.0f} ms each"}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    import torch  # noqa: F401
+
+    import synth
+    cols = synth.gen_c2(n=args.events, seed=1710002)
+    n_sample = min(args.ref_sample, args.events)
+    rates = []
+    for _ in range(args.warmup):
+        oracle_rate(cols, n_sample, min_seconds=0.0, max_evals=1)
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        rates.append(oracle_rate(cols, n_sample, min_seconds=0.0, max_evals=1))
+    elapsed = time.perf_counter() - t_all
+    value = n_sample * args.steps / elapsed
+    base = dict(rates[-1])
+    base["value"] = value
+    base["sample"] = f"{args.steps} steps, each one FP64 NLL + gradient of the first {n_sample:,} events"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"c2_3d: {args.events:,} events (m, dE, t), 12 params, {GRID}^3 grid",
+                       "events_per_step": n_sample},
+            "cpu_baseline": base,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+# our path
+# ---------------------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1710_08826_gb300 import build
+    build()
+    from paper_1710_08826_gb300 import goo
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    spec = synth.c2_spec(bins=GRID)
+    n = args.events
+    cols = synth.gen_c2(n=n, seed=1710002 + rank)      # each rank holds its own shard (weak scaling)
+    stream = torch.cuda.Stream()                       # the library and torch share this stream
+    torch.cuda.set_stream(stream)
+    ctx = goo.Context(local_rank, stream=stream.cuda_stream)
+    ds = goo.Dataset.from_spec(ctx, spec, cols, dtype="f64")
+    model = goo.Model(ctx, spec)
+    theta = np.array(synth.param_values(spec))
+    P = len(theta)
+
+    def step(precision, grad=True):
+        if grad:
+            out = model.nll_partial(ds, 0, ds.n, theta, precision, want_grad=True)
+        else:
+            out = model.nll_partial(ds, 0, ds.n, theta, precision, want_grad=False)
+        if pg is not None:
+            t = torch.tensor(out, dtype=torch.float64, device="cuda")
+            pg.all_reduce(t)
+            out = t.cpu().numpy()
+        return out
+
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def timed(precision, grad, steps, warmup):
+        for _ in range(warmup):
+            step(precision, grad)
+        barrier()
+        ms = []
+        launches0 = ctx.launches
+        ctx.kernel_times(reset=True)
+        ctx.timing(True)
+        for _ in range(steps):
+            flush.zero_()                       # L2 flush between timed steps (not timed)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(precision, grad)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        barrier()
+        ctx.timing(False)
+        kt = ctx.kernel_times(reset=True)
+        launches = ctx.launches - launches0
+        total = sum(ms)
+        if pg is not None:
+            t = torch.tensor([total], dtype=torch.float64, device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            total = float(t.item())
+        return total, ms, kt, launches
+
+    with ClockSampler(local_rank) as clocks:
+        total_mix, ms_mix, kt_mix, launches = timed("f32", True, args.steps, args.warmup)
+        steps64 = max(3, args.steps // 5)
+        total_64, ms_64, kt_64, _ = timed("f64", False, steps64, min(args.warmup, 3))
+    clk = clocks.summary()
+
+    # parity spot check of this very configuration against the FP64 path
+    nll32 = step("f32", True)[0]
+    nll64 = step("f64", False)[0]
+
+    # ---- end-to-end through the public API: pinned host columns -> device -> NLL+grad -> host
+    host_cols = {k: torch.from_numpy(np.asarray(v, dtype=np.float32)).pin_memory() for k, v in cols.items()}
+    lo = [o[1] for o in spec["observables"]]
+    hi = [o[2] for o in spec["observables"]]
+    names = [o[0] for o in spec["observables"]]
+
+    def e2e_step():
+        d = goo.Dataset(ctx, [host_cols[k].numpy() for k in names], lo, hi, dtype="f32")
+        out = model.nll_grad(d, theta, "f32")
+        d.close()
+        return out
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    e2e_steps = max(3, args.steps // 5)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if pg is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # ---- roofline of the dominant kernel of the FP32+grad step
+    name, (cnt, kms) = max(kt_mix.items(), key=lambda kv: kv[1][1])
+    per_launch_s = kms / cnt * 1e-3
+    peak, peak_kind = measured_peaks()
+    if name.startswith("sop_nll"):
+        alg_bytes = n * BYTES_PER_EVENT_F32
+    else:
+        alg_bytes = 0
+    achieved = alg_bytes / per_launch_s / 1e9
+    roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "launch_ms": per_launch_s * 1e3,
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "kernel_share": {k: round(v[1] / max(sum(x[1] for x in kt_mix.values()), 1e-12), 4)
+                                 for k, v in kt_mix.items()}}
+
+    value = n * world * args.steps / (total_mix * 1e-3)
+    e2e_value = n * world * e2e_steps / e2e_s
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_mix / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"c2_3d: {n:,} events/GPU over (m, dE, t), signal Gauss*Gauss*Exp + background "
+                               f"Argus*Poly2*Exp, 12 free params, {GRID}^3 grid normalisation, NLL + adjoint gradient",
+                   "events_per_gpu": n, "params": P, "grid": [GRID] * 3,
+                   "precision": "FP32 per-event, compensated FP32 / double-float accumulation, FP64 final combine",
+                   "l2": "flushed between timed steps (256 MB write, not timed)",
+                   "parallelism": f"dp{world} (events sharded, partials all-reduced)" if world > 1 else "single GPU"},
+        "nll_evals_per_s": args.steps / (total_mix * 1e-3),
+        "fp64_plain": {"events_per_s": n * world * steps64 / (total_64 * 1e-3),
+                       "evals_per_s": steps64 / (total_64 * 1e-3), "ms_per_eval": total_64 / steps64,
+                       "what": "goo_nll in float64 (FP64 per-event arithmetic and grid), no gradient",
+                       "kernels_ms": {k: v[1] / v[0] for k, v in kt_64.items()}},
+        "parity_this_run": {"nll_f32": nll32, "nll_f64": nll64, "rel": abs(nll32 - nll64) / abs(nll64)},
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * BYTES_PER_EVENT_F32 + 8 * P,
+                "d2h_bytes_per_step": 8 * (2 + P), "ms_per_step": e2e_s / e2e_steps * 1e3,
+                "what": "goo_dataset_upload from pinned float32 host columns + goo_nll_grad + dataset free"},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_rate(cols, min(args.cpu_sample, n))
+    if rank == 0:
+        print(json.dumps(line))
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

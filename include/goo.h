@@ -1,0 +1,192 @@
+/*
+ * goo.h -- C ABI of the GB300 unbinned-likelihood engine.
+ *
+ * The engine evaluates a composite probability density f(x; theta) at every event of
+ * an unbinned, structure-of-arrays dataset, normalises it (closed form, midpoint grid
+ * or Monte-Carlo phase-space sample) and reduces the negative log-likelihood
+ *     NLL(theta) = - sum_i log f(x_i; theta)
+ * and its gradient with respect to theta in hand-written sm_103a kernels.
+ *
+ * Paper: GooFit 2.0 (arXiv:1710.08826).  The paper's user model is Variables
+ * (observables and parameters) feeding PDFs, combination PDFs that combine them, and a
+ * FitManager that fits the final PDF to a binned or unbinned DataSet (Fig. 1); the
+ * time of a fit is dominated by evaluating the function independently at every data
+ * point (Sec. 1).  Each call below cites the passage it restates.
+ *
+ * Conventions for every call:
+ *   - Return value: GOO_OK (0) or a negative GOO_ERR_* code.  No C++ exception crosses
+ *     this boundary.  goo_last_error() returns a thread-local message for the last
+ *     failing call on the calling thread.
+ *   - "host" pointers are CPU memory owned by the caller; "device" pointers are CUDA
+ *     global memory on the context's device.  Output pointers are host memory unless
+ *     stated otherwise, and every call is synchronous with respect to its host outputs.
+ *   - theta is a host array of n_params doubles in the order of the model's parameter
+ *     indices.  Gradients are returned for all n_params entries.
+ *   - Objects (goo_ctx, goo_dataset, goo_model) are owned by the library and released
+ *     with the matching *_free / goo_finalize call.  A dataset or model must not outlive
+ *     its context.  Calls on one context must not run concurrently from several threads.
+ */
+#ifndef GOO_H
+#define GOO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------ */
+enum {
+  GOO_OK = 0,
+  GOO_ERR_ARG = -1,             /* invalid argument (null pointer, bad size, bad node)     */
+  GOO_ERR_RANGE = -2,           /* event outside its observable's [lo, hi] at upload       */
+  GOO_ERR_CUDA = -3,            /* a CUDA runtime call failed                               */
+  GOO_ERR_OOM = -4,             /* device allocation failed or an admission budget is full  */
+  GOO_ERR_NONPOSITIVE_PDF = -5, /* f(x_i) <= 0 for some event: the NLL is +inf              */
+  GOO_ERR_TIMEOUT = -6,         /* a bounded device wait gave up                            */
+  GOO_ERR_STATE = -7,           /* call not valid in the object's current state            */
+  GOO_ERR_UNSUPPORTED = -8      /* model/normalisation combination not implemented          */
+};
+
+/* ---- precisions / column types ----------------------------------------------------- */
+enum {
+  GOO_F64 = 0, /* float64 columns; plain FP64 evaluation and accumulation                  */
+  GOO_F32 = 1  /* float32 columns; FP32 per-event evaluation, compensated FP32/double-float
+                  accumulation, FP64 final combination                                    */
+};
+
+/* ---- dataset upload flags ----------------------------------------------------------- */
+enum {
+  GOO_COPY = 0,         /* cols are host pointers; the library copies them                 */
+  GOO_BORROW_DEVICE = 1 /* cols are device pointers that must outlive the dataset         */
+};
+
+/* ---- model nodes --------------------------------------------------------------------- */
+enum {
+  GOO_OP_GAUSS = 1,  /* par[0]=mu, par[1]=sigma          exp(-(x-mu)^2/(2 sigma^2))           */
+  GOO_OP_EXPO = 2,   /* par[0]=lambda                     exp(lambda x)                        */
+  GOO_OP_POLY2 = 3,  /* par[0]=a1, par[1]=a2              1 + a1 x + a2 x^2                    */
+  GOO_OP_ARGUS = 4,  /* par[0]=m0, par[1]=c, par[2]=p     m (1-m^2/m0^2)^p exp(c(1-m^2/m0^2)) */
+  GOO_OP_PROD = 10,  /* product of the children (children on disjoint observables)        */
+  GOO_OP_ADD = 11,   /* sum_k w_k child_k / norm(child_k); par[0..K-2] = fractions,
+                        w_{K-1} = 1 - sum of the fractions                                 */
+  GOO_OP_BW = 20,    /* Breit-Wigner amplitude: par[0]=m0, par[1]=width, par[2]=Re c,
+                        par[3]=Im c; ival[0]=spin (0..2), ival[1]=pair (0:12, 1:13, 2:23) */
+  GOO_OP_NR = 21,    /* constant (non-resonant) amplitude: par[2]=Re c, par[3]=Im c       */
+  GOO_OP_COHERENT = 22 /* |sum_k c_k A_k|^2 over its BW/NR children; obs[0]=s12, obs[1]=s13;
+                          dval = {M, m1, m2, m3, r_res, r_parent}                          */
+};
+
+#define GOO_MAX_CHILD 16
+
+/* One node of the model's expression tree.  Nodes are given in post-order: every child
+ * index is smaller than its parent's, and the last node is the root.  Unused par[] and
+ * obs[] slots are -1.  Paper: basic PDFs, combination PDFs and amplitude PDFs
+ * (Fig. 1; Sec. 1). */
+typedef struct goo_node {
+  int32_t op;
+  int32_t obs[2];                 /* observable (dataset column) indices                  */
+  int32_t par[8];                 /* parameter indices into theta                         */
+  int32_t n_child;
+  int32_t child[GOO_MAX_CHILD];   /* indices of the child nodes                           */
+  int32_t ival[2];                /* integer attributes (GOO_OP_BW)                        */
+  double dval[6];                 /* real attributes (GOO_OP_COHERENT)                     */
+} goo_node;
+
+/* ---- normalisation ------------------------------------------------------------------- */
+enum {
+  GOO_NORM_ANALYTIC = 0, /* closed-form integrals of the leaves over the observable ranges */
+  GOO_NORM_GRID = 1,     /* midpoint rule per normalised component, bins[] per observable  */
+  GOO_NORM_MC = 2        /* mean of |S|^2 over a phase-space MC dataset (amplitude models) */
+};
+
+typedef struct goo_dataset goo_dataset;
+
+typedef struct goo_norm_spec {
+  int32_t kind;            /* GOO_NORM_*                                                  */
+  int32_t bins[4];         /* GRID: number of bins of observable 0..3                    */
+  const goo_dataset* mc;   /* MC: phase-space sample; borrowed, must outlive the model   */
+} goo_norm_spec;
+
+typedef struct goo_ctx goo_ctx;
+typedef struct goo_model goo_model;
+
+/* ---- context ------------------------------------------------------------------------- */
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t (for example
+ * torch.cuda.current_stream().cuda_stream) or NULL for a stream the library creates.
+ * All work of the context is ordered on that stream. */
+int goo_init(int device, void* cuda_stream, goo_ctx** out);
+int goo_finalize(goo_ctx* ctx);
+const char* goo_last_error(void);
+/* Library version string and the number of kernel launches issued so far by ctx. */
+const char* goo_version(void);
+int64_t goo_launch_count(const goo_ctx* ctx);
+/* Per-kernel timing statistics (paper Sec. 4: timing statistics in the standard output).
+ * When enabled, every kernel launch of ctx is bracketed by CUDA events on ctx's stream.
+ * goo_timing_read folds finished launches into per-kernel totals and copies up to
+ * max_entries of them: names (64 chars each, NUL-terminated), launch counts and total
+ * milliseconds; it returns the number of kernels with statistics (or a negative code),
+ * and clears the table when reset != 0.  It waits for the recorded launches to finish. */
+int goo_timing_enable(goo_ctx* ctx, int on);
+int goo_timing_read(goo_ctx* ctx, int max_entries, char* names, int64_t* counts, double* total_ms, int reset);
+
+/* ---- data (paper: DataSet, Fig. 1 and Sec. 5) ------------------------------------------------
+ * Upload `ncols` structure-of-arrays columns of n_events values each, of type `dtype`
+ * (GOO_F64 or GOO_F32).  With GOO_COPY the columns are host arrays copied to the device;
+ * with GOO_BORROW_DEVICE they are device arrays (16-byte aligned) kept by reference.
+ * lo[c], hi[c] are the limits of observable c.  Every event is range-checked on the device
+ * (Sec. 5: "runtime checks ... warn unsuspecting users who load data out of range"): if
+ * any value lies outside its [lo, hi] (or is NaN) the call fails with GOO_ERR_RANGE, no
+ * dataset is created, and *n_bad (if not NULL) receives the number of offending events.
+ * The device keeps both a float64 and a float32 copy of every column. */
+int goo_dataset_upload(goo_ctx* ctx, int ncols, const void* const* cols, int dtype,
+                       int64_t n_events, const double* lo, const double* hi, int flags,
+                       goo_dataset** out, int64_t* n_bad);
+int goo_dataset_free(goo_dataset* ds);
+int64_t goo_dataset_size(const goo_dataset* ds);
+/* Device pointer of column `col` in the given precision (for zero-copy consumers). */
+const void* goo_dataset_column(const goo_dataset* ds, int col, int dtype);
+
+/* ---- model (paper: PDFs and combination PDFs, Fig. 1 and Sec. 1) -----------------------------
+ * Build a model from `n_nodes` post-order nodes over `n_params` parameters and `n_obs`
+ * observables with limits obs_lo/obs_hi (the normalisation range).  Sum/product trees are
+ * flattened to a sum of products of leaves (at most 4 products of at most 4 leaves after
+ * flattening); a GOO_OP_COHERENT root builds an amplitude model.  The default
+ * normalisation is GOO_NORM_ANALYTIC for sum/product trees. */
+int goo_model_build(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_params, int n_obs,
+                    const double* obs_lo, const double* obs_hi, goo_model** out);
+int goo_model_set_norm(goo_model* model, const goo_norm_spec* spec);
+int goo_model_free(goo_model* model);
+/* Number of normalised components (products) of the flattened model. */
+int goo_model_components(const goo_model* model);
+
+/* ---- normalisation (a5) ---------------------------------------------------------------------
+ * Integral of each normalised component at theta, in `precision`; norms_out receives
+ * goo_model_components() doubles (for amplitude models: one value, the MC mean of |S|^2). */
+int goo_normalise(goo_model* model, const double* theta, int precision, double* norms_out);
+
+/* ---- likelihood (a1-a7; paper Sec. 1: the per-event evaluation dominates a fit) -------------- */
+int goo_nll(goo_model* model, const goo_dataset* ds, const double* theta, int precision,
+            double* nll_out);
+/* NLL and its gradient d NLL / d theta (hand-written adjoint).  grad_out: n_params doubles. */
+int goo_nll_grad(goo_model* model, const goo_dataset* ds, const double* theta, int precision,
+                 double* nll_out, double* grad_out);
+/* Per-event log f(x_i; theta) written to the device array logf_dev (n_events doubles). */
+int goo_eval_logf(goo_model* model, const goo_dataset* ds, const double* theta, int precision,
+                  double* logf_dev);
+
+/* ---- shards (paper Sec. 5: MPI divides the dataset among processes) --------------------------
+ * Partial sums over events [begin, end) of ds: out[0] = sum of -log f, out[1] = its
+ * compensation term, out[2] = number of events, out[3 .. 3+n_params) = gradient partials
+ * (zero unless want_grad).  The normalisation is computed in full by every shard.
+ * goo_combine_partials adds n_parts such records (stride 3+n_params) in index order with
+ * compensated arithmetic into out (same layout); nll = out[0] + out[1]. */
+int goo_nll_partial(goo_model* model, const goo_dataset* ds, int64_t begin, int64_t end,
+                    const double* theta, int precision, int want_grad, double* out);
+int goo_combine_partials(int n_parts, int n_params, const double* parts, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GOO_H */

@@ -40,7 +40,7 @@ def expo_shape(x, lam):
 
 
 def expo_integral(lo, hi, lam):
-    if float(lam) == 0.0:
+    if float(torch.as_tensor(lam).detach()) == 0.0:
         return torch.as_tensor(hi - lo, dtype=torch.float64) + 0.0 * lam
     # (exp(lam hi) - exp(lam lo)) / lam, written with expm1 so that it stays accurate
     # as lam -> 0.

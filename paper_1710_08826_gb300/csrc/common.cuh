@@ -1,0 +1,249 @@
+// common.cuh -- shared infrastructure of the goo library: errors, context, datasets,
+// double-float (float hi + float lo) arithmetic and the deterministic block / last-block
+// reductions used by every likelihood kernel.
+//
+// GB300's FP64 pipe runs at 1/64 of the FP32 rate (measured: 6.0e11 FP64 FMA/s against
+// 3.75e13 FP32 FMA/s), so cross-thread and cross-block sums are carried in double-float
+// (a pair of floats holding ~48 significant bits) rather than in FP64.  Only the final
+// combination of a few hundred numbers runs in FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "goo.h"
+
+namespace goo {
+
+// ---------------------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------------------
+int set_error(int code, const char* fmt, ...);
+int log_level();
+
+#define GOO_CUDA_TRY(expr)                                                                 \
+  do {                                                                                     \
+    cudaError_t _e = (expr);                                                               \
+    if (_e != cudaSuccess)                                                                 \
+      return ::goo::set_error(GOO_ERR_CUDA, "%s failed: %s (%s:%d)", #expr,                \
+                              cudaGetErrorString(_e), __FILE__, __LINE__);                 \
+  } while (0)
+
+#define GOO_TRY(expr)                                                                      \
+  do {                                                                                     \
+    int _rc = (expr);                                                                      \
+    if (_rc != GOO_OK) return _rc;                                                         \
+  } while (0)
+
+// ---------------------------------------------------------------------------------------
+// limits
+// ---------------------------------------------------------------------------------------
+constexpr int kMaxParams = 32;     // parameters of one model
+constexpr int kMaxObs = 4;         // observables of one model
+constexpr int kMaxComp = 4;        // products in the flattened sum of products
+constexpr int kMaxLeaf = 4;        // leaves per product
+constexpr int kMaxSlots = 64;      // reduction lanes of one kernel
+constexpr int kBlock = 256;        // threads per block of the likelihood kernels
+
+// ---------------------------------------------------------------------------------------
+// context and datasets
+// ---------------------------------------------------------------------------------------
+struct Scratch {
+  // Per-context device scratch for one likelihood evaluation: per-block partial sums in
+  // double-float, the last-block ticket counter, the non-positive-density counter and the
+  // result record.  Reused by every call on the context's stream.
+  float2* partials = nullptr;
+  size_t partials_cap = 0;          // in float2 elements
+  unsigned* counters = nullptr;     // [0]: ticket, [1]: non-positive events, [2..]: spare
+  double* result = nullptr;         // kMaxSlots + 8 doubles
+  double* theta = nullptr;          // kMaxParams doubles
+  double* host_pinned = nullptr;    // pinned staging: theta in, result out (2 x 128 doubles)
+};
+
+}  // namespace goo
+
+namespace goo {
+// Optional per-kernel timing: CUDA events recorded around each launch on the context's
+// stream, folded into per-kernel totals when the table is read.
+struct TimedLaunch {
+  const char* name;
+  cudaEvent_t start, stop;
+};
+struct KernelStat {
+  std::string name;
+  int64_t count = 0;
+  double ms = 0.0;
+};
+}  // namespace goo
+
+struct goo_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool owns_stream = false;
+  int num_sms = 0;
+  int64_t launches = 0;
+  goo::Scratch scratch;
+  bool timing = false;
+  std::vector<goo::TimedLaunch> pending;
+  std::vector<cudaEvent_t> event_pool;
+  std::vector<goo::KernelStat> stats;
+};
+
+struct goo_dataset {
+  goo_ctx* ctx = nullptr;
+  int64_t n = 0;
+  int ncols = 0;
+  double* d64[goo::kMaxObs] = {nullptr, nullptr, nullptr, nullptr};
+  float* d32[goo::kMaxObs] = {nullptr, nullptr, nullptr, nullptr};
+  bool owns64 = true, owns32 = true;
+  double lo[goo::kMaxObs] = {0, 0, 0, 0};
+  double hi[goo::kMaxObs] = {0, 0, 0, 0};
+  // amplitude-model cache attached to this dataset (built lazily by the Dalitz path)
+  void* amp_cache = nullptr;
+  size_t amp_cache_bytes = 0;
+  uint64_t amp_cache_key = 0;
+};
+
+namespace goo {
+
+int ensure_partials(goo_ctx* ctx, size_t n_float2);
+
+// Brackets one kernel launch: counts it and, when timing is on, records CUDA events
+// around it on the context's stream.
+struct LaunchScope {
+  goo_ctx* ctx;
+  const char* name;
+  cudaEvent_t start = nullptr, stop = nullptr;
+  LaunchScope(goo_ctx* c, const char* n);
+  ~LaunchScope();
+};
+int grid_blocks(goo_ctx* ctx, int64_t work_items, int blocks_per_sm);
+
+// ---------------------------------------------------------------------------------------
+// double-float arithmetic (Dekker / Knuth two-sum); every operation is exact up to the
+// final renormalisation, giving ~2^-48 relative precision.
+// ---------------------------------------------------------------------------------------
+struct ddf {
+  float hi, lo;
+};
+
+__device__ __forceinline__ ddf dd_make(float hi, float lo) {
+  float s = hi + lo;
+  float e = lo - (s - hi);
+  return {s, e};
+}
+
+__device__ __forceinline__ ddf dd_add(ddf a, ddf b) {
+  float s = a.hi + b.hi;
+  float v = s - a.hi;
+  float e = (a.hi - (s - v)) + (b.hi - v);
+  e += a.lo + b.lo;
+  float h = s + e;
+  return {h, e - (h - s)};
+}
+
+__device__ __forceinline__ ddf dd_from_double(double x) {
+  float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+
+__device__ __forceinline__ double dd_to_double(ddf a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ ddf dd_shfl_xor(ddf a, int m) {
+  return {__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
+}
+
+__device__ __forceinline__ ddf dd_warp_sum(ddf v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v = dd_add(v, dd_shfl_xor(v, m));
+  return v;
+}
+
+// Kahan-compensated FP32 accumulator (the per-thread NLL lane of the FP32 path).
+struct Kahan {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float y = x - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ ddf value() const { return dd_make(s, -c); }
+};
+
+// ---------------------------------------------------------------------------------------
+// Block reduction of `nslots` double-float lanes held per thread in `v[]` (compile-time
+// count NS, runtime count nslots <= NS).  Lane results of block b go to
+// partials[b * nslots + s].  Fixed order: warp xor-tree, then warps in index order.
+// ---------------------------------------------------------------------------------------
+template <int NS>
+__device__ __forceinline__ void block_reduce_to_partials(ddf (&v)[NS], int nslots, float2* partials,
+                                                         ddf* smem /* [kBlock/32][NS] */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    if (s < nslots) {
+      ddf w = dd_warp_sum(v[s]);
+      if (lane == 0) smem[warp * NS + s] = w;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < nslots) {
+    ddf acc = smem[threadIdx.x];
+    for (int w = 1; w < nwarps; ++w) acc = dd_add(acc, smem[w * NS + threadIdx.x]);
+    partials[(size_t)blockIdx.x * nslots + threadIdx.x] = make_float2(acc.hi, acc.lo);
+  }
+}
+
+// After every block has written its partials: take a ticket; the block that draws the
+// last ticket reduces partials[0 .. nblocks) lane by lane (blocks in index order within
+// each of the block's threads, then a fixed xor tree) into out[s] (FP64).  Returns true
+// in the last block.  The ticket counter is reset by the last block.
+__device__ __forceinline__ bool last_block_reduce(const float2* partials, int nslots, int nblocks,
+                                                  unsigned* ticket, double* out, ddf* smem) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == (unsigned)(nblocks - 1));
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  // Each lane s is summed by `per` consecutive threads (per = a power of two): thread g of
+  // the group adds blocks g, g + per, ...; the group is then combined by an xor tree (and,
+  // for groups wider than a warp, by the warps in index order).
+  int per = 1;
+  while (per * 2 * nslots <= (int)blockDim.x) per *= 2;
+  const int s = threadIdx.x / per, g = threadIdx.x % per;
+  ddf acc = {0.f, 0.f};
+  if (s < nslots) {
+    for (int b = g; b < nblocks; b += per) {
+      float2 p = __ldcg(partials + (size_t)b * nslots + s);
+      acc = dd_add(acc, {p.x, p.y});
+    }
+  }
+  const int wper = per < 32 ? per : 32;
+  for (int m = wper / 2; m > 0; m >>= 1) acc = dd_add(acc, dd_shfl_xor(acc, m));
+  if (per <= 32) {
+    if (g == 0 && s < nslots) out[s] = dd_to_double(acc);
+  } else {
+    if ((threadIdx.x & 31) == 0) smem[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if ((int)threadIdx.x < nslots) {
+      const int w0 = threadIdx.x * (per / 32);
+      ddf tot = smem[w0];
+      for (int k = 1; k < per / 32; ++k) tot = dd_add(tot, smem[w0 + k]);
+      out[threadIdx.x] = dd_to_double(tot);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+}  // namespace goo

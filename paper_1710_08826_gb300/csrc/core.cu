@@ -1,0 +1,390 @@
+// core.cu -- context, error reporting, dataset upload with the on-device range check,
+// and the host combination of shard partials.
+//
+// Paper: DataSets attach event data to observables (Fig. 1); input is range-checked so
+// that users who load data out of range are warned (Sec. 5); MPI runs divide the dataset
+// among processes and sum their partial results (Sec. 5).
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace goo {
+
+static thread_local std::string g_last_error;
+
+int log_level() {
+  static int level = [] {
+    const char* s = std::getenv("GOO_LOG");
+    return s ? std::atoi(s) : 0;
+  }();
+  return level;
+}
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  if (log_level() >= 1) std::fprintf(stderr, "[goo] error %d: %s\n", code, buf);
+  return code;
+}
+
+int ensure_partials(goo_ctx* ctx, size_t n_float2) {
+  Scratch& s = ctx->scratch;
+  if (n_float2 <= s.partials_cap) return GOO_OK;
+  if (s.partials) cudaFree(s.partials);
+  s.partials = nullptr;
+  s.partials_cap = 0;
+  size_t cap = n_float2 < 65536 ? 65536 : n_float2;
+  if (cudaMalloc(&s.partials, cap * sizeof(float2)) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(GOO_ERR_OOM, "cannot allocate %zu reduction partials", cap);
+  }
+  s.partials_cap = cap;
+  return GOO_OK;
+}
+
+static cudaEvent_t pool_event(goo_ctx* ctx) {
+  if (!ctx->event_pool.empty()) {
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+LaunchScope::LaunchScope(goo_ctx* c, const char* n) : ctx(c), name(n) {
+  ctx->launches++;
+  if (ctx->timing) {
+    start = pool_event(ctx);
+    stop = pool_event(ctx);
+    if (start) cudaEventRecord(start, ctx->stream);
+  }
+}
+
+LaunchScope::~LaunchScope() {
+  if (start && stop) {
+    cudaEventRecord(stop, ctx->stream);
+    ctx->pending.push_back({name, start, stop});
+  }
+}
+
+static void fold_timings(goo_ctx* ctx) {
+  for (auto& p : ctx->pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.stop) == cudaSuccess && cudaEventElapsedTime(&ms, p.start, p.stop) == cudaSuccess) {
+      KernelStat* st = nullptr;
+      for (auto& s : ctx->stats)
+        if (s.name == p.name) st = &s;
+      if (!st) {
+        ctx->stats.push_back(KernelStat{p.name, 0, 0.0});
+        st = &ctx->stats.back();
+      }
+      st->count++;
+      st->ms += ms;
+    }
+    cudaGetLastError();
+    ctx->event_pool.push_back(p.start);
+    ctx->event_pool.push_back(p.stop);
+  }
+  ctx->pending.clear();
+}
+
+int grid_blocks(goo_ctx* ctx, int64_t work_items, int blocks_per_sm) {
+  int64_t need = (work_items + kBlock - 1) / kBlock;
+  int64_t cap = (int64_t)ctx->num_sms * blocks_per_sm;
+  if (need < 1) need = 1;
+  return (int)(need < cap ? need : cap);
+}
+
+// ---------------------------------------------------------------------------------------
+// dataset kernels
+// ---------------------------------------------------------------------------------------
+__global__ void convert_f64_to_f32(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+__global__ void convert_f32_to_f64(const float* __restrict__ in, double* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+
+struct RangeArgs {
+  const double* col[kMaxObs];
+  double lo[kMaxObs], hi[kMaxObs];
+  int ncols;
+};
+
+// Counts events with any column outside [lo, hi] (NaN counts as outside).  One integer
+// atomic per block: the count is exact and order-independent.
+__global__ void range_check_kernel(RangeArgs a, int64_t n, unsigned long long* bad) {
+  unsigned local = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    bool ok = true;
+    for (int c = 0; c < a.ncols; ++c) {
+      double v = a.col[c][i];
+      ok = ok && (v >= a.lo[c]) && (v <= a.hi[c]);
+    }
+    local += ok ? 0u : 1u;
+  }
+  for (int m = 16; m > 0; m >>= 1) local += __shfl_xor_sync(0xffffffffu, local, m);
+  __shared__ unsigned warp_sum[32];
+  if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = local;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += warp_sum[w];
+    if (t) atomicAdd(bad, t);
+  }
+}
+
+static void free_dataset_memory(goo_dataset* ds) {
+  for (int c = 0; c < kMaxObs; ++c) {
+    if (ds->d64[c] && ds->owns64) cudaFree(ds->d64[c]);
+    if (ds->d32[c] && ds->owns32) cudaFree(ds->d32[c]);
+    ds->d64[c] = nullptr;
+    ds->d32[c] = nullptr;
+  }
+  if (ds->amp_cache) cudaFree(ds->amp_cache);
+  ds->amp_cache = nullptr;
+}
+
+}  // namespace goo
+
+using namespace goo;
+
+extern "C" {
+
+const char* goo_last_error(void) { return g_last_error.c_str(); }
+
+const char* goo_version(void) { return "goo-gb300 0.1 (sm_103a)"; }
+
+int64_t goo_launch_count(const goo_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int goo_timing_enable(goo_ctx* ctx, int on) {
+  if (!ctx) return set_error(GOO_ERR_ARG, "goo_timing_enable: NULL context");
+  fold_timings(ctx);
+  ctx->timing = on != 0;
+  return GOO_OK;
+}
+
+int goo_timing_read(goo_ctx* ctx, int max_entries, char* names, int64_t* counts, double* total_ms, int reset) {
+  if (!ctx || max_entries < 0 || (max_entries > 0 && (!names || !counts || !total_ms)))
+    return set_error(GOO_ERR_ARG, "goo_timing_read: bad arguments");
+  fold_timings(ctx);
+  const int n = (int)ctx->stats.size();
+  for (int i = 0; i < n && i < max_entries; ++i) {
+    std::snprintf(names + 64 * i, 64, "%s", ctx->stats[i].name.c_str());
+    counts[i] = ctx->stats[i].count;
+    total_ms[i] = ctx->stats[i].ms;
+  }
+  if (reset) ctx->stats.clear();
+  return n;
+}
+
+int goo_init(int device, void* cuda_stream, goo_ctx** out) {
+  if (!out) return set_error(GOO_ERR_ARG, "goo_init: out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  GOO_CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return set_error(GOO_ERR_ARG, "goo_init: device %d of %d", device, ndev);
+  GOO_CUDA_TRY(cudaSetDevice(device));
+  goo_ctx* ctx = new goo_ctx();
+  ctx->device = device;
+  GOO_CUDA_TRY(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
+  if (cuda_stream) {
+    ctx->stream = (cudaStream_t)cuda_stream;
+  } else {
+    GOO_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+    ctx->owns_stream = true;
+  }
+  Scratch& s = ctx->scratch;
+  GOO_CUDA_TRY(cudaMalloc(&s.counters, 64 * sizeof(unsigned)));
+  GOO_CUDA_TRY(cudaMemset(s.counters, 0, 64 * sizeof(unsigned)));
+  GOO_CUDA_TRY(cudaMalloc(&s.result, (kMaxSlots + 64) * sizeof(double)));
+  GOO_CUDA_TRY(cudaMalloc(&s.theta, 2 * kMaxParams * sizeof(double)));
+  GOO_CUDA_TRY(cudaMallocHost(&s.host_pinned, 256 * sizeof(double)));
+  int rc = ensure_partials(ctx, 65536);
+  if (rc != GOO_OK) {
+    goo_finalize(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return GOO_OK;
+}
+
+int goo_finalize(goo_ctx* ctx) {
+  if (!ctx) return set_error(GOO_ERR_ARG, "goo_finalize: NULL context");
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  Scratch& s = ctx->scratch;
+  if (s.partials) cudaFree(s.partials);
+  if (s.counters) cudaFree(s.counters);
+  if (s.result) cudaFree(s.result);
+  if (s.theta) cudaFree(s.theta);
+  if (s.host_pinned) cudaFreeHost(s.host_pinned);
+  fold_timings(ctx);
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  if (ctx->owns_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return GOO_OK;
+}
+
+int goo_dataset_upload(goo_ctx* ctx, int ncols, const void* const* cols, int dtype, int64_t n_events,
+                       const double* lo, const double* hi, int flags, goo_dataset** out, int64_t* n_bad) {
+  if (n_bad) *n_bad = 0;
+  if (!ctx || !cols || !lo || !hi || !out) return set_error(GOO_ERR_ARG, "goo_dataset_upload: NULL argument");
+  *out = nullptr;
+  if (ncols < 1 || ncols > kMaxObs) return set_error(GOO_ERR_ARG, "goo_dataset_upload: ncols=%d (1..%d)", ncols, kMaxObs);
+  if (n_events < 0) return set_error(GOO_ERR_ARG, "goo_dataset_upload: n_events=%lld", (long long)n_events);
+  if (dtype != GOO_F64 && dtype != GOO_F32) return set_error(GOO_ERR_ARG, "goo_dataset_upload: dtype=%d", dtype);
+  if (flags != GOO_COPY && flags != GOO_BORROW_DEVICE) return set_error(GOO_ERR_ARG, "goo_dataset_upload: flags=%d", flags);
+  for (int c = 0; c < ncols; ++c) {
+    if (!(lo[c] < hi[c])) return set_error(GOO_ERR_ARG, "goo_dataset_upload: column %d has lo >= hi", c);
+    if (n_events > 0 && !cols[c]) return set_error(GOO_ERR_ARG, "goo_dataset_upload: column %d is NULL", c);
+    if (flags == GOO_BORROW_DEVICE && ((uintptr_t)cols[c] & 15))
+      return set_error(GOO_ERR_ARG, "goo_dataset_upload: borrowed column %d is not 16-byte aligned", c);
+  }
+  GOO_CUDA_TRY(cudaSetDevice(ctx->device));
+  goo_dataset* ds = new goo_dataset();
+  ds->ctx = ctx;
+  ds->n = n_events;
+  ds->ncols = ncols;
+  ds->owns64 = !(flags == GOO_BORROW_DEVICE && dtype == GOO_F64);
+  ds->owns32 = !(flags == GOO_BORROW_DEVICE && dtype == GOO_F32);
+  const size_t n_alloc = (size_t)(n_events > 0 ? n_events : 1) + 4;  // +4: room for vector tails
+  auto fail = [&](int code, const char* what) {
+    cudaGetLastError();
+    free_dataset_memory(ds);
+    delete ds;
+    return set_error(code, "goo_dataset_upload: %s", what);
+  };
+  for (int c = 0; c < ncols; ++c) {
+    ds->lo[c] = lo[c];
+    ds->hi[c] = hi[c];
+    if (dtype == GOO_F64) {
+      if (flags == GOO_BORROW_DEVICE) {
+        ds->d64[c] = (double*)cols[c];
+      } else {
+        if (cudaMalloc(&ds->d64[c], n_alloc * sizeof(double)) != cudaSuccess) return fail(GOO_ERR_OOM, "out of device memory");
+        if (n_events && cudaMemcpyAsync(ds->d64[c], cols[c], n_events * sizeof(double), cudaMemcpyHostToDevice,
+                                        ctx->stream) != cudaSuccess)
+          return fail(GOO_ERR_CUDA, "host-to-device copy failed");
+      }
+      if (cudaMalloc(&ds->d32[c], n_alloc * sizeof(float)) != cudaSuccess) return fail(GOO_ERR_OOM, "out of device memory");
+      if (n_events) {
+        LaunchScope ls(ctx, "convert_f64_to_f32");
+        convert_f64_to_f32<<<grid_blocks(ctx, n_events, 8), kBlock, 0, ctx->stream>>>(ds->d64[c], ds->d32[c], n_events);
+      }
+    } else {
+      if (flags == GOO_BORROW_DEVICE) {
+        ds->d32[c] = (float*)cols[c];
+      } else {
+        if (cudaMalloc(&ds->d32[c], n_alloc * sizeof(float)) != cudaSuccess) return fail(GOO_ERR_OOM, "out of device memory");
+        if (n_events && cudaMemcpyAsync(ds->d32[c], cols[c], n_events * sizeof(float), cudaMemcpyHostToDevice,
+                                        ctx->stream) != cudaSuccess)
+          return fail(GOO_ERR_CUDA, "host-to-device copy failed");
+      }
+      if (cudaMalloc(&ds->d64[c], n_alloc * sizeof(double)) != cudaSuccess) return fail(GOO_ERR_OOM, "out of device memory");
+      if (n_events) {
+        LaunchScope ls(ctx, "convert_f32_to_f64");
+        convert_f32_to_f64<<<grid_blocks(ctx, n_events, 8), kBlock, 0, ctx->stream>>>(ds->d32[c], ds->d64[c], n_events);
+      }
+    }
+  }
+  if (n_events > 0) {
+    RangeArgs ra{};
+    ra.ncols = ncols;
+    for (int c = 0; c < ncols; ++c) {
+      ra.col[c] = ds->d64[c];
+      ra.lo[c] = lo[c];
+      ra.hi[c] = hi[c];
+    }
+    unsigned long long* bad = (unsigned long long*)(ctx->scratch.counters + 8);
+    if (cudaMemsetAsync(bad, 0, sizeof(unsigned long long), ctx->stream) != cudaSuccess)
+      return fail(GOO_ERR_CUDA, "memset failed");
+    {
+      LaunchScope ls(ctx, "range_check");
+      range_check_kernel<<<grid_blocks(ctx, n_events, 8), kBlock, 0, ctx->stream>>>(ra, n_events, bad);
+    }
+    unsigned long long nb = 0;
+    if (cudaMemcpyAsync(&nb, bad, sizeof nb, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+      return fail(GOO_ERR_CUDA, "range check failed");
+    if (nb) {
+      if (n_bad) *n_bad = (int64_t)nb;
+      free_dataset_memory(ds);
+      delete ds;
+      return set_error(GOO_ERR_RANGE, "goo_dataset_upload: %llu of %lld events lie outside the observable limits",
+                       nb, (long long)n_events);
+    }
+  } else {
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return fail(GOO_ERR_CUDA, "stream sync failed");
+  }
+  *out = ds;
+  return GOO_OK;
+}
+
+int goo_dataset_free(goo_dataset* ds) {
+  if (!ds) return set_error(GOO_ERR_ARG, "goo_dataset_free: NULL dataset");
+  cudaSetDevice(ds->ctx->device);
+  cudaStreamSynchronize(ds->ctx->stream);
+  free_dataset_memory(ds);
+  delete ds;
+  return GOO_OK;
+}
+
+int64_t goo_dataset_size(const goo_dataset* ds) { return ds ? ds->n : -1; }
+
+const void* goo_dataset_column(const goo_dataset* ds, int col, int dtype) {
+  if (!ds || col < 0 || col >= ds->ncols) return nullptr;
+  return dtype == GOO_F32 ? (const void*)ds->d32[col] : (const void*)ds->d64[col];
+}
+
+// Compensated (two-sum) addition of shard records in index order.
+int goo_combine_partials(int n_parts, int n_params, const double* parts, double* out) {
+  if (n_parts < 0 || n_params < 0 || (n_parts && !parts) || !out)
+    return set_error(GOO_ERR_ARG, "goo_combine_partials: bad arguments");
+  const int stride = 3 + n_params;
+  double s = 0.0, c = 0.0, cnt = 0.0;
+  std::vector<double> g(n_params, 0.0), gc(n_params, 0.0);
+  auto two_sum = [](double a, double b, double& err) {
+    double t = a + b;
+    double v = t - a;
+    err = (a - (t - v)) + (b - v);
+    return t;
+  };
+  for (int p = 0; p < n_parts; ++p) {
+    const double* r = parts + (size_t)p * stride;
+    double e1, e2;
+    s = two_sum(s, r[0], e1);
+    c += e1 + r[1];
+    (void)e2;
+    cnt += r[2];
+    for (int j = 0; j < n_params; ++j) {
+      double e;
+      g[j] = two_sum(g[j], r[3 + j], e);
+      gc[j] += e;
+    }
+  }
+  double e;
+  double hi = two_sum(s, c, e);
+  out[0] = hi;
+  out[1] = e;
+  out[2] = cnt;
+  for (int j = 0; j < n_params; ++j) out[3 + j] = g[j] + gc[j];
+  return GOO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// model.cuh -- device-side layout of a flattened sum-of-products model and the library's
+// model object.
+#pragma once
+
+#include "common.cuh"
+
+namespace goo {
+
+constexpr int kMaxAdd = 8;
+
+struct LeafDev {
+  int op, col;
+  int par[3];          // parameter indices (-1: unused)
+  int pad;
+  float f[6];          // FP32 constants (offsets as hi/lo pairs)
+  double d[6];         // FP64 constants
+};
+
+struct CompDev {
+  int n_leaf, n_fac;
+  int fac_add[8], fac_pos[8];      // weight = product of ADD factors (add index, child position)
+  float off_hi, off_lo;            // -log N_k as float hi + lo
+  float w_hi, w_lo;                // w_k as float hi + lo
+  float a_ref_hi, a_ref_lo;        // grid reference exponent
+  double w, log_norm, a_ref;
+};
+
+struct AddDev {
+  int n_child;
+  int frac[GOO_MAX_CHILD];
+};
+
+struct GridDev {
+  int ndim;
+  int bins[kMaxObs];
+  int dim_of_col[kMaxObs];         // grid dimension of each observable (-1: not used)
+  float h_hi[kMaxObs], h_lo[kMaxObs], lo_hi[kMaxObs], lo_lo[kMaxObs];
+  double h64[kMaxObs], lo64[kMaxObs];
+  double cell_volume;
+};
+
+struct ModelDev {
+  int nK, n_obs, n_params, norm_kind, n_add;
+  double lo[kMaxObs], hi[kMaxObs];
+  CompDev comp[kMaxComp];
+  LeafDev leaf[kMaxComp * kMaxLeaf];   // leaf l of product k at [k * kMaxLeaf + l]
+  AddDev add[kMaxAdd];
+  GridDev grid[kMaxComp];
+  double dw[kMaxComp][kMaxParams];     // d w_k / d theta_p
+  double dlogN[kMaxComp][kMaxParams];  // d log N_k / d theta_p
+};
+
+struct DalitzModel;  // amplitude models (dalitz.cu)
+
+int build_sop_model(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_params, int n_obs,
+                    const double* lo, const double* hi, goo_model* m);
+int sop_set_norm(goo_model* m, const goo_norm_spec* spec);
+int sop_prepare(goo_model* m, const double* theta_host, int precision);
+int sop_events(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int precision, bool grad,
+               int out_mode);
+int sop_eval_logf(goo_model* m, const goo_dataset* ds, int precision, double* logf_dev);
+
+int build_dalitz_model(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_params, int n_obs,
+                       const double* lo, const double* hi, goo_model* m);
+int dalitz_set_norm(goo_model* m, const goo_norm_spec* spec);
+void dalitz_free(goo_model* m);
+int dalitz_normalise(goo_model* m, const double* theta, int precision, double* norm_out);
+int dalitz_nll(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, const double* theta,
+               int precision, bool grad, double* out, int out_mode);
+int dalitz_eval_logf(goo_model* m, const goo_dataset* ds, const double* theta, int precision, double* logf_dev);
+
+}  // namespace goo
+
+struct goo_model {
+  goo_ctx* ctx = nullptr;
+  int kind = 0;  // 0: sum of products, 1: coherent amplitude sum
+  int n_params = 0, n_obs = 0;
+  double lo[goo::kMaxObs] = {0, 0, 0, 0};
+  double hi[goo::kMaxObs] = {0, 0, 0, 0};
+  goo_norm_spec norm{};
+  int max_leaf = 0;
+  goo::ModelDev host{};
+  goo::ModelDev* dev = nullptr;
+  goo::DalitzModel* dalitz = nullptr;
+};

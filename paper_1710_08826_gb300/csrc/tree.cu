@@ -1,0 +1,1205 @@
+// tree.cu -- sum/product PDF models: flattening, parameter preparation, grid
+// normalisation and the fused per-event NLL (+ adjoint gradient) kernel.
+//
+// Paper: PDFs are composed from basic PDFs by combination PDFs (Fig. 1; Sec. 1) and the
+// time of a fit goes into evaluating the function at every point of the dataset (Sec. 1).
+//
+// Model semantics (the paper prints no formulas; RooFit conventions, Sec. 1):
+//   leaf shapes       GAUSS exp(-(x-mu)^2/2s^2), EXPO exp(l x), POLY2 1+a1 x+a2 x^2,
+//                     ARGUS m u^p exp(c u) with u = 1 - m^2/m0^2 (0 for u <= 0)
+//   PROD              product of its children (disjoint observables)
+//   ADD               sum_k w_k child_k / norm(child_k), w_k = frac_k, last = 1 - sum(frac)
+// The host flattens any such tree into a sum of products
+//   f(x) = sum_k w_k U_k(x) / N_k,   U_k = product of the leaves of product k,
+// where w_k is a product of ADD fractions (or one minus their sum) and N_k is the integral
+// of U_k: the product of the leaves' closed forms (ANALYTIC) or the midpoint sum over a
+// grid of product k's observables (GRID).  This equals the recursive definition whenever
+// PROD children act on disjoint observables.
+//
+// Per event every value is carried as r * exp(a) (a "log-domain" pair) so that tiny
+// densities (far Gaussian tails, exponentials) never underflow:
+//   U_k = r_k exp(a_k),  log f = M + log S,  M = max_k (a_k - log N_k),
+//   S = sum_k w_k r_k exp(a_k - log N_k - M).
+// Adjoint gradient: with c_k = r_k exp(a_k - log N_k - M) / S (so the share of product k in
+// f is w_k c_k), the per-event derivative is
+//   d log f / d theta = sum_k [ w_k c_k d log U_k/d theta + c_k d w_k/d theta
+//                              - w_k c_k d log N_k/d theta ],
+// so the kernel only accumulates C_k = sum_i c_k and A_{k,l,j} = sum_i c_k d log U_leaf/d theta_j
+// per leaf parameter; the last block maps these lanes to d NLL / d theta in FP64.
+//
+// FP32 path precision: offsets of an observable (mu, m0), the weights w_k and the offsets
+// -log N_k are passed as float hi + lo pairs, so that FP32 rounding of a constant does not
+// bias the fit; per-event rounding is random and averages out.  Closed-form norms in the
+// FP32 path are taken at the FP32-rounded parameters the kernel actually uses, so the NLL is
+// the exact likelihood of those parameters.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "model.cuh"
+
+namespace goo {
+
+// =======================================================================================
+// parameter preparation (one warp)
+// =======================================================================================
+__device__ double gauss_log_norm(double lo, double hi, double mu, double sig, double* dmu, double* dsig) {
+  // N = sig sqrt(pi/2) [erf(b) - erf(a)], a = (lo-mu)/(sqrt2 sig), b = (hi-mu)/(sqrt2 sig)
+  const double r2 = 1.4142135623730951, c = 1.2533141373155003;  // sqrt(2), sqrt(pi/2)
+  double a = (lo - mu) / (r2 * sig), b = (hi - mu) / (r2 * sig);
+  double diff;
+  if (a > 0.0) diff = erfc(a) - erfc(b);
+  else if (b < 0.0) diff = erfc(-b) - erfc(-a);
+  else diff = erf(b) - erf(a);
+  double N = sig * c * diff;
+  double ga = exp(-a * a), gb = exp(-b * b);
+  // dN/dmu = g(lo) - g(hi);  dN/dsig = (N - [(x-mu) g(x)]_lo^hi) / sig
+  *dmu = (ga - gb) / N;
+  *dsig = (N - ((hi - mu) * gb - (lo - mu) * ga)) / (sig * N);
+  return log(N);
+}
+
+__device__ double expo_log_norm(double lo, double hi, double lam, double* dlam) {
+  const double d = hi - lo;
+  if (fabs(lam * d) < 1e-5) {
+    // N = d (1 + lam (lo+hi)/2 + ...),  d log N / d lam = mean of x + lam d^2/12 + ...
+    *dlam = 0.5 * (lo + hi) + lam * d * d / 12.0;
+    return log(d) + lam * 0.5 * (lo + hi) + lam * lam * d * d / 24.0;
+  }
+  double logN;
+  if (lam < 0.0) logN = lam * lo + log(expm1(lam * d) / lam);
+  else logN = lam * hi + log(-expm1(-lam * d) / lam);
+  // d log N / d lam = (hi e^{lam hi} - lo e^{lam lo}) / (e^{lam hi} - e^{lam lo}) - 1/lam
+  const double mean = (lam < 0.0) ? (hi * exp(lam * d) - lo) / (exp(lam * d) - 1.0)
+                                  : (hi - lo * exp(-lam * d)) / (1.0 - exp(-lam * d));
+  *dlam = mean - 1.0 / lam;
+  return logN;
+}
+
+__device__ double poly2_log_norm(double lo, double hi, double a1, double a2, double* da1, double* da2) {
+  double i1 = 0.5 * (hi * hi - lo * lo), i2 = (hi * hi * hi - lo * lo * lo) / 3.0;
+  double N = (hi - lo) + a1 * i1 + a2 * i2;
+  *da1 = i1 / N;
+  *da2 = i2 / N;
+  return log(N);
+}
+
+// Upper bound of the leaf's log-domain exponent a over [lo, hi] (grid reference scale).
+__device__ double leaf_max_exponent(int op, double lo, double hi, const double* d) {
+  if (op == GOO_OP_GAUSS) {
+    double mu = d[0], is = d[1];
+    double x = mu < lo ? lo : (mu > hi ? hi : mu);
+    double z = (x - mu) * is;
+    return -0.5 * z * z;
+  }
+  if (op == GOO_OP_EXPO) return fmax(d[0] * lo, d[0] * hi);
+  if (op == GOO_OP_ARGUS) {
+    double m0 = d[0], c = d[2], p = d[3];
+    double umax = 1.0 - lo * lo / (m0 * m0);
+    if (umax <= 0.0) return 0.0;
+    double u = (c < 0.0) ? fmin(-p / c, umax) : umax;
+    if (u <= 0.0) u = umax;
+    return p * log(u) + c * u;
+  }
+  return 0.0;
+}
+
+__global__ void prep_kernel(ModelDev* md, const double* __restrict__ theta, int precision) {
+  __shared__ double s_logN[kMaxComp * kMaxLeaf];
+  __shared__ double s_dlogN[kMaxComp * kMaxLeaf][3];
+  __shared__ double s_amax[kMaxComp * kMaxLeaf];
+  const int t = threadIdx.x;
+  const int nK = md->nK;
+  const bool f32 = precision == GOO_F32;
+  if (t < kMaxComp * kMaxLeaf) {
+    const int k = t / kMaxLeaf, l = t % kMaxLeaf;
+    s_logN[t] = 0.0;
+    s_dlogN[t][0] = s_dlogN[t][1] = s_dlogN[t][2] = 0.0;
+    s_amax[t] = 0.0;
+    if (k < nK && l < md->comp[k].n_leaf) {
+      LeafDev& L = md->leaf[t];
+      const double lo = md->lo[L.col], hi = md->hi[L.col];
+      double p0 = L.par[0] >= 0 ? theta[L.par[0]] : 0.0;
+      double p1 = L.par[1] >= 0 ? theta[L.par[1]] : 0.0;
+      double p2 = L.par[2] >= 0 ? theta[L.par[2]] : 0.0;
+      for (int i = 0; i < 6; ++i) {
+        L.d[i] = 0.0;
+        L.f[i] = 0.f;
+      }
+      double logN = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+      switch (L.op) {
+        case GOO_OP_GAUSS: {
+          L.d[0] = p0;
+          L.d[1] = 1.0 / p1;
+          float hi32 = (float)p0;
+          L.f[0] = hi32;
+          L.f[1] = (float)(p0 - (double)hi32);
+          L.f[2] = (float)(1.0 / p1);
+          double mu = f32 ? (double)L.f[0] + (double)L.f[1] : p0;
+          double sg = f32 ? 1.0 / (double)L.f[2] : p1;
+          logN = gauss_log_norm(lo, hi, mu, sg, &g0, &g1);
+          s_amax[t] = leaf_max_exponent(L.op, lo, hi, L.d);
+          break;
+        }
+        case GOO_OP_EXPO: {
+          L.d[0] = p0;
+          L.f[0] = (float)p0;
+          double lam = f32 ? (double)L.f[0] : p0;
+          logN = expo_log_norm(lo, hi, lam, &g0);
+          s_amax[t] = leaf_max_exponent(L.op, lo, hi, L.d);
+          break;
+        }
+        case GOO_OP_POLY2: {
+          L.d[0] = p0;
+          L.d[1] = p1;
+          L.f[0] = (float)p0;
+          L.f[1] = (float)p1;
+          double a1 = f32 ? (double)L.f[0] : p0, a2 = f32 ? (double)L.f[1] : p1;
+          logN = poly2_log_norm(lo, hi, a1, a2, &g0, &g1);
+          break;
+        }
+        case GOO_OP_ARGUS: {
+          L.d[0] = p0;
+          L.d[1] = 1.0 / (p0 * p0);
+          L.d[2] = p1;
+          L.d[3] = p2;
+          L.d[4] = 2.0 / p0;
+          float hi32 = (float)p0;
+          L.f[0] = hi32;
+          L.f[1] = (float)(p0 - (double)hi32);
+          L.f[2] = (float)(1.0 / (p0 * p0));
+          L.f[3] = (float)p1;
+          L.f[4] = (float)p2;
+          L.f[5] = (float)(2.0 / p0);
+          s_amax[t] = leaf_max_exponent(L.op, lo, hi, L.d);
+          break;
+        }
+        default:
+          break;
+      }
+      s_logN[t] = logN;
+      s_dlogN[t][0] = g0;
+      s_dlogN[t][1] = g1;
+      s_dlogN[t][2] = g2;
+    }
+  }
+  __syncthreads();
+  if (t < kMaxComp) {
+    const int k = t;
+    for (int p = 0; p < kMaxParams; ++p) {
+      md->dw[k][p] = 0.0;
+      if (md->norm_kind == GOO_NORM_ANALYTIC) md->dlogN[k][p] = 0.0;
+    }
+    if (k < nK) {
+      CompDev& C = md->comp[k];
+      // weight: product of ADD factors
+      double w = 1.0;
+      for (int f = 0; f < C.n_fac; ++f) {
+        const AddDev& A = md->add[C.fac_add[f]];
+        double v;
+        if (C.fac_pos[f] < A.n_child - 1) {
+          v = theta[A.frac[C.fac_pos[f]]];
+        } else {
+          v = 1.0;
+          for (int j = 0; j < A.n_child - 1; ++j) v -= theta[A.frac[j]];
+        }
+        w *= v;
+      }
+      // dw/dtheta: product rule over the factors
+      for (int f = 0; f < C.n_fac; ++f) {
+        const AddDev& A = md->add[C.fac_add[f]];
+        double rest = 1.0;
+        for (int g = 0; g < C.n_fac; ++g) {
+          if (g == f) continue;
+          const AddDev& B = md->add[C.fac_add[g]];
+          double v;
+          if (C.fac_pos[g] < B.n_child - 1) {
+            v = theta[B.frac[C.fac_pos[g]]];
+          } else {
+            v = 1.0;
+            for (int j = 0; j < B.n_child - 1; ++j) v -= theta[B.frac[j]];
+          }
+          rest *= v;
+        }
+        if (C.fac_pos[f] < A.n_child - 1) {
+          md->dw[k][A.frac[C.fac_pos[f]]] += rest;
+        } else {
+          for (int j = 0; j < A.n_child - 1; ++j) md->dw[k][A.frac[j]] -= rest;
+        }
+      }
+      C.w = w;
+      float wh = (float)w;
+      C.w_hi = wh;
+      C.w_lo = (float)(w - (double)wh);
+      double amax = 0.0;
+      for (int l = 0; l < C.n_leaf; ++l) amax += s_amax[k * kMaxLeaf + l];
+      C.a_ref = amax;
+      float ah = (float)amax;
+      C.a_ref_hi = ah;
+      C.a_ref_lo = (float)(amax - (double)ah);
+      if (md->norm_kind == GOO_NORM_ANALYTIC) {
+        double logN = 0.0;
+        for (int l = 0; l < C.n_leaf; ++l) {
+          const int li = k * kMaxLeaf + l;
+          logN += s_logN[li];
+          const LeafDev& L = md->leaf[li];
+          for (int j = 0; j < 3; ++j)
+            if (L.par[j] >= 0) md->dlogN[k][L.par[j]] += s_dlogN[li][j];
+        }
+        C.log_norm = logN;
+        float oh = (float)(-logN);
+        C.off_hi = oh;
+        C.off_lo = (float)(-logN - (double)oh);
+      }
+    }
+  }
+}
+
+// =======================================================================================
+// leaf evaluation: value r * exp(a) and, separately, d log(leaf) / d par_j
+// (pass 1 of the event kernel needs only values; pass 2 recomputes the cheap derivatives
+// once the share of the leaf's product is known, instead of keeping them in registers)
+// =======================================================================================
+template <bool HasLo>
+__device__ __forceinline__ void leaf_val_f32(const LeafDev& L, float x, float xlo, float& r, float& a) {
+  const float* f = L.f;
+  switch (L.op) {
+    case GOO_OP_GAUSS: {
+      float dx = (x - f[0]);
+      dx = HasLo ? dx + (xlo - f[1]) : dx - f[1];
+      float z = dx * f[2];
+      r = 1.f;
+      a = -0.5f * z * z;
+      break;
+    }
+    case GOO_OP_EXPO:
+      r = 1.f;
+      a = HasLo ? fmaf(f[0], x, f[0] * xlo) : f[0] * x;
+      break;
+    case GOO_OP_POLY2: {
+      float xx = HasLo ? x + xlo : x;
+      r = fmaf(xx, fmaf(f[1], xx, f[0]), 1.f);
+      a = 0.f;
+      break;
+    }
+    case GOO_OP_ARGUS: {
+      float dm = HasLo ? (f[0] - x) + (f[1] - xlo) : (f[0] - x) + f[1];
+      float sm = HasLo ? (f[0] + x) + (f[1] + xlo) : (f[0] + x) + f[1];
+      float u = dm * sm * f[2];
+      if (u > 0.f) {
+        r = HasLo ? x + xlo : x;
+        a = fmaf(f[4], __logf(u), f[3] * u);
+      } else {
+        r = 0.f;
+        a = 0.f;
+      }
+      break;
+    }
+    default:
+      r = 1.f;
+      a = 0.f;
+  }
+}
+
+template <bool HasLo>
+__device__ __forceinline__ void leaf_der_f32(const LeafDev& L, float x, float xlo, float* d) {
+  const float* f = L.f;
+  switch (L.op) {
+    case GOO_OP_GAUSS: {
+      float dx = (x - f[0]);
+      dx = HasLo ? dx + (xlo - f[1]) : dx - f[1];
+      float z = dx * f[2];
+      d[0] = z * f[2];
+      d[1] = z * z * f[2];
+      d[2] = 0.f;
+      break;
+    }
+    case GOO_OP_EXPO:
+      d[0] = HasLo ? x + xlo : x;
+      d[1] = d[2] = 0.f;
+      break;
+    case GOO_OP_POLY2: {
+      float xx = HasLo ? x + xlo : x;
+      float ir = __fdividef(1.f, fmaf(xx, fmaf(f[1], xx, f[0]), 1.f));
+      d[0] = xx * ir;
+      d[1] = xx * xx * ir;
+      d[2] = 0.f;
+      break;
+    }
+    case GOO_OP_ARGUS: {
+      float dm = HasLo ? (f[0] - x) + (f[1] - xlo) : (f[0] - x) + f[1];
+      float sm = HasLo ? (f[0] + x) + (f[1] + xlo) : (f[0] + x) + f[1];
+      float u = dm * sm * f[2];
+      if (u > 0.f) {
+        d[0] = f[5] * (1.f - u) * (__fdividef(f[4], u) + f[3]);
+        d[1] = u;
+        d[2] = __logf(u);
+      } else {
+        d[0] = d[1] = d[2] = 0.f;
+      }
+      break;
+    }
+    default:
+      d[0] = d[1] = d[2] = 0.f;
+  }
+}
+
+__device__ __forceinline__ void leaf_val_f64(const LeafDev& L, double x, double& r, double& a) {
+  const double* c = L.d;
+  switch (L.op) {
+    case GOO_OP_GAUSS: {
+      double z = (x - c[0]) * c[1];
+      r = 1.0;
+      a = -0.5 * z * z;
+      break;
+    }
+    case GOO_OP_EXPO:
+      r = 1.0;
+      a = c[0] * x;
+      break;
+    case GOO_OP_POLY2:
+      r = 1.0 + x * (c[0] + c[1] * x);
+      a = 0.0;
+      break;
+    case GOO_OP_ARGUS: {
+      double u = (c[0] - x) * (c[0] + x) * c[1];
+      if (u > 0.0) {
+        r = x;
+        a = c[3] * log(u) + c[2] * u;
+      } else {
+        r = 0.0;
+        a = 0.0;
+      }
+      break;
+    }
+    default:
+      r = 1.0;
+      a = 0.0;
+  }
+}
+
+__device__ __forceinline__ void leaf_der_f64(const LeafDev& L, double x, double* d) {
+  const double* c = L.d;
+  switch (L.op) {
+    case GOO_OP_GAUSS: {
+      double z = (x - c[0]) * c[1];
+      d[0] = z * c[1];
+      d[1] = z * z * c[1];
+      d[2] = 0.0;
+      break;
+    }
+    case GOO_OP_EXPO:
+      d[0] = x;
+      d[1] = d[2] = 0.0;
+      break;
+    case GOO_OP_POLY2: {
+      double r = 1.0 + x * (c[0] + c[1] * x);
+      d[0] = x / r;
+      d[1] = x * x / r;
+      d[2] = 0.0;
+      break;
+    }
+    case GOO_OP_ARGUS: {
+      double u = (c[0] - x) * (c[0] + x) * c[1];
+      if (u > 0.0) {
+        d[0] = c[4] * (1.0 - u) * (c[3] / u + c[2]);
+        d[1] = u;
+        d[2] = log(u);
+      } else {
+        d[0] = d[1] = d[2] = 0.0;
+      }
+      break;
+    }
+    default:
+      d[0] = d[1] = d[2] = 0.0;
+  }
+}
+
+template <typename T, bool HasLo>
+__device__ __forceinline__ void leaf_val(const LeafDev& L, T x, T xlo, T& r, T& a) {
+  if constexpr (sizeof(T) == 4) leaf_val_f32<HasLo>(L, x, xlo, r, a);
+  else leaf_val_f64(L, x, r, a);
+}
+
+template <typename T, bool HasLo>
+__device__ __forceinline__ void leaf_der(const LeafDev& L, T x, T xlo, T* d) {
+  if constexpr (sizeof(T) == 4) leaf_der_f32<HasLo>(L, x, xlo, d);
+  else leaf_der_f64(L, x, d);
+}
+
+template <typename T>
+struct Cols {
+  const T* c[kMaxObs];
+};
+
+template <typename T>
+__device__ __forceinline__ T pick(int col, T x0, T x1, T x2, T x3) {
+  return col == 0 ? x0 : (col == 1 ? x1 : (col == 2 ? x2 : x3));
+}
+
+// =======================================================================================
+// fused per-event kernel: evaluate, log, accumulate (and adjoint lanes), reduce
+// Lanes: 0 = sum log f; 1..K = C_k; then A_{k,l,j} at 1 + K + (k*L + l)*3 + j.
+// =======================================================================================
+template <typename T, int K, int L, bool GRAD>
+struct EventLanes {
+  static constexpr int NS = GRAD ? 1 + K + K * L * 3 : 1;
+};
+
+template <typename T, int K, int L, bool GRAD>
+__global__ void __launch_bounds__(kBlock) sop_event_kernel(const ModelDev* __restrict__ md, Cols<T> cols,
+                                                           int64_t begin, int64_t end, float2* partials,
+                                                           unsigned* counters, double* result, int out_mode) {
+  constexpr int NS = EventLanes<T, K, L, GRAD>::NS;
+  __shared__ LeafDev s_leaf[K * L];
+  __shared__ CompDev s_comp[K];
+  __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
+  __shared__ unsigned s_bad[kBlock / 32];
+  const int nK = md->nK;
+  for (int i = threadIdx.x; i < K * L; i += blockDim.x) {
+    const int k = i / L, l = i % L;
+    if (k < kMaxComp && l < kMaxLeaf) s_leaf[i] = md->leaf[k * kMaxLeaf + l];
+  }
+  for (int i = threadIdx.x; i < K; i += blockDim.x) s_comp[i] = md->comp[i];
+  __syncthreads();
+
+  // per-thread accumulators
+  double acc64 = 0.0;
+  Kahan acc32;
+  float Cacc[K];
+  float Aacc[K][L][3];
+  double Cacc64[K];
+  double Aacc64[K][L][3];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    Cacc[k] = 0.f;
+    Cacc64[k] = 0.0;
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Aacc[k][l][j] = 0.f;
+        Aacc64[k][l][j] = 0.0;
+      }
+  }
+  unsigned bad = 0;
+  const int nobs = md->n_obs;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end; i += stride) {
+    T x0 = cols.c[0][i];
+    T x1 = nobs > 1 ? cols.c[1][i] : T(0);
+    T x2 = nobs > 2 ? cols.c[2][i] : T(0);
+    T x3 = nobs > 3 ? cols.c[3][i] : T(0);
+    T rk[K], ak[K];
+    // pass 1: values of every product, in the log domain
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      T r = T(1), a = T(0);
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        if (k < nK && l < s_comp[k].n_leaf) {
+          const LeafDev& lf = s_leaf[k * L + l];
+          T lr, la;
+          leaf_val<T, false>(lf, pick<T>(lf.col, x0, x1, x2, x3), T(0), lr, la);
+          r *= lr;
+          a += la;
+        }
+      }
+      if constexpr (sizeof(T) == 4) {
+        a = (a + s_comp[k].off_hi) + s_comp[k].off_lo;
+      } else {
+        a = a - s_comp[k].log_norm;
+      }
+      rk[k] = (k < nK) ? r : T(0);
+      ak[k] = (rk[k] != T(0)) ? a : T(-1e30);
+    }
+    T M = ak[0];
+#pragma unroll
+    for (int k = 1; k < K; ++k) M = ak[k] > M ? ak[k] : M;
+    T S = T(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if constexpr (sizeof(T) == 4) {
+        rk[k] = rk[k] * expf(ak[k] - M);
+        S += fmaf(s_comp[k].w_hi, rk[k], s_comp[k].w_lo * rk[k]);
+      } else {
+        rk[k] = rk[k] * exp(ak[k] - M);
+        S += s_comp[k].w * rk[k];
+      }
+    }
+    if (S > T(0) && M > T(-1e29)) {
+      if constexpr (sizeof(T) == 4) {
+        acc32.add(M + __logf(S));
+      } else {
+        acc64 += M + log(S);
+      }
+      if constexpr (GRAD) {
+        // pass 2: adjoint lanes
+        const T invS = T(1) / S;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const T ck = rk[k] * invS;
+          if constexpr (sizeof(T) == 4) {
+            Cacc[k] += ck;
+          } else {
+            Cacc64[k] += ck;
+          }
+#pragma unroll
+          for (int l = 0; l < L; ++l) {
+            if (k < nK && l < s_comp[k].n_leaf) {
+              const LeafDev& lf = s_leaf[k * L + l];
+              T d[3];
+              leaf_der<T, false>(lf, pick<T>(lf.col, x0, x1, x2, x3), T(0), d);
+#pragma unroll
+              for (int j = 0; j < 3; ++j) {
+                if constexpr (sizeof(T) == 4) {
+                  Aacc[k][l][j] = fmaf(ck, d[j], Aacc[k][l][j]);
+                } else {
+                  Aacc64[k][l][j] += ck * d[j];
+                }
+              }
+            }
+          }
+        }
+      }
+    } else {
+      bad++;
+    }
+  }
+
+  // ---- block reduction ----
+  ddf v[NS];
+  if constexpr (sizeof(T) == 4) {
+    v[0] = acc32.value();
+  } else {
+    v[0] = dd_from_double(acc64);
+  }
+  if constexpr (GRAD) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      v[1 + k] = (sizeof(T) == 4) ? ddf{Cacc[k], 0.f} : dd_from_double(Cacc64[k]);
+#pragma unroll
+      for (int l = 0; l < L; ++l)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          v[1 + K + (k * L + l) * 3 + j] =
+              (sizeof(T) == 4) ? ddf{Aacc[k][l][j], 0.f} : dd_from_double(Aacc64[k][l][j]);
+    }
+  }
+  for (int m = 16; m > 0; m >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, m);
+  if ((threadIdx.x & 31) == 0) s_bad[threadIdx.x >> 5] = bad;
+  block_reduce_to_partials<NS>(v, NS, partials, s_red);
+  if (threadIdx.x == 0) {
+    unsigned b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_bad[w];
+    if (b) atomicAdd(counters + 1, b);
+  }
+  __shared__ double s_out[NS];
+  if (!last_block_reduce(partials, NS, gridDim.x, counters, s_out, s_red)) return;
+
+  // ---- final combination (last block, FP64) ----
+  if (threadIdx.x == 0) {
+    const unsigned nbad = atomicAdd(counters + 1, 0u);
+    counters[1] = 0u;
+    const int P = md->n_params;
+    const double sumlogf = s_out[0];
+    double g[kMaxParams];
+    for (int p = 0; p < kMaxParams; ++p) g[p] = 0.0;
+    if (GRAD) {
+      for (int k = 0; k < nK; ++k) {
+        const double Ck = s_out[1 + k];
+        const double wk = md->comp[k].w;
+        for (int p = 0; p < P; ++p) g[p] += wk * Ck * md->dlogN[k][p] - Ck * md->dw[k][p];
+        for (int l = 0; l < md->comp[k].n_leaf && l < L; ++l) {
+          const LeafDev& lf = md->leaf[k * kMaxLeaf + l];
+          for (int j = 0; j < 3; ++j)
+            if (lf.par[j] >= 0) g[lf.par[j]] -= wk * s_out[1 + K + (k * L + l) * 3 + j];
+        }
+      }
+    }
+    if (out_mode == 0) {
+      result[0] = -sumlogf;
+      result[1] = (double)nbad;
+      for (int p = 0; p < P; ++p) result[2 + p] = g[p];
+    } else {
+      result[0] = -sumlogf;
+      result[1] = 0.0;
+      result[2] = (double)nbad;
+      for (int p = 0; p < P; ++p) result[3 + p] = g[p];
+    }
+  }
+}
+
+// =======================================================================================
+// grid normalisation: per product k, midpoint sum of U_k over the grid of its observables
+// and of U_k * d log(leaf)/d par.  Work unit: a segment of kSeg points along the last grid
+// dimension; leaves on the other observables are evaluated once per segment (they are
+// constant along it).  Lanes per product: 0 = sum U exp(-a_ref), 1 + l*3 + j = sum U d_lj.
+// =======================================================================================
+constexpr int kSeg = 16;
+
+template <typename T, int L>
+__global__ void __launch_bounds__(kBlock) grid_kernel(ModelDev* md, float2* partials, unsigned* counters) {
+  constexpr int NS = 1 + 3 * L;
+  const int k = blockIdx.y;
+  __shared__ LeafDev s_leaf[L];
+  __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
+  const CompDev& C = md->comp[k];
+  const int nleaf = C.n_leaf;
+  if (threadIdx.x < L && threadIdx.x < nleaf) s_leaf[threadIdx.x] = md->leaf[k * kMaxLeaf + threadIdx.x];
+  __syncthreads();
+  const GridDev& G = md->grid[k];
+  const int last = G.ndim - 1;
+  const int nlast = G.bins[last];
+  const int nseg = (nlast + kSeg - 1) / kSeg;
+  int64_t nrows = 1;
+  for (int d = 0; d < last; ++d) nrows *= G.bins[d];
+  const int64_t units = nrows * nseg;
+
+  T acc[NS];
+  Kahan acc_s;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) acc[s] = T(0);
+  const T aref = (sizeof(T) == 4) ? T(C.a_ref_hi) : T(C.a_ref);
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
+    int64_t row = u / nseg;
+    const int seg = (int)(u - row * nseg);
+    // coordinates of the non-last dimensions
+    T xo[kMaxObs], xo_lo[kMaxObs];
+    for (int d = last - 1; d >= 0; --d) {
+      const int64_t b = G.bins[d];
+      const int64_t idx = row % b;
+      row /= b;
+      if constexpr (sizeof(T) == 4) {
+        // x = lo + (idx + 1/2) h as a float hi + lo pair
+        const float off = (float)idx + 0.5f;
+        const float p = off * G.h_hi[d];
+        const float perr = fmaf(off, G.h_hi[d], -p) + off * G.h_lo[d];
+        ddf xs = dd_add({G.lo_hi[d], G.lo_lo[d]}, dd_make(p, perr));
+        xo[d] = xs.hi;
+        xo_lo[d] = xs.lo;
+      } else {
+        xo[d] = G.lo64[d] + ((double)idx + 0.5) * G.h64[d];
+        xo_lo[d] = 0.0;
+      }
+    }
+    // segment-invariant leaves
+    T r_row = T(1), a_row = T(0);
+    T d_row[L][3];
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      d_row[l][0] = d_row[l][1] = d_row[l][2] = T(0);
+      if (l < nleaf && G.dim_of_col[s_leaf[l].col] != last) {
+        const int dd = G.dim_of_col[s_leaf[l].col];
+        T lr, la;
+        leaf_val<T, true>(s_leaf[l], xo[dd], xo_lo[dd], lr, la);
+        leaf_der<T, true>(s_leaf[l], xo[dd], xo_lo[dd], d_row[l]);
+        r_row *= lr;
+        a_row += la;
+      }
+    }
+    T sumU = T(0);
+    T dpt[L][3];
+#pragma unroll
+    for (int l = 0; l < L; ++l) dpt[l][0] = dpt[l][1] = dpt[l][2] = T(0);
+    const int i0 = seg * kSeg;
+    const int i1 = min(nlast, i0 + kSeg);
+    for (int i = i0; i < i1; ++i) {
+      T x, xlo;
+      if constexpr (sizeof(T) == 4) {
+        const float off = (float)i + 0.5f;
+        const float p = off * G.h_hi[last];
+        const float perr = fmaf(off, G.h_hi[last], -p) + off * G.h_lo[last];
+        ddf xs = dd_add({G.lo_hi[last], G.lo_lo[last]}, dd_make(p, perr));
+        x = xs.hi;
+        xlo = xs.lo;
+      } else {
+        x = G.lo64[last] + ((double)i + 0.5) * G.h64[last];
+        xlo = 0.0;
+      }
+      T r = r_row, a = a_row;
+      T dl[L][3];
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        dl[l][0] = dl[l][1] = dl[l][2] = T(0);
+        if (l < nleaf && G.dim_of_col[s_leaf[l].col] == last) {
+          T lr, la;
+          leaf_val<T, true>(s_leaf[l], x, xlo, lr, la);
+          leaf_der<T, true>(s_leaf[l], x, xlo, dl[l]);
+          r *= lr;
+          a += la;
+        }
+      }
+      T U;
+      if constexpr (sizeof(T) == 4) {
+        U = r * expf((a - aref) - C.a_ref_lo);
+      } else {
+        U = r * exp(a - aref);
+      }
+      sumU += U;
+#pragma unroll
+      for (int l = 0; l < L; ++l)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) dpt[l][j] += U * dl[l][j];
+    }
+    if constexpr (sizeof(T) == 4) {
+      acc_s.add(sumU);
+    } else {
+      acc[0] += sumU;
+    }
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) acc[1 + l * 3 + j] += dpt[l][j] + sumU * d_row[l][j];
+  }
+  ddf v[NS];
+  v[0] = (sizeof(T) == 4) ? acc_s.value() : dd_from_double((double)acc[0]);
+#pragma unroll
+  for (int s = 1; s < NS; ++s) v[s] = (sizeof(T) == 4) ? ddf{(float)acc[s], 0.f} : dd_from_double((double)acc[s]);
+  // partials of product k occupy blocks [k * gridDim.x, (k+1) * gridDim.x)
+  const int nbx = gridDim.x;
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      ddf w = dd_warp_sum(v[s]);
+      if (lane == 0) s_red[warp * NS + s] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x < NS) {
+      ddf a = s_red[threadIdx.x];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) a = dd_add(a, s_red[w * NS + threadIdx.x]);
+      partials[((size_t)k * nbx + blockIdx.x) * NS + threadIdx.x] = make_float2(a.hi, a.lo);
+    }
+  }
+  // last block over the whole launch combines every product
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(counters, 1u) == (unsigned)(nbx * gridDim.y - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  __shared__ double s_tot[kMaxComp][NS];
+  for (int lane_id = threadIdx.x; lane_id < (int)gridDim.y * NS; lane_id += blockDim.x) {
+    const int kk = lane_id / NS, s = lane_id % NS;
+    ddf a = {0.f, 0.f};
+    for (int b = 0; b < nbx; ++b) {
+      float2 p = __ldcg(partials + ((size_t)kk * nbx + b) * NS + s);
+      a = dd_add(a, {p.x, p.y});
+    }
+    s_tot[kk][s] = dd_to_double(a);
+  }
+  __syncthreads();
+  if (threadIdx.x < (int)gridDim.y) {
+    const int kk = threadIdx.x;
+    CompDev& Ck = md->comp[kk];
+    const GridDev& Gk = md->grid[kk];
+    const double S = s_tot[kk][0];
+    const double aref_used = (sizeof(T) == 4) ? (double)Ck.a_ref_hi + (double)Ck.a_ref_lo : Ck.a_ref;
+    const double logN = log(Gk.cell_volume) + aref_used + log(S);
+    Ck.log_norm = logN;
+    float oh = (float)(-logN);
+    Ck.off_hi = oh;
+    Ck.off_lo = (float)(-logN - (double)oh);
+    for (int p = 0; p < kMaxParams; ++p) md->dlogN[kk][p] = 0.0;
+    for (int l = 0; l < Ck.n_leaf && l < L; ++l) {
+      const LeafDev& lf = md->leaf[kk * kMaxLeaf + l];
+      for (int j = 0; j < 3; ++j)
+        if (lf.par[j] >= 0) md->dlogN[kk][lf.par[j]] += s_tot[kk][1 + l * 3 + j] / S;
+    }
+  }
+  if (threadIdx.x == 0) *counters = 0u;
+}
+
+// =======================================================================================
+// per-event log f (no reduction): the product of the same evaluation as sop_event_kernel
+// =======================================================================================
+template <typename T, int K, int L>
+__global__ void __launch_bounds__(kBlock) sop_logf_kernel(const ModelDev* __restrict__ md, Cols<T> cols, int64_t n,
+                                                          double* __restrict__ logf) {
+  __shared__ LeafDev s_leaf[K * L];
+  __shared__ CompDev s_comp[K];
+  const int nK = md->nK;
+  for (int i = threadIdx.x; i < K * L; i += blockDim.x) s_leaf[i] = md->leaf[(i / L) * kMaxLeaf + (i % L)];
+  for (int i = threadIdx.x; i < K; i += blockDim.x) s_comp[i] = md->comp[i];
+  __syncthreads();
+  const int nobs = md->n_obs;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T x0 = cols.c[0][i];
+    T x1 = nobs > 1 ? cols.c[1][i] : T(0);
+    T x2 = nobs > 2 ? cols.c[2][i] : T(0);
+    T x3 = nobs > 3 ? cols.c[3][i] : T(0);
+    T rk[K], ak[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      T r = T(1), a = T(0);
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        if (k < nK && l < s_comp[k].n_leaf) {
+          const LeafDev& lf = s_leaf[k * L + l];
+          T xv = pick<T>(lf.col, x0, x1, x2, x3);
+          T lr, la;
+          leaf_val<T, false>(lf, xv, T(0), lr, la);
+          r *= lr;
+          a += la;
+        }
+      }
+      if constexpr (sizeof(T) == 4) {
+        a = (a + s_comp[k].off_hi) + s_comp[k].off_lo;
+      } else {
+        a = a - s_comp[k].log_norm;
+      }
+      rk[k] = (k < nK) ? r : T(0);
+      ak[k] = (rk[k] != T(0)) ? a : T(-1e30);
+    }
+    T M = ak[0];
+#pragma unroll
+    for (int k = 1; k < K; ++k) M = ak[k] > M ? ak[k] : M;
+    T S = T(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if constexpr (sizeof(T) == 4) {
+        float u = rk[k] * expf(ak[k] - M);
+        S += fmaf(s_comp[k].w_hi, u, s_comp[k].w_lo * u);
+      } else {
+        S += s_comp[k].w * rk[k] * exp(ak[k] - M);
+      }
+    }
+    double out;
+    if (S > T(0) && M > T(-1e29)) {
+      if constexpr (sizeof(T) == 4) out = (double)M + (double)__logf(S);
+      else out = M + log(S);
+    } else {
+      out = -HUGE_VAL;
+    }
+    logf[i] = out;
+  }
+}
+
+// =======================================================================================
+// host side
+// =======================================================================================
+struct Term {
+  std::vector<int> leaves;                 // node ids
+  std::vector<std::pair<int, int>> facs;   // (add index, child position)
+};
+
+static int flatten(const goo_node* nodes, int id, std::vector<int>& add_ids, std::vector<Term>& out) {
+  const goo_node& n = nodes[id];
+  out.clear();
+  switch (n.op) {
+    case GOO_OP_GAUSS:
+    case GOO_OP_EXPO:
+    case GOO_OP_POLY2:
+    case GOO_OP_ARGUS: {
+      Term t;
+      t.leaves.push_back(id);
+      out.push_back(t);
+      return GOO_OK;
+    }
+    case GOO_OP_PROD: {
+      std::vector<Term> acc(1);
+      for (int c = 0; c < n.n_child; ++c) {
+        std::vector<Term> sub;
+        GOO_TRY(flatten(nodes, n.child[c], add_ids, sub));
+        std::vector<Term> next;
+        for (auto& a : acc)
+          for (auto& b : sub) {
+            Term t = a;
+            t.leaves.insert(t.leaves.end(), b.leaves.begin(), b.leaves.end());
+            t.facs.insert(t.facs.end(), b.facs.begin(), b.facs.end());
+            next.push_back(t);
+          }
+        acc.swap(next);
+      }
+      out = acc;
+      return GOO_OK;
+    }
+    case GOO_OP_ADD: {
+      const int ai = (int)add_ids.size();
+      add_ids.push_back(id);
+      for (int c = 0; c < n.n_child; ++c) {
+        std::vector<Term> sub;
+        GOO_TRY(flatten(nodes, n.child[c], add_ids, sub));
+        for (auto& t : sub) {
+          t.facs.push_back({ai, c});
+          out.push_back(t);
+        }
+      }
+      return GOO_OK;
+    }
+    default:
+      return set_error(GOO_ERR_ARG, "goo_model_build: node %d has op %d, not allowed in a sum/product tree", id, n.op);
+  }
+}
+
+static int leaf_npar(int op) {
+  switch (op) {
+    case GOO_OP_GAUSS: return 2;
+    case GOO_OP_EXPO: return 1;
+    case GOO_OP_POLY2: return 2;
+    case GOO_OP_ARGUS: return 3;
+  }
+  return 0;
+}
+
+int build_sop_model(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_params, int n_obs,
+                    const double* lo, const double* hi, goo_model* m) {
+  std::vector<int> add_ids;
+  std::vector<Term> terms;
+  GOO_TRY(flatten(nodes, n_nodes - 1, add_ids, terms));
+  if ((int)terms.size() > kMaxComp)
+    return set_error(GOO_ERR_UNSUPPORTED, "goo_model_build: %zu products after flattening (max %d)", terms.size(), kMaxComp);
+  if ((int)add_ids.size() > kMaxAdd)
+    return set_error(GOO_ERR_UNSUPPORTED, "goo_model_build: %zu ADD nodes (max %d)", add_ids.size(), kMaxAdd);
+  ModelDev& h = m->host;
+  std::memset(&h, 0, sizeof h);
+  h.nK = (int)terms.size();
+  h.n_obs = n_obs;
+  h.n_params = n_params;
+  h.norm_kind = GOO_NORM_ANALYTIC;
+  for (int o = 0; o < n_obs; ++o) {
+    h.lo[o] = lo[o];
+    h.hi[o] = hi[o];
+  }
+  for (size_t a = 0; a < add_ids.size(); ++a) {
+    const goo_node& n = nodes[add_ids[a]];
+    if (n.n_child < 2 || n.n_child > GOO_MAX_CHILD)
+      return set_error(GOO_ERR_ARG, "goo_model_build: ADD node %d has %d children", add_ids[a], n.n_child);
+    h.add[a].n_child = n.n_child;
+    for (int j = 0; j < n.n_child - 1; ++j) {
+      int p = n.par[j];
+      if (j >= 8 || p < 0 || p >= n_params)
+        return set_error(GOO_ERR_ARG, "goo_model_build: ADD node %d fraction %d has parameter %d", add_ids[a], j, p);
+      h.add[a].frac[j] = p;
+    }
+  }
+  h.n_add = (int)add_ids.size();
+  int max_leaf = 0;
+  for (int k = 0; k < h.nK; ++k) {
+    const Term& t = terms[k];
+    if ((int)t.leaves.size() > kMaxLeaf)
+      return set_error(GOO_ERR_UNSUPPORTED, "goo_model_build: product %d has %zu leaves (max %d)", k, t.leaves.size(), kMaxLeaf);
+    if ((int)t.facs.size() > 8) return set_error(GOO_ERR_UNSUPPORTED, "goo_model_build: ADD nesting deeper than 8");
+    CompDev& C = h.comp[k];
+    C.n_leaf = (int)t.leaves.size();
+    max_leaf = C.n_leaf > max_leaf ? C.n_leaf : max_leaf;
+    C.n_fac = (int)t.facs.size();
+    for (int f = 0; f < C.n_fac; ++f) {
+      C.fac_add[f] = t.facs[f].first;
+      C.fac_pos[f] = t.facs[f].second;
+    }
+    for (int l = 0; l < C.n_leaf; ++l) {
+      const goo_node& n = nodes[t.leaves[l]];
+      LeafDev& L = h.leaf[k * kMaxLeaf + l];
+      L.op = n.op;
+      L.col = n.obs[0];
+      if (L.col < 0 || L.col >= n_obs)
+        return set_error(GOO_ERR_ARG, "goo_model_build: leaf node %d uses observable %d of %d", t.leaves[l], L.col, n_obs);
+      for (int j = 0; j < 3; ++j) L.par[j] = -1;
+      for (int j = 0; j < leaf_npar(n.op); ++j) {
+        if (n.par[j] < 0 || n.par[j] >= n_params)
+          return set_error(GOO_ERR_ARG, "goo_model_build: leaf node %d parameter slot %d = %d", t.leaves[l], j, n.par[j]);
+        L.par[j] = n.par[j];
+      }
+    }
+  }
+  m->max_leaf = max_leaf;
+  m->kind = 0;
+  if (cudaMalloc(&m->dev, sizeof(ModelDev)) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(GOO_ERR_OOM, "goo_model_build: cannot allocate model block");
+  }
+  GOO_CUDA_TRY(cudaMemcpyAsync(m->dev, &h, sizeof(ModelDev), cudaMemcpyHostToDevice, ctx->stream));
+  GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return GOO_OK;
+}
+
+int sop_set_norm(goo_model* m, const goo_norm_spec* spec) {
+  ModelDev& h = m->host;
+  if (spec->kind == GOO_NORM_ANALYTIC) {
+    for (int k = 0; k < h.nK; ++k)
+      for (int l = 0; l < h.comp[k].n_leaf; ++l) {
+        const LeafDev& L = h.leaf[k * kMaxLeaf + l];
+        if (L.op == GOO_OP_ARGUS)
+          return set_error(GOO_ERR_UNSUPPORTED, "goo_model_set_norm: the Argus shape has no closed-form integral; use GOO_NORM_GRID");
+        for (int l2 = 0; l2 < l; ++l2)
+          if (h.leaf[k * kMaxLeaf + l2].col == L.col)
+            return set_error(GOO_ERR_UNSUPPORTED,
+                             "goo_model_set_norm: product %d has two leaves on observable %d; use GOO_NORM_GRID", k, L.col);
+      }
+  } else if (spec->kind == GOO_NORM_GRID) {
+    for (int o = 0; o < h.n_obs; ++o)
+      if (spec->bins[o] < 1 || spec->bins[o] > (1 << 20))
+        return set_error(GOO_ERR_ARG, "goo_model_set_norm: bins[%d] = %d", o, spec->bins[o]);
+    for (int k = 0; k < h.nK; ++k) {
+      GridDev& G = h.grid[k];
+      std::memset(&G, 0, sizeof G);
+      bool used[kMaxObs] = {false, false, false, false};
+      for (int l = 0; l < h.comp[k].n_leaf; ++l) used[h.leaf[k * kMaxLeaf + l].col] = true;
+      for (int o = 0; o < kMaxObs; ++o) G.dim_of_col[o] = -1;
+      G.cell_volume = 1.0;
+      for (int o = 0; o < h.n_obs; ++o) {
+        if (!used[o]) continue;
+        const int d = G.ndim++;
+        G.dim_of_col[o] = d;
+        G.bins[d] = spec->bins[o];
+        const double step = (h.hi[o] - h.lo[o]) / spec->bins[o];
+        G.h64[d] = step;
+        G.lo64[d] = h.lo[o];
+        float hh = (float)step;
+        G.h_hi[d] = hh;
+        G.h_lo[d] = (float)(step - (double)hh);
+        float lh = (float)h.lo[o];
+        G.lo_hi[d] = lh;
+        G.lo_lo[d] = (float)(h.lo[o] - (double)lh);
+        G.cell_volume *= step;
+      }
+    }
+  } else {
+    return set_error(GOO_ERR_UNSUPPORTED, "goo_model_set_norm: MC normalisation needs an amplitude model");
+  }
+  h.norm_kind = spec->kind;
+  m->norm = *spec;
+  goo_ctx* ctx = m->ctx;
+  GOO_CUDA_TRY(cudaMemcpyAsync(m->dev, &h, sizeof(ModelDev), cudaMemcpyHostToDevice, ctx->stream));
+  GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return GOO_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// launches
+// ---------------------------------------------------------------------------------------
+template <typename KernelT>
+static int blocks_per_sm(KernelT kernel, int* cache) {
+  if (*cache > 0) return *cache;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kBlock, 0) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = 1;
+  }
+  *cache = n;
+  return n;
+}
+
+template <typename T, int L>
+static int launch_grid_T(goo_model* m) {
+  goo_ctx* ctx = m->ctx;
+  static int occ = 0;
+  const int bps = blocks_per_sm(grid_kernel<T, L>, &occ);
+  const ModelDev& h = m->host;
+  int64_t units_max = 1;
+  for (int k = 0; k < h.nK; ++k) {
+    const GridDev& G = h.grid[k];
+    int64_t rows = 1;
+    for (int d = 0; d < G.ndim - 1; ++d) rows *= G.bins[d];
+    int64_t u = rows * ((G.bins[G.ndim - 1] + kSeg - 1) / kSeg);
+    units_max = u > units_max ? u : units_max;
+  }
+  int64_t need = (units_max + kBlock - 1) / kBlock;
+  int64_t cap = ((int64_t)ctx->num_sms * bps + h.nK - 1) / h.nK;
+  const int nbx = (int)(need < cap ? (need < 1 ? 1 : need) : cap);
+  constexpr int NS = 1 + 3 * L;
+  GOO_TRY(ensure_partials(ctx, (size_t)nbx * h.nK * NS));
+  dim3 grid(nbx, h.nK);
+  {
+    LaunchScope ls(ctx, sizeof(T) == 4 ? "grid_norm_f32" : "grid_norm_f64");
+    grid_kernel<T, L><<<grid, kBlock, 0, ctx->stream>>>(m->dev, ctx->scratch.partials, ctx->scratch.counters);
+  }
+  GOO_CUDA_TRY(cudaGetLastError());
+  return GOO_OK;
+}
+
+int sop_prepare(goo_model* m, const double* theta_host, int precision) {
+  goo_ctx* ctx = m->ctx;
+  Scratch& s = ctx->scratch;
+  const int P = m->host.n_params;
+  std::memcpy(s.host_pinned, theta_host, P * sizeof(double));
+  GOO_CUDA_TRY(cudaMemcpyAsync(s.theta, s.host_pinned, P * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  {
+    LaunchScope ls(ctx, "prep");
+    prep_kernel<<<1, 32, 0, ctx->stream>>>(m->dev, s.theta, precision);
+  }
+  GOO_CUDA_TRY(cudaGetLastError());
+  if (m->host.norm_kind == GOO_NORM_GRID) {
+    if (precision == GOO_F32) {
+      GOO_TRY((m->max_leaf <= 2 ? launch_grid_T<float, 2>(m) : launch_grid_T<float, 4>(m)));
+    } else {
+      GOO_TRY((m->max_leaf <= 2 ? launch_grid_T<double, 2>(m) : launch_grid_T<double, 4>(m)));
+    }
+  }
+  return GOO_OK;
+}
+
+template <typename T, int K, int L, bool GRAD>
+static int launch_event_T(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int out_mode) {
+  goo_ctx* ctx = m->ctx;
+  static int occ = 0;
+  const int bps = blocks_per_sm(sop_event_kernel<T, K, L, GRAD>, &occ);
+  const int nb = grid_blocks(ctx, end - begin, bps);
+  constexpr int NS = EventLanes<T, K, L, GRAD>::NS;
+  GOO_TRY(ensure_partials(ctx, (size_t)nb * NS));
+  Cols<T> cols{};
+  for (int c = 0; c < kMaxObs; ++c) {
+    if (sizeof(T) == 4) cols.c[c] = (const T*)(c < ds->ncols ? (const void*)ds->d32[c] : (const void*)ds->d32[0]);
+    else cols.c[c] = (const T*)(c < ds->ncols ? (const void*)ds->d64[c] : (const void*)ds->d64[0]);
+  }
+  {
+    LaunchScope ls(ctx, sizeof(T) == 4 ? (GRAD ? "sop_nll_grad_f32" : "sop_nll_f32") : (GRAD ? "sop_nll_grad_f64" : "sop_nll_f64"));
+    sop_event_kernel<T, K, L, GRAD><<<nb, kBlock, 0, ctx->stream>>>(m->dev, cols, begin, end, ctx->scratch.partials,
+                                                                   ctx->scratch.counters, ctx->scratch.result, out_mode);
+  }
+  GOO_CUDA_TRY(cudaGetLastError());
+  return GOO_OK;
+}
+
+template <typename T, bool GRAD>
+static int launch_event_sel(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int out_mode) {
+  if (m->host.nK <= 2 && m->max_leaf <= 3) return launch_event_T<T, 2, 3, GRAD>(m, ds, begin, end, out_mode);
+  return launch_event_T<T, 4, 4, GRAD>(m, ds, begin, end, out_mode);
+}
+
+int sop_events(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int precision, bool grad, int out_mode) {
+  if (end <= begin) {
+    // empty range: write a zero result without a kernel
+    double z[3 + kMaxParams] = {0};
+    GOO_CUDA_TRY(cudaMemcpyAsync(m->ctx->scratch.result, z, sizeof z, cudaMemcpyHostToDevice, m->ctx->stream));
+    return GOO_OK;
+  }
+  if (precision == GOO_F32) {
+    return grad ? launch_event_sel<float, true>(m, ds, begin, end, out_mode)
+                : launch_event_sel<float, false>(m, ds, begin, end, out_mode);
+  }
+  return grad ? launch_event_sel<double, true>(m, ds, begin, end, out_mode)
+              : launch_event_sel<double, false>(m, ds, begin, end, out_mode);
+}
+
+template <typename T, int K, int L>
+static int launch_logf_T(goo_model* m, const goo_dataset* ds, double* logf_dev) {
+  goo_ctx* ctx = m->ctx;
+  Cols<T> cols{};
+  for (int c = 0; c < kMaxObs; ++c) {
+    if (sizeof(T) == 4) cols.c[c] = (const T*)(c < ds->ncols ? (const void*)ds->d32[c] : (const void*)ds->d32[0]);
+    else cols.c[c] = (const T*)(c < ds->ncols ? (const void*)ds->d64[c] : (const void*)ds->d64[0]);
+  }
+  const int nb = grid_blocks(ctx, ds->n, 4);
+  {
+    LaunchScope ls(ctx, "sop_logf");
+    sop_logf_kernel<T, K, L><<<nb, kBlock, 0, ctx->stream>>>(m->dev, cols, ds->n, logf_dev);
+  }
+  GOO_CUDA_TRY(cudaGetLastError());
+  return GOO_OK;
+}
+
+int sop_eval_logf(goo_model* m, const goo_dataset* ds, int precision, double* logf_dev) {
+  if (ds->n == 0) return GOO_OK;
+  if (precision == GOO_F32)
+    return (m->host.nK <= 2 && m->max_leaf <= 3) ? launch_logf_T<float, 2, 3>(m, ds, logf_dev)
+                                                 : launch_logf_T<float, 4, 4>(m, ds, logf_dev);
+  return (m->host.nK <= 2 && m->max_leaf <= 3) ? launch_logf_T<double, 2, 3>(m, ds, logf_dev)
+                                               : launch_logf_T<double, 4, 4>(m, ds, logf_dev);
+}
+
+}  // namespace goo

@@ -1,0 +1,382 @@
+"""Thin ctypes binding of libgoo.so (include/goo.h).
+
+Argument marshalling only: model specs become goo_node arrays, numpy arrays and torch
+tensors become column pointers, precision names become GOO_F64/GOO_F32.  Every step of
+the likelihood runs in the library's CUDA kernels; there is no CPU fallback -- importing
+this module fails if libgoo.so has not been built.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libgoo.so")
+
+GOO_OK, GOO_ERR_ARG, GOO_ERR_RANGE, GOO_ERR_CUDA, GOO_ERR_OOM = 0, -1, -2, -3, -4
+GOO_ERR_NONPOSITIVE_PDF, GOO_ERR_TIMEOUT, GOO_ERR_STATE, GOO_ERR_UNSUPPORTED = -5, -6, -7, -8
+GOO_F64, GOO_F32 = 0, 1
+GOO_COPY, GOO_BORROW_DEVICE = 0, 1
+OP = dict(gauss=1, expo=2, poly2=3, argus=4, prod=10, add=11, bw=20, nr=21, coherent=22)
+NORM = dict(analytic=0, grid=1, mc=2)
+MAX_CHILD = 16
+PAIR_INDEX = {"12": 0, "13": 1, "23": 2}
+
+
+class GooNode(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("obs", ctypes.c_int32 * 2), ("par", ctypes.c_int32 * 8),
+                ("n_child", ctypes.c_int32), ("child", ctypes.c_int32 * MAX_CHILD),
+                ("ival", ctypes.c_int32 * 2), ("dval", ctypes.c_double * 6)]
+
+
+class GooNormSpec(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("bins", ctypes.c_int32 * 4), ("mc", ctypes.c_void_p)]
+
+
+class GooError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"goo error {code}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+    lib = ctypes.CDLL(_LIB_PATH)
+    vp, dp, i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64
+    sig = {
+        "goo_init": (ctypes.c_int, [ctypes.c_int, vp, ctypes.POINTER(vp)]),
+        "goo_finalize": (ctypes.c_int, [vp]),
+        "goo_last_error": (ctypes.c_char_p, []),
+        "goo_version": (ctypes.c_char_p, []),
+        "goo_launch_count": (i64, [vp]),
+        "goo_timing_enable": (ctypes.c_int, [vp, ctypes.c_int]),
+        "goo_timing_read": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(i64), dp, ctypes.c_int]),
+        "goo_dataset_upload": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int, i64, dp, dp,
+                                              ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(i64)]),
+        "goo_dataset_free": (ctypes.c_int, [vp]),
+        "goo_dataset_size": (i64, [vp]),
+        "goo_dataset_column": (vp, [vp, ctypes.c_int, ctypes.c_int]),
+        "goo_model_build": (ctypes.c_int, [vp, ctypes.POINTER(GooNode), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           dp, dp, ctypes.POINTER(vp)]),
+        "goo_model_set_norm": (ctypes.c_int, [vp, ctypes.POINTER(GooNormSpec)]),
+        "goo_model_free": (ctypes.c_int, [vp]),
+        "goo_model_components": (ctypes.c_int, [vp]),
+        "goo_normalise": (ctypes.c_int, [vp, dp, ctypes.c_int, dp]),
+        "goo_nll": (ctypes.c_int, [vp, vp, dp, ctypes.c_int, dp]),
+        "goo_nll_grad": (ctypes.c_int, [vp, vp, dp, ctypes.c_int, dp, dp]),
+        "goo_eval_logf": (ctypes.c_int, [vp, vp, dp, ctypes.c_int, vp]),
+        "goo_nll_partial": (ctypes.c_int, [vp, vp, i64, i64, dp, ctypes.c_int, ctypes.c_int, dp]),
+        "goo_combine_partials": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, dp, dp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(rc):
+    if rc != GOO_OK:
+        raise GooError(rc, lib.goo_last_error().decode(errors="replace"))
+    return rc
+
+
+def _dbuf(values, n=None):
+    a = np.ascontiguousarray(values, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def precision_code(precision):
+    if precision in (GOO_F64, GOO_F32):
+        return precision
+    return {"f64": GOO_F64, "fp64": GOO_F64, "float64": GOO_F64,
+            "f32": GOO_F32, "fp32": GOO_F32, "float32": GOO_F32, "mixed": GOO_F32}[precision]
+
+
+class Context:
+    """A device and a CUDA stream; every call of the library on this context is ordered on it."""
+
+    def __init__(self, device=0, stream=None):
+        h = ctypes.c_void_p()
+        _check(lib.goo_init(int(device), ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)))
+        self.handle = h
+        self.device = device
+
+    @property
+    def launches(self):
+        return int(lib.goo_launch_count(self.handle))
+
+    def timing(self, on=True):
+        _check(lib.goo_timing_enable(self.handle, int(bool(on))))
+
+    def kernel_times(self, reset=True):
+        """{kernel name: (launches, total ms)} recorded since the last reset."""
+        cap = 64
+        names = ctypes.create_string_buffer(64 * cap)
+        counts = (ctypes.c_int64 * cap)()
+        ms = (ctypes.c_double * cap)()
+        n = lib.goo_timing_read(self.handle, cap, names, counts, ms, int(bool(reset)))
+        if n < 0:
+            _check(n)
+        out = {}
+        for i in range(min(n, cap)):
+            nm = names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
+            out[nm] = (int(counts[i]), float(ms[i]))
+        return out
+
+    def close(self):
+        if self.handle:
+            _check(lib.goo_finalize(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Dataset:
+    """Structure-of-arrays event columns on the device (goo_dataset_upload)."""
+
+    def __init__(self, ctx, columns, lo, hi, dtype="f64"):
+        self.ctx = ctx
+        cols = list(columns)
+        ncols = len(cols)
+        dt = precision_code(dtype)
+        self._keep = []
+        ptrs = (ctypes.c_void_p * ncols)()
+        flags = GOO_COPY
+        n = None
+        for i, c in enumerate(cols):
+            if hasattr(c, "is_cuda") and c.is_cuda:
+                flags = GOO_BORROW_DEVICE
+                want = "float64" if dt == GOO_F64 else "float32"
+                if str(c.dtype) != "torch." + want or not c.is_contiguous():
+                    raise ValueError(f"borrowed column {i} must be a contiguous torch.{want} tensor")
+                self._keep.append(c)
+                ptrs[i] = c.data_ptr()
+                size = c.numel()
+            else:
+                a = np.ascontiguousarray(c, dtype=np.float64 if dt == GOO_F64 else np.float32)
+                self._keep.append(a)
+                ptrs[i] = a.ctypes.data
+                size = a.size
+            if n is None:
+                n = size
+            elif size != n:
+                raise ValueError("columns differ in length")
+        lo_a, lo_p = _dbuf(lo, ncols)
+        hi_a, hi_p = _dbuf(hi, ncols)
+        h = ctypes.c_void_p()
+        nbad = ctypes.c_int64(0)
+        rc = lib.goo_dataset_upload(ctx.handle, ncols, ptrs, dt, int(n or 0), lo_p, hi_p, flags, ctypes.byref(h),
+                                    ctypes.byref(nbad))
+        self.n_bad = int(nbad.value)
+        _check(rc)
+        if flags == GOO_COPY:
+            self._keep = []
+        self.handle = h
+        self.n = int(n or 0)
+        self.ncols = ncols
+        self.lo, self.hi = list(lo_a), list(hi_a)
+
+    @classmethod
+    def from_spec(cls, ctx, spec, cols, dtype="f64"):
+        names = [o[0] for o in spec["observables"]]
+        return cls(ctx, [cols[n] for n in names], [o[1] for o in spec["observables"]],
+                   [o[2] for o in spec["observables"]], dtype)
+
+    def column_ptr(self, col, dtype="f64"):
+        return lib.goo_dataset_column(self.handle, col, precision_code(dtype))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib.goo_dataset_free(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spec_to_nodes(spec):
+    """Post-order goo_node array for a model spec (see synth/specs.py for the format)."""
+    pidx = {p[0]: i for i, p in enumerate(spec["params"])}
+    oidx = {o[0]: i for i, o in enumerate(spec["observables"])}
+    nodes = []
+
+    def new():
+        n = GooNode()
+        for j in range(2):
+            n.obs[j] = -1
+        for j in range(8):
+            n.par[j] = -1
+        return n
+
+    def emit(node):
+        op = node[0]
+        n = None
+        if op in ("gauss", "expo", "poly2", "argus"):
+            n = new()
+            n.op = OP[op]
+            n.obs[0] = oidx[node[1]]
+            for j, name in enumerate(node[2:]):
+                n.par[j] = pidx[name]
+        elif op == "prod":
+            kids = [emit(c) for c in node[1]]
+            n = new()
+            n.op = OP["prod"]
+            n.n_child = len(kids)
+            for j, k in enumerate(kids):
+                n.child[j] = k
+        elif op == "add":
+            kids = [emit(c) for c in node[2]]
+            n = new()
+            n.op = OP["add"]
+            n.n_child = len(kids)
+            for j, k in enumerate(kids):
+                n.child[j] = k
+            for j, name in enumerate(node[1]):
+                n.par[j] = pidx[name]
+        elif op == "coherent":
+            kin, amps = node[1], node[2]
+            kids = []
+            for a in amps:
+                m = new()
+                m.obs[0], m.obs[1] = oidx["s12"], oidx["s13"]
+                if a[0] == "bw":
+                    _, pair, spin, m0, w, re, im = a
+                    m.op = OP["bw"]
+                    m.par[0], m.par[1], m.par[2], m.par[3] = pidx[m0], pidx[w], pidx[re], pidx[im]
+                    m.ival[0], m.ival[1] = int(spin), PAIR_INDEX[pair]
+                elif a[0] == "nr":
+                    m.op = OP["nr"]
+                    m.par[2], m.par[3] = pidx[a[1]], pidx[a[2]]
+                else:
+                    raise ValueError(a[0])
+                nodes.append(m)
+                kids.append(len(nodes) - 1)
+            n = new()
+            n.op = OP["coherent"]
+            n.obs[0], n.obs[1] = oidx["s12"], oidx["s13"]
+            n.n_child = len(kids)
+            for j, k in enumerate(kids):
+                n.child[j] = k
+            for j, key in enumerate(["M", "m1", "m2", "m3", "r_res", "r_par"]):
+                n.dval[j] = float(kin[key])
+        else:
+            raise ValueError(f"unknown node {op}")
+        nodes.append(n)
+        return len(nodes) - 1
+
+    emit(spec["pdf"])
+    arr = (GooNode * len(nodes))(*nodes)
+    return arr, len(nodes)
+
+
+class Model:
+    """A compiled model (goo_model_build + goo_model_set_norm)."""
+
+    def __init__(self, ctx, spec, mc=None, norm=None):
+        self.ctx = ctx
+        self.spec = spec
+        self.n_params = len(spec["params"])
+        nodes, nn = spec_to_nodes(spec)
+        lo_a, lo_p = _dbuf([o[1] for o in spec["observables"]])
+        hi_a, hi_p = _dbuf([o[2] for o in spec["observables"]])
+        h = ctypes.c_void_p()
+        _check(lib.goo_model_build(ctx.handle, nodes, nn, self.n_params, len(spec["observables"]), lo_p, hi_p,
+                                   ctypes.byref(h)))
+        self.handle = h
+        self.mc = mc
+        self.set_norm(norm or spec["norm"], mc)
+
+    def set_norm(self, norm, mc=None):
+        ns = GooNormSpec()
+        ns.kind = NORM[norm[0]]
+        if norm[0] == "grid":
+            for j, b in enumerate(norm[1]):
+                ns.bins[j] = int(b)
+        if norm[0] == "mc":
+            if mc is None:
+                raise ValueError("MC normalisation needs the phase-space Dataset")
+            ns.mc = mc.handle
+            self.mc = mc
+        _check(lib.goo_model_set_norm(self.handle, ctypes.byref(ns)))
+
+    @property
+    def n_components(self):
+        return int(lib.goo_model_components(self.handle))
+
+    def _theta(self, theta):
+        return _dbuf(theta, self.n_params)
+
+    def normalise(self, theta, precision="f64"):
+        t, tp = self._theta(theta)
+        out = np.zeros(max(self.n_components, 1))
+        _check(lib.goo_normalise(self.handle, tp, precision_code(precision),
+                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def nll(self, ds, theta, precision="f64"):
+        t, tp = self._theta(theta)
+        out = ctypes.c_double()
+        _check(lib.goo_nll(self.handle, ds.handle, tp, precision_code(precision), ctypes.byref(out)))
+        return out.value
+
+    def nll_grad(self, ds, theta, precision="f64"):
+        t, tp = self._theta(theta)
+        out = ctypes.c_double()
+        g = np.zeros(self.n_params)
+        _check(lib.goo_nll_grad(self.handle, ds.handle, tp, precision_code(precision), ctypes.byref(out),
+                                g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out.value, g
+
+    def eval_logf(self, ds, theta, precision="f64"):
+        import torch
+        t, tp = self._theta(theta)
+        out = torch.empty(ds.n, dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+        _check(lib.goo_eval_logf(self.handle, ds.handle, tp, precision_code(precision),
+                                 ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def nll_partial(self, ds, begin, end, theta, precision="f64", want_grad=True):
+        t, tp = self._theta(theta)
+        out = np.zeros(3 + self.n_params)
+        _check(lib.goo_nll_partial(self.handle, ds.handle, int(begin), int(end), tp, precision_code(precision),
+                                   int(bool(want_grad)), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib.goo_model_free(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def combine_partials(parts, n_params):
+    """Compensated, index-ordered sum of shard records (goo_combine_partials)."""
+    p = np.ascontiguousarray(parts, dtype=np.float64).reshape(-1, 3 + n_params)
+    out = np.zeros(3 + n_params)
+    _check(lib.goo_combine_partials(p.shape[0], n_params, p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def version():
+    return lib.goo_version().decode()

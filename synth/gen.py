@@ -75,9 +75,27 @@ def gen_c2(n=10_000_000, seed=1710002):
     return {k: v[perm] for k, v in cols.items()}
 
 
-def round_to_f32(cols):
-    """Round every column to the nearest float32 value (kept as float64 arrays)."""
-    return {k: np.asarray(v, dtype=np.float32).astype(np.float64) for k, v in cols.items()}
+def round_to_f32(cols, spec=None):
+    """Round every column to the nearest float32 value (kept as float64 arrays).
+
+    With a spec, a value whose rounding leaves its observable's [lo, hi] is replaced by the
+    nearest float32 inside the range.
+    """
+    lims = {o[0]: (o[1], o[2]) for o in spec["observables"]} if spec else {}
+    out = {}
+    for k, v in cols.items():
+        r = np.asarray(v, dtype=np.float32)
+        if k in lims:
+            lo, hi = lims[k]
+            lo32 = np.float32(lo)
+            hi32 = np.float32(hi)
+            if lo32 < lo:
+                lo32 = np.nextafter(lo32, np.float32(np.inf))
+            if hi32 > hi:
+                hi32 = np.nextafter(hi32, np.float32(-np.inf))
+            r = np.clip(r, lo32, hi32)
+        out[k] = r.astype(np.float64)
+    return out
 
 
 def dalitz_box(M, m1, m2, m3):
