@@ -89,9 +89,9 @@ def round_to_f32(cols, spec=None):
             lo, hi = lims[k]
             lo32 = np.float32(lo)
             hi32 = np.float32(hi)
-            if lo32 < lo:
+            if float(lo32) < lo:
                 lo32 = np.nextafter(lo32, np.float32(np.inf))
-            if hi32 > hi:
+            if float(hi32) > hi:
                 hi32 = np.nextafter(hi32, np.float32(-np.inf))
             r = np.clip(r, lo32, hi32)
         out[k] = r.astype(np.float64)
