@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--ref-sample", type=int, default=250_000)
+    ap.add_argument("--profile", action="store_true",
+                    help="minimal run for ncu: 2 warm-up + 2 FP32+grad steps + 1 FP64 step, no baselines")
     return ap.parse_args()
 
 
@@ -339,8 +341,30 @@ def run_ours(args):
     return 0
 
 
+def run_profile(args):
+    """Launch sequence for ncu: [prep, grid, event] x (2 warm-up + 2 FP32+grad) then 1 FP64."""
+    import numpy as np
+
+    import synth
+    from paper_1710_08826_gb300 import build
+    build()
+    from paper_1710_08826_gb300 import goo
+    spec = synth.c2_spec(bins=GRID)
+    cols = synth.gen_c2(n=args.events, seed=1710002)
+    ctx = goo.Context(0)
+    ds = goo.Dataset.from_spec(ctx, spec, cols, dtype="f64")
+    model = goo.Model(ctx, spec)
+    theta = np.array(synth.param_values(spec))
+    out = [model.nll_grad(ds, theta, "f32")[0] for _ in range(4)]
+    out.append(model.nll(ds, theta, "f64"))
+    print(json.dumps({"profile": "c2_3d", "events": args.events, "nll": out, "launches": ctx.launches}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile:
+        return run_profile(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

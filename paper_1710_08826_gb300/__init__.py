@@ -2,14 +2,14 @@
 
 Layout:
   csrc/        CUDA C++ (sm_103a) kernels and the C ABI of include/goo.h -> libgoo.so
-  build.py     in-tree nvcc build of libgoo.so
+  buildlib.py  in-tree nvcc build of libgoo.so
   goo.py       ctypes binding (argument marshalling only)
   autograd.py  torch.autograd.Function over goo_nll_grad
 """
 
 
 def build(verbose=False, force=False):
-    from .build import build as _build
+    from .buildlib import build as _build
     return _build(verbose=verbose, force=force)
 
 

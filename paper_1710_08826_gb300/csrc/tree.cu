@@ -34,6 +34,7 @@
 // the exact likelihood of those parameters.
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -105,24 +106,65 @@ __device__ double leaf_max_exponent(int op, double lo, double hi, const double* 
   return 0.0;
 }
 
-__global__ void prep_kernel(ModelDev* md, const double* __restrict__ theta, int precision) {
+// One block of 64 threads: the model's leaf, product and ADD tables and theta are first
+// copied into shared memory (dependent global loads are the latency that dominates this
+// tiny kernel), one thread per leaf then derives its constants (and, for analytic
+// normalisation, its closed-form log-integral and derivatives), one thread per product
+// forms the weight, its derivatives and log N, and the tables are written back.
+__global__ void __launch_bounds__(64) prep_kernel(ModelDev* md, const double* __restrict__ theta, int precision) {
+  __shared__ CompDev s_comp[kMaxComp];
+  __shared__ LeafDev s_leaf[kMaxComp * kMaxLeaf];
+  __shared__ AddDev s_add[kMaxAdd];
+  __shared__ double s_theta[kMaxParams];
+  __shared__ double s_lo[kMaxObs], s_hi[kMaxObs];
   __shared__ double s_logN[kMaxComp * kMaxLeaf];
   __shared__ double s_dlogN[kMaxComp * kMaxLeaf][3];
   __shared__ double s_amax[kMaxComp * kMaxLeaf];
+  __shared__ double s_dw[kMaxComp][kMaxParams];
+  __shared__ double s_dN[kMaxComp][kMaxParams];
+  __shared__ int s_meta[3];
   const int t = threadIdx.x;
-  const int nK = md->nK;
+  {
+    // cooperative copies of the static tables
+    const int* src = (const int*)md->comp;
+    int* dst = (int*)s_comp;
+    for (int i = t; i < (int)(sizeof(s_comp) / 4); i += blockDim.x) dst[i] = src[i];
+    src = (const int*)md->leaf;
+    dst = (int*)s_leaf;
+    for (int i = t; i < (int)(sizeof(s_leaf) / 4); i += blockDim.x) dst[i] = src[i];
+    src = (const int*)md->add;
+    dst = (int*)s_add;
+    for (int i = t; i < (int)(sizeof(s_add) / 4); i += blockDim.x) dst[i] = src[i];
+    if (t < kMaxParams) s_theta[t] = t < md->n_params ? theta[t] : 0.0;
+    if (t < kMaxObs) {
+      s_lo[t] = md->lo[t];
+      s_hi[t] = md->hi[t];
+    }
+    if (t == 0) {
+      s_meta[0] = md->nK;
+      s_meta[1] = md->norm_kind;
+      s_meta[2] = md->n_params;
+    }
+    for (int i = t; i < kMaxComp * kMaxParams; i += blockDim.x) {
+      s_dw[i / kMaxParams][i % kMaxParams] = 0.0;
+      s_dN[i / kMaxParams][i % kMaxParams] = 0.0;
+    }
+  }
+  __syncthreads();
+  const int nK = s_meta[0];
+  const bool analytic = s_meta[1] == GOO_NORM_ANALYTIC;
   const bool f32 = precision == GOO_F32;
   if (t < kMaxComp * kMaxLeaf) {
     const int k = t / kMaxLeaf, l = t % kMaxLeaf;
     s_logN[t] = 0.0;
     s_dlogN[t][0] = s_dlogN[t][1] = s_dlogN[t][2] = 0.0;
     s_amax[t] = 0.0;
-    if (k < nK && l < md->comp[k].n_leaf) {
-      LeafDev& L = md->leaf[t];
-      const double lo = md->lo[L.col], hi = md->hi[L.col];
-      double p0 = L.par[0] >= 0 ? theta[L.par[0]] : 0.0;
-      double p1 = L.par[1] >= 0 ? theta[L.par[1]] : 0.0;
-      double p2 = L.par[2] >= 0 ? theta[L.par[2]] : 0.0;
+    if (k < nK && l < s_comp[k].n_leaf) {
+      LeafDev& L = s_leaf[t];
+      const double lo = s_lo[L.col], hi = s_hi[L.col];
+      const double p0 = L.par[0] >= 0 ? s_theta[L.par[0]] : 0.0;
+      const double p1 = L.par[1] >= 0 ? s_theta[L.par[1]] : 0.0;
+      const double p2 = L.par[2] >= 0 ? s_theta[L.par[2]] : 0.0;
       for (int i = 0; i < 6; ++i) {
         L.d[i] = 0.0;
         L.f[i] = 0.f;
@@ -132,22 +174,24 @@ __global__ void prep_kernel(ModelDev* md, const double* __restrict__ theta, int 
         case GOO_OP_GAUSS: {
           L.d[0] = p0;
           L.d[1] = 1.0 / p1;
-          float hi32 = (float)p0;
+          const float hi32 = (float)p0;
           L.f[0] = hi32;
           L.f[1] = (float)(p0 - (double)hi32);
           L.f[2] = (float)(1.0 / p1);
-          double mu = f32 ? (double)L.f[0] + (double)L.f[1] : p0;
-          double sg = f32 ? 1.0 / (double)L.f[2] : p1;
-          logN = gauss_log_norm(lo, hi, mu, sg, &g0, &g1);
-          s_amax[t] = leaf_max_exponent(L.op, lo, hi, L.d);
+          if (analytic) {
+            const double mu = f32 ? (double)L.f[0] + (double)L.f[1] : p0;
+            const double sg = f32 ? 1.0 / (double)L.f[2] : p1;
+            logN = gauss_log_norm(lo, hi, mu, sg, &g0, &g1);
+          } else {
+            s_amax[t] = leaf_max_exponent(L.op, lo, hi, L.d);
+          }
           break;
         }
         case GOO_OP_EXPO: {
           L.d[0] = p0;
           L.f[0] = (float)p0;
-          double lam = f32 ? (double)L.f[0] : p0;
-          logN = expo_log_norm(lo, hi, lam, &g0);
-          s_amax[t] = leaf_max_exponent(L.op, lo, hi, L.d);
+          if (analytic) logN = expo_log_norm(lo, hi, f32 ? (double)L.f[0] : p0, &g0);
+          else s_amax[t] = leaf_max_exponent(L.op, lo, hi, L.d);
           break;
         }
         case GOO_OP_POLY2: {
@@ -155,8 +199,7 @@ __global__ void prep_kernel(ModelDev* md, const double* __restrict__ theta, int 
           L.d[1] = p1;
           L.f[0] = (float)p0;
           L.f[1] = (float)p1;
-          double a1 = f32 ? (double)L.f[0] : p0, a2 = f32 ? (double)L.f[1] : p1;
-          logN = poly2_log_norm(lo, hi, a1, a2, &g0, &g1);
+          if (analytic) logN = poly2_log_norm(lo, hi, f32 ? (double)L.f[0] : p0, f32 ? (double)L.f[1] : p1, &g0, &g1);
           break;
         }
         case GOO_OP_ARGUS: {
@@ -165,14 +208,14 @@ __global__ void prep_kernel(ModelDev* md, const double* __restrict__ theta, int 
           L.d[2] = p1;
           L.d[3] = p2;
           L.d[4] = 2.0 / p0;
-          float hi32 = (float)p0;
+          const float hi32 = (float)p0;
           L.f[0] = hi32;
           L.f[1] = (float)(p0 - (double)hi32);
           L.f[2] = (float)(1.0 / (p0 * p0));
           L.f[3] = (float)p1;
           L.f[4] = (float)p2;
           L.f[5] = (float)(2.0 / p0);
-          s_amax[t] = leaf_max_exponent(L.op, lo, hi, L.d);
+          if (!analytic) s_amax[t] = leaf_max_exponent(L.op, lo, hi, L.d);
           break;
         }
         default:
@@ -185,247 +228,73 @@ __global__ void prep_kernel(ModelDev* md, const double* __restrict__ theta, int 
     }
   }
   __syncthreads();
-  if (t < kMaxComp) {
+  if (t < nK) {
     const int k = t;
-    for (int p = 0; p < kMaxParams; ++p) {
-      md->dw[k][p] = 0.0;
-      if (md->norm_kind == GOO_NORM_ANALYTIC) md->dlogN[k][p] = 0.0;
-    }
-    if (k < nK) {
-      CompDev& C = md->comp[k];
-      // weight: product of ADD factors
-      double w = 1.0;
-      for (int f = 0; f < C.n_fac; ++f) {
-        const AddDev& A = md->add[C.fac_add[f]];
-        double v;
-        if (C.fac_pos[f] < A.n_child - 1) {
-          v = theta[A.frac[C.fac_pos[f]]];
-        } else {
-          v = 1.0;
-          for (int j = 0; j < A.n_child - 1; ++j) v -= theta[A.frac[j]];
-        }
-        w *= v;
-      }
-      // dw/dtheta: product rule over the factors
-      for (int f = 0; f < C.n_fac; ++f) {
-        const AddDev& A = md->add[C.fac_add[f]];
-        double rest = 1.0;
-        for (int g = 0; g < C.n_fac; ++g) {
-          if (g == f) continue;
-          const AddDev& B = md->add[C.fac_add[g]];
-          double v;
-          if (C.fac_pos[g] < B.n_child - 1) {
-            v = theta[B.frac[C.fac_pos[g]]];
-          } else {
-            v = 1.0;
-            for (int j = 0; j < B.n_child - 1; ++j) v -= theta[B.frac[j]];
-          }
-          rest *= v;
-        }
-        if (C.fac_pos[f] < A.n_child - 1) {
-          md->dw[k][A.frac[C.fac_pos[f]]] += rest;
-        } else {
-          for (int j = 0; j < A.n_child - 1; ++j) md->dw[k][A.frac[j]] -= rest;
-        }
-      }
-      C.w = w;
-      float wh = (float)w;
-      C.w_hi = wh;
-      C.w_lo = (float)(w - (double)wh);
-      double amax = 0.0;
-      for (int l = 0; l < C.n_leaf; ++l) amax += s_amax[k * kMaxLeaf + l];
-      C.a_ref = amax;
-      float ah = (float)amax;
-      C.a_ref_hi = ah;
-      C.a_ref_lo = (float)(amax - (double)ah);
-      if (md->norm_kind == GOO_NORM_ANALYTIC) {
-        double logN = 0.0;
-        for (int l = 0; l < C.n_leaf; ++l) {
-          const int li = k * kMaxLeaf + l;
-          logN += s_logN[li];
-          const LeafDev& L = md->leaf[li];
-          for (int j = 0; j < 3; ++j)
-            if (L.par[j] >= 0) md->dlogN[k][L.par[j]] += s_dlogN[li][j];
-        }
-        C.log_norm = logN;
-        float oh = (float)(-logN);
-        C.off_hi = oh;
-        C.off_lo = (float)(-logN - (double)oh);
-      }
-    }
-  }
-}
-
-// =======================================================================================
-// leaf evaluation: value r * exp(a) and, separately, d log(leaf) / d par_j
-// (pass 1 of the event kernel needs only values; pass 2 recomputes the cheap derivatives
-// once the share of the leaf's product is known, instead of keeping them in registers)
-// =======================================================================================
-template <bool HasLo>
-__device__ __forceinline__ void leaf_val_f32(const LeafDev& L, float x, float xlo, float& r, float& a) {
-  const float* f = L.f;
-  switch (L.op) {
-    case GOO_OP_GAUSS: {
-      float dx = (x - f[0]);
-      dx = HasLo ? dx + (xlo - f[1]) : dx - f[1];
-      float z = dx * f[2];
-      r = 1.f;
-      a = -0.5f * z * z;
-      break;
-    }
-    case GOO_OP_EXPO:
-      r = 1.f;
-      a = HasLo ? fmaf(f[0], x, f[0] * xlo) : f[0] * x;
-      break;
-    case GOO_OP_POLY2: {
-      float xx = HasLo ? x + xlo : x;
-      r = fmaf(xx, fmaf(f[1], xx, f[0]), 1.f);
-      a = 0.f;
-      break;
-    }
-    case GOO_OP_ARGUS: {
-      float dm = HasLo ? (f[0] - x) + (f[1] - xlo) : (f[0] - x) + f[1];
-      float sm = HasLo ? (f[0] + x) + (f[1] + xlo) : (f[0] + x) + f[1];
-      float u = dm * sm * f[2];
-      if (u > 0.f) {
-        r = HasLo ? x + xlo : x;
-        a = fmaf(f[4], __logf(u), f[3] * u);
+    CompDev& C = s_comp[k];
+    double fac[8];
+    double w = 1.0;
+    for (int f = 0; f < C.n_fac; ++f) {
+      const AddDev& A = s_add[C.fac_add[f]];
+      double v;
+      if (C.fac_pos[f] < A.n_child - 1) {
+        v = s_theta[A.frac[C.fac_pos[f]]];
       } else {
-        r = 0.f;
-        a = 0.f;
+        v = 1.0;
+        for (int j = 0; j < A.n_child - 1; ++j) v -= s_theta[A.frac[j]];
       }
-      break;
+      fac[f] = v;
+      w *= v;
     }
-    default:
-      r = 1.f;
-      a = 0.f;
-  }
-}
-
-template <bool HasLo>
-__device__ __forceinline__ void leaf_der_f32(const LeafDev& L, float x, float xlo, float* d) {
-  const float* f = L.f;
-  switch (L.op) {
-    case GOO_OP_GAUSS: {
-      float dx = (x - f[0]);
-      dx = HasLo ? dx + (xlo - f[1]) : dx - f[1];
-      float z = dx * f[2];
-      d[0] = z * f[2];
-      d[1] = z * z * f[2];
-      d[2] = 0.f;
-      break;
-    }
-    case GOO_OP_EXPO:
-      d[0] = HasLo ? x + xlo : x;
-      d[1] = d[2] = 0.f;
-      break;
-    case GOO_OP_POLY2: {
-      float xx = HasLo ? x + xlo : x;
-      float ir = __fdividef(1.f, fmaf(xx, fmaf(f[1], xx, f[0]), 1.f));
-      d[0] = xx * ir;
-      d[1] = xx * xx * ir;
-      d[2] = 0.f;
-      break;
-    }
-    case GOO_OP_ARGUS: {
-      float dm = HasLo ? (f[0] - x) + (f[1] - xlo) : (f[0] - x) + f[1];
-      float sm = HasLo ? (f[0] + x) + (f[1] + xlo) : (f[0] + x) + f[1];
-      float u = dm * sm * f[2];
-      if (u > 0.f) {
-        d[0] = f[5] * (1.f - u) * (__fdividef(f[4], u) + f[3]);
-        d[1] = u;
-        d[2] = __logf(u);
+    // dw/dtheta: product rule over the factors
+    for (int f = 0; f < C.n_fac; ++f) {
+      const AddDev& A = s_add[C.fac_add[f]];
+      double rest = 1.0;
+      for (int g = 0; g < C.n_fac; ++g)
+        if (g != f) rest *= fac[g];
+      if (C.fac_pos[f] < A.n_child - 1) {
+        s_dw[k][A.frac[C.fac_pos[f]]] += rest;
       } else {
-        d[0] = d[1] = d[2] = 0.f;
+        for (int j = 0; j < A.n_child - 1; ++j) s_dw[k][A.frac[j]] -= rest;
       }
-      break;
     }
-    default:
-      d[0] = d[1] = d[2] = 0.f;
-  }
-}
-
-__device__ __forceinline__ void leaf_val_f64(const LeafDev& L, double x, double& r, double& a) {
-  const double* c = L.d;
-  switch (L.op) {
-    case GOO_OP_GAUSS: {
-      double z = (x - c[0]) * c[1];
-      r = 1.0;
-      a = -0.5 * z * z;
-      break;
-    }
-    case GOO_OP_EXPO:
-      r = 1.0;
-      a = c[0] * x;
-      break;
-    case GOO_OP_POLY2:
-      r = 1.0 + x * (c[0] + c[1] * x);
-      a = 0.0;
-      break;
-    case GOO_OP_ARGUS: {
-      double u = (c[0] - x) * (c[0] + x) * c[1];
-      if (u > 0.0) {
-        r = x;
-        a = c[3] * log(u) + c[2] * u;
-      } else {
-        r = 0.0;
-        a = 0.0;
+    C.w = w;
+    const float wh = (float)w;
+    C.w_hi = wh;
+    C.w_lo = (float)(w - (double)wh);
+    double amax = 0.0;
+    for (int l = 0; l < C.n_leaf; ++l) amax += s_amax[k * kMaxLeaf + l];
+    C.a_ref = amax;
+    const float ah = (float)amax;
+    C.a_ref_hi = ah;
+    C.a_ref_lo = (float)(amax - (double)ah);
+    if (analytic) {
+      double logN = 0.0;
+      for (int l = 0; l < C.n_leaf; ++l) {
+        const int li = k * kMaxLeaf + l;
+        logN += s_logN[li];
+        const LeafDev& L = s_leaf[li];
+        for (int j = 0; j < 3; ++j)
+          if (L.par[j] >= 0) s_dN[k][L.par[j]] += s_dlogN[li][j];
       }
-      break;
+      C.log_norm = logN;
+      const float oh = (float)(-logN);
+      C.off_hi = oh;
+      C.off_lo = (float)(-logN - (double)oh);
     }
-    default:
-      r = 1.0;
-      a = 0.0;
   }
-}
-
-__device__ __forceinline__ void leaf_der_f64(const LeafDev& L, double x, double* d) {
-  const double* c = L.d;
-  switch (L.op) {
-    case GOO_OP_GAUSS: {
-      double z = (x - c[0]) * c[1];
-      d[0] = z * c[1];
-      d[1] = z * z * c[1];
-      d[2] = 0.0;
-      break;
+  __syncthreads();
+  {
+    const int* src = (const int*)s_comp;
+    int* dst = (int*)md->comp;
+    for (int i = t; i < (int)(sizeof(s_comp) / 4); i += blockDim.x) dst[i] = src[i];
+    src = (const int*)s_leaf;
+    dst = (int*)md->leaf;
+    for (int i = t; i < (int)(sizeof(s_leaf) / 4); i += blockDim.x) dst[i] = src[i];
+    for (int i = t; i < kMaxComp * kMaxParams; i += blockDim.x) {
+      md->dw[i / kMaxParams][i % kMaxParams] = s_dw[i / kMaxParams][i % kMaxParams];
+      if (analytic) md->dlogN[i / kMaxParams][i % kMaxParams] = s_dN[i / kMaxParams][i % kMaxParams];
     }
-    case GOO_OP_EXPO:
-      d[0] = x;
-      d[1] = d[2] = 0.0;
-      break;
-    case GOO_OP_POLY2: {
-      double r = 1.0 + x * (c[0] + c[1] * x);
-      d[0] = x / r;
-      d[1] = x * x / r;
-      d[2] = 0.0;
-      break;
-    }
-    case GOO_OP_ARGUS: {
-      double u = (c[0] - x) * (c[0] + x) * c[1];
-      if (u > 0.0) {
-        d[0] = c[4] * (1.0 - u) * (c[3] / u + c[2]);
-        d[1] = u;
-        d[2] = log(u);
-      } else {
-        d[0] = d[1] = d[2] = 0.0;
-      }
-      break;
-    }
-    default:
-      d[0] = d[1] = d[2] = 0.0;
   }
-}
-
-template <typename T, bool HasLo>
-__device__ __forceinline__ void leaf_val(const LeafDev& L, T x, T xlo, T& r, T& a) {
-  if constexpr (sizeof(T) == 4) leaf_val_f32<HasLo>(L, x, xlo, r, a);
-  else leaf_val_f64(L, x, r, a);
-}
-
-template <typename T, bool HasLo>
-__device__ __forceinline__ void leaf_der(const LeafDev& L, T x, T xlo, T* d) {
-  if constexpr (sizeof(T) == 4) leaf_der_f32<HasLo>(L, x, xlo, d);
-  else leaf_der_f64(L, x, d);
 }
 
 template <typename T>
@@ -439,6 +308,228 @@ __device__ __forceinline__ T pick(int col, T x0, T x1, T x2, T x3) {
 }
 
 // =======================================================================================
+// register-resident interpreter: before the event loop every thread copies the constants,
+// opcode and column of each leaf slot (k, l) into registers (compile-time indices), so the
+// per-event work is one uniform dispatch per leaf plus the leaf's arithmetic.  Absent leaf
+// slots carry opcode 0 (value 1, no derivative); absent products are excluded by k < nK.
+// =======================================================================================
+template <typename T>
+struct LeafReg {
+  int op, col;
+  T c[6];
+};
+
+template <typename T>
+struct CompReg {
+  T off_hi, off_lo;   // -log N_k (FP64 path: off_hi only)
+  T w_hi, w_lo;       // w_k     (FP64 path: w_hi only)
+};
+
+template <typename T>
+__device__ __forceinline__ LeafReg<T> load_leaf(const LeafDev& L) {
+  LeafReg<T> R;
+  R.op = L.op;
+  R.col = L.col;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) R.c[j] = (sizeof(T) == 4) ? (T)L.f[j] : (T)L.d[j];
+  return R;
+}
+
+template <typename T>
+__device__ __forceinline__ CompReg<T> load_comp(const CompDev& C) {
+  CompReg<T> R;
+  if constexpr (sizeof(T) == 4) {
+    R.off_hi = C.off_hi;
+    R.off_lo = C.off_lo;
+    R.w_hi = C.w_hi;
+    R.w_lo = C.w_lo;
+  } else {
+    R.off_hi = -C.log_norm;
+    R.off_lo = 0.0;
+    R.w_hi = C.w;
+    R.w_lo = 0.0;
+  }
+  return R;
+}
+
+// Value r * exp(a) of one leaf at x (+ xlo, the low part of a double-float coordinate when
+// HasLo) and, if GRAD, d log(leaf) / d par_j.
+template <bool GRAD, bool HasLo = false>
+__device__ __forceinline__ void leaf_eval(const LeafReg<float>& L, float x, float& r, float& a, float* d,
+                                          float xlo = 0.f) {
+  const float* c = L.c;
+  d[0] = d[1] = d[2] = 0.f;
+  switch (L.op) {
+    case GOO_OP_GAUSS: {
+      const float z = (HasLo ? (x - c[0]) + (xlo - c[1]) : (x - c[0]) - c[1]) * c[2];
+      r = 1.f;
+      a = -0.5f * z * z;
+      if (GRAD) {
+        d[0] = z * c[2];
+        d[1] = z * z * c[2];
+      }
+      break;
+    }
+    case GOO_OP_EXPO:
+      r = 1.f;
+      a = HasLo ? fmaf(c[0], x, c[0] * xlo) : c[0] * x;
+      if (GRAD) d[0] = HasLo ? x + xlo : x;
+      break;
+    case GOO_OP_POLY2: {
+      const float xx = HasLo ? x + xlo : x;
+      r = fmaf(xx, fmaf(c[1], xx, c[0]), 1.f);
+      a = 0.f;
+      if (GRAD) {
+        const float ir = __fdividef(1.f, r);
+        d[0] = xx * ir;
+        d[1] = xx * xx * ir;
+      }
+      break;
+    }
+    case GOO_OP_ARGUS: {
+      const float u = HasLo ? ((c[0] - x) + (c[1] - xlo)) * ((c[0] + x) + (c[1] + xlo)) * c[2]
+                            : ((c[0] - x) + c[1]) * ((c[0] + x) + c[1]) * c[2];
+      if (u > 0.f) {
+        const float lu = __logf(u);
+        r = HasLo ? x + xlo : x;
+        a = fmaf(c[4], lu, c[3] * u);
+        if (GRAD) {
+          d[0] = c[5] * (1.f - u) * (__fdividef(c[4], u) + c[3]);
+          d[1] = u;
+          d[2] = lu;
+        }
+      } else {
+        r = 0.f;
+        a = 0.f;
+      }
+      break;
+    }
+    default:
+      r = 1.f;
+      a = 0.f;
+  }
+}
+
+template <bool GRAD, bool HasLo = false>
+__device__ __forceinline__ void leaf_eval(const LeafReg<double>& L, double x, double& r, double& a, double* d,
+                                          double xlo = 0.0) {
+  const double* c = L.c;
+  d[0] = d[1] = d[2] = 0.0;
+  switch (L.op) {
+    case GOO_OP_GAUSS: {
+      const double z = (x - c[0]) * c[1];
+      r = 1.0;
+      a = -0.5 * z * z;
+      if (GRAD) {
+        d[0] = z * c[1];
+        d[1] = z * z * c[1];
+      }
+      break;
+    }
+    case GOO_OP_EXPO:
+      r = 1.0;
+      a = c[0] * x;
+      if (GRAD) d[0] = x;
+      break;
+    case GOO_OP_POLY2:
+      r = 1.0 + x * (c[0] + c[1] * x);
+      a = 0.0;
+      if (GRAD) {
+        d[0] = x / r;
+        d[1] = x * x / r;
+      }
+      break;
+    case GOO_OP_ARGUS: {
+      const double u = (c[0] - x) * (c[0] + x) * c[1];
+      if (u > 0.0) {
+        const double lu = log(u);
+        r = x;
+        a = c[3] * lu + c[2] * u;
+        if (GRAD) {
+          d[0] = c[4] * (1.0 - u) * (c[3] / u + c[2]);
+          d[1] = u;
+          d[2] = lu;
+        }
+      } else {
+        r = 0.0;
+        a = 0.0;
+      }
+      break;
+    }
+    default:
+      r = 1.0;
+      a = 0.0;
+  }
+}
+
+// One event: log f (returned through logf) and, if GRAD, the shares c_k and the leaf
+// derivatives.  Returns false when f <= 0.
+template <typename T, int K, int L, bool GRAD>
+__device__ __forceinline__ bool eval_event(const LeafReg<T> (&lr)[K][L], const CompReg<T> (&cr)[K], int nK, T x0, T x1,
+                                           T x2, T x3, T& logf, T (&ck)[K], T (&dk)[K][L][3]) {
+  T rk[K], ak[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    T r = T(1), a = T(0);
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      T lr_, la_;
+      leaf_eval<GRAD>(lr[k][l], pick<T>(lr[k][l].col, x0, x1, x2, x3), lr_, la_, dk[k][l]);
+      r *= lr_;
+      a += la_;
+    }
+    a = (a + cr[k].off_hi) + cr[k].off_lo;
+    rk[k] = r;
+    ak[k] = (k < nK && r != T(0)) ? a : T(-1e30);
+  }
+  T M = ak[0];
+#pragma unroll
+  for (int k = 1; k < K; ++k) M = ak[k] > M ? ak[k] : M;
+  T S = T(0);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if constexpr (sizeof(T) == 4) {
+      rk[k] = rk[k] * expf(ak[k] - M);
+      S += fmaf(cr[k].w_hi, rk[k], cr[k].w_lo * rk[k]);
+    } else {
+      rk[k] = rk[k] * exp(ak[k] - M);
+      S += cr[k].w_hi * rk[k];
+    }
+  }
+  if (!(S > T(0)) || !(M > T(-1e29))) return false;
+  if constexpr (sizeof(T) == 4) logf = M + __logf(S);
+  else logf = M + log(S);
+  if constexpr (GRAD) {
+    const T invS = T(1) / S;
+#pragma unroll
+    for (int k = 0; k < K; ++k) ck[k] = rk[k] * invS;
+  }
+  return true;
+}
+
+// Every thread copies the model's leaf and product constants into registers.
+template <typename T, int K, int L>
+__device__ __forceinline__ int load_model_regs(const ModelDev* __restrict__ md, LeafReg<T> (&lr)[K][L],
+                                               CompReg<T> (&cr)[K]) {
+  __shared__ LeafDev s_leaf[K * L];
+  __shared__ CompDev s_comp[K];
+  for (int i = threadIdx.x; i < K * L; i += blockDim.x) s_leaf[i] = md->leaf[(i / L) * kMaxLeaf + (i % L)];
+  for (int i = threadIdx.x; i < K; i += blockDim.x) s_comp[i] = md->comp[i];
+  __syncthreads();
+  const int nK = md->nK;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    cr[k] = load_comp<T>(s_comp[k]);
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      lr[k][l] = load_leaf<T>(s_leaf[k * L + l]);
+      if (k >= nK || l >= s_comp[k].n_leaf) lr[k][l].op = 0;
+    }
+  }
+  return nK;
+}
+
+// =======================================================================================
 // fused per-event kernel: evaluate, log, accumulate (and adjoint lanes), reduce
 // Lanes: 0 = sum log f; 1..K = C_k; then A_{k,l,j} at 1 + K + (k*L + l)*3 + j.
 // =======================================================================================
@@ -448,119 +539,54 @@ struct EventLanes {
 };
 
 template <typename T, int K, int L, bool GRAD>
-__global__ void __launch_bounds__(kBlock) sop_event_kernel(const ModelDev* __restrict__ md, Cols<T> cols,
-                                                           int64_t begin, int64_t end, float2* partials,
-                                                           unsigned* counters, double* result, int out_mode) {
+__global__ void __launch_bounds__(kBlock, 2) sop_event_kernel(const ModelDev* __restrict__ md, Cols<T> cols,
+                                                              int64_t begin, int64_t end, float2* partials,
+                                                              unsigned* counters, double* result, int out_mode) {
   constexpr int NS = EventLanes<T, K, L, GRAD>::NS;
-  __shared__ LeafDev s_leaf[K * L];
-  __shared__ CompDev s_comp[K];
   __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
   __shared__ unsigned s_bad[kBlock / 32];
-  const int nK = md->nK;
-  for (int i = threadIdx.x; i < K * L; i += blockDim.x) {
-    const int k = i / L, l = i % L;
-    if (k < kMaxComp && l < kMaxLeaf) s_leaf[i] = md->leaf[k * kMaxLeaf + l];
-  }
-  for (int i = threadIdx.x; i < K; i += blockDim.x) s_comp[i] = md->comp[i];
-  __syncthreads();
+  LeafReg<T> lr[K][L];
+  CompReg<T> cr[K];
+  const int nK = load_model_regs<T, K, L>(md, lr, cr);
 
-  // per-thread accumulators
+  // per-thread accumulators: FP32 path -> Kahan for sum log f, plain FP32 for the adjoint
+  // lanes; FP64 path -> plain FP64
+  using Acc = typename std::conditional<sizeof(T) == 4, float, double>::type;
   double acc64 = 0.0;
   Kahan acc32;
-  float Cacc[K];
-  float Aacc[K][L][3];
-  double Cacc64[K];
-  double Aacc64[K][L][3];
+  Acc Cacc[K];
+  Acc Aacc[K][L][3];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    Cacc[k] = 0.f;
-    Cacc64[k] = 0.0;
+    Cacc[k] = Acc(0);
 #pragma unroll
     for (int l = 0; l < L; ++l)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        Aacc[k][l][j] = 0.f;
-        Aacc64[k][l][j] = 0.0;
-      }
+      for (int j = 0; j < 3; ++j) Aacc[k][l][j] = Acc(0);
   }
   unsigned bad = 0;
   const int nobs = md->n_obs;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end; i += stride) {
-    T x0 = cols.c[0][i];
-    T x1 = nobs > 1 ? cols.c[1][i] : T(0);
-    T x2 = nobs > 2 ? cols.c[2][i] : T(0);
-    T x3 = nobs > 3 ? cols.c[3][i] : T(0);
-    T rk[K], ak[K];
-    // pass 1: values of every product, in the log domain
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      T r = T(1), a = T(0);
-#pragma unroll
-      for (int l = 0; l < L; ++l) {
-        if (k < nK && l < s_comp[k].n_leaf) {
-          const LeafDev& lf = s_leaf[k * L + l];
-          T lr, la;
-          leaf_val<T, false>(lf, pick<T>(lf.col, x0, x1, x2, x3), T(0), lr, la);
-          r *= lr;
-          a += la;
-        }
-      }
+    const T x0 = cols.c[0][i];
+    const T x1 = nobs > 1 ? cols.c[1][i] : T(0);
+    const T x2 = nobs > 2 ? cols.c[2][i] : T(0);
+    const T x3 = nobs > 3 ? cols.c[3][i] : T(0);
+    T logf, ck[K], dk[K][L][3];
+    if (eval_event<T, K, L, GRAD>(lr, cr, nK, x0, x1, x2, x3, logf, ck, dk)) {
       if constexpr (sizeof(T) == 4) {
-        a = (a + s_comp[k].off_hi) + s_comp[k].off_lo;
+        acc32.add(logf);
       } else {
-        a = a - s_comp[k].log_norm;
-      }
-      rk[k] = (k < nK) ? r : T(0);
-      ak[k] = (rk[k] != T(0)) ? a : T(-1e30);
-    }
-    T M = ak[0];
-#pragma unroll
-    for (int k = 1; k < K; ++k) M = ak[k] > M ? ak[k] : M;
-    T S = T(0);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      if constexpr (sizeof(T) == 4) {
-        rk[k] = rk[k] * expf(ak[k] - M);
-        S += fmaf(s_comp[k].w_hi, rk[k], s_comp[k].w_lo * rk[k]);
-      } else {
-        rk[k] = rk[k] * exp(ak[k] - M);
-        S += s_comp[k].w * rk[k];
-      }
-    }
-    if (S > T(0) && M > T(-1e29)) {
-      if constexpr (sizeof(T) == 4) {
-        acc32.add(M + __logf(S));
-      } else {
-        acc64 += M + log(S);
+        acc64 += logf;
       }
       if constexpr (GRAD) {
-        // pass 2: adjoint lanes
-        const T invS = T(1) / S;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-          const T ck = rk[k] * invS;
-          if constexpr (sizeof(T) == 4) {
-            Cacc[k] += ck;
-          } else {
-            Cacc64[k] += ck;
-          }
+          Cacc[k] += ck[k];
 #pragma unroll
-          for (int l = 0; l < L; ++l) {
-            if (k < nK && l < s_comp[k].n_leaf) {
-              const LeafDev& lf = s_leaf[k * L + l];
-              T d[3];
-              leaf_der<T, false>(lf, pick<T>(lf.col, x0, x1, x2, x3), T(0), d);
+          for (int l = 0; l < L; ++l)
 #pragma unroll
-              for (int j = 0; j < 3; ++j) {
-                if constexpr (sizeof(T) == 4) {
-                  Aacc[k][l][j] = fmaf(ck, d[j], Aacc[k][l][j]);
-                } else {
-                  Aacc64[k][l][j] += ck * d[j];
-                }
-              }
-            }
-          }
+            for (int j = 0; j < 3; ++j) Aacc[k][l][j] += ck[k] * dk[k][l][j];
         }
       }
     } else {
@@ -578,13 +604,13 @@ __global__ void __launch_bounds__(kBlock) sop_event_kernel(const ModelDev* __res
   if constexpr (GRAD) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      v[1 + k] = (sizeof(T) == 4) ? ddf{Cacc[k], 0.f} : dd_from_double(Cacc64[k]);
+      v[1 + k] = (sizeof(T) == 4) ? ddf{(float)Cacc[k], 0.f} : dd_from_double((double)Cacc[k]);
 #pragma unroll
       for (int l = 0; l < L; ++l)
 #pragma unroll
         for (int j = 0; j < 3; ++j)
           v[1 + K + (k * L + l) * 3 + j] =
-              (sizeof(T) == 4) ? ddf{Aacc[k][l][j], 0.f} : dd_from_double(Aacc64[k][l][j]);
+              (sizeof(T) == 4) ? ddf{(float)Aacc[k][l][j], 0.f} : dd_from_double((double)Aacc[k][l][j]);
     }
   }
   for (int m = 16; m > 0; m >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, m);
@@ -635,53 +661,88 @@ __global__ void __launch_bounds__(kBlock) sop_event_kernel(const ModelDev* __res
 // grid normalisation: per product k, midpoint sum of U_k over the grid of its observables
 // and of U_k * d log(leaf)/d par.  Work unit: a segment of kSeg points along the last grid
 // dimension; leaves on the other observables are evaluated once per segment (they are
-// constant along it).  Lanes per product: 0 = sum U exp(-a_ref), 1 + l*3 + j = sum U d_lj.
+// constant along it).  The last dimension's coordinates are computed once per block into
+// shared memory (double-float in the FP32 path).  Lanes per product: 0 = sum U exp(-a_ref),
+// 1 + l*3 + j = sum U d_lj.
 // =======================================================================================
 constexpr int kSeg = 16;
+constexpr int kGridCache = 2048;
+
+template <typename T>
+__device__ __forceinline__ void grid_coord(const GridDev& G, int d, int64_t idx, T& x, T& xlo) {
+  if constexpr (sizeof(T) == 4) {
+    const float off = (float)idx + 0.5f;
+    const float p = off * G.h_hi[d];
+    const float perr = fmaf(off, G.h_hi[d], -p) + off * G.h_lo[d];
+    const ddf xs = dd_add({G.lo_hi[d], G.lo_lo[d]}, dd_make(p, perr));
+    x = xs.hi;
+    xlo = xs.lo;
+  } else {
+    x = G.lo64[d] + ((double)idx + 0.5) * G.h64[d];
+    xlo = 0.0;
+  }
+}
 
 template <typename T, int L>
-__global__ void __launch_bounds__(kBlock) grid_kernel(ModelDev* md, float2* partials, unsigned* counters) {
+__global__ void __launch_bounds__(kBlock, 2) grid_kernel(ModelDev* md, float2* partials, unsigned* counters) {
   constexpr int NS = 1 + 3 * L;
   const int k = blockIdx.y;
   __shared__ LeafDev s_leaf[L];
+  __shared__ T s_xh[kGridCache], s_xl[kGridCache];
   __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
   const CompDev& C = md->comp[k];
   const int nleaf = C.n_leaf;
   if (threadIdx.x < L && threadIdx.x < nleaf) s_leaf[threadIdx.x] = md->leaf[k * kMaxLeaf + threadIdx.x];
-  __syncthreads();
   const GridDev& G = md->grid[k];
   const int last = G.ndim - 1;
   const int nlast = G.bins[last];
+  const bool cached = nlast <= kGridCache;
+  if (cached)
+    for (int i = threadIdx.x; i < nlast; i += blockDim.x) grid_coord<T>(G, last, i, s_xh[i], s_xl[i]);
+  __syncthreads();
+  LeafReg<T> lr[L];
+  int dimof[L];
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    if (l < nleaf) {
+      lr[l] = load_leaf<T>(s_leaf[l]);
+      dimof[l] = G.dim_of_col[lr[l].col];
+    } else {
+      lr[l].op = 0;
+      lr[l].col = 0;
+      dimof[l] = -1;
+    }
+  }
   const int nseg = (nlast + kSeg - 1) / kSeg;
   int64_t nrows = 1;
   for (int d = 0; d < last; ++d) nrows *= G.bins[d];
   const int64_t units = nrows * nseg;
+  int bins_d[kMaxObs];
+#pragma unroll
+  for (int d = 0; d < kMaxObs; ++d) bins_d[d] = G.bins[d];
 
   T acc[NS];
   Kahan acc_s;
 #pragma unroll
   for (int s = 0; s < NS; ++s) acc[s] = T(0);
   const T aref = (sizeof(T) == 4) ? T(C.a_ref_hi) : T(C.a_ref);
+  const T aref_lo = (sizeof(T) == 4) ? T(C.a_ref_lo) : T(0);
   for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
     int64_t row = u / nseg;
     const int seg = (int)(u - row * nseg);
-    // coordinates of the non-last dimensions
-    T xo[kMaxObs], xo_lo[kMaxObs];
-    for (int d = last - 1; d >= 0; --d) {
-      const int64_t b = G.bins[d];
-      const int64_t idx = row % b;
-      row /= b;
-      if constexpr (sizeof(T) == 4) {
-        // x = lo + (idx + 1/2) h as a float hi + lo pair
-        const float off = (float)idx + 0.5f;
-        const float p = off * G.h_hi[d];
-        const float perr = fmaf(off, G.h_hi[d], -p) + off * G.h_lo[d];
-        ddf xs = dd_add({G.lo_hi[d], G.lo_lo[d]}, dd_make(p, perr));
-        xo[d] = xs.hi;
-        xo_lo[d] = xs.lo;
-      } else {
-        xo[d] = G.lo64[d] + ((double)idx + 0.5) * G.h64[d];
-        xo_lo[d] = 0.0;
+    // coordinates of the other dimensions (at most three)
+    T xo0 = T(0), xo1 = T(0), xo2 = T(0), lo0 = T(0), lo1 = T(0), lo2 = T(0);
+#pragma unroll
+    for (int d = kMaxObs - 2; d >= 0; --d) {
+      if (d < last) {
+        const int64_t b = bins_d[d];
+        const int64_t idx = row % b;
+        row /= b;
+        T xv, xl;
+        grid_coord<T>(G, d, idx, xv, xl);
+        if (d == 0) { xo0 = xv; lo0 = xl; }
+        if (d == 1) { xo1 = xv; lo1 = xl; }
+        if (d == 2) { xo2 = xv; lo2 = xl; }
       }
     }
     // segment-invariant leaves
@@ -690,15 +751,17 @@ __global__ void __launch_bounds__(kBlock) grid_kernel(ModelDev* md, float2* part
 #pragma unroll
     for (int l = 0; l < L; ++l) {
       d_row[l][0] = d_row[l][1] = d_row[l][2] = T(0);
-      if (l < nleaf && G.dim_of_col[s_leaf[l].col] != last) {
-        const int dd = G.dim_of_col[s_leaf[l].col];
-        T lr, la;
-        leaf_val<T, true>(s_leaf[l], xo[dd], xo_lo[dd], lr, la);
-        leaf_der<T, true>(s_leaf[l], xo[dd], xo_lo[dd], d_row[l]);
-        r_row *= lr;
-        a_row += la;
+      if (dimof[l] >= 0 && dimof[l] != last) {
+        const int dd = dimof[l];
+        const T xv = dd == 0 ? xo0 : (dd == 1 ? xo1 : xo2);
+        const T xl = dd == 0 ? lo0 : (dd == 1 ? lo1 : lo2);
+        T lr_, la_;
+        leaf_eval<true, true>(lr[l], xv, lr_, la_, d_row[l], xl);
+        r_row *= lr_;
+        a_row += la_;
       }
     }
+    a_row = (a_row - aref) - aref_lo;
     T sumU = T(0);
     T dpt[L][3];
 #pragma unroll
@@ -707,35 +770,29 @@ __global__ void __launch_bounds__(kBlock) grid_kernel(ModelDev* md, float2* part
     const int i1 = min(nlast, i0 + kSeg);
     for (int i = i0; i < i1; ++i) {
       T x, xlo;
-      if constexpr (sizeof(T) == 4) {
-        const float off = (float)i + 0.5f;
-        const float p = off * G.h_hi[last];
-        const float perr = fmaf(off, G.h_hi[last], -p) + off * G.h_lo[last];
-        ddf xs = dd_add({G.lo_hi[last], G.lo_lo[last]}, dd_make(p, perr));
-        x = xs.hi;
-        xlo = xs.lo;
+      if (cached) {
+        x = s_xh[i];
+        xlo = s_xl[i];
       } else {
-        x = G.lo64[last] + ((double)i + 0.5) * G.h64[last];
-        xlo = 0.0;
+        grid_coord<T>(G, last, i, x, xlo);
       }
       T r = r_row, a = a_row;
       T dl[L][3];
 #pragma unroll
       for (int l = 0; l < L; ++l) {
         dl[l][0] = dl[l][1] = dl[l][2] = T(0);
-        if (l < nleaf && G.dim_of_col[s_leaf[l].col] == last) {
-          T lr, la;
-          leaf_val<T, true>(s_leaf[l], x, xlo, lr, la);
-          leaf_der<T, true>(s_leaf[l], x, xlo, dl[l]);
-          r *= lr;
-          a += la;
+        if (dimof[l] == last) {
+          T lr_, la_;
+          leaf_eval<true, true>(lr[l], x, lr_, la_, dl[l], xlo);
+          r *= lr_;
+          a += la_;
         }
       }
       T U;
       if constexpr (sizeof(T) == 4) {
-        U = r * expf((a - aref) - C.a_ref_lo);
+        U = r * expf(a);
       } else {
-        U = r * exp(a - aref);
+        U = r * exp(a);
       }
       sumU += U;
 #pragma unroll
@@ -819,62 +876,18 @@ __global__ void __launch_bounds__(kBlock) grid_kernel(ModelDev* md, float2* part
 template <typename T, int K, int L>
 __global__ void __launch_bounds__(kBlock) sop_logf_kernel(const ModelDev* __restrict__ md, Cols<T> cols, int64_t n,
                                                           double* __restrict__ logf) {
-  __shared__ LeafDev s_leaf[K * L];
-  __shared__ CompDev s_comp[K];
-  const int nK = md->nK;
-  for (int i = threadIdx.x; i < K * L; i += blockDim.x) s_leaf[i] = md->leaf[(i / L) * kMaxLeaf + (i % L)];
-  for (int i = threadIdx.x; i < K; i += blockDim.x) s_comp[i] = md->comp[i];
-  __syncthreads();
+  LeafReg<T> lr[K][L];
+  CompReg<T> cr[K];
+  const int nK = load_model_regs<T, K, L>(md, lr, cr);
   const int nobs = md->n_obs;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    T x0 = cols.c[0][i];
-    T x1 = nobs > 1 ? cols.c[1][i] : T(0);
-    T x2 = nobs > 2 ? cols.c[2][i] : T(0);
-    T x3 = nobs > 3 ? cols.c[3][i] : T(0);
-    T rk[K], ak[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      T r = T(1), a = T(0);
-#pragma unroll
-      for (int l = 0; l < L; ++l) {
-        if (k < nK && l < s_comp[k].n_leaf) {
-          const LeafDev& lf = s_leaf[k * L + l];
-          T xv = pick<T>(lf.col, x0, x1, x2, x3);
-          T lr, la;
-          leaf_val<T, false>(lf, xv, T(0), lr, la);
-          r *= lr;
-          a += la;
-        }
-      }
-      if constexpr (sizeof(T) == 4) {
-        a = (a + s_comp[k].off_hi) + s_comp[k].off_lo;
-      } else {
-        a = a - s_comp[k].log_norm;
-      }
-      rk[k] = (k < nK) ? r : T(0);
-      ak[k] = (rk[k] != T(0)) ? a : T(-1e30);
-    }
-    T M = ak[0];
-#pragma unroll
-    for (int k = 1; k < K; ++k) M = ak[k] > M ? ak[k] : M;
-    T S = T(0);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      if constexpr (sizeof(T) == 4) {
-        float u = rk[k] * expf(ak[k] - M);
-        S += fmaf(s_comp[k].w_hi, u, s_comp[k].w_lo * u);
-      } else {
-        S += s_comp[k].w * rk[k] * exp(ak[k] - M);
-      }
-    }
-    double out;
-    if (S > T(0) && M > T(-1e29)) {
-      if constexpr (sizeof(T) == 4) out = (double)M + (double)__logf(S);
-      else out = M + log(S);
-    } else {
-      out = -HUGE_VAL;
-    }
-    logf[i] = out;
+    const T x0 = cols.c[0][i];
+    const T x1 = nobs > 1 ? cols.c[1][i] : T(0);
+    const T x2 = nobs > 2 ? cols.c[2][i] : T(0);
+    const T x3 = nobs > 3 ? cols.c[3][i] : T(0);
+    T lf, ck[K], dk[K][L][3];
+    const bool ok = eval_event<T, K, L, false>(lr, cr, nK, x0, x1, x2, x3, lf, ck, dk);
+    logf[i] = ok ? (double)lf : -HUGE_VAL;
   }
 }
 
@@ -1120,7 +1133,7 @@ int sop_prepare(goo_model* m, const double* theta_host, int precision) {
   GOO_CUDA_TRY(cudaMemcpyAsync(s.theta, s.host_pinned, P * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   {
     LaunchScope ls(ctx, "prep");
-    prep_kernel<<<1, 32, 0, ctx->stream>>>(m->dev, s.theta, precision);
+    prep_kernel<<<1, 64, 0, ctx->stream>>>(m->dev, s.theta, precision);
   }
   GOO_CUDA_TRY(cudaGetLastError());
   if (m->host.norm_kind == GOO_NORM_GRID) {
@@ -1203,3 +1216,4 @@ int sop_eval_logf(goo_model* m, const goo_dataset* ds, int precision, double* lo
 }
 
 }  // namespace goo
+
