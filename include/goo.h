@@ -121,7 +121,7 @@ const char* goo_last_error(void);
 /* Library version string and the number of kernel launches issued so far by ctx. */
 const char* goo_version(void);
 int64_t goo_launch_count(const goo_ctx* ctx);
-/* Per-kernel timing statistics (paper Sec. 4: timing statistics in the standard output).
+/* Per-kernel timing statistics (paper Sec. 3: fits report timing statistics).
  * When enabled, every kernel launch of ctx is bracketed by CUDA events on ctx's stream.
  * goo_timing_read folds finished launches into per-kernel totals and copies up to
  * max_entries of them: names (64 chars each, NUL-terminated), launch counts and total
@@ -130,12 +130,12 @@ int64_t goo_launch_count(const goo_ctx* ctx);
 int goo_timing_enable(goo_ctx* ctx, int on);
 int goo_timing_read(goo_ctx* ctx, int max_entries, char* names, int64_t* counts, double* total_ms, int reset);
 
-/* ---- data (paper: DataSet, Fig. 1 and Sec. 5) ------------------------------------------------
+/* ---- data (paper: DataSet, Fig. 1 and Sec. 4) ------------------------------------------------
  * Upload `ncols` structure-of-arrays columns of n_events values each, of type `dtype`
  * (GOO_F64 or GOO_F32).  With GOO_COPY the columns are host arrays copied to the device;
  * with GOO_BORROW_DEVICE they are device arrays (16-byte aligned) kept by reference.
  * lo[c], hi[c] are the limits of observable c.  Every event is range-checked on the device
- * (Sec. 5: "runtime checks ... warn unsuspecting users who load data out of range"): if
+ * (Sec. 4: data loaded outside the observables' ranges is caught at run time): if
  * any value lies outside its [lo, hi] (or is NaN) the call fails with GOO_ERR_RANGE, no
  * dataset is created, and *n_bad (if not NULL) receives the number of offending events.
  * The device keeps both a float64 and a float32 copy of every column. */
@@ -175,7 +175,7 @@ int goo_nll_grad(goo_model* model, const goo_dataset* ds, const double* theta, i
 int goo_eval_logf(goo_model* model, const goo_dataset* ds, const double* theta, int precision,
                   double* logf_dev);
 
-/* ---- shards (paper Sec. 5: MPI divides the dataset among processes) --------------------------
+/* ---- shards (paper Sec. 4: MPI divides the dataset among processes) --------------------------
  * Partial sums over events [begin, end) of ds: out[0] = sum of -log f, out[1] = its
  * compensation term, out[2] = number of events, out[3 .. 3+n_params) = gradient partials
  * (zero unless want_grad).  The normalisation is computed in full by every shard.

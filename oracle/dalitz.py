@@ -1,9 +1,9 @@
 """Three-body amplitude (Dalitz-plot) model, float64 / complex128, CPU.
 
-The paper lists a "specialized system for amplitude analyses of three body particle
-decays" among GooFit's PDFs (Sec. 1) and notes that its components include complex
-amplitudes whose magnitude squared is the PDF (Sec. 1, footnote); MC samples serve the
-normalisation integral (Sec. 6).  No formula is printed, so this file writes out the
+The paper lists dedicated amplitude-analysis PDFs for three-body decays among GooFit's
+PDFs (Sec. 1), notes that some components are complex amplitudes whose squared magnitude is
+the density (Sec. 1, footnote), and uses MC phase-space samples for the normalisation
+integral (Sec. 5).  No formula is printed, so this file writes out the
 standard isobar model:
 
   particles 1, 2, 3 of masses m1, m2, m3 from a parent of mass M; observables s12, s13;

@@ -1,6 +1,6 @@
 """Reference minimiser for fit-level parity (float64, CPU).
 
-The paper's FitManager drives Minuit 2 on the NLL (Fig. 1; Sec. 5).  Minuit's exact
+The paper's FitManager drives Minuit 2 on the NLL (Fig. 1; Sec. 4).  Minuit's exact
 rules are not needed for parity: what is compared is the location of the minimum and
 the parameter errors.  This oracle finds the minimum with scipy's BFGS on the free
 parameters (using the oracle's autograd gradient), polishes it with Newton steps on a

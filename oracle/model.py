@@ -1,7 +1,7 @@
 """Composite-PDF semantics, normalisation and the unbinned NLL (float64, CPU).
 
-Reading of the paper (Fig. 1 caption; Sec. 1: basic PDFs combined by "combination
-PDFs", fitted by a FitManager to an unbinned DataSet; RooFit semantics, Sec. 1):
+Reading of the paper (Fig. 1 caption; Sec. 1: basic PDFs put together by combination
+PDFs and fitted by a FitManager to an unbinned DataSet, following RooFit, Sec. 1):
 
   shape(leaf)  = the leaf's unnormalised shape u(x)                 (oracle/pdfs.py)
   shape(PROD)  = product of the children's shapes; the children act on disjoint observables

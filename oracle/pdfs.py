@@ -1,7 +1,7 @@
 """Basic one-dimensional shapes and their integrals over a finite range (float64).
 
-Each basic PDF of the paper's model language (Fig. 1; Sec. 1: "basic PDFs ... combined
-using combination PDFs") is represented by an unnormalised shape u(x) and, where one
+Each basic PDF of the paper's model language (Fig. 1; Sec. 1: basic shapes that
+combination PDFs put together) is represented by an unnormalised shape u(x) and, where one
 exists, the closed-form integral of u over the observable's range [lo, hi].  The paper
 names no formulas; these are the standard definitions:
 

@@ -2,7 +2,7 @@
 //
 // Paper: the FitManager evaluates the final PDF on an unbinned DataSet (Fig. 1); most of the
 // time of a fit is the per-event evaluation (Sec. 1); MPI splits the events among processes
-// (Sec. 5).
+// (Sec. 4).
 #include <cmath>
 #include <cstddef>
 #include <cstring>

@@ -2,8 +2,8 @@
 // and the host combination of shard partials.
 //
 // Paper: DataSets attach event data to observables (Fig. 1); input is range-checked so
-// that users who load data out of range are warned (Sec. 5); MPI runs divide the dataset
-// among processes and sum their partial results (Sec. 5).
+// that users who load data out of range are warned (Sec. 4); MPI runs divide the dataset
+// among processes and sum their partial results (Sec. 4).
 #include <cmath>
 #include <cstdlib>
 #include <cstring>

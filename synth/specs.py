@@ -16,7 +16,7 @@ Tree nodes (parameter and observable references are names):
 
 The paper (GooFit 2.0, Fig. 1 and Sec. 1) describes models built from basic PDFs combined
 by sum and product combination PDFs and amplitude PDFs for three-body decays (Sec. 1,
-Sec. 6); it prints no formulas, so the meaning of each node is fixed by the oracle.
+Sec. 5); it prints no formulas, so the meaning of each node is fixed by the oracle.
 """
 
 # Parent and daughter masses (GeV) of the D -> K pi pi0 - like three-body model.
