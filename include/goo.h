@@ -185,6 +185,36 @@ int goo_nll_partial(goo_model* model, const goo_dataset* ds, int64_t begin, int6
                     const double* theta, int precision, int want_grad, double* out);
 int goo_combine_partials(int n_parts, int n_params, const double* parts, double* out);
 
+/* ---- likelihood without device allocation ------------------------------------------------
+ * The paper has no counterpart to this call.  It computes the same NLL and gradient as
+ * goo_nll_grad for a sum/product model, but allocates nothing: no goo_ctx, goo_dataset or
+ * goo_model is needed.  It serves callers that cannot call cudaMalloc -- code running where
+ * another component owns all device memory (an application's own pool, a host framework
+ * whose allocator forbids side allocations) or code that cannot pay the implicit device
+ * synchronisation and latency of cudaMalloc/cudaFree on every call.
+ *
+ *   nodes..obs_hi, norm  the model exactly as for goo_model_build / goo_model_set_norm, but
+ *                        limited to two levels: a leaf, a PROD of leaves, or an ADD of leaves
+ *                        and PRODs of leaves; GOO_NORM_ANALYTIC or GOO_NORM_GRID.
+ *   cols_dev             n_obs device column pointers (16-byte aligned) of n_events values:
+ *                        float for GOO_F32, double for GOO_F64.  Not range-checked.
+ *   theta, nll_out, grad_out   host arrays as for goo_nll_grad.
+ *   cuda_stream          stream for the work (NULL: the legacy default stream).
+ *
+ * All intermediate device state lives in one file-scope device array of 1 MiB, which every
+ * GPU that loads the library holds until the process exits.  Maximum sizes: n_params <= 32,
+ * n_obs <= 4, <= 4 products of <= 4 leaves; larger requests fail with GOO_ERR_ARG or
+ * GOO_ERR_UNSUPPORTED and a message.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call reuses the same array and clears its counters
+ * first; the array keeps the previous call's contents otherwise.  Calls that overlap on the
+ * GPU (different streams or host threads, same device) race on the array: serialise them.
+ * The call returns after the result has been copied to the host. */
+int goo_nll_grad_static(const goo_node* nodes, int n_nodes, int n_params, int n_obs, const double* obs_lo,
+                        const double* obs_hi, const goo_norm_spec* norm, const void* const* cols_dev,
+                        int precision, int64_t n_events, const double* theta, void* cuda_stream,
+                        double* nll_out, double* grad_out);
+
 #ifdef __cplusplus
 }
 #endif

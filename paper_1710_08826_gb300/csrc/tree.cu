@@ -1217,3 +1217,264 @@ int sop_eval_logf(goo_model* m, const goo_dataset* ds, int precision, double* lo
 
 }  // namespace goo
 
+// =======================================================================================
+// goo_nll_grad_static: the sum/product likelihood without any device allocation
+//
+// For callers that cannot call cudaMalloc: code that runs where another component owns
+// all device memory (an application-level pool or a framework allocator that forbids side
+// allocations), or where the implicit device synchronisation and latency of cudaMalloc /
+// cudaFree cannot be paid on every call.  The caller passes the model description (host),
+// its device event columns and host outputs; everything else -- the model block, theta,
+// the reduction partials, counters and the result record -- lives in one file-scope
+// device array of fixed size.
+// =======================================================================================
+namespace goo {
+
+constexpr size_t kStaticScratchBytes = size_t(1) << 20;  // 1 MiB per device that loads the library
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr size_t kStOffModel = 0;
+constexpr size_t kStOffTheta = (sizeof(ModelDev) + 255) / 256 * 256;
+constexpr size_t kStOffCounters = kStOffTheta + 256;
+constexpr size_t kStOffResult = kStOffCounters + 256;
+constexpr size_t kStOffPartials = kStOffResult + 1024;
+constexpr size_t kStPartialsCap = (kStaticScratchBytes - kStOffPartials) / sizeof(float2);
+static_assert(kStOffPartials < kStaticScratchBytes, "static scratch too small for the model block");
+
+constexpr int kMaxDevices = 64;
+static unsigned char* g_static_ptr[kMaxDevices] = {nullptr};
+static int g_static_sms[kMaxDevices] = {0};
+
+// Once per device, with that device current: the device address of the scratch array.
+static int static_scratch_setup(int dev) {
+  if (g_static_ptr[dev]) return GOO_OK;
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess) return set_error(GOO_ERR_CUDA, "goo_nll_grad_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return set_error(GOO_ERR_CUDA, "goo_nll_grad_static: %s", cudaGetErrorString(e));
+  g_static_sms[dev] = sms;
+  g_static_ptr[dev] = (unsigned char*)p;
+  return GOO_OK;
+}
+
+// Host plan of a two-level model (leaf | PROD of leaves | ADD of leaves / PRODs), written
+// into a caller-stack ModelDev without heap use.
+static int static_plan(const goo_node* nodes, int n_nodes, int n_params, int n_obs, const double* lo, const double* hi,
+                       const goo_norm_spec* norm, ModelDev& h) {
+  std::memset(&h, 0, sizeof h);
+  h.n_obs = n_obs;
+  h.n_params = n_params;
+  for (int o = 0; o < n_obs; ++o) {
+    h.lo[o] = lo[o];
+    h.hi[o] = hi[o];
+  }
+  const goo_node& root = nodes[n_nodes - 1];
+  int comps[kMaxComp];
+  int nK = 0;
+  if (root.op == GOO_OP_ADD) {
+    if (root.n_child < 2 || root.n_child > kMaxComp)
+      return set_error(GOO_ERR_UNSUPPORTED, "goo_nll_grad_static: ADD with %d children (2..%d)", root.n_child, kMaxComp);
+    for (int c = 0; c < root.n_child; ++c) comps[nK++] = root.child[c];
+    h.n_add = 1;
+    h.add[0].n_child = root.n_child;
+    for (int j = 0; j < root.n_child - 1; ++j) {
+      if (root.par[j] < 0 || root.par[j] >= n_params)
+        return set_error(GOO_ERR_ARG, "goo_nll_grad_static: fraction %d has parameter %d", j, root.par[j]);
+      h.add[0].frac[j] = root.par[j];
+    }
+  } else {
+    comps[nK++] = n_nodes - 1;
+  }
+  h.nK = nK;
+  for (int k = 0; k < nK; ++k) {
+    const goo_node& cn = nodes[comps[k]];
+    int leaves[kMaxLeaf];
+    int nl = 0;
+    if (cn.op == GOO_OP_PROD) {
+      if (cn.n_child < 1 || cn.n_child > kMaxLeaf)
+        return set_error(GOO_ERR_UNSUPPORTED, "goo_nll_grad_static: product with %d factors (1..%d)", cn.n_child, kMaxLeaf);
+      for (int c = 0; c < cn.n_child; ++c) leaves[nl++] = cn.child[c];
+    } else {
+      leaves[nl++] = comps[k];
+    }
+    CompDev& C = h.comp[k];
+    C.n_leaf = nl;
+    if (root.op == GOO_OP_ADD) {
+      C.n_fac = 1;
+      C.fac_add[0] = 0;
+      C.fac_pos[0] = k;
+    }
+    for (int l = 0; l < nl; ++l) {
+      const goo_node& n = nodes[leaves[l]];
+      if (n.op < GOO_OP_GAUSS || n.op > GOO_OP_ARGUS)
+        return set_error(GOO_ERR_UNSUPPORTED, "goo_nll_grad_static: node %d (op %d) is not a leaf of a two-level "
+                         "sum of products", leaves[l], n.op);
+      LeafDev& L = h.leaf[k * kMaxLeaf + l];
+      L.op = n.op;
+      L.col = n.obs[0];
+      if (L.col < 0 || L.col >= n_obs) return set_error(GOO_ERR_ARG, "goo_nll_grad_static: observable %d", L.col);
+      for (int j = 0; j < 3; ++j) L.par[j] = -1;
+      for (int j = 0; j < leaf_npar(n.op); ++j) {
+        if (n.par[j] < 0 || n.par[j] >= n_params)
+          return set_error(GOO_ERR_ARG, "goo_nll_grad_static: leaf %d parameter %d", leaves[l], n.par[j]);
+        L.par[j] = n.par[j];
+      }
+    }
+  }
+  if (norm->kind == GOO_NORM_ANALYTIC) {
+    for (int k = 0; k < nK; ++k)
+      for (int l = 0; l < h.comp[k].n_leaf; ++l) {
+        const LeafDev& L = h.leaf[k * kMaxLeaf + l];
+        if (L.op == GOO_OP_ARGUS)
+          return set_error(GOO_ERR_UNSUPPORTED, "goo_nll_grad_static: Argus needs GOO_NORM_GRID");
+        for (int l2 = 0; l2 < l; ++l2)
+          if (h.leaf[k * kMaxLeaf + l2].col == L.col)
+            return set_error(GOO_ERR_UNSUPPORTED, "goo_nll_grad_static: two leaves on one observable need GOO_NORM_GRID");
+      }
+  } else if (norm->kind == GOO_NORM_GRID) {
+    for (int o = 0; o < n_obs; ++o)
+      if (norm->bins[o] < 1 || norm->bins[o] > (1 << 20))
+        return set_error(GOO_ERR_ARG, "goo_nll_grad_static: bins[%d] = %d", o, norm->bins[o]);
+    for (int k = 0; k < nK; ++k) {
+      GridDev& G = h.grid[k];
+      bool used[kMaxObs] = {false, false, false, false};
+      for (int l = 0; l < h.comp[k].n_leaf; ++l) used[h.leaf[k * kMaxLeaf + l].col] = true;
+      for (int o = 0; o < kMaxObs; ++o) G.dim_of_col[o] = -1;
+      G.cell_volume = 1.0;
+      for (int o = 0; o < n_obs; ++o) {
+        if (!used[o]) continue;
+        const int d = G.ndim++;
+        G.dim_of_col[o] = d;
+        G.bins[d] = norm->bins[o];
+        const double step = (hi[o] - lo[o]) / norm->bins[o];
+        G.h64[d] = step;
+        G.lo64[d] = lo[o];
+        G.h_hi[d] = (float)step;
+        G.h_lo[d] = (float)(step - (double)(float)step);
+        G.lo_hi[d] = (float)lo[o];
+        G.lo_lo[d] = (float)(lo[o] - (double)(float)lo[o]);
+        G.cell_volume *= step;
+      }
+    }
+  } else {
+    return set_error(GOO_ERR_UNSUPPORTED, "goo_nll_grad_static: only GOO_NORM_ANALYTIC and GOO_NORM_GRID");
+  }
+  h.norm_kind = norm->kind;
+  return GOO_OK;
+}
+
+template <typename T, int K, int L>
+static int static_launch(const ModelDev& h, int max_leaf, unsigned char* base, int sms, const void* const* cols_dev,
+                         int64_t n, int precision, cudaStream_t st) {
+  ModelDev* md = (ModelDev*)(base + kStOffModel);
+  double* theta_d = (double*)(base + kStOffTheta);
+  unsigned* counters = (unsigned*)(base + kStOffCounters);
+  double* result = (double*)(base + kStOffResult);
+  float2* partials = (float2*)(base + kStOffPartials);
+  prep_kernel<<<1, 64, 0, st>>>(md, theta_d, precision);
+  if (h.norm_kind == GOO_NORM_GRID) {
+    constexpr int NSg = 1 + 3 * L;
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, grid_kernel<T, L>, kBlock, 0) != cudaSuccess || bps < 1) {
+      cudaGetLastError();
+      bps = 1;
+    }
+    int64_t units_max = 1;
+    for (int k = 0; k < h.nK; ++k) {
+      const GridDev& G = h.grid[k];
+      int64_t rows = 1;
+      for (int d = 0; d < G.ndim - 1; ++d) rows *= G.bins[d];
+      const int64_t u = rows * ((G.bins[G.ndim - 1] + kSeg - 1) / kSeg);
+      units_max = u > units_max ? u : units_max;
+    }
+    int64_t nbx = (units_max + kBlock - 1) / kBlock;
+    const int64_t cap = ((int64_t)sms * bps + h.nK - 1) / h.nK;
+    if (nbx > cap) nbx = cap;
+    const int64_t fit = (int64_t)(kStPartialsCap / ((size_t)NSg * h.nK));
+    if (nbx > fit) nbx = fit;
+    if (nbx < 1) return set_error(GOO_ERR_UNSUPPORTED, "goo_nll_grad_static: scratch too small for the grid");
+    grid_kernel<T, L><<<dim3((unsigned)nbx, h.nK), kBlock, 0, st>>>(md, partials, counters);
+  }
+  constexpr int NS = EventLanes<T, K, L, true>::NS;
+  int bps = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, sop_event_kernel<T, K, L, true>, kBlock, 0) != cudaSuccess ||
+      bps < 1) {
+    cudaGetLastError();
+    bps = 1;
+  }
+  int64_t nb = (n + kBlock - 1) / kBlock;
+  if (nb > (int64_t)sms * bps) nb = (int64_t)sms * bps;
+  if (nb > (int64_t)(kStPartialsCap / NS)) nb = (int64_t)(kStPartialsCap / NS);
+  if (nb < 1) nb = 1;
+  Cols<T> cols{};
+  for (int c = 0; c < kMaxObs; ++c) cols.c[c] = (const T*)cols_dev[c < h.n_obs ? c : 0];
+  sop_event_kernel<T, K, L, true><<<(unsigned)nb, kBlock, 0, st>>>(md, cols, 0, n, partials, counters, result, 0);
+  (void)max_leaf;
+  GOO_CUDA_TRY(cudaGetLastError());
+  return GOO_OK;
+}
+
+}  // namespace goo
+
+extern "C" int goo_nll_grad_static(const goo_node* nodes, int n_nodes, int n_params, int n_obs, const double* obs_lo,
+                                   const double* obs_hi, const goo_norm_spec* norm, const void* const* cols_dev,
+                                   int precision, int64_t n_events, const double* theta, void* cuda_stream,
+                                   double* nll_out, double* grad_out) {
+  using namespace goo;
+  if (!nodes || !obs_lo || !obs_hi || !norm || !theta || !nll_out || !grad_out || (n_events > 0 && !cols_dev))
+    return set_error(GOO_ERR_ARG, "goo_nll_grad_static: NULL argument");
+  if (n_nodes < 1 || n_nodes > 256) return set_error(GOO_ERR_ARG, "goo_nll_grad_static: n_nodes=%d", n_nodes);
+  if (n_params < 0 || n_params > kMaxParams)
+    return set_error(GOO_ERR_ARG, "goo_nll_grad_static: n_params=%d exceeds the maximum %d", n_params, kMaxParams);
+  if (n_obs < 1 || n_obs > kMaxObs) return set_error(GOO_ERR_ARG, "goo_nll_grad_static: n_obs=%d (1..%d)", n_obs, kMaxObs);
+  if (n_events < 0) return set_error(GOO_ERR_ARG, "goo_nll_grad_static: n_events=%lld", (long long)n_events);
+  if (precision != GOO_F64 && precision != GOO_F32) return set_error(GOO_ERR_ARG, "goo_nll_grad_static: precision");
+  for (int i = 0; i < n_nodes; ++i)
+    for (int c = 0; c < nodes[i].n_child; ++c)
+      if (nodes[i].n_child > GOO_MAX_CHILD || nodes[i].child[c] < 0 || nodes[i].child[c] >= i)
+        return set_error(GOO_ERR_ARG, "goo_nll_grad_static: node %d is not in post-order", i);
+  for (int p = 0; p < n_params; ++p)
+    if (!std::isfinite(theta[p])) return set_error(GOO_ERR_ARG, "goo_nll_grad_static: theta[%d] is not finite", p);
+  for (int c = 0; n_events > 0 && c < n_obs; ++c)
+    if (!cols_dev[c] || ((uintptr_t)cols_dev[c] & 15))
+      return set_error(GOO_ERR_ARG, "goo_nll_grad_static: column %d is NULL or not 16-byte aligned", c);
+  ModelDev h;
+  GOO_TRY(static_plan(nodes, n_nodes, n_params, n_obs, obs_lo, obs_hi, norm, h));
+  int max_leaf = 0;
+  for (int k = 0; k < h.nK; ++k) max_leaf = h.comp[k].n_leaf > max_leaf ? h.comp[k].n_leaf : max_leaf;
+  int dev = 0;
+  GOO_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(GOO_ERR_ARG, "goo_nll_grad_static: device %d", dev);
+  GOO_TRY(static_scratch_setup(dev));
+  unsigned char* base = g_static_ptr[dev];
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (n_events == 0) {
+    *nll_out = 0.0;
+    for (int p = 0; p < n_params; ++p) grad_out[p] = 0.0;
+    return GOO_OK;
+  }
+  GOO_CUDA_TRY(cudaMemcpyAsync(base + kStOffModel, &h, sizeof(ModelDev), cudaMemcpyHostToDevice, st));
+  GOO_CUDA_TRY(cudaMemcpyAsync(base + kStOffTheta, theta, n_params * sizeof(double), cudaMemcpyHostToDevice, st));
+  GOO_CUDA_TRY(cudaMemsetAsync(base + kStOffCounters, 0, 256, st));
+  const bool small = h.nK <= 2 && max_leaf <= 3;
+  if (precision == GOO_F32) {
+    GOO_TRY((small ? static_launch<float, 2, 3>(h, max_leaf, base, g_static_sms[dev], cols_dev, n_events, precision, st)
+                   : static_launch<float, 4, 4>(h, max_leaf, base, g_static_sms[dev], cols_dev, n_events, precision, st)));
+  } else {
+    GOO_TRY((small ? static_launch<double, 2, 3>(h, max_leaf, base, g_static_sms[dev], cols_dev, n_events, precision, st)
+                   : static_launch<double, 4, 4>(h, max_leaf, base, g_static_sms[dev], cols_dev, n_events, precision, st)));
+  }
+  double res[2 + kMaxParams];
+  GOO_CUDA_TRY(cudaMemcpyAsync(res, base + kStOffResult, (2 + n_params) * sizeof(double), cudaMemcpyDeviceToHost, st));
+  GOO_CUDA_TRY(cudaStreamSynchronize(st));
+  if (res[1] > 0) {
+    *nll_out = HUGE_VAL;
+    for (int p = 0; p < n_params; ++p) grad_out[p] = 0.0;
+    return set_error(GOO_ERR_NONPOSITIVE_PDF, "goo_nll_grad_static: density <= 0 for %.0f events", res[1]);
+  }
+  *nll_out = res[0];
+  for (int p = 0; p < n_params; ++p) grad_out[p] = res[2 + p];
+  return GOO_OK;
+}
