@@ -135,6 +135,7 @@ int goo_model_free(goo_model* m) {
   cudaSetDevice(m->ctx->device);
   cudaStreamSynchronize(m->ctx->stream);
   if (m->dev) cudaFree(m->dev);
+  if (m->stage) cudaFreeHost(m->stage);
   if (m->dalitz) dalitz_free(m);
   delete m;
   return GOO_OK;
@@ -222,6 +223,25 @@ int goo_nll_partial(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t 
                      (long long)begin, (long long)end);
   }
   return GOO_OK;
+}
+
+int goo_gram(goo_model* m, const double* theta, int precision, double* out, int* K_out) {
+  if (!m || !out || !K_out) return set_error(GOO_ERR_ARG, "goo_gram: NULL argument");
+  if (m->kind != 1) return set_error(GOO_ERR_STATE, "goo_gram: not an amplitude model");
+  if (precision != GOO_F64 && precision != GOO_F32) return set_error(GOO_ERR_ARG, "precision=%d", precision);
+  GOO_TRY(check_theta(m, theta));
+  GOO_CUDA_TRY(cudaSetDevice(m->ctx->device));
+  return dalitz_gram(m, theta, precision, out, K_out);
+}
+
+int goo_amplitude_cache(goo_model* m, const goo_dataset* ds, const double* theta, int precision, const void** dev_ptr,
+                        int* n_amp) {
+  if (!m || !ds || !dev_ptr || !n_amp) return set_error(GOO_ERR_ARG, "goo_amplitude_cache: NULL argument");
+  if (m->kind != 1) return set_error(GOO_ERR_STATE, "goo_amplitude_cache: not an amplitude model");
+  GOO_TRY(check_model_dataset(m, ds, precision));
+  GOO_TRY(check_theta(m, theta));
+  GOO_CUDA_TRY(cudaSetDevice(m->ctx->device));
+  return dalitz_amplitudes(m, ds, theta, precision, dev_ptr, n_amp);
 }
 
 }  // extern "C"

@@ -56,6 +56,7 @@ int build_sop_model(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_para
                     const double* lo, const double* hi, goo_model* m);
 int sop_set_norm(goo_model* m, const goo_norm_spec* spec);
 int sop_prepare(goo_model* m, const double* theta_host, int precision);
+void host_prep(ModelDev& h, const double* theta, int precision);
 int sop_events(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int precision, bool grad,
                int out_mode);
 int sop_eval_logf(goo_model* m, const goo_dataset* ds, int precision, double* logf_dev);
@@ -68,6 +69,9 @@ int dalitz_normalise(goo_model* m, const double* theta, int precision, double* n
 int dalitz_nll(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, const double* theta,
                int precision, bool grad, double* out, int out_mode);
 int dalitz_eval_logf(goo_model* m, const goo_dataset* ds, const double* theta, int precision, double* logf_dev);
+int dalitz_gram(goo_model* m, const double* theta, int precision, double* out, int* K_out);
+int dalitz_amplitudes(goo_model* m, const goo_dataset* ds, const double* theta, int precision, const void** cache,
+                      int* nbw);
 
 }  // namespace goo
 
@@ -81,5 +85,6 @@ struct goo_model {
   int max_leaf = 0;
   goo::ModelDev host{};
   goo::ModelDev* dev = nullptr;
+  goo::ModelDev* stage = nullptr;  // pinned host staging of the per-call model block
   goo::DalitzModel* dalitz = nullptr;
 };

@@ -43,9 +43,10 @@
 namespace goo {
 
 // =======================================================================================
-// parameter preparation (one warp)
+// parameter preparation (a1): per-theta derived constants, computed on the host in FP64
+// and uploaded with theta in one copy (O(number of leaves) work)
 // =======================================================================================
-__device__ double gauss_log_norm(double lo, double hi, double mu, double sig, double* dmu, double* dsig) {
+static double gauss_log_norm(double lo, double hi, double mu, double sig, double* dmu, double* dsig) {
   // N = sig sqrt(pi/2) [erf(b) - erf(a)], a = (lo-mu)/(sqrt2 sig), b = (hi-mu)/(sqrt2 sig)
   const double r2 = 1.4142135623730951, c = 1.2533141373155003;  // sqrt(2), sqrt(pi/2)
   double a = (lo - mu) / (r2 * sig), b = (hi - mu) / (r2 * sig);
@@ -61,7 +62,7 @@ __device__ double gauss_log_norm(double lo, double hi, double mu, double sig, do
   return log(N);
 }
 
-__device__ double expo_log_norm(double lo, double hi, double lam, double* dlam) {
+static double expo_log_norm(double lo, double hi, double lam, double* dlam) {
   const double d = hi - lo;
   if (fabs(lam * d) < 1e-5) {
     // N = d (1 + lam (lo+hi)/2 + ...),  d log N / d lam = mean of x + lam d^2/12 + ...
@@ -78,7 +79,7 @@ __device__ double expo_log_norm(double lo, double hi, double lam, double* dlam) 
   return logN;
 }
 
-__device__ double poly2_log_norm(double lo, double hi, double a1, double a2, double* da1, double* da2) {
+static double poly2_log_norm(double lo, double hi, double a1, double a2, double* da1, double* da2) {
   double i1 = 0.5 * (hi * hi - lo * lo), i2 = (hi * hi * hi - lo * lo * lo) / 3.0;
   double N = (hi - lo) + a1 * i1 + a2 * i2;
   *da1 = i1 / N;
@@ -87,7 +88,7 @@ __device__ double poly2_log_norm(double lo, double hi, double a1, double a2, dou
 }
 
 // Upper bound of the leaf's log-domain exponent a over [lo, hi] (grid reference scale).
-__device__ double leaf_max_exponent(int op, double lo, double hi, const double* d) {
+static double leaf_max_exponent(int op, double lo, double hi, const double* d) {
   if (op == GOO_OP_GAUSS) {
     double mu = d[0], is = d[1];
     double x = mu < lo ? lo : (mu > hi ? hi : mu);
@@ -106,70 +107,30 @@ __device__ double leaf_max_exponent(int op, double lo, double hi, const double* 
   return 0.0;
 }
 
-// One block of 64 threads: the model's leaf, product and ADD tables and theta are first
-// copied into shared memory (dependent global loads are the latency that dominates this
-// tiny kernel), one thread per leaf then derives its constants (and, for analytic
-// normalisation, its closed-form log-integral and derivatives), one thread per product
-// forms the weight, its derivatives and log N, and the tables are written back.
-__global__ void __launch_bounds__(64) prep_kernel(ModelDev* md, const double* __restrict__ theta, int precision) {
-  __shared__ CompDev s_comp[kMaxComp];
-  __shared__ LeafDev s_leaf[kMaxComp * kMaxLeaf];
-  __shared__ AddDev s_add[kMaxAdd];
-  __shared__ double s_theta[kMaxParams];
-  __shared__ double s_lo[kMaxObs], s_hi[kMaxObs];
-  __shared__ double s_logN[kMaxComp * kMaxLeaf];
-  __shared__ double s_dlogN[kMaxComp * kMaxLeaf][3];
-  __shared__ double s_amax[kMaxComp * kMaxLeaf];
-  __shared__ double s_dw[kMaxComp][kMaxParams];
-  __shared__ double s_dN[kMaxComp][kMaxParams];
-  __shared__ int s_meta[3];
-  const int t = threadIdx.x;
-  {
-    // cooperative copies of the static tables
-    const int* src = (const int*)md->comp;
-    int* dst = (int*)s_comp;
-    for (int i = t; i < (int)(sizeof(s_comp) / 4); i += blockDim.x) dst[i] = src[i];
-    src = (const int*)md->leaf;
-    dst = (int*)s_leaf;
-    for (int i = t; i < (int)(sizeof(s_leaf) / 4); i += blockDim.x) dst[i] = src[i];
-    src = (const int*)md->add;
-    dst = (int*)s_add;
-    for (int i = t; i < (int)(sizeof(s_add) / 4); i += blockDim.x) dst[i] = src[i];
-    if (t < kMaxParams) s_theta[t] = t < md->n_params ? theta[t] : 0.0;
-    if (t < kMaxObs) {
-      s_lo[t] = md->lo[t];
-      s_hi[t] = md->hi[t];
-    }
-    if (t == 0) {
-      s_meta[0] = md->nK;
-      s_meta[1] = md->norm_kind;
-      s_meta[2] = md->n_params;
-    }
-    for (int i = t; i < kMaxComp * kMaxParams; i += blockDim.x) {
-      s_dw[i / kMaxParams][i % kMaxParams] = 0.0;
-      s_dN[i / kMaxParams][i % kMaxParams] = 0.0;
-    }
-  }
-  __syncthreads();
-  const int nK = s_meta[0];
-  const bool analytic = s_meta[1] == GOO_NORM_ANALYTIC;
+// Fills the per-theta fields of a model block whose static fields (opcodes, columns,
+// parameter indices, products, ADD tables, grid geometry) are already set: per-leaf FP32 and
+// FP64 constants, per-product weights w_k and dw/dtheta, the grid reference exponents, and
+// for analytic normalisation log N_k with d log N_k / d theta.  In the FP32 path the closed
+// forms are taken at the FP32-rounded parameters the kernels use.
+void host_prep(ModelDev& h, const double* theta, int precision) {
+  const bool analytic = h.norm_kind == GOO_NORM_ANALYTIC;
   const bool f32 = precision == GOO_F32;
-  if (t < kMaxComp * kMaxLeaf) {
-    const int k = t / kMaxLeaf, l = t % kMaxLeaf;
-    s_logN[t] = 0.0;
-    s_dlogN[t][0] = s_dlogN[t][1] = s_dlogN[t][2] = 0.0;
-    s_amax[t] = 0.0;
-    if (k < nK && l < s_comp[k].n_leaf) {
-      LeafDev& L = s_leaf[t];
-      const double lo = s_lo[L.col], hi = s_hi[L.col];
-      const double p0 = L.par[0] >= 0 ? s_theta[L.par[0]] : 0.0;
-      const double p1 = L.par[1] >= 0 ? s_theta[L.par[1]] : 0.0;
-      const double p2 = L.par[2] >= 0 ? s_theta[L.par[2]] : 0.0;
+  double logN_leaf[kMaxComp * kMaxLeaf] = {0};
+  double dlog_leaf[kMaxComp * kMaxLeaf][3] = {{0}};
+  double amax_leaf[kMaxComp * kMaxLeaf] = {0};
+  for (int k = 0; k < h.nK; ++k) {
+    for (int l = 0; l < h.comp[k].n_leaf; ++l) {
+      const int t = k * kMaxLeaf + l;
+      LeafDev& L = h.leaf[t];
+      const double lo = h.lo[L.col], hi = h.hi[L.col];
+      const double p0 = L.par[0] >= 0 ? theta[L.par[0]] : 0.0;
+      const double p1 = L.par[1] >= 0 ? theta[L.par[1]] : 0.0;
+      const double p2 = L.par[2] >= 0 ? theta[L.par[2]] : 0.0;
       for (int i = 0; i < 6; ++i) {
         L.d[i] = 0.0;
         L.f[i] = 0.f;
       }
-      double logN = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+      double g0 = 0.0, g1 = 0.0;
       switch (L.op) {
         case GOO_OP_GAUSS: {
           L.d[0] = p0;
@@ -181,27 +142,26 @@ __global__ void __launch_bounds__(64) prep_kernel(ModelDev* md, const double* __
           if (analytic) {
             const double mu = f32 ? (double)L.f[0] + (double)L.f[1] : p0;
             const double sg = f32 ? 1.0 / (double)L.f[2] : p1;
-            logN = gauss_log_norm(lo, hi, mu, sg, &g0, &g1);
+            logN_leaf[t] = gauss_log_norm(lo, hi, mu, sg, &g0, &g1);
           } else {
-            s_amax[t] = leaf_max_exponent(L.op, lo, hi, L.d);
+            amax_leaf[t] = leaf_max_exponent(L.op, lo, hi, L.d);
           }
           break;
         }
-        case GOO_OP_EXPO: {
+        case GOO_OP_EXPO:
           L.d[0] = p0;
           L.f[0] = (float)p0;
-          if (analytic) logN = expo_log_norm(lo, hi, f32 ? (double)L.f[0] : p0, &g0);
-          else s_amax[t] = leaf_max_exponent(L.op, lo, hi, L.d);
+          if (analytic) logN_leaf[t] = expo_log_norm(lo, hi, f32 ? (double)L.f[0] : p0, &g0);
+          else amax_leaf[t] = leaf_max_exponent(L.op, lo, hi, L.d);
           break;
-        }
-        case GOO_OP_POLY2: {
+        case GOO_OP_POLY2:
           L.d[0] = p0;
           L.d[1] = p1;
           L.f[0] = (float)p0;
           L.f[1] = (float)p1;
-          if (analytic) logN = poly2_log_norm(lo, hi, f32 ? (double)L.f[0] : p0, f32 ? (double)L.f[1] : p1, &g0, &g1);
+          if (analytic)
+            logN_leaf[t] = poly2_log_norm(lo, hi, f32 ? (double)L.f[0] : p0, f32 ? (double)L.f[1] : p1, &g0, &g1);
           break;
-        }
         case GOO_OP_ARGUS: {
           L.d[0] = p0;
           L.d[1] = 1.0 / (p0 * p0);
@@ -215,84 +175,69 @@ __global__ void __launch_bounds__(64) prep_kernel(ModelDev* md, const double* __
           L.f[3] = (float)p1;
           L.f[4] = (float)p2;
           L.f[5] = (float)(2.0 / p0);
-          if (!analytic) s_amax[t] = leaf_max_exponent(L.op, lo, hi, L.d);
+          if (!analytic) amax_leaf[t] = leaf_max_exponent(L.op, lo, hi, L.d);
           break;
         }
         default:
           break;
       }
-      s_logN[t] = logN;
-      s_dlogN[t][0] = g0;
-      s_dlogN[t][1] = g1;
-      s_dlogN[t][2] = g2;
+      dlog_leaf[t][0] = g0;
+      dlog_leaf[t][1] = g1;
     }
   }
-  __syncthreads();
-  if (t < nK) {
-    const int k = t;
-    CompDev& C = s_comp[k];
+  for (int k = 0; k < kMaxComp; ++k)
+    for (int p = 0; p < kMaxParams; ++p) {
+      h.dw[k][p] = 0.0;
+      if (analytic) h.dlogN[k][p] = 0.0;
+    }
+  for (int k = 0; k < h.nK; ++k) {
+    CompDev& C = h.comp[k];
     double fac[8];
     double w = 1.0;
     for (int f = 0; f < C.n_fac; ++f) {
-      const AddDev& A = s_add[C.fac_add[f]];
+      const AddDev& A = h.add[C.fac_add[f]];
       double v;
       if (C.fac_pos[f] < A.n_child - 1) {
-        v = s_theta[A.frac[C.fac_pos[f]]];
+        v = theta[A.frac[C.fac_pos[f]]];
       } else {
         v = 1.0;
-        for (int j = 0; j < A.n_child - 1; ++j) v -= s_theta[A.frac[j]];
+        for (int j = 0; j < A.n_child - 1; ++j) v -= theta[A.frac[j]];
       }
       fac[f] = v;
       w *= v;
     }
-    // dw/dtheta: product rule over the factors
+    // dw/dtheta: product rule over the ADD factors
     for (int f = 0; f < C.n_fac; ++f) {
-      const AddDev& A = s_add[C.fac_add[f]];
+      const AddDev& A = h.add[C.fac_add[f]];
       double rest = 1.0;
       for (int g = 0; g < C.n_fac; ++g)
         if (g != f) rest *= fac[g];
       if (C.fac_pos[f] < A.n_child - 1) {
-        s_dw[k][A.frac[C.fac_pos[f]]] += rest;
+        h.dw[k][A.frac[C.fac_pos[f]]] += rest;
       } else {
-        for (int j = 0; j < A.n_child - 1; ++j) s_dw[k][A.frac[j]] -= rest;
+        for (int j = 0; j < A.n_child - 1; ++j) h.dw[k][A.frac[j]] -= rest;
       }
     }
     C.w = w;
-    const float wh = (float)w;
-    C.w_hi = wh;
-    C.w_lo = (float)(w - (double)wh);
+    C.w_hi = (float)w;
+    C.w_lo = (float)(w - (double)C.w_hi);
     double amax = 0.0;
-    for (int l = 0; l < C.n_leaf; ++l) amax += s_amax[k * kMaxLeaf + l];
+    for (int l = 0; l < C.n_leaf; ++l) amax += amax_leaf[k * kMaxLeaf + l];
     C.a_ref = amax;
-    const float ah = (float)amax;
-    C.a_ref_hi = ah;
-    C.a_ref_lo = (float)(amax - (double)ah);
+    C.a_ref_hi = (float)amax;
+    C.a_ref_lo = (float)(amax - (double)C.a_ref_hi);
     if (analytic) {
       double logN = 0.0;
       for (int l = 0; l < C.n_leaf; ++l) {
         const int li = k * kMaxLeaf + l;
-        logN += s_logN[li];
-        const LeafDev& L = s_leaf[li];
+        logN += logN_leaf[li];
+        const LeafDev& L = h.leaf[li];
         for (int j = 0; j < 3; ++j)
-          if (L.par[j] >= 0) s_dN[k][L.par[j]] += s_dlogN[li][j];
+          if (L.par[j] >= 0) h.dlogN[k][L.par[j]] += dlog_leaf[li][j];
       }
       C.log_norm = logN;
-      const float oh = (float)(-logN);
-      C.off_hi = oh;
-      C.off_lo = (float)(-logN - (double)oh);
-    }
-  }
-  __syncthreads();
-  {
-    const int* src = (const int*)s_comp;
-    int* dst = (int*)md->comp;
-    for (int i = t; i < (int)(sizeof(s_comp) / 4); i += blockDim.x) dst[i] = src[i];
-    src = (const int*)s_leaf;
-    dst = (int*)md->leaf;
-    for (int i = t; i < (int)(sizeof(s_leaf) / 4); i += blockDim.x) dst[i] = src[i];
-    for (int i = t; i < kMaxComp * kMaxParams; i += blockDim.x) {
-      md->dw[i / kMaxParams][i % kMaxParams] = s_dw[i / kMaxParams][i % kMaxParams];
-      if (analytic) md->dlogN[i / kMaxParams][i % kMaxParams] = s_dN[i / kMaxParams][i % kMaxParams];
+      C.off_hi = (float)(-logN);
+      C.off_lo = (float)(-logN - (double)C.off_hi);
     }
   }
 }
@@ -567,11 +512,25 @@ __global__ void __launch_bounds__(kBlock, 2) sop_event_kernel(const ModelDev* __
   unsigned bad = 0;
   const int nobs = md->n_obs;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end; i += stride) {
-    const T x0 = cols.c[0][i];
-    const T x1 = nobs > 1 ? cols.c[1][i] : T(0);
-    const T x2 = nobs > 2 ? cols.c[2][i] : T(0);
-    const T x3 = nobs > 3 ? cols.c[3][i] : T(0);
+  // software pipelining: the next event's columns are requested before this event is
+  // evaluated, so the loads' latency overlaps the arithmetic
+  int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  T n0 = T(0), n1 = T(0), n2 = T(0), n3 = T(0);
+  if (i < end) {
+    n0 = cols.c[0][i];
+    n1 = nobs > 1 ? cols.c[1][i] : T(0);
+    n2 = nobs > 2 ? cols.c[2][i] : T(0);
+    n3 = nobs > 3 ? cols.c[3][i] : T(0);
+  }
+  for (; i < end; i += stride) {
+    const T x0 = n0, x1 = n1, x2 = n2, x3 = n3;
+    const int64_t inext = i + stride;
+    if (inext < end) {
+      n0 = cols.c[0][inext];
+      n1 = nobs > 1 ? cols.c[1][inext] : T(0);
+      n2 = nobs > 2 ? cols.c[2][inext] : T(0);
+      n3 = nobs > 3 ? cols.c[3][inext] : T(0);
+    }
     T logf, ck[K], dk[K][L][3];
     if (eval_event<T, K, L, GRAD>(lr, cr, nK, x0, x1, x2, x3, logf, ck, dk)) {
       if constexpr (sizeof(T) == 4) {
@@ -1021,7 +980,7 @@ int build_sop_model(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_para
   }
   m->max_leaf = max_leaf;
   m->kind = 0;
-  if (cudaMalloc(&m->dev, sizeof(ModelDev)) != cudaSuccess) {
+  if (cudaMalloc(&m->dev, sizeof(ModelDev)) != cudaSuccess || cudaMallocHost(&m->stage, sizeof(ModelDev)) != cudaSuccess) {
     cudaGetLastError();
     return set_error(GOO_ERR_OOM, "goo_model_build: cannot allocate model block");
   }
@@ -1127,20 +1086,17 @@ static int launch_grid_T(goo_model* m) {
 
 int sop_prepare(goo_model* m, const double* theta_host, int precision) {
   goo_ctx* ctx = m->ctx;
-  Scratch& s = ctx->scratch;
-  const int P = m->host.n_params;
-  std::memcpy(s.host_pinned, theta_host, P * sizeof(double));
-  GOO_CUDA_TRY(cudaMemcpyAsync(s.theta, s.host_pinned, P * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-  {
-    LaunchScope ls(ctx, "prep");
-    prep_kernel<<<1, 64, 0, ctx->stream>>>(m->dev, s.theta, precision);
-  }
-  GOO_CUDA_TRY(cudaGetLastError());
+  ModelDev* stage = m->stage;
+  *stage = m->host;
+  host_prep(*stage, theta_host, precision);
+  GOO_CUDA_TRY(cudaMemcpyAsync(m->dev, stage, sizeof(ModelDev), cudaMemcpyHostToDevice, ctx->stream));
   if (m->host.norm_kind == GOO_NORM_GRID) {
     if (precision == GOO_F32) {
-      GOO_TRY((m->max_leaf <= 2 ? launch_grid_T<float, 2>(m) : launch_grid_T<float, 4>(m)));
+      GOO_TRY((m->max_leaf <= 2 ? launch_grid_T<float, 2>(m)
+                                : (m->max_leaf <= 3 ? launch_grid_T<float, 3>(m) : launch_grid_T<float, 4>(m))));
     } else {
-      GOO_TRY((m->max_leaf <= 2 ? launch_grid_T<double, 2>(m) : launch_grid_T<double, 4>(m)));
+      GOO_TRY((m->max_leaf <= 2 ? launch_grid_T<double, 2>(m)
+                                : (m->max_leaf <= 3 ? launch_grid_T<double, 3>(m) : launch_grid_T<double, 4>(m))));
     }
   }
   return GOO_OK;
@@ -1369,11 +1325,10 @@ template <typename T, int K, int L>
 static int static_launch(const ModelDev& h, int max_leaf, unsigned char* base, int sms, const void* const* cols_dev,
                          int64_t n, int precision, cudaStream_t st) {
   ModelDev* md = (ModelDev*)(base + kStOffModel);
-  double* theta_d = (double*)(base + kStOffTheta);
   unsigned* counters = (unsigned*)(base + kStOffCounters);
   double* result = (double*)(base + kStOffResult);
   float2* partials = (float2*)(base + kStOffPartials);
-  prep_kernel<<<1, 64, 0, st>>>(md, theta_d, precision);
+  (void)precision;
   if (h.norm_kind == GOO_NORM_GRID) {
     constexpr int NSg = 1 + 3 * L;
     int bps = 0;
@@ -1455,8 +1410,8 @@ extern "C" int goo_nll_grad_static(const goo_node* nodes, int n_nodes, int n_par
     for (int p = 0; p < n_params; ++p) grad_out[p] = 0.0;
     return GOO_OK;
   }
+  host_prep(h, theta, precision);
   GOO_CUDA_TRY(cudaMemcpyAsync(base + kStOffModel, &h, sizeof(ModelDev), cudaMemcpyHostToDevice, st));
-  GOO_CUDA_TRY(cudaMemcpyAsync(base + kStOffTheta, theta, n_params * sizeof(double), cudaMemcpyHostToDevice, st));
   GOO_CUDA_TRY(cudaMemsetAsync(base + kStOffCounters, 0, 256, st));
   const bool small = h.nK <= 2 && max_leaf <= 3;
   if (precision == GOO_F32) {
