@@ -175,6 +175,19 @@ int goo_nll_grad(goo_model* model, const goo_dataset* ds, const double* theta, i
 int goo_eval_logf(goo_model* model, const goo_dataset* ds, const double* theta, int precision,
                   double* logf_dev);
 
+/* ---- amplitude models (paper Sec. 1, Sec. 4, Sec. 5) ------------------------------------------
+ * For a GOO_OP_COHERENT model: the MC Gram matrix G_kl = mean over the MC sample of
+ * A_k conj(A_l) at theta's lineshape parameters (K x K complex, row-major, re/im interleaved,
+ * amplitudes in tree order with the non-resonant amplitude last), K written to *K_out; and
+ * the device pointer of the dataset's cached resonance amplitudes (built if stale; layout:
+ * GOO_F32 -> ceil(n_amp/2) planes of float4 (re_k, im_k, re_k+1, im_k+1) per event,
+ * GOO_F64 -> n_amp planes of double2 per event; plane p starts at p * n_events).  The cache
+ * is owned by the dataset and rebuilt when the model or its lineshape parameters change
+ * (paper Sec. 4: cached partial results in structure-of-arrays form, change detection). */
+int goo_gram(goo_model* model, const double* theta, int precision, double* out, int* K_out);
+int goo_amplitude_cache(goo_model* model, const goo_dataset* ds, const double* theta, int precision,
+                        const void** dev_ptr, int* n_amp);
+
 /* ---- shards (paper Sec. 4: MPI divides the dataset among processes) --------------------------
  * Partial sums over events [begin, end) of ds: out[0] = sum of -log f, out[1] = its
  * compensation term, out[2] = number of events, out[3 .. 3+n_params) = gradient partials

@@ -36,7 +36,7 @@ int check_theta(const goo_model* m, const double* theta) {
 
 // Reads `n` result doubles into the pinned staging area and waits for the stream.
 int read_result(goo_ctx* ctx, int n, double* dst) {
-  double* stage = ctx->scratch.host_pinned + 128;
+  double* stage = ctx->scratch.host_pinned + kPinnedResult;
   GOO_CUDA_TRY(cudaMemcpyAsync(stage, ctx->scratch.result, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   std::memcpy(dst, stage, n * sizeof(double));

@@ -43,12 +43,14 @@ int log_level();
 // ---------------------------------------------------------------------------------------
 // limits
 // ---------------------------------------------------------------------------------------
-constexpr int kMaxParams = 32;     // parameters of one model
+constexpr int kMaxParams = 128;    // parameters of one model
 constexpr int kMaxObs = 4;         // observables of one model
 constexpr int kMaxComp = 4;        // products in the flattened sum of products
 constexpr int kMaxLeaf = 4;        // leaves per product
 constexpr int kMaxSlots = 64;      // reduction lanes of one kernel
 constexpr int kBlock = 256;        // threads per block of the likelihood kernels
+constexpr int kResultDoubles = 4 + kMaxParams + 60;  // result record of one evaluation
+constexpr int kPinnedResult = 256;                   // offset of the result in host_pinned
 
 // ---------------------------------------------------------------------------------------
 // context and datasets
@@ -60,9 +62,9 @@ struct Scratch {
   float2* partials = nullptr;
   size_t partials_cap = 0;          // in float2 elements
   unsigned* counters = nullptr;     // [0]: ticket, [1]: non-positive events, [2..]: spare
-  double* result = nullptr;         // kMaxSlots + 8 doubles
+  double* result = nullptr;         // kResultDoubles doubles
   double* theta = nullptr;          // kMaxParams doubles
-  double* host_pinned = nullptr;    // pinned staging: theta in, result out (2 x 128 doubles)
+  double* host_pinned = nullptr;    // pinned staging: [0, 256) theta in, [256, 512) result out
 };
 
 }  // namespace goo
@@ -78,6 +80,11 @@ struct KernelStat {
   std::string name;
   int64_t count = 0;
   double ms = 0.0;
+};
+struct CacheSlot {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  uint64_t key = 0;
 };
 }  // namespace goo
 
@@ -103,10 +110,9 @@ struct goo_dataset {
   bool owns64 = true, owns32 = true;
   double lo[goo::kMaxObs] = {0, 0, 0, 0};
   double hi[goo::kMaxObs] = {0, 0, 0, 0};
-  // amplitude-model cache attached to this dataset (built lazily by the Dalitz path)
-  void* amp_cache = nullptr;
-  size_t amp_cache_bytes = 0;
-  uint64_t amp_cache_key = 0;
+  // amplitude caches attached to this dataset, [0]: float32, [1]: float64 (built lazily by
+  // the amplitude-model path and rebuilt when the model or its lineshapes change)
+  goo::CacheSlot cache[2];
 };
 
 namespace goo {

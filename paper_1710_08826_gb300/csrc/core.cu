@@ -156,8 +156,12 @@ static void free_dataset_memory(goo_dataset* ds) {
     ds->d64[c] = nullptr;
     ds->d32[c] = nullptr;
   }
-  if (ds->amp_cache) cudaFree(ds->amp_cache);
-  ds->amp_cache = nullptr;
+  for (auto& c : ds->cache) {
+    if (c.ptr) cudaFree(c.ptr);
+    c.ptr = nullptr;
+    c.bytes = 0;
+    c.key = 0;
+  }
 }
 
 }  // namespace goo
@@ -212,9 +216,9 @@ int goo_init(int device, void* cuda_stream, goo_ctx** out) {
   Scratch& s = ctx->scratch;
   GOO_CUDA_TRY(cudaMalloc(&s.counters, 64 * sizeof(unsigned)));
   GOO_CUDA_TRY(cudaMemset(s.counters, 0, 64 * sizeof(unsigned)));
-  GOO_CUDA_TRY(cudaMalloc(&s.result, (kMaxSlots + 64) * sizeof(double)));
+  GOO_CUDA_TRY(cudaMalloc(&s.result, kResultDoubles * sizeof(double)));
   GOO_CUDA_TRY(cudaMalloc(&s.theta, 2 * kMaxParams * sizeof(double)));
-  GOO_CUDA_TRY(cudaMallocHost(&s.host_pinned, 256 * sizeof(double)));
+  GOO_CUDA_TRY(cudaMallocHost(&s.host_pinned, 512 * sizeof(double)));
   int rc = ensure_partials(ctx, 65536);
   if (rc != GOO_OK) {
     goo_finalize(ctx);

@@ -1,18 +1,895 @@
-// dalitz.cu -- three-body amplitude models (placeholder until the amplitude kernels land).
+// dalitz.cu -- three-body amplitude (Dalitz-plot) models: amplitude cache, MC Gram matrix
+// and the coherent-sum NLL with its adjoint gradient.
+//
+// Paper: GooFit carries dedicated amplitude PDFs for three-body decays (Sec. 1), whose
+// components are complex amplitudes with the density given by the squared magnitude of
+// their sum (Sec. 1, footnote); PDFs cache partial results in structure-of-arrays form
+// and recompute them only when their parameters change (Sec. 4); MC phase-space samples
+// provide the normalisation integral (Sec. 5).
+//
+// Model (isobar convention; the paper prints no formulas):
+//   S(x) = sum_k c_k A_k(x),  f = |S|^2 / N,  N = c^H G c,  G_kl = mean over the MC sample
+//   of A_k conj(A_l);  NLL = -sum_i log |S_i|^2 + n log N.
+//   A_R(s12, s13) = BW(s_AB) * B_L(r q)/B_L(r q0) * B_L(r_par p*) * Z_L for resonance R in
+//   pair (A, B) with bachelor C, where
+//     q^2  = lambda(s, mA^2, mB^2) / (4 s),   p*^2 = lambda(M^2, s, mC^2) / (4 M^2),
+//     B_0 = 1, B_1(z) = sqrt(1/(1+z)), B_2(z) = sqrt(9/(9+3z+z^2)),   z = r^2 q^2,
+//     Gamma(s) = G0 (q/q0)^(2L+1) (m0/sqrt s) (B_L(z)/B_L(z0))^2,
+//     BW(s) = 1 / (m0^2 - s - i m0 Gamma(s)),
+//     Z_0 = 1,  Z_1 = s_AC - s_BC - (mA^2 - mB^2)(M^2 - mC^2)/s,
+//     Z_2 = Z_1^2 - lambda(s, mA^2, mB^2) lambda(M^2, s, mC^2) / (3 s^2)
+//   (Z_1 = -4 q k cos(theta) and Z_2 = 16 q^2 k^2 (cos^2 - 1/3) in the resonance frame).
+//   lambda(s, a^2, b^2) is evaluated in its factorised form (s-(a+b)^2)(s-(a-b)^2).
+//
+// Gradient: d|S|^2/d Re c_k = 2 Re(A_k conj S), d|S|^2/d Im c_k = -2 Im(A_k conj S), and
+// for the normalisation dN/d Re c_k = 2 Re(v_k), dN/d Im c_k = -2 Im(v_k), v = G conj(c).
+// The event kernel accumulates sum_i A_k conj(S_i) / |S_i|^2 (2K lanes) and sum log|S|^2.
+//
+// FP32 path: amplitudes and S in FP32, Kahan per thread, double-float across threads; the
+// final FP64 combination takes c at the FP32-rounded values the kernel used, so the NLL is
+// the exact likelihood at those coefficients.
+#include <cmath>
+#include <cstring>
+#include <type_traits>
+#include <vector>
+
 #include "common.cuh"
 #include "model.cuh"
 
 namespace goo {
-int build_dalitz_model(goo_ctx*, const goo_node*, int, int, int, const double*, const double*, goo_model*) {
-  return set_error(GOO_ERR_UNSUPPORTED, "amplitude models are not built yet");
+
+constexpr int kMaxAmp = 16;
+
+struct BwConst {
+  int spin, pair;       // pair 0: (12)+3, 1: (13)+2, 2: (23)+1
+  double m0sq, m0w;     // m0^2, m0 * Gamma0
+  double inv_q0sq;      // 1 / q0^2
+  double r2, rp2;       // resonance and parent barrier radii squared
+  double thrP, thrM;    // (mA + mB)^2, (mA - mB)^2
+  double pthrP, pthrM;  // (M + mC)^2, (M - mC)^2
+  double zconst;        // (mA^2 - mB^2)(M^2 - mC^2)
+  double inv4M2;        // 1 / (4 M^2)
+  double Fz0;           // 1 + z0 (L=1) or 9 + 3 z0 + z0^2 (L=2)
+};
+
+struct DalitzDev {
+  int nbw;              // number of Breit-Wigner amplitudes (cached)
+  double sumsq;         // M^2 + m1^2 + m2^2 + m3^2  (s23 = sumsq - s12 - s13)
+  BwConst bw[kMaxAmp];
+};
+
+struct DalitzModel {
+  int K = 0;                       // amplitudes, BWs first then the NR (if any)
+  int nbw = 0;
+  bool has_nr = false;
+  int par_re[kMaxAmp], par_im[kMaxAmp];
+  int par_m0[kMaxAmp], par_w[kMaxAmp];
+  int spin[kMaxAmp], pair[kMaxAmp];
+  int col12 = 0, col13 = 1;
+  double M = 0, m1 = 0, m2 = 0, m3 = 0, r_res = 0, r_par = 0;
+  DalitzDev host{};
+  DalitzDev* dev = nullptr;
+  uint64_t ls_key = 0;             // lineshape version of `host`/`dev`
+  // Gram matrices (K x K complex, row-major, FP64) per precision, with their keys
+  double* gram_dev[2] = {nullptr, nullptr};
+  double gram_host[2][kMaxAmp * kMaxAmp * 2];
+  uint64_t gram_key[2] = {0, 0};
+  const goo_dataset* mc = nullptr;
+};
+
+// ---------------------------------------------------------------------------------------
+// amplitude of one Breit-Wigner resonance at (s12, s13, s23), in precision T
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void bw_amp(const BwConst& b, T s12, T s13, T s23, T& re, T& im) {
+  const int L = b.spin;
+  T s, sac, sbc;
+  if (b.pair == 0) {
+    s = s12;
+    sac = s13;
+    sbc = s23;
+  } else if (b.pair == 1) {
+    s = s13;
+    sac = s12;
+    sbc = s23;
+  } else {
+    s = s23;
+    sac = s12;
+    sbc = s13;
+  }
+  const T lam1 = (s - T(b.thrP)) * (s - T(b.thrM));
+  T q2 = lam1 / (T(4) * s);
+  q2 = q2 > T(0) ? q2 : T(0);
+  const T z = T(b.r2) * q2;
+  const T t = q2 * T(b.inv_q0sq);
+  const T st = sqrt(t);
+  T ratio2, pw;
+  if (L == 0) {
+    ratio2 = T(1);
+    pw = st;
+  } else if (L == 1) {
+    ratio2 = T(b.Fz0) / (T(1) + z);
+    pw = t * st;
+  } else {
+    ratio2 = T(b.Fz0) / (T(9) + T(3) * z + z * z);
+    pw = t * t * st;
+  }
+  const T rs = T(1) / sqrt(s);
+  const T m0 = sqrt(T(b.m0sq));
+  const T di = T(b.m0w) * pw * m0 * rs * ratio2;  // m0 Gamma(s)
+  const T dr = T(b.m0sq) - s;
+  const T inv = T(1) / (dr * dr + di * di);
+  const T lam2 = (s - T(b.pthrP)) * (s - T(b.pthrM));
+  T zp = T(b.rp2) * lam2 * T(b.inv4M2);
+  zp = zp > T(0) ? zp : T(0);
+  T parent, spinf;
+  if (L == 0) {
+    parent = T(1);
+    spinf = T(1);
+  } else if (L == 1) {
+    parent = T(1) / sqrt(T(1) + zp);
+    spinf = sac - sbc - T(b.zconst) / s;
+  } else {
+    parent = T(3) / sqrt(T(9) + T(3) * zp + zp * zp);
+    const T z1 = sac - sbc - T(b.zconst) / s;
+    spinf = z1 * z1 - lam1 * lam2 / (T(3) * s * s);
+  }
+  const T scale = sqrt(ratio2) * parent * spinf * inv;
+  re = dr * scale;
+  im = di * scale;
 }
-int dalitz_set_norm(goo_model*, const goo_norm_spec*) { return set_error(GOO_ERR_UNSUPPORTED, "amplitude models"); }
-void dalitz_free(goo_model*) {}
-int dalitz_normalise(goo_model*, const double*, int, double*) { return set_error(GOO_ERR_UNSUPPORTED, "amplitude models"); }
-int dalitz_nll(goo_model*, const goo_dataset*, int64_t, int64_t, const double*, int, bool, double*, int) {
-  return set_error(GOO_ERR_UNSUPPORTED, "amplitude models");
+
+// Cache layout.  FP32: ceil(nbw/2) planes of float4 (re_k, im_k, re_k+1, im_k+1) per event;
+// FP64: nbw planes of double2 (re, im) per event.  Plane p of an n-event dataset starts at
+// element p * n.
+__global__ void amp_cache_f32_kernel(const DalitzDev* __restrict__ dd, const float* __restrict__ s12c,
+                                     const float* __restrict__ s13c, int64_t n, float4* __restrict__ cache) {
+  __shared__ DalitzDev s_dd;
+  for (int i = threadIdx.x; i < (int)(sizeof(DalitzDev) / 4); i += blockDim.x)
+    ((int*)&s_dd)[i] = ((const int*)dd)[i];
+  __syncthreads();
+  const int nbw = s_dd.nbw;
+  const int planes = (nbw + 1) / 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float a = s12c[i], b = s13c[i];
+    const float c = (float)(s_dd.sumsq - (double)a - (double)b);
+    for (int p = 0; p < planes; ++p) {
+      float r0, i0, r1 = 0.f, i1 = 0.f;
+      bw_amp<float>(s_dd.bw[2 * p], a, b, c, r0, i0);
+      if (2 * p + 1 < nbw) bw_amp<float>(s_dd.bw[2 * p + 1], a, b, c, r1, i1);
+      cache[(int64_t)p * n + i] = make_float4(r0, i0, r1, i1);
+    }
+  }
 }
-int dalitz_eval_logf(goo_model*, const goo_dataset*, const double*, int, double*) {
-  return set_error(GOO_ERR_UNSUPPORTED, "amplitude models");
+
+__global__ void amp_cache_f64_kernel(const DalitzDev* __restrict__ dd, const double* __restrict__ s12c,
+                                     const double* __restrict__ s13c, int64_t n, double2* __restrict__ cache) {
+  __shared__ DalitzDev s_dd;
+  for (int i = threadIdx.x; i < (int)(sizeof(DalitzDev) / 4); i += blockDim.x)
+    ((int*)&s_dd)[i] = ((const int*)dd)[i];
+  __syncthreads();
+  const int nbw = s_dd.nbw;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = s12c[i], b = s13c[i];
+    const double c = s_dd.sumsq - a - b;
+    for (int k = 0; k < nbw; ++k) {
+      double re, im;
+      bw_amp<double>(s_dd.bw[k], a, b, c, re, im);
+      cache[(int64_t)k * n + i] = make_double2(re, im);
+    }
+  }
 }
+
+// Loads the nbw cached amplitudes of event i (compile-time bound KB, runtime nbw).
+template <int KB>
+__device__ __forceinline__ void load_amps(const float4* __restrict__ cache, int64_t n, int64_t i, int nbw,
+                                          float (&ar)[KB + 1], float (&ai)[KB + 1]) {
+#pragma unroll
+  for (int p = 0; p < (KB + 1) / 2; ++p) {
+    if (2 * p < nbw) {
+      const float4 v = __ldg(cache + (int64_t)p * n + i);
+      ar[2 * p] = v.x;
+      ai[2 * p] = v.y;
+      if (2 * p + 1 < KB) {
+        ar[2 * p + 1] = v.z;
+        ai[2 * p + 1] = v.w;
+      }
+    } else {
+      ar[2 * p] = ai[2 * p] = 0.f;
+      if (2 * p + 1 < KB) ar[2 * p + 1] = ai[2 * p + 1] = 0.f;
+    }
+  }
+}
+
+template <int KB>
+__device__ __forceinline__ void load_amps(const double2* __restrict__ cache, int64_t n, int64_t i, int nbw,
+                                          double (&ar)[KB + 1], double (&ai)[KB + 1]) {
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    if (k < nbw) {
+      const double2 v = cache[(int64_t)k * n + i];
+      ar[k] = v.x;
+      ai[k] = v.y;
+    } else {
+      ar[k] = ai[k] = 0.0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// coherent NLL (+ gradient lanes) over events [begin, end) of one dataset
+// ---------------------------------------------------------------------------------------
+template <typename T>
+struct CohArgs {
+  T cr[kMaxAmp], ci[kMaxAmp];  // coefficients (BWs first, then NR)
+  int nbw, K, has_nr;
+  int par_re[kMaxAmp], par_im[kMaxAmp];
+  int n_params;
+  int64_t n_total;             // events of the dataset (cache plane length)
+};
+
+template <typename T, int KB, bool GRAD>
+struct CohLanes {
+  static constexpr int NS = GRAD ? 1 + 2 * (KB + 1) : 1;
+};
+
+template <typename T, int KB, bool GRAD>
+__global__ void __launch_bounds__(kBlock, 2) coh_nll_kernel(const __grid_constant__ CohArgs<T> a, const void* cache_v,
+                                                            int64_t begin, int64_t end, const double* __restrict__ gram,
+                                                            float2* partials, unsigned* counters, double* result,
+                                                            int out_mode) {
+  constexpr int NS = CohLanes<T, KB, GRAD>::NS;
+  constexpr int KA = KB + 1;  // BW slots + NR slot
+  __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
+  __shared__ unsigned s_bad[kBlock / 32];
+  using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const Vec* cache = (const Vec*)cache_v;
+  const int nbw = a.nbw;
+  T cr[KA], ci[KA];
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    cr[k] = k < nbw ? a.cr[k] : T(0);
+    ci[k] = k < nbw ? a.ci[k] : T(0);
+  }
+  cr[KB] = a.has_nr ? a.cr[nbw] : T(0);
+  ci[KB] = a.has_nr ? a.ci[nbw] : T(0);
+  Kahan acc32;
+  double acc64 = 0.0;
+  T gre[KA], gim[KA];
+#pragma unroll
+  for (int k = 0; k < KA; ++k) gre[k] = gim[k] = T(0);
+  unsigned bad = 0;
+  const int64_t n = a.n_total;
+  for (int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T ar[KA], ai[KA];
+    load_amps<KB>(cache, n, i, nbw, ar, ai);
+    ar[KB] = T(1);
+    ai[KB] = T(0);
+    T sr = T(0), si = T(0);
+#pragma unroll
+    for (int k = 0; k < KA; ++k) {
+      sr += cr[k] * ar[k] - ci[k] * ai[k];
+      si += cr[k] * ai[k] + ci[k] * ar[k];
+    }
+    const T s2 = sr * sr + si * si;
+    if (s2 > T(0)) {
+      if constexpr (sizeof(T) == 4) {
+        acc32.add(__logf(s2));
+      } else {
+        acc64 += log(s2);
+      }
+      if constexpr (GRAD) {
+        const T inv = T(1) / s2;
+        const T tr = sr * inv, ti = -si * inv;  // conj(S) / |S|^2
+#pragma unroll
+        for (int k = 0; k < KA; ++k) {
+          gre[k] += ar[k] * tr - ai[k] * ti;
+          gim[k] += ar[k] * ti + ai[k] * tr;
+        }
+      }
+    } else {
+      bad++;
+    }
+  }
+  ddf v[NS];
+  v[0] = (sizeof(T) == 4) ? acc32.value() : dd_from_double(acc64);
+  if constexpr (GRAD) {
+#pragma unroll
+    for (int k = 0; k < KA; ++k) {
+      v[1 + 2 * k] = (sizeof(T) == 4) ? ddf{(float)gre[k], 0.f} : dd_from_double((double)gre[k]);
+      v[2 + 2 * k] = (sizeof(T) == 4) ? ddf{(float)gim[k], 0.f} : dd_from_double((double)gim[k]);
+    }
+  }
+  for (int m = 16; m > 0; m >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, m);
+  if ((threadIdx.x & 31) == 0) s_bad[threadIdx.x >> 5] = bad;
+  block_reduce_to_partials<NS>(v, NS, partials, s_red);
+  if (threadIdx.x == 0) {
+    unsigned b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_bad[w];
+    if (b) atomicAdd(counters + 1, b);
+  }
+  __shared__ double s_out[NS];
+  if (!last_block_reduce(partials, NS, gridDim.x, counters, s_out, s_red)) return;
+  if (threadIdx.x == 0) {
+    const unsigned nbad = atomicAdd(counters + 1, 0u);
+    counters[1] = 0u;
+    // FP64 combination at the coefficients the kernel used
+    const int K = a.K;
+    double c_re[kMaxAmp], c_im[kMaxAmp];
+    for (int k = 0; k < K; ++k) {
+      c_re[k] = (double)a.cr[k];
+      c_im[k] = (double)a.ci[k];
+    }
+    double N = 0.0;
+    double vr[kMaxAmp], vi[kMaxAmp];
+    for (int k = 0; k < K; ++k) {
+      double sr = 0.0, si = 0.0;  // v_k = sum_l G_kl conj(c_l)
+      for (int l = 0; l < K; ++l) {
+        const double gr = gram[2 * (k * K + l)], gi = gram[2 * (k * K + l) + 1];
+        sr += gr * c_re[l] + gi * c_im[l];
+        si += gi * c_re[l] - gr * c_im[l];
+      }
+      vr[k] = sr;
+      vi[k] = si;
+      N += c_re[k] * sr - c_im[k] * si;  // Re(c_k v_k)
+    }
+    const double nev = (double)(end - begin);
+    const double nll = -s_out[0] + nev * log(N);
+    double g[kMaxParams];
+    for (int p = 0; p < kMaxParams; ++p) g[p] = 0.0;
+    if (GRAD) {
+      for (int k = 0; k < K; ++k) {
+        const int slot = (k < a.nbw) ? k : KB;  // NR lives in the last slot
+        const double lre = s_out[1 + 2 * slot], lim = s_out[2 + 2 * slot];
+        g[a.par_re[k]] += -2.0 * lre + nev * 2.0 * vr[k] / N;
+        g[a.par_im[k]] += 2.0 * lim - nev * 2.0 * vi[k] / N;
+      }
+    }
+    const int P = a.n_params;
+    if (out_mode == 0) {
+      result[0] = nll;
+      result[1] = (double)nbad;
+      for (int p = 0; p < P; ++p) result[2 + p] = g[p];
+      result[2 + P] = N;
+    } else {
+      result[0] = nll;
+      result[1] = 0.0;
+      result[2] = (double)nbad;
+      for (int p = 0; p < P; ++p) result[3 + p] = g[p];
+    }
+  }
+}
+
+// per-event log f = log|S|^2 - log N
+template <typename T, int KB>
+__global__ void coh_logf_kernel(const __grid_constant__ CohArgs<T> a, const void* cache_v, double logN,
+                                double* __restrict__ out) {
+  constexpr int KA = KB + 1;
+  using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const Vec* cache = (const Vec*)cache_v;
+  const int nbw = a.nbw;
+  const int64_t n = a.n_total;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T ar[KA], ai[KA];
+    load_amps<KB>(cache, n, i, nbw, ar, ai);
+    ar[KB] = T(1);
+    ai[KB] = T(0);
+    T sr = T(0), si = T(0);
+#pragma unroll
+    for (int k = 0; k < KA; ++k) {
+      const T c_r = k < nbw ? a.cr[k] : (k == KB && a.has_nr ? a.cr[nbw] : T(0));
+      const T c_i = k < nbw ? a.ci[k] : (k == KB && a.has_nr ? a.ci[nbw] : T(0));
+      sr += c_r * ar[k] - c_i * ai[k];
+      si += c_r * ai[k] + c_i * ar[k];
+    }
+    const T s2 = sr * sr + si * si;
+    out[i] = s2 > T(0) ? log((double)s2) - logN : -HUGE_VAL;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Gram matrix over an MC cache: block (x, k) accumulates row k, G_kl for all l, over its
+// share of the MC events.  Lanes: 2 per l (re, im).  K <= kMaxAmp incl. the NR amplitude.
+// ---------------------------------------------------------------------------------------
+template <typename T, int KB>
+__global__ void __launch_bounds__(kBlock, 2) gram_kernel(const void* cache_v, int64_t n, int nbw, int has_nr,
+                                                         float2* partials, unsigned* counters, double* gram_out) {
+  constexpr int KA = KB + 1;
+  constexpr int NS = 2 * KA;
+  __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
+  using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const Vec* cache = (const Vec*)cache_v;
+  const int k = blockIdx.y;  // row, in slot numbering (BW slots, NR = KB)
+  const int krow = k < nbw ? k : KB;
+  Kahan kr[KA], ki[KA];
+  double dr[KA], di[KA];
+#pragma unroll
+  for (int l = 0; l < KA; ++l) dr[l] = di[l] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T ar[KA], ai[KA];
+    load_amps<KB>(cache, n, i, nbw, ar, ai);
+    ar[KB] = has_nr ? T(1) : T(0);
+    ai[KB] = T(0);
+    T xr = T(0), xi = T(0);
+#pragma unroll
+    for (int l = 0; l < KA; ++l)
+      if (l == krow) {
+        xr = ar[l];
+        xi = ai[l];
+      }
+#pragma unroll
+    for (int l = 0; l < KA; ++l) {
+      // A_k conj(A_l)
+      const T pr = xr * ar[l] + xi * ai[l];
+      const T pi = xi * ar[l] - xr * ai[l];
+      if constexpr (sizeof(T) == 4) {
+        kr[l].add(pr);
+        ki[l].add(pi);
+      } else {
+        dr[l] += pr;
+        di[l] += pi;
+      }
+    }
+  }
+  ddf v[NS];
+#pragma unroll
+  for (int l = 0; l < KA; ++l) {
+    v[2 * l] = (sizeof(T) == 4) ? kr[l].value() : dd_from_double(dr[l]);
+    v[2 * l + 1] = (sizeof(T) == 4) ? ki[l].value() : dd_from_double(di[l]);
+  }
+  const int nbx = gridDim.x;
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      ddf w = dd_warp_sum(v[s]);
+      if (lane == 0) s_red[warp * NS + s] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x < NS) {
+      ddf acc = s_red[threadIdx.x];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) acc = dd_add(acc, s_red[w * NS + threadIdx.x]);
+      partials[((size_t)k * nbx + blockIdx.x) * NS + threadIdx.x] = make_float2(acc.hi, acc.lo);
+    }
+  }
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(counters, 1u) == (unsigned)(nbx * gridDim.y - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  // G in model order: BW amplitudes 0..nbw-1, then NR at index nbw
+  const int K = nbw + (has_nr ? 1 : 0);
+  for (int lane_id = threadIdx.x; lane_id < (int)gridDim.y * NS; lane_id += blockDim.x) {
+    const int kk = lane_id / NS, s = lane_id % NS;
+    const int l = s / 2;
+    ddf acc = {0.f, 0.f};
+    for (int b = 0; b < nbx; ++b) {
+      const float2 p = __ldcg(partials + ((size_t)kk * nbx + b) * NS + s);
+      acc = dd_add(acc, {p.x, p.y});
+    }
+    const int krow_model = kk;                              // rows were launched in model order
+    const int lcol_model = l < nbw ? l : (l == KB ? nbw : -1);
+    // upper triangle from row k, mirrored with conjugation: G is Hermitian by construction
+    if (lcol_model >= krow_model && lcol_model < K && krow_model < K) {
+      double v = dd_to_double(acc) / (double)n;
+      if ((s & 1) && lcol_model == krow_model) v = 0.0;
+      gram_out[2 * (krow_model * K + lcol_model) + (s & 1)] = v;
+      gram_out[2 * (lcol_model * K + krow_model) + (s & 1)] = (s & 1) ? -v : v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *counters = 0u;
+}
+
+// ---------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------
+static double kallen(double a, double b, double c) { return a * a + b * b + c * c - 2 * a * b - 2 * a * c - 2 * b * c; }
+
+static void pair_masses(const DalitzModel& d, int pair, double& mA, double& mB, double& mC) {
+  if (pair == 0) {
+    mA = d.m1;
+    mB = d.m2;
+    mC = d.m3;
+  } else if (pair == 1) {
+    mA = d.m1;
+    mB = d.m3;
+    mC = d.m2;
+  } else {
+    mA = d.m2;
+    mB = d.m3;
+    mC = d.m1;
+  }
+}
+
+static uint64_t lineshape_key(const DalitzModel& d, const double* theta) {
+  uint64_t h = 1469598103934665603ull;
+  for (int k = 0; k < d.nbw; ++k) {
+    double v[2] = {theta[d.par_m0[k]], theta[d.par_w[k]]};
+    const unsigned char* p = (const unsigned char*)v;
+    for (size_t j = 0; j < sizeof v; ++j) h = (h ^ p[j]) * 1099511628211ull;
+  }
+  return h ? h : 1;
+}
+
+// Lineshape constants for the current theta (FP64, once per lineshape version).
+static int dalitz_constants(goo_model* m, const double* theta) {
+  DalitzModel& d = *m->dalitz;
+  const uint64_t key = lineshape_key(d, theta);
+  if (key == d.ls_key) return GOO_OK;
+  DalitzDev& h = d.host;
+  h.nbw = d.nbw;
+  const double M = d.M;
+  h.sumsq = M * M + d.m1 * d.m1 + d.m2 * d.m2 + d.m3 * d.m3;
+  for (int k = 0; k < d.nbw; ++k) {
+    BwConst& b = h.bw[k];
+    const int L = d.spin[k];
+    double mA, mB, mC;
+    pair_masses(d, d.pair[k], mA, mB, mC);
+    const double m0 = theta[d.par_m0[k]], g0 = theta[d.par_w[k]];
+    if (!(m0 > mA + mB) || !(g0 > 0))
+      return set_error(GOO_ERR_ARG, "amplitude %d: mass %g must exceed its threshold %g and width %g be > 0", k, m0,
+                       mA + mB, g0);
+    b.spin = L;
+    b.pair = d.pair[k];
+    b.m0sq = m0 * m0;
+    b.m0w = m0 * g0;
+    const double q0sq = kallen(m0 * m0, mA * mA, mB * mB) / (4 * m0 * m0);
+    b.inv_q0sq = 1.0 / q0sq;
+    b.r2 = d.r_res * d.r_res;
+    b.rp2 = d.r_par * d.r_par;
+    b.thrP = (mA + mB) * (mA + mB);
+    b.thrM = (mA - mB) * (mA - mB);
+    b.pthrP = (M + mC) * (M + mC);
+    b.pthrM = (M - mC) * (M - mC);
+    b.zconst = (mA * mA - mB * mB) * (M * M - mC * mC);
+    b.inv4M2 = 1.0 / (4 * M * M);
+    const double z0 = b.r2 * q0sq;
+    b.Fz0 = (L == 1) ? 1.0 + z0 : (L == 2 ? 9.0 + 3.0 * z0 + z0 * z0 : 1.0);
+  }
+  goo_ctx* ctx = m->ctx;
+  GOO_CUDA_TRY(cudaMemcpyAsync(d.dev, &h, sizeof(DalitzDev), cudaMemcpyHostToDevice, ctx->stream));
+  GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  d.ls_key = key;
+  d.gram_key[0] = d.gram_key[1] = 0;
+  return GOO_OK;
+}
+
+// Builds (if stale) the amplitude cache of `ds` in `precision`; returns its device pointer.
+static int ensure_cache(goo_model* m, const goo_dataset* ds_c, int precision, const void** out) {
+  goo_dataset* ds = const_cast<goo_dataset*>(ds_c);
+  DalitzModel& d = *m->dalitz;
+  goo_ctx* ctx = m->ctx;
+  const int pi = precision == GOO_F32 ? 0 : 1;
+  const uint64_t key = d.ls_key ^ (uint64_t)(uintptr_t)m ^ (uint64_t)(pi + 1) * 0x9e3779b97f4a7c15ull;
+  CacheSlot& slot = ds->cache[pi];
+  const int64_t n = ds->n;
+  const size_t bytes = pi == 0 ? (size_t)((d.nbw + 1) / 2) * (size_t)n * sizeof(float4)
+                               : (size_t)d.nbw * (size_t)n * sizeof(double2);
+  if (slot.ptr && slot.key == key && slot.bytes >= bytes) {
+    *out = slot.ptr;
+    return GOO_OK;
+  }
+  if (!slot.ptr || slot.bytes < bytes) {
+    if (slot.ptr) cudaFree(slot.ptr);
+    slot.ptr = nullptr;
+    slot.bytes = 0;
+    if (cudaMalloc(&slot.ptr, bytes > 0 ? bytes : 16) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(GOO_ERR_OOM, "amplitude cache of %zu bytes does not fit", bytes);
+    }
+    slot.bytes = bytes;
+  }
+  if (n > 0 && d.nbw > 0) {
+    const int nb = grid_blocks(ctx, n, 4);
+    if (pi == 0) {
+      LaunchScope ls(ctx, "amp_cache_f32");
+      amp_cache_f32_kernel<<<nb, kBlock, 0, ctx->stream>>>(d.dev, ds->d32[d.col12], ds->d32[d.col13], n,
+                                                          (float4*)slot.ptr);
+    } else {
+      LaunchScope ls(ctx, "amp_cache_f64");
+      amp_cache_f64_kernel<<<nb, kBlock, 0, ctx->stream>>>(d.dev, ds->d64[d.col12], ds->d64[d.col13], n,
+                                                          (double2*)slot.ptr);
+    }
+    GOO_CUDA_TRY(cudaGetLastError());
+  }
+  slot.key = key;
+  *out = slot.ptr;
+  return GOO_OK;
+}
+
+template <typename T, int KB>
+static int launch_gram(goo_model* m, const void* cache, int64_t n, int pi) {
+  DalitzModel& d = *m->dalitz;
+  goo_ctx* ctx = m->ctx;
+  constexpr int NS = 2 * (KB + 1);
+  int bps = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, gram_kernel<T, KB>, kBlock, 0) != cudaSuccess || bps < 1) {
+    cudaGetLastError();
+    bps = 1;
+  }
+  const int K = d.K;
+  int64_t nbx = (n + kBlock - 1) / kBlock;
+  const int64_t cap = ((int64_t)ctx->num_sms * bps + K - 1) / K;
+  if (nbx > cap) nbx = cap;
+  if (nbx < 1) nbx = 1;
+  GOO_TRY(ensure_partials(ctx, (size_t)nbx * K * NS));
+  {
+    LaunchScope ls(ctx, sizeof(T) == 4 ? "gram_f32" : "gram_f64");
+    gram_kernel<T, KB><<<dim3((unsigned)nbx, K), kBlock, 0, ctx->stream>>>(
+        cache, n, d.nbw, d.has_nr ? 1 : 0, ctx->scratch.partials, ctx->scratch.counters, d.gram_dev[pi]);
+  }
+  GOO_CUDA_TRY(cudaGetLastError());
+  return GOO_OK;
+}
+
+static int ensure_gram(goo_model* m, int precision) {
+  DalitzModel& d = *m->dalitz;
+  const int pi = precision == GOO_F32 ? 0 : 1;
+  if (!d.mc) return set_error(GOO_ERR_STATE, "amplitude model has no MC normalisation sample (goo_model_set_norm)");
+  const uint64_t key = d.ls_key ^ (uint64_t)(uintptr_t)d.mc ^ (uint64_t)(pi + 7);
+  if (d.gram_key[pi] == key) return GOO_OK;
+  const void* cache = nullptr;
+  GOO_TRY(ensure_cache(m, d.mc, precision, &cache));
+  if (d.mc->n < 1) return set_error(GOO_ERR_ARG, "the MC normalisation sample is empty");
+  if (pi == 0) {
+    GOO_TRY((d.nbw <= 8 ? launch_gram<float, 8>(m, cache, d.mc->n, pi) : launch_gram<float, 15>(m, cache, d.mc->n, pi)));
+  } else {
+    GOO_TRY((d.nbw <= 8 ? launch_gram<double, 8>(m, cache, d.mc->n, pi) : launch_gram<double, 15>(m, cache, d.mc->n, pi)));
+  }
+  GOO_CUDA_TRY(cudaMemcpyAsync(d.gram_host[pi], d.gram_dev[pi], sizeof(double) * 2 * d.K * d.K, cudaMemcpyDeviceToHost,
+                               m->ctx->stream));
+  GOO_CUDA_TRY(cudaStreamSynchronize(m->ctx->stream));
+  d.gram_key[pi] = key;
+  return GOO_OK;
+}
+
+template <typename T>
+static void fill_args(const DalitzModel& d, const double* theta, int n_params, int64_t n_total, CohArgs<T>& a) {
+  std::memset(&a, 0, sizeof a);
+  a.nbw = d.nbw;
+  a.K = d.K;
+  a.has_nr = d.has_nr ? 1 : 0;
+  a.n_params = n_params;
+  a.n_total = n_total;
+  for (int k = 0; k < d.K; ++k) {
+    a.cr[k] = (T)theta[d.par_re[k]];
+    a.ci[k] = (T)theta[d.par_im[k]];
+    a.par_re[k] = d.par_re[k];
+    a.par_im[k] = d.par_im[k];
+  }
+}
+
+template <typename T, int KB, bool GRAD>
+static int launch_coh(goo_model* m, const void* cache, const goo_dataset* ds, int64_t begin, int64_t end,
+                      const double* theta, int out_mode, int pi) {
+  DalitzModel& d = *m->dalitz;
+  goo_ctx* ctx = m->ctx;
+  static int occ = 0;
+  if (occ == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, coh_nll_kernel<T, KB, GRAD>, kBlock, 0) != cudaSuccess ||
+        occ < 1) {
+      cudaGetLastError();
+      occ = 1;
+    }
+  }
+  const int nb = grid_blocks(ctx, end - begin, occ);
+  constexpr int NS = CohLanes<T, KB, GRAD>::NS;
+  GOO_TRY(ensure_partials(ctx, (size_t)nb * NS));
+  CohArgs<T> a;
+  fill_args<T>(d, theta, m->n_params, ds->n, a);
+  {
+    LaunchScope ls(ctx, sizeof(T) == 4 ? (GRAD ? "coh_nll_grad_f32" : "coh_nll_f32")
+                                       : (GRAD ? "coh_nll_grad_f64" : "coh_nll_f64"));
+    coh_nll_kernel<T, KB, GRAD><<<nb, kBlock, 0, ctx->stream>>>(a, cache, begin, end, d.gram_dev[pi],
+                                                                ctx->scratch.partials, ctx->scratch.counters,
+                                                                ctx->scratch.result, out_mode);
+  }
+  GOO_CUDA_TRY(cudaGetLastError());
+  return GOO_OK;
+}
+
+template <typename T, bool GRAD>
+static int launch_coh_sel(goo_model* m, const void* cache, const goo_dataset* ds, int64_t begin, int64_t end,
+                          const double* theta, int out_mode, int pi) {
+  if (m->dalitz->nbw <= 8) return launch_coh<T, 8, GRAD>(m, cache, ds, begin, end, theta, out_mode, pi);
+  return launch_coh<T, 15, GRAD>(m, cache, ds, begin, end, theta, out_mode, pi);
+}
+
+int build_dalitz_model(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_params, int n_obs, const double* lo,
+                       const double* hi, goo_model* m) {
+  const goo_node& root = nodes[n_nodes - 1];
+  if (root.n_child < 1 || root.n_child > kMaxAmp)
+    return set_error(GOO_ERR_UNSUPPORTED, "coherent sum of %d amplitudes (1..%d)", root.n_child, kMaxAmp);
+  if (n_obs < 2 || root.obs[0] < 0 || root.obs[1] < 0 || root.obs[0] >= n_obs || root.obs[1] >= n_obs)
+    return set_error(GOO_ERR_ARG, "coherent node needs observables s12 and s13");
+  DalitzModel* d = new DalitzModel();
+  m->dalitz = d;
+  m->kind = 1;
+  d->col12 = root.obs[0];
+  d->col13 = root.obs[1];
+  d->M = root.dval[0];
+  d->m1 = root.dval[1];
+  d->m2 = root.dval[2];
+  d->m3 = root.dval[3];
+  d->r_res = root.dval[4];
+  d->r_par = root.dval[5];
+  if (!(d->M > d->m1 + d->m2 + d->m3) || d->m1 < 0 || d->m2 < 0 || d->m3 < 0)
+    return set_error(GOO_ERR_ARG, "parent mass %g below the sum of the daughter masses", d->M);
+  auto check_par = [&](int p) { return p >= 0 && p < n_params; };
+  // BWs first (in tree order), then the NR amplitude
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int c = 0; c < root.n_child; ++c) {
+      const goo_node& a = nodes[root.child[c]];
+      if (a.op != GOO_OP_BW && a.op != GOO_OP_NR)
+        return set_error(GOO_ERR_ARG, "coherent child %d has op %d (BW or NR expected)", c, a.op);
+      if ((pass == 0) != (a.op == GOO_OP_BW)) continue;
+      const int k = d->K++;
+      if (!check_par(a.par[2]) || !check_par(a.par[3]))
+        return set_error(GOO_ERR_ARG, "amplitude %d has no coefficient parameters", c);
+      d->par_re[k] = a.par[2];
+      d->par_im[k] = a.par[3];
+      if (a.op == GOO_OP_BW) {
+        if (!check_par(a.par[0]) || !check_par(a.par[1]))
+          return set_error(GOO_ERR_ARG, "BW amplitude %d has no mass/width parameters", c);
+        if (a.ival[0] < 0 || a.ival[0] > 2) return set_error(GOO_ERR_UNSUPPORTED, "BW spin %d (0..2)", a.ival[0]);
+        if (a.ival[1] < 0 || a.ival[1] > 2) return set_error(GOO_ERR_ARG, "BW pair %d (0..2)", a.ival[1]);
+        d->par_m0[k] = a.par[0];
+        d->par_w[k] = a.par[1];
+        d->spin[k] = a.ival[0];
+        d->pair[k] = a.ival[1];
+        d->nbw++;
+      } else {
+        if (d->has_nr) return set_error(GOO_ERR_UNSUPPORTED, "at most one non-resonant amplitude");
+        d->has_nr = true;
+      }
+    }
+  }
+  if (d->nbw > 15) return set_error(GOO_ERR_UNSUPPORTED, "at most 15 resonances");
+  (void)lo;
+  (void)hi;
+  if (cudaMalloc(&d->dev, sizeof(DalitzDev)) != cudaSuccess ||
+      cudaMalloc(&d->gram_dev[0], sizeof(double) * 2 * kMaxAmp * kMaxAmp) != cudaSuccess ||
+      cudaMalloc(&d->gram_dev[1], sizeof(double) * 2 * kMaxAmp * kMaxAmp) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(GOO_ERR_OOM, "cannot allocate the amplitude model");
+  }
+  m->norm.kind = GOO_NORM_MC;
+  (void)ctx;
+  return GOO_OK;
+}
+
+int dalitz_set_norm(goo_model* m, const goo_norm_spec* spec) {
+  if (spec->kind != GOO_NORM_MC || !spec->mc)
+    return set_error(GOO_ERR_UNSUPPORTED, "amplitude models are normalised with an MC sample (GOO_NORM_MC)");
+  const goo_dataset* mc = spec->mc;
+  DalitzModel& d = *m->dalitz;
+  if (mc->ctx != m->ctx) return set_error(GOO_ERR_ARG, "MC sample belongs to another context");
+  if (mc->ncols <= d.col12 || mc->ncols <= d.col13) return set_error(GOO_ERR_ARG, "MC sample lacks s12/s13 columns");
+  d.mc = mc;
+  d.gram_key[0] = d.gram_key[1] = 0;
+  m->norm = *spec;
+  return GOO_OK;
+}
+
+void dalitz_free(goo_model* m) {
+  DalitzModel* d = m->dalitz;
+  if (!d) return;
+  if (d->dev) cudaFree(d->dev);
+  for (int i = 0; i < 2; ++i)
+    if (d->gram_dev[i]) cudaFree(d->gram_dev[i]);
+  delete d;
+  m->dalitz = nullptr;
+}
+
+static double quad_form(const DalitzModel& d, const double* G, const double* theta, bool f32) {
+  double N = 0.0;
+  for (int k = 0; k < d.K; ++k)
+    for (int l = 0; l < d.K; ++l) {
+      double ckr = theta[d.par_re[k]], cki = theta[d.par_im[k]];
+      double clr = theta[d.par_re[l]], cli = theta[d.par_im[l]];
+      if (f32) {
+        ckr = (double)(float)ckr;
+        cki = (double)(float)cki;
+        clr = (double)(float)clr;
+        cli = (double)(float)cli;
+      }
+      const double gr = G[2 * (k * d.K + l)], gi = G[2 * (k * d.K + l) + 1];
+      // Re(c_k conj(c_l) G_kl)
+      const double pr = ckr * clr + cki * cli, pim = cki * clr - ckr * cli;
+      N += pr * gr - pim * gi;
+    }
+  return N;
+}
+
+int dalitz_normalise(goo_model* m, const double* theta, int precision, double* norm_out) {
+  GOO_TRY(dalitz_constants(m, theta));
+  GOO_TRY(ensure_gram(m, precision));
+  const int pi = precision == GOO_F32 ? 0 : 1;
+  norm_out[0] = quad_form(*m->dalitz, m->dalitz->gram_host[pi], theta, precision == GOO_F32);
+  return GOO_OK;
+}
+
+int dalitz_nll(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, const double* theta, int precision,
+               bool grad, double* out, int out_mode) {
+  DalitzModel& d = *m->dalitz;
+  goo_ctx* ctx = m->ctx;
+  const int P = m->n_params;
+  if (ds->ncols <= d.col12 || ds->ncols <= d.col13) return set_error(GOO_ERR_ARG, "dataset lacks s12/s13 columns");
+  GOO_TRY(dalitz_constants(m, theta));
+  GOO_TRY(ensure_gram(m, precision));
+  const int pi = precision == GOO_F32 ? 0 : 1;
+  const int nout = (out_mode == 0 ? 2 : 3) + P;
+  if (end <= begin) {
+    for (int i = 0; i < nout; ++i) out[i] = 0.0;
+    return GOO_OK;
+  }
+  const void* cache = nullptr;
+  GOO_TRY(ensure_cache(m, ds, precision, &cache));
+  if (precision == GOO_F32) {
+    GOO_TRY((grad ? launch_coh_sel<float, true>(m, cache, ds, begin, end, theta, out_mode, pi)
+                  : launch_coh_sel<float, false>(m, cache, ds, begin, end, theta, out_mode, pi)));
+  } else {
+    GOO_TRY((grad ? launch_coh_sel<double, true>(m, cache, ds, begin, end, theta, out_mode, pi)
+                  : launch_coh_sel<double, false>(m, cache, ds, begin, end, theta, out_mode, pi)));
+  }
+  double* stage = ctx->scratch.host_pinned + kPinnedResult;
+  GOO_CUDA_TRY(cudaMemcpyAsync(stage, ctx->scratch.result, nout * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  std::memcpy(out, stage, nout * sizeof(double));
+  return GOO_OK;
+}
+
+int dalitz_eval_logf(goo_model* m, const goo_dataset* ds, const double* theta, int precision, double* logf_dev) {
+  DalitzModel& d = *m->dalitz;
+  goo_ctx* ctx = m->ctx;
+  if (ds->ncols <= d.col12 || ds->ncols <= d.col13) return set_error(GOO_ERR_ARG, "dataset lacks s12/s13 columns");
+  GOO_TRY(dalitz_constants(m, theta));
+  GOO_TRY(ensure_gram(m, precision));
+  if (ds->n == 0) return GOO_OK;
+  const int pi = precision == GOO_F32 ? 0 : 1;
+  const double logN = std::log(quad_form(d, d.gram_host[pi], theta, precision == GOO_F32));
+  const void* cache = nullptr;
+  GOO_TRY(ensure_cache(m, ds, precision, &cache));
+  const int nb = grid_blocks(ctx, ds->n, 4);
+  LaunchScope ls(ctx, "coh_logf");
+  if (precision == GOO_F32) {
+    CohArgs<float> a;
+    fill_args<float>(d, theta, m->n_params, ds->n, a);
+    if (d.nbw <= 8) coh_logf_kernel<float, 8><<<nb, kBlock, 0, ctx->stream>>>(a, cache, logN, logf_dev);
+    else coh_logf_kernel<float, 15><<<nb, kBlock, 0, ctx->stream>>>(a, cache, logN, logf_dev);
+  } else {
+    CohArgs<double> a;
+    fill_args<double>(d, theta, m->n_params, ds->n, a);
+    if (d.nbw <= 8) coh_logf_kernel<double, 8><<<nb, kBlock, 0, ctx->stream>>>(a, cache, logN, logf_dev);
+    else coh_logf_kernel<double, 15><<<nb, kBlock, 0, ctx->stream>>>(a, cache, logN, logf_dev);
+  }
+  GOO_CUDA_TRY(cudaGetLastError());
+  return GOO_OK;
+}
+
+// Host copies of the Gram matrix (K x K complex, model amplitude order: resonances in tree
+// order, then the non-resonant amplitude) and of the per-event amplitude cache (test access).
+int dalitz_gram(goo_model* m, const double* theta, int precision, double* out, int* K_out) {
+  GOO_TRY(dalitz_constants(m, theta));
+  GOO_TRY(ensure_gram(m, precision));
+  const int pi = precision == GOO_F32 ? 0 : 1;
+  const int K = m->dalitz->K;
+  std::memcpy(out, m->dalitz->gram_host[pi], sizeof(double) * 2 * K * K);
+  *K_out = K;
+  return GOO_OK;
+}
+
+int dalitz_amplitudes(goo_model* m, const goo_dataset* ds, const double* theta, int precision, const void** cache,
+                      int* nbw) {
+  GOO_TRY(dalitz_constants(m, theta));
+  GOO_TRY(ensure_cache(m, ds, precision, cache));
+  *nbw = m->dalitz->nbw;
+  GOO_CUDA_TRY(cudaStreamSynchronize(m->ctx->stream));
+  return GOO_OK;
+}
+
 }  // namespace goo

@@ -1193,7 +1193,8 @@ constexpr size_t kStOffModel = 0;
 constexpr size_t kStOffTheta = (sizeof(ModelDev) + 255) / 256 * 256;
 constexpr size_t kStOffCounters = kStOffTheta + 256;
 constexpr size_t kStOffResult = kStOffCounters + 256;
-constexpr size_t kStOffPartials = kStOffResult + 1024;
+constexpr size_t kStOffPartials = kStOffResult + kResultDoubles * sizeof(double);
+constexpr int kStaticMaxParams = 32;  // documented limit of goo_nll_grad_static
 constexpr size_t kStPartialsCap = (kStaticScratchBytes - kStOffPartials) / sizeof(float2);
 static_assert(kStOffPartials < kStaticScratchBytes, "static scratch too small for the model block");
 
@@ -1381,8 +1382,8 @@ extern "C" int goo_nll_grad_static(const goo_node* nodes, int n_nodes, int n_par
   if (!nodes || !obs_lo || !obs_hi || !norm || !theta || !nll_out || !grad_out || (n_events > 0 && !cols_dev))
     return set_error(GOO_ERR_ARG, "goo_nll_grad_static: NULL argument");
   if (n_nodes < 1 || n_nodes > 256) return set_error(GOO_ERR_ARG, "goo_nll_grad_static: n_nodes=%d", n_nodes);
-  if (n_params < 0 || n_params > kMaxParams)
-    return set_error(GOO_ERR_ARG, "goo_nll_grad_static: n_params=%d exceeds the maximum %d", n_params, kMaxParams);
+  if (n_params < 0 || n_params > kStaticMaxParams)
+    return set_error(GOO_ERR_ARG, "goo_nll_grad_static: n_params=%d exceeds the maximum %d", n_params, kStaticMaxParams);
   if (n_obs < 1 || n_obs > kMaxObs) return set_error(GOO_ERR_ARG, "goo_nll_grad_static: n_obs=%d (1..%d)", n_obs, kMaxObs);
   if (n_events < 0) return set_error(GOO_ERR_ARG, "goo_nll_grad_static: n_events=%lld", (long long)n_events);
   if (precision != GOO_F64 && precision != GOO_F32) return set_error(GOO_ERR_ARG, "goo_nll_grad_static: precision");
@@ -1421,7 +1422,7 @@ extern "C" int goo_nll_grad_static(const goo_node* nodes, int n_nodes, int n_par
     GOO_TRY((small ? static_launch<double, 2, 3>(h, max_leaf, base, g_static_sms[dev], cols_dev, n_events, precision, st)
                    : static_launch<double, 4, 4>(h, max_leaf, base, g_static_sms[dev], cols_dev, n_events, precision, st)));
   }
-  double res[2 + kMaxParams];
+  double res[2 + kStaticMaxParams];
   GOO_CUDA_TRY(cudaMemcpyAsync(res, base + kStOffResult, (2 + n_params) * sizeof(double), cudaMemcpyDeviceToHost, st));
   GOO_CUDA_TRY(cudaStreamSynchronize(st));
   if (res[1] > 0) {

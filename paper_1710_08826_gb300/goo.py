@@ -69,6 +69,9 @@ def _load():
         "goo_eval_logf": (ctypes.c_int, [vp, vp, dp, ctypes.c_int, vp]),
         "goo_nll_partial": (ctypes.c_int, [vp, vp, i64, i64, dp, ctypes.c_int, ctypes.c_int, dp]),
         "goo_combine_partials": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, dp, dp]),
+        "goo_gram": (ctypes.c_int, [vp, dp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int)]),
+        "goo_amplitude_cache": (ctypes.c_int, [vp, vp, dp, ctypes.c_int, ctypes.POINTER(vp),
+                                               ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -356,6 +359,49 @@ class Model:
         _check(lib.goo_nll_partial(self.handle, ds.handle, int(begin), int(end), tp, precision_code(precision),
                                    int(bool(want_grad)), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out
+
+    def gram(self, theta, precision="f64"):
+        """MC Gram matrix G_kl (complex K x K, resonances in tree order then the NR amplitude)."""
+        t, tp = self._theta(theta)
+        out = np.zeros(2 * 16 * 16)
+        K = ctypes.c_int()
+        _check(lib.goo_gram(self.handle, tp, precision_code(precision),
+                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(K)))
+        k = K.value
+        g = out[:2 * k * k].reshape(k, k, 2)
+        return g[..., 0] + 1j * g[..., 1]
+
+    def amplitudes(self, ds, theta, precision="f64"):
+        """Cached resonance amplitudes of ds as a complex [n_events, n_res] numpy array."""
+        import torch
+        t, tp = self._theta(theta)
+        ptr = ctypes.c_void_p()
+        nres = ctypes.c_int()
+        _check(lib.goo_amplitude_cache(self.handle, ds.handle, tp, precision_code(precision), ctypes.byref(ptr),
+                                       ctypes.byref(nres)))
+        n, k = ds.n, nres.value
+        if precision_code(precision) == GOO_F32:
+            planes = (k + 1) // 2
+            buf = torch.empty(planes * n * 4, dtype=torch.float32, device=f"cuda:{self.ctx.device}")
+            nbytes = buf.numel() * 4
+        else:
+            buf = torch.empty(k * n * 2, dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+            nbytes = buf.numel() * 8
+        torch.cuda.synchronize()
+        cudart = ctypes.CDLL("libcudart.so.13")
+        rc = cudart.cudaMemcpy(ctypes.c_void_p(buf.data_ptr()), ptr, ctypes.c_size_t(nbytes), 3)
+        if rc != 0:
+            raise GooError(GOO_ERR_CUDA, f"cudaMemcpy failed ({rc})")
+        a = buf.cpu().numpy()
+        if precision_code(precision) == GOO_F32:
+            a = a.reshape(planes, n, 4)
+            out = np.empty((n, k), dtype=np.complex128)
+            for j in range(k):
+                plane, half = divmod(j, 2)
+                out[:, j] = a[plane, :, 2 * half] + 1j * a[plane, :, 2 * half + 1]
+            return out
+        a = a.reshape(k, n, 2)
+        return (a[..., 0] + 1j * a[..., 1]).T
 
     def close(self):
         if getattr(self, "handle", None):
