@@ -188,6 +188,31 @@ int goo_gram(goo_model* model, const double* theta, int precision, double* out, 
 int goo_amplitude_cache(goo_model* model, const goo_dataset* ds, const double* theta, int precision,
                         const void** dev_ptr, int* n_amp);
 
+/* ---- fitting (paper: the FitManager, Fig. 1; Minuit 2 as the default minimiser, Sec. 4) -------
+ * Minimises the NLL of `model` on `ds` over the parameters with free_mask[p] != 0, starting
+ * from theta (host, n_params doubles), which receives the minimum.  scale[p] > 0 is a typical
+ * step of each free parameter (the minimiser works in units of it).  Quasi-Newton BFGS with a
+ * backtracking line search, then (polish != 0) Newton steps on a finite-difference Hessian
+ * of the gradient; errors_out (NULL or n_params doubles) receives sqrt(diag(H^-1)) for free
+ * parameters and 0 for fixed ones.  The gradient is the adjoint kernel (GOO_GRAD_ADJOINT) or
+ * central differences of goo_nll (GOO_GRAD_FD, the plain path).  res->status: 0 converged
+ * (EDM = g^T H^-1 g / 2 < edm_tol), 1 iteration limit, 2 line-search failure.  Returns an
+ * error code only for invalid arguments or a non-finite NLL at the start. */
+enum { GOO_GRAD_ADJOINT = 0, GOO_GRAD_FD = 1 };
+typedef struct goo_fit_options {
+  int32_t precision;  /* GOO_F64 or GOO_F32                                                 */
+  int32_t gradient;   /* GOO_GRAD_ADJOINT or GOO_GRAD_FD                                    */
+  int32_t max_iter;   /* BFGS iterations (<= 0: 500)                                        */
+  int32_t polish;     /* Newton steps on the finite-difference Hessian after BFGS           */
+  double edm_tol;     /* convergence threshold on EDM (<= 0: 1e-6)                          */
+} goo_fit_options;
+typedef struct goo_fit_result {
+  double nll, edm, wall_ms;
+  int32_t iterations, nll_evals, grad_evals, status;
+} goo_fit_result;
+int goo_fit(goo_model* model, const goo_dataset* ds, double* theta, const int* free_mask, const double* scale,
+            const goo_fit_options* options, double* errors_out, goo_fit_result* res);
+
 /* ---- shards (paper Sec. 4: MPI divides the dataset among processes) --------------------------
  * Partial sums over events [begin, end) of ds: out[0] = sum of -log f, out[1] = its
  * compensation term, out[2] = number of events, out[3 .. 3+n_params) = gradient partials

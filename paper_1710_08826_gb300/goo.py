@@ -33,6 +33,17 @@ class GooNormSpec(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("bins", ctypes.c_int32 * 4), ("mc", ctypes.c_void_p)]
 
 
+class GooFitOptions(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("gradient", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("polish", ctypes.c_int32), ("edm_tol", ctypes.c_double)]
+
+
+class GooFitResult(ctypes.Structure):
+    _fields_ = [("nll", ctypes.c_double), ("edm", ctypes.c_double), ("wall_ms", ctypes.c_double),
+                ("iterations", ctypes.c_int32), ("nll_evals", ctypes.c_int32), ("grad_evals", ctypes.c_int32),
+                ("status", ctypes.c_int32)]
+
+
 class GooError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"goo error {code}: {msg}")
@@ -70,6 +81,8 @@ def _load():
         "goo_nll_partial": (ctypes.c_int, [vp, vp, i64, i64, dp, ctypes.c_int, ctypes.c_int, dp]),
         "goo_combine_partials": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, dp, dp]),
         "goo_gram": (ctypes.c_int, [vp, dp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int)]),
+        "goo_fit": (ctypes.c_int, [vp, vp, dp, ctypes.POINTER(ctypes.c_int), dp, ctypes.POINTER(GooFitOptions), dp,
+                                   ctypes.POINTER(GooFitResult)]),
         "goo_amplitude_cache": (ctypes.c_int, [vp, vp, dp, ctypes.c_int, ctypes.POINTER(vp),
                                                ctypes.POINTER(ctypes.c_int)]),
     }
@@ -359,6 +372,26 @@ class Model:
         _check(lib.goo_nll_partial(self.handle, ds.handle, int(begin), int(end), tp, precision_code(precision),
                                    int(bool(want_grad)), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out
+
+    def fit(self, ds, theta0, free=None, scale=None, precision="f32", gradient="adjoint", max_iter=500,
+            edm_tol=1e-6, polish=True, errors=True):
+        """Minimise the NLL (goo_fit).  Returns (theta_hat, errors, info dict)."""
+        th, thp = _dbuf(np.array(theta0, dtype=np.float64, copy=True), self.n_params)
+        if free is None:
+            free = [not p[2] for p in self.spec["params"]]
+        if scale is None:
+            scale = [p[3] if p[3] > 0 else 1.0 for p in self.spec["params"]]
+        fm = (ctypes.c_int * self.n_params)(*[int(bool(v)) for v in free])
+        sc, scp = _dbuf(scale, self.n_params)
+        opt = GooFitOptions(precision_code(precision), {"adjoint": 0, "fd": 1}[gradient], int(max_iter),
+                            int(bool(polish)), float(edm_tol))
+        err = np.zeros(self.n_params)
+        res = GooFitResult()
+        _check(lib.goo_fit(self.handle, ds.handle, thp, fm, scp, ctypes.byref(opt),
+                           err.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if errors else None,
+                           ctypes.byref(res)))
+        info = {k: getattr(res, k) for k, _ in GooFitResult._fields_}
+        return th.copy(), err, info
 
     def gram(self, theta, precision="f64"):
         """MC Gram matrix G_kl (complex K x K, resonances in tree order then the NR amplitude)."""

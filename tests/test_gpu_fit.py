@@ -1,0 +1,110 @@
+"""Fit-level parity: the library's FitManager (goo_fit) against the oracle's minimiser.
+
+Criterion: every fitted parameter within 0.01 sigma of the oracle's minimum, sigma being
+the oracle's error; errors agree to a few percent.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import dalitz as od
+from oracle import fit as ofit
+from oracle import model as om
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def goo():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1710_08826_gb300 import goo as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def ctx(goo):
+    return goo.Context(0)
+
+
+def _compare(th, err, rth, rerr, free, tol_sigma=0.01, tol_err=0.03):
+    idx = np.flatnonzero(free)
+    pulls = np.abs(th[idx] - rth[idx]) / rerr[idx]
+    assert np.all(pulls < tol_sigma), pulls
+    np.testing.assert_allclose(err[idx], rerr[idx], rtol=tol_err)
+    return pulls.max()
+
+
+@pytest.mark.parametrize("precision,gradient", [("f64", "fd"), ("f64", "adjoint"), ("f32", "adjoint")])
+def test_c1_fit_matches_oracle(goo, ctx, precision, gradient):
+    spec = synth.c1_spec()
+    cols = synth.gen_c1()
+    if precision == "f32":
+        cols = synth.round_to_f32(cols, spec)
+    truth = np.array(synth.param_values(spec))
+    start = truth * 1.05
+    steps = np.array([p[3] for p in spec["params"]])
+    free = np.ones(4, bool)
+    ref = om.TreeModel(spec)
+    rth, rerr, _, redm = ofit.fit(lambda t: ref.nll_grad(cols, t), start, free, steps)
+    assert 0 <= redm < 1e-8
+    ds = goo.Dataset.from_spec(ctx, spec, cols)
+    model = goo.Model(ctx, spec)
+    th, err, info = model.fit(ds, start, free, steps, precision=precision, gradient=gradient)
+    assert info["status"] == 0, info
+    _compare(th, err, rth, rerr, free)
+
+
+def test_c2_fit_matches_oracle(goo, ctx):
+    # The Argus endpoint m0 is held fixed here: the likelihood is not differentiable where m0
+    # crosses a data point, so its maximum-likelihood estimate is non-regular and Hessian
+    # errors do not describe it.  The NLL and gradient parity tests cover m0.
+    spec = synth.c2_spec(bins=48)
+    cols = synth.round_to_f32(synth.gen_c2(n=200_000, seed=41), spec)
+    truth = np.array(synth.param_values(spec))
+    start = truth.copy()
+    start[[0, 2]] += np.array([2e-4, 2e-3])   # shifted offsets
+    start[[1, 3, 4, 6, 7, 8, 9, 10, 11]] *= 1.03
+    steps = np.array([p[3] for p in spec["params"]])
+    free = np.ones(len(truth), bool)
+    free[5] = False
+    ref = om.TreeModel(spec)
+    rth, rerr, _, redm = ofit.fit(lambda t: ref.nll_grad(cols, t), start, free, steps)
+    assert 0 <= redm < 1e-8
+    ds = goo.Dataset.from_spec(ctx, spec, cols)
+    model = goo.Model(ctx, spec)
+    th, err, info = model.fit(ds, start, free, steps, precision="f32", gradient="adjoint")
+    assert info["status"] == 0, info
+    _compare(th, err, rth, rerr, free)
+
+
+def test_c3_fit_matches_oracle(goo, ctx):
+    spec = synth.c3_spec(n_mc=40_000)
+    kin = synth.DALITZ_MASSES
+    cand = lambda k, s: synth.dalitz_candidates(k, s, kin["M"], kin["m1"], kin["m2"], kin["m3"])  # noqa: E731
+    ref = od.DalitzModel(spec)
+    truth = np.array(synth.param_values(spec))
+    fmax = 1.2 * od.max_intensity_scan(ref, truth, n=300)
+
+    def dens(cols):
+        with torch.no_grad():
+            th = torch.as_tensor(truth, dtype=torch.float64)
+            return ref.intensity(ref.amplitude_matrix(cols, th), th).numpy()
+    data, _ = synth.accept_reject(cand, dens, fmax, 20_000, 91, chunk=200_000)
+    data = synth.round_to_f32(data, spec)
+    mc = synth.round_to_f32(cand(40_000, 1710013), spec)
+    names = synth.param_names(spec)
+    free = np.array([not p[2] for p in spec["params"]])
+    steps = np.array([p[3] if p[3] > 0 else 1.0 for p in spec["params"]])
+    start = truth.copy()
+    start[free] *= 1.1
+    rth, rerr, _, redm = ofit.fit(lambda t: ref.nll_grad(data, mc, t), start, free, steps)
+    assert 0 <= redm < 1e-8
+    ds = goo.Dataset.from_spec(ctx, spec, data)
+    mcds = goo.Dataset.from_spec(ctx, spec, mc)
+    model = goo.Model(ctx, spec, mc=mcds)
+    th, err, info = model.fit(ds, start, free, steps, precision="f32", gradient="adjoint")
+    assert info["status"] == 0, info
+    _compare(th, err, rth, rerr, free)
+    assert names  # parameter order is the spec's
