@@ -213,6 +213,49 @@ typedef struct goo_fit_result {
 int goo_fit(goo_model* model, const goo_dataset* ds, double* theta, const int* free_mask, const double* scale,
             const goo_fit_options* options, double* errors_out, goo_fit_result* res);
 
+/* ---- toy-MC fits served with continuous batching (paper Sec. 5: toy MC generation; Fig. 1) ----
+ * For an amplitude model with a non-resonant reference amplitude, <= 8 resonances, fixed
+ * lineshapes and an MC normalisation sample.  A request is one pseudo-experiment: n_events
+ * generated on the device from the model at theta_gen (Philox4x64-10 streams keyed by `seed`,
+ * accept-reject against the envelope fmax; the toy is the first n accepted candidates in
+ * candidate order), then fitted from theta_start (NULL: theta_gen) over the resonance
+ * coefficients (free_mask must mark exactly those).  Requests are admitted in submission
+ * order while a fit slot and 72 bytes per event of the device arena are free.  Each
+ * goo_server_step admits and generates new fits, runs ONE batched NLL+gradient launch over
+ * every active fit (fixed per-fit tiles, per-fit reduction in tile order: a fit's result
+ * does not depend on the other fits in the batch) and ONE launch advancing every fit's
+ * device-resident minimiser (BFGS, then Newton steps on a finite-difference Hessian whose
+ * inverse gives the errors), then retires finished fits.  goo_server_result returns
+ * GOO_ERR_STATE until the fit is finished.  stats: [rounds, evaluation ms, generation ms,
+ * candidates, accepted, fmax, arena bytes, arena bytes in use]. */
+typedef struct goo_server goo_server;
+typedef struct goo_server_options {
+  int64_t hbm_budget_bytes; /* event arena (<= 0: half of the free device memory)           */
+  int32_t max_fits;         /* fit slots (<= 0: 4096)                                       */
+  int32_t tile_events;      /* events per tile of the batched launch (<= 0: 16384)          */
+  int32_t max_iter;         /* BFGS iterations per fit (<= 0: 200)                          */
+  int32_t pad;
+  double edm_tol;           /* (<= 0: 1e-6)                                                 */
+  double fmax;              /* generator envelope (<= 0: 1.2 x the maximum on a 1024^2 grid) */
+} goo_server_options;
+int goo_server_create(goo_model* model, const double* theta_gen, const int* free_mask, const double* scale,
+                      const goo_server_options* options, goo_server** out);
+int goo_server_submit(goo_server* server, int64_t n_events, uint64_t seed, const double* theta_start,
+                      int64_t* ticket);
+int goo_server_step(goo_server* server, int* n_queued, int* n_active, int* n_done);
+int goo_server_result(goo_server* server, int64_t ticket, double* theta_out, double* errors_out,
+                      goo_fit_result* res);
+int goo_server_stats(const goo_server* server, double* out /* 8 doubles */);
+int goo_server_free(goo_server* server);
+/* One toy from the same generator, written to host float arrays s12_out, s13_out. */
+int goo_toy_generate(goo_model* model, const double* theta, double fmax, uint64_t seed, int64_t n_events,
+                     float* s12_out, float* s13_out);
+/* NLL and gradient of n_fits (dataset, theta) pairs of one amplitude model in one launch
+ * (FP32 path); theta: n_fits x n_params, nll_out: n_fits, grad_out: n_fits x n_params.  The
+ * fits must share every non-coefficient parameter. */
+int goo_nll_grad_batch(goo_model* model, int n_fits, const goo_dataset* const* datasets, const double* theta,
+                       int precision, double* nll_out, double* grad_out);
+
 /* ---- shards (paper Sec. 4: MPI divides the dataset among processes) --------------------------
  * Partial sums over events [begin, end) of ds: out[0] = sum of -log f, out[1] = its
  * compensation term, out[2] = number of events, out[3 .. 3+n_params) = gradient partials

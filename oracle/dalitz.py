@@ -88,7 +88,7 @@ def spin_factor(L, q, k, cos):
     raise ValueError("spin > 2 not supported")
 
 
-def resonance_amplitude(s12, s13, kin, pair, L, m0, g0):
+def resonance_amplitude(s12, s13, kin, pair, L, m0, g0, dtype=torch.float64):
     M = kin["M"]
     masses = {1: kin["m1"], 2: kin["m2"], 3: kin["m3"]}
     inv = invariants(s12, s13, M, kin["m1"], kin["m2"], kin["m3"])
@@ -97,7 +97,8 @@ def resonance_amplitude(s12, s13, kin, pair, L, m0, g0):
     s = s_of(inv, a, b)
     s_ac = s_of(inv, a, c)
     q, k, cos = helicity_frame(s, s_ac, M, mA, mB, mC)
-    m0 = torch.as_tensor(m0, dtype=torch.float64)
+    m0 = torch.as_tensor(m0, dtype=dtype)
+    g0 = torch.as_tensor(g0, dtype=dtype)
     q0 = torch.sqrt(kallen(m0 * m0, mA * mA, mB * mB)) / (2 * m0)
     r = kin["r_res"]
     ratio = barrier(L, (r * q) ** 2) / barrier(L, (r * q0) ** 2)
@@ -138,17 +139,17 @@ class DalitzModel:
         self.amps = spec["pdf"][2]
         self.pidx = {p[0]: i for i, p in enumerate(spec["params"])}
 
-    def amplitude_matrix(self, cols, theta):
+    def amplitude_matrix(self, cols, theta, dtype=torch.float64):
         """Complex [n_events, K] matrix of the amplitudes A_k (coefficients not applied)."""
-        th = torch.as_tensor(theta, dtype=torch.float64)
-        s12 = torch.as_tensor(cols["s12"], dtype=torch.float64)
-        s13 = torch.as_tensor(cols["s13"], dtype=torch.float64)
+        th = torch.as_tensor(theta, dtype=dtype) if not torch.is_tensor(theta) else theta.to(dtype)
+        s12 = torch.as_tensor(cols["s12"], dtype=dtype)
+        s13 = torch.as_tensor(cols["s13"], dtype=dtype)
         out = []
         for amp in self.amps:
             if amp[0] == "bw":
                 _, pair, L, m0n, g0n, _, _ = amp
                 out.append(resonance_amplitude(s12, s13, self.kin, pair, L,
-                                               th[self.pidx[m0n]], th[self.pidx[g0n]]))
+                                               th[self.pidx[m0n]], th[self.pidx[g0n]], dtype=dtype))
             elif amp[0] == "nr":
                 out.append(torch.complex(torch.ones_like(s12), torch.zeros_like(s12)))
             else:

@@ -1,0 +1,129 @@
+// dalitz.cuh -- device code shared by the amplitude-model kernels (dalitz.cu) and the
+// toy-MC server (serve.cu): lineshape constants, the Breit-Wigner amplitude of one
+// resonance, and the loads of the cached amplitudes of one event.  The formulas are stated
+// at the top of dalitz.cu.
+#pragma once
+
+#include "common.cuh"
+
+namespace goo {
+
+constexpr int kMaxAmp = 16;
+
+struct BwConst {
+  int spin, pair;       // pair 0: (12)+3, 1: (13)+2, 2: (23)+1
+  double m0sq, m0w;     // m0^2, m0 * Gamma0
+  double inv_q0sq;      // 1 / q0^2
+  double r2, rp2;       // resonance and parent barrier radii squared
+  double thrP, thrM;    // (mA + mB)^2, (mA - mB)^2
+  double pthrP, pthrM;  // (M + mC)^2, (M - mC)^2
+  double zconst;        // (mA^2 - mB^2)(M^2 - mC^2)
+  double inv4M2;        // 1 / (4 M^2)
+  double Fz0;           // 1 + z0 (L=1) or 9 + 3 z0 + z0^2 (L=2)
+};
+
+struct DalitzDev {
+  int nbw;              // number of Breit-Wigner amplitudes (cached)
+  double sumsq;         // M^2 + m1^2 + m2^2 + m3^2  (s23 = sumsq - s12 - s13)
+  BwConst bw[kMaxAmp];
+};
+
+// ---------------------------------------------------------------------------------------
+// amplitude of one Breit-Wigner resonance at (s12, s13, s23), in precision T
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void bw_amp(const BwConst& b, T s12, T s13, T s23, T& re, T& im) {
+  const int L = b.spin;
+  T s, sac, sbc;
+  if (b.pair == 0) {
+    s = s12;
+    sac = s13;
+    sbc = s23;
+  } else if (b.pair == 1) {
+    s = s13;
+    sac = s12;
+    sbc = s23;
+  } else {
+    s = s23;
+    sac = s12;
+    sbc = s13;
+  }
+  const T lam1 = (s - T(b.thrP)) * (s - T(b.thrM));
+  T q2 = lam1 / (T(4) * s);
+  q2 = q2 > T(0) ? q2 : T(0);
+  const T z = T(b.r2) * q2;
+  const T t = q2 * T(b.inv_q0sq);
+  const T st = sqrt(t);
+  T ratio2, pw;
+  if (L == 0) {
+    ratio2 = T(1);
+    pw = st;
+  } else if (L == 1) {
+    ratio2 = T(b.Fz0) / (T(1) + z);
+    pw = t * st;
+  } else {
+    ratio2 = T(b.Fz0) / (T(9) + T(3) * z + z * z);
+    pw = t * t * st;
+  }
+  const T rs = T(1) / sqrt(s);
+  const T m0 = sqrt(T(b.m0sq));
+  const T di = T(b.m0w) * pw * m0 * rs * ratio2;  // m0 Gamma(s)
+  const T dr = T(b.m0sq) - s;
+  const T inv = T(1) / (dr * dr + di * di);
+  const T lam2 = (s - T(b.pthrP)) * (s - T(b.pthrM));
+  T zp = T(b.rp2) * lam2 * T(b.inv4M2);
+  zp = zp > T(0) ? zp : T(0);
+  T parent, spinf;
+  if (L == 0) {
+    parent = T(1);
+    spinf = T(1);
+  } else if (L == 1) {
+    parent = T(1) / sqrt(T(1) + zp);
+    spinf = sac - sbc - T(b.zconst) / s;
+  } else {
+    parent = T(3) / sqrt(T(9) + T(3) * zp + zp * zp);
+    const T z1 = sac - sbc - T(b.zconst) / s;
+    spinf = z1 * z1 - lam1 * lam2 / (T(3) * s * s);
+  }
+  const T scale = sqrt(ratio2) * parent * spinf * inv;
+  re = dr * scale;
+  im = di * scale;
+}
+
+// Loads the nbw cached amplitudes of event i (compile-time bound KB, runtime nbw).
+template <int KB>
+__device__ __forceinline__ void load_amps(const float4* __restrict__ cache, int64_t n, int64_t i, int nbw,
+                                          float (&ar)[KB + 1], float (&ai)[KB + 1]) {
+#pragma unroll
+  for (int p = 0; p < (KB + 1) / 2; ++p) {
+    if (2 * p < nbw) {
+      const float4 v = __ldg(cache + (int64_t)p * n + i);
+      ar[2 * p] = v.x;
+      ai[2 * p] = v.y;
+      if (2 * p + 1 < KB) {
+        ar[2 * p + 1] = v.z;
+        ai[2 * p + 1] = v.w;
+      }
+    } else {
+      ar[2 * p] = ai[2 * p] = 0.f;
+      if (2 * p + 1 < KB) ar[2 * p + 1] = ai[2 * p + 1] = 0.f;
+    }
+  }
+}
+
+template <int KB>
+__device__ __forceinline__ void load_amps(const double2* __restrict__ cache, int64_t n, int64_t i, int nbw,
+                                          double (&ar)[KB + 1], double (&ai)[KB + 1]) {
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    if (k < nbw) {
+      const double2 v = cache[(int64_t)k * n + i];
+      ar[k] = v.x;
+      ai[k] = v.y;
+    } else {
+      ar[k] = ai[k] = 0.0;
+    }
+  }
+}
+
+}  // namespace goo

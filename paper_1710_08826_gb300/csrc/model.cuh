@@ -88,3 +88,17 @@ struct goo_model {
   goo::ModelDev* stage = nullptr;  // pinned host staging of the per-call model block
   goo::DalitzModel* dalitz = nullptr;
 };
+
+namespace goo {
+// What the toy-MC server needs from an amplitude model (dalitz.cu): device lineshape
+// constants and FP32-path Gram matrix at theta, amplitude/parameter layout and the box.
+struct AmpModelInfo {
+  const void* dalitz_dev;   // DalitzDev*
+  const double* gram_dev;   // K x K complex, FP64 (from the float32 MC cache)
+  int K, nbw, has_nr;
+  int par_re[16], par_im[16];
+  double lo12, hi12, lo13, hi13;
+  double M, m1, m2, m3;
+};
+int dalitz_server_info(goo_model* m, const double* theta, AmpModelInfo* info);
+}  // namespace goo

@@ -44,6 +44,12 @@ class GooFitResult(ctypes.Structure):
                 ("status", ctypes.c_int32)]
 
 
+class GooServerOptions(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_fits", ctypes.c_int32), ("tile_events", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("pad", ctypes.c_int32), ("edm_tol", ctypes.c_double),
+                ("fmax", ctypes.c_double)]
+
+
 class GooError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"goo error {code}: {msg}")
@@ -81,6 +87,17 @@ def _load():
         "goo_nll_partial": (ctypes.c_int, [vp, vp, i64, i64, dp, ctypes.c_int, ctypes.c_int, dp]),
         "goo_combine_partials": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, dp, dp]),
         "goo_gram": (ctypes.c_int, [vp, dp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int)]),
+        "goo_server_create": (ctypes.c_int, [vp, dp, ctypes.POINTER(ctypes.c_int), dp, ctypes.POINTER(GooServerOptions),
+                                             ctypes.POINTER(vp)]),
+        "goo_server_submit": (ctypes.c_int, [vp, i64, ctypes.c_uint64, dp, ctypes.POINTER(i64)]),
+        "goo_server_step": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int)]),
+        "goo_server_result": (ctypes.c_int, [vp, i64, dp, dp, ctypes.c_void_p]),
+        "goo_server_stats": (ctypes.c_int, [vp, dp]),
+        "goo_server_free": (ctypes.c_int, [vp]),
+        "goo_toy_generate": (ctypes.c_int, [vp, dp, ctypes.c_double, ctypes.c_uint64, i64,
+                                            ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+        "goo_nll_grad_batch": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), dp, ctypes.c_int, dp, dp]),
         "goo_fit": (ctypes.c_int, [vp, vp, dp, ctypes.POINTER(ctypes.c_int), dp, ctypes.POINTER(GooFitOptions), dp,
                                    ctypes.POINTER(GooFitResult)]),
         "goo_amplitude_cache": (ctypes.c_int, [vp, vp, dp, ctypes.c_int, ctypes.POINTER(vp),
@@ -439,6 +456,95 @@ class Model:
     def close(self):
         if getattr(self, "handle", None):
             _check(lib.goo_model_free(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def toy_generate(model, theta, fmax, seed, n):
+    """One toy from the device generator: (s12, s13) float32 arrays."""
+    t, tp = _dbuf(theta, model.n_params)
+    a = np.zeros(n, dtype=np.float32)
+    b = np.zeros(n, dtype=np.float32)
+    _check(lib.goo_toy_generate(model.handle, tp, float(fmax), int(seed), int(n),
+                                a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                b.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return a, b
+
+
+def nll_grad_batch(model, datasets, thetas, precision="f32"):
+    """NLL and gradient of several (dataset, theta) pairs in one launch."""
+    F = len(datasets)
+    th = np.ascontiguousarray(np.asarray(thetas, dtype=np.float64).reshape(F, model.n_params))
+    handles = (ctypes.c_void_p * F)(*[d.handle.value for d in datasets])
+    nll = np.zeros(F)
+    g = np.zeros((F, model.n_params))
+    _check(lib.goo_nll_grad_batch(model.handle, F, handles, th.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  precision_code(precision), nll.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return nll, g
+
+
+class Server:
+    """Continuous-batching toy-MC fit server (goo_server_*)."""
+
+    def __init__(self, model, theta_gen, free=None, scale=None, budget_bytes=0, max_fits=0, tile_events=0,
+                 max_iter=0, edm_tol=0.0, fmax=0.0):
+        self.model = model
+        P = model.n_params
+        if free is None:
+            free = [not p[2] for p in model.spec["params"]]
+        if scale is None:
+            scale = [p[3] if p[3] > 0 else 1.0 for p in model.spec["params"]]
+        tg, tgp = _dbuf(theta_gen, P)
+        fm = (ctypes.c_int * P)(*[int(bool(v)) for v in free])
+        sc, scp = _dbuf(scale, P)
+        o = GooServerOptions(int(budget_bytes), int(max_fits), int(tile_events), int(max_iter), 0, float(edm_tol),
+                             float(fmax))
+        h = ctypes.c_void_p()
+        _check(lib.goo_server_create(model.handle, tgp, fm, scp, ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h
+
+    def submit(self, n_events, seed, theta_start=None):
+        t = ctypes.c_int64()
+        if theta_start is None:
+            tp = None
+        else:
+            ts, tp = _dbuf(theta_start, self.model.n_params)
+            self._keep = ts
+        _check(lib.goo_server_submit(self.handle, int(n_events), int(seed), tp, ctypes.byref(t)))
+        return t.value
+
+    def step(self):
+        q, a, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib.goo_server_step(self.handle, ctypes.byref(q), ctypes.byref(a), ctypes.byref(d)))
+        return q.value, a.value, d.value
+
+    def result(self, ticket):
+        P = self.model.n_params
+        th = np.zeros(P)
+        err = np.zeros(P)
+        res = GooFitResult()
+        rc = lib.goo_server_result(self.handle, int(ticket), th.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   err.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(res))
+        if rc == GOO_ERR_STATE:
+            return None
+        _check(rc)
+        return th, err, {k: getattr(res, k) for k, _ in GooFitResult._fields_}
+
+    def stats(self):
+        out = np.zeros(8)
+        _check(lib.goo_server_stats(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        keys = ["rounds", "eval_ms", "gen_ms", "candidates", "accepted", "fmax", "arena_bytes", "arena_used"]
+        return dict(zip(keys, out.tolist()))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib.goo_server_free(self.handle))
             self.handle = None
 
     def __del__(self):

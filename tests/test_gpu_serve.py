@@ -1,0 +1,151 @@
+"""GPU tests of the toy-MC server: device toy generation, batched NLL, continuous batching."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dalitz as od
+from oracle import fit as ofit
+from oracle import toys as otoys
+
+pytestmark = pytest.mark.gpu
+
+KIN = synth.DALITZ_MASSES
+
+
+@pytest.fixture(scope="module")
+def goo():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1710_08826_gb300 import goo as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def setup(goo):
+    ctx = goo.Context(0)
+    spec = synth.c3_spec(n_mc=200_000)
+    mc = synth.round_to_f32(synth.dalitz_candidates(200_000, 1710013, KIN["M"], KIN["m1"], KIN["m2"], KIN["m3"]), spec)
+    mcds = goo.Dataset.from_spec(ctx, spec, mc)
+    model = goo.Model(ctx, spec, mc=mcds)
+    theta = np.array(synth.param_values(spec))
+    fmax = 1.2 * od.max_intensity_scan(od.DalitzModel(spec), theta, n=300)
+    return ctx, spec, mc, mcds, model, theta, fmax
+
+
+def test_toy_generator_matches_oracle(goo, setup):
+    ctx, spec, mc, mcds, model, theta, fmax = setup
+    for seed, n in [(1710100, 700), (1710101, 1500), (1710777, 300)]:
+        a, b = goo.toy_generate(model, theta, fmax, seed, n)
+        ra, rb, _ = otoys.generate_toy(spec, theta, fmax, seed, n)
+        np.testing.assert_array_equal(a, ra)
+        np.testing.assert_array_equal(b, rb)
+
+
+def test_toys_follow_the_model(goo, setup):
+    # the generated Dalitz distribution has the model's density: the NLL of the toy at the
+    # generating point is lower than at a distorted point (by far more than statistics)
+    ctx, spec, mc, mcds, model, theta, fmax = setup
+    a, b = goo.toy_generate(model, theta, fmax, 1710200, 20_000)
+    ds = goo.Dataset.from_spec(ctx, spec, {"s12": a.astype(np.float64), "s13": b.astype(np.float64)})
+    th2 = theta.copy()
+    names = synth.param_names(spec)
+    th2[names.index("re_rho770_23")] *= 0.5
+    assert model.nll(ds, theta, "f32") < model.nll(ds, th2, "f32") - 100
+
+
+def _toy_ds(goo, ctx, spec, model, theta, fmax, seed, n):
+    a, b = goo.toy_generate(model, theta, fmax, seed, n)
+    return goo.Dataset.from_spec(ctx, spec, {"s12": a.astype(np.float64), "s13": b.astype(np.float64)})
+
+
+def test_batch_matches_single_and_is_mix_independent(goo, setup):
+    ctx, spec, mc, mcds, model, theta, fmax = setup
+    sizes = [1000, 40_000, 17, 70_001]
+    dss = [_toy_ds(goo, ctx, spec, model, theta, fmax, 1710300 + i, n) for i, n in enumerate(sizes)]
+    rng = np.random.default_rng(5)
+    names = synth.param_names(spec)
+    coef = np.array([nm.startswith(("re_", "im_")) and not nm.endswith("NR") for nm in names])
+    thetas = np.array([theta * np.where(coef, rng.uniform(0.9, 1.1, len(theta)), 1.0) for _ in sizes])
+    nll, g = goo.nll_grad_batch(model, dss, thetas)
+    for i, ds in enumerate(dss):
+        n1, g1 = model.nll_grad(ds, thetas[i], "f32")
+        assert abs(nll[i] - n1) <= 1e-6 * abs(n1) + 1e-6
+        np.testing.assert_allclose(g[i][coef], g1[coef], rtol=1e-4, atol=1e-4 * np.abs(g1).max())
+    # the same fit alone and in a different mix: bit-identical
+    alone_n, alone_g = goo.nll_grad_batch(model, [dss[1]], thetas[1:2])
+    mix_n, mix_g = goo.nll_grad_batch(model, [dss[3], dss[1], dss[0]], thetas[[3, 1, 0]])
+    assert alone_n[0] == mix_n[1] and np.array_equal(alone_g[0], mix_g[1])
+
+
+def _run(server, tickets, max_rounds=5000):
+    for _ in range(max_rounds):
+        q, a, d = server.step()
+        if q == 0 and a == 0:
+            break
+    return {t: server.result(t) for t in tickets}
+
+
+def test_server_fits_match_host_fitter_and_oracle(goo, setup):
+    ctx, spec, mc, mcds, model, theta, fmax = setup
+    names = synth.param_names(spec)
+    free = np.array([not p[2] for p in spec["params"]])
+    steps = np.array([p[3] if p[3] > 0 else 1.0 for p in spec["params"]])
+    server = goo.Server(model, theta, fmax=fmax)
+    toys = [(1710400 + i, n) for i, n in enumerate([3000, 800, 12_000, 5000, 1500, 30_000])]
+    start = theta.copy()
+    start[free] *= 1.05
+    tickets = [server.submit(n, seed, start) for seed, n in toys]
+    res = _run(server, tickets)
+    for (seed, n), t in zip(toys, tickets):
+        th, err, info = res[t]
+        assert info["status"] == 0, info
+        ds = _toy_ds(goo, ctx, spec, model, theta, fmax, seed, n)
+        hth, herr, hinfo = model.fit(ds, start, free, steps, precision="f32")
+        idx = np.flatnonzero(free)
+        assert np.all(np.abs(th[idx] - hth[idx]) / herr[idx] < 0.01), (th[idx] - hth[idx]) / herr[idx]
+        np.testing.assert_allclose(err[idx], herr[idx], rtol=0.03)
+    # oracle fit of one toy (float32 events, float64 oracle)
+    seed, n = toys[0]
+    a, b = goo.toy_generate(model, theta, fmax, seed, n)
+    data = {"s12": a.astype(np.float64), "s13": b.astype(np.float64)}
+    ref = od.DalitzModel(spec)
+    rth, rerr, _, redm = ofit.fit(lambda t: ref.nll_grad(data, mc, t), start, free, steps)
+    th = res[tickets[0]][0]
+    idx = np.flatnonzero(free)
+    assert np.all(np.abs(th[idx] - rth[idx]) / rerr[idx] < 0.01)
+    assert names
+
+
+def test_result_same_alone_and_in_mix(goo, setup):
+    ctx, spec, mc, mcds, model, theta, fmax = setup
+    start = theta.copy()
+    free = np.array([not p[2] for p in spec["params"]])
+    start[free] *= 0.95
+    alone = goo.Server(model, theta, fmax=fmax)
+    t = alone.submit(7000, 1710500, start)
+    r_alone = _run(alone, [t])[t]
+    mixed = goo.Server(model, theta, fmax=fmax, max_fits=3)
+    tickets = [mixed.submit(n, s, start) for s, n in [(1710501, 20_000), (1710502, 900)]]
+    tm = mixed.submit(7000, 1710500, start)
+    tickets += [mixed.submit(n, s, start) for s, n in [(1710503, 4000), (1710504, 15_000)]]
+    res = _run(mixed, tickets + [tm])
+    assert np.array_equal(res[tm][0], r_alone[0]) and np.array_equal(res[tm][1], r_alone[1])
+    assert res[tm][2]["iterations"] == r_alone[2]["iterations"]
+
+
+def test_admission_respects_the_budget(goo, setup):
+    ctx, spec, mc, mcds, model, theta, fmax = setup
+    budget = 72 * 25_000 + 64 * 1024  # room for about one 20k-event toy at a time
+    server = goo.Server(model, theta, fmax=fmax, budget_bytes=budget)
+    tickets = [server.submit(n, 1710600 + i) for i, n in enumerate([20_000, 5000, 18_000, 9000])]
+    peak_active = 0
+    for _ in range(5000):
+        q, a, d = server.step()
+        peak_active = max(peak_active, a)
+        assert server.stats()["arena_used"] <= budget
+        if q == 0 and a == 0:
+            break
+    assert all(server.result(t) is not None for t in tickets)
+    assert peak_active <= 2
+    with pytest.raises(goo.GooError):
+        server.submit(10_000_000, 1)
