@@ -40,6 +40,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--ref-sample", type=int, default=250_000)
+    ap.add_argument("--no-extra", action="store_true", help="skip the Dalitz and serving measurements")
+    ap.add_argument("--toys", type=int, default=4096)
+    ap.add_argument("--rate", type=float, default=1000.0, help="Poisson arrival rate of the second serving run")
     ap.add_argument("--profile", action="store_true",
                     help="minimal run for ncu: 2 warm-up + 2 FP32+grad steps + 1 FP64 step, no baselines")
     return ap.parse_args()
@@ -331,6 +334,10 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if rank == 0 and world == 1 and not args.no_extra:
+        line["c3_dalitz"] = c3_measure(goo, ctx, stream, max(5, args.steps // 2))
+        line["c5_serving"] = c5_study(goo, ctx, n_toys=args.toys)
+        line["c5_serving_poisson"] = c5_study(goo, ctx, n_toys=max(64, args.toys // 4), rate=args.rate, plain_sample=0)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_rate(cols, min(args.cpu_sample, n))
     if rank == 0:
@@ -339,6 +346,135 @@ def run_ours(args):
         pg.barrier()
         pg.destroy_process_group()
     return 0
+
+
+# ---------------------------------------------------------------------------------------
+# three-body amplitude workload (5M events, 1M-point MC normalisation)
+# ---------------------------------------------------------------------------------------
+def c3_measure(goo, ctx, stream, steps, n_events=5_000_000, n_mc=1_000_000):
+    import numpy as np
+    import torch
+
+    import synth
+    spec = synth.c3_spec(n_mc=n_mc)
+    kin = synth.DALITZ_MASSES
+    mc = synth.round_to_f32(synth.dalitz_candidates(n_mc, 1710013, kin["M"], kin["m1"], kin["m2"], kin["m3"]), spec)
+    mcds = goo.Dataset.from_spec(ctx, spec, mc)
+    model = goo.Model(ctx, spec, mc=mcds)
+    theta = np.array(synth.param_values(spec))
+    t0 = time.perf_counter()
+    a, b = goo.toy_generate(model, theta, 0.0, 1710003, n_events)   # accept-reject on the device
+    gen_s = time.perf_counter() - t0
+    ds = goo.Dataset.from_spec(ctx, spec, {"s12": a.astype(np.float64), "s13": b.astype(np.float64)})
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    out = {"workload": f"c3_dalitz: {n_events:,} events generated on the device from the 8-resonance model, "
+                       f"{n_mc:,}-point phase-space MC, 16 free coefficients",
+           "generation_s": gen_s}
+    for prec, grad, k in (("f32", True, steps), ("f64", False, max(3, steps // 5))):
+        for _ in range(3):
+            model.nll_grad(ds, theta, prec) if grad else model.nll(ds, theta, prec)
+        torch.cuda.synchronize()
+        ctx.kernel_times(reset=True)
+        ctx.timing(True)
+        ms = 0.0
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            model.nll_grad(ds, theta, prec) if grad else model.nll(ds, theta, prec)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        ctx.timing(False)
+        kt = ctx.kernel_times(reset=True)
+        name, (cnt, kms) = max(kt.items(), key=lambda kv: kv[1][1])
+        bytes_per_event = 64 if prec == "f32" else 128
+        per = kms / cnt
+        out["f32_grad" if grad else "f64_plain"] = {
+            "evals_per_s": k / (ms * 1e-3), "events_per_s": n_events * k / (ms * 1e-3), "ms_per_eval": ms / k,
+            "kernel": name, "kernel_ms": per,
+            "hbm_frac": n_events * bytes_per_event / (per * 1e-3) / 1e9 / measured_peaks()[0],
+            "what": ("goo_nll_grad, FP32 amplitude cache (64 B/event), adjoint gradient" if grad
+                     else "goo_nll, FP64 amplitude cache (128 B/event)")}
+    return out
+
+
+# ---------------------------------------------------------------------------------------
+# served toy-MC study
+# ---------------------------------------------------------------------------------------
+def c5_study(goo, ctx, n_toys=4096, rate=None, plain_sample=8, n_mc=1_000_000, seed0=1710100):
+    import numpy as np
+
+    import synth
+    spec = synth.c3_spec(n_mc=n_mc)
+    kin = synth.DALITZ_MASSES
+    mc = synth.round_to_f32(synth.dalitz_candidates(n_mc, 1710013, kin["M"], kin["m1"], kin["m2"], kin["m3"]), spec)
+    mcds = goo.Dataset.from_spec(ctx, spec, mc)
+    model = goo.Model(ctx, spec, mc=mcds)
+    theta = np.array(synth.param_values(spec))
+    free = np.array([not p[2] for p in spec["params"]])
+    steps = np.array([p[3] if p[3] > 0 else 1.0 for p in spec["params"]])
+    sizes = synth.toy_sizes(n_toys)
+    rng = np.random.default_rng(1710098)
+    arrivals = np.zeros(n_toys) if rate is None else np.cumsum(rng.exponential(1.0 / rate, n_toys))
+    server = goo.Server(model, theta)
+    submitted, pending = {}, {}
+    finish = np.full(n_toys, np.nan)
+    results = {}
+    t0 = time.perf_counter()
+    nxt = 0
+    last_done = 0
+    rounds = 0
+    while True:
+        now = time.perf_counter() - t0
+        while nxt < n_toys and arrivals[nxt] <= now:
+            tk = server.submit(int(sizes[nxt]), seed0 + nxt)
+            submitted[nxt] = tk
+            pending[tk] = nxt
+            nxt += 1
+        q, a, d = server.step()
+        rounds += 1
+        if d != last_done:
+            now = time.perf_counter() - t0
+            for tk in list(pending):
+                r = server.result(tk)
+                if r is not None:
+                    i = pending.pop(tk)
+                    finish[i] = now
+                    results[i] = r
+            last_done = d
+        if nxt == n_toys and q == 0 and a == 0:
+            break
+        if nxt < n_toys and q == 0 and a == 0:
+            time.sleep(max(0.0, min(arrivals[nxt] - (time.perf_counter() - t0), 0.01)))
+    wall = time.perf_counter() - t0
+    lat = finish - arrivals
+    stats = server.stats()
+    statuses = np.array([results[i][2]["status"] for i in range(n_toys)])
+    out = {"toys": n_toys, "events_total": int(sizes.sum()), "arrival": "all at once" if rate is None
+           else f"Poisson, {rate:g} fits/s", "wall_s": wall, "fits_per_s": n_toys / wall,
+           "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+           "rounds": int(stats["rounds"]), "generation_s": stats["gen_ms"] / 1e3, "converged": int((statuses == 0).sum())}
+    if plain_sample:
+        # the plain form: per-fit serial FP64 with the finite-difference gradient, same toys
+        sample = list(range(plain_sample))
+        t_plain = 0.0
+        worst = 0.0
+        for i in sample:
+            a, b = goo.toy_generate(model, theta, stats["fmax"], seed0 + i, int(sizes[i]))
+            ds = goo.Dataset.from_spec(ctx, spec, {"s12": a.astype(np.float64), "s13": b.astype(np.float64)})
+            model.nll(ds, theta, "f64")   # builds the FP64 amplitude cache outside the timing
+            tp = time.perf_counter()
+            th, err, info = model.fit(ds, theta, free, steps, precision="f64", gradient="fd")
+            t_plain += time.perf_counter() - tp
+            idx = np.flatnonzero(free)
+            worst = max(worst, float(np.max(np.abs(results[i][0][idx] - th[idx]) / err[idx])))
+        out["plain_fp64_fd"] = {"fits_per_s": len(sample) / t_plain, "sample": f"first {len(sample)} toys "
+                                f"({int(sizes[:len(sample)].sum()):,} events), goo_fit FP64 + central-difference gradient",
+                                "max_abs_diff_sigma_vs_served": worst}
+        out["speedup_vs_plain"] = out["fits_per_s"] / out["plain_fp64_fd"]["fits_per_s"]
+    return out
 
 
 def run_profile(args):

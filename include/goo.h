@@ -247,9 +247,13 @@ int goo_server_result(goo_server* server, int64_t ticket, double* theta_out, dou
                       goo_fit_result* res);
 int goo_server_stats(const goo_server* server, double* out /* 8 doubles */);
 int goo_server_free(goo_server* server);
-/* One toy from the same generator, written to host float arrays s12_out, s13_out. */
+/* Toys from the same generator, written to host float arrays: one toy, or n_toys toys
+ * generated together (toy i at offset n[0] + ... + n[i-1]); a toy does not depend on the
+ * others it is generated with. */
 int goo_toy_generate(goo_model* model, const double* theta, double fmax, uint64_t seed, int64_t n_events,
                      float* s12_out, float* s13_out);
+int goo_toys_generate(goo_model* model, const double* theta, double fmax, int n_toys, const uint64_t* seeds,
+                      const int64_t* n_events, float* s12_out, float* s13_out);
 /* NLL and gradient of n_fits (dataset, theta) pairs of one amplitude model in one launch
  * (FP32 path); theta: n_fits x n_params, nll_out: n_fits, grad_out: n_fits x n_params.  The
  * fits must share every non-coefficient parameter. */

@@ -74,8 +74,8 @@ __global__ void amp_cache_f32_kernel(const DalitzDev* __restrict__ dd, const flo
     const float c = (float)(s_dd.sumsq - (double)a - (double)b);
     for (int p = 0; p < planes; ++p) {
       float r0, i0, r1 = 0.f, i1 = 0.f;
-      bw_amp<float>(s_dd.bw[2 * p], a, b, c, r0, i0);
-      if (2 * p + 1 < nbw) bw_amp<float>(s_dd.bw[2 * p + 1], a, b, c, r1, i1);
+      bw_amp<float>(s_dd.bwf[2 * p], a, b, c, r0, i0);
+      if (2 * p + 1 < nbw) bw_amp<float>(s_dd.bwf[2 * p + 1], a, b, c, r1, i1);
       cache[(int64_t)p * n + i] = make_float4(r0, i0, r1, i1);
     }
   }
@@ -432,6 +432,23 @@ static int dalitz_constants(goo_model* m, const double* theta) {
     b.inv4M2 = 1.0 / (4 * M * M);
     const double z0 = b.r2 * q0sq;
     b.Fz0 = (L == 1) ? 1.0 + z0 : (L == 2 ? 9.0 + 3.0 * z0 + z0 * z0 : 1.0);
+    b.m0 = m0;
+    BwConstT<float>& f = h.bwf[k];
+    f.spin = b.spin;
+    f.pair = b.pair;
+    f.m0sq = (float)b.m0sq;
+    f.m0w = (float)b.m0w;
+    f.inv_q0sq = (float)b.inv_q0sq;
+    f.r2 = (float)b.r2;
+    f.rp2 = (float)b.rp2;
+    f.thrP = (float)b.thrP;
+    f.thrM = (float)b.thrM;
+    f.pthrP = (float)b.pthrP;
+    f.pthrM = (float)b.pthrM;
+    f.zconst = (float)b.zconst;
+    f.inv4M2 = (float)b.inv4M2;
+    f.Fz0 = (float)b.Fz0;
+    f.m0 = (float)b.m0;
   }
   goo_ctx* ctx = m->ctx;
   GOO_CUDA_TRY(cudaMemcpyAsync(d.dev, &h, sizeof(DalitzDev), cudaMemcpyHostToDevice, ctx->stream));

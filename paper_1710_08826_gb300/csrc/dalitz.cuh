@@ -10,29 +10,40 @@ namespace goo {
 
 constexpr int kMaxAmp = 16;
 
-struct BwConst {
-  int spin, pair;       // pair 0: (12)+3, 1: (13)+2, 2: (23)+1
-  double m0sq, m0w;     // m0^2, m0 * Gamma0
-  double inv_q0sq;      // 1 / q0^2
-  double r2, rp2;       // resonance and parent barrier radii squared
-  double thrP, thrM;    // (mA + mB)^2, (mA - mB)^2
-  double pthrP, pthrM;  // (M + mC)^2, (M - mC)^2
-  double zconst;        // (mA^2 - mB^2)(M^2 - mC^2)
-  double inv4M2;        // 1 / (4 M^2)
-  double Fz0;           // 1 + z0 (L=1) or 9 + 3 z0 + z0^2 (L=2)
+template <typename T>
+struct BwConstT {
+  int spin, pair;  // pair 0: (12)+3, 1: (13)+2, 2: (23)+1
+  T m0sq, m0w;     // m0^2, m0 * Gamma0
+  T inv_q0sq;      // 1 / q0^2
+  T r2, rp2;       // resonance and parent barrier radii squared
+  T thrP, thrM;    // (mA + mB)^2, (mA - mB)^2
+  T pthrP, pthrM;  // (M + mC)^2, (M - mC)^2
+  T zconst;        // (mA^2 - mB^2)(M^2 - mC^2)
+  T inv4M2;        // 1 / (4 M^2)
+  T Fz0;           // 1 + z0 (L=1) or 9 + 3 z0 + z0^2 (L=2)
+  T m0;            // m0
 };
+using BwConst = BwConstT<double>;
 
 struct DalitzDev {
   int nbw;              // number of Breit-Wigner amplitudes (cached)
   double sumsq;         // M^2 + m1^2 + m2^2 + m3^2  (s23 = sumsq - s12 - s13)
-  BwConst bw[kMaxAmp];
+  BwConstT<double> bw[kMaxAmp];
+  BwConstT<float> bwf[kMaxAmp];  // the same constants rounded to float (FP32 path)
 };
+
+template <typename T>
+__device__ __forceinline__ const BwConstT<T>& bw_of(const DalitzDev& d, int k);
+template <>
+__device__ __forceinline__ const BwConstT<double>& bw_of<double>(const DalitzDev& d, int k) { return d.bw[k]; }
+template <>
+__device__ __forceinline__ const BwConstT<float>& bw_of<float>(const DalitzDev& d, int k) { return d.bwf[k]; }
 
 // ---------------------------------------------------------------------------------------
 // amplitude of one Breit-Wigner resonance at (s12, s13, s23), in precision T
 // ---------------------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ void bw_amp(const BwConst& b, T s12, T s13, T s23, T& re, T& im) {
+__device__ __forceinline__ void bw_amp(const BwConstT<T>& b, T s12, T s13, T s23, T& re, T& im) {
   const int L = b.spin;
   T s, sac, sbc;
   if (b.pair == 0) {
@@ -66,7 +77,7 @@ __device__ __forceinline__ void bw_amp(const BwConst& b, T s12, T s13, T s23, T&
     pw = t * t * st;
   }
   const T rs = T(1) / sqrt(s);
-  const T m0 = sqrt(T(b.m0sq));
+  const T m0 = b.m0;
   const T di = T(b.m0w) * pw * m0 * rs * ratio2;  // m0 Gamma(s)
   const T dr = T(b.m0sq) - s;
   const T inv = T(1) / (dr * dr + di * di);

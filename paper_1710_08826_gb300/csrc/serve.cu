@@ -77,20 +77,18 @@ struct GenConst {
   int nbw;
 };
 
-struct GenBlock {
-  int fit;
-  int out_base;       // position of this block's first accepted event in the toy (-1: count only)
-  int64_t cand0;      // first candidate of the block
-  int64_t ncand;      // candidates in the block (<= kGenBlockCands)
+// One toy of a generation pass: candidates [cand0, cand0 + nblocks * kGenBlockCands) in
+// blocks of kGenBlockCands; `have` events are already accepted, `n` are wanted.
+struct GenToy {
+  int64_t cand0, nblocks, have, n;
   uint64_t seed;
-  int64_t n_target;   // events of the toy
-  float* s12;         // toy columns and amplitude planes (write pass)
+  float* s12;
   float* s13;
   float4* cache;
 };
 
-// Candidate j: (s12, s13), inside test and acceptance; amplitudes of an accepted candidate
-// are returned in (ar, ai).
+// Candidate j: (s12, s13), inside test and acceptance; the amplitudes of an accepted
+// candidate are returned in (ar, ai).
 __device__ __forceinline__ bool gen_candidate(const GenConst& g, const DalitzDev& dd, uint64_t seed, int64_t j,
                                               float& s12, float& s13, float (&ar)[kSrvKB], float (&ai)[kSrvKB]) {
   uint64_t c[4] = {(uint64_t)j, 0ull, 0ull, 0ull};
@@ -112,36 +110,136 @@ __device__ __forceinline__ bool gen_candidate(const GenConst& g, const DalitzDev
 #pragma unroll
   for (int k = 0; k < kSrvKB; ++k) {
     if (k < g.nbw) {
-      bw_amp<float>(dd.bw[k], s12, s13, s23, ar[k], ai[k]);
+      bw_amp<float>(dd.bwf[k], s12, s13, s23, ar[k], ai[k]);
+      sr += g.cr[k] * ar[k] - g.ci[k] * ai[k];
+      si += g.cr[k] * ai[k] + g.ci[k] * ar[k];
     } else {
       ar[k] = ai[k] = 0.f;
     }
-    sr += g.cr[k] * ar[k] - g.ci[k] * ai[k];
-    si += g.cr[k] * ai[k] + g.ci[k] * ar[k];
   }
   return __fmul_rn(ua, g.fmax) < sr * sr + si * si;
 }
 
-// Count pass (out_base < 0) or write pass.  Each thread owns kGenPerThread consecutive
-// candidates; a block-wide exclusive scan of the per-thread counts places accepted events
-// in candidate order.
-__global__ void __launch_bounds__(kBlock) toy_gen_kernel(const __grid_constant__ GenConst g, const DalitzDev* ddp,
-                                                         const GenBlock* __restrict__ blocks, unsigned* counts) {
+// Acceptance of candidate j only (the amplitudes are summed on the fly, not kept).
+__device__ __forceinline__ bool gen_accept(const GenConst& g, const DalitzDev& dd, uint64_t seed, int64_t j) {
+  uint64_t c[4] = {(uint64_t)j, 0ull, 0ull, 0ull};
+  philox4x64(c, seed, kToyKey1);
+  const float s12 = __fadd_rn(g.lo12, __fmul_rn(u24(c[0]), g.w12));
+  const float s13 = __fadd_rn(g.lo13, __fmul_rn(u24(c[1]), g.w13));
+  const float ua = u24(c[2]);
+  const float r = sqrtf(s12);
+  const float e1 = (s12 + g.m1s - g.m2s) / (2.f * r);
+  const float e3 = (g.M2 - s12 - g.m3s) / (2.f * r);
+  const float p1 = sqrtf(fmaxf(e1 * e1 - g.m1s, 0.f));
+  const float p3 = sqrtf(fmaxf(e3 * e3 - g.m3s, 0.f));
+  const float es = (e1 + e3) * (e1 + e3);
+  if (!(s13 > es - (p1 + p3) * (p1 + p3) && s13 < es - (p1 - p3) * (p1 - p3) && e3 > sqrtf(g.m3s))) return false;
+  const float s23 = (float)(dd.sumsq - (double)s12 - (double)s13);
+  float sr = g.cr[kSrvKB], si = g.ci[kSrvKB];
+  for (int k = 0; k < g.nbw; ++k) {
+    float ar, ai;
+    bw_amp<float>(dd.bwf[k], s12, s13, s23, ar, ai);
+    sr += g.cr[k] * ar - g.ci[k] * ai;
+    si += g.cr[k] * ai + g.ci[k] * ar;
+  }
+  return __fmul_rn(ua, g.fmax) < sr * sr + si * si;
+}
+
+__device__ __forceinline__ int gen_find_toy(const int64_t* __restrict__ bprefix, int ntoys, int64_t b) {
+  int lo = 0, hi = ntoys - 1;  // largest t with bprefix[t] <= b
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bprefix[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void gen_load_dd(DalitzDev& dd, const DalitzDev* ddp) {
+  for (int i = threadIdx.x; i < (int)(sizeof(DalitzDev) / 4); i += blockDim.x) ((int*)&dd)[i] = ((const int*)ddp)[i];
+}
+
+// Pass 1: accepted candidates per block (each thread owns kGenPerThread consecutive ones);
+// the per-thread accept masks are kept for the write pass.
+__global__ void __launch_bounds__(kBlock, 2) toy_count_kernel(const __grid_constant__ GenConst g, const DalitzDev* ddp,
+                                                           const GenToy* __restrict__ toys,
+                                                           const int64_t* __restrict__ bprefix, int ntoys,
+                                                           unsigned* counts, unsigned short* masks) {
   __shared__ DalitzDev dd;
   __shared__ unsigned s_warp[kBlock / 32];
-  for (int i = threadIdx.x; i < (int)(sizeof(DalitzDev) / 4); i += blockDim.x) ((int*)&dd)[i] = ((const int*)ddp)[i];
-  const GenBlock b = blocks[blockIdx.x];
+  gen_load_dd(dd, ddp);
   __syncthreads();
-  const int64_t first = b.cand0 + (int64_t)threadIdx.x * kGenPerThread;
+  const int t = gen_find_toy(bprefix, ntoys, blockIdx.x);
+  const GenToy& T = toys[t];
+  const int64_t first = T.cand0 + (int64_t)(blockIdx.x - bprefix[t]) * kGenBlockCands + (int64_t)threadIdx.x * kGenPerThread;
   unsigned mask = 0;
-  for (int r = 0; r < kGenPerThread; ++r) {
-    const int64_t j = first + r;
-    if (j >= b.cand0 + b.ncand) break;
-    float s12, s13, ar[kSrvKB], ai[kSrvKB];
-    if (gen_candidate(g, dd, b.seed, j, s12, s13, ar, ai)) mask |= 1u << r;
+  for (int r = 0; r < kGenPerThread; ++r)
+    if (gen_accept(g, dd, T.seed, first + r)) mask |= 1u << r;
+  masks[(size_t)blockIdx.x * kBlock + threadIdx.x] = (unsigned short)mask;
+  unsigned cnt = __popc(mask);
+  for (int m = 16; m > 0; m >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, m);
+  if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_warp[w];
+    counts[blockIdx.x] = tot;
   }
+}
+
+// Pass 2 (one block per toy): exclusive scan of the toy's block counts in candidate order;
+// out_base[b] = position of block b's first accepted event, or -1 when the toy is complete
+// before it (or the block accepted nothing); accepted[2t] = events of toy t after this pass
+// (capped at n), accepted[2t+1] = candidates it accepted in this pass.
+__global__ void toy_scan_kernel(const GenToy* __restrict__ toys, const int64_t* __restrict__ bprefix,
+                                const unsigned* __restrict__ counts, int* out_base, int64_t* accepted) {
+  __shared__ int64_t s_sum[kBlock];
+  const GenToy& T = toys[blockIdx.x];
+  const int64_t b0 = bprefix[blockIdx.x], nb = T.nblocks;
+  int64_t running = T.have;
+  for (int64_t c0 = 0; c0 < nb; c0 += blockDim.x) {
+    const int64_t b = c0 + threadIdx.x;
+    const int64_t v = b < nb ? (int64_t)counts[b0 + b] : 0;
+    s_sum[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {  // Hillis-Steele inclusive scan
+      const int64_t add = threadIdx.x >= o ? s_sum[threadIdx.x - o] : 0;
+      __syncthreads();
+      s_sum[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (b < nb) {
+      const int64_t base = running + s_sum[threadIdx.x] - v;
+      out_base[b0 + b] = (v > 0 && base < T.n) ? (int)base : -1;
+    }
+    running += s_sum[blockDim.x - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    accepted[2 * blockIdx.x] = running < T.n ? running : T.n;  // capped at n
+    accepted[2 * blockIdx.x + 1] = running - T.have;           // accepted in this pass
+  }
+}
+
+// Pass 3: accepted candidates (from the count pass's per-thread masks) of blocks with
+// out_base >= 0 are re-evaluated and written in candidate order (event columns and the
+// amplitude-cache planes).
+__global__ void __launch_bounds__(kBlock, 2) toy_write_kernel(const __grid_constant__ GenConst g, const DalitzDev* ddp,
+                                                           const GenToy* __restrict__ toys,
+                                                           const int64_t* __restrict__ bprefix, int ntoys,
+                                                           const int* __restrict__ out_base,
+                                                           const unsigned short* __restrict__ masks) {
+  __shared__ DalitzDev dd;
+  __shared__ unsigned s_warp[kBlock / 32];
+  const int ob = out_base[blockIdx.x];
+  if (ob < 0) return;  // uniform over the block
+  gen_load_dd(dd, ddp);
+  __syncthreads();
+  const int t = gen_find_toy(bprefix, ntoys, blockIdx.x);
+  const GenToy& T = toys[t];
+  const int64_t first = T.cand0 + (int64_t)(blockIdx.x - bprefix[t]) * kGenBlockCands + (int64_t)threadIdx.x * kGenPerThread;
+  unsigned mask = masks[(size_t)blockIdx.x * kBlock + threadIdx.x];
   const unsigned cnt = __popc(mask);
-  // block exclusive scan of cnt
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned incl = cnt;
   for (int o = 1; o < 32; o <<= 1) {
@@ -150,27 +248,19 @@ __global__ void __launch_bounds__(kBlock) toy_gen_kernel(const __grid_constant__
   }
   if (lane == 31) s_warp[warp] = incl;
   __syncthreads();
-  unsigned before = 0, total = 0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-    if (w < warp) before += s_warp[w];
-    total += s_warp[w];
-  }
-  if (b.out_base < 0) {
-    if (threadIdx.x == 0) counts[blockIdx.x] = total;
-    return;
-  }
-  int64_t pos = (int64_t)b.out_base + before + (incl - cnt);
-  for (int r = 0; r < kGenPerThread && mask; ++r) {
-    if (!(mask & (1u << r))) continue;
-    mask &= ~(1u << r);
-    if (pos >= b.n_target) break;
+  unsigned before = 0;
+  for (int w = 0; w < warp; ++w) before += s_warp[w];
+  int64_t pos = (int64_t)ob + before + (incl - cnt);
+  while (mask && pos < T.n) {
+    const int r = __ffs(mask) - 1;
+    mask &= mask - 1;
     float s12, s13, ar[kSrvKB], ai[kSrvKB];
-    gen_candidate(g, dd, b.seed, first + r, s12, s13, ar, ai);
-    b.s12[pos] = s12;
-    b.s13[pos] = s13;
+    gen_candidate(g, dd, T.seed, first + r, s12, s13, ar, ai);
+    T.s12[pos] = s12;
+    T.s13[pos] = s13;
 #pragma unroll
     for (int p = 0; p < kSrvKB / 2; ++p)
-      if (2 * p < g.nbw) b.cache[(int64_t)p * b.n_target + pos] = make_float4(ar[2 * p], ai[2 * p], ar[2 * p + 1], ai[2 * p + 1]);
+      if (2 * p < g.nbw) T.cache[(int64_t)p * T.n + pos] = make_float4(ar[2 * p], ai[2 * p], ar[2 * p + 1], ai[2 * p + 1]);
     ++pos;
   }
 }
@@ -663,7 +753,7 @@ __global__ void envelope_kernel(const __grid_constant__ GenConst g, const Dalitz
     float sr = g.cr[kSrvKB], si = g.ci[kSrvKB];
     for (int k = 0; k < g.nbw; ++k) {
       float ar, ai;
-      bw_amp<float>(dd.bw[k], s12, s13, s23, ar, ai);
+      bw_amp<float>(dd.bwf[k], s12, s13, s23, ar, ai);
       sr += g.cr[k] * ar - g.ci[k] * ai;
       si += g.cr[k] * ai + g.ci[k] * ar;
     }
@@ -729,10 +819,18 @@ struct goo_server {
   size_t tiles_cap = 0;
   float2* d_tile_partials = nullptr;
   size_t partials_cap = 0;
-  goo::GenBlock* d_gen = nullptr;
-  size_t gen_cap = 0;
+  goo::GenToy* d_gtoys = nullptr;
+  size_t gtoys_cap = 0;
+  int64_t* d_bprefix = nullptr;
+  size_t bprefix_cap = 0;
   unsigned* d_counts = nullptr;
   size_t counts_cap = 0;
+  int* d_outbase = nullptr;
+  size_t outbase_cap = 0;
+  unsigned short* d_masks = nullptr;
+  size_t masks_cap = 0;
+  int64_t* d_accepted = nullptr;
+  size_t accepted_cap = 0;
   goo::GenConst gen{};
   double gen_eff = 0.03;
   // host
@@ -798,79 +896,94 @@ static int grow(void** p, size_t* cap, size_t need) {
   return GOO_OK;
 }
 
-// Generates the toys of newly admitted slots: a count pass over blocks of candidates, a host
-// prefix sum in candidate order, and a write pass; repeated for toys still short of events.
+// Generates the toys of newly admitted slots.  Each pass covers, per toy still short of
+// events, enough candidates for the remaining events at the running acceptance estimate;
+// count, ordered scan and write run on the device, and only per-toy records cross to the
+// host.
 static int generate(goo_server* s, const std::vector<int>& new_slots) {
   goo_ctx* ctx = s->ctx;
   const auto t0 = std::chrono::steady_clock::now();
   std::vector<int64_t> have(new_slots.size(), 0), cand(new_slots.size(), 0);
   for (int pass = 0; pass < 256; ++pass) {
-    std::vector<GenBlock> blocks;
+    std::vector<GenToy> toys;
     std::vector<int> owner;
+    std::vector<int64_t> bprefix(1, 0);
     for (size_t i = 0; i < new_slots.size(); ++i) {
       const Slot& sl = s->slots[new_slots[i]];
       const int64_t need = sl.n - have[i];
       if (need <= 0) continue;
       const int64_t nc = (int64_t)((double)need / s->gen_eff * 1.1) + kGenBlockCands;
-      const int64_t nb = (nc + kGenBlockCands - 1) / kGenBlockCands;
-      for (int64_t b = 0; b < nb; ++b) {
-        GenBlock g{};
-        g.fit = new_slots[i];
-        g.out_base = -1;
-        g.cand0 = cand[i] + b * kGenBlockCands;
-        g.ncand = kGenBlockCands;
-        g.seed = sl.seed;
-        g.n_target = sl.n;
-        g.s12 = sl.s12;
-        g.s13 = sl.s13;
-        g.cache = sl.cache;
-        blocks.push_back(g);
-        owner.push_back((int)i);
-      }
+      GenToy g{};
+      g.cand0 = cand[i];
+      g.nblocks = (nc + kGenBlockCands - 1) / kGenBlockCands;
+      g.have = have[i];
+      g.n = sl.n;
+      g.seed = sl.seed;
+      g.s12 = sl.s12;
+      g.s13 = sl.s13;
+      g.cache = sl.cache;
+      toys.push_back(g);
+      owner.push_back((int)i);
+      bprefix.push_back(bprefix.back() + g.nblocks);
     }
-    if (blocks.empty()) break;
-    GOO_TRY(grow((void**)&s->d_gen, &s->gen_cap, blocks.size() * sizeof(GenBlock)));
-    GOO_TRY(grow((void**)&s->d_counts, &s->counts_cap, blocks.size() * sizeof(unsigned)));
-    GOO_CUDA_TRY(cudaMemcpyAsync(s->d_gen, blocks.data(), blocks.size() * sizeof(GenBlock), cudaMemcpyHostToDevice,
+    if (toys.empty()) break;
+    const int nt = (int)toys.size();
+    const int64_t nblocks = bprefix.back();
+    if (nblocks > (int64_t)INT32_MAX) return set_error(GOO_ERR_UNSUPPORTED, "toy generation pass too large");
+    GOO_TRY(grow((void**)&s->d_gtoys, &s->gtoys_cap, nt * sizeof(GenToy)));
+    GOO_TRY(grow((void**)&s->d_bprefix, &s->bprefix_cap, (nt + 1) * sizeof(int64_t)));
+    GOO_TRY(grow((void**)&s->d_counts, &s->counts_cap, nblocks * sizeof(unsigned)));
+    GOO_TRY(grow((void**)&s->d_outbase, &s->outbase_cap, nblocks * sizeof(int)));
+    GOO_TRY(grow((void**)&s->d_masks, &s->masks_cap, (size_t)nblocks * kBlock * sizeof(unsigned short)));
+    GOO_TRY(grow((void**)&s->d_accepted, &s->accepted_cap, 2 * nt * sizeof(int64_t)));
+    GOO_CUDA_TRY(cudaMemcpyAsync(s->d_gtoys, toys.data(), nt * sizeof(GenToy), cudaMemcpyHostToDevice, ctx->stream));
+    GOO_CUDA_TRY(cudaMemcpyAsync(s->d_bprefix, bprefix.data(), (nt + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
                                  ctx->stream));
+    const DalitzDev* dd = (const DalitzDev*)s->info.dalitz_dev;
     {
-      LaunchScope ls(ctx, "toy_gen_count");
-      toy_gen_kernel<<<(unsigned)blocks.size(), kBlock, 0, ctx->stream>>>(s->gen, (const DalitzDev*)s->info.dalitz_dev,
-                                                                         s->d_gen, s->d_counts);
+      LaunchScope ls(ctx, "toy_count");
+      toy_count_kernel<<<(unsigned)nblocks, kBlock, 0, ctx->stream>>>(s->gen, dd, s->d_gtoys, s->d_bprefix, nt,
+                                                                     s->d_counts, s->d_masks);
+    }
+    {
+      LaunchScope ls(ctx, "toy_scan");
+      toy_scan_kernel<<<nt, kBlock, 0, ctx->stream>>>(s->d_gtoys, s->d_bprefix, s->d_counts, s->d_outbase,
+                                                      s->d_accepted);
+    }
+    {
+      LaunchScope ls(ctx, "toy_write");
+      toy_write_kernel<<<(unsigned)nblocks, kBlock, 0, ctx->stream>>>(s->gen, dd, s->d_gtoys, s->d_bprefix, nt,
+                                                                     s->d_outbase, s->d_masks);
     }
     GOO_CUDA_TRY(cudaGetLastError());
-    std::vector<unsigned> counts(blocks.size());
-    GOO_CUDA_TRY(cudaMemcpyAsync(counts.data(), s->d_counts, counts.size() * sizeof(unsigned), cudaMemcpyDeviceToHost,
+    std::vector<int64_t> acc(2 * nt);
+    GOO_CUDA_TRY(cudaMemcpyAsync(acc.data(), s->d_accepted, 2 * nt * sizeof(int64_t), cudaMemcpyDeviceToHost,
                                  ctx->stream));
     GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-    std::vector<GenBlock> writes;
-    std::vector<int64_t> running(have);
-    double acc = 0.0;
-    for (size_t k = 0; k < blocks.size(); ++k) {
-      const int i = owner[k];
-      GenBlock g = blocks[k];
-      acc += counts[k];
-      if (counts[k] > 0 && running[i] < g.n_target) {
-        g.out_base = (int)running[i];
-        writes.push_back(g);
+    if (log_level() >= 3) {
+      std::vector<unsigned> cnt(nblocks);
+      std::vector<int> ob(nblocks);
+      cudaMemcpy(cnt.data(), s->d_counts, nblocks * sizeof(unsigned), cudaMemcpyDeviceToHost);
+      cudaMemcpy(ob.data(), s->d_outbase, nblocks * sizeof(int), cudaMemcpyDeviceToHost);
+      for (int t = 0; t < nt; ++t) {
+        std::fprintf(stderr, "[goo] gen pass=%d toy=%d slot=%d seed=%llu cand0=%lld nblocks=%lld have=%lld n=%lld -> %lld (+%lld)\n",
+                     pass, t, new_slots[owner[t]], (unsigned long long)toys[t].seed, (long long)toys[t].cand0,
+                     (long long)toys[t].nblocks, (long long)toys[t].have, (long long)toys[t].n, (long long)acc[2 * t],
+                     (long long)acc[2 * t + 1]);
+        for (int64_t b = bprefix[t]; b < bprefix[t + 1] && b < bprefix[t] + 4; ++b)
+          std::fprintf(stderr, "[goo]    block %lld count=%u out_base=%d\n", (long long)b, cnt[b], ob[b]);
       }
-      running[i] += counts[k];
-      cand[i] = g.cand0 + g.ncand;
     }
-    s->gen_candidates += (double)blocks.size() * kGenBlockCands;
-    s->gen_accepted += acc;
+    double raw = 0.0;
+    for (int t = 0; t < nt; ++t) {
+      const int i = owner[t];
+      have[i] = acc[2 * t];
+      raw += (double)acc[2 * t + 1];
+      cand[i] = toys[t].cand0 + toys[t].nblocks * kGenBlockCands;
+    }
+    s->gen_candidates += (double)nblocks * kGenBlockCands;
+    s->gen_accepted += raw;
     if (s->gen_accepted > 1000) s->gen_eff = s->gen_accepted / s->gen_candidates;
-    for (size_t i = 0; i < have.size(); ++i) have[i] = std::min(running[i], s->slots[new_slots[i]].n);
-    if (!writes.empty()) {
-      GOO_TRY(grow((void**)&s->d_gen, &s->gen_cap, writes.size() * sizeof(GenBlock)));
-      GOO_CUDA_TRY(cudaMemcpyAsync(s->d_gen, writes.data(), writes.size() * sizeof(GenBlock), cudaMemcpyHostToDevice,
-                                   ctx->stream));
-      LaunchScope ls(ctx, "toy_gen_write");
-      toy_gen_kernel<<<(unsigned)writes.size(), kBlock, 0, ctx->stream>>>(s->gen, (const DalitzDev*)s->info.dalitz_dev,
-                                                                         s->d_gen, s->d_counts);
-      GOO_CUDA_TRY(cudaGetLastError());
-      GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));  // the host block list is reused next pass
-    }
   }
   for (size_t i = 0; i < have.size(); ++i)
     if (have[i] < s->slots[new_slots[i]].n) return set_error(GOO_ERR_STATE, "toy generation did not converge");
@@ -1235,44 +1348,61 @@ int goo_server_free(goo_server* s) {
   cudaStreamSynchronize(s->ctx->stream);
   void* ptrs[] = {s->arena, s->d_states, s->d_evals, s->d_results, s->d_model, s->d_params, s->d_tickets,
                   s->d_fit_tiles, s->d_slots, s->d_done, s->d_done_count, s->d_tiles, s->d_tile_partials,
-                  s->d_gen, s->d_counts};
+                  s->d_gtoys, s->d_bprefix, s->d_counts, s->d_outbase, s->d_accepted, s->d_masks};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete s;
   return GOO_OK;
 }
 
-// One toy with the server's generator, written to host arrays (test and user access).
-int goo_toy_generate(goo_model* m, const double* theta, double fmax, uint64_t seed, int64_t n, float* s12_out,
-                     float* s13_out) {
-  if (!m || !theta || n < 0 || (n > 0 && (!s12_out || !s13_out))) return set_error(GOO_ERR_ARG, "goo_toy_generate: bad arguments");
-  if (n == 0) return GOO_OK;
+// Toys from the server's generator, all generated in the same passes and written to host
+// arrays: toy i (seed seeds[i], n[i] events) goes to s12_out/s13_out at offset sum(n[:i]).
+int goo_toys_generate(goo_model* m, const double* theta, double fmax, int n_toys, const uint64_t* seeds,
+                      const int64_t* n, float* s12_out, float* s13_out) {
+  if (!m || !theta || n_toys < 0 || (n_toys > 0 && (!seeds || !n || !s12_out || !s13_out)))
+    return set_error(GOO_ERR_ARG, "goo_toys_generate: bad arguments");
+  if (n_toys == 0) return GOO_OK;
   goo_ctx* ctx = m->ctx;
   GOO_CUDA_TRY(cudaSetDevice(ctx->device));
-  std::vector<int> free_mask(m->n_params, 0);
-  std::vector<double> scale(m->n_params, 1.0);
   AmpModelInfo info;
   GOO_TRY(dalitz_server_info(m, theta, &info));
+  std::vector<int> free_mask(m->n_params, 0);
+  std::vector<double> scale(m->n_params, 1.0);
   for (int k = 0; k < info.nbw; ++k) free_mask[info.par_re[k]] = free_mask[info.par_im[k]] = 1;
   goo_server_options o{};
-  o.max_fits = 1;
-  o.hbm_budget_bytes = (int64_t)fit_bytes(n, info.nbw) + 4096;
+  o.max_fits = n_toys;
+  int64_t bytes = 4096;
+  for (int i = 0; i < n_toys; ++i) {
+    if (n[i] < 1) return set_error(GOO_ERR_ARG, "goo_toys_generate: toy %d has %lld events", i, (long long)n[i]);
+    bytes += (int64_t)fit_bytes(n[i], info.nbw);
+  }
+  o.hbm_budget_bytes = bytes;
   o.fmax = fmax;
   goo_server* s = nullptr;
   GOO_TRY(goo_server_create(m, theta, free_mask.data(), scale.data(), &o, &s));
-  int64_t ticket = 0;
-  int rc = goo_server_submit(s, n, seed, theta, &ticket);
+  int rc = GOO_OK;
+  std::vector<int64_t> tickets(n_toys);
+  for (int i = 0; i < n_toys && rc == GOO_OK; ++i) rc = goo_server_submit(s, n[i], seeds[i], theta, &tickets[i]);
   std::vector<int> admitted;
   if (rc == GOO_OK) rc = admit(s, admitted);
+  if (rc == GOO_OK && (int)admitted.size() != n_toys) rc = set_error(GOO_ERR_OOM, "goo_toys_generate: not all toys fit");
   if (rc == GOO_OK) rc = generate(s, admitted);
-  if (rc == GOO_OK) {
-    const Slot& sl = s->slots[admitted[0]];
-    if (cudaMemcpy(s12_out, sl.s12, n * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(s13_out, sl.s13, n * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
-      rc = set_error(GOO_ERR_CUDA, "goo_toy_generate: copy failed");
+  int64_t off = 0;
+  for (int i = 0; i < n_toys && rc == GOO_OK; ++i) {
+    const Slot& sl = s->slots[admitted[i]];
+    if (cudaMemcpy(s12_out + off, sl.s12, n[i] * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(s13_out + off, sl.s13, n[i] * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = set_error(GOO_ERR_CUDA, "goo_toys_generate: copy failed");
+    off += n[i];
   }
   goo_server_free(s);
   return rc;
+}
+
+int goo_toy_generate(goo_model* m, const double* theta, double fmax, uint64_t seed, int64_t n, float* s12_out,
+                     float* s13_out) {
+  if (n == 0) return GOO_OK;
+  return goo_toys_generate(m, theta, fmax, 1, &seed, &n, s12_out, s13_out);
 }
 
 // Batched NLL + gradient of n_fits (dataset, theta) pairs with one launch (per-fit tiles,

@@ -97,6 +97,9 @@ def _load():
         "goo_server_free": (ctypes.c_int, [vp]),
         "goo_toy_generate": (ctypes.c_int, [vp, dp, ctypes.c_double, ctypes.c_uint64, i64,
                                             ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+        "goo_toys_generate": (ctypes.c_int, [vp, dp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
+                                             ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_float),
+                                             ctypes.POINTER(ctypes.c_float)]),
         "goo_nll_grad_batch": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), dp, ctypes.c_int, dp, dp]),
         "goo_fit": (ctypes.c_int, [vp, vp, dp, ctypes.POINTER(ctypes.c_int), dp, ctypes.POINTER(GooFitOptions), dp,
                                    ctypes.POINTER(GooFitResult)]),
@@ -474,6 +477,25 @@ def toy_generate(model, theta, fmax, seed, n):
                                 a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                 b.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
     return a, b
+
+
+def toys_generate(model, theta, fmax, seeds, sizes):
+    """Several toys generated together: list of (s12, s13) float32 arrays."""
+    t, tp = _dbuf(theta, model.n_params)
+    k = len(seeds)
+    sd = (ctypes.c_uint64 * k)(*[int(v) for v in seeds])
+    nn = (ctypes.c_int64 * k)(*[int(v) for v in sizes])
+    tot = int(sum(int(v) for v in sizes))
+    a = np.zeros(tot, dtype=np.float32)
+    b = np.zeros(tot, dtype=np.float32)
+    _check(lib.goo_toys_generate(model.handle, tp, float(fmax), k, sd, nn,
+                                 a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                 b.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    out, off = [], 0
+    for v in sizes:
+        out.append((a[off:off + int(v)], b[off:off + int(v)]))
+        off += int(v)
+    return out
 
 
 def nll_grad_batch(model, datasets, thetas, precision="f32"):

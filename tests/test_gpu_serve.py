@@ -41,6 +41,19 @@ def test_toy_generator_matches_oracle(goo, setup):
         np.testing.assert_array_equal(b, rb)
 
 
+def test_toys_generated_together_equal_alone(goo, setup):
+    ctx, spec, mc, mcds, model, theta, fmax = setup
+    seeds = [1710150 + i for i in range(5)]
+    sizes = [400, 3000, 17, 1200, 9000]
+    together = goo.toys_generate(model, theta, fmax, seeds, sizes)
+    for (a, b), sd, n in zip(together, seeds, sizes):
+        a1, b1 = goo.toy_generate(model, theta, fmax, sd, n)
+        np.testing.assert_array_equal(a, a1)
+        np.testing.assert_array_equal(b, b1)
+    ra, rb, _ = otoys.generate_toy(spec, theta, fmax, seeds[1], sizes[1])
+    np.testing.assert_array_equal(together[1][0], ra)
+
+
 def test_toys_follow_the_model(goo, setup):
     # the generated Dalitz distribution has the model's density: the NLL of the toy at the
     # generating point is lower than at a distorted point (by far more than statistics)
