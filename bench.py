@@ -43,8 +43,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the Dalitz and serving measurements")
     ap.add_argument("--toys", type=int, default=4096)
     ap.add_argument("--rate", type=float, default=1000.0, help="Poisson arrival rate of the second serving run")
-    ap.add_argument("--profile", action="store_true",
-                    help="minimal run for ncu: 2 warm-up + 2 FP32+grad steps + 1 FP64 step, no baselines")
+    ap.add_argument("--profile", action="store_true", help="short fixed launch sequence for ncu captures")
+    ap.add_argument("--profile-workload", default="c2", choices=["c2", "c3", "c5"])
     return ap.parse_args()
 
 
@@ -478,22 +478,56 @@ def c5_study(goo, ctx, n_toys=4096, rate=None, plain_sample=8, n_mc=1_000_000, s
 
 
 def run_profile(args):
-    """Launch sequence for ncu: [prep, grid, event] x (2 warm-up + 2 FP32+grad) then 1 FP64."""
+    """Short fixed launch sequences for ncu captures.
+
+    c2: [grid, event] x 4 FP32+grad evaluations, then one FP64 evaluation (10M events).
+    c3: amplitude caches and Gram (first call), then 4 FP32+grad and 1 FP64 coherent
+        evaluations on 5M events generated on the device.
+    c5: a served study of 64 toys (generation passes, then rounds of batched evaluation and
+        minimiser updates).
+    """
     import numpy as np
 
     import synth
     from paper_1710_08826_gb300 import build
     build()
     from paper_1710_08826_gb300 import goo
-    spec = synth.c2_spec(bins=GRID)
-    cols = synth.gen_c2(n=args.events, seed=1710002)
     ctx = goo.Context(0)
-    ds = goo.Dataset.from_spec(ctx, spec, cols, dtype="f64")
-    model = goo.Model(ctx, spec)
-    theta = np.array(synth.param_values(spec))
-    out = [model.nll_grad(ds, theta, "f32")[0] for _ in range(4)]
-    out.append(model.nll(ds, theta, "f64"))
-    print(json.dumps({"profile": "c2_3d", "events": args.events, "nll": out, "launches": ctx.launches}))
+    w = args.profile_workload
+    if w == "c2":
+        spec = synth.c2_spec(bins=GRID)
+        cols = synth.gen_c2(n=args.events, seed=1710002)
+        ds = goo.Dataset.from_spec(ctx, spec, cols, dtype="f64")
+        model = goo.Model(ctx, spec)
+        theta = np.array(synth.param_values(spec))
+        out = [model.nll_grad(ds, theta, "f32")[0] for _ in range(4)]
+        out.append(model.nll(ds, theta, "f64"))
+    else:
+        spec = synth.c3_spec()
+        kin = synth.DALITZ_MASSES
+        mc = synth.round_to_f32(synth.dalitz_candidates(1_000_000, 1710013, kin["M"], kin["m1"], kin["m2"], kin["m3"]),
+                                spec)
+        mcds = goo.Dataset.from_spec(ctx, spec, mc)
+        model = goo.Model(ctx, spec, mc=mcds)
+        theta = np.array(synth.param_values(spec))
+        if w == "c3":
+            a, b = goo.toy_generate(model, theta, 0.0, 1710003, 5_000_000)
+            ds = goo.Dataset.from_spec(ctx, spec, {"s12": a.astype(np.float64), "s13": b.astype(np.float64)})
+            out = [model.nll_grad(ds, theta, "f32")[0] for _ in range(4)]
+            out.append(model.nll(ds, theta, "f64"))
+        else:
+            server = goo.Server(model, theta)
+            sizes = synth.toy_sizes(64)
+            for i, n in enumerate(sizes):
+                server.submit(int(n), 1710100 + i)
+            rounds = 0
+            while True:
+                q, a_, d = server.step()
+                rounds += 1
+                if q == 0 and a_ == 0:
+                    break
+            out = [rounds, d]
+    print(json.dumps({"profile": w, "result": out, "launches": ctx.launches}))
     return 0
 
 
