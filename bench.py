@@ -28,6 +28,31 @@ METRIC = "NLL evals/s (events/s) FP64 plain vs FP32+grad; toy fits/s, p50/p99 la
 UNIT = "events/s"
 BYTES_PER_EVENT_F32 = 12   # three float32 columns
 BYTES_PER_EVENT_F64 = 24
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant
+# kernel, from one ncu capture of `bench.py --profile --profile-workload c2`
+# (profiles/sop_event_kernel_f32_c2_10M.md).  Reported only while the kernel's sources
+# still hash to the captured value; scaled by events when the bench runs another size.
+NCU_TRAFFIC = {"sop_nll_grad_f32": {"bytes": 123_343_872, "events": 10_000_000,
+                                    "sources": ["paper_1710_08826_gb300/csrc/tree.cu",
+                                                "paper_1710_08826_gb300/csrc/common.cuh",
+                                                "paper_1710_08826_gb300/csrc/model.cuh"],
+                                    "sha256": "5de31be8be84ae359ab90828efdbddbcaaaf1da4bd35c6f2516b744a03822302"}}
+
+
+def sources_sha256(paths):
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(kernel, n_events):
+    rec = NCU_TRAFFIC.get(kernel)
+    if rec is None or sources_sha256(rec["sources"]) != rec["sha256"]:
+        return None
+    return rec["bytes"] * n_events / rec["events"]
 
 
 def parse():
@@ -303,7 +328,7 @@ def run_ours(args):
         alg_bytes = 0
     achieved = alg_bytes / per_launch_s / 1e9
     roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "frac": achieved / peak, "traffic": ncu_traffic(name, n), "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                 "launch_ms": per_launch_s * 1e3,
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel_share": {k: round(v[1] / max(sum(x[1] for x in kt_mix.values()), 1e-12), 4)
