@@ -65,6 +65,10 @@ int nll_common(goo_model* m, const goo_dataset* ds, const double* theta, int pre
       GOO_TRY(read_result(ctx, 2 + P, res));
     }
   }
+  if (res[1] < 0) {
+    *nll_out = HUGE_VAL;
+    return set_error(GOO_ERR_TIMEOUT, "a device wait for event data gave up; the result is invalid");
+  }
   if (res[1] > 0) {
     *nll_out = HUGE_VAL;
     if (grad_out)
@@ -217,6 +221,11 @@ int goo_nll_partial(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t 
   out[1] = res[1];
   out[2] = (double)(end - begin);
   for (int p = 0; p < P; ++p) out[3 + p] = want_grad ? res[3 + p] : 0.0;
+  if (nbad < 0) {
+    out[0] = HUGE_VAL;
+    return set_error(GOO_ERR_TIMEOUT, "a device wait for event data gave up in [%lld, %lld)", (long long)begin,
+                     (long long)end);
+  }
   if (nbad > 0) {
     out[0] = HUGE_VAL;
     return set_error(GOO_ERR_NONPOSITIVE_PDF, "density is <= 0 for %.0f events in [%lld, %lld)", nbad,

@@ -14,6 +14,8 @@ struct LeafDev {
   int pad;
   float f[6];          // FP32 constants (offsets as hi/lo pairs)
   double d[6];         // FP64 constants
+  double a_ref;        // grid reference exponent of this leaf (upper bound of a over its range)
+  float a_ref_hi, a_ref_lo;
 };
 
 struct CompDev {
@@ -41,6 +43,7 @@ struct GridDev {
 
 struct ModelDev {
   int nK, n_obs, n_params, norm_kind, n_add;
+  int grid_separable;                  // GRID: every product's leaves on distinct observables
   double lo[kMaxObs], hi[kMaxObs];
   CompDev comp[kMaxComp];
   LeafDev leaf[kMaxComp * kMaxLeaf];   // leaf l of product k at [k * kMaxLeaf + l]

@@ -32,6 +32,7 @@
 // bias the fit; per-event rounding is random and averages out.  Closed-form norms in the
 // FP32 path are taken at the FP32-rounded parameters the kernel actually uses, so the NLL is
 // the exact likelihood of those parameters.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <type_traits>
@@ -183,6 +184,9 @@ void host_prep(ModelDev& h, const double* theta, int precision) {
       }
       dlog_leaf[t][0] = g0;
       dlog_leaf[t][1] = g1;
+      L.a_ref = amax_leaf[t];
+      L.a_ref_hi = (float)amax_leaf[t];
+      L.a_ref_lo = (float)(amax_leaf[t] - (double)L.a_ref_hi);
     }
   }
   for (int k = 0; k < kMaxComp; ++k)
@@ -265,12 +269,6 @@ struct LeafReg {
 };
 
 template <typename T>
-struct CompReg {
-  T off_hi, off_lo;   // -log N_k (FP64 path: off_hi only)
-  T w_hi, w_lo;       // w_k     (FP64 path: w_hi only)
-};
-
-template <typename T>
 __device__ __forceinline__ LeafReg<T> load_leaf(const LeafDev& L) {
   LeafReg<T> R;
   R.op = L.op;
@@ -280,22 +278,15 @@ __device__ __forceinline__ LeafReg<T> load_leaf(const LeafDev& L) {
   return R;
 }
 
-template <typename T>
-__device__ __forceinline__ CompReg<T> load_comp(const CompDev& C) {
-  CompReg<T> R;
-  if constexpr (sizeof(T) == 4) {
-    R.off_hi = C.off_hi;
-    R.off_lo = C.off_lo;
-    R.w_hi = C.w_hi;
-    R.w_lo = C.w_lo;
-  } else {
-    R.off_hi = -C.log_norm;
-    R.off_lo = 0.0;
-    R.w_hi = C.w;
-    R.w_lo = 0.0;
-  }
-  return R;
-}
+// Per-call constants of the event kernels, passed by value as a kernel parameter: every
+// field is read with compile-time indices after unrolling, so the arithmetic takes it as a
+// constant-bank operand and it occupies no registers.  Absent leaf slots carry opcode 0.
+template <typename T, int K, int L>
+struct EvConst {
+  LeafReg<T> leaf[K][L];
+  T w_hi[K], w_lo[K];   // w_k (FP64 path: w_hi only)
+  int nK, nobs;
+};
 
 // Value r * exp(a) of one leaf at x (+ xlo, the low part of a double-float coordinate when
 // HasLo) and, if GRAD, d log(leaf) / d par_j.
@@ -410,8 +401,8 @@ __device__ __forceinline__ void leaf_eval(const LeafReg<double>& L, double x, do
 // One event: log f (returned through logf) and, if GRAD, the shares c_k and the leaf
 // derivatives.  Returns false when f <= 0.
 template <typename T, int K, int L, bool GRAD>
-__device__ __forceinline__ bool eval_event(const LeafReg<T> (&lr)[K][L], const CompReg<T> (&cr)[K], int nK, T x0, T x1,
-                                           T x2, T x3, T& logf, T (&ck)[K], T (&dk)[K][L][3]) {
+__device__ __forceinline__ bool eval_event(const EvConst<T, K, L>& P, const T (&off_hi)[K], const T (&off_lo)[K], T x0,
+                                           T x1, T x2, T x3, T& logf, T (&ck)[K], T (&dk)[K][L][3]) {
   T rk[K], ak[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -419,13 +410,13 @@ __device__ __forceinline__ bool eval_event(const LeafReg<T> (&lr)[K][L], const C
 #pragma unroll
     for (int l = 0; l < L; ++l) {
       T lr_, la_;
-      leaf_eval<GRAD>(lr[k][l], pick<T>(lr[k][l].col, x0, x1, x2, x3), lr_, la_, dk[k][l]);
+      leaf_eval<GRAD>(P.leaf[k][l], pick<T>(P.leaf[k][l].col, x0, x1, x2, x3), lr_, la_, dk[k][l]);
       r *= lr_;
       a += la_;
     }
-    a = (a + cr[k].off_hi) + cr[k].off_lo;
+    a = (a + off_hi[k]) + off_lo[k];
     rk[k] = r;
-    ak[k] = (k < nK && r != T(0)) ? a : T(-1e30);
+    ak[k] = (k < P.nK && r != T(0)) ? a : T(-1e30);
   }
   T M = ak[0];
 #pragma unroll
@@ -434,44 +425,39 @@ __device__ __forceinline__ bool eval_event(const LeafReg<T> (&lr)[K][L], const C
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     if constexpr (sizeof(T) == 4) {
-      rk[k] = rk[k] * expf(ak[k] - M);
-      S += fmaf(cr[k].w_hi, rk[k], cr[k].w_lo * rk[k]);
+      rk[k] = rk[k] * __expf(ak[k] - M);
+      S += fmaf(P.w_hi[k], rk[k], P.w_lo[k] * rk[k]);
     } else {
       rk[k] = rk[k] * exp(ak[k] - M);
-      S += cr[k].w_hi * rk[k];
+      S += P.w_hi[k] * rk[k];
     }
   }
   if (!(S > T(0)) || !(M > T(-1e29))) return false;
   if constexpr (sizeof(T) == 4) logf = M + __logf(S);
   else logf = M + log(S);
   if constexpr (GRAD) {
-    const T invS = T(1) / S;
+    T invS;
+    if constexpr (sizeof(T) == 4) invS = __fdividef(1.f, S);
+    else invS = T(1) / S;
 #pragma unroll
     for (int k = 0; k < K; ++k) ck[k] = rk[k] * invS;
   }
   return true;
 }
 
-// Every thread copies the model's leaf and product constants into registers.
-template <typename T, int K, int L>
-__device__ __forceinline__ int load_model_regs(const ModelDev* __restrict__ md, LeafReg<T> (&lr)[K][L],
-                                               CompReg<T> (&cr)[K]) {
-  __shared__ LeafDev s_leaf[K * L];
-  __shared__ CompDev s_comp[K];
-  for (int i = threadIdx.x; i < K * L; i += blockDim.x) s_leaf[i] = md->leaf[(i / L) * kMaxLeaf + (i % L)];
-  for (int i = threadIdx.x; i < K; i += blockDim.x) s_comp[i] = md->comp[i];
-  __syncthreads();
-  const int nK = md->nK;
+// -log N_k of every product (written by the normalisation step) into registers.
+template <typename T, int K>
+__device__ __forceinline__ void load_offsets(const ModelDev* __restrict__ md, T (&off_hi)[K], T (&off_lo)[K]) {
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    cr[k] = load_comp<T>(s_comp[k]);
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-      lr[k][l] = load_leaf<T>(s_leaf[k * L + l]);
-      if (k >= nK || l >= s_comp[k].n_leaf) lr[k][l].op = 0;
+    if constexpr (sizeof(T) == 4) {
+      off_hi[k] = md->comp[k].off_hi;
+      off_lo[k] = md->comp[k].off_lo;
+    } else {
+      off_hi[k] = -md->comp[k].log_norm;
+      off_lo[k] = 0.0;
     }
   }
-  return nK;
 }
 
 // =======================================================================================
@@ -483,16 +469,79 @@ struct EventLanes {
   static constexpr int NS = GRAD ? 1 + K + K * L * 3 : 1;
 };
 
+// Block reduction of the per-thread lanes, last-block reduction over the blocks and the
+// final FP64 combination (lanes -> NLL and d NLL / d theta), shared by the event kernels.
+template <int K, int L, bool GRAD>
+__device__ __forceinline__ void event_finish(ddf (&v)[EventLanes<float, K, L, GRAD>::NS], unsigned bad,
+                                             const ModelDev* __restrict__ md, int nK, float2* partials,
+                                             unsigned* counters, double* result, int out_mode, ddf* s_red,
+                                             unsigned* s_bad) {
+  constexpr int NS = EventLanes<float, K, L, GRAD>::NS;
+  for (int m = 16; m > 0; m >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, m);
+  if ((threadIdx.x & 31) == 0) s_bad[threadIdx.x >> 5] = bad;
+  block_reduce_to_partials<NS>(v, NS, partials, s_red);
+  if (threadIdx.x == 0) {
+    unsigned b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_bad[w];
+    if (b) atomicAdd(counters + 1, b);
+  }
+  __shared__ double s_out[NS];
+  if (!last_block_reduce(partials, NS, gridDim.x, counters, s_out, s_red)) return;
+
+  // ---- final combination (last block, FP64) ----
+  if (threadIdx.x == 0) {
+    const unsigned nbad = atomicAdd(counters + 1, 0u);
+    counters[1] = 0u;
+    const unsigned status = atomicAdd(counters + kStatusWord, 0u);
+    counters[kStatusWord] = 0u;
+    const int P = md->n_params;
+    const double sumlogf = s_out[0];
+    double g[kMaxParams];
+    for (int p = 0; p < kMaxParams; ++p) g[p] = 0.0;
+    if (GRAD) {
+      for (int k = 0; k < nK; ++k) {
+        const double Ck = s_out[1 + k];
+        const double wk = md->comp[k].w;
+        for (int p = 0; p < P; ++p) g[p] += wk * Ck * md->dlogN[k][p] - Ck * md->dw[k][p];
+        for (int l = 0; l < md->comp[k].n_leaf && l < L; ++l) {
+          const LeafDev& lf = md->leaf[k * kMaxLeaf + l];
+          for (int j = 0; j < 3; ++j)
+            if (lf.par[j] >= 0) g[lf.par[j]] -= wk * s_out[1 + K + (k * L + l) * 3 + j];
+        }
+      }
+    }
+    // a device wait that gave up is reported as a negative event count
+    const double nb = status ? -1.0 : (double)nbad;
+    if (out_mode == 0) {
+      result[0] = -sumlogf;
+      result[1] = nb;
+      for (int p = 0; p < P; ++p) result[2 + p] = g[p];
+    } else {
+      result[0] = -sumlogf;
+      result[1] = 0.0;
+      result[2] = nb;
+      for (int p = 0; p < P; ++p) result[3 + p] = g[p];
+    }
+  }
+}
+
+// Resident blocks per SM the event kernel is compiled for: the FP32 form of the small shape
+// fits three 256-thread blocks (<= 80 registers) with its leaf constants in the parameter bank.
+template <typename T, int K, int L>
+struct EventOcc {
+  static constexpr int value = (sizeof(T) == 4 && K * L <= 6) ? 3 : 2;
+};
+
 template <typename T, int K, int L, bool GRAD>
-__global__ void __launch_bounds__(kBlock, 2) sop_event_kernel(const ModelDev* __restrict__ md, Cols<T> cols,
-                                                              int64_t begin, int64_t end, float2* partials,
+__global__ void __launch_bounds__(kBlock, EventOcc<T, K, L>::value) sop_event_kernel(const ModelDev* __restrict__ md, const EvConst<T, K, L> P,
+                                                              Cols<T> cols, int64_t begin, int64_t end, float2* partials,
                                                               unsigned* counters, double* result, int out_mode) {
   constexpr int NS = EventLanes<T, K, L, GRAD>::NS;
   __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
   __shared__ unsigned s_bad[kBlock / 32];
-  LeafReg<T> lr[K][L];
-  CompReg<T> cr[K];
-  const int nK = load_model_regs<T, K, L>(md, lr, cr);
+  T off_hi[K], off_lo[K];
+  load_offsets<T, K>(md, off_hi, off_lo);
+  const int nK = P.nK;
 
   // per-thread accumulators: FP32 path -> Kahan for sum log f, plain FP32 for the adjoint
   // lanes; FP64 path -> plain FP64
@@ -510,7 +559,7 @@ __global__ void __launch_bounds__(kBlock, 2) sop_event_kernel(const ModelDev* __
       for (int j = 0; j < 3; ++j) Aacc[k][l][j] = Acc(0);
   }
   unsigned bad = 0;
-  const int nobs = md->n_obs;
+  const int nobs = P.nobs;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // software pipelining: the next event's columns are requested before this event is
   // evaluated, so the loads' latency overlaps the arithmetic
@@ -532,7 +581,7 @@ __global__ void __launch_bounds__(kBlock, 2) sop_event_kernel(const ModelDev* __
       n3 = nobs > 3 ? cols.c[3][inext] : T(0);
     }
     T logf, ck[K], dk[K][L][3];
-    if (eval_event<T, K, L, GRAD>(lr, cr, nK, x0, x1, x2, x3, logf, ck, dk)) {
+    if (eval_event<T, K, L, GRAD>(P, off_hi, off_lo, x0, x1, x2, x3, logf, ck, dk)) {
       if constexpr (sizeof(T) == 4) {
         acc32.add(logf);
       } else {
@@ -572,48 +621,367 @@ __global__ void __launch_bounds__(kBlock, 2) sop_event_kernel(const ModelDev* __
               (sizeof(T) == 4) ? ddf{(float)Aacc[k][l][j], 0.f} : dd_from_double((double)Aacc[k][l][j]);
     }
   }
-  for (int m = 16; m > 0; m >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, m);
-  if ((threadIdx.x & 31) == 0) s_bad[threadIdx.x >> 5] = bad;
-  block_reduce_to_partials<NS>(v, NS, partials, s_red);
-  if (threadIdx.x == 0) {
-    unsigned b = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_bad[w];
-    if (b) atomicAdd(counters + 1, b);
-  }
-  __shared__ double s_out[NS];
-  if (!last_block_reduce(partials, NS, gridDim.x, counters, s_out, s_red)) return;
+  event_finish<K, L, GRAD>(v, bad, md, nK, partials, counters, result, out_mode, s_red, s_bad);
+}
 
-  // ---- final combination (last block, FP64) ----
-  if (threadIdx.x == 0) {
-    const unsigned nbad = atomicAdd(counters + 1, 0u);
-    counters[1] = 0u;
-    const int P = md->n_params;
-    const double sumlogf = s_out[0];
-    double g[kMaxParams];
-    for (int p = 0; p < kMaxParams; ++p) g[p] = 0.0;
-    if (GRAD) {
-      for (int k = 0; k < nK; ++k) {
-        const double Ck = s_out[1 + k];
-        const double wk = md->comp[k].w;
-        for (int p = 0; p < P; ++p) g[p] += wk * Ck * md->dlogN[k][p] - Ck * md->dw[k][p];
-        for (int l = 0; l < md->comp[k].n_leaf && l < L; ++l) {
-          const LeafDev& lf = md->leaf[k * kMaxLeaf + l];
-          for (int j = 0; j < 3; ++j)
-            if (lf.par[j] >= 0) g[lf.par[j]] -= wk * s_out[1 + K + (k * L + l) * 3 + j];
+// =======================================================================================
+// FP32 event kernel on packed pairs.  Each thread takes two consecutive events at a time and
+// evaluates both with the packed FP32 instructions of sm_100-class GPUs (add / sub / mul /
+// fma on .f32x2 register pairs), so the arithmetic, the leaf dispatch and the index work
+// each issue once per two events; exp2 / lg2 / rcp stay per lane.  Pairs are aligned to
+// even event indices (8-byte column loads); a lane outside [begin, end) is masked.  Each
+// lane is rounded exactly as a scalar FP32 evaluation of the same formulas.
+// =======================================================================================
+namespace pk {
+__device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<const unsigned long long*>(&a)), "l"(*reinterpret_cast<const unsigned long long*>(&b)));
+  return *reinterpret_cast<const float2*>(&d);
+}
+// hardware base-2 exponential / logarithm / reciprocal (PTX .approx forms, denormals flushed)
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+constexpr float kLog2e = 1.4426950408889634f;  // 1 / ln 2
+constexpr float kLn2 = 0.6931471805599453f;
+__device__ __forceinline__ float2 exp(float2 x) {  // e^x per lane
+  const float2 t = mul(x, splat(kLog2e));
+  return make_float2(ex2(t.x), ex2(t.y));
+}
+__device__ __forceinline__ float2 log(float2 x) {  // natural log per lane
+  return mul(make_float2(lg2(x.x), lg2(x.y)), splat(kLn2));
+}
+__device__ __forceinline__ float2 rcp(float2 x) { return make_float2(rcp(x.x), rcp(x.y)); }
+__device__ __forceinline__ float2 pick(int col, float2 x0, float2 x1, float2 x2, float2 x3) {
+  return col == 0 ? x0 : (col == 1 ? x1 : (col == 2 ? x2 : x3));
+}
+}  // namespace pk
+
+// Two events of one leaf: r * exp(a) per lane and, if GRAD, d log(leaf) / d par_j.
+template <bool GRAD>
+__device__ __forceinline__ void leaf_eval2(const LeafReg<float>& L, float2 x, float2& r, float2& a, float2* d) {
+  using namespace pk;
+  const float* c = L.c;
+  d[0] = d[1] = d[2] = splat(0.f);
+  switch (L.op) {
+    case GOO_OP_GAUSS: {
+      const float2 z = mul(sub(sub(x, splat(c[0])), splat(c[1])), splat(c[2]));
+      const float2 zz = mul(z, z);
+      r = splat(1.f);
+      a = mul(splat(-0.5f), zz);
+      if (GRAD) {
+        d[0] = mul(z, splat(c[2]));
+        d[1] = mul(zz, splat(c[2]));
+      }
+      break;
+    }
+    case GOO_OP_EXPO:
+      r = splat(1.f);
+      a = mul(splat(c[0]), x);
+      if (GRAD) d[0] = x;
+      break;
+    case GOO_OP_POLY2: {
+      r = fma(x, fma(splat(c[1]), x, splat(c[0])), splat(1.f));
+      a = splat(0.f);
+      if (GRAD) {
+        const float2 ir = rcp(r);
+        d[0] = mul(x, ir);
+        d[1] = mul(mul(x, x), ir);
+      }
+      break;
+    }
+    case GOO_OP_ARGUS: {
+      const float2 u = mul(mul(add(sub(splat(c[0]), x), splat(c[1])), add(add(splat(c[0]), x), splat(c[1]))), splat(c[2]));
+      // a lane with u <= 0 has value 0 (r = 0); u is replaced by 1 there to keep it finite
+      const bool p0 = u.x > 0.f, p1 = u.y > 0.f;
+      const float2 us = make_float2(p0 ? u.x : 1.f, p1 ? u.y : 1.f);
+      const float2 lu = pk::log(us);
+      r = make_float2(p0 ? x.x : 0.f, p1 ? x.y : 0.f);
+      a = fma(splat(c[4]), lu, mul(splat(c[3]), us));
+      if (GRAD) {
+        d[0] = mul(mul(splat(c[5]), sub(splat(1.f), us)), fma(splat(c[4]), rcp(us), splat(c[3])));
+        d[1] = us;
+        d[2] = lu;
+      }
+      break;
+    }
+    default:
+      r = splat(1.f);
+      a = splat(0.f);
+  }
+}
+
+// Two events: log f per lane, ok per lane (f > 0) and, if GRAD, c_k and the leaf derivatives.
+template <int K, int L, bool GRAD>
+__device__ __forceinline__ void eval_event2(const EvConst<float, K, L>& P, const float (&off_hi)[K],
+                                            const float (&off_lo)[K], float2 x0, float2 x1, float2 x2, float2 x3,
+                                            float2& logf, bool& ok0, bool& ok1, float2 (&ck)[K],
+                                            float2 (&dk)[K][L][3]) {
+  using namespace pk;
+  float2 rk[K], ak[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    float2 r = splat(1.f), a = splat(0.f);
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      float2 lr_, la_;
+      leaf_eval2<GRAD>(P.leaf[k][l], pick(P.leaf[k][l].col, x0, x1, x2, x3), lr_, la_, dk[k][l]);
+      r = mul(r, lr_);
+      a = add(a, la_);
+    }
+    a = add(add(a, splat(off_hi[k])), splat(off_lo[k]));
+    rk[k] = r;
+    const bool on = k < P.nK;
+    ak[k] = make_float2((on && r.x != 0.f) ? a.x : -1e30f, (on && r.y != 0.f) ? a.y : -1e30f);
+  }
+  float2 M = ak[0];
+#pragma unroll
+  for (int k = 1; k < K; ++k) M = make_float2(fmaxf(M.x, ak[k].x), fmaxf(M.y, ak[k].y));
+  float2 S = splat(0.f);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    rk[k] = mul(rk[k], pk::exp(sub(ak[k], M)));
+    S = add(S, fma(splat(P.w_hi[k]), rk[k], mul(splat(P.w_lo[k]), rk[k])));
+  }
+  ok0 = S.x > 0.f && M.x > -1e29f;
+  ok1 = S.y > 0.f && M.y > -1e29f;
+  logf = add(M, pk::log(make_float2(ok0 ? S.x : 1.f, ok1 ? S.y : 1.f)));
+  if constexpr (GRAD) {
+    const float2 invS = rcp(S);
+#pragma unroll
+    for (int k = 0; k < K; ++k) ck[k] = mul(rk[k], invS);
+  }
+}
+
+// Compensated FP32 accumulator of an event pair (one Kahan sum per lane, packed).
+struct Kahan2 {
+  float2 s = {0.f, 0.f}, c = {0.f, 0.f};
+  __device__ __forceinline__ void add(float2 x) {
+    const float2 y = pk::sub(x, c);
+    const float2 t = pk::add(s, y);
+    c = pk::sub(pk::sub(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ void add_lane(int lane, float x) {
+    float& sl = lane ? s.y : s.x;
+    float& cl = lane ? c.y : c.x;
+    const float y = x - cl;
+    const float t = sl + y;
+    cl = (t - sl) - y;
+    sl = t;
+  }
+};
+
+constexpr int kEventStages = 3;     // column tiles in flight per block (TMA bulk copies)
+constexpr int kPairsPerThread = 4;  // event pairs per thread per tile
+
+template <int K, int L, bool GRAD>
+struct EventOcc2 {
+  static constexpr int value = (K * L <= 6 && !GRAD) ? 3 : 2;
+};
+
+// Per-thread accumulators of the pair kernel.
+template <int K, int L>
+struct PairAcc {
+  Kahan2 lf;
+  float2 C[K];
+  float2 A[K][L][3];
+  unsigned bad;
+};
+
+// One event pair: evaluate and accumulate the lanes that are in range (v0, v1) with f > 0.
+template <int K, int L, bool GRAD>
+__device__ __forceinline__ void pair_step(const EvConst<float, K, L>& P, const float (&off_hi)[K],
+                                          const float (&off_lo)[K], const float2 (&x)[kMaxObs], bool v0, bool v1,
+                                          PairAcc<K, L>& S) {
+  float2 logf, ck[K], dk[K][L][3];
+  bool ok0, ok1;
+  eval_event2<K, L, GRAD>(P, off_hi, off_lo, x[0], x[1], x[2], x[3], logf, ok0, ok1, ck, dk);
+  const bool m0 = v0 && ok0, m1 = v1 && ok1;
+  S.bad += (unsigned)(v0 && !ok0) + (unsigned)(v1 && !ok1);
+  if (m0 && m1) {
+    S.lf.add(logf);
+    if constexpr (GRAD) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        S.C[k] = pk::add(S.C[k], ck[k]);
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) S.A[k][l][q] = pk::fma(ck[k], dk[k][l][q], S.A[k][l][q]);
+      }
+    }
+  } else {
+    // one lane outside the range or with f <= 0: accumulate the other lane alone
+#pragma unroll
+    for (int lane = 0; lane < 2; ++lane) {
+      if (!(lane ? m1 : m0)) continue;
+      S.lf.add_lane(lane, lane ? logf.y : logf.x);
+      if constexpr (GRAD) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const float c = lane ? ck[k].y : ck[k].x;
+          (lane ? S.C[k].y : S.C[k].x) += c;
+#pragma unroll
+          for (int l = 0; l < L; ++l)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              float& A = lane ? S.A[k][l][q].y : S.A[k][l][q].x;
+              A = fmaf(c, lane ? dk[k][l][q].y : dk[k][l][q].x, A);
+            }
         }
       }
     }
-    if (out_mode == 0) {
-      result[0] = -sumlogf;
-      result[1] = (double)nbad;
-      for (int p = 0; p < P; ++p) result[2 + p] = g[p];
+  }
+}
+
+// Column tiles of TE = 2 * kPairsPerThread * kBlock events (aligned to multiples of TE)
+// are staged in shared memory by bulk copies, kEventStages tiles ahead; block b takes tiles
+// tb0 + b, tb0 + b + gridDim.x, ...  Within a tile thread t takes pairs t, t + kBlock, ...
+// Dynamic shared memory: kEventStages * n_obs * TE floats.
+template <int K, int L, bool GRAD>
+__global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
+    sop_event2_kernel(const ModelDev* __restrict__ md, const EvConst<float, K, L> P, Cols<float> cols, int64_t begin,
+                      int64_t end, float2* partials, unsigned* counters, double* result, int out_mode) {
+  using namespace pk;
+  constexpr int NS = EventLanes<float, K, L, GRAD>::NS;
+  constexpr int PPT = kPairsPerThread;
+  constexpr int TE = 2 * PPT * kBlock;
+  constexpr int NST = kEventStages;
+  __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
+  __shared__ unsigned s_bad[kBlock / 32];
+  __shared__ __align__(8) uint64_t s_bar[NST];
+  extern __shared__ __align__(128) float s_col[];  // [NST][nobs][TE]
+  const int nobs = P.nobs;
+  const int64_t tb0 = begin / TE, tb1 = (end + TE - 1) / TE;
+  auto tile_of = [&](int j) { return tb0 + blockIdx.x + (int64_t)j * gridDim.x; };
+  auto full = [&](int64_t t) { return t * TE >= begin && (t + 1) * TE <= end; };
+  auto buf = [&](int st, int c) { return s_col + ((size_t)st * nobs + c) * TE; };
+  // one thread stages tile j in buffer j % NST: bulk copies for a full tile, a bare arrival
+  // (completes the phase at once) for a ragged one, which its threads read from global memory
+  auto issue = [&](int j) {
+    const int64_t t = tile_of(j);
+    if (t >= tb1) return;
+    uint64_t* bar = &s_bar[j % NST];
+    if (full(t)) {
+      mbar_arrive_expect_tx(bar, (unsigned)(nobs * TE * sizeof(float)));
+      for (int c = 0; c < nobs; ++c) bulk_load(buf(j % NST, c), cols.c[c] + t * TE, TE * sizeof(float), bar);
     } else {
-      result[0] = -sumlogf;
-      result[1] = 0.0;
-      result[2] = (double)nbad;
-      for (int p = 0; p < P; ++p) result[3 + p] = g[p];
+      mbar_arrive(bar);
+    }
+  };
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < NST; ++st) mbar_init(&s_bar[st], 1);
+    mbar_init_fence();
+    for (int j = 0; j < NST; ++j) issue(j);
+  }
+  // the column copies above read only the dataset; the normalisation written by the
+  // previous kernel in the stream is read after this point
+  grid_dep_wait();
+  float off_hi[K], off_lo[K];
+  load_offsets<float, K>(md, off_hi, off_lo);
+  const int nK = P.nK;
+  __syncthreads();  // barriers initialised before any thread waits on them
+  PairAcc<K, L> S;
+  S.bad = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    S.C[k] = splat(0.f);
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) S.A[k][l][q] = splat(0.f);
+  }
+  int j = 0;
+  bool failed = false;
+  for (; tile_of(j) < tb1; ++j) {
+    const int64_t t = tile_of(j);
+    const int st = j % NST;
+    const bool ok_wait = mbar_wait(&s_bar[st], (unsigned)(j / NST) & 1u);
+    if (ok_wait) {
+      if (full(t)) {
+        // every event of the tile is in range: read the staged columns
+#pragma unroll 1
+        for (int u = 0; u < PPT; ++u) {
+          const int pr = threadIdx.x + u * kBlock;
+          float2 x[kMaxObs];
+#pragma unroll
+          for (int c = 0; c < kMaxObs; ++c)
+            x[c] = c < nobs ? reinterpret_cast<const float2*>(buf(st, c))[pr] : splat(0.f);
+          pair_step<K, L, GRAD>(P, off_hi, off_lo, x, true, true, S);
+        }
+      } else {
+#pragma unroll 1
+        for (int u = 0; u < PPT; ++u) {
+          const int64_t i = t * TE + 2 * (threadIdx.x + u * kBlock);
+          const bool v0 = i >= begin && i < end, v1 = i + 1 >= begin && i + 1 < end;
+          float2 x[kMaxObs];
+#pragma unroll
+          for (int c = 0; c < kMaxObs; ++c) {
+            x[c] = splat(0.f);
+            if (c < nobs) {
+              if (v0 && v1) x[c] = __ldg(reinterpret_cast<const float2*>(cols.c[c] + i));
+              else if (v0) x[c].x = cols.c[c][i];
+              else if (v1) x[c].y = cols.c[c][i + 1];
+            }
+          }
+          if (v0 || v1) pair_step<K, L, GRAD>(P, off_hi, off_lo, x, v0, v1, S);
+        }
+      }
+    }
+    // every thread is done with buffer st (and agrees on whether a wait gave up) before
+    // the buffer is refilled
+    if (__syncthreads_or(!ok_wait)) {
+      failed = true;
+      break;
+    }
+    if (threadIdx.x == 0) {
+      fence_proxy_async();  // the reads of buffer st precede the copy that overwrites it
+      issue(j + NST);
     }
   }
+  if (failed) {
+    // a copy did not arrive in time: record it, then wait (again bounded) for this block's
+    // copies still in flight before the block's shared memory is released
+    if (threadIdx.x == 0) {
+      atomicOr(counters + kStatusWord, 1u);
+      for (int jj = j; jj < j + NST && tile_of(jj) < tb1; ++jj) mbar_wait(&s_bar[jj % NST], (unsigned)(jj / NST) & 1u);
+    }
+    __syncthreads();
+  }
+  // lanes: the two Kahan sums as one double-float, the gradient lanes as the lane sums
+  ddf v[NS];
+  v[0] = dd_add(dd_make(S.lf.s.x, -S.lf.c.x), dd_make(S.lf.s.y, -S.lf.c.y));
+  if constexpr (GRAD) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      v[1 + k] = dd_add(ddf{S.C[k].x, 0.f}, ddf{S.C[k].y, 0.f});
+#pragma unroll
+      for (int l = 0; l < L; ++l)
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          v[1 + K + (k * L + l) * 3 + q] = dd_add(ddf{S.A[k][l][q].x, 0.f}, ddf{S.A[k][l][q].y, 0.f});
+    }
+  }
+  event_finish<K, L, GRAD>(v, S.bad, md, nK, partials, counters, result, out_mode, s_red, s_bad);
 }
 
 // =======================================================================================
@@ -830,22 +1198,116 @@ __global__ void __launch_bounds__(kBlock, 2) grid_kernel(ModelDev* md, float2* p
 }
 
 // =======================================================================================
+// separable grid normalisation: when every leaf of product k acts on its own observable, the
+// midpoint sum over product k's grid factorises exactly into one 1-D midpoint sum per leaf,
+//   N_k = prod_l h_l exp(a_l) S_l,  S_l = sum_i U_l(x_i) exp(-a_l)  (a_l: reference exponent),
+//   d log N_k / d theta = sum_l D_l / S_l,  D_l = sum_i U_l(x_i) exp(-a_l) d log U_l / d theta,
+// so the grid costs the sum of the bins instead of their product.  One block per leaf slot
+// (blockIdx.x = l, blockIdx.y = k); each leaf is evaluated at its observable's bin centres in
+// the path's precision, exactly as in the event kernel, and summed in FP64 in a fixed order;
+// the last block to finish combines the products.
+// =======================================================================================
+template <typename T>
+__global__ void __launch_bounds__(kBlock) grid_sep_kernel(ModelDev* md, double* sums, unsigned* counter) {
+  grid_dep_launch();  // the event kernel after this one may start its column copies now
+  const int k = blockIdx.y, l = blockIdx.x;
+  __shared__ double s_red[kBlock / 32][4];
+  __shared__ bool s_last;
+  const int nleaf = md->comp[k].n_leaf;
+  if (l < nleaf) {  // uniform over the block
+    const LeafDev& LD = md->leaf[k * kMaxLeaf + l];
+    const LeafReg<T> lr = load_leaf<T>(LD);
+    const GridDev& G = md->grid[k];
+    const int d = G.dim_of_col[lr.col];
+    const int nb = G.bins[d];
+    const T aref = (sizeof(T) == 4) ? T(LD.a_ref_hi) : T(LD.a_ref);
+    const T aref_lo = (sizeof(T) == 4) ? T(LD.a_ref_lo) : T(0);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+      T x, xlo;
+      grid_coord<T>(G, d, i, x, xlo);
+      T r, a, dl[3];
+      leaf_eval<true, true>(lr, x, r, a, dl, xlo);
+      T U;
+      if constexpr (sizeof(T) == 4) U = r * expf((a - aref) - aref_lo);
+      else U = r * exp(a - aref);
+      const double u = (double)U;
+      acc[0] += u;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) acc[1 + j] += u * (double)dl[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      for (int m = 16; m > 0; m >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], m);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) s_red[threadIdx.x >> 5][j] = acc[j];
+    __syncthreads();
+    // per leaf, in parallel over the blocks: log(h S) + a_ref and D_j / S
+    if (threadIdx.x < 4) {
+      double S = 0.0, t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        S += s_red[w][0];
+        t += s_red[w][threadIdx.x];
+      }
+      const double aref_used = (sizeof(T) == 4) ? (double)LD.a_ref_hi + (double)LD.a_ref_lo : LD.a_ref;
+      sums[(k * kMaxLeaf + l) * 4 + threadIdx.x] = threadIdx.x == 0 ? log(G.h64[d] * S) + aref_used : t / S;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // last block: log N_k = sum over leaves; d log N_k / d theta scattered to parameters in
+  // shared memory (leaves may share a parameter), then written out in parallel
+  __shared__ double s_dlogN[kMaxComp][kMaxParams];
+  __shared__ double s_term[kMaxComp * kMaxLeaf * 4];
+  __shared__ int s_par[kMaxComp * kMaxLeaf][3];
+  const int nK = gridDim.y, P = md->n_params;
+  for (int t = threadIdx.x; t < kMaxComp * kMaxParams; t += blockDim.x) s_dlogN[t / kMaxParams][t % kMaxParams] = 0.0;
+  for (int t = threadIdx.x; t < nK * kMaxLeaf * 4; t += blockDim.x) s_term[t] = __ldcg(sums + t);
+  for (int t = threadIdx.x; t < nK * kMaxLeaf * 3; t += blockDim.x)
+    s_par[t / 3][t % 3] = (t / 3) % kMaxLeaf < md->comp[t / 3 / kMaxLeaf].n_leaf ? md->leaf[t / 3].par[t % 3] : -1;
+  __syncthreads();
+  if (threadIdx.x < nK) {
+    const int kk = threadIdx.x;
+    const int nl = md->comp[kk].n_leaf;
+    double logN = 0.0;
+    for (int ll = 0; ll < nl; ++ll) {
+      const int slot = kk * kMaxLeaf + ll;
+      logN += s_term[slot * 4];
+      for (int j = 0; j < 3; ++j)
+        if (s_par[slot][j] >= 0) s_dlogN[kk][s_par[slot][j]] += s_term[slot * 4 + 1 + j];
+    }
+    CompDev& Ck = md->comp[kk];
+    Ck.log_norm = logN;
+    const float oh = (float)(-logN);
+    Ck.off_hi = oh;
+    Ck.off_lo = (float)(-logN - (double)oh);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nK * P; t += blockDim.x) md->dlogN[t / P][t % P] = s_dlogN[t / P][t % P];
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// =======================================================================================
 // per-event log f (no reduction): the product of the same evaluation as sop_event_kernel
 // =======================================================================================
 template <typename T, int K, int L>
-__global__ void __launch_bounds__(kBlock) sop_logf_kernel(const ModelDev* __restrict__ md, Cols<T> cols, int64_t n,
-                                                          double* __restrict__ logf) {
-  LeafReg<T> lr[K][L];
-  CompReg<T> cr[K];
-  const int nK = load_model_regs<T, K, L>(md, lr, cr);
-  const int nobs = md->n_obs;
+__global__ void __launch_bounds__(kBlock) sop_logf_kernel(const ModelDev* __restrict__ md, const EvConst<T, K, L> P,
+                                                          Cols<T> cols, int64_t n, double* __restrict__ logf) {
+  T off_hi[K], off_lo[K];
+  load_offsets<T, K>(md, off_hi, off_lo);
+  const int nobs = P.nobs;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const T x0 = cols.c[0][i];
     const T x1 = nobs > 1 ? cols.c[1][i] : T(0);
     const T x2 = nobs > 2 ? cols.c[2][i] : T(0);
     const T x3 = nobs > 3 ? cols.c[3][i] : T(0);
     T lf, ck[K], dk[K][L][3];
-    const bool ok = eval_event<T, K, L, false>(lr, cr, nK, x0, x1, x2, x3, lf, ck, dk);
+    const bool ok = eval_event<T, K, L, false>(P, off_hi, off_lo, x0, x1, x2, x3, lf, ck, dk);
     logf[i] = ok ? (double)lf : -HUGE_VAL;
   }
 }
@@ -989,6 +1451,15 @@ int build_sop_model(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_para
   return GOO_OK;
 }
 
+// True when every product's leaves act on distinct observables (the grid sum factorises).
+static int grid_separable(const ModelDev& h) {
+  for (int k = 0; k < h.nK; ++k)
+    for (int l = 0; l < h.comp[k].n_leaf; ++l)
+      for (int l2 = 0; l2 < l; ++l2)
+        if (h.leaf[k * kMaxLeaf + l2].col == h.leaf[k * kMaxLeaf + l].col) return 0;
+  return 1;
+}
+
 int sop_set_norm(goo_model* m, const goo_norm_spec* spec) {
   ModelDev& h = m->host;
   if (spec->kind == GOO_NORM_ANALYTIC) {
@@ -1034,6 +1505,7 @@ int sop_set_norm(goo_model* m, const goo_norm_spec* spec) {
     return set_error(GOO_ERR_UNSUPPORTED, "goo_model_set_norm: MC normalisation needs an amplitude model");
   }
   h.norm_kind = spec->kind;
+  h.grid_separable = spec->kind == GOO_NORM_GRID ? grid_separable(h) : 0;
   m->norm = *spec;
   goo_ctx* ctx = m->ctx;
   GOO_CUDA_TRY(cudaMemcpyAsync(m->dev, &h, sizeof(ModelDev), cudaMemcpyHostToDevice, ctx->stream));
@@ -1054,6 +1526,20 @@ static int blocks_per_sm(KernelT kernel, int* cache) {
   }
   *cache = n;
   return n;
+}
+
+template <typename T>
+static int launch_grid_sep(goo_model* m) {
+  goo_ctx* ctx = m->ctx;
+  // the per-leaf sums (4 doubles per leaf slot) live in the partials scratch
+  GOO_TRY(ensure_partials(ctx, (size_t)kMaxComp * kMaxLeaf * 4));
+  {
+    LaunchScope ls(ctx, sizeof(T) == 4 ? "grid_norm_f32" : "grid_norm_f64");
+    grid_sep_kernel<T><<<dim3(m->max_leaf, m->host.nK), kBlock, 0, ctx->stream>>>(
+        m->dev, (double*)ctx->scratch.partials, ctx->scratch.counters);
+  }
+  GOO_CUDA_TRY(cudaGetLastError());
+  return GOO_OK;
 }
 
 template <typename T, int L>
@@ -1090,7 +1576,9 @@ int sop_prepare(goo_model* m, const double* theta_host, int precision) {
   *stage = m->host;
   host_prep(*stage, theta_host, precision);
   GOO_CUDA_TRY(cudaMemcpyAsync(m->dev, stage, sizeof(ModelDev), cudaMemcpyHostToDevice, ctx->stream));
-  if (m->host.norm_kind == GOO_NORM_GRID) {
+  if (m->host.norm_kind == GOO_NORM_GRID && m->host.grid_separable) {
+    GOO_TRY((precision == GOO_F32 ? launch_grid_sep<float>(m) : launch_grid_sep<double>(m)));
+  } else if (m->host.norm_kind == GOO_NORM_GRID) {
     if (precision == GOO_F32) {
       GOO_TRY((m->max_leaf <= 2 ? launch_grid_T<float, 2>(m)
                                 : (m->max_leaf <= 3 ? launch_grid_T<float, 3>(m) : launch_grid_T<float, 4>(m))));
@@ -1100,6 +1588,31 @@ int sop_prepare(goo_model* m, const double* theta_host, int precision) {
     }
   }
   return GOO_OK;
+}
+
+// Event-kernel constants from a prepared model block (host_prep already applied).
+template <typename T, int K, int L>
+static EvConst<T, K, L> make_evconst(const ModelDev& h) {
+  EvConst<T, K, L> P;
+  std::memset(&P, 0, sizeof P);
+  P.nK = h.nK;
+  P.nobs = h.n_obs;
+  for (int k = 0; k < K; ++k) {
+    if (k < h.nK) {
+      const CompDev& C = h.comp[k];
+      P.w_hi[k] = (sizeof(T) == 4) ? (T)C.w_hi : (T)C.w;
+      P.w_lo[k] = (sizeof(T) == 4) ? (T)C.w_lo : T(0);
+    }
+    for (int l = 0; l < L; ++l) {
+      LeafReg<T>& R = P.leaf[k][l];
+      if (k >= h.nK || l >= h.comp[k].n_leaf) continue;  // opcode 0: value 1, no derivative
+      const LeafDev& LD = h.leaf[k * kMaxLeaf + l];
+      R.op = LD.op;
+      R.col = LD.col;
+      for (int j = 0; j < 6; ++j) R.c[j] = (sizeof(T) == 4) ? (T)LD.f[j] : (T)LD.d[j];
+    }
+  }
+  return P;
 }
 
 template <typename T, int K, int L, bool GRAD>
@@ -1117,8 +1630,58 @@ static int launch_event_T(goo_model* m, const goo_dataset* ds, int64_t begin, in
   }
   {
     LaunchScope ls(ctx, sizeof(T) == 4 ? (GRAD ? "sop_nll_grad_f32" : "sop_nll_f32") : (GRAD ? "sop_nll_grad_f64" : "sop_nll_f64"));
-    sop_event_kernel<T, K, L, GRAD><<<nb, kBlock, 0, ctx->stream>>>(m->dev, cols, begin, end, ctx->scratch.partials,
+    sop_event_kernel<T, K, L, GRAD><<<nb, kBlock, 0, ctx->stream>>>(m->dev, make_evconst<T, K, L>(*m->stage), cols,
+                                                                   begin, end, ctx->scratch.partials,
                                                                    ctx->scratch.counters, ctx->scratch.result, out_mode);
+  }
+  GOO_CUDA_TRY(cudaGetLastError());
+  return GOO_OK;
+}
+
+constexpr int kMaxDevicesEv = 64;
+
+template <int K, int L, bool GRAD>
+static int launch_event2(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int out_mode) {
+  goo_ctx* ctx = m->ctx;
+  constexpr int TE = 2 * kPairsPerThread * kBlock;
+  const size_t smem = (size_t)kEventStages * m->host.n_obs * TE * sizeof(float);
+  static bool configured[kMaxDevicesEv] = {};
+  if (ctx->device < 0 || ctx->device >= kMaxDevicesEv) return set_error(GOO_ERR_ARG, "device %d", ctx->device);
+  if (!configured[ctx->device]) {
+    // room for the largest column count, so one setting serves every model on this device
+    GOO_CUDA_TRY(cudaFuncSetAttribute(sop_event2_kernel<K, L, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)((size_t)kEventStages * kMaxObs * TE * sizeof(float))));
+    configured[ctx->device] = true;
+  }
+  int bps = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, sop_event2_kernel<K, L, GRAD>, kBlock, smem) != cudaSuccess ||
+      bps < 1) {
+    cudaGetLastError();
+    bps = 1;
+  }
+  const int64_t tiles = (end + TE - 1) / TE - begin / TE;
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)ctx->num_sms * bps));
+  constexpr int NS = EventLanes<float, K, L, GRAD>::NS;
+  GOO_TRY(ensure_partials(ctx, (size_t)nb * NS));
+  Cols<float> cols{};
+  for (int c = 0; c < kMaxObs; ++c) cols.c[c] = ds->d32[c < ds->ncols ? c : 0];
+  {
+    // programmatic dependent launch: the kernel's blocks start (and put their first column
+    // tiles in flight) while the normalisation kernel before it finishes
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb);
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    LaunchScope ls(ctx, GRAD ? "sop_nll_grad_f32" : "sop_nll_f32");
+    GOO_CUDA_TRY(cudaLaunchKernelEx(&cfg, sop_event2_kernel<K, L, GRAD>, (const ModelDev*)m->dev,
+                                    make_evconst<float, K, L>(*m->stage), cols, begin, end, ctx->scratch.partials,
+                                    ctx->scratch.counters, ctx->scratch.result, out_mode));
   }
   GOO_CUDA_TRY(cudaGetLastError());
   return GOO_OK;
@@ -1126,6 +1689,12 @@ static int launch_event_T(goo_model* m, const goo_dataset* ds, int64_t begin, in
 
 template <typename T, bool GRAD>
 static int launch_event_sel(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int out_mode) {
+  if constexpr (sizeof(T) == 4) {
+    // packed pairs, except the largest shape with gradient lanes (its pair accumulators do
+    // not fit in registers)
+    if (m->host.nK <= 2 && m->max_leaf <= 3) return launch_event2<2, 3, GRAD>(m, ds, begin, end, out_mode);
+    if constexpr (!GRAD) return launch_event2<4, 4, GRAD>(m, ds, begin, end, out_mode);
+  }
   if (m->host.nK <= 2 && m->max_leaf <= 3) return launch_event_T<T, 2, 3, GRAD>(m, ds, begin, end, out_mode);
   return launch_event_T<T, 4, 4, GRAD>(m, ds, begin, end, out_mode);
 }
@@ -1156,7 +1725,8 @@ static int launch_logf_T(goo_model* m, const goo_dataset* ds, double* logf_dev) 
   const int nb = grid_blocks(ctx, ds->n, 4);
   {
     LaunchScope ls(ctx, "sop_logf");
-    sop_logf_kernel<T, K, L><<<nb, kBlock, 0, ctx->stream>>>(m->dev, cols, ds->n, logf_dev);
+    sop_logf_kernel<T, K, L><<<nb, kBlock, 0, ctx->stream>>>(m->dev, make_evconst<T, K, L>(*m->stage), cols, ds->n,
+                                                             logf_dev);
   }
   GOO_CUDA_TRY(cudaGetLastError());
   return GOO_OK;
@@ -1319,6 +1889,7 @@ static int static_plan(const goo_node* nodes, int n_nodes, int n_params, int n_o
     return set_error(GOO_ERR_UNSUPPORTED, "goo_nll_grad_static: only GOO_NORM_ANALYTIC and GOO_NORM_GRID");
   }
   h.norm_kind = norm->kind;
+  h.grid_separable = norm->kind == GOO_NORM_GRID ? grid_separable(h) : 0;
   return GOO_OK;
 }
 
@@ -1330,7 +1901,11 @@ static int static_launch(const ModelDev& h, int max_leaf, unsigned char* base, i
   double* result = (double*)(base + kStOffResult);
   float2* partials = (float2*)(base + kStOffPartials);
   (void)precision;
-  if (h.norm_kind == GOO_NORM_GRID) {
+  if (h.norm_kind == GOO_NORM_GRID && h.grid_separable) {
+    static_assert((size_t)kMaxComp * kMaxLeaf * 4 * sizeof(double) <= kStPartialsCap * sizeof(float2),
+                  "static scratch too small for the separable grid sums");
+    grid_sep_kernel<T><<<dim3((unsigned)max_leaf, h.nK), kBlock, 0, st>>>(md, (double*)partials, counters);
+  } else if (h.norm_kind == GOO_NORM_GRID) {
     constexpr int NSg = 1 + 3 * L;
     int bps = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, grid_kernel<T, L>, kBlock, 0) != cudaSuccess || bps < 1) {
@@ -1366,8 +1941,8 @@ static int static_launch(const ModelDev& h, int max_leaf, unsigned char* base, i
   if (nb < 1) nb = 1;
   Cols<T> cols{};
   for (int c = 0; c < kMaxObs; ++c) cols.c[c] = (const T*)cols_dev[c < h.n_obs ? c : 0];
-  sop_event_kernel<T, K, L, true><<<(unsigned)nb, kBlock, 0, st>>>(md, cols, 0, n, partials, counters, result, 0);
-  (void)max_leaf;
+  sop_event_kernel<T, K, L, true><<<(unsigned)nb, kBlock, 0, st>>>(md, make_evconst<T, K, L>(h), cols, 0, n, partials,
+                                                                   counters, result, 0);
   GOO_CUDA_TRY(cudaGetLastError());
   return GOO_OK;
 }

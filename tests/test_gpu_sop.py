@@ -166,6 +166,24 @@ def test_nested_tree_matches_oracle(goo, ctx):
     _check(goo, ctx, spec_g, cols, theta, "f64")
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_grid_with_shared_observable(goo, ctx, precision):
+    # two leaves of one product on the same observable: the grid sum does not factorise, so
+    # this takes the dense grid kernel (the C2 model takes the separable one)
+    spec = dict(
+        name="shared", observables=[("x", 0.0, 4.0), ("y", -1.0, 1.0)],
+        params=[("a", 1.5, False, 0), ("b", 0.6, False, 0), ("l", -0.4, False, 0), ("f", 0.4, False, 0),
+                ("l2", 0.3, False, 0), ("c", 0.2, False, 0), ("d", 0.1, False, 0)],
+        pdf=("add", ["f"], [
+            ("prod", [("gauss", "x", "a", "b"), ("expo", "x", "l")]),
+            ("prod", [("expo", "x", "l2"), ("poly2", "y", "c", "d")])]),
+        norm=("grid", [256, 64]))
+    rng = np.random.default_rng(2)
+    cols = {"x": rng.uniform(0, 4, 30000), "y": rng.uniform(-1, 1, 30000)}
+    theta = np.array([p[1] for p in spec["params"]]) * 1.02
+    _check(goo, ctx, spec, cols, theta, precision)
+
+
 def test_borrowed_torch_columns(goo, ctx):
     import torch
     spec = synth.c1_spec()
