@@ -254,26 +254,36 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def timed(precision, grad, steps, warmup):
+        # the step time is taken without the library's per-kernel events (they would sit
+        # between the normalisation and event kernels and serialise them); a second pass of
+        # the same steps with per-kernel events gives each kernel's launch duration
         for _ in range(warmup):
             step(precision, grad)
         barrier()
-        ms = []
         launches0 = ctx.launches
+
+        def run(n):
+            ms = []
+            for _ in range(n):
+                flush.zero_()                       # L2 flush between timed steps (not timed)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step(precision, grad)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            return ms
+
+        ms = run(steps)
+        barrier()
+        launches = ctx.launches - launches0
         ctx.kernel_times(reset=True)
         ctx.timing(True)
-        for _ in range(steps):
-            flush.zero_()                       # L2 flush between timed steps (not timed)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step(precision, grad)
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
+        run(max(3, min(steps, 10)))
         barrier()
         ctx.timing(False)
         kt = ctx.kernel_times(reset=True)
-        launches = ctx.launches - launches0
         total = sum(ms)
         if pg is not None:
             t = torch.tensor([total], dtype=torch.float64, device="cuda")

@@ -183,6 +183,51 @@ struct Kahan {
 };
 
 // ---------------------------------------------------------------------------------------
+// Packed FP32 arithmetic of sm_100-class GPUs: add / sub / mul / fma on .f32x2 register
+// pairs (each lane rounded as the scalar instruction), and the hardware base-2 exponential,
+// logarithm and reciprocal (PTX .approx forms, denormals flushed).
+// ---------------------------------------------------------------------------------------
+namespace pk {
+__device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<const unsigned long long*>(&a)), "l"(*reinterpret_cast<const unsigned long long*>(&b)));
+  return *reinterpret_cast<const float2*>(&d);
+}
+// hardware base-2 exponential / logarithm / reciprocal (PTX .approx forms, denormals flushed)
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+constexpr float kLog2e = 1.4426950408889634f;  // 1 / ln 2
+constexpr float kLn2 = 0.6931471805599453f;
+__device__ __forceinline__ float2 exp(float2 x) {  // e^x per lane
+  const float2 t = mul(x, splat(kLog2e));
+  return make_float2(ex2(t.x), ex2(t.y));
+}
+__device__ __forceinline__ float2 log(float2 x) {  // natural log per lane
+  return mul(make_float2(lg2(x.x), lg2(x.y)), splat(kLn2));
+}
+__device__ __forceinline__ float2 rcp(float2 x) { return make_float2(rcp(x.x), rcp(x.y)); }
+}  // namespace pk
+
+// ---------------------------------------------------------------------------------------
 // Bulk asynchronous copies global -> shared (the non-tensor TMA form, cp.async.bulk) that
 // signal an mbarrier with their byte count, and waits on that barrier with a time limit.
 // A wait that exceeds kWaitCycles SM clocks (about one second) gives up and returns false;
@@ -296,9 +341,19 @@ __device__ __forceinline__ bool last_block_reduce(const float2* partials, int ns
   const int s = threadIdx.x / per, g = threadIdx.x % per;
   ddf acc = {0.f, 0.f};
   if (s < nslots) {
-    for (int b = g; b < nblocks; b += per) {
-      float2 p = __ldcg(partials + (size_t)b * nslots + s);
-      acc = dd_add(acc, {p.x, p.y});
+    // eight independent loads in flight before they are added in block order
+    constexpr int U = 8;
+    int b = g;
+    for (; b + (U - 1) * per < nblocks; b += U * per) {
+      float2 q[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) q[u] = __ldcg(partials + (size_t)(b + u * per) * nslots + s);
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc = dd_add(acc, {q[u].x, q[u].y});
+    }
+    for (; b < nblocks; b += per) {
+      const float2 q = __ldcg(partials + (size_t)b * nslots + s);
+      acc = dd_add(acc, {q.x, q.y});
     }
   }
   const int wper = per < 32 ? per : 32;

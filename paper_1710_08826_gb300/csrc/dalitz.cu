@@ -28,6 +28,7 @@
 // FP32 path: amplitudes and S in FP32, Kahan per thread, double-float across threads; the
 // final FP64 combination takes c at the FP32-rounded values the kernel used, so the NLL is
 // the exact likelihood at those coefficients.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <type_traits>
@@ -116,6 +117,151 @@ struct CohLanes {
   static constexpr int NS = GRAD ? 1 + 2 * (KB + 1) : 1;
 };
 
+// Per-thread accumulators of the coherent kernels.
+template <typename T, int KB>
+struct CohAcc {
+  Kahan lf32;
+  double lf64 = 0.0;
+  T gre[KB + 1], gim[KB + 1];
+  unsigned bad = 0;
+};
+
+// One event: S = sum_k c_k A_k, log |S|^2 and the lanes Re / Im of A_k conj(S) / |S|^2.
+template <typename T, int KB, bool GRAD>
+__device__ __forceinline__ void coh_event(const T (&cr)[KB + 1], const T (&ci)[KB + 1], const T (&ar)[KB + 1],
+                                          const T (&ai)[KB + 1], CohAcc<T, KB>& acc) {
+  constexpr int KA = KB + 1;
+  T sr = T(0), si = T(0);
+#pragma unroll
+  for (int k = 0; k < KA; ++k) {
+    sr += cr[k] * ar[k] - ci[k] * ai[k];
+    si += cr[k] * ai[k] + ci[k] * ar[k];
+  }
+  const T s2 = sr * sr + si * si;
+  if (s2 > T(0)) {
+    if constexpr (sizeof(T) == 4) {
+      acc.lf32.add(__logf(s2));
+    } else {
+      acc.lf64 += log(s2);
+    }
+    if constexpr (GRAD) {
+      const T inv = T(1) / s2;
+      const T tr = sr * inv, ti = -si * inv;  // conj(S) / |S|^2
+#pragma unroll
+      for (int k = 0; k < KA; ++k) {
+        acc.gre[k] += ar[k] * tr - ai[k] * ti;
+        acc.gim[k] += ar[k] * ti + ai[k] * tr;
+      }
+    }
+  } else {
+    acc.bad++;
+  }
+}
+
+// Block and last-block reductions of the lanes, then the FP64 combination with the Gram
+// matrix at the coefficients the kernel used.
+template <typename T, int KB, bool GRAD>
+__device__ __forceinline__ void coh_finish(const CohArgs<T>& a, CohAcc<T, KB>& acc, int64_t begin, int64_t end,
+                                           const double* __restrict__ gram, float2* partials, unsigned* counters,
+                                           double* result, int out_mode, ddf* s_red, unsigned* s_bad) {
+  constexpr int NS = CohLanes<T, KB, GRAD>::NS;
+  constexpr int KA = KB + 1;
+  ddf v[NS];
+  v[0] = (sizeof(T) == 4) ? acc.lf32.value() : dd_from_double(acc.lf64);
+  if constexpr (GRAD) {
+#pragma unroll
+    for (int k = 0; k < KA; ++k) {
+      v[1 + 2 * k] = (sizeof(T) == 4) ? ddf{(float)acc.gre[k], 0.f} : dd_from_double((double)acc.gre[k]);
+      v[2 + 2 * k] = (sizeof(T) == 4) ? ddf{(float)acc.gim[k], 0.f} : dd_from_double((double)acc.gim[k]);
+    }
+  }
+  unsigned bad = acc.bad;
+  for (int m = 16; m > 0; m >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, m);
+  if ((threadIdx.x & 31) == 0) s_bad[threadIdx.x >> 5] = bad;
+  block_reduce_to_partials<NS>(v, NS, partials, s_red);
+  if (threadIdx.x == 0) {
+    unsigned b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_bad[w];
+    if (b) atomicAdd(counters + 1, b);
+  }
+  __shared__ double s_out[NS];
+  if (!last_block_reduce(partials, NS, gridDim.x, counters, s_out, s_red)) return;
+  // FP64 combination in parallel: the Gram matrix is staged in shared memory, lane k of
+  // warp 0 forms v_k = sum_l G_kl conj(c_l), N = sum_k Re(c_k v_k) by a fixed xor tree, and
+  // one thread scatters the per-coefficient gradients (parameters may be shared).
+  __shared__ double s_G[2 * kMaxAmp * kMaxAmp];
+  __shared__ double s_gre[kMaxAmp], s_gim[kMaxAmp];
+  __shared__ double s_N;
+  const int K = a.K;
+  for (int t = threadIdx.x; t < 2 * K * K; t += blockDim.x) s_G[t] = gram[t];
+  __syncthreads();
+  const double nev = (double)(end - begin);
+  if (threadIdx.x < 32) {
+    const int k = threadIdx.x;
+    double vr = 0.0, vi = 0.0, Nk = 0.0;
+    if (k < K) {
+      for (int l = 0; l < K; ++l) {
+        const double gr = s_G[2 * (k * K + l)], gi = s_G[2 * (k * K + l) + 1];
+        const double clr = (double)a.cr[l], cli = (double)a.ci[l];
+        vr += gr * clr + gi * cli;  // v_k = sum_l G_kl conj(c_l)
+        vi += gi * clr - gr * cli;
+      }
+      Nk = (double)a.cr[k] * vr - (double)a.ci[k] * vi;  // Re(c_k v_k)
+    }
+    double N = Nk;
+    for (int m = 16; m > 0; m >>= 1) N += __shfl_xor_sync(0xffffffffu, N, m);
+    if (k < K && GRAD) {
+      const int slot = (k < a.nbw) ? k : KB;  // NR lives in the last slot
+      s_gre[k] = -2.0 * s_out[1 + 2 * slot] + nev * 2.0 * vr / N;
+      s_gim[k] = 2.0 * s_out[2 + 2 * slot] - nev * 2.0 * vi / N;
+    }
+    if (k == 0) s_N = N;
+  }
+  __shared__ double s_g[kMaxParams];
+  const int P = a.n_params;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) s_g[p] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0 && GRAD)
+    for (int k = 0; k < K; ++k) {
+      s_g[a.par_re[k]] += s_gre[k];
+      s_g[a.par_im[k]] += s_gim[k];
+    }
+  __syncthreads();
+  const int off = out_mode == 0 ? 2 : 3;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) result[off + p] = s_g[p];
+  if (threadIdx.x == 0) {
+    const unsigned nbad = atomicAdd(counters + 1, 0u);
+    counters[1] = 0u;
+    const unsigned status = atomicAdd(counters + kStatusWord, 0u);
+    counters[kStatusWord] = 0u;
+    const double N = s_N;
+    const double nll = -s_out[0] + nev * log(N);
+    // a device wait that gave up is reported as a negative event count
+    const double nb = status ? -1.0 : (double)nbad;
+    result[0] = nll;
+    if (out_mode == 0) {
+      result[1] = nb;
+      result[2 + P] = N;
+    } else {
+      result[1] = 0.0;
+      result[2] = nb;
+    }
+  }
+}
+
+template <typename T, int KB>
+__device__ __forceinline__ void coh_coeffs(const CohArgs<T>& a, T (&cr)[KB + 1], T (&ci)[KB + 1]) {
+  const int nbw = a.nbw;
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    cr[k] = k < nbw ? a.cr[k] : T(0);
+    ci[k] = k < nbw ? a.ci[k] : T(0);
+  }
+  cr[KB] = a.has_nr ? a.cr[nbw] : T(0);
+  ci[KB] = a.has_nr ? a.ci[nbw] : T(0);
+}
+
+// Direct form (one event per thread per grid-stride step); the FP64 path uses it.
 template <typename T, int KB, bool GRAD>
 __global__ void __launch_bounds__(kBlock, 2) coh_nll_kernel(const __grid_constant__ CohArgs<T> a, const void* cache_v,
                                                             int64_t begin, int64_t end, const double* __restrict__ gram,
@@ -129,19 +275,10 @@ __global__ void __launch_bounds__(kBlock, 2) coh_nll_kernel(const __grid_constan
   const Vec* cache = (const Vec*)cache_v;
   const int nbw = a.nbw;
   T cr[KA], ci[KA];
+  coh_coeffs<T, KB>(a, cr, ci);
+  CohAcc<T, KB> acc;
 #pragma unroll
-  for (int k = 0; k < KB; ++k) {
-    cr[k] = k < nbw ? a.cr[k] : T(0);
-    ci[k] = k < nbw ? a.ci[k] : T(0);
-  }
-  cr[KB] = a.has_nr ? a.cr[nbw] : T(0);
-  ci[KB] = a.has_nr ? a.ci[nbw] : T(0);
-  Kahan acc32;
-  double acc64 = 0.0;
-  T gre[KA], gim[KA];
-#pragma unroll
-  for (int k = 0; k < KA; ++k) gre[k] = gim[k] = T(0);
-  unsigned bad = 0;
+  for (int k = 0; k < KA; ++k) acc.gre[k] = acc.gim[k] = T(0);
   const int64_t n = a.n_total;
   for (int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -149,99 +286,124 @@ __global__ void __launch_bounds__(kBlock, 2) coh_nll_kernel(const __grid_constan
     load_amps<KB>(cache, n, i, nbw, ar, ai);
     ar[KB] = T(1);
     ai[KB] = T(0);
-    T sr = T(0), si = T(0);
+    coh_event<T, KB, GRAD>(cr, ci, ar, ai, acc);
+  }
+  coh_finish<T, KB, GRAD>(a, acc, begin, end, gram, partials, counters, result, out_mode, s_red, s_bad);
+}
+
+// FP32 form with the amplitude-cache tiles staged in shared memory.  A tile holds
+// kCohTile events of every float4 plane (aligned to multiples of kCohTile); one thread
+// issues a bulk copy per plane kCohStages tiles ahead, and block b takes tiles
+// tb0 + b, tb0 + b + gridDim.x, ...  Ragged first / last tiles are read from global memory.
+// Dynamic shared memory: kCohStages * n_planes * kCohTile float4.
+constexpr int kCohTile = 512;
+constexpr int kCohStages = 3;
+
+template <int KB, bool GRAD>
+__global__ void __launch_bounds__(kBlock, 2) coh_nll_staged_kernel(const __grid_constant__ CohArgs<float> a,
+                                                                   const float4* __restrict__ cache, int64_t begin,
+                                                                   int64_t end, const double* __restrict__ gram,
+                                                                   float2* partials, unsigned* counters, double* result,
+                                                                   int out_mode) {
+  constexpr int NS = CohLanes<float, KB, GRAD>::NS;
+  constexpr int KA = KB + 1;
+  constexpr int TE = kCohTile;
+  constexpr int NST = kCohStages;
+  __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
+  __shared__ unsigned s_bad[kBlock / 32];
+  __shared__ __align__(8) uint64_t s_bar[NST];
+  extern __shared__ __align__(128) float4 s_amp[];  // [NST][planes][TE]
+  const int nbw = a.nbw;
+  const int planes = (nbw + 1) / 2;
+  const int64_t n = a.n_total;
+  const int64_t tb0 = begin / TE, tb1 = (end + TE - 1) / TE;
+  auto tile_of = [&](int j) { return tb0 + blockIdx.x + (int64_t)j * gridDim.x; };
+  auto full = [&](int64_t t) { return t * TE >= begin && (t + 1) * TE <= end; };
+  auto buf = [&](int st, int p) { return s_amp + ((size_t)st * planes + p) * TE; };
+  auto issue = [&](int j) {
+    const int64_t t = tile_of(j);
+    if (t >= tb1) return;
+    uint64_t* bar = &s_bar[j % NST];
+    if (full(t)) {
+      mbar_arrive_expect_tx(bar, (unsigned)(planes * TE * sizeof(float4)));
+      for (int p = 0; p < planes; ++p) bulk_load(buf(j % NST, p), cache + (int64_t)p * n + t * TE, TE * sizeof(float4), bar);
+    } else {
+      mbar_arrive(bar);
+    }
+  };
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < NST; ++st) mbar_init(&s_bar[st], 1);
+    mbar_init_fence();
+    for (int j = 0; j < NST; ++j) issue(j);
+  }
+  float2 cre[KA], cim[KA];
+  {
+    float cr[KA], ci[KA];
+    coh_coeffs<float, KB>(a, cr, ci);
 #pragma unroll
     for (int k = 0; k < KA; ++k) {
-      sr += cr[k] * ar[k] - ci[k] * ai[k];
-      si += cr[k] * ai[k] + ci[k] * ar[k];
+      cre[k] = pk::splat(cr[k]);
+      cim[k] = pk::splat(ci[k]);
     }
-    const T s2 = sr * sr + si * si;
-    if (s2 > T(0)) {
-      if constexpr (sizeof(T) == 4) {
-        acc32.add(__logf(s2));
-      } else {
-        acc64 += log(s2);
-      }
-      if constexpr (GRAD) {
-        const T inv = T(1) / s2;
-        const T tr = sr * inv, ti = -si * inv;  // conj(S) / |S|^2
+  }
+  Kahan lf;
+  float2 G1[KA], G2[KA];
 #pragma unroll
-        for (int k = 0; k < KA; ++k) {
-          gre[k] += ar[k] * tr - ai[k] * ti;
-          gim[k] += ar[k] * ti + ai[k] * tr;
+  for (int k = 0; k < KA; ++k) G1[k] = G2[k] = pk::splat(0.f);
+  unsigned bad = 0;
+  __syncthreads();  // barriers initialised before any thread waits on them
+  int j = 0;
+  bool failed = false;
+  for (; tile_of(j) < tb1; ++j) {
+    const int64_t t = tile_of(j);
+    const int st = j % NST;
+    const bool ok_wait = mbar_wait(&s_bar[st], (unsigned)(j / NST) & 1u);
+    if (ok_wait) {
+      const float4* sb = buf(st, 0);  // plane p of the tile at sb + p * TE
+      const bool staged = full(t);
+#pragma unroll 1
+      for (int e = threadIdx.x; e < TE; e += blockDim.x) {
+        const int64_t i = t * TE + e;
+        if (!staged && (i < begin || i >= end)) continue;
+        float2 amp[KA];
+#pragma unroll
+        for (int p = 0; p < (KB + 1) / 2; ++p) {
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (p < planes) v = staged ? sb[p * TE + e] : __ldg(cache + (int64_t)p * n + i);
+          amp[2 * p] = make_float2(v.x, v.y);
+          if (2 * p + 1 < KB) amp[2 * p + 1] = make_float2(v.z, v.w);
         }
+        amp[KB] = make_float2(1.f, 0.f);
+        coh_event_pk<KA, GRAD>(cre, cim, amp, lf, G1, G2, bad);
       }
-    } else {
-      bad++;
+    }
+    if (__syncthreads_or(!ok_wait)) {
+      failed = true;
+      break;
+    }
+    if (threadIdx.x == 0) {
+      fence_proxy_async();
+      issue(j + NST);
     }
   }
-  ddf v[NS];
-  v[0] = (sizeof(T) == 4) ? acc32.value() : dd_from_double(acc64);
-  if constexpr (GRAD) {
+  if (failed) {
+    // a copy did not arrive in time: record it, then wait (again bounded) for this block's
+    // copies still in flight before the block's shared memory is released
+    if (threadIdx.x == 0) {
+      atomicOr(counters + kStatusWord, 1u);
+      for (int jj = j; jj < j + NST && tile_of(jj) < tb1; ++jj) mbar_wait(&s_bar[jj % NST], (unsigned)(jj / NST) & 1u);
+    }
+    __syncthreads();
+  }
+  CohAcc<float, KB> acc;
+  acc.lf32 = lf;
+  acc.bad = bad;
 #pragma unroll
-    for (int k = 0; k < KA; ++k) {
-      v[1 + 2 * k] = (sizeof(T) == 4) ? ddf{(float)gre[k], 0.f} : dd_from_double((double)gre[k]);
-      v[2 + 2 * k] = (sizeof(T) == 4) ? ddf{(float)gim[k], 0.f} : dd_from_double((double)gim[k]);
-    }
+  for (int k = 0; k < KA; ++k) {
+    acc.gre[k] = G1[k].x - G2[k].y;
+    acc.gim[k] = G1[k].y + G2[k].x;
   }
-  for (int m = 16; m > 0; m >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, m);
-  if ((threadIdx.x & 31) == 0) s_bad[threadIdx.x >> 5] = bad;
-  block_reduce_to_partials<NS>(v, NS, partials, s_red);
-  if (threadIdx.x == 0) {
-    unsigned b = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_bad[w];
-    if (b) atomicAdd(counters + 1, b);
-  }
-  __shared__ double s_out[NS];
-  if (!last_block_reduce(partials, NS, gridDim.x, counters, s_out, s_red)) return;
-  if (threadIdx.x == 0) {
-    const unsigned nbad = atomicAdd(counters + 1, 0u);
-    counters[1] = 0u;
-    // FP64 combination at the coefficients the kernel used
-    const int K = a.K;
-    double c_re[kMaxAmp], c_im[kMaxAmp];
-    for (int k = 0; k < K; ++k) {
-      c_re[k] = (double)a.cr[k];
-      c_im[k] = (double)a.ci[k];
-    }
-    double N = 0.0;
-    double vr[kMaxAmp], vi[kMaxAmp];
-    for (int k = 0; k < K; ++k) {
-      double sr = 0.0, si = 0.0;  // v_k = sum_l G_kl conj(c_l)
-      for (int l = 0; l < K; ++l) {
-        const double gr = gram[2 * (k * K + l)], gi = gram[2 * (k * K + l) + 1];
-        sr += gr * c_re[l] + gi * c_im[l];
-        si += gi * c_re[l] - gr * c_im[l];
-      }
-      vr[k] = sr;
-      vi[k] = si;
-      N += c_re[k] * sr - c_im[k] * si;  // Re(c_k v_k)
-    }
-    const double nev = (double)(end - begin);
-    const double nll = -s_out[0] + nev * log(N);
-    double g[kMaxParams];
-    for (int p = 0; p < kMaxParams; ++p) g[p] = 0.0;
-    if (GRAD) {
-      for (int k = 0; k < K; ++k) {
-        const int slot = (k < a.nbw) ? k : KB;  // NR lives in the last slot
-        const double lre = s_out[1 + 2 * slot], lim = s_out[2 + 2 * slot];
-        g[a.par_re[k]] += -2.0 * lre + nev * 2.0 * vr[k] / N;
-        g[a.par_im[k]] += 2.0 * lim - nev * 2.0 * vi[k] / N;
-      }
-    }
-    const int P = a.n_params;
-    if (out_mode == 0) {
-      result[0] = nll;
-      result[1] = (double)nbad;
-      for (int p = 0; p < P; ++p) result[2 + p] = g[p];
-      result[2 + P] = N;
-    } else {
-      result[0] = nll;
-      result[1] = 0.0;
-      result[2] = (double)nbad;
-      for (int p = 0; p < P; ++p) result[3 + p] = g[p];
-    }
-  }
+  coh_finish<float, KB, GRAD>(a, acc, begin, end, gram, partials, counters, result, out_mode, s_red, s_bad);
 }
 
 // per-event log f = log|S|^2 - log N
@@ -563,9 +725,49 @@ static void fill_args(const DalitzModel& d, const double* theta, int n_params, i
   }
 }
 
+constexpr int kMaxDevicesCoh = 64;
+
+template <int KB, bool GRAD>
+static int launch_coh_staged(goo_model* m, const void* cache, const goo_dataset* ds, int64_t begin, int64_t end,
+                             const double* theta, int out_mode, int pi) {
+  DalitzModel& d = *m->dalitz;
+  goo_ctx* ctx = m->ctx;
+  const int planes = (d.nbw + 1) / 2;
+  const size_t smem = (size_t)kCohStages * planes * kCohTile * sizeof(float4);
+  static bool configured[kMaxDevicesCoh] = {};
+  if (ctx->device < 0 || ctx->device >= kMaxDevicesCoh) return set_error(GOO_ERR_ARG, "device %d", ctx->device);
+  if (!configured[ctx->device]) {
+    GOO_CUDA_TRY(cudaFuncSetAttribute(coh_nll_staged_kernel<KB, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)((size_t)kCohStages * ((KB + 1) / 2) * kCohTile * sizeof(float4))));
+    configured[ctx->device] = true;
+  }
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, coh_nll_staged_kernel<KB, GRAD>, kBlock, smem) != cudaSuccess ||
+      occ < 1) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  const int64_t tiles = (end + kCohTile - 1) / kCohTile - begin / kCohTile;
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)ctx->num_sms * occ));
+  constexpr int NS = CohLanes<float, KB, GRAD>::NS;
+  GOO_TRY(ensure_partials(ctx, (size_t)nb * NS));
+  CohArgs<float> a;
+  fill_args<float>(d, theta, m->n_params, ds->n, a);
+  {
+    LaunchScope ls(ctx, GRAD ? "coh_nll_grad_f32" : "coh_nll_f32");
+    coh_nll_staged_kernel<KB, GRAD><<<nb, kBlock, smem, ctx->stream>>>(a, (const float4*)cache, begin, end,
+                                                                       d.gram_dev[pi], ctx->scratch.partials,
+                                                                       ctx->scratch.counters, ctx->scratch.result,
+                                                                       out_mode);
+  }
+  GOO_CUDA_TRY(cudaGetLastError());
+  return GOO_OK;
+}
+
 template <typename T, int KB, bool GRAD>
 static int launch_coh(goo_model* m, const void* cache, const goo_dataset* ds, int64_t begin, int64_t end,
                       const double* theta, int out_mode, int pi) {
+  if constexpr (sizeof(T) == 4) return launch_coh_staged<KB, GRAD>(m, cache, ds, begin, end, theta, out_mode, pi);
   DalitzModel& d = *m->dalitz;
   goo_ctx* ctx = m->ctx;
   static int occ = 0;

@@ -137,4 +137,37 @@ __device__ __forceinline__ void load_amps(const double2* __restrict__ cache, int
   }
 }
 
+// One event of a coherent sum in packed FP32 form.  With a_k = (Re A_k, Im A_k) held as a
+// register pair and cre_k = (Re c_k, Re c_k), cim_k = (Im c_k, Im c_k):
+//   P = sum_k Re c_k a_k,  Q = sum_k Im c_k a_k,  S = (P.x - Q.y) + i (P.y + Q.x),
+// and the gradient lanes A_k conj(S) / |S|^2 = (t_r + i t_i) A_k are accumulated as
+//   G1_k += t_r a_k,  G2_k += t_i a_k   (Re = G1.x - G2.y, Im = G1.y + G2.x at the end),
+// so each amplitude costs two packed fma for S and two for the gradient.
+template <int KA, bool GRAD>
+__device__ __forceinline__ void coh_event_pk(const float2 (&cre)[KA], const float2 (&cim)[KA], const float2 (&a)[KA],
+                                             Kahan& lf, float2 (&G1)[KA], float2 (&G2)[KA], unsigned& bad) {
+  float2 P = pk::mul(cre[0], a[0]), Q = pk::mul(cim[0], a[0]);
+#pragma unroll
+  for (int k = 1; k < KA; ++k) {
+    P = pk::fma(cre[k], a[k], P);
+    Q = pk::fma(cim[k], a[k], Q);
+  }
+  const float sr = P.x - Q.y, si = P.y + Q.x;
+  const float s2 = fmaf(sr, sr, si * si);
+  if (s2 > 0.f) {
+    lf.add(pk::kLn2 * pk::lg2(s2));
+    if constexpr (GRAD) {
+      const float inv = pk::rcp(s2);
+      const float2 tr = pk::splat(sr * inv), ti = pk::splat(-si * inv);  // conj(S) / |S|^2
+#pragma unroll
+      for (int k = 0; k < KA; ++k) {
+        G1[k] = pk::fma(tr, a[k], G1[k]);
+        G2[k] = pk::fma(ti, a[k], G2[k]);
+      }
+    }
+  } else {
+    bad++;
+  }
+}
+
 }  // namespace goo

@@ -289,58 +289,130 @@ struct SrvModel {   // shared by every fit of a batch
   int nbw, has_ref;
 };
 
-// tiles[t] = (fit, tile index within the fit); fit_tiles[fit] = (number of tiles, first tile)
+// tiles[t] = (fit, tile index within the fit); fit_tiles[fit] = (number of tiles, first tile).
+// A block takes work items t = blockIdx.x, + gridDim.x, ...; each item is consumed in
+// sub-tiles of kSrvSub events whose amplitude planes are staged in shared memory by bulk
+// copies (every event is one 16-byte float4 per plane, so any sub-range is a legal copy),
+// kSrvStages sub-tiles ahead of the consumers.  Dynamic shared memory:
+// kSrvStages * (kSrvKB / 2) * kSrvSub float4.  status[0] is set when a copy wait gave up.
+constexpr int kSrvSub = 512;
+constexpr int kSrvStages = 3;
+constexpr size_t kSrvSmem = (size_t)kSrvStages * (kSrvKB / 2) * kSrvSub * sizeof(float4);
+
 __global__ void __launch_bounds__(kBlock, 2) srv_nll_kernel(const SrvEval* __restrict__ ev, const int2* __restrict__ tiles,
                                                            const int2* __restrict__ fit_tiles, int ntiles,
                                                            int tile_events, const SrvModel* __restrict__ sm,
                                                            float2* tile_partials, unsigned* fit_ticket,
-                                                           SrvResult* results) {
+                                                           SrvResult* results, unsigned* status) {
   __shared__ ddf s_red[(kBlock / 32) * kSrvLanes > kBlock ? (kBlock / 32) * kSrvLanes : kBlock];
   __shared__ unsigned s_bad[kBlock / 32];
   __shared__ bool s_last;
   __shared__ double s_fin[kSrvLanes];
+  __shared__ __align__(8) uint64_t s_bar[kSrvStages];
+  extern __shared__ __align__(128) float4 s_amp[];  // [kSrvStages][kSrvKB / 2][kSrvSub]
+  constexpr int NST = kSrvStages, TE = kSrvSub, NP = kSrvKB / 2;
+  __shared__ double s_G[kSrvKA * kSrvKA * 2];
+  for (int q = threadIdx.x; q < kSrvKA * kSrvKA * 2; q += blockDim.x) s_G[q] = sm->G[q];
   const int nbw = sm->nbw;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int fit = tiles[t].x, tin = tiles[t].y;
+  const int planes = (nbw + 1) / 2;
+  // the event range [b0, b1) of work item t
+  auto item_range = [&](int t, int64_t& b0, int64_t& b1) {
+    const SrvEval& e = ev[tiles[t].x];
+    b0 = e.begin + (int64_t)tiles[t].y * tile_events;
+    b1 = min(e.begin + e.n, b0 + tile_events);
+  };
+  auto nsub_of = [&](int t) {
+    int64_t b0, b1;
+    item_range(t, b0, b1);
+    return b1 > b0 ? (int)((b1 - b0 + TE - 1) / TE) : 1;  // an empty item still takes one (empty) step
+  };
+  // producer cursor (thread 0): work item pt, sub-tile ps, job number pj
+  int pt = blockIdx.x, ps = 0, pj = 0;
+  auto issue_next = [&]() {
+    if (pt >= ntiles) return;
+    int64_t b0, b1;
+    item_range(pt, b0, b1);
+    const SrvEval& e = ev[tiles[pt].x];
+    const int64_t lo = b0 + (int64_t)ps * TE, hi = min(b1, lo + TE);
+    uint64_t* bar = &s_bar[pj % NST];
+    if (hi > lo) {
+      mbar_arrive_expect_tx(bar, (unsigned)(planes * (hi - lo) * sizeof(float4)));
+      for (int p = 0; p < planes; ++p)
+        bulk_load(s_amp + ((size_t)(pj % NST) * NP + p) * TE, e.cache + (int64_t)p * e.plane + lo,
+                  (unsigned)((hi - lo) * sizeof(float4)), bar);
+    } else {
+      mbar_arrive(bar);
+    }
+    ++pj;
+    if (++ps == nsub_of(pt)) {
+      ps = 0;
+      pt += gridDim.x;
+    }
+  };
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < NST; ++st) mbar_init(&s_bar[st], 1);
+    mbar_init_fence();
+    for (int q = 0; q < NST; ++q) issue_next();
+  }
+  __syncthreads();  // barriers initialised before any thread waits on them
+  int j = 0;  // consumer job number
+  bool failed = false;
+  for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+    const int fit = tiles[t].x;
     const SrvEval& e = ev[fit];
     const int2 ft = fit_tiles[fit];
-    const int64_t b0 = e.begin + (int64_t)tin * tile_events;
-    const int64_t b1 = min(e.begin + e.n, b0 + tile_events);
-    float cr[kSrvKA], ci[kSrvKA];
+    int64_t b0, b1;
+    item_range(t, b0, b1);
+    const int nsub = nsub_of(t);
+    float2 cre[kSrvKA], cim[kSrvKA];
 #pragma unroll
     for (int k = 0; k < kSrvKA; ++k) {
-      cr[k] = e.cr[k];
-      ci[k] = e.ci[k];
+      cre[k] = pk::splat(e.cr[k]);
+      cim[k] = pk::splat(e.ci[k]);
     }
     Kahan acc;
+    float2 G1[kSrvKA], G2[kSrvKA];
+#pragma unroll
+    for (int k = 0; k < kSrvKA; ++k) G1[k] = G2[k] = pk::splat(0.f);
+    unsigned bad = 0;
+    for (int sub = 0; sub < nsub; ++sub, ++j) {
+      const int st = j % NST;
+      const bool ok_wait = mbar_wait(&s_bar[st], (unsigned)(j / NST) & 1u);
+      const int64_t lo = b0 + (int64_t)sub * TE;
+      const int64_t left = b1 - lo;
+      const int cnt = left <= 0 ? 0 : (left < TE ? (int)left : TE);
+      if (ok_wait) {
+        const float4* sb = s_amp + (size_t)st * NP * TE;  // plane p at sb + p * TE
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+          float2 amp[kSrvKA];
+#pragma unroll
+          for (int p = 0; p < NP; ++p) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (p < planes) v = sb[p * TE + q];
+            amp[2 * p] = make_float2(v.x, v.y);
+            amp[2 * p + 1] = make_float2(v.z, v.w);
+          }
+          amp[kSrvKB] = make_float2(1.f, 0.f);
+          coh_event_pk<kSrvKA, true>(cre, cim, amp, acc, G1, G2, bad);
+        }
+      }
+      // every thread is done with buffer st (and agrees on whether a wait gave up) before
+      // the buffer is refilled
+      if (__syncthreads_or(!ok_wait)) {
+        failed = true;
+        break;
+      }
+      if (threadIdx.x == 0) {
+        fence_proxy_async();
+        issue_next();
+      }
+    }
+    if (failed) break;
     float gre[kSrvKA], gim[kSrvKA];
 #pragma unroll
-    for (int k = 0; k < kSrvKA; ++k) gre[k] = gim[k] = 0.f;
-    unsigned bad = 0;
-    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-      float ar[kSrvKA], ai[kSrvKA];
-      load_amps<kSrvKB>(e.cache, e.plane, i, nbw, ar, ai);
-      ar[kSrvKB] = 1.f;
-      ai[kSrvKB] = 0.f;
-      float sr = 0.f, si = 0.f;
-#pragma unroll
-      for (int k = 0; k < kSrvKA; ++k) {
-        sr += cr[k] * ar[k] - ci[k] * ai[k];
-        si += cr[k] * ai[k] + ci[k] * ar[k];
-      }
-      const float s2 = sr * sr + si * si;
-      if (s2 > 0.f) {
-        acc.add(__logf(s2));
-        const float inv = 1.f / s2;
-        const float tr = sr * inv, ti = -si * inv;
-#pragma unroll
-        for (int k = 0; k < kSrvKA; ++k) {
-          gre[k] += ar[k] * tr - ai[k] * ti;
-          gim[k] += ar[k] * ti + ai[k] * tr;
-        }
-      } else {
-        bad++;
-      }
+    for (int k = 0; k < kSrvKA; ++k) {
+      gre[k] = G1[k].x - G2[k].y;
+      gim[k] = G1[k].y + G2[k].x;
     }
     ddf v[kSrvLanes];
     v[0] = acc.value();
@@ -379,10 +451,19 @@ __global__ void __launch_bounds__(kBlock, 2) srv_nll_kernel(const SrvEval* __res
     __threadfence();
     // last tile of this fit: reduce its tiles in order
     if (threadIdx.x < kSrvLanes) {
+      // tiles in index order, eight independent loads in flight at a time
       ddf a = {0.f, 0.f};
-      for (int k = 0; k < ft.x; ++k) {
-        const float2 p = __ldcg(tile_partials + (size_t)(ft.y + k) * kSrvLanes + threadIdx.x);
-        a = dd_add(a, {p.x, p.y});
+      int k = 0;
+      for (; k + 8 <= ft.x; k += 8) {
+        float2 q[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) q[u] = __ldcg(tile_partials + (size_t)(ft.y + k + u) * kSrvLanes + threadIdx.x);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a = dd_add(a, {q[u].x, q[u].y});
+      }
+      for (; k < ft.x; ++k) {
+        const float2 q = __ldcg(tile_partials + (size_t)(ft.y + k) * kSrvLanes + threadIdx.x);
+        a = dd_add(a, {q.x, q.y});
       }
       s_fin[threadIdx.x] = dd_to_double(a);
     }
@@ -393,13 +474,13 @@ __global__ void __launch_bounds__(kBlock, 2) srv_nll_kernel(const SrvEval* __res
       double vr = 0.0, vi = 0.0, ckr = 0.0, cki = 0.0;
       const bool live = k < kSrvKA && (k < nbw || (k == kSrvKB && sm->has_ref));
       if (live) {
-        ckr = (double)cr[k];
-        cki = (double)ci[k];
+        ckr = (double)cre[k].x;
+        cki = (double)cim[k].x;
         for (int l = 0; l < kSrvKA; ++l) {
           const bool lv = l < nbw || (l == kSrvKB && sm->has_ref);
           if (!lv) continue;
-          const double gr = sm->G[2 * (k * kSrvKA + l)], gi = sm->G[2 * (k * kSrvKA + l) + 1];
-          const double clr = (double)cr[l], cli = (double)ci[l];
+          const double gr = s_G[2 * (k * kSrvKA + l)], gi = s_G[2 * (k * kSrvKA + l) + 1];
+          const double clr = (double)cre[l].x, cli = (double)cim[l].x;
           vr += gr * clr + gi * cli;
           vi += gi * clr - gr * cli;
         }
@@ -419,6 +500,12 @@ __global__ void __launch_bounds__(kBlock, 2) srv_nll_kernel(const SrvEval* __res
       }
     }
     __syncthreads();
+  }
+  if (failed && threadIdx.x == 0) {
+    // a copy did not arrive in time: record it, then wait (again bounded) for the copies this
+    // block still has in flight before its shared memory is released
+    atomicOr(status, 1u);
+    for (int q = j; q < pj; ++q) mbar_wait(&s_bar[q % NST], (unsigned)(q / NST) & 1u);
   }
 }
 
@@ -1069,9 +1156,11 @@ static int upload_active(goo_server* s) {
 
 static int retire(goo_server* s) {
   goo_ctx* ctx = s->ctx;
-  unsigned nd = 0;
-  GOO_CUDA_TRY(cudaMemcpyAsync(&nd, s->d_done_count, sizeof nd, cudaMemcpyDeviceToHost, ctx->stream));
+  unsigned cs[2] = {0u, 0u};  // done count, status word of the evaluation kernel
+  GOO_CUDA_TRY(cudaMemcpyAsync(cs, s->d_done_count, sizeof cs, cudaMemcpyDeviceToHost, ctx->stream));
   GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (cs[1]) return set_error(GOO_ERR_TIMEOUT, "goo_server_step: a device wait for amplitude data gave up");
+  const unsigned nd = cs[0];
   if (nd == 0) return GOO_OK;
   std::vector<int> list(nd);
   GOO_CUDA_TRY(cudaMemcpyAsync(list.data(), s->d_done, nd * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1179,11 +1268,11 @@ int goo_server_create(goo_model* model, const double* theta_gen, const int* free
       cudaMalloc(&s->d_tickets, F * sizeof(unsigned)) != cudaSuccess ||
       cudaMalloc(&s->d_fit_tiles, F * sizeof(int2)) != cudaSuccess ||
       cudaMalloc(&s->d_slots, F * sizeof(int)) != cudaSuccess || cudaMalloc(&s->d_done, F * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&s->d_done_count, sizeof(unsigned)) != cudaSuccess)
+      cudaMalloc(&s->d_done_count, 2 * sizeof(unsigned)) != cudaSuccess)
     return fail("the fit slots");
   cudaMemsetAsync(s->d_states, 0, F * sizeof(SrvState), ctx->stream);
   cudaMemsetAsync(s->d_tickets, 0, F * sizeof(unsigned), ctx->stream);
-  cudaMemsetAsync(s->d_done_count, 0, sizeof(unsigned), ctx->stream);
+  cudaMemsetAsync(s->d_done_count, 0, 2 * sizeof(unsigned), ctx->stream);
   s->slots.resize(F);
   for (int i = F - 1; i >= 0; --i) s->free_slots.push_back(i);
   // shared model block: Gram matrix in slot order (resonances, then the reference)
@@ -1285,7 +1374,8 @@ int goo_server_step(goo_server* s, int* n_queued, int* n_active, int* n_done) {
     const auto t0 = std::chrono::steady_clock::now();
     GOO_CUDA_TRY(cudaMemsetAsync(s->d_results, 0, s->opt.max_fits * sizeof(SrvResult), ctx->stream));
     if (s->occ_nll == 0) {
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s->occ_nll, srv_nll_kernel, kBlock, 0) != cudaSuccess ||
+      GOO_CUDA_TRY(cudaFuncSetAttribute(srv_nll_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSrvSmem));
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s->occ_nll, srv_nll_kernel, kBlock, kSrvSmem) != cudaSuccess ||
           s->occ_nll < 1) {
         cudaGetLastError();
         s->occ_nll = 1;
@@ -1294,9 +1384,9 @@ int goo_server_step(goo_server* s, int* n_queued, int* n_active, int* n_done) {
     const int nb = (int)std::min<int64_t>(s->ntiles, (int64_t)ctx->num_sms * s->occ_nll);
     {
       LaunchScope ls(ctx, "srv_nll_grad");
-      srv_nll_kernel<<<nb, kBlock, 0, ctx->stream>>>(s->d_evals, s->d_tiles, s->d_fit_tiles, (int)s->ntiles,
-                                                     s->opt.tile_events, s->d_model, s->d_tile_partials, s->d_tickets,
-                                                     s->d_results);
+      srv_nll_kernel<<<nb, kBlock, kSrvSmem, ctx->stream>>>(s->d_evals, s->d_tiles, s->d_fit_tiles, (int)s->ntiles,
+                                                            s->opt.tile_events, s->d_model, s->d_tile_partials,
+                                                            s->d_tickets, s->d_results, s->d_done_count + 1);
     }
     GOO_CUDA_TRY(cudaGetLastError());
     {
@@ -1463,7 +1553,7 @@ int goo_nll_grad_batch(goo_model* m, int n_fits, const goo_dataset* const* ds, c
   // one allocation for the work space of this call
   const size_t bytes = sizeof(SrvEval) * n_fits + sizeof(int2) * (tiles.size() + n_fits) + sizeof(SrvModel) +
                        sizeof(SrvResult) * n_fits + sizeof(unsigned) * n_fits + sizeof(float2) * kSrvLanes * tiles.size() +
-                       8 * 256;
+                       sizeof(unsigned) + 9 * 256;
   unsigned char* w = nullptr;
   if (cudaMalloc(&w, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -1482,7 +1572,9 @@ int goo_nll_grad_batch(goo_model* m, int n_fits, const goo_dataset* const* ds, c
   SrvResult* d_res = (SrvResult*)take(sizeof(SrvResult) * n_fits);
   unsigned* d_tk = (unsigned*)take(sizeof(unsigned) * n_fits);
   float2* d_part = (float2*)take(sizeof(float2) * kSrvLanes * tiles.size());
+  unsigned* d_status = (unsigned*)take(sizeof(unsigned));
   int rc = GOO_OK;
+  unsigned status = 0;
   std::vector<SrvResult> res(n_fits);
   do {
     if (cudaMemcpyAsync(d_ev, ev.data(), sizeof(SrvEval) * n_fits, cudaMemcpyHostToDevice, ctx->stream) ||
@@ -1490,20 +1582,25 @@ int goo_nll_grad_batch(goo_model* m, int n_fits, const goo_dataset* const* ds, c
         cudaMemcpyAsync(d_ft, fit_tiles.data(), sizeof(int2) * n_fits, cudaMemcpyHostToDevice, ctx->stream) ||
         cudaMemcpyAsync(d_sm, &sm, sizeof sm, cudaMemcpyHostToDevice, ctx->stream) ||
         cudaMemsetAsync(d_res, 0, sizeof(SrvResult) * n_fits, ctx->stream) ||
-        cudaMemsetAsync(d_tk, 0, sizeof(unsigned) * n_fits, ctx->stream)) {
+        cudaMemsetAsync(d_tk, 0, sizeof(unsigned) * n_fits, ctx->stream) ||
+        cudaMemsetAsync(d_status, 0, sizeof(unsigned), ctx->stream)) {
       rc = set_error(GOO_ERR_CUDA, "goo_nll_grad_batch: copy failed");
       break;
     }
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, srv_nll_kernel, kBlock, 0) != cudaSuccess || occ < 1) occ = 1;
+    if (cudaFuncSetAttribute(srv_nll_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSrvSmem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, srv_nll_kernel, kBlock, kSrvSmem) != cudaSuccess || occ < 1)
+      occ = 1;
     cudaGetLastError();
     const int nb = (int)std::min<size_t>(tiles.size(), (size_t)ctx->num_sms * occ);
     {
       LaunchScope ls(ctx, "srv_nll_grad");
-      srv_nll_kernel<<<nb, kBlock, 0, ctx->stream>>>(d_ev, d_tiles, d_ft, (int)tiles.size(), T, d_sm, d_part, d_tk, d_res);
+      srv_nll_kernel<<<nb, kBlock, kSrvSmem, ctx->stream>>>(d_ev, d_tiles, d_ft, (int)tiles.size(), T, d_sm, d_part, d_tk,
+                                                            d_res, d_status);
     }
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(res.data(), d_res, sizeof(SrvResult) * n_fits, cudaMemcpyDeviceToHost, ctx->stream) ||
+        cudaMemcpyAsync(&status, d_status, sizeof status, cudaMemcpyDeviceToHost, ctx->stream) ||
         cudaStreamSynchronize(ctx->stream)) {
       rc = set_error(GOO_ERR_CUDA, "goo_nll_grad_batch: kernel failed");
       break;
@@ -1511,6 +1608,7 @@ int goo_nll_grad_batch(goo_model* m, int n_fits, const goo_dataset* const* ds, c
   } while (false);
   cudaFree(w);
   if (rc != GOO_OK) return rc;
+  if (status) return set_error(GOO_ERR_TIMEOUT, "goo_nll_grad_batch: a device wait for amplitude data gave up");
   for (int f = 0; f < n_fits; ++f) {
     double* g = grad_out + (size_t)f * P;
     for (int p = 0; p < P; ++p) g[p] = 0.0;

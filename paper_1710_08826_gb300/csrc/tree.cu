@@ -489,38 +489,50 @@ __device__ __forceinline__ void event_finish(ddf (&v)[EventLanes<float, K, L, GR
   if (!last_block_reduce(partials, NS, gridDim.x, counters, s_out, s_red)) return;
 
   // ---- final combination (last block, FP64) ----
+  // d NLL / d theta_p = sum_k [w_k C_k dlogN_kp - C_k dw_kp] - sum_{k,l,j: par = p} w_k A_klj.
+  // Column p of the first sum is taken by thread p (independent loads in parallel); the
+  // leaf terms are scattered by one thread from shared memory (leaves may share a parameter).
+  __shared__ double s_g[kMaxParams];
+  __shared__ double s_w[K];
+  __shared__ int s_par[K][L][3];
+  const int P = md->n_params;
+  for (int t = threadIdx.x; t < K * L * 3; t += blockDim.x) {
+    const int k = t / (L * 3), l = (t / 3) % L, jj = t % 3;
+    s_par[k][l][jj] = (k < nK && l < md->comp[k].n_leaf) ? md->leaf[k * kMaxLeaf + l].par[jj] : -1;
+  }
+  if (threadIdx.x < K) s_w[threadIdx.x] = threadIdx.x < nK ? md->comp[threadIdx.x].w : 0.0;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    double gp = 0.0;
+    if (GRAD)
+      for (int k = 0; k < nK; ++k) {
+        const double Ck = s_out[1 + k];
+        gp += md->comp[k].w * Ck * md->dlogN[k][p] - Ck * md->dw[k][p];
+      }
+    s_g[p] = gp;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && GRAD) {
+    for (int k = 0; k < nK; ++k)
+      for (int l = 0; l < L; ++l)
+        for (int jj = 0; jj < 3; ++jj)
+          if (s_par[k][l][jj] >= 0) s_g[s_par[k][l][jj]] -= s_w[k] * s_out[1 + K + (k * L + l) * 3 + jj];
+  }
+  __syncthreads();
+  const int off = out_mode == 0 ? 2 : 3;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) result[off + p] = s_g[p];
   if (threadIdx.x == 0) {
     const unsigned nbad = atomicAdd(counters + 1, 0u);
     counters[1] = 0u;
     const unsigned status = atomicAdd(counters + kStatusWord, 0u);
     counters[kStatusWord] = 0u;
-    const int P = md->n_params;
-    const double sumlogf = s_out[0];
-    double g[kMaxParams];
-    for (int p = 0; p < kMaxParams; ++p) g[p] = 0.0;
-    if (GRAD) {
-      for (int k = 0; k < nK; ++k) {
-        const double Ck = s_out[1 + k];
-        const double wk = md->comp[k].w;
-        for (int p = 0; p < P; ++p) g[p] += wk * Ck * md->dlogN[k][p] - Ck * md->dw[k][p];
-        for (int l = 0; l < md->comp[k].n_leaf && l < L; ++l) {
-          const LeafDev& lf = md->leaf[k * kMaxLeaf + l];
-          for (int j = 0; j < 3; ++j)
-            if (lf.par[j] >= 0) g[lf.par[j]] -= wk * s_out[1 + K + (k * L + l) * 3 + j];
-        }
-      }
-    }
     // a device wait that gave up is reported as a negative event count
     const double nb = status ? -1.0 : (double)nbad;
+    result[0] = -s_out[0];
     if (out_mode == 0) {
-      result[0] = -sumlogf;
       result[1] = nb;
-      for (int p = 0; p < P; ++p) result[2 + p] = g[p];
     } else {
-      result[0] = -sumlogf;
       result[1] = 0.0;
       result[2] = nb;
-      for (int p = 0; p < P; ++p) result[3 + p] = g[p];
     }
   }
 }
@@ -632,44 +644,8 @@ __global__ void __launch_bounds__(kBlock, EventOcc<T, K, L>::value) sop_event_ke
 // even event indices (8-byte column loads); a lane outside [begin, end) is masked.  Each
 // lane is rounded exactly as a scalar FP32 evaluation of the same formulas.
 // =======================================================================================
+
 namespace pk {
-__device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 sub(float2 a, float2 b) {
-  unsigned long long d;
-  asm("sub.rn.f32x2 %0, %1, %2;"
-      : "=l"(d)
-      : "l"(*reinterpret_cast<const unsigned long long*>(&a)), "l"(*reinterpret_cast<const unsigned long long*>(&b)));
-  return *reinterpret_cast<const float2*>(&d);
-}
-// hardware base-2 exponential / logarithm / reciprocal (PTX .approx forms, denormals flushed)
-__device__ __forceinline__ float ex2(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float lg2(float x) {
-  float y;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float rcp(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-constexpr float kLog2e = 1.4426950408889634f;  // 1 / ln 2
-constexpr float kLn2 = 0.6931471805599453f;
-__device__ __forceinline__ float2 exp(float2 x) {  // e^x per lane
-  const float2 t = mul(x, splat(kLog2e));
-  return make_float2(ex2(t.x), ex2(t.y));
-}
-__device__ __forceinline__ float2 log(float2 x) {  // natural log per lane
-  return mul(make_float2(lg2(x.x), lg2(x.y)), splat(kLn2));
-}
-__device__ __forceinline__ float2 rcp(float2 x) { return make_float2(rcp(x.x), rcp(x.y)); }
 __device__ __forceinline__ float2 pick(int col, float2 x0, float2 x1, float2 x2, float2 x3) {
   return col == 0 ? x0 : (col == 1 ? x1 : (col == 2 ? x2 : x3));
 }
