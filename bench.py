@@ -28,15 +28,26 @@ METRIC = "NLL evals/s (events/s) FP64 plain vs FP32+grad; toy fits/s, p50/p99 la
 UNIT = "events/s"
 BYTES_PER_EVENT_F32 = 12   # three float32 columns
 BYTES_PER_EVENT_F64 = 24
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant
-# kernel, from one ncu capture of `bench.py --profile --profile-workload c2`
-# (profiles/sop_event_kernel_f32_c2_10M.md).  Reported only while the kernel's sources
-# still hash to the captured value; scaled by events when the bench runs another size.
-NCU_TRAFFIC = {"sop_nll_grad_f32": {"bytes": 123_343_872, "events": 10_000_000,
-                                    "sources": ["paper_1710_08826_gb300/csrc/tree.cu",
-                                                "paper_1710_08826_gb300/csrc/common.cuh",
-                                                "paper_1710_08826_gb300/csrc/model.cuh"],
-                                    "sha256": "5de31be8be84ae359ab90828efdbddbcaaaf1da4bd35c6f2516b744a03822302"}}
+# Counters of one launch of each timed kernel from one ncu capture (the profiles/ file named
+# in "profile"): DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and, for the FP64
+# kernels, the FP64 pipe's active fraction (sm__pipe_fp64_cycles_active).  A record is used
+# only while the kernel's sources still hash to the captured value; bytes scale with events.
+_SOP_SRC = ['paper_1710_08826_gb300/csrc/tree.cu', 'paper_1710_08826_gb300/csrc/common.cuh', 'paper_1710_08826_gb300/csrc/model.cuh']
+_COH_SRC = ['paper_1710_08826_gb300/csrc/dalitz.cu', 'paper_1710_08826_gb300/csrc/dalitz.cuh', 'paper_1710_08826_gb300/csrc/common.cuh', 'paper_1710_08826_gb300/csrc/model.cuh']
+NCU_RECORDS = {
+    "sop_nll_grad_f32": {"bytes": 125_785_088, "events": 10_000_000, "sources": _SOP_SRC,
+                         "sha256": "8dfab8aa796eadf45ce7f39879b46dadeeae283b22c1ba4f7854ef93258809d2",
+                         "profile": "profiles/sop_event2_kernel_f32_c2_10M.md"},
+    "sop_nll_f64": {"bytes": 243_802_880, "events": 10_000_000, "fp64_pipe": 0.8631, "sources": _SOP_SRC,
+                    "sha256": "8dfab8aa796eadf45ce7f39879b46dadeeae283b22c1ba4f7854ef93258809d2",
+                    "profile": "profiles/sop_event_kernel_f64_c2_10M.md"},
+    "coh_nll_grad_f32": {"bytes": 323_185_664, "events": 5_000_000, "sources": _COH_SRC,
+                         "sha256": "b457246f0a0eadb7f6bcc854a759157881ccae15d5e3f7e00a959af08c1545f9",
+                         "profile": "profiles/coh_nll_staged_kernel_f32_c3_5M.md"},
+    "coh_nll_f64": {"bytes": 643_364_352, "events": 5_000_000, "fp64_pipe": 0.8701, "sources": _COH_SRC,
+                    "sha256": "b457246f0a0eadb7f6bcc854a759157881ccae15d5e3f7e00a959af08c1545f9",
+                    "profile": "profiles/coh_nll_kernel_f64_c3_5M.md"},
+}
 
 
 def sources_sha256(paths):
@@ -48,11 +59,20 @@ def sources_sha256(paths):
     return h.hexdigest()
 
 
-def ncu_traffic(kernel, n_events):
-    rec = NCU_TRAFFIC.get(kernel)
+def ncu_record(kernel, n_events):
+    """The kernel's ncu counters scaled to n_events, or None when absent or stale."""
+    rec = NCU_RECORDS.get(kernel)
     if rec is None or sources_sha256(rec["sources"]) != rec["sha256"]:
         return None
-    return rec["bytes"] * n_events / rec["events"]
+    out = {"traffic": rec["bytes"] * n_events / rec["events"], "profile": rec["profile"]}
+    if "fp64_pipe" in rec:
+        out["fp64_pipe_active"] = rec["fp64_pipe"]
+    return out
+
+
+def ncu_traffic(kernel, n_events):
+    rec = ncu_record(kernel, n_events)
+    return None if rec is None else rec["traffic"]
 
 
 def parse():
@@ -360,7 +380,9 @@ def run_ours(args):
         "fp64_plain": {"events_per_s": n * world * steps64 / (total_64 * 1e-3),
                        "evals_per_s": steps64 / (total_64 * 1e-3), "ms_per_eval": total_64 / steps64,
                        "what": "goo_nll in float64 (FP64 per-event arithmetic and grid), no gradient",
-                       "kernels_ms": {k: v[1] / v[0] for k, v in kt_64.items()}},
+                       "kernels_ms": {k: v[1] / v[0] for k, v in kt_64.items()},
+                       "roofline": {"bound": "fp64", "kernel": "sop_nll_f64",
+                                    "ncu": ncu_record("sop_nll_f64", n)}},
         "parity_this_run": {"nll_f32": nll32, "nll_f64": nll64, "rel": abs(nll32 - nll64) / abs(nll64)},
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * BYTES_PER_EVENT_F32 + 8 * P,
@@ -430,6 +452,7 @@ def c3_measure(goo, ctx, stream, steps, n_events=5_000_000, n_mc=1_000_000):
             "evals_per_s": k / (ms * 1e-3), "events_per_s": n_events * k / (ms * 1e-3), "ms_per_eval": ms / k,
             "kernel": name, "kernel_ms": per,
             "hbm_frac": n_events * bytes_per_event / (per * 1e-3) / 1e9 / measured_peaks()[0],
+            "bound": "hbm" if grad else "fp64", "ncu": ncu_record(name, n_events),
             "what": ("goo_nll_grad, FP32 amplitude cache (64 B/event), adjoint gradient" if grad
                      else "goo_nll, FP64 amplitude cache (128 B/event)")}
     return out
