@@ -234,6 +234,7 @@ def run_ours(args):
     import synth
     from paper_1710_08826_gb300 import build
     build()
+    from paper_1710_08826_gb300 import dist as gdist
     from paper_1710_08826_gb300 import goo
 
     rank, local_rank, world = dist_env()
@@ -261,15 +262,12 @@ def run_ours(args):
     P = len(theta)
 
     def step(precision, grad=True):
-        if grad:
-            out = model.nll_partial(ds, 0, ds.n, theta, precision, want_grad=True)
-        else:
-            out = model.nll_partial(ds, 0, ds.n, theta, precision, want_grad=False)
+        # one shard record per rank; N > 1: all-gather and the ordered, compensated combine
+        out = model.nll_partial(ds, 0, ds.n, theta, precision, want_grad=grad)
         if pg is not None:
-            t = torch.tensor(out, dtype=torch.float64, device="cuda")
-            pg.all_reduce(t)
-            out = t.cpu().numpy()
-        return out
+            nll, g, _ = gdist.combine(gdist.allgather_records(out, device="cuda"), P)
+            return np.concatenate([[nll], g])
+        return np.concatenate([[out[0] + out[1]], out[3:]])
 
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
