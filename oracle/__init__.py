@@ -7,8 +7,8 @@ executes anything here, and this package imports nothing from the product.
 
 The GooFit 2.0 paper prints no formulas: it describes PDFs composed from basic
 shapes by sum and product combination PDFs and fitted to unbinned datasets
-(Fig. 1; Sec. 1), three-body amplitude PDFs (Sec. 1, Sec. 5) and toy MC for
-normalisation integrals (Sec. 5).  Each function here therefore states the
+(Fig. 1; Sec. 1), three-body amplitude PDFs (Sec. 1, Sec. 5), the time-dependent
+four-body amplitude analysis (Sec. 5) and toy MC for normalisation integrals (Sec. 5).  Each function here therefore states the
 textbook definition it implements, written out plainly in float64 with no
 blocking, fusion or reordering; gradients come from PyTorch autograd of these
 definitions.
@@ -19,4 +19,4 @@ factorisation, finite differences, kinematic identities, published RNG
 outputs (numpy's Philox), and recovery of generated parameters within their
 errors on toy fits.
 """
-from . import pdfs, model, dalitz, fit  # noqa: F401
+from . import pdfs, model, dalitz, fit, td4  # noqa: F401

@@ -169,5 +169,60 @@ def toy_sizes(n_toys=4096, lo=1e3, hi=1e6, seed=1710099):
     return np.floor(np.exp(u)).astype(np.int64)
 
 
-def gen_c4_candidates(*args, **kwargs):
-    raise NotImplementedError("four-body phase-space generator")
+def _two_body_momentum(M, ma, mb):
+    """Momentum of either daughter in the rest frame of a mass-M system (0 below threshold)."""
+    lam = (M * M - (ma + mb) ** 2) * (M * M - (ma - mb) ** 2)
+    return np.sqrt(np.clip(lam, 0.0, None)) / (2.0 * M)
+
+
+def four_body_phase_space(n, seed, M, m1, m2, m3, m4):
+    """n points of four-body phase space in (m12, m34, cos th12, cos th34, phi).
+
+    Four-body phase space factorises into the parent's two-body decay to the (12) and (34)
+    systems and their two-body decays; in these variables its density is proportional to
+    p(M; m12, m34) q(m12; m1, m2) q(m34; m3, m4), uniform in both helicity cosines and in the
+    angle phi between the decay planes.  (m12, m34) are drawn uniformly over their box and
+    kept by accept--reject on that weight (zero where m12 + m34 > M).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lo12, hi12 = m1 + m2, M - m3 - m4
+    lo34, hi34 = m3 + m4, M - m1 - m2
+
+    def weight(a, b):
+        inside = a + b < M
+        w = (_two_body_momentum(M, a, np.where(inside, b, 0.0)) * _two_body_momentum(a, m1, m2)
+             * _two_body_momentum(b, m3, m4))
+        return np.where(inside, w, 0.0)
+
+    ga, gb = np.meshgrid(np.linspace(lo12, hi12, 801), np.linspace(lo34, hi34, 801))
+    wmax = 1.05 * float(weight(ga, gb).max())
+    m12 = np.empty(n)
+    m34 = np.empty(n)
+    filled = 0
+    while filled < n:
+        k = int((n - filled) * 3.0) + 4096
+        a = rng.uniform(lo12, hi12, k)
+        b = rng.uniform(lo34, hi34, k)
+        ok = rng.uniform(0.0, wmax, k) < weight(a, b)
+        a, b = a[ok], b[ok]
+        take = min(n - filled, a.size)
+        m12[filled:filled + take] = a[:take]
+        m34[filled:filled + take] = b[:take]
+        filled += take
+    return {"m12": m12, "m34": m34, "c12": rng.uniform(-1.0, 1.0, n), "c34": rng.uniform(-1.0, 1.0, n),
+            "phi": rng.uniform(-math.pi, math.pi, n)}
+
+
+def gen_c4_candidates(n, seed, kin, rate):
+    """Phase-space points plus true decay times t_true ~ Exp(rate) (the envelope in time of an
+    accept--reject against the time-dependent rate, which the caller supplies)."""
+    cols = four_body_phase_space(n, seed, kin["M"], kin["m1"], kin["m2"], kin["m3"], kin["m4"])
+    rng = np.random.Generator(np.random.PCG64(seed + 7_000_001))
+    cols["t_true"] = rng.exponential(1.0 / rate, n)
+    return cols
+
+
+def smear_times(t_true, sigma, seed):
+    """Observed decay times: t_true plus Gaussian resolution N(0, sigma)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return t_true + rng.normal(0.0, sigma, t_true.size)

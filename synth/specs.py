@@ -13,11 +13,15 @@ Tree nodes (parameter and observable references are names):
   ("prod", [child, ...])           ("add", [frac, ...], [child, ...])   K children, K-1 fractions
   ("coherent", kin, [amp, ...])    kin = dict(M, m1, m2, m3, r_res, r_par)
       amp = ("bw", pair, spin, m0, width, re, im) | ("nr", re, im);  pair in {"12","13","23"}
+  ("td4", kin, [amp, ...], (x, y, tau, sigma_t))   kin = dict(M, m1, m2, m3, m4, r_res)
+      amp = (angular, (m0, width) in pair 12, (m0, width) in pair 34, re, im, (cf_re, cf_im))
+      observables in the order m12, m34, cos th12, cos th34, phi, t
 
 The paper (GooFit 2.0, Fig. 1 and Sec. 1) describes models built from basic PDFs combined
 by sum and product combination PDFs and amplitude PDFs for three-body decays (Sec. 1,
 Sec. 5); it prints no formulas, so the meaning of each node is fixed by the oracle.
 """
+import math
 
 # Parent and daughter masses (GeV) of the D -> K pi pi0 - like three-body model.
 DALITZ_MASSES = dict(M=1.865, m1=0.494, m2=0.140, m3=0.135)
@@ -101,8 +105,59 @@ def c3_spec(n_mc=1_000_000, mc_seed=1710013):
     )
 
 
-def c4_spec():
-    raise NotImplementedError("time-dependent four-body model spec")
+# Parent and daughter masses (GeV) of the D -> K pi pi pi - like four-body model; particles
+# 1 = K, 2 = pi (the K pi pair "12"), 3, 4 = pi pi (the pair "34").
+TD4_MASSES = dict(M=1.865, m1=0.494, m2=0.140, m3=0.140, m4=0.140)
+
+# Two-body resonances (m0, width in GeV) of the four-body model.
+TD4_RESONANCES = {
+    "Kst892": (0.8955, 0.0473), "K0st1430": (1.425, 0.270), "K2st1430": (1.4324, 0.109),
+    "Kst1410": (1.414, 0.232), "rho770": (0.7753, 0.1491), "f0980": (0.990, 0.070),
+    "rho1450": (1.465, 0.400),
+}
+
+# The ten amplitudes: (name, angular structure, resonance in pair 12, resonance in pair 34,
+# truth of the free DCS coefficient (Re, Im), fixed CF coefficient (Re, Im)).  Angular
+# structures (spins of the two resonances in brackets):
+#   SS  (0,0): 1                     VS0 (1,0): cos th12          SV0 (0,1): cos th34
+#   VV0 (1,1): cos th12 cos th34     VVpar (1,1): sin th12 sin th34 cos phi
+#   VVperp (1,1): i sin th12 sin th34 sin phi
+#   TS0 (2,0): (3 cos^2 th12 - 1)/2  TV0 (2,1): (3 cos^2 th12 - 1)/2 cos th34
+TD4_AMPS = [
+    ("KstRho_0", "VV0", "Kst892", "rho770", (1.0, 0.0), (0.9, 0.3)),
+    ("KstRho_par", "VVpar", "Kst892", "rho770", (0.45, 0.2), (0.3, -0.1)),
+    ("KstRho_perp", "VVperp", "Kst892", "rho770", (-0.3, 0.25), (0.2, 0.3)),
+    ("KstF0", "VS0", "Kst892", "f0980", (0.35, -0.15), (-0.4, 0.2)),
+    ("K0stRho", "SV0", "K0st1430", "rho770", (0.5, 0.3), (0.45, 0.1)),
+    ("K0stF0", "SS", "K0st1430", "f0980", (0.25, -0.4), (0.3, 0.25)),
+    ("K2stRho", "TV0", "K2st1430", "rho770", (0.3, 0.1), (-0.25, 0.2)),
+    ("K2stF0", "TS0", "K2st1430", "f0980", (-0.2, 0.15), (0.2, -0.1)),
+    ("Kst1410Rho", "VV0", "Kst1410", "rho770", (0.4, -0.25), (0.35, 0.2)),
+    ("KstRho1450", "VV0", "Kst892", "rho1450", (0.3, 0.35), (0.25, -0.3)),
+]
+
+# Mixing and time-resolution truth: x, y, lifetime tau (ps), Gaussian resolution sigma_t (ps).
+TD4_TIME = dict(x=0.004, y=0.006, tau=0.41, sigma_t=0.05)
+
+
+def c4_spec(n_mc=3_000_000, mc_seed=1710014):
+    """Time-dependent four-body model: 10 amplitudes, 20 free DCS coefficients, x, y, tau, sigma_t."""
+    kin = dict(TD4_MASSES, r_res=1.5)
+    M, m1, m2, m3, m4 = kin["M"], kin["m1"], kin["m2"], kin["m3"], kin["m4"]
+    params, amps = [], []
+    for name, ang, r12, r34, (re, im), (cre, cim) in TD4_AMPS:
+        params += [(f"re_{name}", re, False, 0.02), (f"im_{name}", im, False, 0.02)]
+        amps.append((ang, TD4_RESONANCES[r12], TD4_RESONANCES[r34], f"re_{name}", f"im_{name}", (cre, cim)))
+    params += [("x", TD4_TIME["x"], False, 0.002), ("y", TD4_TIME["y"], False, 0.002),
+               ("tau", TD4_TIME["tau"], False, 0.002), ("sigma_t", TD4_TIME["sigma_t"], False, 0.001)]
+    return dict(
+        name="c4_td4",
+        observables=[("m12", m1 + m2, M - m3 - m4), ("m34", m3 + m4, M - m1 - m2), ("c12", -1.0, 1.0),
+                     ("c34", -1.0, 1.0), ("phi", -math.pi, math.pi), ("t", -0.5, 10.0)],
+        params=params,
+        pdf=("td4", kin, amps, ("x", "y", "tau", "sigma_t")),
+        norm=("mc", n_mc, mc_seed),
+    )
 
 
 def param_names(spec):
