@@ -73,8 +73,31 @@ enum {
   GOO_OP_BW = 20,    /* Breit-Wigner amplitude: par[0]=m0, par[1]=width, par[2]=Re c,
                         par[3]=Im c; ival[0]=spin (0..2), ival[1]=pair (0:12, 1:13, 2:23) */
   GOO_OP_NR = 21,    /* constant (non-resonant) amplitude: par[2]=Re c, par[3]=Im c       */
-  GOO_OP_COHERENT = 22 /* |sum_k c_k A_k|^2 over its BW/NR children; obs[0]=s12, obs[1]=s13;
+  GOO_OP_COHERENT = 22, /* |sum_k c_k A_k|^2 over its BW/NR children; obs[0]=s12, obs[1]=s13;
                           dval = {M, m1, m2, m3, r_res, r_parent}                          */
+  /* Time-dependent four-body amplitude model (paper Sec. 5: time-dependent amplitude
+   * analysis of four-body decays for a mixing measurement).  The model's observables are,
+   * in this order, m12, m34, cos th12, cos th34, phi, t (six dataset columns).
+   *   A = sum_k c_k a_k (free coefficients), B = sum_k b_k a_k (fixed coefficients),
+   *   rate R = e^{-G t}[(|A|^2+|B|^2)/2 cosh(yGt) + (|A|^2-|B|^2)/2 cos(xGt)
+   *            + Re(AB*) sinh(yGt) + Im(AB*) sin(xGt)] (G = 1/tau) convolved with a Gaussian
+   *   of width sigma_t; normalised over phase space (MC Gram matrix) and all t.          */
+  GOO_OP_TD4 = 23,   /* root over GOO_OP_AMP4 children: par[0]=x, par[1]=y, par[2]=tau (ps),
+                        par[3]=sigma_t (ps); dval = {M, m1, m2, m3, m4, r (barrier radius)}  */
+  GOO_OP_AMP4 = 24   /* a_k = F(m12; dval[0]=m0, dval[1]=width) F(m34; dval[2]=m0,
+                        dval[3]=width) W(cos th12, cos th34, phi), F a Breit-Wigner with
+                        running width and Blatt-Weisskopf factors of the spins that
+                        ival[0] = GOO_ANG_* fixes; par[0]=Re c_k, par[1]=Im c_k (free),
+                        dval[4]=Re b_k, dval[5]=Im b_k (fixed)                          */
+};
+
+/* Angular structures of GOO_OP_AMP4 (spins of the 12 and 34 resonances in brackets; s = sin):
+ * SS (0,0) 1; VS0 (1,0) cos th12; SV0 (0,1) cos th34; VV0 (1,1) cos th12 cos th34;
+ * VVPAR (1,1) s12 s34 cos phi; VVPERP (1,1) i s12 s34 sin phi; TS0 (2,0) P2(cos th12);
+ * TV0 (2,1) P2(cos th12) cos th34, with P2(c) = (3c^2 - 1)/2. */
+enum {
+  GOO_ANG_SS = 0, GOO_ANG_VS0 = 1, GOO_ANG_SV0 = 2, GOO_ANG_VV0 = 3, GOO_ANG_VVPAR = 4, GOO_ANG_VVPERP = 5,
+  GOO_ANG_TS0 = 6, GOO_ANG_TV0 = 7
 };
 
 #define GOO_MAX_CHILD 16
@@ -97,7 +120,8 @@ typedef struct goo_node {
 enum {
   GOO_NORM_ANALYTIC = 0, /* closed-form integrals of the leaves over the observable ranges */
   GOO_NORM_GRID = 1,     /* midpoint rule per normalised component, bins[] per observable  */
-  GOO_NORM_MC = 2        /* mean of |S|^2 over a phase-space MC dataset (amplitude models) */
+  GOO_NORM_MC = 2        /* mean over a phase-space MC dataset (amplitude models): the Gram
+                            matrix <a_k a_l*>; the t column of a GOO_OP_TD4 MC is ignored */
 };
 
 typedef struct goo_dataset goo_dataset;
@@ -131,7 +155,7 @@ int goo_timing_enable(goo_ctx* ctx, int on);
 int goo_timing_read(goo_ctx* ctx, int max_entries, char* names, int64_t* counts, double* total_ms, int reset);
 
 /* ---- data (paper: DataSet, Fig. 1 and Sec. 4) ------------------------------------------------
- * Upload `ncols` structure-of-arrays columns of n_events values each, of type `dtype`
+ * Upload `ncols` (1..8) structure-of-arrays columns of n_events values each, of type `dtype`
  * (GOO_F64 or GOO_F32).  With GOO_COPY the columns are host arrays copied to the device;
  * with GOO_BORROW_DEVICE they are device arrays (16-byte aligned) kept by reference.
  * lo[c], hi[c] are the limits of observable c.  Every event is range-checked on the device
@@ -151,8 +175,10 @@ const void* goo_dataset_column(const goo_dataset* ds, int col, int dtype);
  * Build a model from `n_nodes` post-order nodes over `n_params` parameters and `n_obs`
  * observables with limits obs_lo/obs_hi (the normalisation range).  Sum/product trees are
  * flattened to a sum of products of leaves (at most 4 products of at most 4 leaves after
- * flattening); a GOO_OP_COHERENT root builds an amplitude model.  The default
- * normalisation is GOO_NORM_ANALYTIC for sum/product trees. */
+ * flattening) over at most 4 observables; a GOO_OP_COHERENT root builds a three-body
+ * amplitude model and a GOO_OP_TD4 root the time-dependent four-body model (6 observables;
+ * at most 8 for any model).  The default normalisation is GOO_NORM_ANALYTIC for sum/product
+ * trees; amplitude models need GOO_NORM_MC. */
 int goo_model_build(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_params, int n_obs,
                     const double* obs_lo, const double* obs_hi, goo_model** out);
 int goo_model_set_norm(goo_model* model, const goo_norm_spec* spec);
@@ -162,7 +188,8 @@ int goo_model_components(const goo_model* model);
 
 /* ---- normalisation (a5) ---------------------------------------------------------------------
  * Integral of each normalised component at theta, in `precision`; norms_out receives
- * goo_model_components() doubles (for amplitude models: one value, the MC mean of |S|^2). */
+ * goo_model_components() doubles (for amplitude models one value: the MC mean of |S|^2, or
+ * for GOO_OP_TD4 the MC mean of the rate integrated over all t). */
 int goo_normalise(goo_model* model, const double* theta, int precision, double* norms_out);
 
 /* ---- likelihood (a1-a7; paper Sec. 1: the per-event evaluation dominates a fit) -------------- */
@@ -269,6 +296,13 @@ int goo_nll_grad_batch(goo_model* model, int n_fits, const goo_dataset* const* d
 int goo_nll_partial(goo_model* model, const goo_dataset* ds, int64_t begin, int64_t end,
                     const double* theta, int precision, int want_grad, double* out);
 int goo_combine_partials(int n_parts, int n_params, const double* parts, double* out);
+
+/* ---- Faddeeva function ------------------------------------------------------------------
+ * w(z) = exp(-z^2) erfc(-i z) for Im z >= 0 by the library's rational approximation
+ * (Weideman 1994; 24 terms for GOO_F32, evaluated in float, 40 terms for GOO_F64), the
+ * function the four-body model's decay-time resolution uses.  Host-only: it lets the
+ * arithmetic the kernels run be checked on the CPU.  out[0] = Re w, out[1] = Im w. */
+int goo_faddeeva(double re, double im, int precision, double* out);
 
 /* ---- likelihood without device allocation ------------------------------------------------
  * The paper has no counterpart to this call.  It computes the same NLL and gradient as

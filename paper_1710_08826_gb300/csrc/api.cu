@@ -53,6 +53,8 @@ int nll_common(goo_model* m, const goo_dataset* ds, const double* theta, int pre
   double res[2 + kMaxParams];
   if (m->kind == 1) {
     GOO_TRY(dalitz_nll(m, ds, 0, ds->n, theta, precision, grad, res, 0));
+  } else if (m->kind == 2) {
+    GOO_TRY(td4_nll(m, ds, 0, ds->n, theta, precision, grad, res, 0));
   } else {
     GOO_TRY(sop_prepare(m, theta, precision));
     GOO_TRY(sop_events(m, ds, 0, ds->n, precision, grad, 0));
@@ -92,7 +94,7 @@ int goo_model_build(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_para
   if (n_nodes < 1 || n_nodes > 256) return set_error(GOO_ERR_ARG, "goo_model_build: n_nodes=%d", n_nodes);
   if (n_params < 0 || n_params > kMaxParams)
     return set_error(GOO_ERR_ARG, "goo_model_build: n_params=%d (max %d)", n_params, kMaxParams);
-  if (n_obs < 1 || n_obs > kMaxObs) return set_error(GOO_ERR_ARG, "goo_model_build: n_obs=%d (1..%d)", n_obs, kMaxObs);
+  if (n_obs < 1 || n_obs > kMaxCols) return set_error(GOO_ERR_ARG, "goo_model_build: n_obs=%d (1..%d)", n_obs, kMaxCols);
   for (int o = 0; o < n_obs; ++o)
     if (!(obs_lo[o] < obs_hi[o])) return set_error(GOO_ERR_ARG, "goo_model_build: observable %d has lo >= hi", o);
   for (int i = 0; i < n_nodes; ++i) {
@@ -116,6 +118,8 @@ int goo_model_build(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_para
   int rc;
   if (nodes[n_nodes - 1].op == GOO_OP_COHERENT) {
     rc = build_dalitz_model(ctx, nodes, n_nodes, n_params, n_obs, obs_lo, obs_hi, m);
+  } else if (nodes[n_nodes - 1].op == GOO_OP_TD4) {
+    rc = build_td4_model(ctx, nodes, n_nodes, n_params, n_obs, m);
   } else {
     rc = build_sop_model(ctx, nodes, n_nodes, n_params, n_obs, obs_lo, obs_hi, m);
     m->norm.kind = GOO_NORM_ANALYTIC;
@@ -131,6 +135,7 @@ int goo_model_build(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_para
 int goo_model_set_norm(goo_model* m, const goo_norm_spec* spec) {
   if (!m || !spec) return set_error(GOO_ERR_ARG, "goo_model_set_norm: NULL argument");
   GOO_CUDA_TRY(cudaSetDevice(m->ctx->device));
+  if (m->kind == 2) return td4_set_norm(m, spec);
   return m->kind == 1 ? dalitz_set_norm(m, spec) : sop_set_norm(m, spec);
 }
 
@@ -141,13 +146,14 @@ int goo_model_free(goo_model* m) {
   if (m->dev) cudaFree(m->dev);
   if (m->stage) cudaFreeHost(m->stage);
   if (m->dalitz) dalitz_free(m);
+  if (m->td4) td4_free(m);
   delete m;
   return GOO_OK;
 }
 
 int goo_model_components(const goo_model* m) {
   if (!m) return set_error(GOO_ERR_ARG, "goo_model_components: NULL model");
-  return m->kind == 1 ? 1 : m->host.nK;
+  return m->kind >= 1 ? 1 : m->host.nK;
 }
 
 int goo_normalise(goo_model* m, const double* theta, int precision, double* norms_out) {
@@ -156,6 +162,7 @@ int goo_normalise(goo_model* m, const double* theta, int precision, double* norm
   GOO_TRY(check_theta(m, theta));
   GOO_CUDA_TRY(cudaSetDevice(m->ctx->device));
   if (m->kind == 1) return dalitz_normalise(m, theta, precision, norms_out);
+  if (m->kind == 2) return td4_normalise(m, theta, precision, norms_out);
   GOO_TRY(sop_prepare(m, theta, precision));
   goo_ctx* ctx = m->ctx;
   CompDev comp[kMaxComp];
@@ -184,6 +191,8 @@ int goo_eval_logf(goo_model* m, const goo_dataset* ds, const double* theta, int 
   GOO_CUDA_TRY(cudaSetDevice(m->ctx->device));
   if (m->kind == 1) {
     GOO_TRY(dalitz_eval_logf(m, ds, theta, precision, logf_dev));
+  } else if (m->kind == 2) {
+    GOO_TRY(td4_eval_logf(m, ds, theta, precision, logf_dev));
   } else {
     GOO_TRY(sop_prepare(m, theta, precision));
     GOO_TRY(sop_eval_logf(m, ds, precision, logf_dev));
@@ -204,7 +213,9 @@ int goo_nll_partial(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t 
   goo_ctx* ctx = m->ctx;
   const int P = m->n_params;
   double res[3 + kMaxParams];
-  if (m->kind == 1) {
+  if (m->kind == 2) {
+    GOO_TRY(td4_nll(m, ds, begin, end, theta, precision, want_grad != 0, res, 1));
+  } else if (m->kind == 1) {
     GOO_TRY(dalitz_nll(m, ds, begin, end, theta, precision, want_grad != 0, res, 1));
   } else {
     GOO_TRY(sop_prepare(m, theta, precision));
@@ -236,20 +247,22 @@ int goo_nll_partial(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t 
 
 int goo_gram(goo_model* m, const double* theta, int precision, double* out, int* K_out) {
   if (!m || !out || !K_out) return set_error(GOO_ERR_ARG, "goo_gram: NULL argument");
-  if (m->kind != 1) return set_error(GOO_ERR_STATE, "goo_gram: not an amplitude model");
+  if (m->kind != 1 && m->kind != 2) return set_error(GOO_ERR_STATE, "goo_gram: not an amplitude model");
   if (precision != GOO_F64 && precision != GOO_F32) return set_error(GOO_ERR_ARG, "precision=%d", precision);
   GOO_TRY(check_theta(m, theta));
   GOO_CUDA_TRY(cudaSetDevice(m->ctx->device));
+  if (m->kind == 2) return td4_gram(m, precision, out, K_out);
   return dalitz_gram(m, theta, precision, out, K_out);
 }
 
 int goo_amplitude_cache(goo_model* m, const goo_dataset* ds, const double* theta, int precision, const void** dev_ptr,
                         int* n_amp) {
   if (!m || !ds || !dev_ptr || !n_amp) return set_error(GOO_ERR_ARG, "goo_amplitude_cache: NULL argument");
-  if (m->kind != 1) return set_error(GOO_ERR_STATE, "goo_amplitude_cache: not an amplitude model");
+  if (m->kind != 1 && m->kind != 2) return set_error(GOO_ERR_STATE, "goo_amplitude_cache: not an amplitude model");
   GOO_TRY(check_model_dataset(m, ds, precision));
   GOO_TRY(check_theta(m, theta));
   GOO_CUDA_TRY(cudaSetDevice(m->ctx->device));
+  if (m->kind == 2) return td4_amplitudes(m, ds, precision, dev_ptr, n_amp);
   return dalitz_amplitudes(m, ds, theta, precision, dev_ptr, n_amp);
 }
 

@@ -44,7 +44,8 @@ int log_level();
 // limits
 // ---------------------------------------------------------------------------------------
 constexpr int kMaxParams = 128;    // parameters of one model
-constexpr int kMaxObs = 4;         // observables of one model
+constexpr int kMaxObs = 4;         // observables of a sum/product model
+constexpr int kMaxCols = 8;        // columns of a dataset, observables of any model
 constexpr int kMaxComp = 4;        // products in the flattened sum of products
 constexpr int kMaxLeaf = 4;        // leaves per product
 constexpr int kMaxSlots = 64;      // reduction lanes of one kernel
@@ -105,11 +106,11 @@ struct goo_dataset {
   goo_ctx* ctx = nullptr;
   int64_t n = 0;
   int ncols = 0;
-  double* d64[goo::kMaxObs] = {nullptr, nullptr, nullptr, nullptr};
-  float* d32[goo::kMaxObs] = {nullptr, nullptr, nullptr, nullptr};
+  double* d64[goo::kMaxCols] = {};
+  float* d32[goo::kMaxCols] = {};
   bool owns64 = true, owns32 = true;
-  double lo[goo::kMaxObs] = {0, 0, 0, 0};
-  double hi[goo::kMaxObs] = {0, 0, 0, 0};
+  double lo[goo::kMaxCols] = {};
+  double hi[goo::kMaxCols] = {};
   // amplitude caches attached to this dataset, [0]: float32, [1]: float64 (built lazily by
   // the amplitude-model path and rebuilt when the model or its lineshapes change)
   goo::CacheSlot cache[2];

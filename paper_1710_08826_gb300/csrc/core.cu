@@ -121,8 +121,8 @@ __global__ void convert_f32_to_f64(const float* __restrict__ in, double* __restr
 }
 
 struct RangeArgs {
-  const double* col[kMaxObs];
-  double lo[kMaxObs], hi[kMaxObs];
+  const double* col[kMaxCols];
+  double lo[kMaxCols], hi[kMaxCols];
   int ncols;
 };
 
@@ -150,7 +150,7 @@ __global__ void range_check_kernel(RangeArgs a, int64_t n, unsigned long long* b
 }
 
 static void free_dataset_memory(goo_dataset* ds) {
-  for (int c = 0; c < kMaxObs; ++c) {
+  for (int c = 0; c < kMaxCols; ++c) {
     if (ds->d64[c] && ds->owns64) cudaFree(ds->d64[c]);
     if (ds->d32[c] && ds->owns32) cudaFree(ds->d32[c]);
     ds->d64[c] = nullptr;
@@ -250,7 +250,7 @@ int goo_dataset_upload(goo_ctx* ctx, int ncols, const void* const* cols, int dty
   if (n_bad) *n_bad = 0;
   if (!ctx || !cols || !lo || !hi || !out) return set_error(GOO_ERR_ARG, "goo_dataset_upload: NULL argument");
   *out = nullptr;
-  if (ncols < 1 || ncols > kMaxObs) return set_error(GOO_ERR_ARG, "goo_dataset_upload: ncols=%d (1..%d)", ncols, kMaxObs);
+  if (ncols < 1 || ncols > kMaxCols) return set_error(GOO_ERR_ARG, "goo_dataset_upload: ncols=%d (1..%d)", ncols, kMaxCols);
   if (n_events < 0) return set_error(GOO_ERR_ARG, "goo_dataset_upload: n_events=%lld", (long long)n_events);
   if (dtype != GOO_F64 && dtype != GOO_F32) return set_error(GOO_ERR_ARG, "goo_dataset_upload: dtype=%d", dtype);
   if (flags != GOO_COPY && flags != GOO_BORROW_DEVICE) return set_error(GOO_ERR_ARG, "goo_dataset_upload: flags=%d", flags);

@@ -4,6 +4,8 @@
 // at the top of dalitz.cu.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace goo {
@@ -168,6 +170,99 @@ __device__ __forceinline__ void coh_event_pk(const float2 (&cre)[KA], const floa
   } else {
     bad++;
   }
+}
+
+// ---------------------------------------------------------------------------------------
+template <typename T, int KB>
+__global__ void __launch_bounds__(kBlock, 2) gram_kernel(const void* cache_v, int64_t n, int nbw, int has_nr,
+                                                         float2* partials, unsigned* counters, double* gram_out) {
+  constexpr int KA = KB + 1;
+  constexpr int NS = 2 * KA;
+  __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
+  using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const Vec* cache = (const Vec*)cache_v;
+  const int k = blockIdx.y;  // row, in slot numbering (BW slots, NR = KB)
+  const int krow = k < nbw ? k : KB;
+  Kahan kr[KA], ki[KA];
+  double dr[KA], di[KA];
+#pragma unroll
+  for (int l = 0; l < KA; ++l) dr[l] = di[l] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T ar[KA], ai[KA];
+    load_amps<KB>(cache, n, i, nbw, ar, ai);
+    ar[KB] = has_nr ? T(1) : T(0);
+    ai[KB] = T(0);
+    T xr = T(0), xi = T(0);
+#pragma unroll
+    for (int l = 0; l < KA; ++l)
+      if (l == krow) {
+        xr = ar[l];
+        xi = ai[l];
+      }
+#pragma unroll
+    for (int l = 0; l < KA; ++l) {
+      // A_k conj(A_l)
+      const T pr = xr * ar[l] + xi * ai[l];
+      const T pi = xi * ar[l] - xr * ai[l];
+      if constexpr (sizeof(T) == 4) {
+        kr[l].add(pr);
+        ki[l].add(pi);
+      } else {
+        dr[l] += pr;
+        di[l] += pi;
+      }
+    }
+  }
+  ddf v[NS];
+#pragma unroll
+  for (int l = 0; l < KA; ++l) {
+    v[2 * l] = (sizeof(T) == 4) ? kr[l].value() : dd_from_double(dr[l]);
+    v[2 * l + 1] = (sizeof(T) == 4) ? ki[l].value() : dd_from_double(di[l]);
+  }
+  const int nbx = gridDim.x;
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      ddf w = dd_warp_sum(v[s]);
+      if (lane == 0) s_red[warp * NS + s] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x < NS) {
+      ddf acc = s_red[threadIdx.x];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) acc = dd_add(acc, s_red[w * NS + threadIdx.x]);
+      partials[((size_t)k * nbx + blockIdx.x) * NS + threadIdx.x] = make_float2(acc.hi, acc.lo);
+    }
+  }
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(counters, 1u) == (unsigned)(nbx * gridDim.y - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  // G in model order: BW amplitudes 0..nbw-1, then NR at index nbw
+  const int K = nbw + (has_nr ? 1 : 0);
+  for (int lane_id = threadIdx.x; lane_id < (int)gridDim.y * NS; lane_id += blockDim.x) {
+    const int kk = lane_id / NS, s = lane_id % NS;
+    const int l = s / 2;
+    ddf acc = {0.f, 0.f};
+    for (int b = 0; b < nbx; ++b) {
+      const float2 p = __ldcg(partials + ((size_t)kk * nbx + b) * NS + s);
+      acc = dd_add(acc, {p.x, p.y});
+    }
+    const int krow_model = kk;                              // rows were launched in model order
+    const int lcol_model = l < nbw ? l : (l == KB ? nbw : -1);
+    // upper triangle from row k, mirrored with conjugation: G is Hermitian by construction
+    if (lcol_model >= krow_model && lcol_model < K && krow_model < K) {
+      double v = dd_to_double(acc) / (double)n;
+      if ((s & 1) && lcol_model == krow_model) v = 0.0;
+      gram_out[2 * (krow_model * K + lcol_model) + (s & 1)] = v;
+      gram_out[2 * (lcol_model * K + krow_model) + (s & 1)] = (s & 1) ? -v : v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *counters = 0u;
 }
 
 }  // namespace goo

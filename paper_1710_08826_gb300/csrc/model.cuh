@@ -53,7 +53,8 @@ struct ModelDev {
   double dlogN[kMaxComp][kMaxParams];  // d log N_k / d theta_p
 };
 
-struct DalitzModel;  // amplitude models (dalitz.cu)
+struct DalitzModel;  // three-body amplitude models (dalitz.cu)
+struct Td4Model;     // time-dependent four-body models (td4.cu)
 
 int build_sop_model(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_params, int n_obs,
                     const double* lo, const double* hi, goo_model* m);
@@ -76,20 +77,31 @@ int dalitz_gram(goo_model* m, const double* theta, int precision, double* out, i
 int dalitz_amplitudes(goo_model* m, const goo_dataset* ds, const double* theta, int precision, const void** cache,
                       int* nbw);
 
+int build_td4_model(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_params, int n_obs, goo_model* m);
+int td4_set_norm(goo_model* m, const goo_norm_spec* spec);
+void td4_free(goo_model* m);
+int td4_normalise(goo_model* m, const double* theta, int precision, double* norm_out);
+int td4_nll(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, const double* theta, int precision,
+            bool grad, double* out, int out_mode);
+int td4_eval_logf(goo_model* m, const goo_dataset* ds, const double* theta, int precision, double* logf_dev);
+int td4_gram(goo_model* m, int precision, double* out, int* K_out);
+int td4_amplitudes(goo_model* m, const goo_dataset* ds, int precision, const void** cache, int* n_amp);
+
 }  // namespace goo
 
 struct goo_model {
   goo_ctx* ctx = nullptr;
-  int kind = 0;  // 0: sum of products, 1: coherent amplitude sum
+  int kind = 0;  // 0: sum of products, 1: coherent amplitude sum, 2: time-dependent four-body
   int n_params = 0, n_obs = 0;
-  double lo[goo::kMaxObs] = {0, 0, 0, 0};
-  double hi[goo::kMaxObs] = {0, 0, 0, 0};
+  double lo[goo::kMaxCols] = {};
+  double hi[goo::kMaxCols] = {};
   goo_norm_spec norm{};
   int max_leaf = 0;
   goo::ModelDev host{};
   goo::ModelDev* dev = nullptr;
   goo::ModelDev* stage = nullptr;  // pinned host staging of the per-call model block
   goo::DalitzModel* dalitz = nullptr;
+  goo::Td4Model* td4 = nullptr;
 };
 
 namespace goo {

@@ -1357,6 +1357,8 @@ static int leaf_npar(int op) {
 
 int build_sop_model(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_params, int n_obs,
                     const double* lo, const double* hi, goo_model* m) {
+  if (n_obs > kMaxObs)
+    return set_error(GOO_ERR_UNSUPPORTED, "goo_model_build: a sum/product model has at most %d observables", kMaxObs);
   std::vector<int> add_ids;
   std::vector<Term> terms;
   GOO_TRY(flatten(nodes, n_nodes - 1, add_ids, terms));

@@ -17,7 +17,8 @@ GOO_OK, GOO_ERR_ARG, GOO_ERR_RANGE, GOO_ERR_CUDA, GOO_ERR_OOM = 0, -1, -2, -3, -
 GOO_ERR_NONPOSITIVE_PDF, GOO_ERR_TIMEOUT, GOO_ERR_STATE, GOO_ERR_UNSUPPORTED = -5, -6, -7, -8
 GOO_F64, GOO_F32 = 0, 1
 GOO_COPY, GOO_BORROW_DEVICE = 0, 1
-OP = dict(gauss=1, expo=2, poly2=3, argus=4, prod=10, add=11, bw=20, nr=21, coherent=22)
+OP = dict(gauss=1, expo=2, poly2=3, argus=4, prod=10, add=11, bw=20, nr=21, coherent=22, td4=23, amp4=24)
+ANG = dict(SS=0, VS0=1, SV0=2, VV0=3, VVpar=4, VVperp=5, TS0=6, TV0=7)
 NORM = dict(analytic=0, grid=1, mc=2)
 MAX_CHILD = 16
 PAIR_INDEX = {"12": 0, "13": 1, "23": 2}
@@ -105,6 +106,7 @@ def _load():
                                    ctypes.POINTER(GooFitResult)]),
         "goo_amplitude_cache": (ctypes.c_int, [vp, vp, dp, ctypes.c_int, ctypes.POINTER(vp),
                                                ctypes.POINTER(ctypes.c_int)]),
+        "goo_faddeeva": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -309,6 +311,27 @@ def spec_to_nodes(spec):
             for j, k in enumerate(kids):
                 n.child[j] = k
             for j, key in enumerate(["M", "m1", "m2", "m3", "r_res", "r_par"]):
+                n.dval[j] = float(kin[key])
+        elif op == "td4":
+            kin, amps, tpar = node[1], node[2], node[3]
+            kids = []
+            for ang, (m0a, ga), (m0b, gb), re, im, (cre, cim) in amps:
+                m = new()
+                m.op = OP["amp4"]
+                m.ival[0] = ANG[ang]
+                m.par[0], m.par[1] = pidx[re], pidx[im]
+                for j, v in enumerate((m0a, ga, m0b, gb, cre, cim)):
+                    m.dval[j] = float(v)
+                nodes.append(m)
+                kids.append(len(nodes) - 1)
+            n = new()
+            n.op = OP["td4"]
+            n.n_child = len(kids)
+            for j, k in enumerate(kids):
+                n.child[j] = k
+            for j, name in enumerate(tpar):
+                n.par[j] = pidx[name]
+            for j, key in enumerate(["M", "m1", "m2", "m3", "m4", "r_res"]):
                 n.dval[j] = float(kin[key])
         else:
             raise ValueError(f"unknown node {op}")
@@ -587,3 +610,11 @@ def combine_partials(parts, n_params):
 
 def version():
     return lib.goo_version().decode()
+
+
+def faddeeva(z, precision="f64"):
+    """The library's Faddeeva approximation w(z), Im z >= 0, evaluated on the host."""
+    out = np.zeros(2)
+    _check(lib.goo_faddeeva(float(np.real(z)), float(np.imag(z)), precision_code(precision),
+                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return complex(out[0], out[1])

@@ -62,3 +62,15 @@ def test_combine_partials_is_compensated_and_ordered():
     assert tot[2] == 150
     exact = [math.fsum(parts[:, 3 + j]) for j in range(P)]  # correctly rounded sums
     np.testing.assert_allclose(tot[3:], exact, rtol=4e-16, atol=0)
+
+
+def test_faddeeva_approximation_against_scipy():
+    from scipy.special import wofz
+    from paper_1710_08826_gb300 import goo
+    worst = {"f64": 0.0, "f32": 0.0}
+    for re in (0.0, 1e-4, 3e-3, 0.05, 0.5, 2.0, 5.0):
+        for im in np.concatenate([np.linspace(0, 10, 41), np.linspace(10, 200, 21)]):
+            ref = wofz(re + 1j * im)
+            for p in worst:
+                worst[p] = max(worst[p], abs(goo.faddeeva(re + 1j * im, p) - ref) / abs(ref))
+    assert worst["f64"] < 2e-14 and worst["f32"] < 2e-6, worst
