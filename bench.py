@@ -34,6 +34,7 @@ BYTES_PER_EVENT_F64 = 24
 # only while the kernel's sources still hash to the captured value; bytes scale with events.
 _SOP_SRC = ['paper_1710_08826_gb300/csrc/tree.cu', 'paper_1710_08826_gb300/csrc/common.cuh', 'paper_1710_08826_gb300/csrc/model.cuh']
 _COH_SRC = ['paper_1710_08826_gb300/csrc/dalitz.cu', 'paper_1710_08826_gb300/csrc/dalitz.cuh', 'paper_1710_08826_gb300/csrc/common.cuh', 'paper_1710_08826_gb300/csrc/model.cuh']
+_TD4_SRC = ['paper_1710_08826_gb300/csrc/td4.cu', 'paper_1710_08826_gb300/csrc/dalitz.cuh', 'paper_1710_08826_gb300/csrc/common.cuh', 'paper_1710_08826_gb300/csrc/model.cuh']
 NCU_RECORDS = {
     "sop_nll_grad_f32": {"bytes": 125_785_088, "events": 10_000_000, "sources": _SOP_SRC,
                          "sha256": "8dfab8aa796eadf45ce7f39879b46dadeeae283b22c1ba4f7854ef93258809d2",
@@ -47,6 +48,12 @@ NCU_RECORDS = {
     "coh_nll_f64": {"bytes": 643_364_352, "events": 5_000_000, "fp64_pipe": 0.8701, "sources": _COH_SRC,
                     "sha256": "b457246f0a0eadb7f6bcc854a759157881ccae15d5e3f7e00a959af08c1545f9",
                     "profile": "profiles/coh_nll_kernel_f64_c3_5M.md"},
+    "td4_nll_grad_f32": {"bytes": 171_191_040, "events": 2_000_000, "sources": _TD4_SRC,
+                         "sha256": "05ea2816e0b9096d1d47ffdabfd7ebb23dd40e6824a0b70795c464f6c12edd8f",
+                         "profile": "profiles/td4_nll_f32_kernel_c4_2M.md"},
+    "td4_nll_f64": {"bytes": 339_361_536, "events": 2_000_000, "fp64_pipe": 0.8663, "sources": _TD4_SRC,
+                    "sha256": "05ea2816e0b9096d1d47ffdabfd7ebb23dd40e6824a0b70795c464f6c12edd8f",
+                    "profile": "profiles/td4_nll_f64_kernel_c4_2M.md"},
 }
 
 
@@ -89,7 +96,7 @@ def parse():
     ap.add_argument("--toys", type=int, default=4096)
     ap.add_argument("--rate", type=float, default=1000.0, help="Poisson arrival rate of the second serving run")
     ap.add_argument("--profile", action="store_true", help="short fixed launch sequence for ncu captures")
-    ap.add_argument("--profile-workload", default="c2", choices=["c2", "c3", "c5"])
+    ap.add_argument("--profile-workload", default="c2", choices=["c2", "c3", "c4", "c5"])
     return ap.parse_args()
 
 
@@ -391,6 +398,7 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_extra:
         line["c3_dalitz"] = c3_measure(goo, ctx, stream, max(5, args.steps // 2))
+        line["c4_td4"] = c4_measure(goo, ctx, stream, max(5, args.steps // 2))
         line["c5_serving"] = c5_study(goo, ctx, n_toys=args.toys)
         line["c5_serving_poisson"] = c5_study(goo, ctx, n_toys=max(64, args.toys // 4), rate=args.rate, plain_sample=0)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -453,6 +461,81 @@ def c3_measure(goo, ctx, stream, steps, n_events=5_000_000, n_mc=1_000_000):
             "bound": "hbm" if grad else "fp64", "ncu": ncu_record(name, n_events),
             "what": ("goo_nll_grad, FP32 amplitude cache (64 B/event), adjoint gradient" if grad
                      else "goo_nll, FP64 amplitude cache (128 B/event)")}
+    return out
+
+
+# ---------------------------------------------------------------------------------------
+# time-dependent four-body workload (2M events, 3M-point MC normalisation)
+# ---------------------------------------------------------------------------------------
+def c4_inputs(n_events, n_mc, seed=1710004):
+    """Four-body phase-space events with decay times Exp(tau) smeared by N(0, sigma_t).
+
+    The events follow phase space and the lifetime, not the amplitude model: the per-event
+    work and the bytes read do not depend on where the events fall.
+    """
+    import numpy as np
+
+    import synth
+    spec = synth.c4_spec(n_mc=n_mc)
+    kin = dict(synth.TD4_MASSES)
+    tau, sig = synth.TD4_TIME["tau"], synth.TD4_TIME["sigma_t"]
+    tlo, thi = spec["observables"][5][1:]
+    data = synth.gen_c4_candidates(n_events, seed, kin, 1.0 / tau)
+    data["t"] = np.clip(synth.smear_times(data.pop("t_true"), sig, seed + 1), tlo, thi)
+    mc = synth.four_body_phase_space(n_mc, 1710014, **kin)
+    mc["t"] = np.zeros(n_mc)
+    return spec, synth.round_to_f32(data, spec), synth.round_to_f32(mc, spec)
+
+
+def c4_measure(goo, ctx, stream, steps, n_events=2_000_000, n_mc=3_000_000):
+    import numpy as np
+    import torch
+
+    import synth
+    spec, data, mc = c4_inputs(n_events, n_mc)
+    mcds = goo.Dataset.from_spec(ctx, spec, mc)
+    model = goo.Model(ctx, spec, mc=mcds)
+    ds = goo.Dataset.from_spec(ctx, spec, data)
+    theta = np.array(synth.param_values(spec))
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    out = {"workload": f"c4_td4: {n_events:,} four-body events (phase space, t = Exp(0.41 ps) + N(0, 0.05 ps)), "
+                       f"{n_mc:,}-point phase-space MC, 10 amplitudes, 24 free parameters (20 coefficients, x, y, "
+                       "tau, sigma_t)"}
+    nll = {}
+    for prec, grad, k in (("f32", True, steps), ("f64", False, max(3, steps // 5))):
+        for _ in range(3):
+            model.nll_grad(ds, theta, prec) if grad else model.nll(ds, theta, prec)
+        torch.cuda.synchronize()
+        ms = 0.0
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            v = model.nll_grad(ds, theta, prec)[0] if grad else model.nll(ds, theta, prec)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        nll[prec] = v
+        ctx.kernel_times(reset=True)
+        ctx.timing(True)
+        for _ in range(3):
+            flush.zero_()
+            model.nll_grad(ds, theta, prec) if grad else model.nll(ds, theta, prec)
+        ctx.timing(False)
+        kt = ctx.kernel_times(reset=True)
+        name, (cnt, kms) = max(kt.items(), key=lambda kv: kv[1][1])
+        bytes_per_event = 84 if prec == "f32" else 168   # amplitude planes + the time column
+        per = kms / cnt
+        out["f32_grad" if grad else "f64_plain"] = {
+            "evals_per_s": k / (ms * 1e-3), "events_per_s": n_events * k / (ms * 1e-3), "ms_per_eval": ms / k,
+            "kernel": name, "kernel_ms": per,
+            "hbm_frac": n_events * bytes_per_event / (per * 1e-3) / 1e9 / measured_peaks()[0],
+            "bound": "hbm" if grad else "fp64", "ncu": ncu_record(name, n_events),
+            "what": ("goo_nll_grad, FP32 amplitude cache (80 B/event) + time, adjoint gradient" if grad
+                     else "goo_nll, FP64 amplitude cache (160 B/event) + time")}
+    out["parity_this_run"] = {"nll_f32": nll["f32"], "nll_f64": nll["f64"],
+                              "rel": abs(nll["f32"] - nll["f64"]) / abs(nll["f64"])}
     return out
 
 
@@ -539,6 +622,8 @@ def run_profile(args):
     c2: [grid, event] x 4 FP32+grad evaluations, then one FP64 evaluation (10M events).
     c3: amplitude caches and Gram (first call), then 4 FP32+grad and 1 FP64 coherent
         evaluations on 5M events generated on the device.
+    c4: amplitude caches and Gram (first call), then 4 FP32+grad and 1 FP64 time-dependent
+        four-body evaluations on 2M events.
     c5: a served study of 64 toys (generation passes, then rounds of batched evaluation and
         minimiser updates).
     """
@@ -550,7 +635,15 @@ def run_profile(args):
     from paper_1710_08826_gb300 import goo
     ctx = goo.Context(0)
     w = args.profile_workload
-    if w == "c2":
+    if w == "c4":
+        spec, data, mc = c4_inputs(2_000_000, 3_000_000)
+        mcds = goo.Dataset.from_spec(ctx, spec, mc)
+        model = goo.Model(ctx, spec, mc=mcds)
+        ds = goo.Dataset.from_spec(ctx, spec, data)
+        theta = np.array(synth.param_values(spec))
+        out = [model.nll_grad(ds, theta, "f32")[0] for _ in range(4)]
+        out.append(model.nll(ds, theta, "f64"))
+    elif w == "c2":
         spec = synth.c2_spec(bins=GRID)
         cols = synth.gen_c2(n=args.events, seed=1710002)
         ds = goo.Dataset.from_spec(ctx, spec, cols, dtype="f64")

@@ -165,3 +165,33 @@ def test_fit_matches_oracle_fit(goo, ctx, sample):
     pulls = np.abs(th_gpu[idx] - th_ref[idx]) / err_ref[idx]
     assert np.max(pulls) < 0.01, pulls
     np.testing.assert_allclose(err_gpu[idx], err_ref[idx], rtol=0.02)
+
+
+def test_full_size_configuration(goo, ctx):
+    # 2,000,000 events and 3,000,000 MC points, the sizes and launch configuration the
+    # benchmark times (phase-space events with Exp(tau) (x) N(0, sigma_t) decay times)
+    spec = synth.c4_spec()
+    theta = np.array(synth.param_values(spec))
+    kin = dict(synth.TD4_MASSES)
+    tau, sig = synth.TD4_TIME["tau"], synth.TD4_TIME["sigma_t"]
+    data = synth.gen_c4_candidates(2_000_000, 1710004, kin, 1.0 / tau)
+    data["t"] = np.clip(synth.smear_times(data.pop("t_true"), sig, 1710005), *spec["observables"][5][1:])
+    mc = _mc_cols(3_000_000)
+    m = ot.TD4Model(spec)
+    th = theta * 1.01
+    for precision in ("f64", "f32"):
+        d, c = _prep(spec, data, mc, precision)
+        ds, _, model = _build(goo, ctx, spec, d, c)
+        nll, g = model.nll_grad(ds, th, precision)
+        a = m.amplitudes(d)
+        rnll, rg = m.nll_grad(d, m.amplitudes(c), th, a=a)
+        assert abs(nll - rnll) <= TOL_NLL[precision] * abs(rnll), (precision, nll, rnll)
+        if precision == "f64":
+            assert np.max(np.abs(g - rg)) <= TOL_GRAD["f64"] * np.max(np.abs(rg))
+        else:
+            # each per-event term d log R_i / d theta carries the FP32 evaluation's relative
+            # error (a few 1e-7 over ~30 operations); the terms of 2M events cancel heavily,
+            # so the bound scales with the sum of their magnitudes, not with the gradient
+            R, dR = m.rate(a, d["t"], th, derivs=True)
+            mag = np.sum(np.abs(dR / R[:, None]), axis=0)
+            assert np.all(np.abs(g - rg) <= 2e-6 * mag + TOL_GRAD["f32"] * np.max(np.abs(rg))), (g - rg, mag)
