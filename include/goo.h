@@ -140,6 +140,8 @@ typedef struct goo_model goo_model;
  * torch.cuda.current_stream().cuda_stream) or NULL for a stream the library creates.
  * All work of the context is ordered on that stream. */
 int goo_init(int device, void* cuda_stream, goo_ctx** out);
+/* goo_finalize fails with GOO_ERR_STATE (and frees nothing) while datasets, models or servers
+ * created on ctx are still alive: free them first. */
 int goo_finalize(goo_ctx* ctx);
 const char* goo_last_error(void);
 /* Library version string and the number of kernel launches issued so far by ctx. */

@@ -128,6 +128,8 @@ int goo_model_build(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_para
     goo_model_free(m);
     return rc;
   }
+  ctx->live++;
+  m->counted = true;
   *out = m;
   return GOO_OK;
 }
@@ -147,6 +149,7 @@ int goo_model_free(goo_model* m) {
   if (m->stage) cudaFreeHost(m->stage);
   if (m->dalitz) dalitz_free(m);
   if (m->td4) td4_free(m);
+  if (m->counted) m->ctx->live--;
   delete m;
   return GOO_OK;
 }

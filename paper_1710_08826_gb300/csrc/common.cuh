@@ -49,6 +49,11 @@ constexpr int kMaxCols = 8;        // columns of a dataset, observables of any m
 constexpr int kMaxComp = 4;        // products in the flattened sum of products
 constexpr int kMaxLeaf = 4;        // leaves per product
 constexpr int kMaxSlots = 64;      // reduction lanes of one kernel
+// Threads per block of the memory-bound coherent kernel, which streams its amplitude tiles
+// through shared memory: one block of 16 warps per SM, so that all warps of an SM draw on one
+// tile stream and finish together (two co-resident blocks of 8 warps drift apart by ~10 %;
+// the compute-bound staged kernels keep two 256-thread blocks, which measured faster).
+constexpr int kStagedBlock = 512;
 constexpr int kBlock = 256;        // threads per block of the likelihood kernels
 constexpr int kResultDoubles = 4 + kMaxParams + 60;  // result record of one evaluation
 constexpr int kPinnedResult = 256;                   // offset of the result in host_pinned
@@ -95,6 +100,7 @@ struct goo_ctx {
   bool owns_stream = false;
   int num_sms = 0;
   int64_t launches = 0;
+  int live = 0;  // datasets, models and servers created on this context and not yet freed
   goo::Scratch scratch;
   bool timing = false;
   std::vector<goo::TimedLaunch> pending;

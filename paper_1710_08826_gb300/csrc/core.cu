@@ -230,6 +230,8 @@ int goo_init(int device, void* cuda_stream, goo_ctx** out) {
 
 int goo_finalize(goo_ctx* ctx) {
   if (!ctx) return set_error(GOO_ERR_ARG, "goo_finalize: NULL context");
+  if (ctx->live > 0)
+    return set_error(GOO_ERR_STATE, "goo_finalize: %d datasets, models or servers of this context are not freed", ctx->live);
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   Scratch& s = ctx->scratch;
@@ -336,6 +338,7 @@ int goo_dataset_upload(goo_ctx* ctx, int ncols, const void* const* cols, int dty
   } else {
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return fail(GOO_ERR_CUDA, "stream sync failed");
   }
+  ctx->live++;
   *out = ds;
   return GOO_OK;
 }
@@ -345,6 +348,7 @@ int goo_dataset_free(goo_dataset* ds) {
   cudaSetDevice(ds->ctx->device);
   cudaStreamSynchronize(ds->ctx->stream);
   free_dataset_memory(ds);
+  ds->ctx->live--;
   delete ds;
   return GOO_OK;
 }

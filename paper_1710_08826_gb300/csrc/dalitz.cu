@@ -296,11 +296,11 @@ __global__ void __launch_bounds__(kBlock, 2) coh_nll_kernel(const __grid_constan
 // issues a bulk copy per plane kCohStages tiles ahead, and block b takes tiles
 // tb0 + b, tb0 + b + gridDim.x, ...  Ragged first / last tiles are read from global memory.
 // Dynamic shared memory: kCohStages * n_planes * kCohTile float4.
-constexpr int kCohTile = 512;
+constexpr int kCohTile = kStagedBlock;  // one event per thread per tile
 constexpr int kCohStages = 3;
 
 template <int KB, bool GRAD>
-__global__ void __launch_bounds__(kBlock, 2) coh_nll_staged_kernel(const __grid_constant__ CohArgs<float> a,
+__global__ void __launch_bounds__(kStagedBlock, 1) coh_nll_staged_kernel(const __grid_constant__ CohArgs<float> a,
                                                                    const float4* __restrict__ cache, int64_t begin,
                                                                    int64_t end, const double* __restrict__ gram,
                                                                    float2* partials, unsigned* counters, double* result,
@@ -309,8 +309,8 @@ __global__ void __launch_bounds__(kBlock, 2) coh_nll_staged_kernel(const __grid_
   constexpr int KA = KB + 1;
   constexpr int TE = kCohTile;
   constexpr int NST = kCohStages;
-  __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
-  __shared__ unsigned s_bad[kBlock / 32];
+  __shared__ ddf s_red[(kStagedBlock / 32) * NS > kStagedBlock ? (kStagedBlock / 32) * NS : kStagedBlock];
+  __shared__ unsigned s_bad[kStagedBlock / 32];
   __shared__ __align__(8) uint64_t s_bar[NST];
   extern __shared__ __align__(128) float4 s_amp[];  // [NST][planes][TE]
   const int nbw = a.nbw;
@@ -649,7 +649,7 @@ static int launch_coh_staged(goo_model* m, const void* cache, const goo_dataset*
     configured[ctx->device] = true;
   }
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, coh_nll_staged_kernel<KB, GRAD>, kBlock, smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, coh_nll_staged_kernel<KB, GRAD>, kStagedBlock, smem) != cudaSuccess ||
       occ < 1) {
     cudaGetLastError();
     occ = 1;
@@ -662,7 +662,7 @@ static int launch_coh_staged(goo_model* m, const void* cache, const goo_dataset*
   fill_args<float>(d, theta, m->n_params, ds->n, a);
   {
     LaunchScope ls(ctx, GRAD ? "coh_nll_grad_f32" : "coh_nll_f32");
-    coh_nll_staged_kernel<KB, GRAD><<<nb, kBlock, smem, ctx->stream>>>(a, (const float4*)cache, begin, end,
+    coh_nll_staged_kernel<KB, GRAD><<<nb, kStagedBlock, smem, ctx->stream>>>(a, (const float4*)cache, begin, end,
                                                                        d.gram_dev[pi], ctx->scratch.partials,
                                                                        ctx->scratch.counters, ctx->scratch.result,
                                                                        out_mode);

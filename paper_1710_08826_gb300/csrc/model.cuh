@@ -102,6 +102,7 @@ struct goo_model {
   goo::ModelDev* stage = nullptr;  // pinned host staging of the per-call model block
   goo::DalitzModel* dalitz = nullptr;
   goo::Td4Model* td4 = nullptr;
+  bool counted = false;  // included in ctx->live
 };
 
 namespace goo {

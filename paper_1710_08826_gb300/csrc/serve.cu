@@ -902,6 +902,7 @@ struct goo_server {
   int* d_slots = nullptr;
   int* d_done = nullptr;
   unsigned* d_done_count = nullptr;
+  bool counted = false;  // included in ctx->live
   int2* d_tiles = nullptr;
   size_t tiles_cap = 0;
   float2* d_tile_partials = nullptr;
@@ -1329,6 +1330,8 @@ int goo_server_create(goo_model* model, const double* theta_gen, const int* free
     s->opt.fmax = g.fmax;
   }
   GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  s->ctx->live++;
+  s->counted = true;
   *out = s;
   return GOO_OK;
 }
@@ -1441,6 +1444,7 @@ int goo_server_free(goo_server* s) {
                   s->d_gtoys, s->d_bprefix, s->d_counts, s->d_outbase, s->d_accepted, s->d_masks};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (s->counted) s->ctx->live--;
   delete s;
   return GOO_OK;
 }

@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(kBlock, 2) td4_nll_f64_kernel(const __grid_con
 // and of the time column staged in shared memory by bulk copies, kTdStages tiles ahead;
 // block b takes tiles tb0 + b, + gridDim.x, ...; ragged first / last tiles read global
 // memory.  Dynamic shared memory: kTdStages * (planes * kTdTile float4 + kTdTile float).
-constexpr int kTdTile = 256;
+constexpr int kTdTile = kBlock;  // one event per thread per tile
 constexpr int kTdStages = 4;
 
 template <int KB, bool GRAD>
