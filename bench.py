@@ -426,7 +426,7 @@ def c3_measure(goo, ctx, stream, steps, n_events=5_000_000, n_mc=1_000_000):
     model = goo.Model(ctx, spec, mc=mcds)
     theta = np.array(synth.param_values(spec))
     t0 = time.perf_counter()
-    a, b = goo.toy_generate(model, theta, 0.0, 1710003, n_events)   # accept-reject on the device
+    a, b = goo.toy_generate(model, theta, None, 1710003, n_events)   # accept-reject on the device
     gen_s = time.perf_counter() - t0
     ds = goo.Dataset.from_spec(ctx, spec, {"s12": a.astype(np.float64), "s13": b.astype(np.float64)})
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
@@ -594,14 +594,16 @@ def c5_study(goo, ctx, n_toys=4096, rate=None, plain_sample=8, n_mc=1_000_000, s
     out = {"toys": n_toys, "events_total": int(sizes.sum()), "arrival": "all at once" if rate is None
            else f"Poisson, {rate:g} fits/s", "wall_s": wall, "fits_per_s": n_toys / wall,
            "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
-           "rounds": int(stats["rounds"]), "generation_s": stats["gen_ms"] / 1e3, "converged": int((statuses == 0).sum())}
+           "rounds": int(stats["rounds"]), "generation_s": stats["gen_ms"] / 1e3,
+           "generator_acceptance": stats["accepted"] / max(stats["candidates"], 1.0),
+           "envelope_violations": int(stats["envelope_violations"]), "converged": int((statuses == 0).sum())}
     if plain_sample:
         # the plain form: per-fit serial FP64 with the finite-difference gradient, same toys
         sample = list(range(plain_sample))
         t_plain = 0.0
         worst = 0.0
         for i in sample:
-            a, b = goo.toy_generate(model, theta, stats["fmax"], seed0 + i, int(sizes[i]))
+            a, b = goo.toy_generate(model, theta, None, seed0 + i, int(sizes[i]))  # the server's toys
             ds = goo.Dataset.from_spec(ctx, spec, {"s12": a.astype(np.float64), "s13": b.astype(np.float64)})
             model.nll(ds, theta, "f64")   # builds the FP64 amplitude cache outside the timing
             tp = time.perf_counter()
@@ -660,7 +662,7 @@ def run_profile(args):
         model = goo.Model(ctx, spec, mc=mcds)
         theta = np.array(synth.param_values(spec))
         if w == "c3":
-            a, b = goo.toy_generate(model, theta, 0.0, 1710003, 5_000_000)
+            a, b = goo.toy_generate(model, theta, None, 1710003, 5_000_000)
             ds = goo.Dataset.from_spec(ctx, spec, {"s12": a.astype(np.float64), "s13": b.astype(np.float64)})
             out = [model.nll_grad(ds, theta, "f32")[0] for _ in range(4)]
             out.append(model.nll(ds, theta, "f64"))

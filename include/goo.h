@@ -246,8 +246,8 @@ int goo_fit(goo_model* model, const goo_dataset* ds, double* theta, const int* f
  * For an amplitude model with a non-resonant reference amplitude, <= 8 resonances, fixed
  * lineshapes and an MC normalisation sample.  A request is one pseudo-experiment: n_events
  * generated on the device from the model at theta_gen (Philox4x64-10 streams keyed by `seed`,
- * accept-reject against the envelope fmax; the toy is the first n accepted candidates in
- * candidate order), then fitted from theta_start (NULL: theta_gen) over the resonance
+ * accept-reject against the cell envelope below; the toy is the first n accepted candidates
+ * in candidate order), then fitted from theta_start (NULL: theta_gen) over the resonance
  * coefficients (free_mask must mark exactly those).  Requests are admitted in submission
  * order while a fit slot and 72 bytes per event of the device arena are free.  Each
  * goo_server_step admits and generates new fits, runs ONE batched NLL+gradient launch over
@@ -255,9 +255,21 @@ int goo_fit(goo_model* model, const goo_dataset* ds, double* theta, const int* f
  * does not depend on the other fits in the batch) and ONE launch advancing every fit's
  * device-resident minimiser (BFGS, then Newton steps on a finite-difference Hessian whose
  * inverse gives the errors), then retires finished fits.  goo_server_result returns
- * GOO_ERR_STATE until the fit is finished.  stats: [rounds, evaluation ms, generation ms,
- * candidates, accepted, fmax, arena bytes, arena bytes in use]. */
+ * GOO_ERR_STATE until the fit is finished.  stats: see goo_server_stats. */
 typedef struct goo_server goo_server;
+/* Envelope of the toy generator: an n12 x n13 grid of equal cells over the Dalitz box
+ * [(m1+m2)^2, (M-m3)^2] x [(m1+m3)^2, (M-m2)^2], cell (i, j) at index i * n13 + j, with
+ * bound[c] >= |S|^2 at every point of cell c inside the kinematic region.  Candidate j of a
+ * toy with seed s uses the Philox4x64-10 words w0..w3 at counter (j, 0, 0, 0), key
+ * (s, 0x6f6f67): the cell is the first c with (w0 >> 32) < thr[c], thr[c] =
+ * floor(S_c / W * 2^32) (S_c the FP64 sum of bound[0..c], W the total; thr[last] = 2^32);
+ * s12 = lo12 + (i + u(w1)) cw12 and s13 = lo13 + (j + u(w2)) cw13 in float32
+ * (u(w) = (w >> 40) 2^-24, cw = (float)(box width / cells)); accepted when the point is in
+ * the kinematic region and u(w3) * bound[c] < |S|^2 (float32). */
+typedef struct goo_envelope {
+  int32_t n12, n13;
+  const float* bound;       /* n12 * n13 values                                            */
+} goo_envelope;
 typedef struct goo_server_options {
   int64_t hbm_budget_bytes; /* event arena (<= 0: half of the free device memory)           */
   int32_t max_fits;         /* fit slots (<= 0: 4096)                                       */
@@ -265,7 +277,8 @@ typedef struct goo_server_options {
   int32_t max_iter;         /* BFGS iterations per fit (<= 0: 200)                          */
   int32_t pad;
   double edm_tol;           /* (<= 0: 1e-6)                                                 */
-  double fmax;              /* generator envelope (<= 0: 1.2 x the maximum on a 1024^2 grid) */
+  const goo_envelope* envelope; /* NULL: 1.2 x the 3x3-neighbourhood maximum of |S|^2 over a
+                               96 x 96 grid, 6 x 6 lattice points per cell                 */
 } goo_server_options;
 int goo_server_create(goo_model* model, const double* theta_gen, const int* free_mask, const double* scale,
                       const goo_server_options* options, goo_server** out);
@@ -274,14 +287,18 @@ int goo_server_submit(goo_server* server, int64_t n_events, uint64_t seed, const
 int goo_server_step(goo_server* server, int* n_queued, int* n_active, int* n_done);
 int goo_server_result(goo_server* server, int64_t ticket, double* theta_out, double* errors_out,
                       goo_fit_result* res);
-int goo_server_stats(const goo_server* server, double* out /* 8 doubles */);
+/* out[0..8]: evaluation rounds, evaluation ms, generation ms, candidates drawn, candidates
+   accepted, largest envelope bound, arena bytes, arena bytes in use, and the candidates inside
+   the region whose |S|^2 exceeded their cell's bound (non-zero: the envelope is too low there
+   and the toys under-populate those points). */
+int goo_server_stats(const goo_server* server, double* out /* 9 doubles */);
 int goo_server_free(goo_server* server);
 /* Toys from the same generator, written to host float arrays: one toy, or n_toys toys
  * generated together (toy i at offset n[0] + ... + n[i-1]); a toy does not depend on the
  * others it is generated with. */
-int goo_toy_generate(goo_model* model, const double* theta, double fmax, uint64_t seed, int64_t n_events,
-                     float* s12_out, float* s13_out);
-int goo_toys_generate(goo_model* model, const double* theta, double fmax, int n_toys, const uint64_t* seeds,
+int goo_toy_generate(goo_model* model, const double* theta, const goo_envelope* env, uint64_t seed,
+                     int64_t n_events, float* s12_out, float* s13_out);
+int goo_toys_generate(goo_model* model, const double* theta, const goo_envelope* env, int n_toys, const uint64_t* seeds,
                       const int64_t* n_events, float* s12_out, float* s13_out);
 /* NLL and gradient of n_fits (dataset, theta) pairs of one amplitude model in one launch
  * (FP32 path); theta: n_fits x n_params, nll_out: n_fits, grad_out: n_fits x n_params.  The

@@ -7,8 +7,8 @@ constants.  Written here from that published definition in plain Python integers
 tests/test_oracle_philox.py against numpy's independent Philox bit generator.
 
 The toy generator's streams: event candidate j of a toy with seed s uses
-counter (j, 0, 0, 0) and key (s, 0x6f6f67); its four outputs give u = (w >> 11) * 2^-53
-uniforms for s12, s13 and the acceptance test (the fourth is unused).
+counter (j, 0, 0, 0) and key (s, 0x6f6f67); the first output picks an envelope cell and the
+other three give the point in the cell and the acceptance uniform (oracle/toys.py).
 """
 M0 = 0xD2E7470EE14C6C93
 M1 = 0xCA5A826395121157

@@ -9,9 +9,11 @@
 //     amplitude cache) from one device arena; requests are admitted in arrival order while
 //     a fit slot and arena space are free;
 //   * generation (on the device): candidate j of a toy with seed s draws Philox4x64-10
-//     (Salmon et al., SC'11) outputs at counter (j,0,0,0), key (s, 0x6f6f67); 24-bit float
-//     uniforms give s12, s13 uniform over the Dalitz box and the acceptance test
-//     u * fmax < |S(s12, s13)|^2 (truth coefficients); the toy is the first n accepted
+//     (Salmon et al., SC'11) outputs w0..w3 at counter (j,0,0,0), key (s, 0x6f6f67); the top
+//     32 bits of w0 pick a cell of an envelope grid over the Dalitz box with probability
+//     proportional to the cell's bound on |S|^2 (importance sampling), 24-bit float uniforms
+//     from w1, w2 place the point in the cell, and it is accepted when
+//     u(w3) * bound < |S(s12, s13)|^2 (truth coefficients); the toy is the first n accepted
 //     candidates in candidate order, so it does not depend on how toys are batched;
 //   * one batched launch per round evaluates NLL and gradient of every active fit at its
 //     current trial point; each fit is split into fixed tiles whose partial sums are
@@ -41,6 +43,9 @@ constexpr int kSrvLanes = 1 + 2 * kSrvKA;   // sum log|S|^2 and 2 lanes per ampl
 constexpr int kGenPerThread = 16;
 constexpr int kGenBlockCands = kBlock * kGenPerThread;
 constexpr uint64_t kToyKey1 = 0x6F6F67ull;
+constexpr int kEnvCells = 96;     // default envelope grid: kEnvCells x kEnvCells cells
+constexpr int kEnvSub = 6;        // lattice points per cell side of the envelope scan
+constexpr float kEnvFactor = 1.2f;  // default bound: factor x the 3 x 3 neighbourhood maximum
 
 // ---------------------------------------------------------------------------------------
 // Philox4x64-10
@@ -69,12 +74,18 @@ __device__ __forceinline__ float u24(uint64_t w) { return (float)(uint32_t)(w >>
 // ---------------------------------------------------------------------------------------
 // toy generation
 // ---------------------------------------------------------------------------------------
+// Generator constants.  Proposal: a cell (i, j) of an n12 x n13 grid over the Dalitz box,
+// chosen by the top 32 bits of the first Philox word against cumulative thresholds thr[]
+// (cell c has probability (thr[c] - thr[c-1]) / 2^32, proportional to its envelope bound), a
+// point uniform in the cell, and acceptance u * bound[cell] < |S|^2.
 struct GenConst {
-  float lo12, w12, lo13, w13;   // box (float)
-  float M2, m1s, m2s, m3s;      // squared masses (float) for the inside test
-  float fmax;
-  float cr[kSrvKA], ci[kSrvKA]; // generating coefficients (slots: resonances, then reference)
-  int nbw;
+  float lo12, lo13, cw12, cw13;  // box corner and cell widths (float)
+  float M2, m1s, m2s, m3s;       // squared masses (float) for the inside test
+  float cr[kSrvKA], ci[kSrvKA];  // generating coefficients (slots: resonances, then reference)
+  int nbw, n12, n13, pad;
+  const float* bound;                   // per-cell envelope of |S|^2 (device)
+  const unsigned long long* thr;        // per-cell cumulative thresholds (device)
+  unsigned long long* viol;             // candidates inside the region with |S|^2 > bound (device)
 };
 
 // One toy of a generation pass: candidates [cand0, cand0 + nblocks * kGenBlockCands) in
@@ -87,15 +98,24 @@ struct GenToy {
   float4* cache;
 };
 
-// Candidate j: (s12, s13), inside test and acceptance; the amplitudes of an accepted
-// candidate are returned in (ar, ai).
-__device__ __forceinline__ bool gen_candidate(const GenConst& g, const DalitzDev& dd, uint64_t seed, int64_t j,
-                                              float& s12, float& s13, float (&ar)[kSrvKB], float (&ai)[kSrvKB]) {
+// Candidate j of the toy with this seed: its point, its cell's bound and u * bound (the
+// acceptance threshold); false when the point lies outside the kinematic region.
+__device__ __forceinline__ bool gen_point(const GenConst& g, uint64_t seed, int64_t j, float& s12, float& s13,
+                                          float& bnd, float& ub) {
   uint64_t c[4] = {(uint64_t)j, 0ull, 0ull, 0ull};
   philox4x64(c, seed, kToyKey1);
-  s12 = __fadd_rn(g.lo12, __fmul_rn(u24(c[0]), g.w12));
-  s13 = __fadd_rn(g.lo13, __fmul_rn(u24(c[1]), g.w13));
-  const float ua = u24(c[2]);
+  const unsigned long long top = c[0] >> 32;
+  int lo = 0, hi = g.n12 * g.n13 - 1;  // first cell with top < thr[cell]; thr[last] = 2^32
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (top < __ldg(g.thr + mid)) hi = mid;
+    else lo = mid + 1;
+  }
+  const int ci = lo / g.n13, cj = lo - ci * g.n13;
+  s12 = __fadd_rn(g.lo12, __fmul_rn(__fadd_rn((float)ci, u24(c[1])), g.cw12));
+  s13 = __fadd_rn(g.lo13, __fmul_rn(__fadd_rn((float)cj, u24(c[2])), g.cw13));
+  bnd = __ldg(g.bound + lo);
+  ub = __fmul_rn(u24(c[3]), bnd);
   // inside the Dalitz region: s13 range at fixed s12 from the energies of particles 1 and 3
   // in the (12) rest frame
   const float r = sqrtf(s12);
@@ -104,7 +124,15 @@ __device__ __forceinline__ bool gen_candidate(const GenConst& g, const DalitzDev
   const float p1 = sqrtf(fmaxf(e1 * e1 - g.m1s, 0.f));
   const float p3 = sqrtf(fmaxf(e3 * e3 - g.m3s, 0.f));
   const float es = (e1 + e3) * (e1 + e3);
-  if (!(s13 > es - (p1 + p3) * (p1 + p3) && s13 < es - (p1 - p3) * (p1 - p3) && e3 > sqrtf(g.m3s))) return false;
+  return s13 > es - (p1 + p3) * (p1 + p3) && s13 < es - (p1 - p3) * (p1 - p3) && e3 > sqrtf(g.m3s);
+}
+
+// Candidate j: point and acceptance; the amplitudes of an accepted candidate are returned in
+// (ar, ai).
+__device__ __forceinline__ bool gen_candidate(const GenConst& g, const DalitzDev& dd, uint64_t seed, int64_t j,
+                                              float& s12, float& s13, float (&ar)[kSrvKB], float (&ai)[kSrvKB]) {
+  float bnd, ub;
+  if (!gen_point(g, seed, j, s12, s13, bnd, ub)) return false;
   const float s23 = (float)(dd.sumsq - (double)s12 - (double)s13);
   float sr = g.cr[kSrvKB], si = g.ci[kSrvKB];  // reference amplitude A = 1
 #pragma unroll
@@ -117,23 +145,15 @@ __device__ __forceinline__ bool gen_candidate(const GenConst& g, const DalitzDev
       ar[k] = ai[k] = 0.f;
     }
   }
-  return __fmul_rn(ua, g.fmax) < sr * sr + si * si;
+  return ub < sr * sr + si * si;
 }
 
-// Acceptance of candidate j only (the amplitudes are summed on the fly, not kept).
-__device__ __forceinline__ bool gen_accept(const GenConst& g, const DalitzDev& dd, uint64_t seed, int64_t j) {
-  uint64_t c[4] = {(uint64_t)j, 0ull, 0ull, 0ull};
-  philox4x64(c, seed, kToyKey1);
-  const float s12 = __fadd_rn(g.lo12, __fmul_rn(u24(c[0]), g.w12));
-  const float s13 = __fadd_rn(g.lo13, __fmul_rn(u24(c[1]), g.w13));
-  const float ua = u24(c[2]);
-  const float r = sqrtf(s12);
-  const float e1 = (s12 + g.m1s - g.m2s) / (2.f * r);
-  const float e3 = (g.M2 - s12 - g.m3s) / (2.f * r);
-  const float p1 = sqrtf(fmaxf(e1 * e1 - g.m1s, 0.f));
-  const float p3 = sqrtf(fmaxf(e3 * e3 - g.m3s, 0.f));
-  const float es = (e1 + e3) * (e1 + e3);
-  if (!(s13 > es - (p1 + p3) * (p1 + p3) && s13 < es - (p1 - p3) * (p1 - p3) && e3 > sqrtf(g.m3s))) return false;
+// Acceptance of candidate j only (the amplitudes are summed on the fly, not kept); nviol counts
+// candidates whose |S|^2 exceeds their cell's bound (the envelope does not bound |S|^2 there).
+__device__ __forceinline__ bool gen_accept(const GenConst& g, const DalitzDev& dd, uint64_t seed, int64_t j,
+                                           unsigned& nviol) {
+  float s12, s13, bnd, ub;
+  if (!gen_point(g, seed, j, s12, s13, bnd, ub)) return false;
   const float s23 = (float)(dd.sumsq - (double)s12 - (double)s13);
   float sr = g.cr[kSrvKB], si = g.ci[kSrvKB];
   for (int k = 0; k < g.nbw; ++k) {
@@ -142,7 +162,9 @@ __device__ __forceinline__ bool gen_accept(const GenConst& g, const DalitzDev& d
     sr += g.cr[k] * ar - g.ci[k] * ai;
     si += g.cr[k] * ai + g.ci[k] * ar;
   }
-  return __fmul_rn(ua, g.fmax) < sr * sr + si * si;
+  const float s2 = sr * sr + si * si;
+  nviol += s2 > bnd ? 1u : 0u;
+  return ub < s2;
 }
 
 __device__ __forceinline__ int gen_find_toy(const int64_t* __restrict__ bprefix, int ntoys, int64_t b) {
@@ -172,10 +194,14 @@ __global__ void __launch_bounds__(kBlock, 2) toy_count_kernel(const __grid_const
   const int t = gen_find_toy(bprefix, ntoys, blockIdx.x);
   const GenToy& T = toys[t];
   const int64_t first = T.cand0 + (int64_t)(blockIdx.x - bprefix[t]) * kGenBlockCands + (int64_t)threadIdx.x * kGenPerThread;
-  unsigned mask = 0;
+  unsigned mask = 0, nviol = 0;
   for (int r = 0; r < kGenPerThread; ++r)
-    if (gen_accept(g, dd, T.seed, first + r)) mask |= 1u << r;
+    if (gen_accept(g, dd, T.seed, first + r, nviol)) mask |= 1u << r;
   masks[(size_t)blockIdx.x * kBlock + threadIdx.x] = (unsigned short)mask;
+  if (__any_sync(0xffffffffu, nviol != 0)) {
+    for (int m = 16; m > 0; m >>= 1) nviol += __shfl_xor_sync(0xffffffffu, nviol, m);
+    if ((threadIdx.x & 31) == 0 && nviol) atomicAdd(g.viol, (unsigned long long)nviol);
+  }
   unsigned cnt = __popc(mask);
   for (int m = 16; m > 0; m >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, m);
   if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = cnt;
@@ -821,21 +847,27 @@ __global__ void srv_bfgs_kernel(SrvState* states, SrvEval* evals, const SrvResul
 }
 
 // ---------------------------------------------------------------------------------------
-// envelope of the generator: max |S|^2 over a grid of the Dalitz region (float32)
+// envelope of the generator: per cell of the n12 x n13 grid, the largest |S|^2 (float32) on
+// a sub x sub lattice of points (cell edges included) inside the kinematic region, and the
+// lattice sum of |S|^2 (points outside the region count 0) for the acceptance estimate
 // ---------------------------------------------------------------------------------------
-__global__ void envelope_kernel(const __grid_constant__ GenConst g, const DalitzDev* ddp, int n, unsigned* out_bits) {
+__global__ void envelope_cells_kernel(const __grid_constant__ GenConst g, const DalitzDev* ddp, int sub,
+                                      unsigned* cell_bits, float* cell_sum) {
   __shared__ DalitzDev dd;
   for (int i = threadIdx.x; i < (int)(sizeof(DalitzDev) / 4); i += blockDim.x) ((int*)&dd)[i] = ((const int*)ddp)[i];
   __syncthreads();
-  float best = 0.f;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * n; idx += gridDim.x * blockDim.x) {
-    const float s12 = g.lo12 + g.w12 * ((idx / n) + 0.5f) / n;
-    const float s13 = g.lo13 + g.w13 * ((idx % n) + 0.5f) / n;
+  const int ncell = g.n12 * g.n13, per = sub * sub;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)ncell * per;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int cell = (int)(idx / per), q = (int)(idx % per);
+    const int ci = cell / g.n13, cj = cell % g.n13;
+    const float s12 = g.lo12 + g.cw12 * (ci + (float)(q / sub) / (sub - 1));
+    const float s13 = g.lo13 + g.cw13 * (cj + (float)(q % sub) / (sub - 1));
     const float r = sqrtf(s12);
     const float e1 = (s12 + g.m1s - g.m2s) / (2.f * r), e3 = (g.M2 - s12 - g.m3s) / (2.f * r);
     const float p1 = sqrtf(fmaxf(e1 * e1 - g.m1s, 0.f)), p3 = sqrtf(fmaxf(e3 * e3 - g.m3s, 0.f));
     const float es = (e1 + e3) * (e1 + e3);
-    if (!(s13 > es - (p1 + p3) * (p1 + p3) && s13 < es - (p1 - p3) * (p1 - p3))) continue;
+    if (!(s13 >= es - (p1 + p3) * (p1 + p3) && s13 <= es - (p1 - p3) * (p1 - p3))) continue;
     const float s23 = (float)(dd.sumsq - (double)s12 - (double)s13);
     float sr = g.cr[kSrvKB], si = g.ci[kSrvKB];
     for (int k = 0; k < g.nbw; ++k) {
@@ -844,10 +876,9 @@ __global__ void envelope_kernel(const __grid_constant__ GenConst g, const Dalitz
       sr += g.cr[k] * ar - g.ci[k] * ai;
       si += g.cr[k] * ai + g.ci[k] * ar;
     }
-    best = fmaxf(best, sr * sr + si * si);
+    atomicMax(cell_bits + cell, __float_as_uint(sr * sr + si * si));  // positive floats order as integers
+    atomicAdd(cell_sum + cell, sr * sr + si * si);
   }
-  for (int m = 16; m > 0; m >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, m));
-  if ((threadIdx.x & 31) == 0) atomicMax(out_bits, __float_as_uint(best));  // positive floats order as integers
 }
 
 // ---------------------------------------------------------------------------------------
@@ -903,6 +934,11 @@ struct goo_server {
   int* d_done = nullptr;
   unsigned* d_done_count = nullptr;
   bool counted = false;  // included in ctx->live
+  float* d_env_bound = nullptr;
+  unsigned long long* d_env_thr = nullptr;
+  unsigned* d_env_bits = nullptr;      // per-cell lattice maxima (float bits), then sums, then the
+                                       // violation counter
+  double env_max = 0.0, gen_violations = 0.0;
   int2* d_tiles = nullptr;
   size_t tiles_cap = 0;
   float2* d_tile_partials = nullptr;
@@ -1045,9 +1081,12 @@ static int generate(goo_server* s, const std::vector<int>& new_slots) {
     }
     GOO_CUDA_TRY(cudaGetLastError());
     std::vector<int64_t> acc(2 * nt);
+    unsigned long long viol = 0;
     GOO_CUDA_TRY(cudaMemcpyAsync(acc.data(), s->d_accepted, 2 * nt * sizeof(int64_t), cudaMemcpyDeviceToHost,
                                  ctx->stream));
+    GOO_CUDA_TRY(cudaMemcpyAsync(&viol, s->gen.viol, sizeof viol, cudaMemcpyDeviceToHost, ctx->stream));
     GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    s->gen_violations = (double)viol;
     if (log_level() >= 3) {
       std::vector<unsigned> cnt(nblocks);
       std::vector<int> ob(nblocks);
@@ -1298,9 +1337,7 @@ int goo_server_create(goo_model* model, const double* theta_gen, const int* free
   // generator constants
   GenConst& g = s->gen;
   g.lo12 = (float)info.lo12;
-  g.w12 = (float)(info.hi12 - info.lo12);
   g.lo13 = (float)info.lo13;
-  g.w13 = (float)(info.hi13 - info.lo13);
   g.M2 = (float)(info.M * info.M);
   g.m1s = (float)(info.m1 * info.m1);
   g.m2s = (float)(info.m2 * info.m2);
@@ -1312,23 +1349,87 @@ int goo_server_create(goo_model* model, const double* theta_gen, const int* free
   }
   g.cr[kSrvKB] = (float)theta_gen[info.par_re[info.nbw]];
   g.ci[kSrvKB] = (float)theta_gen[info.par_im[info.nbw]];
-  if (o.fmax > 0) {
-    g.fmax = (float)o.fmax;
-  } else {
-    unsigned* bits = ctx->scratch.counters + 16;
-    GOO_CUDA_TRY(cudaMemsetAsync(bits, 0, sizeof(unsigned), ctx->stream));
-    {
-      LaunchScope ls(ctx, "toy_envelope");
-      envelope_kernel<<<ctx->num_sms * 4, kBlock, 0, ctx->stream>>>(g, (const DalitzDev*)info.dalitz_dev, 1024, bits);
-    }
-    unsigned hb = 0;
-    GOO_CUDA_TRY(cudaMemcpyAsync(&hb, bits, sizeof hb, cudaMemcpyDeviceToHost, ctx->stream));
-    GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-    float mx;
-    std::memcpy(&mx, &hb, sizeof mx);
-    g.fmax = 1.2f * mx;
-    s->opt.fmax = g.fmax;
+  // generator envelope: given, or kEnvFactor x the 3 x 3 neighbourhood maximum of |S|^2 on a
+  // kEnvCells^2 grid of cells (kEnvSub^2 lattice points per cell).  The lattice scan runs for
+  // a given envelope too: its per-cell sums estimate the acceptance of the first pass.
+  const int n12 = o.envelope ? o.envelope->n12 : kEnvCells, n13 = o.envelope ? o.envelope->n13 : kEnvCells;
+  if (n12 < 1 || n13 < 1 || n12 > 1024 || n13 > 1024 || (o.envelope && !o.envelope->bound)) {
+    goo_server_free(s);
+    return set_error(GOO_ERR_ARG, "goo_server_create: envelope grid %d x %d", n12, n13);
   }
+  const int ncell = n12 * n13;
+  g.n12 = n12;
+  g.n13 = n13;
+  g.cw12 = (float)((info.hi12 - info.lo12) / n12);
+  g.cw13 = (float)((info.hi13 - info.lo13) / n13);
+  const size_t scan_words = 2 * (size_t)ncell + 2;  // maxima, sums, violation counter (8 bytes)
+  if (cudaMalloc(&s->d_env_bits, scan_words * sizeof(unsigned)) != cudaSuccess) return fail("the envelope");
+  GOO_CUDA_TRY(cudaMemsetAsync(s->d_env_bits, 0, scan_words * sizeof(unsigned), ctx->stream));
+  {
+    LaunchScope ls(ctx, "toy_envelope");
+    envelope_cells_kernel<<<ctx->num_sms * 4, kBlock, 0, ctx->stream>>>(g, (const DalitzDev*)info.dalitz_dev, kEnvSub,
+                                                                       s->d_env_bits, (float*)(s->d_env_bits + ncell));
+  }
+  std::vector<float> cmax(ncell), csum(ncell);
+  GOO_CUDA_TRY(cudaMemcpyAsync(cmax.data(), s->d_env_bits, ncell * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  GOO_CUDA_TRY(cudaMemcpyAsync(csum.data(), s->d_env_bits + ncell, ncell * sizeof(float), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  std::vector<float> bound(ncell, 0.f);
+  if (o.envelope) {
+    for (int c = 0; c < ncell; ++c) bound[c] = o.envelope->bound[c];
+  } else {
+    for (int i = 0; i < n12; ++i)
+      for (int j = 0; j < n13; ++j) {
+        float mx = 0.f;
+        for (int di = -1; di <= 1; ++di)
+          for (int dj = -1; dj <= 1; ++dj) {
+            const int ii = i + di, jj = j + dj;
+            if (ii >= 0 && ii < n12 && jj >= 0 && jj < n13) mx = std::max(mx, cmax[ii * n13 + jj]);
+          }
+        bound[i * n13 + j] = kEnvFactor * mx;
+      }
+  }
+  // acceptance estimate: sum over cells of the lattice mean of min(|S|^2, bound) / sum of bounds
+  double eff0 = 0.2, sacc = 0.0, sbound = 0.0;
+  for (int c = 0; c < ncell; ++c) {
+    sacc += std::min((double)csum[c] / (kEnvSub * kEnvSub), (double)bound[c]);
+    sbound += (double)bound[c];
+  }
+  if (sbound > 0 && std::isfinite(sbound) && sacc > 0) eff0 = std::min(0.95, std::max(0.005, 0.97 * sacc / sbound));
+  // cumulative thresholds of the cell choice: thr[c] = floor(S_c / W * 2^32), S_c the sum of
+  // bound[0..c] and W the total (FP64, in index order), thr[last] = 2^32
+  std::vector<unsigned long long> thr(ncell);
+  double W = 0.0, fmax_all = 0.0;
+  for (int c = 0; c < ncell; ++c) {
+    if (!(bound[c] >= 0.f) || !std::isfinite(bound[c])) {
+      goo_server_free(s);
+      return set_error(GOO_ERR_ARG, "goo_server_create: envelope bound %d is not a finite value >= 0", c);
+    }
+    W += (double)bound[c];
+    fmax_all = std::max(fmax_all, (double)bound[c]);
+  }
+  if (!(W > 0)) {
+    goo_server_free(s);
+    return set_error(GOO_ERR_ARG, "goo_server_create: the envelope is zero everywhere");
+  }
+  double S = 0.0;
+  for (int c = 0; c < ncell; ++c) {
+    S += (double)bound[c];
+    thr[c] = (unsigned long long)std::floor(S / W * 4294967296.0);
+  }
+  thr[ncell - 1] = 4294967296ull;
+  if (cudaMalloc(&s->d_env_bound, ncell * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&s->d_env_thr, ncell * sizeof(unsigned long long)) != cudaSuccess)
+    return fail("the envelope");
+  GOO_CUDA_TRY(cudaMemcpyAsync(s->d_env_bound, bound.data(), ncell * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  GOO_CUDA_TRY(cudaMemcpyAsync(s->d_env_thr, thr.data(), ncell * sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                               ctx->stream));
+  g.bound = s->d_env_bound;
+  g.thr = s->d_env_thr;
+  g.viol = (unsigned long long*)(s->d_env_bits + 2 * (size_t)ncell);
+  s->gen_eff = eff0;
+  s->env_max = fmax_all;
   GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   s->ctx->live++;
   s->counted = true;
@@ -1427,11 +1528,12 @@ int goo_server_stats(const goo_server* s, double* out) {
   out[2] = s->gen_ms;
   out[3] = s->gen_candidates;
   out[4] = s->gen_accepted;
-  out[5] = (double)s->opt.fmax;
+  out[5] = s->env_max;
   out[6] = (double)s->arena_bytes;
   size_t fr = 0;
   for (auto& b : s->free_blocks) fr += b.size;
   out[7] = (double)(s->arena_bytes - fr);
+  out[8] = s->gen_violations;
   return GOO_OK;
 }
 
@@ -1441,7 +1543,8 @@ int goo_server_free(goo_server* s) {
   cudaStreamSynchronize(s->ctx->stream);
   void* ptrs[] = {s->arena, s->d_states, s->d_evals, s->d_results, s->d_model, s->d_params, s->d_tickets,
                   s->d_fit_tiles, s->d_slots, s->d_done, s->d_done_count, s->d_tiles, s->d_tile_partials,
-                  s->d_gtoys, s->d_bprefix, s->d_counts, s->d_outbase, s->d_accepted, s->d_masks};
+                  s->d_gtoys, s->d_bprefix, s->d_counts, s->d_outbase, s->d_accepted, s->d_masks,
+                  s->d_env_bound, s->d_env_thr, s->d_env_bits};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->counted) s->ctx->live--;
@@ -1451,7 +1554,7 @@ int goo_server_free(goo_server* s) {
 
 // Toys from the server's generator, all generated in the same passes and written to host
 // arrays: toy i (seed seeds[i], n[i] events) goes to s12_out/s13_out at offset sum(n[:i]).
-int goo_toys_generate(goo_model* m, const double* theta, double fmax, int n_toys, const uint64_t* seeds,
+int goo_toys_generate(goo_model* m, const double* theta, const goo_envelope* env, int n_toys, const uint64_t* seeds,
                       const int64_t* n, float* s12_out, float* s13_out) {
   if (!m || !theta || n_toys < 0 || (n_toys > 0 && (!seeds || !n || !s12_out || !s13_out)))
     return set_error(GOO_ERR_ARG, "goo_toys_generate: bad arguments");
@@ -1471,7 +1574,7 @@ int goo_toys_generate(goo_model* m, const double* theta, double fmax, int n_toys
     bytes += (int64_t)fit_bytes(n[i], info.nbw);
   }
   o.hbm_budget_bytes = bytes;
-  o.fmax = fmax;
+  o.envelope = env;
   goo_server* s = nullptr;
   GOO_TRY(goo_server_create(m, theta, free_mask.data(), scale.data(), &o, &s));
   int rc = GOO_OK;
@@ -1493,10 +1596,10 @@ int goo_toys_generate(goo_model* m, const double* theta, double fmax, int n_toys
   return rc;
 }
 
-int goo_toy_generate(goo_model* m, const double* theta, double fmax, uint64_t seed, int64_t n, float* s12_out,
+int goo_toy_generate(goo_model* m, const double* theta, const goo_envelope* env, uint64_t seed, int64_t n, float* s12_out,
                      float* s13_out) {
   if (n == 0) return GOO_OK;
-  return goo_toys_generate(m, theta, fmax, 1, &seed, &n, s12_out, s13_out);
+  return goo_toys_generate(m, theta, env, 1, &seed, &n, s12_out, s13_out);
 }
 
 // Batched NLL + gradient of n_fits (dataset, theta) pairs with one launch (per-fit tiles,

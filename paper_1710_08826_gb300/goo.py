@@ -45,10 +45,26 @@ class GooFitResult(ctypes.Structure):
                 ("status", ctypes.c_int32)]
 
 
+class GooEnvelope(ctypes.Structure):
+    _fields_ = [("n12", ctypes.c_int32), ("n13", ctypes.c_int32), ("bound", ctypes.POINTER(ctypes.c_float))]
+
+
 class GooServerOptions(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_fits", ctypes.c_int32), ("tile_events", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("pad", ctypes.c_int32), ("edm_tol", ctypes.c_double),
-                ("fmax", ctypes.c_double)]
+                ("envelope", ctypes.c_void_p)]
+
+
+def _envelope(env):
+    """(pointer or None, keep-alive) for an envelope given as None or (n12, n13, bounds)."""
+    if env is None:
+        return None, None
+    n12, n13, bound = env
+    b = np.ascontiguousarray(np.asarray(bound, dtype=np.float32).reshape(-1))
+    if b.size != int(n12) * int(n13):
+        raise ValueError("envelope: n12 * n13 bounds needed")
+    e = GooEnvelope(int(n12), int(n13), b.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    return ctypes.pointer(e), (e, b)
 
 
 class GooError(RuntimeError):
@@ -96,9 +112,9 @@ def _load():
         "goo_server_result": (ctypes.c_int, [vp, i64, dp, dp, ctypes.c_void_p]),
         "goo_server_stats": (ctypes.c_int, [vp, dp]),
         "goo_server_free": (ctypes.c_int, [vp]),
-        "goo_toy_generate": (ctypes.c_int, [vp, dp, ctypes.c_double, ctypes.c_uint64, i64,
+        "goo_toy_generate": (ctypes.c_int, [vp, dp, vp, ctypes.c_uint64, i64,
                                             ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
-        "goo_toys_generate": (ctypes.c_int, [vp, dp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
+        "goo_toys_generate": (ctypes.c_int, [vp, dp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
                                              ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_float),
                                              ctypes.POINTER(ctypes.c_float)]),
         "goo_nll_grad_batch": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), dp, ctypes.c_int, dp, dp]),
@@ -491,27 +507,30 @@ class Model:
             pass
 
 
-def toy_generate(model, theta, fmax, seed, n):
-    """One toy from the device generator: (s12, s13) float32 arrays."""
+def toy_generate(model, theta, envelope, seed, n):
+    """One toy from the device generator: (s12, s13) float32 arrays.  envelope: None (the
+    library's default, computed at theta) or (n12, n13, per-cell bounds)."""
     t, tp = _dbuf(theta, model.n_params)
     a = np.zeros(n, dtype=np.float32)
     b = np.zeros(n, dtype=np.float32)
-    _check(lib.goo_toy_generate(model.handle, tp, float(fmax), int(seed), int(n),
+    ep, keep = _envelope(envelope)
+    _check(lib.goo_toy_generate(model.handle, tp, ctypes.cast(ep, ctypes.c_void_p) if ep else None, int(seed), int(n),
                                 a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                 b.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
     return a, b
 
 
-def toys_generate(model, theta, fmax, seeds, sizes):
+def toys_generate(model, theta, envelope, seeds, sizes):
     """Several toys generated together: list of (s12, s13) float32 arrays."""
     t, tp = _dbuf(theta, model.n_params)
+    ep, keep = _envelope(envelope)
     k = len(seeds)
     sd = (ctypes.c_uint64 * k)(*[int(v) for v in seeds])
     nn = (ctypes.c_int64 * k)(*[int(v) for v in sizes])
     tot = int(sum(int(v) for v in sizes))
     a = np.zeros(tot, dtype=np.float32)
     b = np.zeros(tot, dtype=np.float32)
-    _check(lib.goo_toys_generate(model.handle, tp, float(fmax), k, sd, nn,
+    _check(lib.goo_toys_generate(model.handle, tp, ctypes.cast(ep, ctypes.c_void_p) if ep else None, k, sd, nn,
                                  a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                  b.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
     out, off = [], 0
@@ -538,7 +557,7 @@ class Server:
     """Continuous-batching toy-MC fit server (goo_server_*)."""
 
     def __init__(self, model, theta_gen, free=None, scale=None, budget_bytes=0, max_fits=0, tile_events=0,
-                 max_iter=0, edm_tol=0.0, fmax=0.0):
+                 max_iter=0, edm_tol=0.0, envelope=None):
         self.model = model
         P = model.n_params
         if free is None:
@@ -548,8 +567,9 @@ class Server:
         tg, tgp = _dbuf(theta_gen, P)
         fm = (ctypes.c_int * P)(*[int(bool(v)) for v in free])
         sc, scp = _dbuf(scale, P)
+        ep, self._env_keep = _envelope(envelope)
         o = GooServerOptions(int(budget_bytes), int(max_fits), int(tile_events), int(max_iter), 0, float(edm_tol),
-                             float(fmax))
+                             ctypes.cast(ep, ctypes.c_void_p) if ep else None)
         h = ctypes.c_void_p()
         _check(lib.goo_server_create(model.handle, tgp, fm, scp, ctypes.byref(o), ctypes.byref(h)))
         self.handle = h
@@ -582,9 +602,10 @@ class Server:
         return th, err, {k: getattr(res, k) for k, _ in GooFitResult._fields_}
 
     def stats(self):
-        out = np.zeros(8)
+        out = np.zeros(9)
         _check(lib.goo_server_stats(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
-        keys = ["rounds", "eval_ms", "gen_ms", "candidates", "accepted", "fmax", "arena_bytes", "arena_used"]
+        keys = ["rounds", "eval_ms", "gen_ms", "candidates", "accepted", "bound_max", "arena_bytes", "arena_used",
+                "envelope_violations"]
         return dict(zip(keys, out.tolist()))
 
     def close(self):

@@ -28,37 +28,73 @@ def setup(goo):
     mcds = goo.Dataset.from_spec(ctx, spec, mc)
     model = goo.Model(ctx, spec, mc=mcds)
     theta = np.array(synth.param_values(spec))
-    fmax = 1.2 * od.max_intensity_scan(od.DalitzModel(spec), theta, n=300)
-    return ctx, spec, mc, mcds, model, theta, fmax
+    env = otoys.envelope(spec, theta)   # per-cell bounds of |S|^2, 48 x 48 cells
+    return ctx, spec, mc, mcds, model, theta, env
 
 
 def test_toy_generator_matches_oracle(goo, setup):
-    ctx, spec, mc, mcds, model, theta, fmax = setup
+    ctx, spec, mc, mcds, model, theta, env = setup
     for seed, n in [(1710100, 700), (1710101, 1500), (1710777, 300)]:
-        a, b = goo.toy_generate(model, theta, fmax, seed, n)
-        ra, rb, _ = otoys.generate_toy(spec, theta, fmax, seed, n)
+        a, b = goo.toy_generate(model, theta, env, seed, n)
+        ra, rb, _ = otoys.generate_toy(spec, theta, env, seed, n)
         np.testing.assert_array_equal(a, ra)
         np.testing.assert_array_equal(b, rb)
 
 
+@pytest.mark.parametrize("grid", [(1, 1), (7, 13)])
+def test_other_envelope_grids_match_oracle(goo, setup, grid):
+    # one cell (the uniform box proposal with a single bound) and a non-square grid
+    ctx, spec, mc, mcds, model, theta, env = setup
+    e = otoys.envelope(spec, theta, *grid)
+    a, b = goo.toy_generate(model, theta, e, 1710120, 900)
+    ra, rb, _ = otoys.generate_toy(spec, theta, e, 1710120, 900)
+    np.testing.assert_array_equal(a, ra)
+    np.testing.assert_array_equal(b, rb)
+
+
+def test_default_envelope_follows_the_same_density(goo, setup):
+    # the library's own envelope (computed on the device at theta) gives other toys from the
+    # same density: a two-sample chi2 of the Dalitz histograms against oracle-envelope toys
+    ctx, spec, mc, mcds, model, theta, env = setup
+    a0, b0 = goo.toy_generate(model, theta, None, 1710130, 200_000)
+    a1, b1 = goo.toy_generate(model, theta, env, 1710131, 200_000)
+    lo12, hi12, lo13, hi13 = otoys._box(KIN)
+    h0 = np.histogram2d(a0, b0, 24, [[lo12, hi12], [lo13, hi13]])[0].ravel()
+    h1 = np.histogram2d(a1, b1, 24, [[lo12, hi12], [lo13, hi13]])[0].ravel()
+    k = (h0 + h1) > 20
+    chi2 = np.sum((h0[k] - h1[k]) ** 2 / (h0[k] + h1[k]))
+    assert chi2 / k.sum() < 1.3, (chi2, k.sum())
+
+
+def test_envelope_arguments_are_checked(goo, setup):
+    ctx, spec, mc, mcds, model, theta, env = setup
+    n12, n13, bound = env
+    with pytest.raises(ValueError):
+        goo.toy_generate(model, theta, (n12, n13 + 1, bound), 1, 10)
+    with pytest.raises(goo.GooError):
+        goo.toy_generate(model, theta, (2, 2, np.zeros(4, np.float32)), 1, 10)
+    with pytest.raises(goo.GooError):
+        goo.toy_generate(model, theta, (1, 1, np.array([np.nan], np.float32)), 1, 10)
+
+
 def test_toys_generated_together_equal_alone(goo, setup):
-    ctx, spec, mc, mcds, model, theta, fmax = setup
+    ctx, spec, mc, mcds, model, theta, env = setup
     seeds = [1710150 + i for i in range(5)]
     sizes = [400, 3000, 17, 1200, 9000]
-    together = goo.toys_generate(model, theta, fmax, seeds, sizes)
+    together = goo.toys_generate(model, theta, env, seeds, sizes)
     for (a, b), sd, n in zip(together, seeds, sizes):
-        a1, b1 = goo.toy_generate(model, theta, fmax, sd, n)
+        a1, b1 = goo.toy_generate(model, theta, env, sd, n)
         np.testing.assert_array_equal(a, a1)
         np.testing.assert_array_equal(b, b1)
-    ra, rb, _ = otoys.generate_toy(spec, theta, fmax, seeds[1], sizes[1])
+    ra, rb, _ = otoys.generate_toy(spec, theta, env, seeds[1], sizes[1])
     np.testing.assert_array_equal(together[1][0], ra)
 
 
 def test_toys_follow_the_model(goo, setup):
     # the generated Dalitz distribution has the model's density: the NLL of the toy at the
     # generating point is lower than at a distorted point (by far more than statistics)
-    ctx, spec, mc, mcds, model, theta, fmax = setup
-    a, b = goo.toy_generate(model, theta, fmax, 1710200, 20_000)
+    ctx, spec, mc, mcds, model, theta, env = setup
+    a, b = goo.toy_generate(model, theta, env, 1710200, 20_000)
     ds = goo.Dataset.from_spec(ctx, spec, {"s12": a.astype(np.float64), "s13": b.astype(np.float64)})
     th2 = theta.copy()
     names = synth.param_names(spec)
@@ -66,15 +102,15 @@ def test_toys_follow_the_model(goo, setup):
     assert model.nll(ds, theta, "f32") < model.nll(ds, th2, "f32") - 100
 
 
-def _toy_ds(goo, ctx, spec, model, theta, fmax, seed, n):
-    a, b = goo.toy_generate(model, theta, fmax, seed, n)
+def _toy_ds(goo, ctx, spec, model, theta, env, seed, n):
+    a, b = goo.toy_generate(model, theta, env, seed, n)
     return goo.Dataset.from_spec(ctx, spec, {"s12": a.astype(np.float64), "s13": b.astype(np.float64)})
 
 
 def test_batch_matches_single_and_is_mix_independent(goo, setup):
-    ctx, spec, mc, mcds, model, theta, fmax = setup
+    ctx, spec, mc, mcds, model, theta, env = setup
     sizes = [1000, 40_000, 17, 70_001]
-    dss = [_toy_ds(goo, ctx, spec, model, theta, fmax, 1710300 + i, n) for i, n in enumerate(sizes)]
+    dss = [_toy_ds(goo, ctx, spec, model, theta, env, 1710300 + i, n) for i, n in enumerate(sizes)]
     rng = np.random.default_rng(5)
     names = synth.param_names(spec)
     coef = np.array([nm.startswith(("re_", "im_")) and not nm.endswith("NR") for nm in names])
@@ -99,11 +135,11 @@ def _run(server, tickets, max_rounds=5000):
 
 
 def test_server_fits_match_host_fitter_and_oracle(goo, setup):
-    ctx, spec, mc, mcds, model, theta, fmax = setup
+    ctx, spec, mc, mcds, model, theta, env = setup
     names = synth.param_names(spec)
     free = np.array([not p[2] for p in spec["params"]])
     steps = np.array([p[3] if p[3] > 0 else 1.0 for p in spec["params"]])
-    server = goo.Server(model, theta, fmax=fmax)
+    server = goo.Server(model, theta, envelope=env)
     toys = [(1710400 + i, n) for i, n in enumerate([3000, 800, 12_000, 5000, 1500, 30_000])]
     start = theta.copy()
     start[free] *= 1.05
@@ -112,14 +148,14 @@ def test_server_fits_match_host_fitter_and_oracle(goo, setup):
     for (seed, n), t in zip(toys, tickets):
         th, err, info = res[t]
         assert info["status"] == 0, info
-        ds = _toy_ds(goo, ctx, spec, model, theta, fmax, seed, n)
+        ds = _toy_ds(goo, ctx, spec, model, theta, env, seed, n)
         hth, herr, hinfo = model.fit(ds, start, free, steps, precision="f32")
         idx = np.flatnonzero(free)
         assert np.all(np.abs(th[idx] - hth[idx]) / herr[idx] < 0.01), (th[idx] - hth[idx]) / herr[idx]
         np.testing.assert_allclose(err[idx], herr[idx], rtol=0.03)
     # oracle fit of one toy (float32 events, float64 oracle)
     seed, n = toys[0]
-    a, b = goo.toy_generate(model, theta, fmax, seed, n)
+    a, b = goo.toy_generate(model, theta, env, seed, n)
     data = {"s12": a.astype(np.float64), "s13": b.astype(np.float64)}
     ref = od.DalitzModel(spec)
     rth, rerr, _, redm = ofit.fit(lambda t: ref.nll_grad(data, mc, t), start, free, steps)
@@ -130,14 +166,14 @@ def test_server_fits_match_host_fitter_and_oracle(goo, setup):
 
 
 def test_result_same_alone_and_in_mix(goo, setup):
-    ctx, spec, mc, mcds, model, theta, fmax = setup
+    ctx, spec, mc, mcds, model, theta, env = setup
     start = theta.copy()
     free = np.array([not p[2] for p in spec["params"]])
     start[free] *= 0.95
-    alone = goo.Server(model, theta, fmax=fmax)
+    alone = goo.Server(model, theta, envelope=env)
     t = alone.submit(7000, 1710500, start)
     r_alone = _run(alone, [t])[t]
-    mixed = goo.Server(model, theta, fmax=fmax, max_fits=3)
+    mixed = goo.Server(model, theta, envelope=env, max_fits=3)
     tickets = [mixed.submit(n, s, start) for s, n in [(1710501, 20_000), (1710502, 900)]]
     tm = mixed.submit(7000, 1710500, start)
     tickets += [mixed.submit(n, s, start) for s, n in [(1710503, 4000), (1710504, 15_000)]]
@@ -147,9 +183,9 @@ def test_result_same_alone_and_in_mix(goo, setup):
 
 
 def test_admission_respects_the_budget(goo, setup):
-    ctx, spec, mc, mcds, model, theta, fmax = setup
+    ctx, spec, mc, mcds, model, theta, env = setup
     budget = 72 * 25_000 + 64 * 1024  # room for about one 20k-event toy at a time
-    server = goo.Server(model, theta, fmax=fmax, budget_bytes=budget)
+    server = goo.Server(model, theta, envelope=env, budget_bytes=budget)
     tickets = [server.submit(n, 1710600 + i) for i, n in enumerate([20_000, 5000, 18_000, 9000])]
     peak_active = 0
     for _ in range(5000):
