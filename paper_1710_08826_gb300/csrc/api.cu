@@ -56,8 +56,9 @@ int nll_common(goo_model* m, const goo_dataset* ds, const double* theta, int pre
   } else if (m->kind == 2) {
     GOO_TRY(td4_nll(m, ds, 0, ds->n, theta, precision, grad, res, 0));
   } else {
-    GOO_TRY(sop_prepare(m, theta, precision));
-    GOO_TRY(sop_events(m, ds, 0, ds->n, precision, grad, 0));
+    const bool fuse = ds->n > 0 && sop_norm_in_event(m, precision, grad);
+    GOO_TRY(sop_prepare(m, theta, precision, fuse));
+    GOO_TRY(sop_events(m, ds, 0, ds->n, precision, grad, 0, fuse));
     if (ds->n == 0) {
       res[0] = 0.0;
       res[1] = 0.0;
@@ -221,9 +222,10 @@ int goo_nll_partial(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t 
   } else if (m->kind == 1) {
     GOO_TRY(dalitz_nll(m, ds, begin, end, theta, precision, want_grad != 0, res, 1));
   } else {
-    GOO_TRY(sop_prepare(m, theta, precision));
+    const bool fuse = end > begin && sop_norm_in_event(m, precision, want_grad != 0);
+    GOO_TRY(sop_prepare(m, theta, precision, fuse));
     if (end > begin) {
-      GOO_TRY(sop_events(m, ds, begin, end, precision, want_grad != 0, 1));
+      GOO_TRY(sop_events(m, ds, begin, end, precision, want_grad != 0, 1, fuse));
       GOO_TRY(read_result(ctx, 3 + P, res));
     } else {
       GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));

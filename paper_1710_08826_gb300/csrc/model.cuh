@@ -59,10 +59,14 @@ struct Td4Model;     // time-dependent four-body models (td4.cu)
 int build_sop_model(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_params, int n_obs,
                     const double* lo, const double* hi, goo_model* m);
 int sop_set_norm(goo_model* m, const goo_norm_spec* spec);
-int sop_prepare(goo_model* m, const double* theta_host, int precision);
+// Uploads the prepared model block and launches the grid normalisation, unless norm_in_event
+// (sop_norm_in_event true, and the following sop_events call passes it too).
+int sop_prepare(goo_model* m, const double* theta_host, int precision, bool norm_in_event = false);
+// True when the FP32 event kernel for this model normalises a separable grid itself.
+bool sop_norm_in_event(const goo_model* m, int precision, bool grad);
 void host_prep(ModelDev& h, const double* theta, int precision);
 int sop_events(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int precision, bool grad,
-               int out_mode);
+               int out_mode, bool norm_in_event = false);
 int sop_eval_logf(goo_model* m, const goo_dataset* ds, int precision, double* logf_dev);
 
 int build_dalitz_model(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_params, int n_obs,

@@ -471,12 +471,83 @@ struct EventLanes {
 
 // Block reduction of the per-thread lanes, last-block reduction over the blocks and the
 // final FP64 combination (lanes -> NLL and d NLL / d theta), shared by the event kernels.
+// Constants of the self-contained FP32 event kernel, passed by value so that the kernel reads
+// no model block: per leaf slot the 1-D grid of its observable (separable grid normalisation)
+// and the final combination's weights, parameter map and d w / d theta.
 template <int K, int L, bool GRAD>
-__device__ __forceinline__ void event_finish(ddf (&v)[EventLanes<float, K, L, GRAD>::NS], unsigned bad,
-                                             const ModelDev* __restrict__ md, int nK, float2* partials,
-                                             unsigned* counters, double* result, int out_mode, ddf* s_red,
-                                             unsigned* s_bad) {
+struct EvNorm {
+  float lo_hi[K * L], lo_lo[K * L], h_hi[K * L], h_lo[K * L], aref_hi[K * L], aref_lo[K * L];
+  double h64[K * L];
+  int nb[K * L];                                   // bins (0: no leaf in the slot)
+  double w[K];                                     // w_k
+  int n_params;
+  signed char par[K][L][3];                        // parameter of leaf constant j (-1: none)
+  double dw[GRAD ? K : 1][GRAD ? kMaxParams : 1];  // d w_k / d theta_p
+};
+
+// Sources of the final combination's constants: the model block in device memory (MdFin), or
+// the kernel's by-value constants together with the normalisation terms the block computed
+// itself (ParFin; t[k L + l] = {h S, D_1 / S, D_2 / S, D_3 / S} of leaf slot (k, l)).
+struct MdFin {
+  const ModelDev* __restrict__ md;
+  int nK;
+  static constexpr bool kOwnNorm = false;
+  __device__ int n_params() const { return md->n_params; }
+  __device__ double w(int k) const { return k < nK ? md->comp[k].w : 0.0; }
+  __device__ double dw(int k, int p) const { return md->dw[k][p]; }
+  __device__ double dlogN(int k, int p) const { return md->dlogN[k][p]; }
+  __device__ int par(int k, int l, int j) const {
+    return (k < nK && l < md->comp[k].n_leaf) ? md->leaf[k * kMaxLeaf + l].par[j] : -1;
+  }
+  __device__ double term(int, int, int) const { return 0.0; }
+};
+
+template <int K, int L, bool GRAD>
+struct ParFin {
+  const EvNorm<K, L, GRAD>* N;
+  const double (*t)[4];
+  static constexpr bool kOwnNorm = true;
+  __device__ int n_params() const { return N->n_params; }
+  __device__ double w(int k) const { return N->w[k]; }
+  __device__ double dw(int k, int p) const {
+    if constexpr (GRAD) return N->dw[k][p];
+    else return 0.0;
+  }
+  __device__ double dlogN(int, int) const { return 0.0; }
+  __device__ int par(int k, int l, int j) const { return N->par[k][l][j]; }
+  __device__ double term(int k, int l, int j) const { return t[k * L + l][1 + j]; }
+};
+
+// Block reduction, last-block reduction over the blocks and the final FP64 combination
+// (lanes -> NLL and d NLL / d theta), shared by the event kernels:
+//   d NLL / d theta_p = sum_k [w_k C_k dlogN_kp - C_k dw_kp] - sum_{k,l,j: par = p} w_k A_klj,
+// with dlogN_kp = sum_{l,j: par = p} t_klj for a block's own normalisation terms.  Thread p
+// takes parameter p and gathers its terms in a fixed order.  The constants are loaded before
+// the block's reduction, so that their latency overlaps it; the last block alone combines.
+template <int K, int L, bool GRAD, typename Fin>
+__device__ __forceinline__ void event_finish(ddf (&v)[EventLanes<float, K, L, GRAD>::NS], unsigned bad, const Fin& F,
+                                             int nK, float2* partials, unsigned* counters, double* result,
+                                             int out_mode, ddf* s_red, unsigned* s_bad) {
   constexpr int NS = EventLanes<float, K, L, GRAD>::NS;
+  __shared__ double s_out[NS];
+  __shared__ double s_w[K];
+  __shared__ int s_par[K][L][3];
+  const int p = threadIdx.x;
+  const int P = F.n_params();
+  double dwp[GRAD ? K : 1], dlp[GRAD ? K : 1];
+  if constexpr (GRAD) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const bool on = p < P && k < nK;
+      dwp[k] = on ? F.dw(k, p) : 0.0;
+      dlp[k] = (on && !Fin::kOwnNorm) ? F.dlogN(k, p) : 0.0;
+    }
+    for (int t = threadIdx.x; t < K * L * 3; t += blockDim.x) {
+      const int k = t / (L * 3), l = (t / 3) % L, jj = t % 3;
+      s_par[k][l][jj] = k < nK ? F.par(k, l, jj) : -1;
+    }
+    if (threadIdx.x < K) s_w[threadIdx.x] = F.w(threadIdx.x);
+  }
   for (int m = 16; m > 0; m >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, m);
   if ((threadIdx.x & 31) == 0) s_bad[threadIdx.x >> 5] = bad;
   block_reduce_to_partials<NS>(v, NS, partials, s_red);
@@ -485,45 +556,36 @@ __device__ __forceinline__ void event_finish(ddf (&v)[EventLanes<float, K, L, GR
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_bad[w];
     if (b) atomicAdd(counters + 1, b);
   }
-  __shared__ double s_out[NS];
   if (!last_block_reduce(partials, NS, gridDim.x, counters, s_out, s_red)) return;
 
   // ---- final combination (last block, FP64) ----
-  // d NLL / d theta_p = sum_k [w_k C_k dlogN_kp - C_k dw_kp] - sum_{k,l,j: par = p} w_k A_klj.
-  // Column p of the first sum is taken by thread p (independent loads in parallel); the
-  // leaf terms are scattered by one thread from shared memory (leaves may share a parameter).
-  __shared__ double s_g[kMaxParams];
-  __shared__ double s_w[K];
-  __shared__ int s_par[K][L][3];
-  const int P = md->n_params;
-  for (int t = threadIdx.x; t < K * L * 3; t += blockDim.x) {
-    const int k = t / (L * 3), l = (t / 3) % L, jj = t % 3;
-    s_par[k][l][jj] = (k < nK && l < md->comp[k].n_leaf) ? md->leaf[k * kMaxLeaf + l].par[jj] : -1;
-  }
-  if (threadIdx.x < K) s_w[threadIdx.x] = threadIdx.x < nK ? md->comp[threadIdx.x].w : 0.0;
-  for (int p = threadIdx.x; p < P; p += blockDim.x) {
-    double gp = 0.0;
-    if (GRAD)
-      for (int k = 0; k < nK; ++k) {
-        const double Ck = s_out[1 + k];
-        gp += md->comp[k].w * Ck * md->dlogN[k][p] - Ck * md->dw[k][p];
-      }
-    s_g[p] = gp;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0 && GRAD) {
-    for (int k = 0; k < nK; ++k)
-      for (int l = 0; l < L; ++l)
-        for (int jj = 0; jj < 3; ++jj)
-          if (s_par[k][l][jj] >= 0) s_g[s_par[k][l][jj]] -= s_w[k] * s_out[1 + K + (k * L + l) * 3 + jj];
-  }
-  __syncthreads();
   const int off = out_mode == 0 ? 2 : 3;
-  for (int p = threadIdx.x; p < P; p += blockDim.x) result[off + p] = s_g[p];
+  if (p < P) {
+    double gp = 0.0;
+    if constexpr (GRAD) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (k >= nK) break;
+        const double Ck = s_out[1 + k];
+        gp += s_w[k] * Ck * dlp[k] - Ck * dwp[k];
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+#pragma unroll
+          for (int jj = 0; jj < 3; ++jj)
+            if (s_par[k][l][jj] == p)
+              gp += s_w[k] * ((Fin::kOwnNorm ? s_out[1 + k] * F.term(k, l, jj) : 0.0) -
+                              s_out[1 + K + (k * L + l) * 3 + jj]);
+    }
+    result[off + p] = gp;
+  }
   if (threadIdx.x == 0) {
-    const unsigned nbad = atomicAdd(counters + 1, 0u);
+    // every other block added to these words before its ticket (and a fence): plain L2 reads
+    const unsigned nbad = __ldcg(counters + 1);
+    const unsigned status = __ldcg(counters + kStatusWord);
     counters[1] = 0u;
-    const unsigned status = atomicAdd(counters + kStatusWord, 0u);
     counters[kStatusWord] = 0u;
     // a device wait that gave up is reported as a negative event count
     const double nb = status ? -1.0 : (double)nbad;
@@ -633,7 +695,7 @@ __global__ void __launch_bounds__(kBlock, EventOcc<T, K, L>::value) sop_event_ke
               (sizeof(T) == 4) ? ddf{(float)Aacc[k][l][j], 0.f} : dd_from_double((double)Aacc[k][l][j]);
     }
   }
-  event_finish<K, L, GRAD>(v, bad, md, nK, partials, counters, result, out_mode, s_red, s_bad);
+  event_finish<K, L, GRAD>(v, bad, MdFin{md, nK}, nK, partials, counters, result, out_mode, s_red, s_bad);
 }
 
 // =======================================================================================
@@ -766,6 +828,99 @@ struct Kahan2 {
   }
 };
 
+
+// Midpoint coordinate of bin idx of a 1-D grid as a double-float (the FP32 path's grid_coord).
+__device__ __forceinline__ void grid_coord_f(float lo_hi, float lo_lo, float h_hi, float h_lo, int64_t idx, float& x,
+                                             float& xlo) {
+  const float off = (float)idx + 0.5f;
+  const float p = off * h_hi;
+  const float perr = fmaf(off, h_hi, -p) + off * h_lo;
+  const ddf xs = dd_add({lo_hi, lo_lo}, dd_make(p, perr));
+  x = xs.hi;
+  xlo = xs.lo;
+}
+
+// Midpoint coordinate of bin idx of grid dimension d (double-float in the FP32 path).
+template <typename T>
+__device__ __forceinline__ void grid_coord(const GridDev& G, int d, int64_t idx, T& x, T& xlo) {
+  if constexpr (sizeof(T) == 4) {
+    grid_coord_f(G.lo_hi[d], G.lo_lo[d], G.h_hi[d], G.h_lo[d], idx, x, xlo);
+  } else {
+    x = G.lo64[d] + ((double)idx + 0.5) * G.h64[d];
+    xlo = 0.0;
+  }
+}
+
+// Separable grid normalisation inside the event kernel.  When every leaf of a product acts on
+// its own observable, log N_k = sum_l [log(h_l S_l) + a_l] with one 1-D midpoint sum S_l per
+// leaf (as grid_sep_kernel computes it), a few hundred leaf evaluations in all; every block
+// evaluates them itself at its start instead of waiting for a normalisation kernel, from
+// by-value constants only.  Warp w takes leaf slots w, w + 8, ...; its lanes stride the bins
+// in a fixed order, accumulate in double-float (exact products by fma) and reduce by a fixed
+// shuffle tree, so every block obtains bit-identical sums.  FP64 runs only in the last step,
+// in one warp with a lane per (slot, term) and per product: GB300's FP64 pipe is 1/64 of
+// FP32, and every block pays it.  s_term[k L + l] = {h S, D_1 / S, D_2 / S, D_3 / S} stays
+// for the final combination.
+template <int K, int L, bool GRAD>
+__device__ __forceinline__ void fused_grid_norm(const EvConst<float, K, L>& P, const EvNorm<K, L, GRAD>& N,
+                                                ddf (*s_raw)[4], double (*s_term)[4], float (*s_off)[2],
+                                                float (&off_hi)[K], float (&off_lo)[K]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int sl = 0; sl < K * L; ++sl) {
+    if (sl % (kBlock / 32) != warp || N.nb[sl] == 0) continue;  // uniform over the warp
+    const LeafReg<float>& lr = P.leaf[sl / L][sl % L];
+    const float aref = N.aref_hi[sl], aref_lo = N.aref_lo[sl];
+    ddf acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    for (int i = lane; i < N.nb[sl]; i += 32) {
+      float x, xlo, r, a, dl[3];
+      grid_coord_f(N.lo_hi[sl], N.lo_lo[sl], N.h_hi[sl], N.h_lo[sl], i, x, xlo);
+      leaf_eval<true, true>(lr, x, r, a, dl, xlo);
+      const float U = r * expf((a - aref) - aref_lo);
+      acc[0] = dd_add(acc[0], ddf{U, 0.f});
+#pragma unroll
+      for (int jj = 0; jj < 3; ++jj) {
+        const float pr = U * dl[jj];
+        acc[1 + jj] = dd_add(acc[1 + jj], ddf{pr, fmaf(U, dl[jj], -pr)});
+      }
+    }
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) acc[jj] = dd_warp_sum(acc[jj]);
+    if (lane == 0)
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) s_raw[sl][jj] = acc[jj];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int t = lane; t < K * L * 4; t += 32) {
+      const int sl = t >> 2, jj = t & 3;
+      if (N.nb[sl] == 0) continue;
+      const double S = dd_to_double(s_raw[sl][0]);
+      s_term[sl][jj] = jj == 0 ? N.h64[sl] * S : dd_to_double(s_raw[sl][jj]) / S;
+    }
+    __syncwarp();
+    if (lane < K) {
+      double prod = 1.0, aref = 0.0;
+      for (int l = 0; l < L; ++l) {
+        const int sl = lane * L + l;
+        if (N.nb[sl] == 0) continue;
+        prod *= s_term[sl][0];
+        aref += (double)N.aref_hi[sl] + (double)N.aref_lo[sl];
+      }
+      const double logN = log(prod) + aref;
+      const float oh = (float)(-logN);
+      s_off[lane][0] = oh;
+      s_off[lane][1] = (float)(-logN - (double)oh);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    off_hi[k] = s_off[k][0];
+    off_lo[k] = s_off[k][1];
+  }
+}
+
 constexpr int kEventStages = 3;     // column tiles in flight per block (TMA bulk copies)
 constexpr int kPairsPerThread = 4;  // event pairs per thread per tile
 
@@ -835,8 +990,9 @@ __device__ __forceinline__ void pair_step(const EvConst<float, K, L>& P, const f
 // Dynamic shared memory: kEventStages * n_obs * TE floats.
 template <int K, int L, bool GRAD>
 __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
-    sop_event2_kernel(const ModelDev* __restrict__ md, const EvConst<float, K, L> P, Cols<float> cols, int64_t begin,
-                      int64_t end, float2* partials, unsigned* counters, double* result, int out_mode) {
+    sop_event2_kernel(const ModelDev* __restrict__ md, const EvConst<float, K, L> P,
+                      const __grid_constant__ EvNorm<K, L, GRAD> N, Cols<float> cols, int64_t begin, int64_t end,
+                      float2* partials, unsigned* counters, double* result, int out_mode, int fused_norm) {
   using namespace pk;
   constexpr int NS = EventLanes<float, K, L, GRAD>::NS;
   constexpr int PPT = kPairsPerThread;
@@ -845,6 +1001,9 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
   __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
   __shared__ unsigned s_bad[kBlock / 32];
   __shared__ __align__(8) uint64_t s_bar[NST];
+  __shared__ double s_term[K * L][4];
+  __shared__ ddf s_raw[K * L][4];
+  __shared__ float s_off[K][2];
   extern __shared__ __align__(128) float s_col[];  // [NST][nobs][TE]
   const int nobs = P.nobs;
   const int64_t tb0 = begin / TE, tb1 = (end + TE - 1) / TE;
@@ -873,9 +1032,13 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
   // previous kernel in the stream is read after this point
   grid_dep_wait();
   float off_hi[K], off_lo[K];
-  load_offsets<float, K>(md, off_hi, off_lo);
   const int nK = P.nK;
-  __syncthreads();  // barriers initialised before any thread waits on them
+  if (fused_norm) {
+    fused_grid_norm<K, L, GRAD>(P, N, s_raw, s_term, s_off, off_hi, off_lo);  // synchronises the block
+  } else {
+    load_offsets<float, K>(md, off_hi, off_lo);
+    __syncthreads();  // barriers initialised before any thread waits on them
+  }
   PairAcc<K, L> S;
   S.bad = 0;
 #pragma unroll
@@ -957,7 +1120,11 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
           v[1 + K + (k * L + l) * 3 + q] = dd_add(ddf{S.A[k][l][q].x, 0.f}, ddf{S.A[k][l][q].y, 0.f});
     }
   }
-  event_finish<K, L, GRAD>(v, S.bad, md, nK, partials, counters, result, out_mode, s_red, s_bad);
+  if (fused_norm)
+    event_finish<K, L, GRAD>(v, S.bad, ParFin<K, L, GRAD>{&N, s_term}, nK, partials, counters, result, out_mode, s_red,
+                             s_bad);
+  else
+    event_finish<K, L, GRAD>(v, S.bad, MdFin{md, nK}, nK, partials, counters, result, out_mode, s_red, s_bad);
 }
 
 // =======================================================================================
@@ -971,20 +1138,6 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
 constexpr int kSeg = 16;
 constexpr int kGridCache = 2048;
 
-template <typename T>
-__device__ __forceinline__ void grid_coord(const GridDev& G, int d, int64_t idx, T& x, T& xlo) {
-  if constexpr (sizeof(T) == 4) {
-    const float off = (float)idx + 0.5f;
-    const float p = off * G.h_hi[d];
-    const float perr = fmaf(off, G.h_hi[d], -p) + off * G.h_lo[d];
-    const ddf xs = dd_add({G.lo_hi[d], G.lo_lo[d]}, dd_make(p, perr));
-    x = xs.hi;
-    xlo = xs.lo;
-  } else {
-    x = G.lo64[d] + ((double)idx + 0.5) * G.h64[d];
-    xlo = 0.0;
-  }
-}
 
 template <typename T, int L>
 __global__ void __launch_bounds__(kBlock, 2) grid_kernel(ModelDev* md, float2* partials, unsigned* counters) {
@@ -1548,11 +1701,30 @@ static int launch_grid_T(goo_model* m) {
   return GOO_OK;
 }
 
-int sop_prepare(goo_model* m, const double* theta_host, int precision) {
+// Largest number of 1-D grid bins (summed over the leaves) normalised inside the event kernel.
+constexpr int kFusedNormBins = 4096;
+
+bool sop_norm_in_event(const goo_model* m, int precision, bool grad) {
+  const ModelDev& h = m->host;
+  if (precision != GOO_F32 || h.norm_kind != GOO_NORM_GRID || !h.grid_separable) return false;
+  if (grad && !(h.nK <= 2 && m->max_leaf <= 3)) return false;  // the scalar kernel takes that shape
+  int64_t bins = 0;
+  for (int k = 0; k < h.nK; ++k)
+    for (int l = 0; l < h.comp[k].n_leaf; ++l) {
+      const GridDev& G = h.grid[k];
+      bins += G.bins[G.dim_of_col[h.leaf[k * kMaxLeaf + l].col]];
+    }
+  return bins <= kFusedNormBins;
+}
+
+int sop_prepare(goo_model* m, const double* theta_host, int precision, bool norm_in_event) {
   goo_ctx* ctx = m->ctx;
   ModelDev* stage = m->stage;
   *stage = m->host;
   host_prep(*stage, theta_host, precision);
+  // the self-contained event kernel (sop_norm_in_event) takes its constants by value and reads
+  // no model block: nothing to upload
+  if (norm_in_event) return GOO_OK;
   GOO_CUDA_TRY(cudaMemcpyAsync(m->dev, stage, sizeof(ModelDev), cudaMemcpyHostToDevice, ctx->stream));
   if (m->host.norm_kind == GOO_NORM_GRID && m->host.grid_separable) {
     GOO_TRY((precision == GOO_F32 ? launch_grid_sep<float>(m) : launch_grid_sep<double>(m)));
@@ -1618,8 +1790,41 @@ static int launch_event_T(goo_model* m, const goo_dataset* ds, int64_t begin, in
 
 constexpr int kMaxDevicesEv = 64;
 
+// By-value constants of the self-contained event kernel from a prepared model block.
 template <int K, int L, bool GRAD>
-static int launch_event2(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int out_mode) {
+static EvNorm<K, L, GRAD> make_evnorm(const ModelDev& h) {
+  EvNorm<K, L, GRAD> N;
+  std::memset(&N, 0, sizeof N);
+  for (int k = 0; k < K; ++k) {
+    N.w[k] = k < h.nK ? h.comp[k].w : 0.0;
+    for (int l = 0; l < L; ++l) {
+      const int sl = k * L + l;
+      for (int j = 0; j < 3; ++j) N.par[k][l][j] = -1;
+      if (k >= h.nK || l >= h.comp[k].n_leaf) continue;
+      const LeafDev& LD = h.leaf[k * kMaxLeaf + l];
+      const GridDev& G = h.grid[k];
+      const int d = G.dim_of_col[LD.col];
+      N.nb[sl] = G.bins[d];
+      N.lo_hi[sl] = G.lo_hi[d];
+      N.lo_lo[sl] = G.lo_lo[d];
+      N.h_hi[sl] = G.h_hi[d];
+      N.h_lo[sl] = G.h_lo[d];
+      N.h64[sl] = G.h64[d];
+      N.aref_hi[sl] = LD.a_ref_hi;
+      N.aref_lo[sl] = LD.a_ref_lo;
+      for (int j = 0; j < 3; ++j) N.par[k][l][j] = (signed char)LD.par[j];
+    }
+  }
+  N.n_params = h.n_params;
+  if constexpr (GRAD)
+    for (int k = 0; k < K && k < h.nK; ++k)
+      for (int p = 0; p < h.n_params; ++p) N.dw[k][p] = h.dw[k][p];
+  return N;
+}
+
+template <int K, int L, bool GRAD>
+static int launch_event2(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int out_mode,
+                         bool fused_norm) {
   goo_ctx* ctx = m->ctx;
   constexpr int TE = 2 * kPairsPerThread * kBlock;
   const size_t smem = (size_t)kEventStages * m->host.n_obs * TE * sizeof(float);
@@ -1657,27 +1862,34 @@ static int launch_event2(goo_model* m, const goo_dataset* ds, int64_t begin, int
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     LaunchScope ls(ctx, GRAD ? "sop_nll_grad_f32" : "sop_nll_f32");
+    EvNorm<K, L, GRAD> N;
+    if (fused_norm) N = make_evnorm<K, L, GRAD>(*m->stage);
+    else std::memset(&N, 0, sizeof N);
     GOO_CUDA_TRY(cudaLaunchKernelEx(&cfg, sop_event2_kernel<K, L, GRAD>, (const ModelDev*)m->dev,
-                                    make_evconst<float, K, L>(*m->stage), cols, begin, end, ctx->scratch.partials,
-                                    ctx->scratch.counters, ctx->scratch.result, out_mode));
+                                    make_evconst<float, K, L>(*m->stage), N, cols, begin, end,
+                                    ctx->scratch.partials, ctx->scratch.counters, ctx->scratch.result, out_mode,
+                                    (int)fused_norm));
   }
   GOO_CUDA_TRY(cudaGetLastError());
   return GOO_OK;
 }
 
 template <typename T, bool GRAD>
-static int launch_event_sel(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int out_mode) {
+static int launch_event_sel(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int out_mode,
+                            bool fused_norm) {
   if constexpr (sizeof(T) == 4) {
     // packed pairs, except the largest shape with gradient lanes (its pair accumulators do
     // not fit in registers)
-    if (m->host.nK <= 2 && m->max_leaf <= 3) return launch_event2<2, 3, GRAD>(m, ds, begin, end, out_mode);
-    if constexpr (!GRAD) return launch_event2<4, 4, GRAD>(m, ds, begin, end, out_mode);
+    if (m->host.nK <= 2 && m->max_leaf <= 3) return launch_event2<2, 3, GRAD>(m, ds, begin, end, out_mode, fused_norm);
+    if constexpr (!GRAD) return launch_event2<4, 4, GRAD>(m, ds, begin, end, out_mode, fused_norm);
   }
+  if (fused_norm) return set_error(GOO_ERR_STATE, "sop_events: in-kernel normalisation needs the pair kernel");
   if (m->host.nK <= 2 && m->max_leaf <= 3) return launch_event_T<T, 2, 3, GRAD>(m, ds, begin, end, out_mode);
   return launch_event_T<T, 4, 4, GRAD>(m, ds, begin, end, out_mode);
 }
 
-int sop_events(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int precision, bool grad, int out_mode) {
+int sop_events(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int precision, bool grad, int out_mode,
+               bool norm_in_event) {
   if (end <= begin) {
     // empty range: write a zero result without a kernel
     double z[3 + kMaxParams] = {0};
@@ -1685,11 +1897,12 @@ int sop_events(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, 
     return GOO_OK;
   }
   if (precision == GOO_F32) {
-    return grad ? launch_event_sel<float, true>(m, ds, begin, end, out_mode)
-                : launch_event_sel<float, false>(m, ds, begin, end, out_mode);
+    return grad ? launch_event_sel<float, true>(m, ds, begin, end, out_mode, norm_in_event)
+                : launch_event_sel<float, false>(m, ds, begin, end, out_mode, norm_in_event);
   }
-  return grad ? launch_event_sel<double, true>(m, ds, begin, end, out_mode)
-              : launch_event_sel<double, false>(m, ds, begin, end, out_mode);
+  if (norm_in_event) return set_error(GOO_ERR_STATE, "sop_events: in-kernel normalisation is FP32 only");
+  return grad ? launch_event_sel<double, true>(m, ds, begin, end, out_mode, false)
+              : launch_event_sel<double, false>(m, ds, begin, end, out_mode, false);
 }
 
 template <typename T, int K, int L>

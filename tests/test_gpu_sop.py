@@ -62,6 +62,24 @@ def test_c2_grid_nll_grad(goo, ctx, precision):
     _check(goo, ctx, spec, synth.gen_c2(n=200_000, seed=21), theta, precision)
 
 
+@pytest.mark.parametrize("bins", [[2000, 30, 16], [2000, 40, 16]])
+def test_grid_normalised_in_the_event_kernel_and_apart(goo, ctx, bins):
+    # the FP32 event kernel normalises a separable grid itself up to 4096 1-D bins summed over
+    # the leaves (2 x 2046 here) and leaves larger grids to the normalisation kernel (2 x 2056):
+    # both against the oracle's full midpoint grid
+    spec = synth.c2_spec()
+    spec["norm"] = ("grid", bins)
+    theta = np.array(synth.param_values(spec)) * 1.003
+    _check(goo, ctx, spec, synth.gen_c2(n=100_000, seed=23), theta, "f32")
+    cols = _data(spec, synth.gen_c2(n=100_000, seed=23), "f32")
+    ds = goo.Dataset.from_spec(ctx, spec, cols)
+    model = goo.Model(ctx, spec)
+    full, gfull = model.nll_grad(ds, theta, "f32")
+    parts = [model.nll_partial(ds, a, b, theta, "f32") for a, b in ((0, 777), (777, 50_001), (50_001, 100_000))]
+    tot = goo.combine_partials(parts, model.n_params)
+    assert abs(tot[0] + tot[1] - full) <= 1e-9 * abs(full)
+
+
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 def test_c2_normalise_matches_oracle_grid(goo, ctx, precision):
     spec = synth.c2_spec()
