@@ -768,11 +768,11 @@ __device__ __forceinline__ void leaf_eval2(const LeafReg<float>& L, float2 x, fl
 }
 
 // Two events: log f per lane, ok per lane (f > 0) and, if GRAD, c_k and the leaf derivatives.
+// xl[k][l] holds the observable of leaf l of product k.
 template <int K, int L, bool GRAD>
 __device__ __forceinline__ void eval_event2(const EvConst<float, K, L>& P, const float (&off_hi)[K],
-                                            const float (&off_lo)[K], float2 x0, float2 x1, float2 x2, float2 x3,
-                                            float2& logf, bool& ok0, bool& ok1, float2 (&ck)[K],
-                                            float2 (&dk)[K][L][3]) {
+                                            const float (&off_lo)[K], const float2 (&xl)[K][L], float2& logf,
+                                            bool& ok0, bool& ok1, float2 (&ck)[K], float2 (&dk)[K][L][3]) {
   using namespace pk;
   float2 rk[K], ak[K];
 #pragma unroll
@@ -781,7 +781,7 @@ __device__ __forceinline__ void eval_event2(const EvConst<float, K, L>& P, const
 #pragma unroll
     for (int l = 0; l < L; ++l) {
       float2 lr_, la_;
-      leaf_eval2<GRAD>(P.leaf[k][l], pick(P.leaf[k][l].col, x0, x1, x2, x3), lr_, la_, dk[k][l]);
+      leaf_eval2<GRAD>(P.leaf[k][l], xl[k][l], lr_, la_, dk[k][l]);
       r = mul(r, lr_);
       a = add(a, la_);
     }
@@ -941,11 +941,11 @@ struct PairAcc {
 // One event pair: evaluate and accumulate the lanes that are in range (v0, v1) with f > 0.
 template <int K, int L, bool GRAD>
 __device__ __forceinline__ void pair_step(const EvConst<float, K, L>& P, const float (&off_hi)[K],
-                                          const float (&off_lo)[K], const float2 (&x)[kMaxObs], bool v0, bool v1,
+                                          const float (&off_lo)[K], const float2 (&xl)[K][L], bool v0, bool v1,
                                           PairAcc<K, L>& S) {
   float2 logf, ck[K], dk[K][L][3];
   bool ok0, ok1;
-  eval_event2<K, L, GRAD>(P, off_hi, off_lo, x[0], x[1], x[2], x[3], logf, ok0, ok1, ck, dk);
+  eval_event2<K, L, GRAD>(P, off_hi, off_lo, xl, logf, ok0, ok1, ck, dk);
   const bool m0 = v0 && ok0, m1 = v1 && ok1;
   S.bad += (unsigned)(v0 && !ok0) + (unsigned)(v1 && !ok1);
   if (m0 && m1) {
@@ -1057,15 +1057,22 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
     const bool ok_wait = mbar_wait(&s_bar[st], (unsigned)(j / NST) & 1u);
     if (ok_wait) {
       if (full(t)) {
-        // every event of the tile is in range: read the staged columns
+        // every event of the tile is in range: each leaf reads its own staged column (an
+        // unused leaf slot reads column 0 and is ignored)
+        int coff[K][L];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+          for (int l = 0; l < L; ++l) coff[k][l] = (st * nobs + P.leaf[k][l].col) * TE;
 #pragma unroll 1
         for (int u = 0; u < PPT; ++u) {
           const int pr = threadIdx.x + u * kBlock;
-          float2 x[kMaxObs];
+          float2 xl[K][L];
 #pragma unroll
-          for (int c = 0; c < kMaxObs; ++c)
-            x[c] = c < nobs ? reinterpret_cast<const float2*>(buf(st, c))[pr] : splat(0.f);
-          pair_step<K, L, GRAD>(P, off_hi, off_lo, x, true, true, S);
+          for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int l = 0; l < L; ++l) xl[k][l] = reinterpret_cast<const float2*>(s_col + coff[k][l])[pr];
+          pair_step<K, L, GRAD>(P, off_hi, off_lo, xl, true, true, S);
         }
       } else {
 #pragma unroll 1
@@ -1082,7 +1089,12 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
               else if (v1) x[c].y = cols.c[c][i + 1];
             }
           }
-          if (v0 || v1) pair_step<K, L, GRAD>(P, off_hi, off_lo, x, v0, v1, S);
+          float2 xl[K][L];
+#pragma unroll
+          for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int l = 0; l < L; ++l) xl[k][l] = pick(P.leaf[k][l].col, x[0], x[1], x[2], x[3]);
+          if (v0 || v1) pair_step<K, L, GRAD>(P, off_hi, off_lo, xl, v0, v1, S);
         }
       }
     }
