@@ -348,19 +348,18 @@ __device__ __forceinline__ bool last_block_reduce(const float2* partials, int ns
   const int s = threadIdx.x / per, g = threadIdx.x % per;
   ddf acc = {0.f, 0.f};
   if (s < nslots) {
-    // eight independent loads in flight before they are added in block order
-    constexpr int U = 8;
-    int b = g;
-    for (; b + (U - 1) * per < nblocks; b += U * per) {
+    // rounds of sixteen independent loads in flight (the last round padded with exact zeros),
+    // added in block order: one L2 round trip per round
+    constexpr int U = 16;
+    for (int b = g; b < nblocks; b += U * per) {
       float2 q[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) q[u] = __ldcg(partials + (size_t)(b + u * per) * nslots + s);
+      for (int u = 0; u < U; ++u) {
+        const int bb = b + u * per;
+        q[u] = bb < nblocks ? __ldcg(partials + (size_t)bb * nslots + s) : make_float2(0.f, 0.f);
+      }
 #pragma unroll
       for (int u = 0; u < U; ++u) acc = dd_add(acc, {q[u].x, q[u].y});
-    }
-    for (; b < nblocks; b += per) {
-      const float2 q = __ldcg(partials + (size_t)b * nslots + s);
-      acc = dd_add(acc, {q.x, q.y});
     }
   }
   const int wper = per < 32 ? per : 32;

@@ -230,9 +230,10 @@ __device__ __forceinline__ void coh_finish(const CohArgs<T>& a, CohAcc<T, KB>& a
   const int off = out_mode == 0 ? 2 : 3;
   for (int p = threadIdx.x; p < P; p += blockDim.x) result[off + p] = s_g[p];
   if (threadIdx.x == 0) {
-    const unsigned nbad = atomicAdd(counters + 1, 0u);
+    // every other block added to these words before its ticket (and a fence): plain L2 reads
+    const unsigned nbad = __ldcg(counters + 1);
+    const unsigned status = __ldcg(counters + kStatusWord);
     counters[1] = 0u;
-    const unsigned status = atomicAdd(counters + kStatusWord, 0u);
     counters[kStatusWord] = 0u;
     const double N = s_N;
     const double nll = -s_out[0] + nev * log(N);
