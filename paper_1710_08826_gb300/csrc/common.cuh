@@ -327,12 +327,9 @@ __device__ __forceinline__ void block_reduce_to_partials(ddf (&v)[NS], int nslot
   }
 }
 
-// After every block has written its partials: take a ticket; the block that draws the
-// last ticket reduces partials[0 .. nblocks) lane by lane (blocks in index order within
-// each of the block's threads, then a fixed xor tree) into out[s] (FP64).  Returns true
-// in the last block.  The ticket counter is reset by the last block.
-__device__ __forceinline__ bool last_block_reduce(const float2* partials, int nslots, int nblocks,
-                                                  unsigned* ticket, double* out, ddf* smem) {
+// After every block has written its partials: take a ticket.  True in the block that draws
+// the last one; every partial is then visible to it.  The caller resets the ticket.
+__device__ __forceinline__ bool last_block_ticket(unsigned* ticket, int nblocks) {
   __shared__ bool is_last;
   __threadfence();
   __syncthreads();
@@ -340,14 +337,21 @@ __device__ __forceinline__ bool last_block_reduce(const float2* partials, int ns
   __syncthreads();
   if (!is_last) return false;
   __threadfence();
-  // Each lane s is summed by `per` consecutive threads (per = a power of two): thread g of
-  // the group adds blocks g, g + per, ...; the group is then combined by an xor tree (and,
-  // for groups wider than a warp, by the warps in index order).
+  return true;
+}
+
+// Lane sums of partials[0 .. nblocks) by threads [0, nthreads) of the block (every thread of
+// the block calls it): lane s is summed by `per` consecutive threads (per a power of two),
+// thread g of the group adding blocks g, g + per, ... in order; the group is combined by an
+// xor tree (and, for groups wider than a warp, by the warps in index order) into out[s]
+// (FP64).  Ends with a block barrier.
+__device__ __forceinline__ void reduce_partials(const float2* partials, int nslots, int nblocks, double* out,
+                                                ddf* smem, int nthreads) {
   int per = 1;
-  while (per * 2 * nslots <= (int)blockDim.x) per *= 2;
+  while (per * 2 * nslots <= nthreads) per *= 2;
   const int s = threadIdx.x / per, g = threadIdx.x % per;
   ddf acc = {0.f, 0.f};
-  if (s < nslots) {
+  if (s < nslots && (int)threadIdx.x < nthreads) {
     // rounds of sixteen independent loads in flight (the last round padded with exact zeros),
     // added in block order: one L2 round trip per round
     constexpr int U = 16;
@@ -365,7 +369,7 @@ __device__ __forceinline__ bool last_block_reduce(const float2* partials, int ns
   const int wper = per < 32 ? per : 32;
   for (int m = wper / 2; m > 0; m >>= 1) acc = dd_add(acc, dd_shfl_xor(acc, m));
   if (per <= 32) {
-    if (g == 0 && s < nslots) out[s] = dd_to_double(acc);
+    if (g == 0 && s < nslots && (int)threadIdx.x < nthreads) out[s] = dd_to_double(acc);
   } else {
     if ((threadIdx.x & 31) == 0) smem[threadIdx.x >> 5] = acc;
     __syncthreads();
@@ -377,6 +381,14 @@ __device__ __forceinline__ bool last_block_reduce(const float2* partials, int ns
     }
   }
   __syncthreads();
+}
+
+// The ticket and the reduction by every thread; returns true in the last block, which also
+// resets the ticket.
+__device__ __forceinline__ bool last_block_reduce(const float2* partials, int nslots, int nblocks,
+                                                  unsigned* ticket, double* out, ddf* smem) {
+  if (!last_block_ticket(ticket, nblocks)) return false;
+  reduce_partials(partials, nslots, nblocks, out, smem, blockDim.x);
   if (threadIdx.x == 0) *ticket = 0u;
   return true;
 }

@@ -185,23 +185,23 @@ __device__ __forceinline__ void coh_finish(const CohArgs<T>& a, CohAcc<T, KB>& a
     if (b) atomicAdd(counters + 1, b);
   }
   __shared__ double s_out[NS];
-  if (!last_block_reduce(partials, NS, gridDim.x, counters, s_out, s_red)) return;
-  // FP64 combination in parallel: the Gram matrix is staged in shared memory, lane k of
-  // warp 0 forms v_k = sum_l G_kl conj(c_l), N = sum_k Re(c_k v_k) by a fixed xor tree, and
-  // one thread scatters the per-coefficient gradients (parameters may be shared).
-  __shared__ double s_G[2 * kMaxAmp * kMaxAmp];
-  __shared__ double s_gre[kMaxAmp], s_gim[kMaxAmp];
-  __shared__ double s_N;
+  if (!last_block_ticket(counters, gridDim.x)) return;
+  // The last block: its last warp forms the normalisation, which depends on theta and the
+  // Gram matrix only, while the other threads reduce the blocks' lanes.  Lane k of that warp
+  // forms v_k = sum_l G_kl conj(c_l), N = sum_k Re(c_k v_k) by a fixed xor tree, and the
+  // normalisation parts of the coefficient gradients, 2 v_k / N; then thread p gathers the
+  // gradient of parameter p (parameters may be shared) in a fixed order.
+  __shared__ double s_vr[kMaxAmp], s_vi[kMaxAmp];
+  __shared__ int s_pre[kMaxAmp], s_pim[kMaxAmp];
+  __shared__ double s_N, s_logN;
   const int K = a.K;
-  for (int t = threadIdx.x; t < 2 * K * K; t += blockDim.x) s_G[t] = gram[t];
-  __syncthreads();
-  const double nev = (double)(end - begin);
-  if (threadIdx.x < 32) {
-    const int k = threadIdx.x;
+  const int nwarp = blockDim.x >> 5;
+  if ((int)(threadIdx.x >> 5) == nwarp - 1) {
+    const int k = threadIdx.x & 31;
     double vr = 0.0, vi = 0.0, Nk = 0.0;
     if (k < K) {
       for (int l = 0; l < K; ++l) {
-        const double gr = s_G[2 * (k * K + l)], gi = s_G[2 * (k * K + l) + 1];
+        const double gr = __ldg(gram + 2 * (k * K + l)), gi = __ldg(gram + 2 * (k * K + l) + 1);
         const double clr = (double)a.cr[l], cli = (double)a.ci[l];
         vr += gr * clr + gi * cli;  // v_k = sum_l G_kl conj(c_l)
         vi += gi * clr - gr * cli;
@@ -210,39 +210,46 @@ __device__ __forceinline__ void coh_finish(const CohArgs<T>& a, CohAcc<T, KB>& a
     }
     double N = Nk;
     for (int m = 16; m > 0; m >>= 1) N += __shfl_xor_sync(0xffffffffu, N, m);
-    if (k < K && GRAD) {
-      const int slot = (k < a.nbw) ? k : KB;  // NR lives in the last slot
-      s_gre[k] = -2.0 * s_out[1 + 2 * slot] + nev * 2.0 * vr / N;
-      s_gim[k] = 2.0 * s_out[2 + 2 * slot] - nev * 2.0 * vi / N;
+    const double invN = 1.0 / N;
+    if (k < K) {
+      s_vr[k] = 2.0 * vr * invN;
+      s_vi[k] = 2.0 * vi * invN;
+      s_pre[k] = a.par_re[k];
+      s_pim[k] = a.par_im[k];
     }
-    if (k == 0) s_N = N;
+    if (k == 0) {
+      s_N = N;
+      s_logN = log(N);
+    }
   }
-  __shared__ double s_g[kMaxParams];
+  reduce_partials(partials, NS, gridDim.x, s_out, s_red, blockDim.x - 32);
+  const double nev = (double)(end - begin);
   const int P = a.n_params;
-  for (int p = threadIdx.x; p < P; p += blockDim.x) s_g[p] = 0.0;
-  __syncthreads();
-  if (threadIdx.x == 0 && GRAD)
-    for (int k = 0; k < K; ++k) {
-      s_g[a.par_re[k]] += s_gre[k];
-      s_g[a.par_im[k]] += s_gim[k];
-    }
-  __syncthreads();
   const int off = out_mode == 0 ? 2 : 3;
-  for (int p = threadIdx.x; p < P; p += blockDim.x) result[off + p] = s_g[p];
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    double g = 0.0;
+    if (GRAD)
+      for (int k = 0; k < K; ++k) {
+        const int slot = (k < a.nbw) ? k : KB;  // NR lives in the last slot
+        if (s_pre[k] == p) g += -2.0 * s_out[1 + 2 * slot] + nev * s_vr[k];
+        if (s_pim[k] == p) g += 2.0 * s_out[2 + 2 * slot] - nev * s_vi[k];
+      }
+    result[off + p] = g;
+  }
   if (threadIdx.x == 0) {
     // every other block added to these words before its ticket (and a fence): plain L2 reads
     const unsigned nbad = __ldcg(counters + 1);
     const unsigned status = __ldcg(counters + kStatusWord);
     counters[1] = 0u;
     counters[kStatusWord] = 0u;
-    const double N = s_N;
-    const double nll = -s_out[0] + nev * log(N);
+    *counters = 0u;  // the ticket
+    const double nll = -s_out[0] + nev * s_logN;
     // a device wait that gave up is reported as a negative event count
     const double nb = status ? -1.0 : (double)nbad;
     result[0] = nll;
     if (out_mode == 0) {
       result[1] = nb;
-      result[2 + P] = N;
+      result[2 + P] = s_N;
     } else {
       result[1] = 0.0;
       result[2] = nb;

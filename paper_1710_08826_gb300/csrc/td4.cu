@@ -394,25 +394,26 @@ __device__ __forceinline__ void td4_finish(const Td4Args<T>& a, TdAcc<T, KB>& ac
     if (b) atomicAdd(counters + 1, b);
   }
   __shared__ double s_out[NS];
-  if (!last_block_reduce(partials, NS, gridDim.x, counters, s_out, s_red)) return;
-  // FP64 combination: lane k of warp 0 forms v_c = sum_l G_kl conj(c_l), v_b likewise
-  __shared__ double s_G[2 * kTdMaxAmp * kTdMaxAmp];
-  __shared__ double s_gre[kTdMaxAmp], s_gim[kTdMaxAmp], s_gt[4];
-  __shared__ double s_N;
-  __shared__ double s_g[kMaxParams];
-  const int K = a.K, P = a.n_params;
-  for (int q = threadIdx.x; q < 2 * K * K; q += blockDim.x) s_G[q] = gram[q];
-  for (int p = threadIdx.x; p < P; p += blockDim.x) s_g[p] = 0.0;
-  __syncthreads();
-  const double nev = (double)(end - begin);
-  const double x = (double)a.x, y = (double)a.y, tau = 1.0 / (double)a.G;
-  const double Ich = tau / (1 - y * y), Ish = y * tau / (1 - y * y), Ic = tau / (1 + x * x), Is = x * tau / (1 + x * x);
-  if (threadIdx.x < 32) {
-    const int k = threadIdx.x;
+  if (!last_block_ticket(counters, gridDim.x)) return;
+  // The last block: its last warp forms the normalisation, which depends on theta and the
+  // Gram matrix only, while the other threads reduce the blocks' lanes.  Lane k of that warp
+  // forms v_c = sum_l G_kl conj(c_l) and v_b likewise, the four moments <|A|^2>, <|B|^2>,
+  // <A B*> by fixed xor trees, N with the time integrals, and the normalisation parts of the
+  // gradients (d N / d theta) / N; then thread p gathers the gradient of parameter p.
+  __shared__ double s_ur[kTdMaxAmp], s_ui[kTdMaxAmp], s_dt[3];
+  __shared__ int s_pre[kTdMaxAmp], s_pim[kTdMaxAmp], s_pt[4];
+  __shared__ double s_N, s_logN;
+  const int K = a.K;
+  const int nwarp = blockDim.x >> 5;
+  if ((int)(threadIdx.x >> 5) == nwarp - 1) {
+    const int k = threadIdx.x & 31;
+    const double x = (double)a.x, y = (double)a.y, tau = 1.0 / (double)a.G;
+    const double iy = 1.0 / (1 - y * y), ix = 1.0 / (1 + x * x);
+    const double Ich = tau * iy, Ish = y * tau * iy, Ic = tau * ix, Is = x * tau * ix;
     double vcr = 0, vci = 0, vbr = 0, vbi = 0, aa = 0, bb = 0, abr = 0, abi = 0;
     if (k < K) {
       for (int l = 0; l < K; ++l) {
-        const double gr = s_G[2 * (k * K + l)], gi = s_G[2 * (k * K + l) + 1];
+        const double gr = __ldg(gram + 2 * (k * K + l)), gi = __ldg(gram + 2 * (k * K + l) + 1);
         const double clr = (double)a.cr[l], cli = (double)a.ci[l], blr = (double)a.br[l], bli = (double)a.bi[l];
         vcr += gr * clr + gi * cli;  // G_kl conj(c_l)
         vci += gi * clr - gr * cli;
@@ -432,53 +433,55 @@ __device__ __forceinline__ void td4_finish(const Td4Args<T>& a, TdAcc<T, KB>& ac
       abi += __shfl_xor_sync(0xffffffffu, abi, m);
     }
     const double N = 0.5 * (aa + bb) * Ich + 0.5 * (aa - bb) * Ic + abr * Ish + abi * Is;
-    if (k < K && GRAD) {
+    const double invN = 1.0 / N;
+    if (k < K) {
       // dN/dRe c_k = Re((I_ch + I_c) v_c + (I_sh - i I_s) v_b), dN/dIm c_k = -Im(same)
-      const double ur = (Ich + Ic) * vcr + Ish * vbr + Is * vbi;
-      const double ui = (Ich + Ic) * vci + Ish * vbi - Is * vbr;
-      s_gre[k] = -s_out[1 + 2 * k] + nev * ur / N;
-      s_gim[k] = -s_out[2 + 2 * k] - nev * ui / N;
+      s_ur[k] = ((Ich + Ic) * vcr + Ish * vbr + Is * vbi) * invN;
+      s_ui[k] = ((Ich + Ic) * vci + Ish * vbi - Is * vbr) * invN;
+      s_pre[k] = a.par_re[k];
+      s_pim[k] = a.par_im[k];
     }
+    if (k < 4) s_pt[k] = a.par_t[k];
     if (k == 0) {
       s_N = N;
-      if (GRAD) {
-        const double dxc = -2 * x * tau / ((1 + x * x) * (1 + x * x)), dxs = tau * (1 - x * x) / ((1 + x * x) * (1 + x * x));
-        const double dych = 2 * y * tau / ((1 - y * y) * (1 - y * y)), dysh = tau * (1 + y * y) / ((1 - y * y) * (1 - y * y));
-        const double dNx = 0.5 * (aa - bb) * dxc + abi * dxs;
-        const double dNy = 0.5 * (aa + bb) * dych + abr * dysh;
-        const double dNt = 0.5 * (aa + bb) / (1 - y * y) + 0.5 * (aa - bb) / (1 + x * x) + abr * y / (1 - y * y) +
-                           abi * x / (1 + x * x);
-        const int o = 1 + 2 * KB;
-        s_gt[0] = -s_out[o] + nev * dNx / N;
-        s_gt[1] = -s_out[o + 1] + nev * dNy / N;
-        s_gt[2] = -s_out[o + 2] + nev * dNt / N;
-        s_gt[3] = -s_out[o + 3];
-      }
+      s_logN = log(N);
+      const double ix2 = ix * ix, iy2 = iy * iy;
+      const double dxc = -2 * x * tau * ix2, dxs = tau * (1 - x * x) * ix2;
+      const double dych = 2 * y * tau * iy2, dysh = tau * (1 + y * y) * iy2;
+      s_dt[0] = (0.5 * (aa - bb) * dxc + abi * dxs) * invN;  // (dN/dx) / N
+      s_dt[1] = (0.5 * (aa + bb) * dych + abr * dysh) * invN;
+      s_dt[2] = (0.5 * (aa + bb) * iy + 0.5 * (aa - bb) * ix + abr * y * iy + abi * x * ix) * invN;  // tau dN/dtau / N
     }
   }
-  __syncthreads();
-  if (threadIdx.x == 0 && GRAD) {
-    for (int k = 0; k < K; ++k) {
-      s_g[a.par_re[k]] += s_gre[k];
-      s_g[a.par_im[k]] += s_gim[k];
-    }
-    for (int j = 0; j < 4; ++j) s_g[a.par_t[j]] += s_gt[j];
-  }
-  __syncthreads();
+  reduce_partials(partials, NS, gridDim.x, s_out, s_red, blockDim.x - 32);
+  const double nev = (double)(end - begin);
+  const int P = a.n_params;
   const int off = out_mode == 0 ? 2 : 3;
-  for (int p = threadIdx.x; p < P; p += blockDim.x) result[off + p] = s_g[p];
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    double g = 0.0;
+    if (GRAD) {
+      for (int k = 0; k < K; ++k) {
+        if (s_pre[k] == p) g += -s_out[1 + 2 * k] + nev * s_ur[k];
+        if (s_pim[k] == p) g += -s_out[2 + 2 * k] - nev * s_ui[k];
+      }
+      const int o = 1 + 2 * KB;
+      for (int j = 0; j < 4; ++j)
+        if (s_pt[j] == p) g += -s_out[o + j] + (j < 3 ? nev * s_dt[j] : 0.0);
+    }
+    result[off + p] = g;
+  }
   if (threadIdx.x == 0) {
     // every other block added to these words before its ticket (and a fence): plain L2 reads
     const unsigned nbad = __ldcg(counters + 1);
     const unsigned status = __ldcg(counters + kStatusWord);
     counters[1] = 0u;
     counters[kStatusWord] = 0u;
-    const double N = s_N;
+    *counters = 0u;  // the ticket
     const double nb = status ? -1.0 : (double)nbad;  // a wait that gave up: negative count
-    result[0] = -s_out[0] + nev * log(N);
+    result[0] = -s_out[0] + nev * s_logN;
     if (out_mode == 0) {
       result[1] = nb;
-      result[2 + P] = N;
+      result[2 + P] = s_N;
     } else {
       result[1] = 0.0;
       result[2] = nb;
