@@ -216,6 +216,20 @@ int goo_eval_logf(goo_model* model, const goo_dataset* ds, const double* theta, 
 int goo_gram(goo_model* model, const double* theta, int precision, double* out, int* K_out);
 int goo_amplitude_cache(goo_model* model, const goo_dataset* ds, const double* theta, int precision,
                         const void** dev_ptr, int* n_amp);
+/* Lineshape handling of a GOO_OP_COHERENT model (paper Sec. 4: cached lineshapes, recomputed
+ * when their parameters change).
+ *   GOO_LINESHAPE_CACHED (default): the amplitude cache and the MC Gram matrix hold the
+ *     lineshapes; the NLL is exact at any theta, but goo_nll_grad returns 0 for the
+ *     resonance masses and widths (constants of the cache), and goo_fit refuses to free them
+ *     with the adjoint gradient.
+ *   GOO_LINESHAPE_FLOATING: goo_nll / goo_nll_grad / goo_nll_partial evaluate every
+ *     Breit-Wigner amplitude per event and per MC point on each call (no cache, no Gram
+ *     matrix), with d A / d m0 and d A / d Gamma0 from the lineshape formula, so the gradient
+ *     covers every parameter; N is the MC mean of |S|^2 at theta.  goo_normalise,
+ *     goo_eval_logf and goo_gram keep using the cache.
+ * GOO_ERR_UNSUPPORTED for other models, GOO_ERR_ARG for another mode. */
+enum { GOO_LINESHAPE_CACHED = 0, GOO_LINESHAPE_FLOATING = 1 };
+int goo_model_set_lineshapes(goo_model* model, int mode);
 
 /* ---- fitting (paper: the FitManager, Fig. 1; Minuit 2 as the default minimiser, Sec. 4) -------
  * Minimises the NLL of `model` on `ds` over the parameters with free_mask[p] != 0, starting

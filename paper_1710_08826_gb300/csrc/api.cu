@@ -260,6 +260,12 @@ int goo_gram(goo_model* m, const double* theta, int precision, double* out, int*
   return dalitz_gram(m, theta, precision, out, K_out);
 }
 
+int goo_model_set_lineshapes(goo_model* m, int mode) {
+  if (!m) return set_error(GOO_ERR_ARG, "goo_model_set_lineshapes: NULL model");
+  if (m->kind != 1) return set_error(GOO_ERR_UNSUPPORTED, "goo_model_set_lineshapes: not a three-body amplitude model");
+  return dalitz_set_lineshapes(m, mode);
+}
+
 int goo_amplitude_cache(goo_model* m, const goo_dataset* ds, const double* theta, int precision, const void** dev_ptr,
                         int* n_amp) {
   if (!m || !ds || !dev_ptr || !n_amp) return set_error(GOO_ERR_ARG, "goo_amplitude_cache: NULL argument");

@@ -57,6 +57,8 @@ struct DalitzModel {
   double gram_host[2][kMaxAmp * kMaxAmp * 2];
   uint64_t gram_key[2] = {0, 0};
   const goo_dataset* mc = nullptr;
+  bool floating = false;           // GOO_LINESHAPE_FLOATING: no cache, lineshape gradients
+  double* ls_mc = nullptr;         // MC-pass lane sums of the floating-lineshape path (device)
 };
 
 // Cache layout.  FP32: ceil(nbw/2) planes of float4 (re_k, im_k, re_k+1, im_k+1) per event;
@@ -476,6 +478,174 @@ static uint64_t lineshape_key(const DalitzModel& d, const double* theta) {
 }
 
 // Lineshape constants for the current theta (FP64, once per lineshape version).
+// ---------------------------------------------------------------------------------------
+// floating lineshapes (masses and widths free; paper Sec. 4: the cache is then invalid at
+// every step).  No amplitude cache: each evaluation runs a pass over the MC sample and one
+// over the events, and both evaluate every Breit-Wigner amplitude from (s12, s13) with the
+// parts of its denominator D = m0^2 - s - i m0 Gamma(s), which give
+//   d log A / d m0     = rho - (2 m0 - i kappa m0 Gamma(s)) / D,
+//   d log A / d Gamma0 = i m0 Gamma(s) / (Gamma0 D),
+// where rho = d log(B_L(z) / B_L(z0)) / d m0 (through q0) and kappa = d log(m0 Gamma(s)) /
+// d m0 = 2 / m0 - (2L + 1) d log q0 / d m0 + 2 rho are constants of the resonance (the
+// spin and parent-barrier factors do not depend on m0 or Gamma0).  Lanes: 0 = sum log |S|^2
+// (events) or sum |S|^2 (MC); then per amplitude slot Re / Im of A_k conj(S) w; then per
+// resonance Re(c_k A_k conj(S) w d log A_k / d m0) and the same for Gamma0, with w = 1 / |S|^2
+// for events and 1 for MC points.  The event pass's last block combines both passes:
+//   NLL = -sum log |S|^2 + n log(sum_MC |S|^2 / n_MC),
+//   d NLL / d p = -sum_events (d |S|^2 / d p) / |S|^2 + n (sum_MC d |S|^2 / d p) / sum_MC |S|^2.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+struct LsConst {
+  T cr[kMaxAmp], ci[kMaxAmp];          // coefficients by slot: resonances, then the NR in slot KB
+  T rho[kMaxAmp], kappa[kMaxAmp], two_m0[kMaxAmp], inv_g0[kMaxAmp];
+  int par_m0[kMaxAmp], par_w[kMaxAmp];
+};
+
+template <int KB, bool GRAD>
+struct LsLanes {
+  static constexpr int NS = GRAD ? 1 + 2 * (KB + 1) + 2 * KB : 1;
+};
+
+template <typename T, int KB, bool GRAD, bool MC>
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1)
+    coh_ls_kernel(const __grid_constant__ CohArgs<T> a, const __grid_constant__ LsConst<T> c,
+                  const DalitzDev* __restrict__ ddp, const T* __restrict__ c12, const T* __restrict__ c13,
+                  int64_t begin, int64_t end, const double* __restrict__ mc_sums, double n_mc, float2* partials,
+                  unsigned* counters, double* out, int out_mode) {
+  constexpr int KA = KB + 1;
+  constexpr int NS = LsLanes<KB, GRAD>::NS;
+  __shared__ DalitzDev s_dd;
+  __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
+  __shared__ unsigned s_bad[kBlock / 32];
+  __shared__ double s_out[NS];
+  for (int i = threadIdx.x; i < (int)(sizeof(DalitzDev) / 4); i += blockDim.x) ((int*)&s_dd)[i] = ((const int*)ddp)[i];
+  __syncthreads();
+  const int nbw = s_dd.nbw;
+  Kahan lf32;
+  double lf64 = 0.0;
+  T gre[KA], gim[KA], gm[KB], gg[KB];
+#pragma unroll
+  for (int k = 0; k < KA; ++k) gre[k] = gim[k] = T(0);
+#pragma unroll
+  for (int k = 0; k < KB; ++k) gm[k] = gg[k] = T(0);
+  unsigned bad = 0;
+  for (int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T x12 = c12[i], x13 = c13[i];
+    T x23;
+    if constexpr (sizeof(T) == 4) x23 = (float)(s_dd.sumsq - (double)x12 - (double)x13);
+    else x23 = s_dd.sumsq - x12 - x13;
+    T ar[KA], ai[KA], dr[KB], di[KB], iv[KB];
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      ar[k] = ai[k] = dr[k] = di[k] = iv[k] = T(0);
+      if (k < nbw) bw_amp_parts<T>(bw_of<T>(s_dd, k), x12, x13, x23, ar[k], ai[k], dr[k], di[k], iv[k]);
+    }
+    ar[KB] = T(1);
+    ai[KB] = T(0);
+    T sr = T(0), si = T(0);
+#pragma unroll
+    for (int k = 0; k < KA; ++k) {
+      sr += c.cr[k] * ar[k] - c.ci[k] * ai[k];
+      si += c.cr[k] * ai[k] + c.ci[k] * ar[k];
+    }
+    const T s2 = sr * sr + si * si;
+    if (!MC && !(s2 > T(0))) {
+      ++bad;
+      continue;
+    }
+    if constexpr (sizeof(T) == 4) lf32.add(MC ? s2 : __logf(s2));
+    else lf64 += MC ? s2 : log(s2);
+    if constexpr (GRAD) {
+      const T w = MC ? T(1) : T(1) / s2;
+      const T tr = sr * w, ti = -si * w;  // conj(S) w
+#pragma unroll
+      for (int k = 0; k < KA; ++k) {
+        const T ur = ar[k] * tr - ai[k] * ti, ui = ar[k] * ti + ai[k] * tr;  // A_k conj(S) w
+        gre[k] += ur;
+        gim[k] += ui;
+        if (k < KB) {
+          const T vr = c.cr[k] * ur - c.ci[k] * ui, vi = c.cr[k] * ui + c.ci[k] * ur;  // c_k A_k conj(S) w
+          const T e2 = di[k] * iv[k];
+          const T lmr = c.rho[k] - (c.two_m0[k] * dr[k] + c.kappa[k] * di[k] * di[k]) * iv[k];
+          const T lmi = -(c.two_m0[k] - c.kappa[k] * dr[k]) * e2;
+          const T lgr = -di[k] * e2 * c.inv_g0[k], lgi = dr[k] * e2 * c.inv_g0[k];
+          gm[k] += vr * lmr - vi * lmi;
+          gg[k] += vr * lgr - vi * lgi;
+        }
+      }
+    }
+  }
+  ddf v[NS];
+  v[0] = (sizeof(T) == 4) ? lf32.value() : dd_from_double(lf64);
+  if constexpr (GRAD) {
+#pragma unroll
+    for (int k = 0; k < KA; ++k) {
+      v[1 + 2 * k] = (sizeof(T) == 4) ? ddf{(float)gre[k], 0.f} : dd_from_double((double)gre[k]);
+      v[2 + 2 * k] = (sizeof(T) == 4) ? ddf{(float)gim[k], 0.f} : dd_from_double((double)gim[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      v[1 + 2 * KA + 2 * k] = (sizeof(T) == 4) ? ddf{(float)gm[k], 0.f} : dd_from_double((double)gm[k]);
+      v[2 + 2 * KA + 2 * k] = (sizeof(T) == 4) ? ddf{(float)gg[k], 0.f} : dd_from_double((double)gg[k]);
+    }
+  }
+  for (int m = 16; m > 0; m >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, m);
+  if ((threadIdx.x & 31) == 0) s_bad[threadIdx.x >> 5] = bad;
+  block_reduce_to_partials<NS>(v, NS, partials, s_red);
+  if (threadIdx.x == 0) {
+    unsigned b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_bad[w];
+    if (b) atomicAdd(counters + 1, b);
+  }
+  if (!last_block_ticket(counters, gridDim.x)) return;
+  reduce_partials(partials, NS, gridDim.x, s_out, s_red, blockDim.x);
+  if constexpr (MC) {
+    // the MC pass ends with its lane sums (read by the event pass that follows it)
+    for (int t = threadIdx.x; t < NS; t += blockDim.x) out[t] = s_out[t];
+    if (threadIdx.x == 0) *counters = 0u;  // the ticket
+    return;
+  }
+  const double nev = (double)(end - begin);
+  const double Smc = mc_sums[0];
+  const int P = a.n_params;
+  const int off = out_mode == 0 ? 2 : 3;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    double g = 0.0;
+    if (GRAD) {
+      for (int kk = 0; kk < a.K; ++kk) {
+        const int sl = kk < a.nbw ? kk : KB;  // the NR lives in the last slot
+        if (a.par_re[kk] == p) g += -2.0 * s_out[1 + 2 * sl] + 2.0 * nev * mc_sums[1 + 2 * sl] / Smc;
+        if (a.par_im[kk] == p) g += 2.0 * s_out[2 + 2 * sl] - 2.0 * nev * mc_sums[2 + 2 * sl] / Smc;
+      }
+      for (int k = 0; k < a.nbw; ++k) {
+        const int o = 1 + 2 * KA + 2 * k;
+        if (c.par_m0[k] == p) g += -2.0 * s_out[o] + 2.0 * nev * mc_sums[o] / Smc;
+        if (c.par_w[k] == p) g += -2.0 * s_out[o + 1] + 2.0 * nev * mc_sums[o + 1] / Smc;
+      }
+    }
+    out[off + p] = g;
+  }
+  if (threadIdx.x == 0) {
+    // every other block added to these words before its ticket (and a fence): plain L2 reads
+    const unsigned nbad = __ldcg(counters + 1);
+    const unsigned status = __ldcg(counters + kStatusWord);
+    counters[1] = 0u;
+    counters[kStatusWord] = 0u;
+    *counters = 0u;  // the ticket
+    const double N = Smc / n_mc;
+    const double nb = status ? -1.0 : (double)nbad;  // a device wait that gave up: negative count
+    out[0] = -s_out[0] + nev * log(N);
+    if (out_mode == 0) {
+      out[1] = nb;
+      out[2 + P] = N;
+    } else {
+      out[1] = 0.0;
+      out[2] = nb;
+    }
+  }
+}
+
 static int dalitz_constants(goo_model* m, const double* theta) {
   DalitzModel& d = *m->dalitz;
   const uint64_t key = lineshape_key(d, theta);
@@ -716,6 +886,92 @@ static int launch_coh_sel(goo_model* m, const void* cache, const goo_dataset* ds
   return launch_coh<T, 15, GRAD>(m, cache, ds, begin, end, theta, out_mode, pi);
 }
 
+// Constants of the floating-lineshape kernels at theta (FP64 on the host, rounded to T):
+// the coefficients by slot and, per resonance (mass m0, width Gamma0, spin L, daughters A, B),
+//   d(q0^2) / d m0 = (m0^4 - (mA + mB)^2 (mA - mB)^2) / (2 m0^3),
+//   rho   = F'(z0) / (2 F(z0)) r^2 d(q0^2) / d m0   (F(z) = 1 + z for L = 1, 9 + 3z + z^2 for
+//           L = 2: the squared barrier ratio is F(z0) / F(z); rho = 0 for L = 0),
+//   kappa = 2 / m0 - (2L + 1) d(q0^2) / d m0 / (2 q0^2) + 2 rho.
+template <typename T>
+static void fill_ls(const DalitzModel& d, const double* theta, LsConst<T>& c) {
+  std::memset(&c, 0, sizeof c);
+  for (int k = 0; k < d.nbw; ++k) {
+    c.cr[k] = (T)theta[d.par_re[k]];
+    c.ci[k] = (T)theta[d.par_im[k]];
+    c.par_m0[k] = d.par_m0[k];
+    c.par_w[k] = d.par_w[k];
+    double mA, mB, mC;
+    pair_masses(d, d.pair[k], mA, mB, mC);
+    const int L = d.spin[k];
+    const double m0 = theta[d.par_m0[k]], g0 = theta[d.par_w[k]];
+    const double u = m0 * m0, thrP = (mA + mB) * (mA + mB), thrM = (mA - mB) * (mA - mB);
+    const double q0sq = kallen(u, mA * mA, mB * mB) / (4 * u);
+    const double dq0sq = (u * u - thrP * thrM) / (2 * m0 * m0 * m0);
+    const double r2 = d.r_res * d.r_res, z0 = r2 * q0sq;
+    double rho = 0.0;
+    if (L == 1) rho = 0.5 / (1.0 + z0) * r2 * dq0sq;
+    if (L == 2) rho = 0.5 * (3.0 + 2.0 * z0) / (9.0 + 3.0 * z0 + z0 * z0) * r2 * dq0sq;
+    const double kappa = 2.0 / m0 - (2 * L + 1) * dq0sq / (2.0 * q0sq) + 2.0 * rho;
+    c.rho[k] = (T)rho;
+    c.kappa[k] = (T)kappa;
+    c.two_m0[k] = (T)(2.0 * m0);
+    c.inv_g0[k] = (T)(1.0 / g0);
+  }
+  for (int k = d.nbw; k < kMaxAmp; ++k) c.par_m0[k] = c.par_w[k] = -1;
+}
+
+template <typename T, int KB, bool GRAD, bool MC>
+static int launch_ls(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, const double* theta,
+                     double* out, int out_mode) {
+  DalitzModel& d = *m->dalitz;
+  goo_ctx* ctx = m->ctx;
+  static int occ[2] = {0, 0};
+  int& o = occ[MC ? 1 : 0];
+  if (o == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, coh_ls_kernel<T, KB, GRAD, MC>, kBlock, 0) != cudaSuccess ||
+        o < 1) {
+      cudaGetLastError();
+      o = 1;
+    }
+  }
+  const int nb = grid_blocks(ctx, end - begin, o);
+  constexpr int NS = LsLanes<KB, GRAD>::NS;
+  GOO_TRY(ensure_partials(ctx, (size_t)nb * NS));
+  CohArgs<T> a;
+  fill_args<T>(d, theta, m->n_params, ds->n, a);
+  LsConst<T> c;
+  fill_ls<T>(d, theta, c);
+  if (d.has_nr) {
+    c.cr[KB] = (T)theta[d.par_re[d.nbw]];
+    c.ci[KB] = (T)theta[d.par_im[d.nbw]];
+  }
+  const T* c12 = sizeof(T) == 4 ? (const T*)ds->d32[d.col12] : (const T*)ds->d64[d.col12];
+  const T* c13 = sizeof(T) == 4 ? (const T*)ds->d32[d.col13] : (const T*)ds->d64[d.col13];
+  {
+    LaunchScope ls(ctx, MC ? (sizeof(T) == 4 ? "coh_ls_mc_f32" : "coh_ls_mc_f64")
+                           : (sizeof(T) == 4 ? (GRAD ? "coh_ls_grad_f32" : "coh_ls_f32")
+                                             : (GRAD ? "coh_ls_grad_f64" : "coh_ls_f64")));
+    coh_ls_kernel<T, KB, GRAD, MC><<<nb, kBlock, 0, ctx->stream>>>(
+        a, c, d.dev, c12, c13, begin, end, d.ls_mc, (double)(d.mc ? d.mc->n : 0), ctx->scratch.partials,
+        ctx->scratch.counters, out, out_mode);
+  }
+  GOO_CUDA_TRY(cudaGetLastError());
+  return GOO_OK;
+}
+
+// The floating-lineshape evaluation: the MC pass, then the event pass over [begin, end).
+template <typename T, bool GRAD>
+static int launch_ls_pair(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, const double* theta,
+                          int out_mode) {
+  DalitzModel& d = *m->dalitz;
+  if (d.nbw <= 8) {
+    GOO_TRY((launch_ls<T, 8, GRAD, true>(m, d.mc, 0, d.mc->n, theta, d.ls_mc, 0)));
+    return launch_ls<T, 8, GRAD, false>(m, ds, begin, end, theta, m->ctx->scratch.result, out_mode);
+  }
+  GOO_TRY((launch_ls<T, 15, GRAD, true>(m, d.mc, 0, d.mc->n, theta, d.ls_mc, 0)));
+  return launch_ls<T, 15, GRAD, false>(m, ds, begin, end, theta, m->ctx->scratch.result, out_mode);
+}
+
 int build_dalitz_model(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_params, int n_obs, const double* lo,
                        const double* hi, goo_model* m) {
   const goo_node& root = nodes[n_nodes - 1];
@@ -798,6 +1054,7 @@ void dalitz_free(goo_model* m) {
   if (d->dev) cudaFree(d->dev);
   for (int i = 0; i < 2; ++i)
     if (d->gram_dev[i]) cudaFree(d->gram_dev[i]);
+  if (d->ls_mc) cudaFree(d->ls_mc);
   delete d;
   m->dalitz = nullptr;
 }
@@ -837,9 +1094,30 @@ int dalitz_nll(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, 
   const int P = m->n_params;
   if (ds->ncols <= d.col12 || ds->ncols <= d.col13) return set_error(GOO_ERR_ARG, "dataset lacks s12/s13 columns");
   GOO_TRY(dalitz_constants(m, theta));
+  const int nout = (out_mode == 0 ? 2 : 3) + P;
+  if (d.floating) {
+    // no cache and no Gram matrix: an MC pass and an event pass, lineshape gradients included
+    if (!d.mc) return set_error(GOO_ERR_STATE, "amplitude model has no MC normalisation sample (goo_model_set_norm)");
+    if (d.mc->n < 1) return set_error(GOO_ERR_ARG, "the MC normalisation sample is empty");
+    if (end <= begin) {
+      for (int i = 0; i < nout; ++i) out[i] = 0.0;
+      return GOO_OK;
+    }
+    if (!d.ls_mc && cudaMalloc(&d.ls_mc, 64 * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      d.ls_mc = nullptr;
+      return set_error(GOO_ERR_OOM, "floating-lineshape work space");
+    }
+    if (precision == GOO_F32) {
+      GOO_TRY((grad ? launch_ls_pair<float, true>(m, ds, begin, end, theta, out_mode)
+                    : launch_ls_pair<float, false>(m, ds, begin, end, theta, out_mode)));
+    } else {
+      GOO_TRY((grad ? launch_ls_pair<double, true>(m, ds, begin, end, theta, out_mode)
+                    : launch_ls_pair<double, false>(m, ds, begin, end, theta, out_mode)));
+    }
+  } else {
   GOO_TRY(ensure_gram(m, precision));
   const int pi = precision == GOO_F32 ? 0 : 1;
-  const int nout = (out_mode == 0 ? 2 : 3) + P;
   if (end <= begin) {
     for (int i = 0; i < nout; ++i) out[i] = 0.0;
     return GOO_OK;
@@ -852,6 +1130,7 @@ int dalitz_nll(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, 
   } else {
     GOO_TRY((grad ? launch_coh_sel<double, true>(m, cache, ds, begin, end, theta, out_mode, pi)
                   : launch_coh_sel<double, false>(m, cache, ds, begin, end, theta, out_mode, pi)));
+  }
   }
   double* stage = ctx->scratch.host_pinned + kPinnedResult;
   GOO_CUDA_TRY(cudaMemcpyAsync(stage, ctx->scratch.result, nout * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -934,4 +1213,22 @@ int dalitz_server_info(goo_model* m, const double* theta, AmpModelInfo* info) {
   return GOO_OK;
 }
 
+}  // namespace goo
+
+namespace goo {
+int dalitz_set_lineshapes(goo_model* m, int mode) {
+  if (mode != GOO_LINESHAPE_CACHED && mode != GOO_LINESHAPE_FLOATING)
+    return set_error(GOO_ERR_ARG, "goo_model_set_lineshapes: mode %d", mode);
+  m->dalitz->floating = mode == GOO_LINESHAPE_FLOATING;
+  return GOO_OK;
+}
+
+bool dalitz_lineshape_param(const goo_model* m, int p) {
+  const DalitzModel& d = *m->dalitz;
+  for (int k = 0; k < d.nbw; ++k)
+    if (d.par_m0[k] == p || d.par_w[k] == p) return true;
+  return false;
+}
+
+bool dalitz_floating(const goo_model* m) { return m->dalitz->floating; }
 }  // namespace goo

@@ -265,4 +265,66 @@ __global__ void __launch_bounds__(kBlock, 2) gram_kernel(const void* cache_v, in
   if (threadIdx.x == 0) *counters = 0u;
 }
 
+// The same amplitude with the parts of its denominator D = (m0^2 - s) - i m0 Gamma(s):
+// dr = m0^2 - s, di = m0 Gamma(s), inv = 1 / |D|^2, so that 1 / D = (dr + i di) inv.  The
+// floating-lineshape kernels form d log A / d m0 and d log A / d Gamma0 from them.
+template <typename T>
+__device__ __forceinline__ void bw_amp_parts(const BwConstT<T>& b, T s12, T s13, T s23, T& re, T& im, T& dr,
+                                             T& di, T& inv) {
+  const int L = b.spin;
+  T s, sac, sbc;
+  if (b.pair == 0) {
+    s = s12;
+    sac = s13;
+    sbc = s23;
+  } else if (b.pair == 1) {
+    s = s13;
+    sac = s12;
+    sbc = s23;
+  } else {
+    s = s23;
+    sac = s12;
+    sbc = s13;
+  }
+  const T lam1 = (s - T(b.thrP)) * (s - T(b.thrM));
+  T q2 = lam1 / (T(4) * s);
+  q2 = q2 > T(0) ? q2 : T(0);
+  const T z = T(b.r2) * q2;
+  const T t = q2 * T(b.inv_q0sq);
+  const T st = sqrt(t);
+  T ratio2, pw;
+  if (L == 0) {
+    ratio2 = T(1);
+    pw = st;
+  } else if (L == 1) {
+    ratio2 = T(b.Fz0) / (T(1) + z);
+    pw = t * st;
+  } else {
+    ratio2 = T(b.Fz0) / (T(9) + T(3) * z + z * z);
+    pw = t * t * st;
+  }
+  const T rs = T(1) / sqrt(s);
+  di = T(b.m0w) * pw * T(b.m0) * rs * ratio2;
+  dr = T(b.m0sq) - s;
+  inv = T(1) / (dr * dr + di * di);
+  const T lam2 = (s - T(b.pthrP)) * (s - T(b.pthrM));
+  T zp = T(b.rp2) * lam2 * T(b.inv4M2);
+  zp = zp > T(0) ? zp : T(0);
+  T parent, spinf;
+  if (L == 0) {
+    parent = T(1);
+    spinf = T(1);
+  } else if (L == 1) {
+    parent = T(1) / sqrt(T(1) + zp);
+    spinf = sac - sbc - T(b.zconst) / s;
+  } else {
+    parent = T(3) / sqrt(T(9) + T(3) * zp + zp * zp);
+    const T z1 = sac - sbc - T(b.zconst) / s;
+    spinf = z1 * z1 - lam1 * lam2 / (T(3) * s * s);
+  }
+  const T scale = sqrt(ratio2) * parent * spinf * inv;
+  re = dr * scale;
+  im = di * scale;
+}
+
 }  // namespace goo

@@ -174,6 +174,11 @@ extern "C" int goo_fit(goo_model* model, const goo_dataset* ds, double* theta, c
   for (int p = 0; p < obj.P; ++p)
     if (free_mask[p]) {
       if (!(scale[p] > 0)) return set_error(GOO_ERR_ARG, "goo_fit: parameter %d is free but its scale is %g", p, scale[p]);
+      // the cached lineshape path returns no gradient for masses and widths
+      if (model->kind == 1 && opt.gradient == GOO_GRAD_ADJOINT && dalitz_lineshape_param(model, p) &&
+          !dalitz_floating(model))
+        return set_error(GOO_ERR_STATE, "goo_fit: parameter %d is a resonance mass or width; free lineshape parameters "
+                                        "need goo_model_set_lineshapes(model, GOO_LINESHAPE_FLOATING)", p);
       obj.free_idx.push_back(p);
     }
   const int n = (int)obj.free_idx.size();

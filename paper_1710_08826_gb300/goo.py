@@ -16,6 +16,7 @@ _LIB_PATH = os.path.join(_PKG, "libgoo.so")
 GOO_OK, GOO_ERR_ARG, GOO_ERR_RANGE, GOO_ERR_CUDA, GOO_ERR_OOM = 0, -1, -2, -3, -4
 GOO_ERR_NONPOSITIVE_PDF, GOO_ERR_TIMEOUT, GOO_ERR_STATE, GOO_ERR_UNSUPPORTED = -5, -6, -7, -8
 GOO_F64, GOO_F32 = 0, 1
+GOO_LINESHAPE_CACHED, GOO_LINESHAPE_FLOATING = 0, 1
 GOO_COPY, GOO_BORROW_DEVICE = 0, 1
 OP = dict(gauss=1, expo=2, poly2=3, argus=4, prod=10, add=11, bw=20, nr=21, coherent=22, td4=23, amp4=24)
 ANG = dict(SS=0, VS0=1, SV0=2, VV0=3, VVpar=4, VVperp=5, TS0=6, TV0=7)
@@ -123,6 +124,7 @@ def _load():
         "goo_amplitude_cache": (ctypes.c_int, [vp, vp, dp, ctypes.c_int, ctypes.POINTER(vp),
                                                ctypes.POINTER(ctypes.c_int)]),
         "goo_faddeeva": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]),
+        "goo_model_set_lineshapes": (ctypes.c_int, [vp, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -451,6 +453,13 @@ class Model:
                            ctypes.byref(res)))
         info = {k: getattr(res, k) for k, _ in GooFitResult._fields_}
         return th.copy(), err, info
+
+    def set_lineshapes(self, mode):
+        """'cached' (default: masses and widths are constants of the amplitude cache, their
+        gradient entries are 0) or 'floating' (amplitudes and their lineshape derivatives
+        evaluated per event and per MC point on every call; full gradient)."""
+        code = {"cached": GOO_LINESHAPE_CACHED, "floating": GOO_LINESHAPE_FLOATING}[mode]
+        _check(lib.goo_model_set_lineshapes(self.handle, code))
 
     def gram(self, theta, precision="f64"):
         """MC Gram matrix G_kl (complex K x K, resonances in tree order then the NR amplitude)."""

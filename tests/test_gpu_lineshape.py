@@ -1,0 +1,194 @@
+"""GPU parity of the three-body model with floating lineshapes (resonance masses and widths
+free): NLL and the full gradient against the oracle, agreement with the cached path, shards,
+a fit with a free mass and width, and the full-size configuration."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import dalitz as od
+from oracle import fit as ofit
+
+pytestmark = pytest.mark.gpu
+
+KIN = dict(synth.DALITZ_MASSES)
+TOL_NLL = {"f64": 1e-9, "f32": 1e-6}
+TOL_GRAD = {"f64": 1e-6, "f32": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def goo():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1710_08826_gb300 import goo as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def ctx(goo):
+    return goo.Context(0)
+
+
+def _cands(n, seed):
+    return synth.dalitz_candidates(n, seed, KIN["M"], KIN["m1"], KIN["m2"], KIN["m3"])
+
+
+@pytest.fixture(scope="module")
+def sample():
+    spec = synth.c3_spec(n_mc=50_000)
+    ref = od.DalitzModel(spec)
+    theta = np.array(synth.param_values(spec))
+    fmax = 1.2 * od.max_intensity_scan(ref, theta, n=300)
+
+    def dens(cols):
+        with torch.no_grad():
+            th = torch.as_tensor(theta, dtype=torch.float64)
+            return ref.intensity(ref.amplitude_matrix(cols, th), th).numpy()
+    data, worst = synth.accept_reject(lambda k, s: _cands(k, s), dens, fmax, 20_000, 81, chunk=200_000)
+    assert worst < 1.0
+    return spec, ref, theta, data, _cands(50_000, 1710013)
+
+
+def _prep(spec, data, mc, precision):
+    if precision == "f32":
+        return synth.round_to_f32(data, spec), synth.round_to_f32(mc, spec)
+    return data, mc
+
+
+def _upload(goo, ctx, spec, data, mc, mode="floating"):
+    ds = goo.Dataset.from_spec(ctx, spec, data)
+    mcds = goo.Dataset.from_spec(ctx, spec, mc)
+    model = goo.Model(ctx, spec, mc=mcds)
+    model.set_lineshapes(mode)
+    return ds, mcds, model
+
+
+def _lineshape_mask(spec):
+    return np.array([n.startswith(("m0_", "w_")) for n in synth.param_names(spec)])
+
+
+def _shifted(spec, theta):
+    # masses and widths moved by a few widths' fractions, coefficients by 5 %
+    names = synth.param_names(spec)
+    th = theta.copy()
+    for i, n in enumerate(names):
+        if n.startswith("m0_"):
+            th[i] += 0.004
+        elif n.startswith("w_"):
+            th[i] *= 1.08
+        elif n.startswith(("re_", "im_")) and not n.endswith("NR"):
+            th[i] *= 1.05
+    return th
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("where", ["truth", "shifted"])
+def test_floating_nll_and_full_gradient_match_oracle(goo, ctx, sample, precision, where):
+    spec, ref, theta, data, mc = sample
+    th = theta if where == "truth" else _shifted(spec, theta)
+    d, c = _prep(spec, data, mc, precision)
+    ds, mcds, model = _upload(goo, ctx, spec, d, c)
+    nll, g = model.nll_grad(ds, th, precision)
+    rnll, rg = ref.nll_grad(d, c, th)
+    assert abs(nll - rnll) <= TOL_NLL[precision] * abs(rnll), (nll, rnll)
+    ls = _lineshape_mask(spec)
+    assert np.all(rg[ls] != 0)
+    scale = np.max(np.abs(rg))
+    assert np.max(np.abs(g - rg)) <= TOL_GRAD[precision] * scale, (g - rg) / scale
+    assert model.nll(ds, th, precision) == pytest.approx(nll, rel=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_floating_agrees_with_cached_path(goo, ctx, sample, precision):
+    spec, ref, theta, data, mc = sample
+    th = _shifted(spec, theta)
+    d, c = _prep(spec, data, mc, precision)
+    ds, mcds, model = _upload(goo, ctx, spec, d, c, mode="cached")
+    n_c, g_c = model.nll_grad(ds, th, precision)
+    model.set_lineshapes("floating")
+    n_f, g_f = model.nll_grad(ds, th, precision)
+    assert abs(n_f - n_c) <= (1e-12 if precision == "f64" else 1e-6) * abs(n_c)
+    ls = _lineshape_mask(spec)
+    assert np.all(g_c[ls] == 0) and np.all(g_f[ls] != 0)
+    scale = np.max(np.abs(g_c[~ls]))
+    assert np.max(np.abs(g_f[~ls] - g_c[~ls])) <= (1e-9 if precision == "f64" else 1e-4) * scale
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_floating_shards_combine(goo, ctx, sample, precision):
+    spec, ref, theta, data, mc = sample
+    d, c = _prep(spec, data, mc, precision)
+    ds, mcds, model = _upload(goo, ctx, spec, d, c)
+    th = _shifted(spec, theta)
+    full, g = model.nll_grad(ds, th, precision)
+    edges = [0, 1, 4_097, 12_345, 20_000]
+    parts = [model.nll_partial(ds, a, b, th, precision) for a, b in zip(edges[:-1], edges[1:])]
+    tot = goo.combine_partials(parts, model.n_params)
+    assert tot[2] == 20_000
+    assert abs(tot[0] + tot[1] - full) <= (1e-12 if precision == "f64" else 1e-9) * abs(full)
+    np.testing.assert_allclose(tot[3:], g, rtol=1e-9 if precision == "f64" else 1e-5,
+                               atol=1e-9 * np.abs(g).max())
+    empty = goo.Dataset.from_spec(ctx, spec, {"s12": np.zeros(0), "s13": np.zeros(0)})
+    assert model.nll(empty, th, precision) == 0.0
+
+
+def test_fit_with_free_mass_and_width(goo, ctx, sample):
+    # the K*(892) in (12): mass and width free with the coefficients; the GPU fit (FP32
+    # evaluation, adjoint gradient) against the oracle's FP64 fit of the same events
+    spec, ref, theta, data, mc = sample
+    names = synth.param_names(spec)
+    free = np.array([not p[2] for p in spec["params"]])
+    for n in ("m0_Kst892_12", "w_Kst892_12"):
+        free[names.index(n)] = True
+    steps = np.array([p[3] if p[3] > 0 else 1e-3 for p in spec["params"]])
+    start = theta.copy()
+    start[names.index("m0_Kst892_12")] += 0.002
+    start[names.index("w_Kst892_12")] *= 1.05
+    d, c = _prep(spec, data, mc, "f32")
+    ds, mcds, model = _upload(goo, ctx, spec, d, c, mode="cached")
+    with pytest.raises(goo.GooError):
+        model.fit(ds, start, free, steps, precision="f32", gradient="adjoint")
+    model.set_lineshapes("floating")
+    th_gpu, err_gpu, info = model.fit(ds, start, free, steps, precision="f32", gradient="adjoint")
+    th_ref, err_ref, _, redm = ofit.fit(lambda t: ref.nll_grad(d, c, t), start, free, steps)
+    assert redm < 1e-6
+    idx = np.flatnonzero(free)
+    pulls = np.abs(th_gpu[idx] - th_ref[idx]) / err_ref[idx]
+    assert np.max(pulls) < 0.01, pulls
+    np.testing.assert_allclose(err_gpu[idx], err_ref[idx], rtol=0.03)
+
+
+def _oracle_nll_grad_chunked(ref, data, mc, theta, chunk=500_000):
+    """-sum log |S|^2 + n log N and its gradient, the event sum taken in chunks (memory)."""
+    th = torch.tensor([float(t) for t in theta], dtype=torch.float64, requires_grad=True)
+    n = len(data["s12"])
+    total, grad = 0.0, np.zeros(len(theta))
+    for a in range(0, n, chunk):
+        cols = {k: v[a:a + chunk] for k, v in data.items()}
+        part = -torch.log(ref.intensity(ref.amplitude_matrix(cols, th), th)).sum()
+        (g,) = torch.autograd.grad(part, th)
+        total += float(part.detach())
+        grad += g.numpy()
+    lognorm = n * torch.log(ref.intensity(ref.amplitude_matrix(mc, th), th).mean())
+    (g,) = torch.autograd.grad(lognorm, th)
+    return total + float(lognorm.detach()), grad + g.numpy()
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_floating_full_size(goo, ctx, precision):
+    # 5M events and 1M MC points, the sizes of the three-body workload, at shifted lineshapes
+    spec = synth.c3_spec()
+    data = _cands(5_000_000, 1710003)
+    mc = _cands(1_000_000, 1710013)
+    theta = _shifted(spec, np.array(synth.param_values(spec)))
+    d, c = _prep(spec, data, mc, precision)
+    ds, mcds, model = _upload(goo, ctx, spec, d, c)
+    nll, g = model.nll_grad(ds, theta, precision)
+    ref = od.DalitzModel(spec)
+    rnll, rg = _oracle_nll_grad_chunked(ref, d, c, theta)
+    assert abs(nll - rnll) <= TOL_NLL[precision] * abs(rnll), (nll, rnll)
+    scale = np.max(np.abs(rg))
+    # FP32: every event's derivative carries a few 1e-7 relative error, and 5M of them
+    # cancel to a gradient far below their summed magnitude
+    tol = 1e-6 if precision == "f64" else 2e-3
+    assert np.max(np.abs(g - rg)) <= tol * scale, (g - rg) / scale

@@ -177,3 +177,22 @@ def test_gram_quadratic_form_equals_mc_mean():
     mean = float(m.intensity(m.amplitude_matrix(mc, th), th).mean())
     assert quad_form == pytest.approx(mean, rel=1e-12)
     assert torch.allclose(G, G.conj().T, rtol=0, atol=1e-14)
+
+
+def test_lineshape_gradient_by_finite_differences():
+    # d NLL / d m0 and d NLL / d Gamma0 of every resonance: the oracle's autograd gradient
+    # against fourth-order central differences of its NLL (the masses and widths enter
+    # through q0, the barrier ratio, the running width and the pole)
+    spec, m, mc, data = _small_c3()
+    th = np.array(synth.param_values(spec))
+    names = synth.param_names(spec)
+    _, g = m.nll_grad(data, mc, th)
+    f = lambda t: m.nll(data, mc, t)
+    for i, n in enumerate(names):
+        if not n.startswith(("m0_", "w_")):
+            continue
+        h = 1e-5 * th[i]
+        e = np.zeros_like(th)
+        e[i] = h
+        fd = (8 * (f(th + e) - f(th - e)) - (f(th + 2 * e) - f(th - 2 * e))) / (12 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(abs(g[i]), 1.0), (n, fd, g[i])
