@@ -35,6 +35,10 @@ BYTES_PER_EVENT_F64 = 24
 _SOP_SRC = ['paper_1710_08826_gb300/csrc/tree.cu', 'paper_1710_08826_gb300/csrc/common.cuh', 'paper_1710_08826_gb300/csrc/model.cuh']
 _COH_SRC = ['paper_1710_08826_gb300/csrc/dalitz.cu', 'paper_1710_08826_gb300/csrc/dalitz.cuh', 'paper_1710_08826_gb300/csrc/common.cuh', 'paper_1710_08826_gb300/csrc/model.cuh']
 _TD4_SRC = ['paper_1710_08826_gb300/csrc/td4.cu', 'paper_1710_08826_gb300/csrc/dalitz.cuh', 'paper_1710_08826_gb300/csrc/common.cuh', 'paper_1710_08826_gb300/csrc/model.cuh']
+# warp-instruction issue peak of a GB300: 152 SMs x 4 schedulers x 2.07 GHz (one warp
+# instruction per scheduler per cycle)
+ISSUE_PEAK = 152 * 4 * 2.07e9
+
 NCU_RECORDS = {
     "sop_nll_grad_f32": {"bytes": 125_785_088, "events": 10_000_000, "sources": _SOP_SRC,
                          "sha256": "8dfab8aa796eadf45ce7f39879b46dadeeae283b22c1ba4f7854ef93258809d2",
@@ -74,6 +78,9 @@ def ncu_record(kernel, n_events):
     out = {"traffic": rec["bytes"] * n_events / rec["events"], "profile": rec["profile"]}
     if "fp64_pipe" in rec:
         out["fp64_pipe_active"] = rec["fp64_pipe"]
+    if "warp_inst" in rec:
+        out["warp_inst"] = rec["warp_inst"] * n_events / rec["events"]
+        out["issue_active"] = rec["issue_active"]
     return out
 
 
@@ -96,7 +103,7 @@ def parse():
     ap.add_argument("--toys", type=int, default=4096)
     ap.add_argument("--rate", type=float, default=1000.0, help="Poisson arrival rate of the second serving run")
     ap.add_argument("--profile", action="store_true", help="short fixed launch sequence for ncu captures")
-    ap.add_argument("--profile-workload", default="c2", choices=["c2", "c3", "c4", "c5"])
+    ap.add_argument("--profile-workload", default="c2", choices=["c2", "c3", "c3f", "c4", "c5"])
     return ap.parse_args()
 
 
@@ -461,6 +468,55 @@ def c3_measure(goo, ctx, stream, steps, n_events=5_000_000, n_mc=1_000_000):
             "bound": "hbm" if grad else "fp64", "ncu": ncu_record(name, n_events),
             "what": ("goo_nll_grad, FP32 amplitude cache (64 B/event), adjoint gradient" if grad
                      else "goo_nll, FP64 amplitude cache (128 B/event)")}
+    out["floating_lineshapes"] = c3_floating_measure(goo, ctx, stream, model, ds, theta, flush, steps, n_events, n_mc)
+    return out
+
+
+def c3_floating_measure(goo, ctx, stream, model, ds, theta, flush, steps, n_events, n_mc):
+    """The same events with the resonance masses and widths free: every evaluation runs an MC
+    pass and an event pass that evaluate all amplitudes and their lineshape derivatives."""
+    import numpy as np
+    import torch
+
+    model.set_lineshapes("floating")
+    out = {"workload": f"c3_dalitz floating lineshapes: {n_events:,} events + {n_mc:,} MC points per evaluation, "
+                       "8 resonances recomputed with d/dm0 and d/dGamma0, 32 parameters (16 coefficients, "
+                       "8 masses, 8 widths)"}
+    for prec, grad, k in (("f32", True, steps), ("f64", False, max(3, steps // 5))):
+        for _ in range(3):
+            model.nll_grad(ds, theta, prec) if grad else model.nll(ds, theta, prec)
+        torch.cuda.synchronize()
+        ctx.kernel_times(reset=True)
+        ctx.timing(True)
+        ms = 0.0
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            model.nll_grad(ds, theta, prec) if grad else model.nll(ds, theta, prec)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        ctx.timing(False)
+        kt = ctx.kernel_times(reset=True)
+        kernels = {name: kms / cnt for name, (cnt, kms) in kt.items()}
+        name = max(kernels, key=kernels.get)
+        rec = ncu_record(name, n_events)
+        entry = {"evals_per_s": k / (ms * 1e-3), "events_per_s": n_events * k / (ms * 1e-3), "ms_per_eval": ms / k,
+                 "kernels_ms": kernels, "kernel": name, "bound": "alu (FP32 issue)" if grad else "fp64",
+                 "ncu": rec,
+                 "what": ("goo_nll_grad, FP32 amplitudes and lineshape derivatives per event and MC point, "
+                          "adjoint gradient over all 32 parameters" if grad
+                          else "goo_nll, FP64 amplitudes per event and MC point")}
+        if rec and rec.get("warp_inst") and grad:
+            # issue roofline: warp instructions per launch / duration / (SMs x 4 schedulers x clock)
+            entry["issue_frac"] = rec["warp_inst"] / (kernels[name] * 1e-3) / ISSUE_PEAK
+        out["f32_grad" if grad else "f64_plain"] = entry
+    n32, g32 = model.nll_grad(ds, theta, "f32")
+    n64 = model.nll(ds, theta, "f64")
+    out["parity_this_run"] = {"nll_f32": n32, "nll_f64": n64, "rel": abs(n32 - n64) / abs(n64)}
+    model.set_lineshapes("cached")
     return out
 
 
@@ -624,6 +680,8 @@ def run_profile(args):
     c2: [grid, event] x 4 FP32+grad evaluations, then one FP64 evaluation (10M events).
     c3: amplitude caches and Gram (first call), then 4 FP32+grad and 1 FP64 coherent
         evaluations on 5M events generated on the device.
+    c3f: the same events with floating lineshapes: 4 FP32+grad evaluations (an MC pass and an
+        event pass each), then 1 FP64 evaluation.
     c4: amplitude caches and Gram (first call), then 4 FP32+grad and 1 FP64 time-dependent
         four-body evaluations on 2M events.
     c5: a served study of 64 toys (generation passes, then rounds of batched evaluation and
@@ -661,9 +719,11 @@ def run_profile(args):
         mcds = goo.Dataset.from_spec(ctx, spec, mc)
         model = goo.Model(ctx, spec, mc=mcds)
         theta = np.array(synth.param_values(spec))
-        if w == "c3":
+        if w in ("c3", "c3f"):
             a, b = goo.toy_generate(model, theta, None, 1710003, 5_000_000)
             ds = goo.Dataset.from_spec(ctx, spec, {"s12": a.astype(np.float64), "s13": b.astype(np.float64)})
+            if w == "c3f":
+                model.set_lineshapes("floating")
             out = [model.nll_grad(ds, theta, "f32")[0] for _ in range(4)]
             out.append(model.nll(ds, theta, "f64"))
         else:

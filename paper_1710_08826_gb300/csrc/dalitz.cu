@@ -506,8 +506,18 @@ struct LsLanes {
   static constexpr int NS = GRAD ? 1 + 2 * (KB + 1) + 2 * KB : 1;
 };
 
+// Dynamic shared memory of a floating-lineshape block: per thread, the five parts (re, im,
+// dr, di, inv) of each resonance's amplitude and the NS - 1 gradient lanes, as columns of
+// kBlock values (thread t at offset t: conflict-free), with the gradient only.
+template <typename T, int KB, bool GRAD>
+constexpr size_t ls_smem() {
+  return GRAD ? (size_t)(5 * KB + LsLanes<KB, GRAD>::NS - 1) * kBlock * sizeof(T) : 0;
+}
+
+// The resonances are visited in a run-time loop (not unrolled) whose state lives in those
+// shared-memory columns, so that the kernel needs few registers.
 template <typename T, int KB, bool GRAD, bool MC>
-__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(kBlock)
     coh_ls_kernel(const __grid_constant__ CohArgs<T> a, const __grid_constant__ LsConst<T> c,
                   const DalitzDev* __restrict__ ddp, const T* __restrict__ c12, const T* __restrict__ c13,
                   int64_t begin, int64_t end, const double* __restrict__ mc_sums, double n_mc, float2* partials,
@@ -518,36 +528,39 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1)
   __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
   __shared__ unsigned s_bad[kBlock / 32];
   __shared__ double s_out[NS];
-  for (int i = threadIdx.x; i < (int)(sizeof(DalitzDev) / 4); i += blockDim.x) ((int*)&s_dd)[i] = ((const int*)ddp)[i];
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  T* s_a = reinterpret_cast<T*>(s_dyn);  // [5][KB][kBlock]
+  T* s_l = s_a + 5 * KB * kBlock;        // [NS - 1][kBlock]
+  const int t = threadIdx.x;
+  for (int i = t; i < (int)(sizeof(DalitzDev) / 4); i += blockDim.x) ((int*)&s_dd)[i] = ((const int*)ddp)[i];
+  if constexpr (GRAD)
+    for (int j = 0; j < NS - 1; ++j) s_l[j * kBlock + t] = T(0);
   __syncthreads();
   const int nbw = s_dd.nbw;
+  const T cnr = c.cr[KB], cni = c.ci[KB];
   Kahan lf32;
   double lf64 = 0.0;
-  T gre[KA], gim[KA], gm[KB], gg[KB];
-#pragma unroll
-  for (int k = 0; k < KA; ++k) gre[k] = gim[k] = T(0);
-#pragma unroll
-  for (int k = 0; k < KB; ++k) gm[k] = gg[k] = T(0);
   unsigned bad = 0;
-  for (int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + t; i < end; i += (int64_t)gridDim.x * blockDim.x) {
     const T x12 = c12[i], x13 = c13[i];
     T x23;
     if constexpr (sizeof(T) == 4) x23 = (float)(s_dd.sumsq - (double)x12 - (double)x13);
     else x23 = s_dd.sumsq - x12 - x13;
-    T ar[KA], ai[KA], dr[KB], di[KB], iv[KB];
-#pragma unroll
-    for (int k = 0; k < KB; ++k) {
-      ar[k] = ai[k] = dr[k] = di[k] = iv[k] = T(0);
-      if (k < nbw) bw_amp_parts<T>(bw_of<T>(s_dd, k), x12, x13, x23, ar[k], ai[k], dr[k], di[k], iv[k]);
-    }
-    ar[KB] = T(1);
-    ai[KB] = T(0);
-    T sr = T(0), si = T(0);
-#pragma unroll
-    for (int k = 0; k < KA; ++k) {
-      sr += c.cr[k] * ar[k] - c.ci[k] * ai[k];
-      si += c.cr[k] * ai[k] + c.ci[k] * ar[k];
+    T sr = cnr, si = cni;  // the non-resonant amplitude is 1
+#pragma unroll 1
+    for (int k = 0; k < nbw; ++k) {
+      T ar, ai, dr, di, iv;
+      bw_amp_parts<T>(bw_of<T>(s_dd, k), x12, x13, x23, ar, ai, dr, di, iv);
+      sr += c.cr[k] * ar - c.ci[k] * ai;
+      si += c.cr[k] * ai + c.ci[k] * ar;
+      if constexpr (GRAD) {
+        T* col = s_a + k * kBlock + t;
+        col[0] = ar;
+        col[KB * kBlock] = ai;
+        col[2 * KB * kBlock] = dr;
+        col[3 * KB * kBlock] = di;
+        col[4 * KB * kBlock] = iv;
+      }
     }
     const T s2 = sr * sr + si * si;
     if (!MC && !(s2 > T(0))) {
@@ -559,20 +572,24 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1)
     if constexpr (GRAD) {
       const T w = MC ? T(1) : T(1) / s2;
       const T tr = sr * w, ti = -si * w;  // conj(S) w
-#pragma unroll
-      for (int k = 0; k < KA; ++k) {
-        const T ur = ar[k] * tr - ai[k] * ti, ui = ar[k] * ti + ai[k] * tr;  // A_k conj(S) w
-        gre[k] += ur;
-        gim[k] += ui;
-        if (k < KB) {
-          const T vr = c.cr[k] * ur - c.ci[k] * ui, vi = c.cr[k] * ui + c.ci[k] * ur;  // c_k A_k conj(S) w
-          const T e2 = di[k] * iv[k];
-          const T lmr = c.rho[k] - (c.two_m0[k] * dr[k] + c.kappa[k] * di[k] * di[k]) * iv[k];
-          const T lmi = -(c.two_m0[k] - c.kappa[k] * dr[k]) * e2;
-          const T lgr = -di[k] * e2 * c.inv_g0[k], lgi = dr[k] * e2 * c.inv_g0[k];
-          gm[k] += vr * lmr - vi * lmi;
-          gg[k] += vr * lgr - vi * lgi;
-        }
+      s_l[(2 * KB) * kBlock + t] += tr;   // the non-resonant slot: A = 1
+      s_l[(2 * KB + 1) * kBlock + t] += ti;
+#pragma unroll 1
+      for (int k = 0; k < nbw; ++k) {
+        const T* col = s_a + k * kBlock + t;
+        const T ar = col[0], ai = col[KB * kBlock], dr = col[2 * KB * kBlock], di = col[3 * KB * kBlock],
+                iv = col[4 * KB * kBlock];
+        const T ur = ar * tr - ai * ti, ui = ar * ti + ai * tr;                      // A_k conj(S) w
+        const T vr = c.cr[k] * ur - c.ci[k] * ui, vi = c.cr[k] * ui + c.ci[k] * ur;  // c_k A_k conj(S) w
+        const T e2 = di * iv;
+        const T lmr = c.rho[k] - (c.two_m0[k] * dr + c.kappa[k] * di * di) * iv;
+        const T lmi = -(c.two_m0[k] - c.kappa[k] * dr) * e2;
+        const T lgr = -di * e2 * c.inv_g0[k], lgi = dr * e2 * c.inv_g0[k];
+        T* lane = s_l + 2 * k * kBlock + t;
+        lane[0] += ur;
+        lane[kBlock] += ui;
+        lane[2 * KA * kBlock] += vr * lmr - vi * lmi;
+        lane[(2 * KA + 1) * kBlock] += vr * lgr - vi * lgi;
       }
     }
   }
@@ -580,14 +597,9 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1)
   v[0] = (sizeof(T) == 4) ? lf32.value() : dd_from_double(lf64);
   if constexpr (GRAD) {
 #pragma unroll
-    for (int k = 0; k < KA; ++k) {
-      v[1 + 2 * k] = (sizeof(T) == 4) ? ddf{(float)gre[k], 0.f} : dd_from_double((double)gre[k]);
-      v[2 + 2 * k] = (sizeof(T) == 4) ? ddf{(float)gim[k], 0.f} : dd_from_double((double)gim[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < KB; ++k) {
-      v[1 + 2 * KA + 2 * k] = (sizeof(T) == 4) ? ddf{(float)gm[k], 0.f} : dd_from_double((double)gm[k]);
-      v[2 + 2 * KA + 2 * k] = (sizeof(T) == 4) ? ddf{(float)gg[k], 0.f} : dd_from_double((double)gg[k]);
+    for (int j = 0; j < NS - 1; ++j) {
+      const T x = s_l[j * kBlock + t];
+      v[1 + j] = (sizeof(T) == 4) ? ddf{(float)x, 0.f} : dd_from_double((double)x);
     }
   }
   for (int m = 16; m > 0; m >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, m);
@@ -925,10 +937,14 @@ static int launch_ls(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t
                      double* out, int out_mode) {
   DalitzModel& d = *m->dalitz;
   goo_ctx* ctx = m->ctx;
+  constexpr size_t smem = ls_smem<T, KB, GRAD>();
   static int occ[2] = {0, 0};
   int& o = occ[MC ? 1 : 0];
   if (o == 0) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, coh_ls_kernel<T, KB, GRAD, MC>, kBlock, 0) != cudaSuccess ||
+    if (smem > 48 * 1024)
+      GOO_CUDA_TRY(cudaFuncSetAttribute(coh_ls_kernel<T, KB, GRAD, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, coh_ls_kernel<T, KB, GRAD, MC>, kBlock, smem) != cudaSuccess ||
         o < 1) {
       cudaGetLastError();
       o = 1;
@@ -951,7 +967,7 @@ static int launch_ls(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t
     LaunchScope ls(ctx, MC ? (sizeof(T) == 4 ? "coh_ls_mc_f32" : "coh_ls_mc_f64")
                            : (sizeof(T) == 4 ? (GRAD ? "coh_ls_grad_f32" : "coh_ls_f32")
                                              : (GRAD ? "coh_ls_grad_f64" : "coh_ls_f64")));
-    coh_ls_kernel<T, KB, GRAD, MC><<<nb, kBlock, 0, ctx->stream>>>(
+    coh_ls_kernel<T, KB, GRAD, MC><<<nb, kBlock, smem, ctx->stream>>>(
         a, c, d.dev, c12, c13, begin, end, d.ls_mc, (double)(d.mc ? d.mc->n : 0), ctx->scratch.partials,
         ctx->scratch.counters, out, out_mode);
   }
