@@ -40,23 +40,27 @@ _TD4_SRC = ['paper_1710_08826_gb300/csrc/td4.cu', 'paper_1710_08826_gb300/csrc/d
 ISSUE_PEAK = 152 * 4 * 2.07e9
 
 NCU_RECORDS = {
-    "sop_nll_grad_f32": {"bytes": 125_785_088, "events": 10_000_000, "sources": _SOP_SRC,
-                         "sha256": "8dfab8aa796eadf45ce7f39879b46dadeeae283b22c1ba4f7854ef93258809d2",
+    "sop_nll_grad_f32": {"bytes": 125_935_360, "events": 10_000_000, "sources": _SOP_SRC,
+                         "sha256": "903706de40bde32cb76d7456474a8c09d23988d39e4de0caad990ffbe819fea2",
                          "profile": "profiles/sop_event2_kernel_f32_c2_10M.md"},
-    "sop_nll_f64": {"bytes": 243_802_880, "events": 10_000_000, "fp64_pipe": 0.8631, "sources": _SOP_SRC,
-                    "sha256": "8dfab8aa796eadf45ce7f39879b46dadeeae283b22c1ba4f7854ef93258809d2",
+    "sop_nll_f64": {"bytes": 243_334_400, "events": 10_000_000, "fp64_pipe": 0.8631, "sources": _SOP_SRC,
+                    "sha256": "903706de40bde32cb76d7456474a8c09d23988d39e4de0caad990ffbe819fea2",
                     "profile": "profiles/sop_event_kernel_f64_c2_10M.md"},
-    "coh_nll_grad_f32": {"bytes": 323_185_664, "events": 5_000_000, "sources": _COH_SRC,
-                         "sha256": "b457246f0a0eadb7f6bcc854a759157881ccae15d5e3f7e00a959af08c1545f9",
+    "coh_nll_grad_f32": {"bytes": 323_768_832, "events": 5_000_000, "sources": _COH_SRC,
+                         "sha256": "4fdd73a53f82ab80d472525c791363ef014ad99c4e86ef7718bc5d08feae1355",
                          "profile": "profiles/coh_nll_staged_kernel_f32_c3_5M.md"},
-    "coh_nll_f64": {"bytes": 643_364_352, "events": 5_000_000, "fp64_pipe": 0.8701, "sources": _COH_SRC,
-                    "sha256": "b457246f0a0eadb7f6bcc854a759157881ccae15d5e3f7e00a959af08c1545f9",
+    "coh_nll_f64": {"bytes": 643_385_600, "events": 5_000_000, "fp64_pipe": 0.8702, "sources": _COH_SRC,
+                    "sha256": "4fdd73a53f82ab80d472525c791363ef014ad99c4e86ef7718bc5d08feae1355",
                     "profile": "profiles/coh_nll_kernel_f64_c3_5M.md"},
-    "td4_nll_grad_f32": {"bytes": 171_191_040, "events": 2_000_000, "sources": _TD4_SRC,
-                         "sha256": "05ea2816e0b9096d1d47ffdabfd7ebb23dd40e6824a0b70795c464f6c12edd8f",
+    "coh_ls_grad_f32": {"bytes": 40_093_952, "events": 5_000_000, "warp_inst": 308_097_098, "issue_active": 0.6431,
+                        "sources": _COH_SRC,
+                        "sha256": "4fdd73a53f82ab80d472525c791363ef014ad99c4e86ef7718bc5d08feae1355",
+                        "profile": "profiles/coh_ls_kernel_f32_c3_floating_5M.md"},
+    "td4_nll_grad_f32": {"bytes": 171_436_544, "events": 2_000_000, "sources": _TD4_SRC,
+                         "sha256": "131f99b2bb238619f17851b0d69b70314103761055bee7685c518161fd1923bb",
                          "profile": "profiles/td4_nll_f32_kernel_c4_2M.md"},
-    "td4_nll_f64": {"bytes": 339_361_536, "events": 2_000_000, "fp64_pipe": 0.8663, "sources": _TD4_SRC,
-                    "sha256": "05ea2816e0b9096d1d47ffdabfd7ebb23dd40e6824a0b70795c464f6c12edd8f",
+    "td4_nll_f64": {"bytes": 339_367_424, "events": 2_000_000, "fp64_pipe": 0.8661, "sources": _TD4_SRC,
+                    "sha256": "131f99b2bb238619f17851b0d69b70314103761055bee7685c518161fd1923bb",
                     "profile": "profiles/td4_nll_f64_kernel_c4_2M.md"},
 }
 
