@@ -19,4 +19,4 @@ factorisation, finite differences, kinematic identities, published RNG
 outputs (numpy's Philox), and recovery of generated parameters within their
 errors on toy fits.
 """
-from . import pdfs, model, dalitz, fit, td4  # noqa: F401
+from . import pdfs, model, dalitz, fit, td4, td3  # noqa: F401

@@ -160,6 +160,59 @@ def c4_spec(n_mc=3_000_000, mc_seed=1710014):
     )
 
 
+# Time-dependent three-body model (D0 -> pi+ pi- pi0-like): particle 1 = pi0, 2 = pi+,
+# 3 = pi- (equal charged-pion masses, so the Dalitz plot is symmetric under s12 <-> s13).
+TD3_MASSES = dict(M=1.865, m1=0.1350, m2=0.1396, m3=0.1396)
+
+# The fifteen Breit--Wigner amplitudes (name, pair, spin, m0, width): rho-like vectors in all
+# three pairs and scalar/tensor states in the charged pair "23", with PDG-like round values.
+TD3_RESONANCES = [
+    ("rho770_p", "12", 1, 0.7753, 0.1491), ("rho770_m", "13", 1, 0.7753, 0.1491),
+    ("rho770_0", "23", 1, 0.7753, 0.1491), ("rho1450_p", "12", 1, 1.465, 0.400),
+    ("rho1450_m", "13", 1, 1.465, 0.400), ("rho1450_0", "23", 1, 1.465, 0.400),
+    ("rho1700_p", "12", 1, 1.720, 0.250), ("rho1700_m", "13", 1, 1.720, 0.250),
+    ("rho1700_0", "23", 1, 1.720, 0.250), ("f0_980", "23", 0, 0.990, 0.070),
+    ("f2_1270", "23", 2, 1.2755, 0.1867), ("f0_1370", "23", 0, 1.350, 0.350),
+    ("f0_1500", "23", 0, 1.505, 0.109), ("f0_500", "23", 0, 0.500, 0.400),
+    ("f0_1710", "23", 0, 1.720, 0.135),
+]
+
+# Coefficient truth values (Re, Im): the rho+(770) is the fixed reference (1, 0); the last
+# entry is the non-resonant amplitude.
+TD3_TRUTH = [
+    (1.0, 0.0), (0.55, 0.45), (0.52, 0.28), (0.35, -0.25), (0.30, 0.35), (0.20, 0.10),
+    (0.25, 0.30), (-0.20, 0.30), (0.15, -0.20), (0.12, 0.05), (0.25, 0.15), (0.20, -0.10),
+    (0.10, 0.08), (0.30, 0.20), (0.06, -0.04), (0.50, 0.20),
+]
+
+
+def td3_spec(n_mc=1_000_000, mc_seed=1710015):
+    """Time-dependent three-body model: 15 BW + NR amplitudes (30 free coefficients, the
+    rho+(770) the reference), x, y, tau, sigma_t; observables s12, s13, t."""
+    kin = dict(TD3_MASSES, r_res=1.5, r_par=5.0)
+    M, m1, m2, m3 = kin["M"], kin["m1"], kin["m2"], kin["m3"]
+    params, amps = [], []
+    for k, ((name, pair, spin, m0, w), (re, im)) in enumerate(zip(TD3_RESONANCES, TD3_TRUTH)):
+        fixed = k == 0
+        params += [(f"m0_{name}", m0, True, 0.0), (f"w_{name}", w, True, 0.0),
+                   (f"re_{name}", re, fixed, 0.0 if fixed else 0.02),
+                   (f"im_{name}", im, fixed, 0.0 if fixed else 0.02)]
+        amps.append(("bw", pair, spin, f"m0_{name}", f"w_{name}", f"re_{name}", f"im_{name}"))
+    re, im = TD3_TRUTH[-1]
+    params += [("re_NR", re, False, 0.02), ("im_NR", im, False, 0.02)]
+    amps.append(("nr", "re_NR", "im_NR"))
+    params += [("x", TD4_TIME["x"], False, 0.002), ("y", TD4_TIME["y"], False, 0.002),
+               ("tau", TD4_TIME["tau"], False, 0.002), ("sigma_t", TD4_TIME["sigma_t"], False, 0.001)]
+    return dict(
+        name="td3_dalitz",
+        observables=[("s12", (m1 + m2) ** 2, (M - m3) ** 2), ("s13", (m1 + m3) ** 2, (M - m2) ** 2),
+                     ("t", -0.5, 10.0)],
+        params=params,
+        pdf=("td3", kin, amps, ("x", "y", "tau", "sigma_t")),
+        norm=("mc", n_mc, mc_seed),
+    )
+
+
 def param_names(spec):
     return [p[0] for p in spec["params"]]
 
