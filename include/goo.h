@@ -84,11 +84,21 @@ enum {
    *   of width sigma_t; normalised over phase space (MC Gram matrix) and all t.          */
   GOO_OP_TD4 = 23,   /* root over GOO_OP_AMP4 children: par[0]=x, par[1]=y, par[2]=tau (ps),
                         par[3]=sigma_t (ps); dval = {M, m1, m2, m3, m4, r (barrier radius)}  */
-  GOO_OP_AMP4 = 24   /* a_k = F(m12; dval[0]=m0, dval[1]=width) F(m34; dval[2]=m0,
+  GOO_OP_AMP4 = 24,  /* a_k = F(m12; dval[0]=m0, dval[1]=width) F(m34; dval[2]=m0,
                         dval[3]=width) W(cos th12, cos th34, phi), F a Breit-Wigner with
                         running width and Blatt-Weisskopf factors of the spins that
                         ival[0] = GOO_ANG_* fixes; par[0]=Re c_k, par[1]=Im c_k (free),
                         dval[4]=Re b_k, dval[5]=Im b_k (fixed)                          */
+  /* Time-dependent three-body amplitude model (paper Sec. 5 and Table 2: a time-dependent
+   * amplitude analysis of D0 -> pi+ pi- pi0).  Particle 1 is the neutral, 2 and 3 the
+   * CP-conjugate pair (m2 = m3); observables s12, s13 and t.  The anti-particle's amplitudes
+   * are the same lineshapes at the exchanged point, abar_k(s12, s13) = a_k(s13, s12), and
+   * A = sum_k c_k a_k, B = sum_k c_k abar_k (no CP violation, q/p = 1).  The rate and its
+   * normalisation are GOO_OP_TD4's with these A and B; the normalisation uses three MC Gram
+   * matrices <a_k a_l*>, <abar_k abar_l*>, <a_k abar_l*>. */
+  GOO_OP_TD3 = 25    /* root over GOO_OP_BW / GOO_OP_NR children (as GOO_OP_COHERENT):
+                        obs[0]=s12, obs[1]=s13, ival[0]=t; par[0..3] = x, y, tau (ps),
+                        sigma_t (ps); dval = {M, m1, m2, m3, r_res, r_parent}            */
 };
 
 /* Angular structures of GOO_OP_AMP4 (spins of the 12 and 34 resonances in brackets; s = sin):

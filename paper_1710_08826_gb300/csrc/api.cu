@@ -117,7 +117,7 @@ int goo_model_build(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_para
     m->hi[o] = obs_hi[o];
   }
   int rc;
-  if (nodes[n_nodes - 1].op == GOO_OP_COHERENT) {
+  if (nodes[n_nodes - 1].op == GOO_OP_COHERENT || nodes[n_nodes - 1].op == GOO_OP_TD3) {
     rc = build_dalitz_model(ctx, nodes, n_nodes, n_params, n_obs, obs_lo, obs_hi, m);
   } else if (nodes[n_nodes - 1].op == GOO_OP_TD4) {
     rc = build_td4_model(ctx, nodes, n_nodes, n_params, n_obs, m);

@@ -117,9 +117,10 @@ struct goo_dataset {
   bool owns64 = true, owns32 = true;
   double lo[goo::kMaxCols] = {};
   double hi[goo::kMaxCols] = {};
-  // amplitude caches attached to this dataset, [0]: float32, [1]: float64 (built lazily by
-  // the amplitude-model path and rebuilt when the model or its lineshapes change)
-  goo::CacheSlot cache[2];
+  // amplitude caches attached to this dataset, [0]: float32, [1]: float64, [2], [3]: the
+  // same at the exchanged Dalitz point (time-dependent three-body model); built lazily by the
+  // amplitude-model path and rebuilt when the model or its lineshapes change
+  goo::CacheSlot cache[4];
 };
 
 namespace goo {

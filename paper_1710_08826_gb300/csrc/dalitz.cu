@@ -36,6 +36,7 @@
 
 #include "common.cuh"
 #include "dalitz.cuh"
+#include "timeterms.cuh"
 #include "model.cuh"
 
 namespace goo {
@@ -59,6 +60,13 @@ struct DalitzModel {
   const goo_dataset* mc = nullptr;
   bool floating = false;           // GOO_LINESHAPE_FLOATING: no cache, lineshape gradients
   double* ls_mc = nullptr;         // MC-pass lane sums of the floating-lineshape path (device)
+  // time-dependent three-body model (GOO_OP_TD3)
+  bool td = false;
+  int col_t = 2;
+  int par_t[4] = {-1, -1, -1, -1};  // x, y, tau, sigma_t
+  double* gram3_dev[2] = {nullptr, nullptr};  // per precision: G_aa, G_bb, G_ab (K x K complex each)
+  double gram3_host[2][3 * kMaxAmp * kMaxAmp * 2];
+  uint64_t gram3_key[2] = {0, 0};
 };
 
 // Cache layout.  FP32: ceil(nbw/2) planes of float4 (re_k, im_k, re_k+1, im_k+1) per event;
@@ -658,6 +666,307 @@ __global__ void __launch_bounds__(kBlock)
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// time-dependent three-body model (GOO_OP_TD3; paper Sec. 5, Table 2).  The anti-particle's
+// amplitudes are the same lineshapes at the exchanged point, abar_k(s12, s13) =
+// a_k(s13, s12) (a second cache built from the exchanged columns); A = sum c_k a_k,
+// B = sum c_k abar_k with the same coefficients.  Per event the four decay-time terms of the
+// four-body model (timeterms.cuh) give
+//   R = (|A|^2+|B|^2)/2 T_ch + (|A|^2-|B|^2)/2 T_c + Re(AB*) T_sh + Im(AB*) T_s,
+// and the gradient lanes Re / -Im of (a_k V_A + abar_k V_B) / R with
+//   V_A = (T_ch + T_c) A* + (T_sh - i T_s) B*,  V_B = (T_ch - T_c) B* + (T_sh + i T_s) A*,
+// plus d R / d(x, y, tau, sigma_t) / R.  N comes from three MC Gram matrices,
+//   <|A|^2> = c^T G_aa c*, <|B|^2> = c^T G_bb c*, <AB*> = c^T G_ab c*,
+// and the closed-form time integrals.
+// ---------------------------------------------------------------------------------------
+
+// G_kl = mean over the events of X_k conj(Y_l) (k, l < K; the amplitude nbw is the constant
+// NR amplitude 1 when present), one block per (k, l), FP64 sums in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) gram_cross_kernel(const void* xv, const void* yv, int64_t n, int nbw, int K,
+                                                            double* out) {
+  const int k = blockIdx.x / K, l = blockIdx.x % K;
+  auto amp = [&](const void* c, int j, int64_t i, double& re, double& im) {
+    if (j >= nbw) {
+      re = 1.0;
+      im = 0.0;
+    } else if constexpr (sizeof(T) == 4) {
+      const float4 v = ((const float4*)c)[(int64_t)(j / 2) * n + i];
+      re = (double)((j & 1) ? v.z : v.x);
+      im = (double)((j & 1) ? v.w : v.y);
+    } else {
+      const double2 v = ((const double2*)c)[(int64_t)j * n + i];
+      re = v.x;
+      im = v.y;
+    }
+  };
+  double sr = 0.0, si = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    double xr, xi, yr, yi;
+    amp(xv, k, i, xr, xi);
+    amp(yv, l, i, yr, yi);
+    sr += xr * yr + xi * yi;  // X conj(Y)
+    si += xi * yr - xr * yi;
+  }
+  __shared__ double s_r[kBlock / 32], s_i[kBlock / 32];
+  for (int m = 16; m > 0; m >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, m);
+    si += __shfl_xor_sync(0xffffffffu, si, m);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_r[threadIdx.x >> 5] = sr;
+    s_i[threadIdx.x >> 5] = si;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0.0, ti = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      tr += s_r[w];
+      ti += s_i[w];
+    }
+    out[2 * (k * K + l)] = tr / (double)n;
+    out[2 * (k * K + l) + 1] = ti / (double)n;
+  }
+}
+
+constexpr int kTd3KB = 15;  // resonance slots of the time-dependent three-body kernels (NR in slot 15)
+
+template <typename T>
+struct Td3Args {
+  T cr[kTd3KB + 1], ci[kTd3KB + 1];  // coefficients by slot: resonances, then the NR in slot kTd3KB
+  T G, x, y, s;                      // 1/tau, mixing, resolution in the path's precision
+  T wa[kWMax];                       // Weideman coefficients
+  T wL;
+  int wN, nbw, K, n_params;
+  int par_re[kMaxAmp], par_im[kMaxAmp], par_t[4];  // parameter of each amplitude (tree order)
+  int64_t n_total;                   // events of the dataset (cache plane length)
+};
+
+template <bool GRAD>
+struct Td3Lanes {
+  static constexpr int NS = GRAD ? 1 + 2 * (kTd3KB + 1) + 4 : 1;
+};
+
+template <typename T, bool GRAD>
+__global__ void __launch_bounds__(kBlock)
+    td3_nll_kernel(const __grid_constant__ Td3Args<T> a, const void* __restrict__ cache_a,
+                   const void* __restrict__ cache_b, const T* __restrict__ tcol, int64_t begin, int64_t end,
+                   const double* __restrict__ grams, float2* partials, unsigned* counters, double* out, int out_mode) {
+  constexpr int KB = kTd3KB, KA = KB + 1;
+  constexpr int NS = Td3Lanes<GRAD>::NS;
+  __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
+  __shared__ unsigned s_bad[kBlock / 32];
+  __shared__ double s_out[NS];
+  const int64_t n = a.n_total;
+  const int nbw = a.nbw;
+  // the amplitude pair of slot k (< nbw) at event i: a_k and abar_k
+  auto load = [&](int k, int64_t i, T& ar, T& ai, T& br, T& bi) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 va = __ldg((const float4*)cache_a + (int64_t)(k / 2) * n + i);
+      const float4 vb = __ldg((const float4*)cache_b + (int64_t)(k / 2) * n + i);
+      ar = (k & 1) ? va.z : va.x;
+      ai = (k & 1) ? va.w : va.y;
+      br = (k & 1) ? vb.z : vb.x;
+      bi = (k & 1) ? vb.w : vb.y;
+    } else {
+      const double2 va = __ldg((const double2*)cache_a + (int64_t)k * n + i);
+      const double2 vb = __ldg((const double2*)cache_b + (int64_t)k * n + i);
+      ar = va.x;
+      ai = va.y;
+      br = vb.x;
+      bi = vb.y;
+    }
+  };
+  Kahan lf32;
+  double lf64 = 0.0;
+  T lre[KA], lim[KA], lt[4];
+#pragma unroll
+  for (int k = 0; k < KA; ++k) lre[k] = lim[k] = T(0);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) lt[j] = T(0);
+  unsigned bad = 0;
+  for (int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T t = tcol[i];
+    T Ar = a.cr[KB], Ai = a.ci[KB], Br = a.cr[KB], Bi = a.ci[KB];  // the NR amplitude is 1 for both
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      if (k >= nbw) break;
+      T ar, ai, br, bi;
+      load(k, i, ar, ai, br, bi);
+      Ar += a.cr[k] * ar - a.ci[k] * ai;
+      Ai += a.cr[k] * ai + a.ci[k] * ar;
+      Br += a.cr[k] * br - a.ci[k] * bi;
+      Bi += a.cr[k] * bi + a.ci[k] * br;
+    }
+    TimeTerms<T> tt;
+    time_terms_g<T>(a.G, a.x, a.y, a.s, a.wa, a.wN, a.wL, t, tt);
+    const T AA = Ar * Ar + Ai * Ai, BB = Br * Br + Bi * Bi;
+    const T ABr = Ar * Br + Ai * Bi, ABi = Ai * Br - Ar * Bi;  // A conj(B)
+    const T hp = T(0.5) * (AA + BB), hm = T(0.5) * (AA - BB);
+    const T R = hp * tt.Tch + hm * tt.Tc + ABr * tt.Tsh + ABi * tt.Ts;
+    if (!(R > T(0))) {
+      ++bad;
+      continue;
+    }
+    if constexpr (sizeof(T) == 4) lf32.add(logf(R));
+    else lf64 += log(R);
+    if constexpr (GRAD) {
+      const T invR = T(1) / R;
+      const T cp = (tt.Tch + tt.Tc) * invR, cm = (tt.Tch - tt.Tc) * invR, sh = tt.Tsh * invR, ss = tt.Ts * invR;
+      // V_A / R = cp A* + (sh - i ss) B*,  V_B / R = cm B* + (sh + i ss) A*
+      const T VAr = cp * Ar + sh * Br - ss * Bi, VAi = -cp * Ai - sh * Bi - ss * Br;
+      const T VBr = cm * Br + sh * Ar + ss * Ai, VBi = -cm * Bi - sh * Ai + ss * Ar;
+#pragma unroll
+      for (int k = 0; k < KB; ++k) {
+        if (k >= nbw) break;
+        T ar, ai, br, bi;
+        load(k, i, ar, ai, br, bi);
+        const T qr = ar * VAr - ai * VAi + br * VBr - bi * VBi;  // Re(a V_A + abar V_B) / R
+        const T qi = ar * VAi + ai * VAr + br * VBi + bi * VBr;
+        lre[k] += qr;
+        lim[k] -= qi;
+      }
+      lre[KB] += VAr + VBr;  // the NR slot (a = abar = 1)
+      lim[KB] -= VAi + VBi;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        lt[j] += (hp * tt.d[j][0] + hm * tt.d[j][2] + ABr * tt.d[j][1] + ABi * tt.d[j][3]) * invR;
+    }
+  }
+  ddf v[NS];
+  v[0] = (sizeof(T) == 4) ? lf32.value() : dd_from_double(lf64);
+  if constexpr (GRAD) {
+#pragma unroll
+    for (int k = 0; k < KA; ++k) {
+      v[1 + 2 * k] = (sizeof(T) == 4) ? ddf{(float)lre[k], 0.f} : dd_from_double((double)lre[k]);
+      v[2 + 2 * k] = (sizeof(T) == 4) ? ddf{(float)lim[k], 0.f} : dd_from_double((double)lim[k]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      v[1 + 2 * KA + j] = (sizeof(T) == 4) ? ddf{(float)lt[j], 0.f} : dd_from_double((double)lt[j]);
+  }
+  for (int m = 16; m > 0; m >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, m);
+  if ((threadIdx.x & 31) == 0) s_bad[threadIdx.x >> 5] = bad;
+  block_reduce_to_partials<NS>(v, NS, partials, s_red);
+  if (threadIdx.x == 0) {
+    unsigned b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_bad[w];
+    if (b) atomicAdd(counters + 1, b);
+  }
+  if (!last_block_ticket(counters, gridDim.x)) return;
+  // The last block: its last warp forms the normalisation from the three Gram matrices
+  // (lane kk: amplitude kk in tree order) while the other threads reduce the lanes.
+  __shared__ double s_nre[kMaxAmp], s_nim[kMaxAmp], s_dt[3];
+  __shared__ int s_pre[kMaxAmp], s_pim[kMaxAmp], s_slot[kMaxAmp];
+  __shared__ double s_N, s_logN;
+  const int K = a.K;
+  if ((int)(threadIdx.x >> 5) == (int)(blockDim.x >> 5) - 1) {
+    const int kk = threadIdx.x & 31;
+    const double x = (double)a.x, y = (double)a.y, tau = 1.0 / (double)a.G;
+    const double iy = 1.0 / (1 - y * y), ix = 1.0 / (1 + x * x);
+    const double Ich = tau * iy, Ish = y * tau * iy, Ic = tau * ix, Is = x * tau * ix;
+    const double* Gaa = grams;
+    const double* Gbb = grams + 2 * K * K;
+    const double* Gab = grams + 4 * K * K;
+    auto coef = [&](int j, double& r, double& im) {
+      const int sl = j < nbw ? j : KB;
+      r = (double)a.cr[sl];
+      im = (double)a.ci[sl];
+    };
+    double var = 0, vai = 0, vbr = 0, vbi = 0, ur = 0, ui = 0, wr = 0, wi = 0, PA = 0, PB = 0, Xr = 0, Xi = 0;
+    if (kk < K) {
+      for (int l = 0; l < K; ++l) {
+        double clr, cli;
+        coef(l, clr, cli);
+        const double ar_ = Gaa[2 * (kk * K + l)], ai_ = Gaa[2 * (kk * K + l) + 1];
+        const double br_ = Gbb[2 * (kk * K + l)], bi_ = Gbb[2 * (kk * K + l) + 1];
+        const double xr_ = Gab[2 * (kk * K + l)], xi_ = Gab[2 * (kk * K + l) + 1];
+        const double yr_ = Gab[2 * (l * K + kk)], yi_ = Gab[2 * (l * K + kk) + 1];
+        var += ar_ * clr + ai_ * cli;  // G_aa[kk][l] conj(c_l)
+        vai += ai_ * clr - ar_ * cli;
+        vbr += br_ * clr + bi_ * cli;
+        vbi += bi_ * clr - br_ * cli;
+        ur += xr_ * clr + xi_ * cli;   // G_ab[kk][l] conj(c_l)
+        ui += xi_ * clr - xr_ * cli;
+        wr += clr * yr_ - cli * yi_;   // c_l G_ab[l][kk]
+        wi += clr * yi_ + cli * yr_;
+      }
+      double ckr, cki;
+      coef(kk, ckr, cki);
+      PA = ckr * var - cki * vai;  // Re(c_kk v_a)
+      PB = ckr * vbr - cki * vbi;
+      Xr = ckr * ur - cki * ui;    // c_kk u
+      Xi = ckr * ui + cki * ur;
+    }
+    for (int m = 16; m > 0; m >>= 1) {
+      PA += __shfl_xor_sync(0xffffffffu, PA, m);
+      PB += __shfl_xor_sync(0xffffffffu, PB, m);
+      Xr += __shfl_xor_sync(0xffffffffu, Xr, m);
+      Xi += __shfl_xor_sync(0xffffffffu, Xi, m);
+    }
+    const double N = 0.5 * (PA + PB) * Ich + 0.5 * (PA - PB) * Ic + Xr * Ish + Xi * Is;
+    const double invN = 1.0 / N;
+    if (kk < K) {
+      // d<|A|^2>/dRe c = 2 Re v_a, /dIm c = -2 Im v_a;  dX/dRe c = u + w, dX/dIm c = i (u - w)
+      const double dre = 0.5 * (2 * var + 2 * vbr) * Ich + 0.5 * (2 * var - 2 * vbr) * Ic + (ur + wr) * Ish +
+                         (ui + wi) * Is;
+      const double dim = 0.5 * (-2 * vai - 2 * vbi) * Ich + 0.5 * (-2 * vai + 2 * vbi) * Ic - (ui - wi) * Ish +
+                         (ur - wr) * Is;
+      s_nre[kk] = dre * invN;
+      s_nim[kk] = dim * invN;
+      s_pre[kk] = a.par_re[kk];
+      s_pim[kk] = a.par_im[kk];
+      s_slot[kk] = kk < nbw ? kk : KB;
+    }
+    if (kk == 0) {
+      s_N = N;
+      s_logN = log(N);
+      const double ix2 = ix * ix, iy2 = iy * iy;
+      const double dxc = -2 * x * tau * ix2, dxs = tau * (1 - x * x) * ix2;
+      const double dych = 2 * y * tau * iy2, dysh = tau * (1 + y * y) * iy2;
+      s_dt[0] = (0.5 * (PA - PB) * dxc + Xi * dxs) * invN;
+      s_dt[1] = (0.5 * (PA + PB) * dych + Xr * dysh) * invN;
+      s_dt[2] = (0.5 * (PA + PB) * iy + 0.5 * (PA - PB) * ix + Xr * y * iy + Xi * x * ix) * invN;
+    }
+  }
+  reduce_partials(partials, NS, gridDim.x, s_out, s_red, blockDim.x - 32);
+  const double nev = (double)(end - begin);
+  const int P = a.n_params;
+  const int off = out_mode == 0 ? 2 : 3;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    double g = 0.0;
+    if (GRAD) {
+      for (int kk = 0; kk < K; ++kk) {
+        const int sl = s_slot[kk];
+        if (s_pre[kk] == p) g += -s_out[1 + 2 * sl] + nev * s_nre[kk];
+        if (s_pim[kk] == p) g += -s_out[2 + 2 * sl] + nev * s_nim[kk];
+      }
+      const int o = 1 + 2 * KA;
+      for (int j = 0; j < 4; ++j)
+        if (a.par_t[j] == p) g += -s_out[o + j] + (j < 3 ? nev * s_dt[j] : 0.0);
+    }
+    out[off + p] = g;
+  }
+  if (threadIdx.x == 0) {
+    // every other block added to these words before its ticket (and a fence): plain L2 reads
+    const unsigned nbad = __ldcg(counters + 1);
+    const unsigned status = __ldcg(counters + kStatusWord);
+    counters[1] = 0u;
+    counters[kStatusWord] = 0u;
+    *counters = 0u;  // the ticket
+    const double nb = status ? -1.0 : (double)nbad;  // a device wait that gave up: negative count
+    out[0] = -s_out[0] + nev * s_logN;
+    if (out_mode == 0) {
+      out[1] = nb;
+      out[2 + P] = s_N;
+    } else {
+      out[1] = 0.0;
+      out[2] = nb;
+    }
+  }
+}
+
 static int dalitz_constants(goo_model* m, const double* theta) {
   DalitzModel& d = *m->dalitz;
   const uint64_t key = lineshape_key(d, theta);
@@ -714,17 +1023,22 @@ static int dalitz_constants(goo_model* m, const double* theta) {
   GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   d.ls_key = key;
   d.gram_key[0] = d.gram_key[1] = 0;
+  d.gram3_key[0] = d.gram3_key[1] = 0;
   return GOO_OK;
 }
 
 // Builds (if stale) the amplitude cache of `ds` in `precision`; returns its device pointer.
-static int ensure_cache(goo_model* m, const goo_dataset* ds_c, int precision, const void** out) {
+// With `exchanged`, the amplitudes at the exchanged Dalitz point (s13, s12): the anti-particle
+// amplitudes of the time-dependent three-body model.
+static int ensure_cache(goo_model* m, const goo_dataset* ds_c, int precision, const void** out,
+                        bool exchanged = false) {
   goo_dataset* ds = const_cast<goo_dataset*>(ds_c);
   DalitzModel& d = *m->dalitz;
   goo_ctx* ctx = m->ctx;
   const int pi = precision == GOO_F32 ? 0 : 1;
-  const uint64_t key = d.ls_key ^ (uint64_t)(uintptr_t)m ^ (uint64_t)(pi + 1) * 0x9e3779b97f4a7c15ull;
-  CacheSlot& slot = ds->cache[pi];
+  const uint64_t key = d.ls_key ^ (uint64_t)(uintptr_t)m ^ (uint64_t)(pi + 1 + (exchanged ? 4 : 0)) * 0x9e3779b97f4a7c15ull;
+  CacheSlot& slot = ds->cache[pi + (exchanged ? 2 : 0)];
+  const int ca = exchanged ? d.col13 : d.col12, cb = exchanged ? d.col12 : d.col13;
   const int64_t n = ds->n;
   const size_t bytes = pi == 0 ? (size_t)((d.nbw + 1) / 2) * (size_t)n * sizeof(float4)
                                : (size_t)d.nbw * (size_t)n * sizeof(double2);
@@ -746,12 +1060,10 @@ static int ensure_cache(goo_model* m, const goo_dataset* ds_c, int precision, co
     const int nb = grid_blocks(ctx, n, 4);
     if (pi == 0) {
       LaunchScope ls(ctx, "amp_cache_f32");
-      amp_cache_f32_kernel<<<nb, kBlock, 0, ctx->stream>>>(d.dev, ds->d32[d.col12], ds->d32[d.col13], n,
-                                                          (float4*)slot.ptr);
+      amp_cache_f32_kernel<<<nb, kBlock, 0, ctx->stream>>>(d.dev, ds->d32[ca], ds->d32[cb], n, (float4*)slot.ptr);
     } else {
       LaunchScope ls(ctx, "amp_cache_f64");
-      amp_cache_f64_kernel<<<nb, kBlock, 0, ctx->stream>>>(d.dev, ds->d64[d.col12], ds->d64[d.col13], n,
-                                                          (double2*)slot.ptr);
+      amp_cache_f64_kernel<<<nb, kBlock, 0, ctx->stream>>>(d.dev, ds->d64[ca], ds->d64[cb], n, (double2*)slot.ptr);
     }
     GOO_CUDA_TRY(cudaGetLastError());
   }
@@ -988,6 +1300,132 @@ static int launch_ls_pair(goo_model* m, const goo_dataset* ds, int64_t begin, in
   return launch_ls<T, 15, GRAD, false>(m, ds, begin, end, theta, m->ctx->scratch.result, out_mode);
 }
 
+// The three MC Gram matrices of the time-dependent three-body model (G_aa, G_bb, G_ab) in
+// `precision`, rebuilt when the lineshapes or the MC sample change; a host copy for
+// goo_normalise.
+static int ensure_td_grams(goo_model* m, int precision) {
+  DalitzModel& d = *m->dalitz;
+  goo_ctx* ctx = m->ctx;
+  const int pi = precision == GOO_F32 ? 0 : 1;
+  if (!d.mc) return set_error(GOO_ERR_STATE, "amplitude model has no MC normalisation sample (goo_model_set_norm)");
+  if (d.mc->n < 1) return set_error(GOO_ERR_ARG, "the MC normalisation sample is empty");
+  const uint64_t key = d.ls_key ^ (uint64_t)(uintptr_t)d.mc ^ (uint64_t)(pi + 11);
+  if (d.gram3_key[pi] == key) return GOO_OK;
+  const void *ca = nullptr, *cb = nullptr;
+  GOO_TRY(ensure_cache(m, d.mc, precision, &ca));
+  GOO_TRY(ensure_cache(m, d.mc, precision, &cb, true));
+  const int K = d.K;
+  double* g = d.gram3_dev[pi];
+  const void* pairs[3][2] = {{ca, ca}, {cb, cb}, {ca, cb}};
+  for (int q = 0; q < 3; ++q) {
+    LaunchScope ls(ctx, pi == 0 ? "td3_gram_f32" : "td3_gram_f64");
+    if (pi == 0)
+      gram_cross_kernel<float><<<K * K, kBlock, 0, ctx->stream>>>(pairs[q][0], pairs[q][1], d.mc->n, d.nbw, K,
+                                                                 g + (size_t)q * 2 * K * K);
+    else
+      gram_cross_kernel<double><<<K * K, kBlock, 0, ctx->stream>>>(pairs[q][0], pairs[q][1], d.mc->n, d.nbw, K,
+                                                                  g + (size_t)q * 2 * K * K);
+  }
+  GOO_CUDA_TRY(cudaGetLastError());
+  GOO_CUDA_TRY(cudaMemcpyAsync(d.gram3_host[pi], g, sizeof(double) * 3 * 2 * K * K, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  d.gram3_key[pi] = key;
+  return GOO_OK;
+}
+
+template <typename T>
+static void fill_td3(const DalitzModel& d, const double* theta, int n_params, int64_t n_total, Td3Args<T>& a) {
+  std::memset(&a, 0, sizeof a);
+  for (int k = 0; k < d.K; ++k) {
+    const int sl = k < d.nbw ? k : kTd3KB;
+    a.cr[sl] = (T)theta[d.par_re[k]];
+    a.ci[sl] = (T)theta[d.par_im[k]];
+    a.par_re[k] = d.par_re[k];
+    a.par_im[k] = d.par_im[k];
+  }
+  a.x = (T)theta[d.par_t[0]];
+  a.y = (T)theta[d.par_t[1]];
+  a.G = (T)(1.0 / theta[d.par_t[2]]);
+  a.s = (T)theta[d.par_t[3]];
+  for (int j = 0; j < 4; ++j) a.par_t[j] = d.par_t[j];
+  const WeidemanTables& w = weideman();
+  a.wN = sizeof(T) == 4 ? kWN32 : kWN64;
+  for (int j = 0; j < a.wN; ++j) a.wa[j] = (T)(sizeof(T) == 4 ? w.a32[j] : w.a64[j]);
+  a.wL = (T)(sizeof(T) == 4 ? w.L32 : w.L64);
+  a.nbw = d.nbw;
+  a.K = d.K;
+  a.n_params = n_params;
+  a.n_total = n_total;
+}
+
+template <typename T, bool GRAD>
+static int launch_td3(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, const double* theta,
+                      const void* ca, const void* cb, int out_mode) {
+  DalitzModel& d = *m->dalitz;
+  goo_ctx* ctx = m->ctx;
+  const int pi = sizeof(T) == 4 ? 0 : 1;
+  static int occ[2] = {0, 0};
+  int& o = occ[pi];
+  if (o == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, td3_nll_kernel<T, GRAD>, kBlock, 0) != cudaSuccess || o < 1) {
+      cudaGetLastError();
+      o = 1;
+    }
+  }
+  const int nb = grid_blocks(ctx, end - begin, o);
+  constexpr int NS = Td3Lanes<GRAD>::NS;
+  GOO_TRY(ensure_partials(ctx, (size_t)nb * NS));
+  Td3Args<T> a;
+  fill_td3<T>(d, theta, m->n_params, ds->n, a);
+  const T* tcol = sizeof(T) == 4 ? (const T*)ds->d32[d.col_t] : (const T*)ds->d64[d.col_t];
+  {
+    LaunchScope ls(ctx, sizeof(T) == 4 ? (GRAD ? "td3_nll_grad_f32" : "td3_nll_f32")
+                                       : (GRAD ? "td3_nll_grad_f64" : "td3_nll_f64"));
+    td3_nll_kernel<T, GRAD><<<nb, kBlock, 0, ctx->stream>>>(a, ca, cb, tcol, begin, end, d.gram3_dev[pi],
+                                                            ctx->scratch.partials, ctx->scratch.counters,
+                                                            ctx->scratch.result, out_mode);
+  }
+  GOO_CUDA_TRY(cudaGetLastError());
+  return GOO_OK;
+}
+
+// N of the time-dependent three-body model at theta from the host copy of the Gram matrices.
+static double td3_norm_host(const DalitzModel& d, const double* G, const double* theta, bool f32) {
+  const int K = d.K;
+  auto cf = [&](int k, double& r, double& i) {
+    r = theta[d.par_re[k]];
+    i = theta[d.par_im[k]];
+    if (f32) {
+      r = (double)(float)r;
+      i = (double)(float)i;
+    }
+  };
+  double PA = 0, PB = 0, Xr = 0, Xi = 0;
+  for (int k = 0; k < K; ++k)
+    for (int l = 0; l < K; ++l) {
+      double ckr, cki, clr, cli;
+      cf(k, ckr, cki);
+      cf(l, clr, cli);
+      const double pr = ckr * clr + cki * cli, pim = cki * clr - ckr * cli;  // c_k conj(c_l)
+      const double* Gs[3] = {G, G + 2 * K * K, G + 4 * K * K};
+      const double gr[3] = {Gs[0][2 * (k * K + l)], Gs[1][2 * (k * K + l)], Gs[2][2 * (k * K + l)]};
+      const double gi[3] = {Gs[0][2 * (k * K + l) + 1], Gs[1][2 * (k * K + l) + 1], Gs[2][2 * (k * K + l) + 1]};
+      PA += pr * gr[0] - pim * gi[0];
+      PB += pr * gr[1] - pim * gi[1];
+      Xr += pr * gr[2] - pim * gi[2];
+      Xi += pr * gi[2] + pim * gr[2];
+    }
+  double x = theta[d.par_t[0]], y = theta[d.par_t[1]], tau = theta[d.par_t[2]];
+  if (f32) {
+    x = (double)(float)x;
+    y = (double)(float)y;
+    tau = 1.0 / (double)(float)(1.0 / tau);
+  }
+  const double Ich = tau / (1 - y * y), Ish = y * tau / (1 - y * y), Ic = tau / (1 + x * x), Is = x * tau / (1 + x * x);
+  return 0.5 * (PA + PB) * Ich + 0.5 * (PA - PB) * Ic + Xr * Ish + Xi * Is;
+}
+
 int build_dalitz_model(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_params, int n_obs, const double* lo,
                        const double* hi, goo_model* m) {
   const goo_node& root = nodes[n_nodes - 1];
@@ -1000,6 +1438,17 @@ int build_dalitz_model(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_p
   m->kind = 1;
   d->col12 = root.obs[0];
   d->col13 = root.obs[1];
+  if (root.op == GOO_OP_TD3) {
+    d->td = true;
+    d->col_t = root.ival[0];
+    if (n_obs < 3 || d->col_t < 0 || d->col_t >= n_obs || d->col_t == d->col12 || d->col_t == d->col13)
+      return set_error(GOO_ERR_ARG, "GOO_OP_TD3 needs a decay-time observable (ival[0]) besides s12 and s13");
+    for (int j = 0; j < 4; ++j) {
+      if (root.par[j] < 0 || root.par[j] >= n_params)
+        return set_error(GOO_ERR_ARG, "GOO_OP_TD3: time parameter %d has index %d", j, root.par[j]);
+      d->par_t[j] = root.par[j];
+    }
+  }
   d->M = root.dval[0];
   d->m1 = root.dval[1];
   d->m2 = root.dval[2];
@@ -1038,6 +1487,16 @@ int build_dalitz_model(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_p
     }
   }
   if (d->nbw > 15) return set_error(GOO_ERR_UNSUPPORTED, "at most 15 resonances");
+  if (d->td && std::fabs(d->m2 - d->m3) > 1e-12 * d->M)
+    return set_error(GOO_ERR_ARG, "GOO_OP_TD3: the CP-conjugate particles 2 and 3 need equal masses (%g, %g)", d->m2,
+                     d->m3);
+  if (d->td) {
+    for (int i = 0; i < 2; ++i)
+      if (cudaMalloc(&d->gram3_dev[i], sizeof(double) * 3 * 2 * kMaxAmp * kMaxAmp) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(GOO_ERR_OOM, "cannot allocate the amplitude model");
+      }
+  }
   (void)lo;
   (void)hi;
   if (cudaMalloc(&d->dev, sizeof(DalitzDev)) != cudaSuccess ||
@@ -1060,6 +1519,7 @@ int dalitz_set_norm(goo_model* m, const goo_norm_spec* spec) {
   if (mc->ncols <= d.col12 || mc->ncols <= d.col13) return set_error(GOO_ERR_ARG, "MC sample lacks s12/s13 columns");
   d.mc = mc;
   d.gram_key[0] = d.gram_key[1] = 0;
+  d.gram3_key[0] = d.gram3_key[1] = 0;
   m->norm = *spec;
   return GOO_OK;
 }
@@ -1071,6 +1531,8 @@ void dalitz_free(goo_model* m) {
   for (int i = 0; i < 2; ++i)
     if (d->gram_dev[i]) cudaFree(d->gram_dev[i]);
   if (d->ls_mc) cudaFree(d->ls_mc);
+  for (int i = 0; i < 2; ++i)
+    if (d->gram3_dev[i]) cudaFree(d->gram3_dev[i]);
   delete d;
   m->dalitz = nullptr;
 }
@@ -1097,6 +1559,12 @@ static double quad_form(const DalitzModel& d, const double* G, const double* the
 
 int dalitz_normalise(goo_model* m, const double* theta, int precision, double* norm_out) {
   GOO_TRY(dalitz_constants(m, theta));
+  if (m->dalitz->td) {
+    GOO_TRY(ensure_td_grams(m, precision));
+    norm_out[0] = td3_norm_host(*m->dalitz, m->dalitz->gram3_host[precision == GOO_F32 ? 0 : 1], theta,
+                                precision == GOO_F32);
+    return GOO_OK;
+  }
   GOO_TRY(ensure_gram(m, precision));
   const int pi = precision == GOO_F32 ? 0 : 1;
   norm_out[0] = quad_form(*m->dalitz, m->dalitz->gram_host[pi], theta, precision == GOO_F32);
@@ -1111,7 +1579,25 @@ int dalitz_nll(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, 
   if (ds->ncols <= d.col12 || ds->ncols <= d.col13) return set_error(GOO_ERR_ARG, "dataset lacks s12/s13 columns");
   GOO_TRY(dalitz_constants(m, theta));
   const int nout = (out_mode == 0 ? 2 : 3) + P;
-  if (d.floating) {
+  if (d.td) {
+    // time-dependent three-body model: amplitude caches at the event and the exchanged point
+    if (ds->ncols <= d.col_t) return set_error(GOO_ERR_ARG, "dataset lacks the decay-time column");
+    GOO_TRY(ensure_td_grams(m, precision));
+    if (end <= begin) {
+      for (int i = 0; i < nout; ++i) out[i] = 0.0;
+      return GOO_OK;
+    }
+    const void *ca = nullptr, *cb = nullptr;
+    GOO_TRY(ensure_cache(m, ds, precision, &ca));
+    GOO_TRY(ensure_cache(m, ds, precision, &cb, true));
+    if (precision == GOO_F32) {
+      GOO_TRY((grad ? launch_td3<float, true>(m, ds, begin, end, theta, ca, cb, out_mode)
+                    : launch_td3<float, false>(m, ds, begin, end, theta, ca, cb, out_mode)));
+    } else {
+      GOO_TRY((grad ? launch_td3<double, true>(m, ds, begin, end, theta, ca, cb, out_mode)
+                    : launch_td3<double, false>(m, ds, begin, end, theta, ca, cb, out_mode)));
+    }
+  } else if (d.floating) {
     // no cache and no Gram matrix: an MC pass and an event pass, lineshape gradients included
     if (!d.mc) return set_error(GOO_ERR_STATE, "amplitude model has no MC normalisation sample (goo_model_set_norm)");
     if (d.mc->n < 1) return set_error(GOO_ERR_ARG, "the MC normalisation sample is empty");
@@ -1158,6 +1644,7 @@ int dalitz_nll(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, 
 int dalitz_eval_logf(goo_model* m, const goo_dataset* ds, const double* theta, int precision, double* logf_dev) {
   DalitzModel& d = *m->dalitz;
   goo_ctx* ctx = m->ctx;
+  if (d.td) return set_error(GOO_ERR_UNSUPPORTED, "goo_eval_logf of the time-dependent three-body model");
   if (ds->ncols <= d.col12 || ds->ncols <= d.col13) return set_error(GOO_ERR_ARG, "dataset lacks s12/s13 columns");
   GOO_TRY(dalitz_constants(m, theta));
   GOO_TRY(ensure_gram(m, precision));
@@ -1186,6 +1673,7 @@ int dalitz_eval_logf(goo_model* m, const goo_dataset* ds, const double* theta, i
 // Host copies of the Gram matrix (K x K complex, model amplitude order: resonances in tree
 // order, then the non-resonant amplitude) and of the per-event amplitude cache (test access).
 int dalitz_gram(goo_model* m, const double* theta, int precision, double* out, int* K_out) {
+  if (m->dalitz->td) return set_error(GOO_ERR_UNSUPPORTED, "goo_gram: the time-dependent three-body model has three");
   GOO_TRY(dalitz_constants(m, theta));
   GOO_TRY(ensure_gram(m, precision));
   const int pi = precision == GOO_F32 ? 0 : 1;
@@ -1206,6 +1694,7 @@ int dalitz_amplitudes(goo_model* m, const goo_dataset* ds, const double* theta, 
 
 int dalitz_server_info(goo_model* m, const double* theta, AmpModelInfo* info) {
   if (m->kind != 1) return set_error(GOO_ERR_STATE, "toy server needs an amplitude model");
+  if (m->dalitz->td) return set_error(GOO_ERR_UNSUPPORTED, "toy server of the time-dependent three-body model");
   GOO_TRY(dalitz_constants(m, theta));
   GOO_TRY(ensure_gram(m, GOO_F32));
   const DalitzModel& d = *m->dalitz;
@@ -1235,6 +1724,8 @@ namespace goo {
 int dalitz_set_lineshapes(goo_model* m, int mode) {
   if (mode != GOO_LINESHAPE_CACHED && mode != GOO_LINESHAPE_FLOATING)
     return set_error(GOO_ERR_ARG, "goo_model_set_lineshapes: mode %d", mode);
+  if (m->dalitz->td && mode == GOO_LINESHAPE_FLOATING)
+    return set_error(GOO_ERR_UNSUPPORTED, "floating lineshapes of the time-dependent three-body model");
   m->dalitz->floating = mode == GOO_LINESHAPE_FLOATING;
   return GOO_OK;
 }
@@ -1247,4 +1738,5 @@ bool dalitz_lineshape_param(const goo_model* m, int p) {
 }
 
 bool dalitz_floating(const goo_model* m) { return m->dalitz->floating; }
+bool dalitz_time_dependent(const goo_model* m) { return m->dalitz->td; }
 }  // namespace goo

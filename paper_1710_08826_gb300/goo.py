@@ -18,7 +18,7 @@ GOO_ERR_NONPOSITIVE_PDF, GOO_ERR_TIMEOUT, GOO_ERR_STATE, GOO_ERR_UNSUPPORTED = -
 GOO_F64, GOO_F32 = 0, 1
 GOO_LINESHAPE_CACHED, GOO_LINESHAPE_FLOATING = 0, 1
 GOO_COPY, GOO_BORROW_DEVICE = 0, 1
-OP = dict(gauss=1, expo=2, poly2=3, argus=4, prod=10, add=11, bw=20, nr=21, coherent=22, td4=23, amp4=24)
+OP = dict(gauss=1, expo=2, poly2=3, argus=4, prod=10, add=11, bw=20, nr=21, coherent=22, td4=23, amp4=24, td3=25)
 ANG = dict(SS=0, VS0=1, SV0=2, VV0=3, VVpar=4, VVperp=5, TS0=6, TV0=7)
 NORM = dict(analytic=0, grid=1, mc=2)
 MAX_CHILD = 16
@@ -304,7 +304,7 @@ def spec_to_nodes(spec):
                 n.child[j] = k
             for j, name in enumerate(node[1]):
                 n.par[j] = pidx[name]
-        elif op == "coherent":
+        elif op in ("coherent", "td3"):
             kin, amps = node[1], node[2]
             kids = []
             for a in amps:
@@ -323,8 +323,12 @@ def spec_to_nodes(spec):
                 nodes.append(m)
                 kids.append(len(nodes) - 1)
             n = new()
-            n.op = OP["coherent"]
+            n.op = OP[op]
             n.obs[0], n.obs[1] = oidx["s12"], oidx["s13"]
+            if op == "td3":   # decay-time column and x, y, tau, sigma_t
+                n.ival[0] = oidx["t"]
+                for j, name in enumerate(node[3]):
+                    n.par[j] = pidx[name]
             n.n_child = len(kids)
             for j, k in enumerate(kids):
                 n.child[j] = k

@@ -1,0 +1,183 @@
+"""GPU parity of the time-dependent three-body amplitude path (amplitude caches at the event
+and at the exchanged point, three Gram matrices, NLL + gradient with mixing and resolution,
+shards, a fit, the full-size configuration) against the oracle."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import td3 as ot
+
+pytestmark = pytest.mark.gpu
+
+KIN = synth.TD3_MASSES
+TOL_NLL = {"f64": 1e-9, "f32": 1e-6}
+TOL_GRAD = {"f64": 1e-6, "f32": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def goo():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1710_08826_gb300 import goo as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def ctx(goo):
+    return goo.Context(0)
+
+
+def _cands(n, seed):
+    return synth.dalitz_candidates(n, seed, KIN["M"], KIN["m1"], KIN["m2"], KIN["m3"])
+
+
+def _mc(n, seed=1710015):
+    mc = _cands(n, seed)
+    mc["t"] = np.zeros(n)   # the normalisation ignores the MC's time column
+    return mc
+
+
+@pytest.fixture(scope="module")
+def sample():
+    spec = synth.td3_spec()
+    theta = np.array(synth.param_values(spec))
+    data = ot.generate(spec, theta, 20_000, 61, _cands)
+    return spec, theta, data, _mc(40_000)
+
+
+def _prep(spec, data, mc, precision):
+    if precision == "f32":
+        return synth.round_to_f32(data, spec), synth.round_to_f32(mc, spec)
+    return data, mc
+
+
+def _build(goo, ctx, spec, data, mc):
+    ds = goo.Dataset.from_spec(ctx, spec, data)
+    mcds = goo.Dataset.from_spec(ctx, spec, mc)
+    return ds, mcds, goo.Model(ctx, spec, mc=mcds)
+
+
+def _ref(spec, data, mc, th):
+    m = ot.TD3Model(spec)
+    return m.nll_grad(data, mc, th)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("shift", ["truth", "off", "mixing"])
+def test_nll_grad_matches_oracle(goo, ctx, sample, precision, shift):
+    spec, theta, data, mc = sample
+    m = ot.TD3Model(spec)
+    th = theta.copy()
+    if shift == "off":
+        th = th * 1.03
+    elif shift == "mixing":   # large mixing: every time term carries weight
+        th[m.tp[0]], th[m.tp[1]], th[m.tp[3]] = 0.3, 0.2, 0.08
+    d, c = _prep(spec, data, mc, precision)
+    ds, mcds, model = _build(goo, ctx, spec, d, c)
+    nll, g = model.nll_grad(ds, th, precision)
+    rnll, rg = _ref(spec, d, c, th)
+    assert abs(nll - rnll) <= TOL_NLL[precision] * abs(rnll), (nll, rnll)
+    scale = np.max(np.abs(rg))
+    assert np.max(np.abs(g - rg)) <= TOL_GRAD[precision] * scale, (g - rg) / scale
+    assert model.nll(ds, th, precision) == pytest.approx(nll, rel=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_normalisation(goo, ctx, sample, precision):
+    spec, theta, data, mc = sample
+    d, c = _prep(spec, data, mc, precision)
+    _, mcds, model = _build(goo, ctx, spec, d, c)
+    m = ot.TD3Model(spec)
+    th = theta.copy()
+    th[m.tp[0]], th[m.tp[1]] = 0.2, 0.1
+    N = model.normalise(th, precision)[0]
+    assert N == pytest.approx(m.norm(m.grams(c, th), th), rel=1e-11 if precision == "f64" else 2e-6)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_ragged_sizes_shards_and_empty(goo, ctx, sample, precision):
+    spec, theta, data, mc = sample
+    d, c = _prep(spec, data, mc, precision)
+    th = theta * 1.01
+    for n in (1, 255, 257, 4099):
+        sub = {k: v[:n] for k, v in d.items()}
+        ds, _, model = _build(goo, ctx, spec, sub, c)
+        nll, g = model.nll_grad(ds, th, precision)
+        rnll, rg = _ref(spec, sub, c, th)
+        assert abs(nll - rnll) <= TOL_NLL[precision] * max(abs(rnll), 1.0) * 10, (n, nll, rnll)
+    ds, _, model = _build(goo, ctx, spec, d, c)
+    full, gfull = model.nll_grad(ds, th, precision)
+    edges = [0, 1, 257, 5000, 11111, len(d["t"])]
+    parts = [model.nll_partial(ds, a, b, th, precision) for a, b in zip(edges[:-1], edges[1:])]
+    tot = goo.combine_partials(parts, model.n_params)
+    assert tot[2] == len(d["t"])
+    assert abs(tot[0] + tot[1] - full) <= (1e-12 if precision == "f64" else 1e-8) * abs(full)
+    empty = goo.Dataset.from_spec(ctx, spec, {k: np.zeros(0) for k in ("s12", "s13", "t")})
+    assert model.nll(empty, th, precision) == 0.0
+
+
+def test_fit_matches_oracle_fit(goo, ctx, sample):
+    # the coefficients and the lifetime free; x, y, sigma_t and the reference fixed
+    from oracle import fit as of
+    spec, theta, data, mc = sample
+    m = ot.TD3Model(spec)
+    free = np.array([not p[2] for p in spec["params"]])
+    for i in (m.tp[0], m.tp[1], m.tp[3]):
+        free[i] = False
+    start = theta.copy()
+    names = synth.param_names(spec)
+    coef = np.array([n.startswith(("re_", "im_")) for n in names]) & free
+    start[coef] *= 1.05
+    d, c = _prep(spec, data, mc, "f32")
+    ds, _, model = _build(goo, ctx, spec, d, c)
+    steps = np.array([p[3] if p[3] > 0 else 1.0 for p in spec["params"]])
+    th_gpu, err_gpu, info = model.fit(ds, start, free, steps, precision="f32", gradient="adjoint")
+    amps, grams = m.amplitudes(d, theta), m.grams(c, theta)
+    th_ref, err_ref, _, redm = of.fit(lambda t: m.nll_grad(d, c, t, amps=amps, grams=grams), start, free, steps)
+    assert redm < 1e-6
+    idx = np.flatnonzero(free)
+    pulls = np.abs(th_gpu[idx] - th_ref[idx]) / err_ref[idx]
+    assert np.max(pulls) < 0.01, pulls
+    np.testing.assert_allclose(err_gpu[idx], err_ref[idx], rtol=0.02)
+
+
+def test_full_size_configuration(goo, ctx):
+    # 2,000,000 events and 1,000,000 MC points, the sizes the benchmark times (uniform
+    # Dalitz points with t = Exp(tau) (x) N(0, sigma_t); the per-event work does not depend on
+    # where events fall)
+    spec = synth.td3_spec()
+    theta = np.array(synth.param_values(spec))
+    tau, sig = synth.TD4_TIME["tau"], synth.TD4_TIME["sigma_t"]
+    data = _cands(2_000_000, 1710016)
+    rng = np.random.default_rng(1710017)
+    data["t"] = np.clip(rng.exponential(tau, 2_000_000) + rng.normal(0.0, sig, 2_000_000),
+                        *spec["observables"][2][1:])
+    mc = _mc(1_000_000)
+    m = ot.TD3Model(spec)
+    th = theta * 1.01
+    for precision in ("f64", "f32"):
+        d, c = _prep(spec, data, mc, precision)
+        ds, _, model = _build(goo, ctx, spec, d, c)
+        nll, g = model.nll_grad(ds, th, precision)
+        amps, grams = m.amplitudes(d, th), m.grams(c, th)
+        rnll, rg = m.nll_grad(d, c, th, amps=amps, grams=grams)
+        assert abs(nll - rnll) <= TOL_NLL[precision] * abs(rnll), (precision, nll, rnll)
+        if precision == "f64":
+            assert np.max(np.abs(g - rg)) <= TOL_GRAD["f64"] * np.max(np.abs(rg))
+        else:
+            # each event's FP32 terms carry a relative error of a few 1e-7 times the event's
+            # condition number: A = sum c_k a_k and B are sums of larger terms that cancel
+            # where the amplitudes interfere destructively, and R combines four time terms
+            # that nearly cancel where |B| exceeds |A| (T_ch - T_c is second order in x, y).
+            # Uniform phase-space events sample such regions far more often than the model.
+            R, dR = m.rate(amps, d["t"], th, derivs=True)
+            cf = m.coefficients(th)
+            A, B = amps[0] @ cf, amps[1] @ cf
+            SA, SB = np.abs(amps[0]) @ np.abs(cf), np.abs(amps[1]) @ np.abs(cf)
+            T = ot.time_terms(d["t"], *(th[i] for i in m.tp))
+            AA, BB, AB = np.abs(A) ** 2, np.abs(B) ** 2, A * B.conj()
+            kappa = (SA ** 2 + SB ** 2) / (AA + BB) + (0.5 * (AA + BB) * np.abs(T[0]) + 0.5 * np.abs(AA - BB) * np.abs(T[2])
+                                                       + np.abs(AB.real * T[1]) + np.abs(AB.imag * T[3])) / R
+            mag = np.sum(kappa[:, None] * np.abs(dR / R[:, None]), axis=0)
+            err = np.abs(g - rg)
+            assert np.all(err <= 2e-6 * mag + TOL_GRAD["f32"] * np.max(np.abs(rg))), np.max(err / mag)
