@@ -34,7 +34,8 @@ BYTES_PER_EVENT_F64 = 24
 # only while the kernel's sources still hash to the captured value; bytes scale with events.
 _SOP_SRC = ['paper_1710_08826_gb300/csrc/tree.cu', 'paper_1710_08826_gb300/csrc/common.cuh', 'paper_1710_08826_gb300/csrc/model.cuh']
 _COH_SRC = ['paper_1710_08826_gb300/csrc/dalitz.cu', 'paper_1710_08826_gb300/csrc/dalitz.cuh', 'paper_1710_08826_gb300/csrc/common.cuh', 'paper_1710_08826_gb300/csrc/model.cuh']
-_TD4_SRC = ['paper_1710_08826_gb300/csrc/td4.cu', 'paper_1710_08826_gb300/csrc/dalitz.cuh', 'paper_1710_08826_gb300/csrc/common.cuh', 'paper_1710_08826_gb300/csrc/model.cuh']
+_TD4_SRC = ['paper_1710_08826_gb300/csrc/td4.cu', 'paper_1710_08826_gb300/csrc/dalitz.cuh', 'paper_1710_08826_gb300/csrc/common.cuh', 'paper_1710_08826_gb300/csrc/model.cuh', 'paper_1710_08826_gb300/csrc/timeterms.cuh']
+_TD3_SRC = _COH_SRC + ['paper_1710_08826_gb300/csrc/timeterms.cuh']
 # warp-instruction issue peak of a GB300: 152 SMs x 4 schedulers x 2.07 GHz (one warp
 # instruction per scheduler per cycle)
 ISSUE_PEAK = 152 * 4 * 2.07e9
@@ -56,6 +57,12 @@ NCU_RECORDS = {
                         "sources": _COH_SRC,
                         "sha256": "4fdd73a53f82ab80d472525c791363ef014ad99c4e86ef7718bc5d08feae1355",
                         "profile": "profiles/coh_ls_kernel_f32_c3_floating_5M.md"},
+    "td3_nll_grad_f32": {"bytes": 523_443_968, "events": 2_000_000, "sources": _TD3_SRC,
+                         "sha256": "1908901ab0df1da1e8073e47f19bed9ab0e719bffe016c71d80a877295b9df98",
+                         "profile": "profiles/td3_nll_kernel_td3_2M.md"},
+    "td3_nll_f64": {"bytes": 979_524_864, "events": 2_000_000, "fp64_pipe": 0.8610, "sources": _TD3_SRC,
+                    "sha256": "1908901ab0df1da1e8073e47f19bed9ab0e719bffe016c71d80a877295b9df98",
+                    "profile": "profiles/td3_nll_kernel_td3_2M.md"},
     "td4_nll_grad_f32": {"bytes": 171_436_544, "events": 2_000_000, "sources": _TD4_SRC,
                          "sha256": "131f99b2bb238619f17851b0d69b70314103761055bee7685c518161fd1923bb",
                          "profile": "profiles/td4_nll_f32_kernel_c4_2M.md"},
@@ -107,7 +114,7 @@ def parse():
     ap.add_argument("--toys", type=int, default=4096)
     ap.add_argument("--rate", type=float, default=1000.0, help="Poisson arrival rate of the second serving run")
     ap.add_argument("--profile", action="store_true", help="short fixed launch sequence for ncu captures")
-    ap.add_argument("--profile-workload", default="c2", choices=["c2", "c3", "c3f", "c4", "c5"])
+    ap.add_argument("--profile-workload", default="c2", choices=["c2", "c3", "c3f", "c4", "c5", "td3"])
     return ap.parse_args()
 
 
@@ -410,6 +417,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_extra:
         line["c3_dalitz"] = c3_measure(goo, ctx, stream, max(5, args.steps // 2))
         line["c4_td4"] = c4_measure(goo, ctx, stream, max(5, args.steps // 2))
+        line["td3_dalitz"] = td3_measure(goo, ctx, stream, max(5, args.steps // 2))
         line["c5_serving"] = c5_study(goo, ctx, n_toys=args.toys)
         line["c5_serving_poisson"] = c5_study(goo, ctx, n_toys=max(64, args.toys // 4), rate=args.rate, plain_sample=0)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -599,6 +607,76 @@ def c4_measure(goo, ctx, stream, steps, n_events=2_000_000, n_mc=3_000_000):
     return out
 
 
+def td3_inputs(n_events, n_mc, seed=1710016):
+    """Uniform three-body phase-space events (pi0 pi+ pi- masses) with decay times Exp(tau)
+    smeared by N(0, sigma_t); the per-event work does not depend on where the events fall."""
+    import numpy as np
+
+    import synth
+    spec = synth.td3_spec(n_mc=n_mc)
+    k = synth.TD3_MASSES
+    tau, sig = synth.TD4_TIME["tau"], synth.TD4_TIME["sigma_t"]
+    data = synth.dalitz_candidates(n_events, seed, k["M"], k["m1"], k["m2"], k["m3"])
+    rng = np.random.default_rng(seed + 1)
+    data["t"] = np.clip(rng.exponential(tau, n_events) + rng.normal(0.0, sig, n_events), *spec["observables"][2][1:])
+    mc = synth.dalitz_candidates(n_mc, 1710015, k["M"], k["m1"], k["m2"], k["m3"])
+    mc["t"] = np.zeros(n_mc)
+    return spec, synth.round_to_f32(data, spec), synth.round_to_f32(mc, spec)
+
+
+def td3_measure(goo, ctx, stream, steps, n_events=2_000_000, n_mc=1_000_000):
+    import numpy as np
+    import torch
+
+    import synth
+    spec, data, mc = td3_inputs(n_events, n_mc)
+    mcds = goo.Dataset.from_spec(ctx, spec, mc)
+    model = goo.Model(ctx, spec, mc=mcds)
+    ds = goo.Dataset.from_spec(ctx, spec, data)
+    theta = np.array(synth.param_values(spec))
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    out = {"workload": f"td3_dalitz: {n_events:,} pi0 pi+ pi- phase-space events (t = Exp(0.41 ps) + N(0, 0.05 ps)), "
+                       f"{n_mc:,}-point MC, 15 resonances + NR at the event and the exchanged point, 36 parameters "
+                       "(30 free coefficients, x, y, tau, sigma_t)"}
+    nll = {}
+    for prec, grad, k in (("f32", True, steps), ("f64", False, max(3, steps // 5))):
+        for _ in range(3):
+            model.nll_grad(ds, theta, prec) if grad else model.nll(ds, theta, prec)
+        torch.cuda.synchronize()
+        ms = 0.0
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            v = model.nll_grad(ds, theta, prec)[0] if grad else model.nll(ds, theta, prec)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        nll[prec] = v
+        ctx.kernel_times(reset=True)
+        ctx.timing(True)
+        for _ in range(3):
+            flush.zero_()
+            model.nll_grad(ds, theta, prec) if grad else model.nll(ds, theta, prec)
+        ctx.timing(False)
+        kt = ctx.kernel_times(reset=True)
+        name, (cnt, kms) = max(kt.items(), key=lambda kv: kv[1][1])
+        # two caches of 15 amplitudes (8 float4 / 15 double2 planes each) and the time column
+        bytes_per_event = 2 * 8 * 16 + 4 if prec == "f32" else 2 * 15 * 16 + 8
+        per = kms / cnt
+        out["f32_grad" if grad else "f64_plain"] = {
+            "evals_per_s": k / (ms * 1e-3), "events_per_s": n_events * k / (ms * 1e-3), "ms_per_eval": ms / k,
+            "kernel": name, "kernel_ms": per,
+            "hbm_frac": n_events * bytes_per_event / (per * 1e-3) / 1e9 / measured_peaks()[0],
+            "bound": "issue" if grad else "fp64", "ncu": ncu_record(name, n_events),
+            "what": ("goo_nll_grad, FP32 amplitude caches (2 x 128 B/event) + time, adjoint gradient" if grad
+                     else "goo_nll, FP64 amplitude caches (2 x 240 B/event) + time")}
+    out["parity_this_run"] = {"nll_f32": nll["f32"], "nll_f64": nll["f64"],
+                              "rel": abs(nll["f32"] - nll["f64"]) / abs(nll["f64"])}
+    return out
+
+
 # ---------------------------------------------------------------------------------------
 # served toy-MC study
 # ---------------------------------------------------------------------------------------
@@ -688,6 +766,8 @@ def run_profile(args):
         event pass each), then 1 FP64 evaluation.
     c4: amplitude caches and Gram (first call), then 4 FP32+grad and 1 FP64 time-dependent
         four-body evaluations on 2M events.
+    td3: amplitude caches and Gram matrices (first call), then 4 FP32+grad and 1 FP64
+        time-dependent three-body evaluations on 2M events.
     c5: a served study of 64 toys (generation passes, then rounds of batched evaluation and
         minimiser updates).
     """
@@ -699,8 +779,8 @@ def run_profile(args):
     from paper_1710_08826_gb300 import goo
     ctx = goo.Context(0)
     w = args.profile_workload
-    if w == "c4":
-        spec, data, mc = c4_inputs(2_000_000, 3_000_000)
+    if w in ("c4", "td3"):
+        spec, data, mc = c4_inputs(2_000_000, 3_000_000) if w == "c4" else td3_inputs(2_000_000, 1_000_000)
         mcds = goo.Dataset.from_spec(ctx, spec, mc)
         model = goo.Model(ctx, spec, mc=mcds)
         ds = goo.Dataset.from_spec(ctx, spec, data)
