@@ -157,9 +157,13 @@ class DalitzModel:
         return torch.stack(out, dim=1)
 
     def coefficients(self, th):
-        re = torch.stack([th[self.pidx[a[-2]]] for a in self.amps])
-        im = torch.stack([th[self.pidx[a[-1]]] for a in self.amps])
-        return torch.complex(re, im)
+        """c_k from the two parameters of amplitude k: (Re, Im), or with spec["coef"] ==
+        "polar" (magnitude r, phase phi): c = r (cos phi + i sin phi)."""
+        u = torch.stack([th[self.pidx[a[-2]]] for a in self.amps])
+        v = torch.stack([th[self.pidx[a[-1]]] for a in self.amps])
+        if self.spec.get("coef") == "polar":
+            return torch.complex(u * torch.cos(v), u * torch.sin(v))
+        return torch.complex(u, v)
 
     def intensity(self, A, th):
         S = A @ self.coefficients(th)

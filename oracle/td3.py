@@ -51,6 +51,7 @@ class TD3Model:
         self.re = [self.pidx[a[-2]] for a in amps]
         self.im = [self.pidx[a[-1]] for a in amps]
         self.tp = [self.pidx[n] for n in tpar]  # x, y, tau, sigma_t
+        self.polar = spec.get("coef") == "polar"
         self._dz = od.DalitzModel(dict(spec, pdf=("coherent", kin, amps)))
 
     def amplitudes(self, cols, theta):
@@ -64,8 +65,24 @@ class TD3Model:
         return a, ab
 
     def coefficients(self, theta):
+        """c_k: (Re, Im) parameters, or with spec["coef"] == "polar" (r, phi): r e^{i phi}."""
         th = np.asarray(theta, dtype=np.float64)
+        if self.polar:
+            return th[self.re] * np.exp(1j * th[self.im])
         return th[self.re] + 1j * th[self.im]
+
+    def _to_params(self, g, theta):
+        """Map a gradient over (Re c, Im c) to the coefficient parameters (chain rule; polar:
+        d/dr = cos(phi) d/dRe + sin(phi) d/dIm, d/dphi = -r sin(phi) d/dRe + r cos(phi) d/dIm)."""
+        if not self.polar:
+            return g
+        th = np.asarray(theta, dtype=np.float64)
+        r, ph = th[self.re], th[self.im]
+        gre, gim = g[..., self.re].copy(), g[..., self.im].copy()
+        out = g.copy()
+        out[..., self.re] = np.cos(ph) * gre + np.sin(ph) * gim
+        out[..., self.im] = -r * np.sin(ph) * gre + r * np.cos(ph) * gim
+        return out
 
     def grams(self, mc_cols, theta):
         a, ab = self.amplitudes(mc_cols, theta)
@@ -96,7 +113,7 @@ class TD3Model:
                         + dX[part].real * I[1] + dX[part].imag * I[3])
         for j, d in enumerate(res[1]):
             dN[self.tp[j]] += 0.5 * (PA + PB) * d[0] + 0.5 * (PA - PB) * d[2] + X.real * d[1] + X.imag * d[3]
-        return N, dN
+        return N, self._to_params(dN, th)
 
     def rate(self, amps, t, theta, derivs=False):
         a, ab = amps
@@ -118,7 +135,7 @@ class TD3Model:
         np.add.at(dR, (slice(None), self.im), -q.imag)
         for j, d in enumerate(res[1]):
             dR[:, self.tp[j]] += 0.5 * (AA + BB) * d[0] + 0.5 * (AA - BB) * d[2] + AB.real * d[1] + AB.imag * d[3]
-        return R, dR
+        return R, self._to_params(dR, th)
 
     def nll(self, cols, mc_cols, theta, amps=None, grams=None):
         amps = self.amplitudes(cols, theta) if amps is None else amps

@@ -10,7 +10,7 @@ caller passes that density in as a function.
 """
 from .specs import (c1_spec, c2_spec, c3_spec, c4_spec, td3_spec, dalitz_resonances, DALITZ_MASSES, TD4_MASSES,
                     TD3_MASSES, TD3_RESONANCES, TD3_TRUTH,
-                    TD4_AMPS, TD4_RESONANCES, TD4_TIME, param_names, param_values, observable_names)
+                    TD4_AMPS, TD4_RESONANCES, TD4_TIME, param_names, param_values, observable_names, to_polar)
 from .gen import (gen_c1, gen_c2, dalitz_box, dalitz_candidates, accept_reject, round_to_f32,
                   toy_sizes, gen_c4_candidates, four_body_phase_space, smear_times)
 
@@ -18,5 +18,5 @@ __all__ = [
     "c1_spec", "c2_spec", "c3_spec", "c4_spec", "td3_spec", "TD3_MASSES", "TD3_RESONANCES", "TD3_TRUTH", "dalitz_resonances", "DALITZ_MASSES",
     "param_names", "param_values", "observable_names", "gen_c1", "gen_c2", "dalitz_box",
     "dalitz_candidates", "accept_reject", "round_to_f32", "toy_sizes", "gen_c4_candidates",
-    "four_body_phase_space", "smear_times", "TD4_MASSES", "TD4_AMPS", "TD4_RESONANCES", "TD4_TIME",
+    "four_body_phase_space", "smear_times", "to_polar", "TD4_MASSES", "TD4_AMPS", "TD4_RESONANCES", "TD4_TIME",
 ]

@@ -213,6 +213,28 @@ def td3_spec(n_mc=1_000_000, mc_seed=1710015):
     )
 
 
+def to_polar(spec):
+    """The same amplitude model with each complex coefficient parameterised by its magnitude
+    and phase: parameters re_X / im_X become mag_X / phase_X (values |c|, arg c; steps scaled
+    alike), spec["coef"] = "polar"."""
+    vals = {p[0]: p for p in spec["params"]}
+    ren, params = {}, []
+    for p in spec["params"]:
+        if p[0].startswith("re_") and "im_" + p[0][3:] in vals:
+            q = vals["im_" + p[0][3:]]
+            c = complex(p[1], q[1])
+            r, ph = abs(c), math.atan2(c.imag, c.real)
+            ren[p[0]], ren[q[0]] = "mag_" + p[0][3:], "phase_" + p[0][3:]
+            params.append((ren[p[0]], r, p[2], p[3]))
+            params.append((ren[q[0]], ph, q[2], p[3] / max(r, 1e-3) if p[3] > 0 else 0.0))
+        elif not p[0].startswith("im_"):
+            params.append(p)
+    kind = spec["pdf"][0]
+    amps = [tuple(ren.get(x, x) if isinstance(x, str) else x for x in a) for a in spec["pdf"][2]]
+    pdf = (kind, spec["pdf"][1], amps) + tuple(spec["pdf"][3:])
+    return dict(spec, params=params, pdf=pdf, coef="polar")
+
+
 def param_names(spec):
     return [p[0] for p in spec["params"]]
 

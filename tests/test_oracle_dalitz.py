@@ -196,3 +196,29 @@ def test_lineshape_gradient_by_finite_differences():
         e[i] = h
         fd = (8 * (f(th + e) - f(th - e)) - (f(th + 2 * e) - f(th - 2 * e))) / (12 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(abs(g[i]), 1.0), (n, fd, g[i])
+
+
+def test_polar_coefficients():
+    # magnitude/phase parameters: the same NLL as the Cartesian point c = r e^{i phi}, and the
+    # autograd gradient against central differences in (r, phi)
+    spec, m, mc, data = _small_c3()
+    ps = synth.to_polar(spec)
+    mp = od.DalitzModel(ps)
+    th = np.array(synth.param_values(spec))
+    tp = np.array(synth.param_values(ps))
+    assert mp.nll(data, mc, tp) == pytest.approx(m.nll(data, mc, th), rel=1e-13)
+    tp2 = tp.copy()
+    names = synth.param_names(ps)
+    for i, n in enumerate(names):
+        if n.startswith("phase_") and not n.endswith("NR"):
+            tp2[i] += 0.3
+    _, g = mp.nll_grad(data, mc, tp2)
+    f = lambda t: mp.nll(data, mc, t)
+    for i, n in enumerate(names):
+        if not n.startswith(("mag_", "phase_")):
+            continue
+        h = 1e-6
+        e = np.zeros_like(tp2)
+        e[i] = h
+        fd = (f(tp2 + e) - f(tp2 - e)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-5 * max(abs(g[i]), 1.0), (n, fd, g[i])

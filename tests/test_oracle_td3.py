@@ -110,3 +110,28 @@ def test_generated_times_have_the_lifetime(small):
     t = data["t"]
     tau = theta[m.tp[2]]
     assert abs(t.mean() - tau) < 4 * t.std() / math.sqrt(t.size)
+
+
+def test_polar_coefficients(small):
+    spec, theta, m, mc, data = small
+    ps = synth.to_polar(spec)
+    mp = td3.TD3Model(ps)
+    tp = np.array(synth.param_values(ps))
+    grams, amps = m.grams(mc, theta), m.amplitudes(data, theta)
+    assert mp.nll(data, mc, tp, amps=amps, grams=grams) == pytest.approx(
+        m.nll(data, mc, theta, amps=amps, grams=grams), rel=1e-13)
+    names = synth.param_names(ps)
+    tp2 = tp.copy()
+    for i, n in enumerate(names):
+        if n.startswith("phase_") and i not in (names.index("phase_rho770_p"),):
+            tp2[i] += 0.2
+    _, g = mp.nll_grad(data, mc, tp2, amps=amps, grams=grams)
+    f = lambda t: mp.nll(data, mc, t, amps=amps, grams=grams)
+    for i, n in enumerate(names):
+        if not n.startswith(("mag_", "phase_")):
+            continue
+        h = 1e-4 * max(abs(tp2[i]), 0.1)   # fourth-order stencil: truncation ~h^4
+        e = np.zeros_like(tp2)
+        e[i] = h
+        fd = (8 * (f(tp2 + e) - f(tp2 - e)) - (f(tp2 + 2 * e) - f(tp2 - 2 * e))) / (12 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(abs(g[i]), 1.0), (n, fd, g[i])
