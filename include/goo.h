@@ -240,6 +240,14 @@ int goo_amplitude_cache(goo_model* model, const goo_dataset* ds, const double* t
  * GOO_ERR_UNSUPPORTED for other models, GOO_ERR_ARG for another mode. */
 enum { GOO_LINESHAPE_CACHED = 0, GOO_LINESHAPE_FLOATING = 1 };
 int goo_model_set_lineshapes(goo_model* model, int mode);
+/* Coefficient form of a GOO_OP_COHERENT or GOO_OP_TD3 model's amplitudes (the paper's
+ * amplitude PDFs take complex coefficients; the polar form is the usual alternative).  With
+ * GOO_COEF_POLAR the two coefficient parameters of an amplitude (par[2], par[3]) are its
+ * magnitude r and phase phi (radians): c = r e^{i phi}; goo_nll_grad then returns d/dr and
+ * d/dphi.  GOO_COEF_CARTESIAN (default): (Re c, Im c).  The toy server takes Cartesian models
+ * only.  GOO_ERR_UNSUPPORTED for other models, GOO_ERR_ARG for another form. */
+enum { GOO_COEF_CARTESIAN = 0, GOO_COEF_POLAR = 1 };
+int goo_model_set_coefficients(goo_model* model, int form);
 
 /* ---- fitting (paper: the FitManager, Fig. 1; Minuit 2 as the default minimiser, Sec. 4) -------
  * Minimises the NLL of `model` on `ds` over the parameters with free_mask[p] != 0, starting

@@ -266,6 +266,12 @@ int goo_model_set_lineshapes(goo_model* m, int mode) {
   return dalitz_set_lineshapes(m, mode);
 }
 
+int goo_model_set_coefficients(goo_model* m, int form) {
+  if (!m) return set_error(GOO_ERR_ARG, "goo_model_set_coefficients: NULL model");
+  if (m->kind != 1) return set_error(GOO_ERR_UNSUPPORTED, "goo_model_set_coefficients: not a three-body amplitude model");
+  return dalitz_set_coefficients(m, form);
+}
+
 int goo_amplitude_cache(goo_model* m, const goo_dataset* ds, const double* theta, int precision, const void** dev_ptr,
                         int* n_amp) {
   if (!m || !ds || !dev_ptr || !n_amp) return set_error(GOO_ERR_ARG, "goo_amplitude_cache: NULL argument");

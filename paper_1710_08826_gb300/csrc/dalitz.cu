@@ -60,6 +60,7 @@ struct DalitzModel {
   const goo_dataset* mc = nullptr;
   bool floating = false;           // GOO_LINESHAPE_FLOATING: no cache, lineshape gradients
   double* ls_mc = nullptr;         // MC-pass lane sums of the floating-lineshape path (device)
+  bool polar = false;              // GOO_COEF_POLAR: the coefficient parameters are (r, phi)
   // time-dependent three-body model (GOO_OP_TD3)
   bool td = false;
   int col_t = 2;
@@ -120,7 +121,19 @@ struct CohArgs {
   int par_re[kMaxAmp], par_im[kMaxAmp];
   int n_params;
   int64_t n_total;             // events of the dataset (cache plane length)
+  int polar;                   // the coefficient parameters are (r, phi): c = r e^{i phi}
+  double jc[kMaxAmp], js[kMaxAmp], jr[kMaxAmp];  // cos phi, sin phi, r per amplitude (polar)
 };
+
+// A gradient over (Re c, Im c) of amplitude k mapped to its parameters (FP64): unchanged, or
+// for polar coefficients d/dr = cos(phi) d/dRe + sin(phi) d/dIm and
+// d/dphi = r (-sin(phi) d/dRe + cos(phi) d/dIm).
+__device__ __forceinline__ void coef_chain(int polar, double c, double s, double r, double& gre, double& gim) {
+  if (!polar) return;
+  const double u = c * gre + s * gim, v = r * (c * gim - s * gre);
+  gre = u;
+  gim = v;
+}
 
 template <typename T, int KB, bool GRAD>
 struct CohLanes {
@@ -241,8 +254,10 @@ __device__ __forceinline__ void coh_finish(const CohArgs<T>& a, CohAcc<T, KB>& a
     if (GRAD)
       for (int k = 0; k < K; ++k) {
         const int slot = (k < a.nbw) ? k : KB;  // NR lives in the last slot
-        if (s_pre[k] == p) g += -2.0 * s_out[1 + 2 * slot] + nev * s_vr[k];
-        if (s_pim[k] == p) g += 2.0 * s_out[2 + 2 * slot] - nev * s_vi[k];
+        double gre = -2.0 * s_out[1 + 2 * slot] + nev * s_vr[k], gim = 2.0 * s_out[2 + 2 * slot] - nev * s_vi[k];
+        coef_chain(a.polar, a.jc[k], a.js[k], a.jr[k], gre, gim);
+        if (s_pre[k] == p) g += gre;
+        if (s_pim[k] == p) g += gim;
       }
     result[off + p] = g;
   }
@@ -475,6 +490,30 @@ static void pair_masses(const DalitzModel& d, int pair, double& mA, double& mB, 
   }
 }
 
+// Coefficient k of the amplitude sum from its two parameters: (Re, Im), or (r, phi) with
+// GOO_COEF_POLAR.
+static void coef(const DalitzModel& d, const double* theta, int k, double& re, double& im) {
+  const double u = theta[d.par_re[k]], v = theta[d.par_im[k]];
+  if (d.polar) {
+    re = u * std::cos(v);
+    im = u * std::sin(v);
+  } else {
+    re = u;
+    im = v;
+  }
+}
+
+// The polar Jacobian entries (cos phi, sin phi, r) of every amplitude into kernel arguments.
+template <typename A>
+static void fill_jacobian(const DalitzModel& d, const double* theta, A& a) {
+  a.polar = d.polar ? 1 : 0;
+  for (int k = 0; k < d.K; ++k) {
+    a.jc[k] = d.polar ? std::cos(theta[d.par_im[k]]) : 1.0;
+    a.js[k] = d.polar ? std::sin(theta[d.par_im[k]]) : 0.0;
+    a.jr[k] = d.polar ? theta[d.par_re[k]] : 1.0;
+  }
+}
+
 static uint64_t lineshape_key(const DalitzModel& d, const double* theta) {
   uint64_t h = 1469598103934665603ull;
   for (int k = 0; k < d.nbw; ++k) {
@@ -635,8 +674,11 @@ __global__ void __launch_bounds__(kBlock)
     if (GRAD) {
       for (int kk = 0; kk < a.K; ++kk) {
         const int sl = kk < a.nbw ? kk : KB;  // the NR lives in the last slot
-        if (a.par_re[kk] == p) g += -2.0 * s_out[1 + 2 * sl] + 2.0 * nev * mc_sums[1 + 2 * sl] / Smc;
-        if (a.par_im[kk] == p) g += 2.0 * s_out[2 + 2 * sl] - 2.0 * nev * mc_sums[2 + 2 * sl] / Smc;
+        double gre = -2.0 * s_out[1 + 2 * sl] + 2.0 * nev * mc_sums[1 + 2 * sl] / Smc;
+        double gim = 2.0 * s_out[2 + 2 * sl] - 2.0 * nev * mc_sums[2 + 2 * sl] / Smc;
+        coef_chain(a.polar, a.jc[kk], a.js[kk], a.jr[kk], gre, gim);
+        if (a.par_re[kk] == p) g += gre;
+        if (a.par_im[kk] == p) g += gim;
       }
       for (int k = 0; k < a.nbw; ++k) {
         const int o = 1 + 2 * KA + 2 * k;
@@ -740,6 +782,8 @@ struct Td3Args {
   int wN, nbw, K, n_params;
   int par_re[kMaxAmp], par_im[kMaxAmp], par_t[4];  // parameter of each amplitude (tree order)
   int64_t n_total;                   // events of the dataset (cache plane length)
+  int polar;                         // the coefficient parameters are (r, phi)
+  double jc[kMaxAmp], js[kMaxAmp], jr[kMaxAmp];  // cos phi, sin phi, r per amplitude (polar)
 };
 
 template <bool GRAD>
@@ -939,8 +983,10 @@ __global__ void __launch_bounds__(kBlock)
     if (GRAD) {
       for (int kk = 0; kk < K; ++kk) {
         const int sl = s_slot[kk];
-        if (s_pre[kk] == p) g += -s_out[1 + 2 * sl] + nev * s_nre[kk];
-        if (s_pim[kk] == p) g += -s_out[2 + 2 * sl] + nev * s_nim[kk];
+        double gre = -s_out[1 + 2 * sl] + nev * s_nre[kk], gim = -s_out[2 + 2 * sl] + nev * s_nim[kk];
+        coef_chain(a.polar, a.jc[kk], a.js[kk], a.jr[kk], gre, gim);
+        if (s_pre[kk] == p) g += gre;
+        if (s_pim[kk] == p) g += gim;
       }
       const int o = 1 + 2 * KA;
       for (int j = 0; j < 4; ++j)
@@ -1127,11 +1173,14 @@ static void fill_args(const DalitzModel& d, const double* theta, int n_params, i
   a.n_params = n_params;
   a.n_total = n_total;
   for (int k = 0; k < d.K; ++k) {
-    a.cr[k] = (T)theta[d.par_re[k]];
-    a.ci[k] = (T)theta[d.par_im[k]];
+    double re, im;
+    coef(d, theta, k, re, im);
+    a.cr[k] = (T)re;
+    a.ci[k] = (T)im;
     a.par_re[k] = d.par_re[k];
     a.par_im[k] = d.par_im[k];
   }
+  fill_jacobian(d, theta, a);
 }
 
 constexpr int kMaxDevicesCoh = 64;
@@ -1220,8 +1269,10 @@ template <typename T>
 static void fill_ls(const DalitzModel& d, const double* theta, LsConst<T>& c) {
   std::memset(&c, 0, sizeof c);
   for (int k = 0; k < d.nbw; ++k) {
-    c.cr[k] = (T)theta[d.par_re[k]];
-    c.ci[k] = (T)theta[d.par_im[k]];
+    double re, im;
+    coef(d, theta, k, re, im);
+    c.cr[k] = (T)re;
+    c.ci[k] = (T)im;
     c.par_m0[k] = d.par_m0[k];
     c.par_w[k] = d.par_w[k];
     double mA, mB, mC;
@@ -1270,8 +1321,10 @@ static int launch_ls(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t
   LsConst<T> c;
   fill_ls<T>(d, theta, c);
   if (d.has_nr) {
-    c.cr[KB] = (T)theta[d.par_re[d.nbw]];
-    c.ci[KB] = (T)theta[d.par_im[d.nbw]];
+    double re, im;
+    coef(d, theta, d.nbw, re, im);
+    c.cr[KB] = (T)re;
+    c.ci[KB] = (T)im;
   }
   const T* c12 = sizeof(T) == 4 ? (const T*)ds->d32[d.col12] : (const T*)ds->d64[d.col12];
   const T* c13 = sizeof(T) == 4 ? (const T*)ds->d32[d.col13] : (const T*)ds->d64[d.col13];
@@ -1339,8 +1392,10 @@ static void fill_td3(const DalitzModel& d, const double* theta, int n_params, in
   std::memset(&a, 0, sizeof a);
   for (int k = 0; k < d.K; ++k) {
     const int sl = k < d.nbw ? k : kTd3KB;
-    a.cr[sl] = (T)theta[d.par_re[k]];
-    a.ci[sl] = (T)theta[d.par_im[k]];
+    double re, im;
+    coef(d, theta, k, re, im);
+    a.cr[sl] = (T)re;
+    a.ci[sl] = (T)im;
     a.par_re[k] = d.par_re[k];
     a.par_im[k] = d.par_im[k];
   }
@@ -1357,6 +1412,7 @@ static void fill_td3(const DalitzModel& d, const double* theta, int n_params, in
   a.K = d.K;
   a.n_params = n_params;
   a.n_total = n_total;
+  fill_jacobian(d, theta, a);
 }
 
 template <typename T, bool GRAD>
@@ -1394,8 +1450,7 @@ static int launch_td3(goo_model* m, const goo_dataset* ds, int64_t begin, int64_
 static double td3_norm_host(const DalitzModel& d, const double* G, const double* theta, bool f32) {
   const int K = d.K;
   auto cf = [&](int k, double& r, double& i) {
-    r = theta[d.par_re[k]];
-    i = theta[d.par_im[k]];
+    coef(d, theta, k, r, i);
     if (f32) {
       r = (double)(float)r;
       i = (double)(float)i;
@@ -1541,8 +1596,9 @@ static double quad_form(const DalitzModel& d, const double* G, const double* the
   double N = 0.0;
   for (int k = 0; k < d.K; ++k)
     for (int l = 0; l < d.K; ++l) {
-      double ckr = theta[d.par_re[k]], cki = theta[d.par_im[k]];
-      double clr = theta[d.par_re[l]], cli = theta[d.par_im[l]];
+      double ckr, cki, clr, cli;
+      coef(d, theta, k, ckr, cki);
+      coef(d, theta, l, clr, cli);
       if (f32) {
         ckr = (double)(float)ckr;
         cki = (double)(float)cki;
@@ -1695,6 +1751,7 @@ int dalitz_amplitudes(goo_model* m, const goo_dataset* ds, const double* theta, 
 int dalitz_server_info(goo_model* m, const double* theta, AmpModelInfo* info) {
   if (m->kind != 1) return set_error(GOO_ERR_STATE, "toy server needs an amplitude model");
   if (m->dalitz->td) return set_error(GOO_ERR_UNSUPPORTED, "toy server of the time-dependent three-body model");
+  if (m->dalitz->polar) return set_error(GOO_ERR_UNSUPPORTED, "toy server with polar coefficients");
   GOO_TRY(dalitz_constants(m, theta));
   GOO_TRY(ensure_gram(m, GOO_F32));
   const DalitzModel& d = *m->dalitz;
@@ -1738,5 +1795,12 @@ bool dalitz_lineshape_param(const goo_model* m, int p) {
 }
 
 bool dalitz_floating(const goo_model* m) { return m->dalitz->floating; }
+
+int dalitz_set_coefficients(goo_model* m, int form) {
+  if (form != GOO_COEF_CARTESIAN && form != GOO_COEF_POLAR)
+    return set_error(GOO_ERR_ARG, "goo_model_set_coefficients: form %d", form);
+  m->dalitz->polar = form == GOO_COEF_POLAR;
+  return GOO_OK;
+}
 bool dalitz_time_dependent(const goo_model* m) { return m->dalitz->td; }
 }  // namespace goo

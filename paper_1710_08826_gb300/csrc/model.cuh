@@ -84,6 +84,7 @@ int dalitz_set_lineshapes(goo_model* m, int mode);
 bool dalitz_lineshape_param(const goo_model* m, int p);  // p is a resonance mass or width
 bool dalitz_floating(const goo_model* m);
 bool dalitz_time_dependent(const goo_model* m);
+int dalitz_set_coefficients(goo_model* m, int form);
 
 int build_td4_model(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_params, int n_obs, goo_model* m);
 int td4_set_norm(goo_model* m, const goo_norm_spec* spec);

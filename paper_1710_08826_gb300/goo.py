@@ -17,6 +17,7 @@ GOO_OK, GOO_ERR_ARG, GOO_ERR_RANGE, GOO_ERR_CUDA, GOO_ERR_OOM = 0, -1, -2, -3, -
 GOO_ERR_NONPOSITIVE_PDF, GOO_ERR_TIMEOUT, GOO_ERR_STATE, GOO_ERR_UNSUPPORTED = -5, -6, -7, -8
 GOO_F64, GOO_F32 = 0, 1
 GOO_LINESHAPE_CACHED, GOO_LINESHAPE_FLOATING = 0, 1
+GOO_COEF_CARTESIAN, GOO_COEF_POLAR = 0, 1
 GOO_COPY, GOO_BORROW_DEVICE = 0, 1
 OP = dict(gauss=1, expo=2, poly2=3, argus=4, prod=10, add=11, bw=20, nr=21, coherent=22, td4=23, amp4=24, td3=25)
 ANG = dict(SS=0, VS0=1, SV0=2, VV0=3, VVpar=4, VVperp=5, TS0=6, TV0=7)
@@ -125,6 +126,7 @@ def _load():
                                                ctypes.POINTER(ctypes.c_int)]),
         "goo_faddeeva": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]),
         "goo_model_set_lineshapes": (ctypes.c_int, [vp, ctypes.c_int]),
+        "goo_model_set_coefficients": (ctypes.c_int, [vp, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -381,6 +383,8 @@ class Model:
         self.handle = h
         self.mc = mc
         self.set_norm(norm or spec["norm"], mc)
+        if spec.get("coef") == "polar":   # (magnitude, phase) coefficient parameters
+            _check(lib.goo_model_set_coefficients(self.handle, GOO_COEF_POLAR))
 
     def set_norm(self, norm, mc=None):
         ns = GooNormSpec()
