@@ -142,16 +142,25 @@ class TreeModel:
         cache = {}
         return self.shape(self.tree, X, th, cache) / self.norm(self.tree, th, cache)
 
-    def nll(self, cols, theta):
+    def nll(self, cols, theta, weights=None):
+        """-sum_i w_i log f(x_i): unweighted events, or a binned dataset given as bin centres
+        with their counts as weights (the multinomial likelihood of the bin contents with f
+        at the bin centres; the bin volume is a theta-independent constant and is dropped)."""
         with torch.no_grad():
-            return float(-torch.log(self.density(cols, theta)).sum())
+            lf = torch.log(self.density(cols, theta))
+            if weights is not None:
+                lf = lf * torch.as_tensor(weights, dtype=torch.float64)
+            return float(-lf.sum())
 
-    def nll_grad(self, cols, theta):
+    def nll_grad(self, cols, theta, weights=None):
         th = torch.tensor([float(t) for t in theta], dtype=torch.float64, requires_grad=True)
         X = {k: torch.as_tensor(v, dtype=torch.float64) for k, v in cols.items()}
         cache = {}
         f = self.shape(self.tree, X, th, cache) / self.norm(self.tree, th, cache)
-        nll = -torch.log(f).sum()
+        lf = torch.log(f)
+        if weights is not None:
+            lf = lf * torch.as_tensor(weights, dtype=torch.float64)
+        nll = -lf.sum()
         (g,) = torch.autograd.grad(nll, th)
         return float(nll.detach()), g.numpy().copy()
 

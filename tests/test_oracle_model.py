@@ -198,3 +198,36 @@ def test_sampler_matches_density_chi2():
     expect = cell / cell.sum() * counts.sum()
     chi2 = float(((counts - expect) ** 2 / expect).sum())
     assert chi2 < 30 + 5 * math.sqrt(60)
+
+
+def test_weighted_nll_equals_repeated_events():
+    # a dataset with integer weights is the dataset with each event repeated w times
+    spec = synth.c2_spec(bins=16)
+    m = om.TreeModel(spec)
+    cols = synth.gen_c2(n=500, seed=31)
+    w = np.random.default_rng(5).integers(0, 4, 500).astype(np.float64)
+    rep = {k: np.repeat(v, w.astype(int)) for k, v in cols.items()}
+    th = np.array(synth.param_values(spec)) * 1.01
+    n1, g1 = m.nll_grad(cols, th, weights=w)
+    n2, g2 = m.nll_grad(rep, th)
+    assert n1 == pytest.approx(n2, rel=1e-12)
+    np.testing.assert_allclose(g1, g2, rtol=1e-10, atol=1e-9)
+
+
+def test_binned_nll_is_the_multinomial_likelihood_of_the_bin_contents():
+    # bin centres weighted by their counts: sum_b n_b log(f(x_b) h) is the log of the
+    # multinomial probability of the contents with p_b = f(x_b) h, up to a theta-free term
+    spec = synth.c1_spec()
+    m = om.TreeModel(spec)
+    x = synth.gen_c1(n=5000, seed=9)["x"]
+    counts, edges = np.histogram(x, bins=50, range=(0.0, 10.0))
+    centres = 0.5 * (edges[:-1] + edges[1:])
+    h = edges[1] - edges[0]
+    th = np.array(synth.param_values(spec))
+    nll = m.nll({"x": centres}, th, weights=counts.astype(float))
+    p = m.density({"x": centres}, th).numpy() * h
+    logmult = scipy.stats.multinomial.logpmf(counts, n=counts.sum(), p=p / p.sum())
+    const = math.lgamma(counts.sum() + 1) - np.sum([math.lgamma(c + 1) for c in counts])
+    # logpmf normalises p to sum 1; the midpoint probabilities sum to 1 within O(h^2)
+    assert -nll + counts.sum() * math.log(h) - counts.sum() * math.log(p.sum()) + const == pytest.approx(
+        logmult, rel=1e-12)
