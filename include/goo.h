@@ -182,6 +182,16 @@ int goo_dataset_free(goo_dataset* ds);
 int64_t goo_dataset_size(const goo_dataset* ds);
 /* Device pointer of column `col` in the given precision (for zero-copy consumers). */
 const void* goo_dataset_column(const goo_dataset* ds, int col, int dtype);
+/* Per-event weights w[0..n_events) (paper: binned data sets, Fig. 1 and Sec. 4).  A binned
+ * dataset is uploaded as one event per bin (its centre) and weighted by the bin's count;
+ * the NLL of a sum-of-product model is then -sum_i w_i log f(x_i) (the multinomial
+ * likelihood of the bin contents with f at the bin centres, up to a theta-independent
+ * constant) and its gradient is weighted the same way; events of weight 0 (empty bins) are
+ * skipped.  Weights must be finite and >= 0 (else GOO_ERR_ARG, nothing changed).  The host
+ * array is copied (the caller keeps it); w = NULL removes the weights.  Amplitude models and
+ * goo_nll_grad_batch refuse a weighted dataset with GOO_ERR_UNSUPPORTED; goo_eval_logf
+ * ignores the weights; goo_nll_partial's third record entry stays the event count. */
+int goo_dataset_set_weights(goo_dataset* ds, const double* w);
 
 /* ---- model (paper: PDFs and combination PDFs, Fig. 1 and Sec. 1) -----------------------------
  * Build a model from `n_nodes` post-order nodes over `n_params` parameters and `n_obs`

@@ -18,6 +18,8 @@ int check_model_dataset(const goo_model* m, const goo_dataset* ds, int precision
   if (!m || !ds) return set_error(GOO_ERR_ARG, "NULL model or dataset");
   if (ds->ctx != m->ctx) return set_error(GOO_ERR_ARG, "model and dataset belong to different contexts");
   if (precision != GOO_F64 && precision != GOO_F32) return set_error(GOO_ERR_ARG, "precision=%d", precision);
+  if (ds->w64 && m->kind != 0)
+    return set_error(GOO_ERR_UNSUPPORTED, "per-event weights are supported by sum-of-product models only");
   if (ds->ncols < m->n_obs)
     return set_error(GOO_ERR_ARG, "dataset has %d columns, model uses %d observables", ds->ncols, m->n_obs);
   for (int o = 0; o < m->n_obs; ++o)
@@ -56,7 +58,7 @@ int nll_common(goo_model* m, const goo_dataset* ds, const double* theta, int pre
   } else if (m->kind == 2) {
     GOO_TRY(td4_nll(m, ds, 0, ds->n, theta, precision, grad, res, 0));
   } else {
-    const bool fuse = ds->n > 0 && sop_norm_in_event(m, precision, grad);
+    const bool fuse = ds->n > 0 && !ds->w64 && sop_norm_in_event(m, precision, grad);
     GOO_TRY(sop_prepare(m, theta, precision, fuse));
     GOO_TRY(sop_events(m, ds, 0, ds->n, precision, grad, 0, fuse));
     if (ds->n == 0) {
@@ -222,7 +224,7 @@ int goo_nll_partial(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t 
   } else if (m->kind == 1) {
     GOO_TRY(dalitz_nll(m, ds, begin, end, theta, precision, want_grad != 0, res, 1));
   } else {
-    const bool fuse = end > begin && sop_norm_in_event(m, precision, want_grad != 0);
+    const bool fuse = end > begin && !ds->w64 && sop_norm_in_event(m, precision, want_grad != 0);
     GOO_TRY(sop_prepare(m, theta, precision, fuse));
     if (end > begin) {
       GOO_TRY(sop_events(m, ds, begin, end, precision, want_grad != 0, 1, fuse));

@@ -115,6 +115,9 @@ struct goo_dataset {
   double* d64[goo::kMaxCols] = {};
   float* d32[goo::kMaxCols] = {};
   bool owns64 = true, owns32 = true;
+  // per-event weights (null: every event weighs 1), set by goo_dataset_set_weights
+  double* w64 = nullptr;
+  float* w32 = nullptr;
   double lo[goo::kMaxCols] = {};
   double hi[goo::kMaxCols] = {};
   // amplitude caches attached to this dataset, [0]: float32, [1]: float64, [2], [3]: the

@@ -7,7 +7,9 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -156,6 +158,10 @@ static void free_dataset_memory(goo_dataset* ds) {
     ds->d64[c] = nullptr;
     ds->d32[c] = nullptr;
   }
+  if (ds->w64) cudaFree(ds->w64);
+  if (ds->w32) cudaFree(ds->w32);
+  ds->w64 = nullptr;
+  ds->w32 = nullptr;
   for (auto& c : ds->cache) {
     if (c.ptr) cudaFree(c.ptr);
     c.ptr = nullptr;
@@ -354,6 +360,47 @@ int goo_dataset_free(goo_dataset* ds) {
 }
 
 int64_t goo_dataset_size(const goo_dataset* ds) { return ds ? ds->n : -1; }
+
+// Per-event weights: checked on the host, then copied to the device in both precisions
+// (the float32 copy rounded to nearest).  Replacing or removing them waits for the stream,
+// since a launch in flight may read the old arrays.
+int goo_dataset_set_weights(goo_dataset* ds, const double* w) {
+  if (!ds) return set_error(GOO_ERR_ARG, "goo_dataset_set_weights: NULL dataset");
+  const int64_t n = ds->n;
+  std::vector<float> w32;
+  if (w) {
+    w32.resize((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+      if (!std::isfinite(w[i]) || w[i] < 0.0)
+        return set_error(GOO_ERR_ARG, "goo_dataset_set_weights: weight %lld is %g (finite and >= 0 required)",
+                         (long long)i, w[i]);
+      w32[(size_t)i] = (float)w[i];
+    }
+  }
+  GOO_CUDA_TRY(cudaSetDevice(ds->ctx->device));
+  GOO_CUDA_TRY(cudaStreamSynchronize(ds->ctx->stream));
+  if (ds->w64) cudaFree(ds->w64);
+  if (ds->w32) cudaFree(ds->w32);
+  ds->w64 = nullptr;
+  ds->w32 = nullptr;
+  if (!w) return GOO_OK;
+  const size_t bytes = (size_t)std::max<int64_t>(n, 1);
+  double* d64 = nullptr;
+  float* d32 = nullptr;
+  if (cudaMalloc(&d64, bytes * sizeof(double)) != cudaSuccess || cudaMalloc(&d32, bytes * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    if (d64) cudaFree(d64);
+    return set_error(GOO_ERR_OOM, "goo_dataset_set_weights: device allocation of %lld weights failed", (long long)n);
+  }
+  if (n > 0) {
+    GOO_CUDA_TRY(cudaMemcpyAsync(d64, w, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, ds->ctx->stream));
+    GOO_CUDA_TRY(cudaMemcpyAsync(d32, w32.data(), (size_t)n * sizeof(float), cudaMemcpyHostToDevice, ds->ctx->stream));
+    GOO_CUDA_TRY(cudaStreamSynchronize(ds->ctx->stream));
+  }
+  ds->w64 = d64;
+  ds->w32 = d32;
+  return GOO_OK;
+}
 
 const void* goo_dataset_column(const goo_dataset* ds, int col, int dtype) {
   if (!ds || col < 0 || col >= ds->ncols) return nullptr;

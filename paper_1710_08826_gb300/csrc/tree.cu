@@ -606,10 +606,14 @@ struct EventOcc {
   static constexpr int value = (sizeof(T) == 4 && K * L <= 6) ? 3 : 2;
 };
 
+// wcol (nullable): per-event weights w_i (a binned dataset: bin centres with their counts);
+// the lanes then sum w_i log f_i and w_i times the gradient terms, and events of weight 0 are
+// skipped.
 template <typename T, int K, int L, bool GRAD>
 __global__ void __launch_bounds__(kBlock, EventOcc<T, K, L>::value) sop_event_kernel(const ModelDev* __restrict__ md, const EvConst<T, K, L> P,
                                                               Cols<T> cols, int64_t begin, int64_t end, float2* partials,
-                                                              unsigned* counters, double* result, int out_mode) {
+                                                              unsigned* counters, double* result, int out_mode,
+                                                              const T* __restrict__ wcol) {
   constexpr int NS = EventLanes<T, K, L, GRAD>::NS;
   __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
   __shared__ unsigned s_bad[kBlock / 32];
@@ -638,24 +642,32 @@ __global__ void __launch_bounds__(kBlock, EventOcc<T, K, L>::value) sop_event_ke
   // software pipelining: the next event's columns are requested before this event is
   // evaluated, so the loads' latency overlaps the arithmetic
   int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  T n0 = T(0), n1 = T(0), n2 = T(0), n3 = T(0);
+  T n0 = T(0), n1 = T(0), n2 = T(0), n3 = T(0), nw = T(1);
   if (i < end) {
     n0 = cols.c[0][i];
     n1 = nobs > 1 ? cols.c[1][i] : T(0);
     n2 = nobs > 2 ? cols.c[2][i] : T(0);
     n3 = nobs > 3 ? cols.c[3][i] : T(0);
+    if (wcol) nw = wcol[i];
   }
   for (; i < end; i += stride) {
-    const T x0 = n0, x1 = n1, x2 = n2, x3 = n3;
+    const T x0 = n0, x1 = n1, x2 = n2, x3 = n3, wi = nw;
     const int64_t inext = i + stride;
     if (inext < end) {
       n0 = cols.c[0][inext];
       n1 = nobs > 1 ? cols.c[1][inext] : T(0);
       n2 = nobs > 2 ? cols.c[2][inext] : T(0);
       n3 = nobs > 3 ? cols.c[3][inext] : T(0);
+      if (wcol) nw = wcol[inext];
     }
+    if (wcol && wi == T(0)) continue;  // an empty bin
     T logf, ck[K], dk[K][L][3];
     if (eval_event<T, K, L, GRAD>(P, off_hi, off_lo, x0, x1, x2, x3, logf, ck, dk)) {
+      if (wcol) {
+        logf *= wi;
+#pragma unroll
+        for (int k = 0; k < K; ++k) ck[k] *= wi;
+      }
       if constexpr (sizeof(T) == 4) {
         acc32.add(logf);
       } else {
@@ -1779,6 +1791,7 @@ static EvConst<T, K, L> make_evconst(const ModelDev& h) {
 
 template <typename T, int K, int L, bool GRAD>
 static int launch_event_T(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int out_mode) {
+  const T* wcol = sizeof(T) == 4 ? (const T*)(const void*)ds->w32 : (const T*)(const void*)ds->w64;
   goo_ctx* ctx = m->ctx;
   static int occ = 0;
   const int bps = blocks_per_sm(sop_event_kernel<T, K, L, GRAD>, &occ);
@@ -1794,7 +1807,8 @@ static int launch_event_T(goo_model* m, const goo_dataset* ds, int64_t begin, in
     LaunchScope ls(ctx, sizeof(T) == 4 ? (GRAD ? "sop_nll_grad_f32" : "sop_nll_f32") : (GRAD ? "sop_nll_grad_f64" : "sop_nll_f64"));
     sop_event_kernel<T, K, L, GRAD><<<nb, kBlock, 0, ctx->stream>>>(m->dev, make_evconst<T, K, L>(*m->stage), cols,
                                                                    begin, end, ctx->scratch.partials,
-                                                                   ctx->scratch.counters, ctx->scratch.result, out_mode);
+                                                                   ctx->scratch.counters, ctx->scratch.result, out_mode,
+                                                                   wcol);
   }
   GOO_CUDA_TRY(cudaGetLastError());
   return GOO_OK;
@@ -1891,9 +1905,12 @@ static int launch_event_sel(goo_model* m, const goo_dataset* ds, int64_t begin, 
                             bool fused_norm) {
   if constexpr (sizeof(T) == 4) {
     // packed pairs, except the largest shape with gradient lanes (its pair accumulators do
-    // not fit in registers)
-    if (m->host.nK <= 2 && m->max_leaf <= 3) return launch_event2<2, 3, GRAD>(m, ds, begin, end, out_mode, fused_norm);
-    if constexpr (!GRAD) return launch_event2<4, 4, GRAD>(m, ds, begin, end, out_mode, fused_norm);
+    // not fit in registers) and weighted datasets (the scalar kernel carries the weights)
+    if (!ds->w32) {
+      if (m->host.nK <= 2 && m->max_leaf <= 3)
+        return launch_event2<2, 3, GRAD>(m, ds, begin, end, out_mode, fused_norm);
+      if constexpr (!GRAD) return launch_event2<4, 4, GRAD>(m, ds, begin, end, out_mode, fused_norm);
+    }
   }
   if (fused_norm) return set_error(GOO_ERR_STATE, "sop_events: in-kernel normalisation needs the pair kernel");
   if (m->host.nK <= 2 && m->max_leaf <= 3) return launch_event_T<T, 2, 3, GRAD>(m, ds, begin, end, out_mode);
@@ -2145,7 +2162,7 @@ static int static_launch(const ModelDev& h, int max_leaf, unsigned char* base, i
   Cols<T> cols{};
   for (int c = 0; c < kMaxObs; ++c) cols.c[c] = (const T*)cols_dev[c < h.n_obs ? c : 0];
   sop_event_kernel<T, K, L, true><<<(unsigned)nb, kBlock, 0, st>>>(md, make_evconst<T, K, L>(h), cols, 0, n, partials,
-                                                                   counters, result, 0);
+                                                                   counters, result, 0, nullptr);
   GOO_CUDA_TRY(cudaGetLastError());
   return GOO_OK;
 }

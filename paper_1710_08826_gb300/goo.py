@@ -94,6 +94,7 @@ def _load():
         "goo_dataset_free": (ctypes.c_int, [vp]),
         "goo_dataset_size": (i64, [vp]),
         "goo_dataset_column": (vp, [vp, ctypes.c_int, ctypes.c_int]),
+        "goo_dataset_set_weights": (ctypes.c_int, [vp, dp]),
         "goo_model_build": (ctypes.c_int, [vp, ctypes.POINTER(GooNode), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            dp, dp, ctypes.POINTER(vp)]),
         "goo_model_set_norm": (ctypes.c_int, [vp, ctypes.POINTER(GooNormSpec)]),
@@ -254,6 +255,17 @@ class Dataset:
 
     def column_ptr(self, col, dtype="f64"):
         return lib.goo_dataset_column(self.handle, col, precision_code(dtype))
+
+    def set_weights(self, weights):
+        """Per-event weights (a binned dataset: bin centres with their counts), copied to the
+        device (goo_dataset_set_weights); None removes them."""
+        if weights is None:
+            _check(lib.goo_dataset_set_weights(self.handle, None))
+            return
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        if w.shape != (self.n,):
+            raise ValueError(f"weights must have shape ({self.n},)")
+        _check(lib.goo_dataset_set_weights(self.handle, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
 
     def close(self):
         if getattr(self, "handle", None):
