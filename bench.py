@@ -351,25 +351,57 @@ def run_ours(args):
     hi = [o[2] for o in spec["observables"]]
     names = [o[0] for o in spec["observables"]]
 
-    def e2e_step():
-        d = goo.Dataset(ctx, [host_cols[k].numpy() for k in names], lo, hi, dtype="f32")
+    # Three forms of the user's step, each timed over the same number of steps: a dataset
+    # created and freed every step; one dataset refilled every step through the copy engine
+    # (goo_dataset_update, GOO_COPY); and refilled by the ingest kernel reading the pinned
+    # host columns itself (GOO_COPY_MAPPED).  Every form moves the step's columns host ->
+    # device and reads the NLL and gradient back.
+    cols_np = [host_cols[k].numpy() for k in names]
+    cols_pin = [host_cols[k] for k in names]
+    ds_stream = goo.Dataset(ctx, cols_np, lo, hi, dtype="f32")
+
+    def e2e_fresh():
+        d = goo.Dataset(ctx, cols_np, lo, hi, dtype="f32")
         out = model.nll_grad(d, theta, "f32")
         d.close()
         return out
 
-    for _ in range(2):
-        e2e_step()
-    barrier()
+    def e2e_update():
+        ds_stream.update(cols_np)
+        return model.nll_grad(ds_stream, theta, "f32")
+
+    def e2e_mapped():
+        ds_stream.update(cols_pin, mapped=True)
+        return model.nll_grad(ds_stream, theta, "f32")
+
     e2e_steps = max(3, args.steps // 5)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_step()
-    barrier()
-    e2e_s = time.perf_counter() - t0
-    if pg is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
+
+    def e2e_time(fn):
+        for _ in range(2):
+            fn()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            fn()
+        barrier()
+        sec = time.perf_counter() - t0
+        if pg is not None:
+            t = torch.tensor([sec], dtype=torch.float64, device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            sec = float(t.item())
+        return sec
+
+    e2e_forms = {
+        "update_mapped": (e2e_time(e2e_mapped), "goo_dataset_update (GOO_COPY_MAPPED: the ingest kernel reads the "
+                                                "pinned float32 host columns) + goo_nll_grad"),
+        "update_copy": (e2e_time(e2e_update), "goo_dataset_update (GOO_COPY: copy engine from pinned float32 host "
+                                              "columns) + goo_nll_grad"),
+        "fresh_upload": (e2e_time(e2e_fresh), "goo_dataset_upload from pinned float32 host columns + goo_nll_grad + "
+                                              "goo_dataset_free"),
+    }
+    ds_stream.close()
+    e2e_best = min(e2e_forms, key=lambda k: e2e_forms[k][0])
+    e2e_s = e2e_forms[e2e_best][0]
 
     # ---- roofline of the dominant kernel of the FP32+grad step
     name, (cnt, kms) = max(kt_mix.items(), key=lambda kv: kv[1][1])
@@ -410,7 +442,8 @@ def run_ours(args):
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * BYTES_PER_EVENT_F32 + 8 * P,
                 "d2h_bytes_per_step": 8 * (2 + P), "ms_per_step": e2e_s / e2e_steps * 1e3,
-                "what": "goo_dataset_upload from pinned float32 host columns + goo_nll_grad + dataset free"},
+                "what": e2e_forms[e2e_best][1],
+                "forms_ms_per_step": {k: v[0] / e2e_steps * 1e3 for k, v in e2e_forms.items()}},
         "gpu_launches": launches,
         "clocks": clk,
     }

@@ -58,7 +58,10 @@ enum {
 /* ---- dataset upload flags ----------------------------------------------------------- */
 enum {
   GOO_COPY = 0,         /* cols are host pointers; the library copies them                 */
-  GOO_BORROW_DEVICE = 1 /* cols are device pointers that must outlive the dataset         */
+  GOO_BORROW_DEVICE = 1, /* cols are device pointers that must outlive the dataset        */
+  GOO_COPY_MAPPED = 2   /* cols are pinned host pointers (cudaHostAlloc / registered); the
+                           ingest kernel reads them over the host link itself, with no
+                           separate copy-engine transfer                                   */
 };
 
 /* ---- model nodes --------------------------------------------------------------------- */
@@ -174,11 +177,24 @@ int goo_timing_read(goo_ctx* ctx, int max_entries, char* names, int64_t* counts,
  * (Sec. 4: data loaded outside the observables' ranges is caught at run time): if
  * any value lies outside its [lo, hi] (or is NaN) the call fails with GOO_ERR_RANGE, no
  * dataset is created, and *n_bad (if not NULL) receives the number of offending events.
- * The device keeps both a float64 and a float32 copy of every column. */
+ * The device keeps both a float64 and a float32 copy of every column, written by one fused
+ * conversion and range-check pass.  GOO_COPY_MAPPED fails with GOO_ERR_ARG unless every
+ * column is pinned host memory. */
 int goo_dataset_upload(goo_ctx* ctx, int ncols, const void* const* cols, int dtype,
                        int64_t n_events, const double* lo, const double* hi, int flags,
                        goo_dataset** out, int64_t* n_bad);
 int goo_dataset_free(goo_dataset* ds);
+/* Replace the events of a dataset created with GOO_COPY or GOO_COPY_MAPPED by n_events new
+ * ones (0 <= n_events <= the count it was created with), reusing its device buffers: the
+ * streaming form of goo_dataset_upload for a new batch of events each step.  cols: one host
+ * array per column (the dataset's ncols, the same limits), flags GOO_COPY or GOO_COPY_MAPPED
+ * as for the upload.  Waits for the launches in flight, then copies, converts and
+ * range-checks like the upload.  Weights are removed and amplitude caches and MC Gram
+ * matrices built from the old events are invalidated.  Errors: GOO_ERR_STATE for a dataset
+ * that borrows its columns, GOO_ERR_ARG for a bad size or flag, GOO_ERR_RANGE (with
+ * *n_bad) when events lie outside the limits, after which the dataset holds no events. */
+int goo_dataset_update(goo_dataset* ds, const void* const* cols, int dtype, int64_t n_events, int flags,
+                       int64_t* n_bad);
 int64_t goo_dataset_size(const goo_dataset* ds);
 /* Device pointer of column `col` in the given precision (for zero-copy consumers). */
 const void* goo_dataset_column(const goo_dataset* ds, int col, int dtype);

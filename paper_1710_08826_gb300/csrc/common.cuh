@@ -111,6 +111,10 @@ struct goo_ctx {
 struct goo_dataset {
   goo_ctx* ctx = nullptr;
   int64_t n = 0;
+  int64_t capacity = 0;  // events the owned buffers hold (goo_dataset_update)
+  // changes whenever the events change (goo_dataset_update); part of every key of a result
+  // cached from this dataset's events (amplitude caches, MC Gram matrices)
+  uint64_t epoch = 0;
   int ncols = 0;
   double* d64[goo::kMaxCols] = {};
   float* d32[goo::kMaxCols] = {};

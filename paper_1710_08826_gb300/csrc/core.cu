@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -112,32 +113,74 @@ int grid_blocks(goo_ctx* ctx, int64_t work_items, int blocks_per_sm) {
 // ---------------------------------------------------------------------------------------
 // dataset kernels
 // ---------------------------------------------------------------------------------------
-__global__ void convert_f64_to_f32(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = (float)in[i];
-}
-
-__global__ void convert_f32_to_f64(const float* __restrict__ in, double* __restrict__ out, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = (double)in[i];
-}
-
-struct RangeArgs {
-  const double* col[kMaxCols];
+// One pass over the events at upload: reads each column in the precision it was given
+// (from the dataset's own buffer, or from pinned host memory for a mapped upload), writes the
+// other precision (and, for a mapped upload, the given one), and counts events with any
+// column outside [lo, hi] (NaN counts as outside).  Four events per thread where every source
+// is 16-byte aligned.  One integer atomic per block: the count is exact and order-independent.
+struct IngestArgs {
+  const void* src[kMaxCols];
+  double* d64[kMaxCols];
+  float* d32[kMaxCols];
   double lo[kMaxCols], hi[kMaxCols];
   int ncols;
+  int store_src;  // also store the source values into the buffer of their own precision
 };
 
-// Counts events with any column outside [lo, hi] (NaN counts as outside).  One integer
-// atomic per block: the count is exact and order-independent.
-__global__ void range_check_kernel(RangeArgs a, int64_t n, unsigned long long* bad) {
+template <bool F32>
+__device__ __forceinline__ bool ingest_one(const IngestArgs& a, int c, int64_t i) {
+  double v;
+  if constexpr (F32) {
+    const float f = ((const float*)a.src[c])[i];
+    if (a.store_src) a.d32[c][i] = f;
+    v = (double)f;
+    a.d64[c][i] = v;
+  } else {
+    v = ((const double*)a.src[c])[i];
+    if (a.store_src) a.d64[c][i] = v;
+    a.d32[c][i] = (float)v;
+  }
+  return v >= a.lo[c] && v <= a.hi[c];
+}
+
+template <bool F32, bool VEC>
+__global__ void ingest_kernel(IngestArgs a, int64_t n, unsigned long long* bad) {
   unsigned local = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    bool ok = true;
-    for (int c = 0; c < a.ncols; ++c) {
-      double v = a.col[c][i];
-      ok = ok && (v >= a.lo[c]) && (v <= a.hi[c]);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t tail = 0;
+  if constexpr (VEC) {
+    const int64_t nq = n / 4;
+    tail = nq * 4;
+    for (int64_t q = t0; q < nq; q += stride) {
+      bool ok[4] = {true, true, true, true};
+      for (int c = 0; c < a.ncols; ++c) {
+        double v[4];
+        if constexpr (F32) {
+          const float4 f = ((const float4*)a.src[c])[q];
+          if (a.store_src) ((float4*)a.d32[c])[q] = f;
+          v[0] = f.x, v[1] = f.y, v[2] = f.z, v[3] = f.w;
+          ((double2*)a.d64[c])[2 * q] = make_double2(v[0], v[1]);
+          ((double2*)a.d64[c])[2 * q + 1] = make_double2(v[2], v[3]);
+        } else {
+          const double2 d0 = ((const double2*)a.src[c])[2 * q], d1 = ((const double2*)a.src[c])[2 * q + 1];
+          if (a.store_src) {
+            ((double2*)a.d64[c])[2 * q] = d0;
+            ((double2*)a.d64[c])[2 * q + 1] = d1;
+          }
+          v[0] = d0.x, v[1] = d0.y, v[2] = d1.x, v[3] = d1.y;
+          ((float4*)a.d32[c])[q] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ok[j] = ok[j] && v[j] >= a.lo[c] && v[j] <= a.hi[c];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) local += ok[j] ? 0u : 1u;
     }
+  }
+  for (int64_t i = tail + t0; i < n; i += stride) {
+    bool ok = true;
+    for (int c = 0; c < a.ncols; ++c) ok = ingest_one<F32>(a, c, i) && ok;
     local += ok ? 0u : 1u;
   }
   for (int m = 16; m > 0; m >>= 1) local += __shfl_xor_sync(0xffffffffu, local, m);
@@ -168,6 +211,72 @@ static void free_dataset_memory(goo_dataset* ds) {
     c.bytes = 0;
     c.key = 0;
   }
+}
+
+
+// Brings n events of the given columns into the dataset's buffers and range-checks them:
+// with mapped == false the columns are already in the buffer of `dtype` (copied or borrowed);
+// with mapped == true `cols` are pinned host arrays that the ingest kernel reads itself.
+// Waits for the stream and returns the number of out-of-range events in *nb.
+static int ingest(goo_dataset* ds, const void* const* cols, int dtype, int64_t n, bool mapped,
+                  unsigned long long* nb) {
+  goo_ctx* ctx = ds->ctx;
+  *nb = 0;
+  if (n > 0) {
+    IngestArgs a{};
+    a.ncols = ds->ncols;
+    a.store_src = mapped ? 1 : 0;
+    bool aligned = true;
+    for (int c = 0; c < ds->ncols; ++c) {
+      a.src[c] = mapped ? cols[c] : (dtype == GOO_F32 ? (const void*)ds->d32[c] : (const void*)ds->d64[c]);
+      a.d64[c] = ds->d64[c];
+      a.d32[c] = ds->d32[c];
+      a.lo[c] = ds->lo[c];
+      a.hi[c] = ds->hi[c];
+      aligned = aligned && ((uintptr_t)a.src[c] & 15) == 0 && ((uintptr_t)a.d64[c] & 15) == 0 &&
+                ((uintptr_t)a.d32[c] & 15) == 0;
+    }
+    unsigned long long* bad = (unsigned long long*)(ctx->scratch.counters + 8);
+    GOO_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), ctx->stream));
+    {
+      LaunchScope ls(ctx, "ingest");
+      const int nb_ = grid_blocks(ctx, aligned ? (n + 3) / 4 : n, 8);
+      if (dtype == GOO_F32) {
+        if (aligned) ingest_kernel<true, true><<<nb_, kBlock, 0, ctx->stream>>>(a, n, bad);
+        else ingest_kernel<true, false><<<nb_, kBlock, 0, ctx->stream>>>(a, n, bad);
+      } else {
+        if (aligned) ingest_kernel<false, true><<<nb_, kBlock, 0, ctx->stream>>>(a, n, bad);
+        else ingest_kernel<false, false><<<nb_, kBlock, 0, ctx->stream>>>(a, n, bad);
+      }
+      GOO_CUDA_TRY(cudaGetLastError());
+    }
+    unsigned long long* stage = (unsigned long long*)(ctx->scratch.host_pinned + kPinnedResult);
+    GOO_CUDA_TRY(cudaMemcpyAsync(stage, bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
+    GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    *nb = *stage;
+  } else {
+    GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  }
+  return GOO_OK;
+}
+
+// A fresh value for goo_dataset::epoch (unique over the process).
+static uint64_t next_dataset_epoch() {
+  static std::atomic<uint64_t> counter{1};
+  return counter.fetch_add(1);
+}
+
+// True when every column is host memory the device can address (pinned / registered).
+static bool host_mapped(const void* const* cols, int ncols) {
+  for (int c = 0; c < ncols; ++c) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, cols[c]) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (at.type != cudaMemoryTypeHost || at.devicePointer != cols[c]) return false;
+  }
+  return true;
 }
 
 }  // namespace goo
@@ -253,6 +362,17 @@ int goo_finalize(goo_ctx* ctx) {
   return GOO_OK;
 }
 
+// Copies n events of host columns into the dataset's buffers of `dtype` (copy engine, the
+// context's stream).
+static int copy_columns(goo_dataset* ds, const void* const* cols, int dtype, int64_t n) {
+  const size_t es = dtype == GOO_F32 ? sizeof(float) : sizeof(double);
+  for (int c = 0; c < ds->ncols && n > 0; ++c) {
+    void* dst = dtype == GOO_F32 ? (void*)ds->d32[c] : (void*)ds->d64[c];
+    GOO_CUDA_TRY(cudaMemcpyAsync(dst, cols[c], (size_t)n * es, cudaMemcpyHostToDevice, ds->ctx->stream));
+  }
+  return GOO_OK;
+}
+
 int goo_dataset_upload(goo_ctx* ctx, int ncols, const void* const* cols, int dtype, int64_t n_events,
                        const double* lo, const double* hi, int flags, goo_dataset** out, int64_t* n_bad) {
   if (n_bad) *n_bad = 0;
@@ -261,7 +381,8 @@ int goo_dataset_upload(goo_ctx* ctx, int ncols, const void* const* cols, int dty
   if (ncols < 1 || ncols > kMaxCols) return set_error(GOO_ERR_ARG, "goo_dataset_upload: ncols=%d (1..%d)", ncols, kMaxCols);
   if (n_events < 0) return set_error(GOO_ERR_ARG, "goo_dataset_upload: n_events=%lld", (long long)n_events);
   if (dtype != GOO_F64 && dtype != GOO_F32) return set_error(GOO_ERR_ARG, "goo_dataset_upload: dtype=%d", dtype);
-  if (flags != GOO_COPY && flags != GOO_BORROW_DEVICE) return set_error(GOO_ERR_ARG, "goo_dataset_upload: flags=%d", flags);
+  if (flags != GOO_COPY && flags != GOO_BORROW_DEVICE && flags != GOO_COPY_MAPPED)
+    return set_error(GOO_ERR_ARG, "goo_dataset_upload: flags=%d", flags);
   for (int c = 0; c < ncols; ++c) {
     if (!(lo[c] < hi[c])) return set_error(GOO_ERR_ARG, "goo_dataset_upload: column %d has lo >= hi", c);
     if (n_events > 0 && !cols[c]) return set_error(GOO_ERR_ARG, "goo_dataset_upload: column %d is NULL", c);
@@ -269,9 +390,13 @@ int goo_dataset_upload(goo_ctx* ctx, int ncols, const void* const* cols, int dty
       return set_error(GOO_ERR_ARG, "goo_dataset_upload: borrowed column %d is not 16-byte aligned", c);
   }
   GOO_CUDA_TRY(cudaSetDevice(ctx->device));
+  if (flags == GOO_COPY_MAPPED && n_events > 0 && !host_mapped(cols, ncols))
+    return set_error(GOO_ERR_ARG, "goo_dataset_upload: GOO_COPY_MAPPED needs pinned host columns");
   goo_dataset* ds = new goo_dataset();
   ds->ctx = ctx;
   ds->n = n_events;
+  ds->capacity = n_events;
+  ds->epoch = next_dataset_epoch();
   ds->ncols = ncols;
   ds->owns64 = !(flags == GOO_BORROW_DEVICE && dtype == GOO_F64);
   ds->owns32 = !(flags == GOO_BORROW_DEVICE && dtype == GOO_F32);
@@ -285,67 +410,59 @@ int goo_dataset_upload(goo_ctx* ctx, int ncols, const void* const* cols, int dty
   for (int c = 0; c < ncols; ++c) {
     ds->lo[c] = lo[c];
     ds->hi[c] = hi[c];
-    if (dtype == GOO_F64) {
-      if (flags == GOO_BORROW_DEVICE) {
-        ds->d64[c] = (double*)cols[c];
-      } else {
-        if (cudaMalloc(&ds->d64[c], n_alloc * sizeof(double)) != cudaSuccess) return fail(GOO_ERR_OOM, "out of device memory");
-        if (n_events && cudaMemcpyAsync(ds->d64[c], cols[c], n_events * sizeof(double), cudaMemcpyHostToDevice,
-                                        ctx->stream) != cudaSuccess)
-          return fail(GOO_ERR_CUDA, "host-to-device copy failed");
-      }
-      if (cudaMalloc(&ds->d32[c], n_alloc * sizeof(float)) != cudaSuccess) return fail(GOO_ERR_OOM, "out of device memory");
-      if (n_events) {
-        LaunchScope ls(ctx, "convert_f64_to_f32");
-        convert_f64_to_f32<<<grid_blocks(ctx, n_events, 8), kBlock, 0, ctx->stream>>>(ds->d64[c], ds->d32[c], n_events);
-      }
-    } else {
-      if (flags == GOO_BORROW_DEVICE) {
-        ds->d32[c] = (float*)cols[c];
-      } else {
-        if (cudaMalloc(&ds->d32[c], n_alloc * sizeof(float)) != cudaSuccess) return fail(GOO_ERR_OOM, "out of device memory");
-        if (n_events && cudaMemcpyAsync(ds->d32[c], cols[c], n_events * sizeof(float), cudaMemcpyHostToDevice,
-                                        ctx->stream) != cudaSuccess)
-          return fail(GOO_ERR_CUDA, "host-to-device copy failed");
-      }
-      if (cudaMalloc(&ds->d64[c], n_alloc * sizeof(double)) != cudaSuccess) return fail(GOO_ERR_OOM, "out of device memory");
-      if (n_events) {
-        LaunchScope ls(ctx, "convert_f32_to_f64");
-        convert_f32_to_f64<<<grid_blocks(ctx, n_events, 8), kBlock, 0, ctx->stream>>>(ds->d32[c], ds->d64[c], n_events);
-      }
-    }
+    if (flags == GOO_BORROW_DEVICE && dtype == GOO_F64) ds->d64[c] = (double*)cols[c];
+    else if (cudaMalloc(&ds->d64[c], n_alloc * sizeof(double)) != cudaSuccess) return fail(GOO_ERR_OOM, "out of device memory");
+    if (flags == GOO_BORROW_DEVICE && dtype == GOO_F32) ds->d32[c] = (float*)cols[c];
+    else if (cudaMalloc(&ds->d32[c], n_alloc * sizeof(float)) != cudaSuccess) return fail(GOO_ERR_OOM, "out of device memory");
   }
-  if (n_events > 0) {
-    RangeArgs ra{};
-    ra.ncols = ncols;
-    for (int c = 0; c < ncols; ++c) {
-      ra.col[c] = ds->d64[c];
-      ra.lo[c] = lo[c];
-      ra.hi[c] = hi[c];
-    }
-    unsigned long long* bad = (unsigned long long*)(ctx->scratch.counters + 8);
-    if (cudaMemsetAsync(bad, 0, sizeof(unsigned long long), ctx->stream) != cudaSuccess)
-      return fail(GOO_ERR_CUDA, "memset failed");
-    {
-      LaunchScope ls(ctx, "range_check");
-      range_check_kernel<<<grid_blocks(ctx, n_events, 8), kBlock, 0, ctx->stream>>>(ra, n_events, bad);
-    }
-    unsigned long long nb = 0;
-    if (cudaMemcpyAsync(&nb, bad, sizeof nb, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
-        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
-      return fail(GOO_ERR_CUDA, "range check failed");
-    if (nb) {
-      if (n_bad) *n_bad = (int64_t)nb;
-      free_dataset_memory(ds);
-      delete ds;
-      return set_error(GOO_ERR_RANGE, "goo_dataset_upload: %llu of %lld events lie outside the observable limits",
-                       nb, (long long)n_events);
-    }
-  } else {
-    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return fail(GOO_ERR_CUDA, "stream sync failed");
+  if (flags == GOO_COPY && copy_columns(ds, cols, dtype, n_events) != GOO_OK) return fail(GOO_ERR_CUDA, "host-to-device copy failed");
+  unsigned long long nb = 0;
+  if (ingest(ds, cols, dtype, n_events, flags == GOO_COPY_MAPPED, &nb) != GOO_OK) return fail(GOO_ERR_CUDA, "range check failed");
+  if (nb) {
+    if (n_bad) *n_bad = (int64_t)nb;
+    free_dataset_memory(ds);
+    delete ds;
+    return set_error(GOO_ERR_RANGE, "goo_dataset_upload: %llu of %lld events lie outside the observable limits", nb,
+                     (long long)n_events);
   }
   ctx->live++;
   *out = ds;
+  return GOO_OK;
+}
+
+int goo_dataset_update(goo_dataset* ds, const void* const* cols, int dtype, int64_t n_events, int flags,
+                       int64_t* n_bad) {
+  if (n_bad) *n_bad = 0;
+  if (!ds || !cols) return set_error(GOO_ERR_ARG, "goo_dataset_update: NULL argument");
+  if (!ds->owns32 || !ds->owns64) return set_error(GOO_ERR_STATE, "goo_dataset_update: the dataset borrows its columns");
+  if (n_events < 0 || n_events > ds->capacity)
+    return set_error(GOO_ERR_ARG, "goo_dataset_update: n_events=%lld (capacity %lld)", (long long)n_events,
+                     (long long)ds->capacity);
+  if (dtype != GOO_F64 && dtype != GOO_F32) return set_error(GOO_ERR_ARG, "goo_dataset_update: dtype=%d", dtype);
+  if (flags != GOO_COPY && flags != GOO_COPY_MAPPED) return set_error(GOO_ERR_ARG, "goo_dataset_update: flags=%d", flags);
+  for (int c = 0; c < ds->ncols; ++c)
+    if (n_events > 0 && !cols[c]) return set_error(GOO_ERR_ARG, "goo_dataset_update: column %d is NULL", c);
+  GOO_CUDA_TRY(cudaSetDevice(ds->ctx->device));
+  if (flags == GOO_COPY_MAPPED && n_events > 0 && !host_mapped(cols, ds->ncols))
+    return set_error(GOO_ERR_ARG, "goo_dataset_update: GOO_COPY_MAPPED needs pinned host columns");
+  // launches in flight may still read the old events and weights
+  GOO_CUDA_TRY(cudaStreamSynchronize(ds->ctx->stream));
+  ds->n = 0;
+  ds->epoch = next_dataset_epoch();
+  if (ds->w64) cudaFree(ds->w64);
+  if (ds->w32) cudaFree(ds->w32);
+  ds->w64 = nullptr;
+  ds->w32 = nullptr;
+  for (auto& c : ds->cache) c.key = 0;
+  if (flags == GOO_COPY) GOO_TRY(copy_columns(ds, cols, dtype, n_events));
+  unsigned long long nb = 0;
+  GOO_TRY(ingest(ds, cols, dtype, n_events, flags == GOO_COPY_MAPPED, &nb));
+  if (nb) {
+    if (n_bad) *n_bad = (int64_t)nb;
+    return set_error(GOO_ERR_RANGE, "goo_dataset_update: %llu of %lld events lie outside the observable limits; the "
+                     "dataset now holds no events", nb, (long long)n_events);
+  }
+  ds->n = n_events;
   return GOO_OK;
 }
 

@@ -1082,7 +1082,8 @@ static int ensure_cache(goo_model* m, const goo_dataset* ds_c, int precision, co
   DalitzModel& d = *m->dalitz;
   goo_ctx* ctx = m->ctx;
   const int pi = precision == GOO_F32 ? 0 : 1;
-  const uint64_t key = d.ls_key ^ (uint64_t)(uintptr_t)m ^ (uint64_t)(pi + 1 + (exchanged ? 4 : 0)) * 0x9e3779b97f4a7c15ull;
+  const uint64_t key = d.ls_key ^ (uint64_t)(uintptr_t)m ^ (uint64_t)(pi + 1 + (exchanged ? 4 : 0)) * 0x9e3779b97f4a7c15ull ^
+                       ds->epoch * 0xd6e8feb86659fd93ull;
   CacheSlot& slot = ds->cache[pi + (exchanged ? 2 : 0)];
   const int ca = exchanged ? d.col13 : d.col12, cb = exchanged ? d.col12 : d.col13;
   const int64_t n = ds->n;
@@ -1147,7 +1148,7 @@ static int ensure_gram(goo_model* m, int precision) {
   DalitzModel& d = *m->dalitz;
   const int pi = precision == GOO_F32 ? 0 : 1;
   if (!d.mc) return set_error(GOO_ERR_STATE, "amplitude model has no MC normalisation sample (goo_model_set_norm)");
-  const uint64_t key = d.ls_key ^ (uint64_t)(uintptr_t)d.mc ^ (uint64_t)(pi + 7);
+  const uint64_t key = d.ls_key ^ (uint64_t)(uintptr_t)d.mc ^ (uint64_t)(pi + 7) ^ d.mc->epoch * 0xd6e8feb86659fd93ull;
   if (d.gram_key[pi] == key) return GOO_OK;
   const void* cache = nullptr;
   GOO_TRY(ensure_cache(m, d.mc, precision, &cache));
@@ -1362,7 +1363,7 @@ static int ensure_td_grams(goo_model* m, int precision) {
   const int pi = precision == GOO_F32 ? 0 : 1;
   if (!d.mc) return set_error(GOO_ERR_STATE, "amplitude model has no MC normalisation sample (goo_model_set_norm)");
   if (d.mc->n < 1) return set_error(GOO_ERR_ARG, "the MC normalisation sample is empty");
-  const uint64_t key = d.ls_key ^ (uint64_t)(uintptr_t)d.mc ^ (uint64_t)(pi + 11);
+  const uint64_t key = d.ls_key ^ (uint64_t)(uintptr_t)d.mc ^ (uint64_t)(pi + 11) ^ d.mc->epoch * 0xd6e8feb86659fd93ull;
   if (d.gram3_key[pi] == key) return GOO_OK;
   const void *ca = nullptr, *cb = nullptr;
   GOO_TRY(ensure_cache(m, d.mc, precision, &ca));

@@ -616,7 +616,8 @@ static int td4_cache(goo_model* m, const goo_dataset* ds_c, int precision, const
   Td4Model& d = *m->td4;
   goo_ctx* ctx = m->ctx;
   const int pi = precision == GOO_F32 ? 0 : 1;
-  const uint64_t key = d.key ^ (uint64_t)(uintptr_t)m ^ (uint64_t)(pi + 3) * 0x9e3779b97f4a7c15ull;
+  const uint64_t key = d.key ^ (uint64_t)(uintptr_t)m ^ (uint64_t)(pi + 3) * 0x9e3779b97f4a7c15ull ^
+                       ds->epoch * 0xd6e8feb86659fd93ull;
   CacheSlot& slot = ds->cache[pi];
   const int64_t n = ds->n;
   const size_t bytes = pi == 0 ? (size_t)((d.K + 1) / 2) * (size_t)n * sizeof(float4) : (size_t)d.K * (size_t)n * sizeof(double2);
@@ -684,7 +685,7 @@ static int td4_ensure_gram(goo_model* m, int precision) {
   const int pi = precision == GOO_F32 ? 0 : 1;
   if (!d.mc) return set_error(GOO_ERR_STATE, "the four-body model has no MC normalisation sample (goo_model_set_norm)");
   if (d.K > 15) return set_error(GOO_ERR_UNSUPPORTED, "the Gram matrix supports at most 15 amplitudes");
-  const uint64_t key = d.key ^ (uint64_t)(uintptr_t)d.mc ^ (uint64_t)(pi + 11);
+  const uint64_t key = d.key ^ (uint64_t)(uintptr_t)d.mc ^ (uint64_t)(pi + 11) ^ d.mc->epoch * 0xd6e8feb86659fd93ull;
   if (d.gram_key[pi] == key) return GOO_OK;
   if (d.mc->n < 1) return set_error(GOO_ERR_ARG, "the MC normalisation sample is empty");
   const void* cache = nullptr;

@@ -18,7 +18,7 @@ GOO_ERR_NONPOSITIVE_PDF, GOO_ERR_TIMEOUT, GOO_ERR_STATE, GOO_ERR_UNSUPPORTED = -
 GOO_F64, GOO_F32 = 0, 1
 GOO_LINESHAPE_CACHED, GOO_LINESHAPE_FLOATING = 0, 1
 GOO_COEF_CARTESIAN, GOO_COEF_POLAR = 0, 1
-GOO_COPY, GOO_BORROW_DEVICE = 0, 1
+GOO_COPY, GOO_BORROW_DEVICE, GOO_COPY_MAPPED = 0, 1, 2
 OP = dict(gauss=1, expo=2, poly2=3, argus=4, prod=10, add=11, bw=20, nr=21, coherent=22, td4=23, amp4=24, td3=25)
 ANG = dict(SS=0, VS0=1, SV0=2, VV0=3, VVpar=4, VVperp=5, TS0=6, TV0=7)
 NORM = dict(analytic=0, grid=1, mc=2)
@@ -95,6 +95,8 @@ def _load():
         "goo_dataset_size": (i64, [vp]),
         "goo_dataset_column": (vp, [vp, ctypes.c_int, ctypes.c_int]),
         "goo_dataset_set_weights": (ctypes.c_int, [vp, dp]),
+        "goo_dataset_update": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.c_int, i64, ctypes.c_int,
+                                              ctypes.POINTER(i64)]),
         "goo_model_build": (ctypes.c_int, [vp, ctypes.POINTER(GooNode), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            dp, dp, ctypes.POINTER(vp)]),
         "goo_model_set_norm": (ctypes.c_int, [vp, ctypes.POINTER(GooNormSpec)]),
@@ -205,17 +207,21 @@ class Context:
 class Dataset:
     """Structure-of-arrays event columns on the device (goo_dataset_upload)."""
 
-    def __init__(self, ctx, columns, lo, hi, dtype="f64"):
+    def __init__(self, ctx, columns, lo, hi, dtype="f64", mapped=False):
+        """columns: host arrays (copied), CUDA tensors (borrowed), or with mapped=True pinned
+        host tensors / arrays that the ingest kernel reads directly (GOO_COPY_MAPPED)."""
         self.ctx = ctx
         cols = list(columns)
         ncols = len(cols)
         dt = precision_code(dtype)
         self._keep = []
         ptrs = (ctypes.c_void_p * ncols)()
-        flags = GOO_COPY
+        flags = GOO_COPY_MAPPED if mapped else GOO_COPY
         n = None
         for i, c in enumerate(cols):
             if hasattr(c, "is_cuda") and c.is_cuda:
+                if mapped:
+                    raise ValueError("mapped upload takes pinned host columns, not CUDA tensors")
                 flags = GOO_BORROW_DEVICE
                 want = "float64" if dt == GOO_F64 else "float32"
                 if str(c.dtype) != "torch." + want or not c.is_contiguous():
@@ -240,9 +246,10 @@ class Dataset:
                                     ctypes.byref(nbad))
         self.n_bad = int(nbad.value)
         _check(rc)
-        if flags == GOO_COPY:
+        if flags != GOO_BORROW_DEVICE:
             self._keep = []
         self.handle = h
+        self.dtype = dtype
         self.n = int(n or 0)
         self.ncols = ncols
         self.lo, self.hi = list(lo_a), list(hi_a)
@@ -255,6 +262,39 @@ class Dataset:
 
     def column_ptr(self, col, dtype="f64"):
         return lib.goo_dataset_column(self.handle, col, precision_code(dtype))
+
+    def update(self, columns, mapped=False):
+        """New events into the same device buffers (goo_dataset_update): host arrays, or with
+        mapped=True pinned host columns read by the ingest kernel."""
+        cols = list(columns)
+        if len(cols) != self.ncols:
+            raise ValueError(f"expected {self.ncols} columns")
+        dt = precision_code(self.dtype)
+        ptrs = (ctypes.c_void_p * self.ncols)()
+        keep, n = [], None
+        for i, c in enumerate(cols):
+            if hasattr(c, "data_ptr"):
+                want = "float64" if dt == GOO_F64 else "float32"
+                if c.is_cuda or str(c.dtype) != "torch." + want or not c.is_contiguous():
+                    raise ValueError(f"column {i} must be a contiguous host torch.{want} tensor")
+                ptrs[i] = c.data_ptr()
+                size = c.numel()
+            else:
+                a = np.ascontiguousarray(c, dtype=np.float64 if dt == GOO_F64 else np.float32)
+                keep.append(a)
+                ptrs[i] = a.ctypes.data
+                size = a.size
+            if n is None:
+                n = size
+            elif size != n:
+                raise ValueError("columns differ in length")
+        nbad = ctypes.c_int64(0)
+        rc = lib.goo_dataset_update(self.handle, ptrs, dt, int(n or 0), GOO_COPY_MAPPED if mapped else GOO_COPY,
+                                    ctypes.byref(nbad))
+        self.n_bad = int(nbad.value)
+        if rc == 0 or rc == GOO_ERR_RANGE:
+            self.n = 0 if rc else int(n or 0)
+        _check(rc)
 
     def set_weights(self, weights):
         """Per-event weights (a binned dataset: bin centres with their counts), copied to the
