@@ -29,7 +29,18 @@
 #ifndef GOO_H
 #define GOO_H
 
+#ifdef __CUDACC_RTC__
+/* device code compiled at run time (NVRTC) sees the enums only; the integer types come
+   from the compiler's own headers */
+#include <cuda/std/cstdint>
+typedef cuda::std::int32_t int32_t;
+typedef cuda::std::int64_t int64_t;
+typedef cuda::std::uint64_t uint64_t;
+typedef cuda::std::uint32_t uint32_t;
+typedef cuda::std::uintptr_t uintptr_t;
+#else
 #include <stdint.h>
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -274,6 +285,16 @@ int goo_model_set_lineshapes(goo_model* model, int mode);
  * only.  GOO_ERR_UNSUPPORTED for other models, GOO_ERR_ARG for another form. */
 enum { GOO_COEF_CARTESIAN = 0, GOO_COEF_POLAR = 1 };
 int goo_model_set_coefficients(goo_model* model, int form);
+/* Run-time kernel specialisation of a sum-of-products model's FP32 evaluation.  With mode 1
+ * (the default) the first FP32 evaluation that runs in the packed-pair event kernel compiles
+ * that kernel for the model's leaf signature with NVRTC (a second or so, once per signature
+ * and process); later evaluations launch the compiled kernel.  Mode 0 keeps the interpreter
+ * compiled into the library.  Both compute the same sums; they may differ in the last bits
+ * through fused multiply-adds.  GOO_ERR_ARG for another mode.
+ * goo_model_jit_status: 0 off, 1 on and not yet used, 2 the last FP32 evaluation ran the
+ * specialised kernel, -1 compilation failed and the interpreter ran instead. */
+int goo_model_set_jit(goo_model* model, int mode);
+int goo_model_jit_status(const goo_model* model);
 
 /* ---- fitting (paper: the FitManager, Fig. 1; Minuit 2 as the default minimiser, Sec. 4) -------
  * Minimises the NLL of `model` on `ds` over the parameters with free_mask[p] != 0, starting

@@ -39,13 +39,41 @@ def _headers():
     return hs
 
 
+# Headers that the run-time specialised event kernel is compiled from (jit.cu, NVRTC).
+JIT_HEADERS = [os.path.join(INCLUDE, "goo.h"), os.path.join(CSRC, "common.cuh"), os.path.join(CSRC, "model.cuh"),
+               os.path.join(CSRC, "sop_kernels.cuh")]
+_DELIM = "goo_jit_src"
+
+
+def _write_jit_sources():
+    """_build/jit_sources.inc: the JIT headers as C++ raw string literals (rewritten only when
+    their content changes)."""
+    parts = ["// generated by buildlib.py from " + ", ".join(os.path.basename(h) for h in JIT_HEADERS) + "\n"]
+    parts.append("static const char* const kJitHeaderNames[] = {" +
+                 ", ".join('"%s"' % os.path.basename(h) for h in JIT_HEADERS) + "};\n")
+    parts.append("static const char* const kJitHeaderSources[] = {\n")
+    for h in JIT_HEADERS:
+        text = open(h).read()
+        if ")" + _DELIM + '"' in text:
+            raise RuntimeError(f"{h} contains the raw-string delimiter")
+        parts.append('R"' + _DELIM + "(" + text + ")" + _DELIM + '",\n')
+    parts.append("};\n")
+    out = os.path.join(BUILD, "jit_sources.inc")
+    new = "".join(parts)
+    if not os.path.exists(out) or open(out).read() != new:
+        with open(out, "w") as f:
+            f.write(new)
+
+
 def build(verbose=False, force=False, jobs=None):
     """Compile and link libgoo.so; returns its path."""
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
+    _write_jit_sources()
     newest_header = max((os.path.getmtime(h) for h in _headers()), default=0.0)
-    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
-                    "-Xptxas", "-warn-spills"]
+    cuda_include = os.path.join(os.path.dirname(_cuda_lib_dir(nvcc)), "include")
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + BUILD,
+                    '-DGOO_CUDA_INCLUDE="%s"' % cuda_include, "-Xptxas", "-warn-spills"]
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
@@ -68,7 +96,7 @@ def build(verbose=False, force=False, jobs=None):
         os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs)
     if relink:
         cmd = [nvcc] + ARCH + ["-shared", "-o", LIB] + objs + [
-            "-cudart", "shared", "-Xlinker", "-rpath," + _cuda_lib_dir(nvcc)]
+            "-cudart", "shared", "-lnvrtc", "-Xlinker", "-rpath," + _cuda_lib_dir(nvcc)]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link of libgoo.so failed:\n{r.stdout}\n{r.stderr}")

@@ -274,6 +274,16 @@ int goo_model_set_coefficients(goo_model* m, int form) {
   return dalitz_set_coefficients(m, form);
 }
 
+int goo_model_set_jit(goo_model* m, int mode) {
+  if (!m) return set_error(GOO_ERR_ARG, "goo_model_set_jit: NULL model");
+  if (mode != 0 && mode != 1) return set_error(GOO_ERR_ARG, "goo_model_set_jit: mode=%d", mode);
+  m->jit_mode = mode;
+  m->jit_status = mode;
+  return GOO_OK;
+}
+
+int goo_model_jit_status(const goo_model* m) { return m ? m->jit_status : GOO_ERR_ARG; }
+
 int goo_amplitude_cache(goo_model* m, const goo_dataset* ds, const double* theta, int precision, const void** dev_ptr,
                         int* n_amp) {
   if (!m || !ds || !dev_ptr || !n_amp) return set_error(GOO_ERR_ARG, "goo_amplitude_cache: NULL argument");

@@ -8,6 +8,10 @@
 // combination of a few hundred numbers runs in FP64.
 #pragma once
 
+// The device parts of this header (limits, double-float arithmetic, packed FP32, mbarrier
+// and bulk-copy helpers, reductions) are also compiled at run time by NVRTC for the
+// model-specialised event kernels; the host parts are left out there.
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -15,11 +19,13 @@
 #include <cstdio>
 #include <string>
 #include <vector>
+#endif
 
 #include "goo.h"
 
 namespace goo {
 
+#ifndef __CUDACC_RTC__
 // ---------------------------------------------------------------------------------------
 // errors
 // ---------------------------------------------------------------------------------------
@@ -39,6 +45,7 @@ int log_level();
     int _rc = (expr);                                                                      \
     if (_rc != GOO_OK) return _rc;                                                         \
   } while (0)
+#endif
 
 // ---------------------------------------------------------------------------------------
 // limits
@@ -58,6 +65,7 @@ constexpr int kBlock = 256;        // threads per block of the likelihood kernel
 constexpr int kResultDoubles = 4 + kMaxParams + 60;  // result record of one evaluation
 constexpr int kPinnedResult = 256;                   // offset of the result in host_pinned
 
+#ifndef __CUDACC_RTC__
 // ---------------------------------------------------------------------------------------
 // context and datasets
 // ---------------------------------------------------------------------------------------
@@ -144,6 +152,8 @@ struct LaunchScope {
   ~LaunchScope();
 };
 int grid_blocks(goo_ctx* ctx, int64_t work_items, int blocks_per_sm);
+
+#endif  // __CUDACC_RTC__
 
 // ---------------------------------------------------------------------------------------
 // double-float arithmetic (Dekker / Knuth two-sum); every operation is exact up to the

@@ -53,6 +53,7 @@ struct ModelDev {
   double dlogN[kMaxComp][kMaxParams];  // d log N_k / d theta_p
 };
 
+#ifndef __CUDACC_RTC__
 struct DalitzModel;  // three-body amplitude models (dalitz.cu)
 struct Td4Model;     // time-dependent four-body models (td4.cu)
 
@@ -112,6 +113,10 @@ struct goo_model {
   goo::DalitzModel* dalitz = nullptr;
   goo::Td4Model* td4 = nullptr;
   bool counted = false;  // included in ctx->live
+  // FP32 packed-pair kernel specialised for this model at run time (goo_model_set_jit):
+  // jit_mode 1 (default) or 0; jit_status as goo_model_jit_status reports it
+  int jit_mode = 1;
+  int jit_status = 1;
 };
 
 namespace goo {
@@ -127,3 +132,6 @@ struct AmpModelInfo {
 };
 int dalitz_server_info(goo_model* m, const double* theta, AmpModelInfo* info);
 }  // namespace goo
+#else
+}  // namespace goo
+#endif  // __CUDACC_RTC__

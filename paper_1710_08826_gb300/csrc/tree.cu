@@ -40,6 +40,8 @@
 
 #include "common.cuh"
 #include "model.cuh"
+#include "jit.cuh"
+#include "sop_kernels.cuh"
 
 namespace goo {
 
@@ -244,911 +246,6 @@ void host_prep(ModelDev& h, const double* theta, int precision) {
       C.off_lo = (float)(-logN - (double)C.off_hi);
     }
   }
-}
-
-template <typename T>
-struct Cols {
-  const T* c[kMaxObs];
-};
-
-template <typename T>
-__device__ __forceinline__ T pick(int col, T x0, T x1, T x2, T x3) {
-  return col == 0 ? x0 : (col == 1 ? x1 : (col == 2 ? x2 : x3));
-}
-
-// =======================================================================================
-// register-resident interpreter: before the event loop every thread copies the constants,
-// opcode and column of each leaf slot (k, l) into registers (compile-time indices), so the
-// per-event work is one uniform dispatch per leaf plus the leaf's arithmetic.  Absent leaf
-// slots carry opcode 0 (value 1, no derivative); absent products are excluded by k < nK.
-// =======================================================================================
-template <typename T>
-struct LeafReg {
-  int op, col;
-  T c[6];
-};
-
-template <typename T>
-__device__ __forceinline__ LeafReg<T> load_leaf(const LeafDev& L) {
-  LeafReg<T> R;
-  R.op = L.op;
-  R.col = L.col;
-#pragma unroll
-  for (int j = 0; j < 6; ++j) R.c[j] = (sizeof(T) == 4) ? (T)L.f[j] : (T)L.d[j];
-  return R;
-}
-
-// Per-call constants of the event kernels, passed by value as a kernel parameter: every
-// field is read with compile-time indices after unrolling, so the arithmetic takes it as a
-// constant-bank operand and it occupies no registers.  Absent leaf slots carry opcode 0.
-template <typename T, int K, int L>
-struct EvConst {
-  LeafReg<T> leaf[K][L];
-  T w_hi[K], w_lo[K];   // w_k (FP64 path: w_hi only)
-  int nK, nobs;
-};
-
-// Value r * exp(a) of one leaf at x (+ xlo, the low part of a double-float coordinate when
-// HasLo) and, if GRAD, d log(leaf) / d par_j.
-template <bool GRAD, bool HasLo = false>
-__device__ __forceinline__ void leaf_eval(const LeafReg<float>& L, float x, float& r, float& a, float* d,
-                                          float xlo = 0.f) {
-  const float* c = L.c;
-  d[0] = d[1] = d[2] = 0.f;
-  switch (L.op) {
-    case GOO_OP_GAUSS: {
-      const float z = (HasLo ? (x - c[0]) + (xlo - c[1]) : (x - c[0]) - c[1]) * c[2];
-      r = 1.f;
-      a = -0.5f * z * z;
-      if (GRAD) {
-        d[0] = z * c[2];
-        d[1] = z * z * c[2];
-      }
-      break;
-    }
-    case GOO_OP_EXPO:
-      r = 1.f;
-      a = HasLo ? fmaf(c[0], x, c[0] * xlo) : c[0] * x;
-      if (GRAD) d[0] = HasLo ? x + xlo : x;
-      break;
-    case GOO_OP_POLY2: {
-      const float xx = HasLo ? x + xlo : x;
-      r = fmaf(xx, fmaf(c[1], xx, c[0]), 1.f);
-      a = 0.f;
-      if (GRAD) {
-        const float ir = __fdividef(1.f, r);
-        d[0] = xx * ir;
-        d[1] = xx * xx * ir;
-      }
-      break;
-    }
-    case GOO_OP_ARGUS: {
-      const float u = HasLo ? ((c[0] - x) + (c[1] - xlo)) * ((c[0] + x) + (c[1] + xlo)) * c[2]
-                            : ((c[0] - x) + c[1]) * ((c[0] + x) + c[1]) * c[2];
-      if (u > 0.f) {
-        const float lu = __logf(u);
-        r = HasLo ? x + xlo : x;
-        a = fmaf(c[4], lu, c[3] * u);
-        if (GRAD) {
-          d[0] = c[5] * (1.f - u) * (__fdividef(c[4], u) + c[3]);
-          d[1] = u;
-          d[2] = lu;
-        }
-      } else {
-        r = 0.f;
-        a = 0.f;
-      }
-      break;
-    }
-    default:
-      r = 1.f;
-      a = 0.f;
-  }
-}
-
-template <bool GRAD, bool HasLo = false>
-__device__ __forceinline__ void leaf_eval(const LeafReg<double>& L, double x, double& r, double& a, double* d,
-                                          double xlo = 0.0) {
-  const double* c = L.c;
-  d[0] = d[1] = d[2] = 0.0;
-  switch (L.op) {
-    case GOO_OP_GAUSS: {
-      const double z = (x - c[0]) * c[1];
-      r = 1.0;
-      a = -0.5 * z * z;
-      if (GRAD) {
-        d[0] = z * c[1];
-        d[1] = z * z * c[1];
-      }
-      break;
-    }
-    case GOO_OP_EXPO:
-      r = 1.0;
-      a = c[0] * x;
-      if (GRAD) d[0] = x;
-      break;
-    case GOO_OP_POLY2:
-      r = 1.0 + x * (c[0] + c[1] * x);
-      a = 0.0;
-      if (GRAD) {
-        d[0] = x / r;
-        d[1] = x * x / r;
-      }
-      break;
-    case GOO_OP_ARGUS: {
-      const double u = (c[0] - x) * (c[0] + x) * c[1];
-      if (u > 0.0) {
-        const double lu = log(u);
-        r = x;
-        a = c[3] * lu + c[2] * u;
-        if (GRAD) {
-          d[0] = c[4] * (1.0 - u) * (c[3] / u + c[2]);
-          d[1] = u;
-          d[2] = lu;
-        }
-      } else {
-        r = 0.0;
-        a = 0.0;
-      }
-      break;
-    }
-    default:
-      r = 1.0;
-      a = 0.0;
-  }
-}
-
-// One event: log f (returned through logf) and, if GRAD, the shares c_k and the leaf
-// derivatives.  Returns false when f <= 0.
-template <typename T, int K, int L, bool GRAD>
-__device__ __forceinline__ bool eval_event(const EvConst<T, K, L>& P, const T (&off_hi)[K], const T (&off_lo)[K], T x0,
-                                           T x1, T x2, T x3, T& logf, T (&ck)[K], T (&dk)[K][L][3]) {
-  T rk[K], ak[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    T r = T(1), a = T(0);
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-      T lr_, la_;
-      leaf_eval<GRAD>(P.leaf[k][l], pick<T>(P.leaf[k][l].col, x0, x1, x2, x3), lr_, la_, dk[k][l]);
-      r *= lr_;
-      a += la_;
-    }
-    a = (a + off_hi[k]) + off_lo[k];
-    rk[k] = r;
-    ak[k] = (k < P.nK && r != T(0)) ? a : T(-1e30);
-  }
-  T M = ak[0];
-#pragma unroll
-  for (int k = 1; k < K; ++k) M = ak[k] > M ? ak[k] : M;
-  T S = T(0);
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if constexpr (sizeof(T) == 4) {
-      rk[k] = rk[k] * __expf(ak[k] - M);
-      S += fmaf(P.w_hi[k], rk[k], P.w_lo[k] * rk[k]);
-    } else {
-      rk[k] = rk[k] * exp(ak[k] - M);
-      S += P.w_hi[k] * rk[k];
-    }
-  }
-  if (!(S > T(0)) || !(M > T(-1e29))) return false;
-  if constexpr (sizeof(T) == 4) logf = M + __logf(S);
-  else logf = M + log(S);
-  if constexpr (GRAD) {
-    T invS;
-    if constexpr (sizeof(T) == 4) invS = __fdividef(1.f, S);
-    else invS = T(1) / S;
-#pragma unroll
-    for (int k = 0; k < K; ++k) ck[k] = rk[k] * invS;
-  }
-  return true;
-}
-
-// -log N_k of every product (written by the normalisation step) into registers.
-template <typename T, int K>
-__device__ __forceinline__ void load_offsets(const ModelDev* __restrict__ md, T (&off_hi)[K], T (&off_lo)[K]) {
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if constexpr (sizeof(T) == 4) {
-      off_hi[k] = md->comp[k].off_hi;
-      off_lo[k] = md->comp[k].off_lo;
-    } else {
-      off_hi[k] = -md->comp[k].log_norm;
-      off_lo[k] = 0.0;
-    }
-  }
-}
-
-// =======================================================================================
-// fused per-event kernel: evaluate, log, accumulate (and adjoint lanes), reduce
-// Lanes: 0 = sum log f; 1..K = C_k; then A_{k,l,j} at 1 + K + (k*L + l)*3 + j.
-// =======================================================================================
-template <typename T, int K, int L, bool GRAD>
-struct EventLanes {
-  static constexpr int NS = GRAD ? 1 + K + K * L * 3 : 1;
-};
-
-// Block reduction of the per-thread lanes, last-block reduction over the blocks and the
-// final FP64 combination (lanes -> NLL and d NLL / d theta), shared by the event kernels.
-// Constants of the self-contained FP32 event kernel, passed by value so that the kernel reads
-// no model block: per leaf slot the 1-D grid of its observable (separable grid normalisation)
-// and the final combination's weights, parameter map and d w / d theta.
-template <int K, int L, bool GRAD>
-struct EvNorm {
-  float lo_hi[K * L], lo_lo[K * L], h_hi[K * L], h_lo[K * L], aref_hi[K * L], aref_lo[K * L];
-  double h64[K * L];
-  int nb[K * L];                                   // bins (0: no leaf in the slot)
-  double w[K];                                     // w_k
-  int n_params;
-  signed char par[K][L][3];                        // parameter of leaf constant j (-1: none)
-  double dw[GRAD ? K : 1][GRAD ? kMaxParams : 1];  // d w_k / d theta_p
-};
-
-// Sources of the final combination's constants: the model block in device memory (MdFin), or
-// the kernel's by-value constants together with the normalisation terms the block computed
-// itself (ParFin; t[k L + l] = {h S, D_1 / S, D_2 / S, D_3 / S} of leaf slot (k, l)).
-struct MdFin {
-  const ModelDev* __restrict__ md;
-  int nK;
-  static constexpr bool kOwnNorm = false;
-  __device__ int n_params() const { return md->n_params; }
-  __device__ double w(int k) const { return k < nK ? md->comp[k].w : 0.0; }
-  __device__ double dw(int k, int p) const { return md->dw[k][p]; }
-  __device__ double dlogN(int k, int p) const { return md->dlogN[k][p]; }
-  __device__ int par(int k, int l, int j) const {
-    return (k < nK && l < md->comp[k].n_leaf) ? md->leaf[k * kMaxLeaf + l].par[j] : -1;
-  }
-  __device__ double term(int, int, int) const { return 0.0; }
-};
-
-template <int K, int L, bool GRAD>
-struct ParFin {
-  const EvNorm<K, L, GRAD>* N;
-  const double (*t)[4];
-  static constexpr bool kOwnNorm = true;
-  __device__ int n_params() const { return N->n_params; }
-  __device__ double w(int k) const { return N->w[k]; }
-  __device__ double dw(int k, int p) const {
-    if constexpr (GRAD) return N->dw[k][p];
-    else return 0.0;
-  }
-  __device__ double dlogN(int, int) const { return 0.0; }
-  __device__ int par(int k, int l, int j) const { return N->par[k][l][j]; }
-  __device__ double term(int k, int l, int j) const { return t[k * L + l][1 + j]; }
-};
-
-// Block reduction, last-block reduction over the blocks and the final FP64 combination
-// (lanes -> NLL and d NLL / d theta), shared by the event kernels:
-//   d NLL / d theta_p = sum_k [w_k C_k dlogN_kp - C_k dw_kp] - sum_{k,l,j: par = p} w_k A_klj,
-// with dlogN_kp = sum_{l,j: par = p} t_klj for a block's own normalisation terms.  Thread p
-// takes parameter p and gathers its terms in a fixed order.  The constants are loaded before
-// the block's reduction, so that their latency overlaps it; the last block alone combines.
-template <int K, int L, bool GRAD, typename Fin>
-__device__ __forceinline__ void event_finish(ddf (&v)[EventLanes<float, K, L, GRAD>::NS], unsigned bad, const Fin& F,
-                                             int nK, float2* partials, unsigned* counters, double* result,
-                                             int out_mode, ddf* s_red, unsigned* s_bad) {
-  constexpr int NS = EventLanes<float, K, L, GRAD>::NS;
-  __shared__ double s_out[NS];
-  __shared__ double s_w[K];
-  __shared__ int s_par[K][L][3];
-  const int p = threadIdx.x;
-  const int P = F.n_params();
-  double dwp[GRAD ? K : 1], dlp[GRAD ? K : 1];
-  if constexpr (GRAD) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const bool on = p < P && k < nK;
-      dwp[k] = on ? F.dw(k, p) : 0.0;
-      dlp[k] = (on && !Fin::kOwnNorm) ? F.dlogN(k, p) : 0.0;
-    }
-    for (int t = threadIdx.x; t < K * L * 3; t += blockDim.x) {
-      const int k = t / (L * 3), l = (t / 3) % L, jj = t % 3;
-      s_par[k][l][jj] = k < nK ? F.par(k, l, jj) : -1;
-    }
-    if (threadIdx.x < K) s_w[threadIdx.x] = F.w(threadIdx.x);
-  }
-  for (int m = 16; m > 0; m >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, m);
-  if ((threadIdx.x & 31) == 0) s_bad[threadIdx.x >> 5] = bad;
-  block_reduce_to_partials<NS>(v, NS, partials, s_red);
-  if (threadIdx.x == 0) {
-    unsigned b = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_bad[w];
-    if (b) atomicAdd(counters + 1, b);
-  }
-  if (!last_block_reduce(partials, NS, gridDim.x, counters, s_out, s_red)) return;
-
-  // ---- final combination (last block, FP64) ----
-  const int off = out_mode == 0 ? 2 : 3;
-  if (p < P) {
-    double gp = 0.0;
-    if constexpr (GRAD) {
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        if (k >= nK) break;
-        const double Ck = s_out[1 + k];
-        gp += s_w[k] * Ck * dlp[k] - Ck * dwp[k];
-      }
-#pragma unroll
-      for (int k = 0; k < K; ++k)
-#pragma unroll
-        for (int l = 0; l < L; ++l)
-#pragma unroll
-          for (int jj = 0; jj < 3; ++jj)
-            if (s_par[k][l][jj] == p)
-              gp += s_w[k] * ((Fin::kOwnNorm ? s_out[1 + k] * F.term(k, l, jj) : 0.0) -
-                              s_out[1 + K + (k * L + l) * 3 + jj]);
-    }
-    result[off + p] = gp;
-  }
-  if (threadIdx.x == 0) {
-    // every other block added to these words before its ticket (and a fence): plain L2 reads
-    const unsigned nbad = __ldcg(counters + 1);
-    const unsigned status = __ldcg(counters + kStatusWord);
-    counters[1] = 0u;
-    counters[kStatusWord] = 0u;
-    // a device wait that gave up is reported as a negative event count
-    const double nb = status ? -1.0 : (double)nbad;
-    result[0] = -s_out[0];
-    if (out_mode == 0) {
-      result[1] = nb;
-    } else {
-      result[1] = 0.0;
-      result[2] = nb;
-    }
-  }
-}
-
-// Resident blocks per SM the event kernel is compiled for: the FP32 form of the small shape
-// fits three 256-thread blocks (<= 80 registers) with its leaf constants in the parameter bank.
-template <typename T, int K, int L>
-struct EventOcc {
-  static constexpr int value = (sizeof(T) == 4 && K * L <= 6) ? 3 : 2;
-};
-
-// wcol (nullable): per-event weights w_i (a binned dataset: bin centres with their counts);
-// the lanes then sum w_i log f_i and w_i times the gradient terms, and events of weight 0 are
-// skipped.
-template <typename T, int K, int L, bool GRAD>
-__global__ void __launch_bounds__(kBlock, EventOcc<T, K, L>::value) sop_event_kernel(const ModelDev* __restrict__ md, const EvConst<T, K, L> P,
-                                                              Cols<T> cols, int64_t begin, int64_t end, float2* partials,
-                                                              unsigned* counters, double* result, int out_mode,
-                                                              const T* __restrict__ wcol) {
-  constexpr int NS = EventLanes<T, K, L, GRAD>::NS;
-  __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
-  __shared__ unsigned s_bad[kBlock / 32];
-  T off_hi[K], off_lo[K];
-  load_offsets<T, K>(md, off_hi, off_lo);
-  const int nK = P.nK;
-
-  // per-thread accumulators: FP32 path -> Kahan for sum log f, plain FP32 for the adjoint
-  // lanes; FP64 path -> plain FP64
-  using Acc = typename std::conditional<sizeof(T) == 4, float, double>::type;
-  double acc64 = 0.0;
-  Kahan acc32;
-  Acc Cacc[K];
-  Acc Aacc[K][L][3];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    Cacc[k] = Acc(0);
-#pragma unroll
-    for (int l = 0; l < L; ++l)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) Aacc[k][l][j] = Acc(0);
-  }
-  unsigned bad = 0;
-  const int nobs = P.nobs;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // software pipelining: the next event's columns are requested before this event is
-  // evaluated, so the loads' latency overlaps the arithmetic
-  int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  T n0 = T(0), n1 = T(0), n2 = T(0), n3 = T(0), nw = T(1);
-  if (i < end) {
-    n0 = cols.c[0][i];
-    n1 = nobs > 1 ? cols.c[1][i] : T(0);
-    n2 = nobs > 2 ? cols.c[2][i] : T(0);
-    n3 = nobs > 3 ? cols.c[3][i] : T(0);
-    if (wcol) nw = wcol[i];
-  }
-  for (; i < end; i += stride) {
-    const T x0 = n0, x1 = n1, x2 = n2, x3 = n3, wi = nw;
-    const int64_t inext = i + stride;
-    if (inext < end) {
-      n0 = cols.c[0][inext];
-      n1 = nobs > 1 ? cols.c[1][inext] : T(0);
-      n2 = nobs > 2 ? cols.c[2][inext] : T(0);
-      n3 = nobs > 3 ? cols.c[3][inext] : T(0);
-      if (wcol) nw = wcol[inext];
-    }
-    if (wcol && wi == T(0)) continue;  // an empty bin
-    T logf, ck[K], dk[K][L][3];
-    if (eval_event<T, K, L, GRAD>(P, off_hi, off_lo, x0, x1, x2, x3, logf, ck, dk)) {
-      if (wcol) {
-        logf *= wi;
-#pragma unroll
-        for (int k = 0; k < K; ++k) ck[k] *= wi;
-      }
-      if constexpr (sizeof(T) == 4) {
-        acc32.add(logf);
-      } else {
-        acc64 += logf;
-      }
-      if constexpr (GRAD) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          Cacc[k] += ck[k];
-#pragma unroll
-          for (int l = 0; l < L; ++l)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) Aacc[k][l][j] += ck[k] * dk[k][l][j];
-        }
-      }
-    } else {
-      bad++;
-    }
-  }
-
-  // ---- block reduction ----
-  ddf v[NS];
-  if constexpr (sizeof(T) == 4) {
-    v[0] = acc32.value();
-  } else {
-    v[0] = dd_from_double(acc64);
-  }
-  if constexpr (GRAD) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      v[1 + k] = (sizeof(T) == 4) ? ddf{(float)Cacc[k], 0.f} : dd_from_double((double)Cacc[k]);
-#pragma unroll
-      for (int l = 0; l < L; ++l)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-          v[1 + K + (k * L + l) * 3 + j] =
-              (sizeof(T) == 4) ? ddf{(float)Aacc[k][l][j], 0.f} : dd_from_double((double)Aacc[k][l][j]);
-    }
-  }
-  event_finish<K, L, GRAD>(v, bad, MdFin{md, nK}, nK, partials, counters, result, out_mode, s_red, s_bad);
-}
-
-// =======================================================================================
-// FP32 event kernel on packed pairs.  Each thread takes two consecutive events at a time and
-// evaluates both with the packed FP32 instructions of sm_100-class GPUs (add / sub / mul /
-// fma on .f32x2 register pairs), so the arithmetic, the leaf dispatch and the index work
-// each issue once per two events; exp2 / lg2 / rcp stay per lane.  Pairs are aligned to
-// even event indices (8-byte column loads); a lane outside [begin, end) is masked.  Each
-// lane is rounded exactly as a scalar FP32 evaluation of the same formulas.
-// =======================================================================================
-
-namespace pk {
-__device__ __forceinline__ float2 pick(int col, float2 x0, float2 x1, float2 x2, float2 x3) {
-  return col == 0 ? x0 : (col == 1 ? x1 : (col == 2 ? x2 : x3));
-}
-}  // namespace pk
-
-// Two events of one leaf: r * exp(a) per lane and, if GRAD, d log(leaf) / d par_j.
-template <bool GRAD>
-__device__ __forceinline__ void leaf_eval2(const LeafReg<float>& L, float2 x, float2& r, float2& a, float2* d) {
-  using namespace pk;
-  const float* c = L.c;
-  d[0] = d[1] = d[2] = splat(0.f);
-  switch (L.op) {
-    case GOO_OP_GAUSS: {
-      const float2 z = mul(sub(sub(x, splat(c[0])), splat(c[1])), splat(c[2]));
-      const float2 zz = mul(z, z);
-      r = splat(1.f);
-      a = mul(splat(-0.5f), zz);
-      if (GRAD) {
-        d[0] = mul(z, splat(c[2]));
-        d[1] = mul(zz, splat(c[2]));
-      }
-      break;
-    }
-    case GOO_OP_EXPO:
-      r = splat(1.f);
-      a = mul(splat(c[0]), x);
-      if (GRAD) d[0] = x;
-      break;
-    case GOO_OP_POLY2: {
-      r = fma(x, fma(splat(c[1]), x, splat(c[0])), splat(1.f));
-      a = splat(0.f);
-      if (GRAD) {
-        const float2 ir = rcp(r);
-        d[0] = mul(x, ir);
-        d[1] = mul(mul(x, x), ir);
-      }
-      break;
-    }
-    case GOO_OP_ARGUS: {
-      const float2 u = mul(mul(add(sub(splat(c[0]), x), splat(c[1])), add(add(splat(c[0]), x), splat(c[1]))), splat(c[2]));
-      // a lane with u <= 0 has value 0 (r = 0); u is replaced by 1 there to keep it finite
-      const bool p0 = u.x > 0.f, p1 = u.y > 0.f;
-      const float2 us = make_float2(p0 ? u.x : 1.f, p1 ? u.y : 1.f);
-      const float2 lu = pk::log(us);
-      r = make_float2(p0 ? x.x : 0.f, p1 ? x.y : 0.f);
-      a = fma(splat(c[4]), lu, mul(splat(c[3]), us));
-      if (GRAD) {
-        d[0] = mul(mul(splat(c[5]), sub(splat(1.f), us)), fma(splat(c[4]), rcp(us), splat(c[3])));
-        d[1] = us;
-        d[2] = lu;
-      }
-      break;
-    }
-    default:
-      r = splat(1.f);
-      a = splat(0.f);
-  }
-}
-
-// Two events: log f per lane, ok per lane (f > 0) and, if GRAD, c_k and the leaf derivatives.
-// xl[k][l] holds the observable of leaf l of product k.
-template <int K, int L, bool GRAD>
-__device__ __forceinline__ void eval_event2(const EvConst<float, K, L>& P, const float (&off_hi)[K],
-                                            const float (&off_lo)[K], const float2 (&xl)[K][L], float2& logf,
-                                            bool& ok0, bool& ok1, float2 (&ck)[K], float2 (&dk)[K][L][3]) {
-  using namespace pk;
-  float2 rk[K], ak[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    float2 r = splat(1.f), a = splat(0.f);
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-      float2 lr_, la_;
-      leaf_eval2<GRAD>(P.leaf[k][l], xl[k][l], lr_, la_, dk[k][l]);
-      r = mul(r, lr_);
-      a = add(a, la_);
-    }
-    a = add(add(a, splat(off_hi[k])), splat(off_lo[k]));
-    rk[k] = r;
-    const bool on = k < P.nK;
-    ak[k] = make_float2((on && r.x != 0.f) ? a.x : -1e30f, (on && r.y != 0.f) ? a.y : -1e30f);
-  }
-  float2 M = ak[0];
-#pragma unroll
-  for (int k = 1; k < K; ++k) M = make_float2(fmaxf(M.x, ak[k].x), fmaxf(M.y, ak[k].y));
-  float2 S = splat(0.f);
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    rk[k] = mul(rk[k], pk::exp(sub(ak[k], M)));
-    S = add(S, fma(splat(P.w_hi[k]), rk[k], mul(splat(P.w_lo[k]), rk[k])));
-  }
-  ok0 = S.x > 0.f && M.x > -1e29f;
-  ok1 = S.y > 0.f && M.y > -1e29f;
-  logf = add(M, pk::log(make_float2(ok0 ? S.x : 1.f, ok1 ? S.y : 1.f)));
-  if constexpr (GRAD) {
-    const float2 invS = rcp(S);
-#pragma unroll
-    for (int k = 0; k < K; ++k) ck[k] = mul(rk[k], invS);
-  }
-}
-
-// Compensated FP32 accumulator of an event pair (one Kahan sum per lane, packed).
-struct Kahan2 {
-  float2 s = {0.f, 0.f}, c = {0.f, 0.f};
-  __device__ __forceinline__ void add(float2 x) {
-    const float2 y = pk::sub(x, c);
-    const float2 t = pk::add(s, y);
-    c = pk::sub(pk::sub(t, s), y);
-    s = t;
-  }
-  __device__ __forceinline__ void add_lane(int lane, float x) {
-    float& sl = lane ? s.y : s.x;
-    float& cl = lane ? c.y : c.x;
-    const float y = x - cl;
-    const float t = sl + y;
-    cl = (t - sl) - y;
-    sl = t;
-  }
-};
-
-
-// Midpoint coordinate of bin idx of a 1-D grid as a double-float (the FP32 path's grid_coord).
-__device__ __forceinline__ void grid_coord_f(float lo_hi, float lo_lo, float h_hi, float h_lo, int64_t idx, float& x,
-                                             float& xlo) {
-  const float off = (float)idx + 0.5f;
-  const float p = off * h_hi;
-  const float perr = fmaf(off, h_hi, -p) + off * h_lo;
-  const ddf xs = dd_add({lo_hi, lo_lo}, dd_make(p, perr));
-  x = xs.hi;
-  xlo = xs.lo;
-}
-
-// Midpoint coordinate of bin idx of grid dimension d (double-float in the FP32 path).
-template <typename T>
-__device__ __forceinline__ void grid_coord(const GridDev& G, int d, int64_t idx, T& x, T& xlo) {
-  if constexpr (sizeof(T) == 4) {
-    grid_coord_f(G.lo_hi[d], G.lo_lo[d], G.h_hi[d], G.h_lo[d], idx, x, xlo);
-  } else {
-    x = G.lo64[d] + ((double)idx + 0.5) * G.h64[d];
-    xlo = 0.0;
-  }
-}
-
-// Separable grid normalisation inside the event kernel.  When every leaf of a product acts on
-// its own observable, log N_k = sum_l [log(h_l S_l) + a_l] with one 1-D midpoint sum S_l per
-// leaf (as grid_sep_kernel computes it), a few hundred leaf evaluations in all; every block
-// evaluates them itself at its start instead of waiting for a normalisation kernel, from
-// by-value constants only.  Warp w takes leaf slots w, w + 8, ...; its lanes stride the bins
-// in a fixed order, accumulate in double-float (exact products by fma) and reduce by a fixed
-// shuffle tree, so every block obtains bit-identical sums.  FP64 runs only in the last step,
-// in one warp with a lane per (slot, term) and per product: GB300's FP64 pipe is 1/64 of
-// FP32, and every block pays it.  s_term[k L + l] = {h S, D_1 / S, D_2 / S, D_3 / S} stays
-// for the final combination.
-template <int K, int L, bool GRAD>
-__device__ __forceinline__ void fused_grid_norm(const EvConst<float, K, L>& P, const EvNorm<K, L, GRAD>& N,
-                                                ddf (*s_raw)[4], double (*s_term)[4], float (*s_off)[2],
-                                                float (&off_hi)[K], float (&off_lo)[K]) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int sl = 0; sl < K * L; ++sl) {
-    if (sl % (kBlock / 32) != warp || N.nb[sl] == 0) continue;  // uniform over the warp
-    const LeafReg<float>& lr = P.leaf[sl / L][sl % L];
-    const float aref = N.aref_hi[sl], aref_lo = N.aref_lo[sl];
-    ddf acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    for (int i = lane; i < N.nb[sl]; i += 32) {
-      float x, xlo, r, a, dl[3];
-      grid_coord_f(N.lo_hi[sl], N.lo_lo[sl], N.h_hi[sl], N.h_lo[sl], i, x, xlo);
-      leaf_eval<true, true>(lr, x, r, a, dl, xlo);
-      const float U = r * expf((a - aref) - aref_lo);
-      acc[0] = dd_add(acc[0], ddf{U, 0.f});
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj) {
-        const float pr = U * dl[jj];
-        acc[1 + jj] = dd_add(acc[1 + jj], ddf{pr, fmaf(U, dl[jj], -pr)});
-      }
-    }
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) acc[jj] = dd_warp_sum(acc[jj]);
-    if (lane == 0)
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) s_raw[sl][jj] = acc[jj];
-  }
-  __syncthreads();
-  if (warp == 0) {
-    for (int t = lane; t < K * L * 4; t += 32) {
-      const int sl = t >> 2, jj = t & 3;
-      if (N.nb[sl] == 0) continue;
-      const double S = dd_to_double(s_raw[sl][0]);
-      s_term[sl][jj] = jj == 0 ? N.h64[sl] * S : dd_to_double(s_raw[sl][jj]) / S;
-    }
-    __syncwarp();
-    if (lane < K) {
-      double prod = 1.0, aref = 0.0;
-      for (int l = 0; l < L; ++l) {
-        const int sl = lane * L + l;
-        if (N.nb[sl] == 0) continue;
-        prod *= s_term[sl][0];
-        aref += (double)N.aref_hi[sl] + (double)N.aref_lo[sl];
-      }
-      const double logN = log(prod) + aref;
-      const float oh = (float)(-logN);
-      s_off[lane][0] = oh;
-      s_off[lane][1] = (float)(-logN - (double)oh);
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    off_hi[k] = s_off[k][0];
-    off_lo[k] = s_off[k][1];
-  }
-}
-
-constexpr int kEventStages = 3;     // column tiles in flight per block (TMA bulk copies)
-constexpr int kPairsPerThread = 4;  // event pairs per thread per tile
-
-template <int K, int L, bool GRAD>
-struct EventOcc2 {
-  static constexpr int value = (K * L <= 6 && !GRAD) ? 3 : 2;
-};
-
-// Per-thread accumulators of the pair kernel.
-template <int K, int L>
-struct PairAcc {
-  Kahan2 lf;
-  float2 C[K];
-  float2 A[K][L][3];
-  unsigned bad;
-};
-
-// One event pair: evaluate and accumulate the lanes that are in range (v0, v1) with f > 0.
-template <int K, int L, bool GRAD>
-__device__ __forceinline__ void pair_step(const EvConst<float, K, L>& P, const float (&off_hi)[K],
-                                          const float (&off_lo)[K], const float2 (&xl)[K][L], bool v0, bool v1,
-                                          PairAcc<K, L>& S) {
-  float2 logf, ck[K], dk[K][L][3];
-  bool ok0, ok1;
-  eval_event2<K, L, GRAD>(P, off_hi, off_lo, xl, logf, ok0, ok1, ck, dk);
-  const bool m0 = v0 && ok0, m1 = v1 && ok1;
-  S.bad += (unsigned)(v0 && !ok0) + (unsigned)(v1 && !ok1);
-  if (m0 && m1) {
-    S.lf.add(logf);
-    if constexpr (GRAD) {
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        S.C[k] = pk::add(S.C[k], ck[k]);
-#pragma unroll
-        for (int l = 0; l < L; ++l)
-#pragma unroll
-          for (int q = 0; q < 3; ++q) S.A[k][l][q] = pk::fma(ck[k], dk[k][l][q], S.A[k][l][q]);
-      }
-    }
-  } else {
-    // one lane outside the range or with f <= 0: accumulate the other lane alone
-#pragma unroll
-    for (int lane = 0; lane < 2; ++lane) {
-      if (!(lane ? m1 : m0)) continue;
-      S.lf.add_lane(lane, lane ? logf.y : logf.x);
-      if constexpr (GRAD) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          const float c = lane ? ck[k].y : ck[k].x;
-          (lane ? S.C[k].y : S.C[k].x) += c;
-#pragma unroll
-          for (int l = 0; l < L; ++l)
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-              float& A = lane ? S.A[k][l][q].y : S.A[k][l][q].x;
-              A = fmaf(c, lane ? dk[k][l][q].y : dk[k][l][q].x, A);
-            }
-        }
-      }
-    }
-  }
-}
-
-// Column tiles of TE = 2 * kPairsPerThread * kBlock events (aligned to multiples of TE)
-// are staged in shared memory by bulk copies, kEventStages tiles ahead; block b takes tiles
-// tb0 + b, tb0 + b + gridDim.x, ...  Within a tile thread t takes pairs t, t + kBlock, ...
-// Dynamic shared memory: kEventStages * n_obs * TE floats.
-template <int K, int L, bool GRAD>
-__global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
-    sop_event2_kernel(const ModelDev* __restrict__ md, const EvConst<float, K, L> P,
-                      const __grid_constant__ EvNorm<K, L, GRAD> N, Cols<float> cols, int64_t begin, int64_t end,
-                      float2* partials, unsigned* counters, double* result, int out_mode, int fused_norm) {
-  using namespace pk;
-  constexpr int NS = EventLanes<float, K, L, GRAD>::NS;
-  constexpr int PPT = kPairsPerThread;
-  constexpr int TE = 2 * PPT * kBlock;
-  constexpr int NST = kEventStages;
-  __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
-  __shared__ unsigned s_bad[kBlock / 32];
-  __shared__ __align__(8) uint64_t s_bar[NST];
-  __shared__ double s_term[K * L][4];
-  __shared__ ddf s_raw[K * L][4];
-  __shared__ float s_off[K][2];
-  extern __shared__ __align__(128) float s_col[];  // [NST][nobs][TE]
-  const int nobs = P.nobs;
-  const int64_t tb0 = begin / TE, tb1 = (end + TE - 1) / TE;
-  auto tile_of = [&](int j) { return tb0 + blockIdx.x + (int64_t)j * gridDim.x; };
-  auto full = [&](int64_t t) { return t * TE >= begin && (t + 1) * TE <= end; };
-  auto buf = [&](int st, int c) { return s_col + ((size_t)st * nobs + c) * TE; };
-  // one thread stages tile j in buffer j % NST: bulk copies for a full tile, a bare arrival
-  // (completes the phase at once) for a ragged one, which its threads read from global memory
-  auto issue = [&](int j) {
-    const int64_t t = tile_of(j);
-    if (t >= tb1) return;
-    uint64_t* bar = &s_bar[j % NST];
-    if (full(t)) {
-      mbar_arrive_expect_tx(bar, (unsigned)(nobs * TE * sizeof(float)));
-      for (int c = 0; c < nobs; ++c) bulk_load(buf(j % NST, c), cols.c[c] + t * TE, TE * sizeof(float), bar);
-    } else {
-      mbar_arrive(bar);
-    }
-  };
-  if (threadIdx.x == 0) {
-    for (int st = 0; st < NST; ++st) mbar_init(&s_bar[st], 1);
-    mbar_init_fence();
-    for (int j = 0; j < NST; ++j) issue(j);
-  }
-  // the column copies above read only the dataset; the normalisation written by the
-  // previous kernel in the stream is read after this point
-  grid_dep_wait();
-  float off_hi[K], off_lo[K];
-  const int nK = P.nK;
-  if (fused_norm) {
-    fused_grid_norm<K, L, GRAD>(P, N, s_raw, s_term, s_off, off_hi, off_lo);  // synchronises the block
-  } else {
-    load_offsets<float, K>(md, off_hi, off_lo);
-    __syncthreads();  // barriers initialised before any thread waits on them
-  }
-  PairAcc<K, L> S;
-  S.bad = 0;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    S.C[k] = splat(0.f);
-#pragma unroll
-    for (int l = 0; l < L; ++l)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) S.A[k][l][q] = splat(0.f);
-  }
-  int j = 0;
-  bool failed = false;
-  for (; tile_of(j) < tb1; ++j) {
-    const int64_t t = tile_of(j);
-    const int st = j % NST;
-    const bool ok_wait = mbar_wait(&s_bar[st], (unsigned)(j / NST) & 1u);
-    if (ok_wait) {
-      if (full(t)) {
-        // every event of the tile is in range: each leaf reads its own staged column (an
-        // unused leaf slot reads column 0 and is ignored)
-        int coff[K][L];
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-#pragma unroll
-          for (int l = 0; l < L; ++l) coff[k][l] = (st * nobs + P.leaf[k][l].col) * TE;
-#pragma unroll 1
-        for (int u = 0; u < PPT; ++u) {
-          const int pr = threadIdx.x + u * kBlock;
-          float2 xl[K][L];
-#pragma unroll
-          for (int k = 0; k < K; ++k)
-#pragma unroll
-            for (int l = 0; l < L; ++l) xl[k][l] = reinterpret_cast<const float2*>(s_col + coff[k][l])[pr];
-          pair_step<K, L, GRAD>(P, off_hi, off_lo, xl, true, true, S);
-        }
-      } else {
-#pragma unroll 1
-        for (int u = 0; u < PPT; ++u) {
-          const int64_t i = t * TE + 2 * (threadIdx.x + u * kBlock);
-          const bool v0 = i >= begin && i < end, v1 = i + 1 >= begin && i + 1 < end;
-          float2 x[kMaxObs];
-#pragma unroll
-          for (int c = 0; c < kMaxObs; ++c) {
-            x[c] = splat(0.f);
-            if (c < nobs) {
-              if (v0 && v1) x[c] = __ldg(reinterpret_cast<const float2*>(cols.c[c] + i));
-              else if (v0) x[c].x = cols.c[c][i];
-              else if (v1) x[c].y = cols.c[c][i + 1];
-            }
-          }
-          float2 xl[K][L];
-#pragma unroll
-          for (int k = 0; k < K; ++k)
-#pragma unroll
-            for (int l = 0; l < L; ++l) xl[k][l] = pick(P.leaf[k][l].col, x[0], x[1], x[2], x[3]);
-          if (v0 || v1) pair_step<K, L, GRAD>(P, off_hi, off_lo, xl, v0, v1, S);
-        }
-      }
-    }
-    // every thread is done with buffer st (and agrees on whether a wait gave up) before
-    // the buffer is refilled
-    if (__syncthreads_or(!ok_wait)) {
-      failed = true;
-      break;
-    }
-    if (threadIdx.x == 0) {
-      fence_proxy_async();  // the reads of buffer st precede the copy that overwrites it
-      issue(j + NST);
-    }
-  }
-  if (failed) {
-    // a copy did not arrive in time: record it, then wait (again bounded) for this block's
-    // copies still in flight before the block's shared memory is released
-    if (threadIdx.x == 0) {
-      atomicOr(counters + kStatusWord, 1u);
-      for (int jj = j; jj < j + NST && tile_of(jj) < tb1; ++jj) mbar_wait(&s_bar[jj % NST], (unsigned)(jj / NST) & 1u);
-    }
-    __syncthreads();
-  }
-  // lanes: the two Kahan sums as one double-float, the gradient lanes as the lane sums
-  ddf v[NS];
-  v[0] = dd_add(dd_make(S.lf.s.x, -S.lf.c.x), dd_make(S.lf.s.y, -S.lf.c.y));
-  if constexpr (GRAD) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      v[1 + k] = dd_add(ddf{S.C[k].x, 0.f}, ddf{S.C[k].y, 0.f});
-#pragma unroll
-      for (int l = 0; l < L; ++l)
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-          v[1 + K + (k * L + l) * 3 + q] = dd_add(ddf{S.A[k][l][q].x, 0.f}, ddf{S.A[k][l][q].y, 0.f});
-    }
-  }
-  if (fused_norm)
-    event_finish<K, L, GRAD>(v, S.bad, ParFin<K, L, GRAD>{&N, s_term}, nK, partials, counters, result, out_mode, s_red,
-                             s_bad);
-  else
-    event_finish<K, L, GRAD>(v, S.bad, MdFin{md, nK}, nK, partials, counters, result, out_mode, s_red, s_bad);
 }
 
 // =======================================================================================
@@ -1854,17 +951,29 @@ static int launch_event2(goo_model* m, const goo_dataset* ds, int64_t begin, int
   goo_ctx* ctx = m->ctx;
   constexpr int TE = 2 * kPairsPerThread * kBlock;
   const size_t smem = (size_t)kEventStages * m->host.n_obs * TE * sizeof(float);
+  // room for the largest column count, so one setting serves every model on this device
+  const size_t smem_max = (size_t)kEventStages * kMaxObs * TE * sizeof(float);
   static bool configured[kMaxDevicesEv] = {};
   if (ctx->device < 0 || ctx->device >= kMaxDevicesEv) return set_error(GOO_ERR_ARG, "device %d", ctx->device);
-  if (!configured[ctx->device]) {
-    // room for the largest column count, so one setting serves every model on this device
-    GOO_CUDA_TRY(cudaFuncSetAttribute(sop_event2_kernel<K, L, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)((size_t)kEventStages * kMaxObs * TE * sizeof(float))));
+  const void* fn = (const void*)sop_event2_kernel<K, L, GRAD>;
+  m->jit_status = m->jit_mode;
+  if (m->jit_mode) {
+    // the kernel specialised for this model's leaf signature (jit.cu), else the interpreter
+    unsigned long long sig = 0;
+    for (int k = 0; k < m->host.nK && k < K; ++k)
+      for (int l = 0; l < m->host.comp[k].n_leaf && l < L; ++l)
+        sig |= (unsigned long long)(m->host.leaf[k * kMaxLeaf + l].op & 15) << (4 * (k * L + l));
+    int st = 0;
+    const void* jf = jit_event2_kernel(ctx->device, K, L, GRAD, sig, smem_max, &st);
+    m->jit_status = st;
+    if (jf) fn = jf;
+  }
+  if (fn == (const void*)sop_event2_kernel<K, L, GRAD> && !configured[ctx->device]) {
+    GOO_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
     configured[ctx->device] = true;
   }
   int bps = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, sop_event2_kernel<K, L, GRAD>, kBlock, smem) != cudaSuccess ||
-      bps < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, smem) != cudaSuccess || bps < 1) {
     cudaGetLastError();
     bps = 1;
   }
@@ -1891,10 +1000,15 @@ static int launch_event2(goo_model* m, const goo_dataset* ds, int64_t begin, int
     EvNorm<K, L, GRAD> N;
     if (fused_norm) N = make_evnorm<K, L, GRAD>(*m->stage);
     else std::memset(&N, 0, sizeof N);
-    GOO_CUDA_TRY(cudaLaunchKernelEx(&cfg, sop_event2_kernel<K, L, GRAD>, (const ModelDev*)m->dev,
-                                    make_evconst<float, K, L>(*m->stage), N, cols, begin, end,
-                                    ctx->scratch.partials, ctx->scratch.counters, ctx->scratch.result, out_mode,
-                                    (int)fused_norm));
+    // the argument list of sop_event2_kernel, for the interpreter and the specialised kernel
+    const ModelDev* md = m->dev;
+    EvConst<float, K, L> P = make_evconst<float, K, L>(*m->stage);
+    float2* partials = ctx->scratch.partials;
+    unsigned* counters = ctx->scratch.counters;
+    double* result = ctx->scratch.result;
+    int fused = (int)fused_norm;
+    void* args[] = {&md, &P, &N, &cols, &begin, &end, &partials, &counters, &result, &out_mode, &fused};
+    GOO_CUDA_TRY(cudaLaunchKernelExC(&cfg, fn, args));
   }
   GOO_CUDA_TRY(cudaGetLastError());
   return GOO_OK;

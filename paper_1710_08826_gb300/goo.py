@@ -130,6 +130,8 @@ def _load():
         "goo_faddeeva": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]),
         "goo_model_set_lineshapes": (ctypes.c_int, [vp, ctypes.c_int]),
         "goo_model_set_coefficients": (ctypes.c_int, [vp, ctypes.c_int]),
+        "goo_model_set_jit": (ctypes.c_int, [vp, ctypes.c_int]),
+        "goo_model_jit_status": (ctypes.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -513,6 +515,18 @@ class Model:
                            ctypes.byref(res)))
         info = {k: getattr(res, k) for k, _ in GooFitResult._fields_}
         return th.copy(), err, info
+
+    def set_jit(self, on):
+        """Run-time specialisation of the FP32 event kernel for this model (goo_model_set_jit):
+        True (default) compiles the kernel for the model's leaf signature on first use, False
+        keeps the library's interpreter."""
+        _check(lib.goo_model_set_jit(self.handle, 1 if on else 0))
+
+    @property
+    def jit_status(self):
+        """0 off, 1 on and unused, 2 the last FP32 evaluation ran the specialised kernel, -1
+        compilation failed (the interpreter ran)."""
+        return int(lib.goo_model_jit_status(self.handle))
 
     def set_lineshapes(self, mode):
         """'cached' (default: masses and widths are constants of the amplitude cache, their

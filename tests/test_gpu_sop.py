@@ -244,3 +244,60 @@ def test_c2_full_size(goo, ctx, precision):
     # a shifted point
     scale = np.maximum(np.abs(rg), np.sqrt(len(cols["m"])) * 1e-2)
     assert np.all(np.abs(g - rg) <= TOL_GRAD[precision] * np.max(scale) + 1e-12), (g, rg)
+
+
+SPECIALISED_SPECS = {
+    "c1": (synth.c1_spec, lambda: synth.gen_c1(), 1.02),
+    "c2": (synth.c2_spec, lambda: synth.gen_c2(n=150_000, seed=51), 1.002),
+}
+
+
+@pytest.mark.parametrize("precision_grad", [("f32", True), ("f32", False)])
+@pytest.mark.parametrize("which", ["c1", "c2"])
+def test_specialised_and_interpreted_kernels_match_oracle(goo, ctx, which, precision_grad):
+    # the FP32 event kernel compiled for the model's leaf signature at run time and the
+    # library's interpreter: both against the oracle, and against each other
+    precision, grad = precision_grad
+    mk, gen, off = SPECIALISED_SPECS[which]
+    spec = mk()
+    cols = _data(spec, gen(), precision)
+    theta = np.array(synth.param_values(spec)) * off
+    ds = goo.Dataset.from_spec(ctx, spec, cols)
+    out = {}
+    for jit in (True, False):
+        model = goo.Model(ctx, spec)
+        model.set_jit(jit)
+        out[jit] = model.nll_grad(ds, theta, precision) if grad else (model.nll(ds, theta, precision), None)
+        assert model.jit_status == (2 if jit else 0)
+    ref = om.TreeModel(spec)
+    rnll, rg = ref.nll_grad(cols, theta)
+    for jit in (True, False):
+        nll, g = out[jit]
+        assert abs(nll - rnll) <= TOL_NLL[precision] * abs(rnll), (jit, nll, rnll)
+        if grad:
+            assert np.max(np.abs(g - rg)) <= TOL_GRAD[precision] * np.max(np.abs(rg)), (jit, g, rg)
+    assert abs(out[True][0] - out[False][0]) <= 1e-7 * abs(rnll)
+
+
+def test_specialised_kernel_on_sparse_and_nested_signatures(goo, ctx):
+    # products with fewer leaves than the kernel's slots and the leaf types in other slots,
+    # with and without gradient
+    spec = synth.c2_spec(bins=32)
+    spec["pdf"] = ("add", ["frac"], [
+        ("prod", [("expo", "t", "lam_s"), ("gauss", "m", "mu_m", "sig_m")]),
+        ("prod", [("poly2", "dE", "a1", "a2"), ("argus", "m", "m0", "c", "p"), ("expo", "t", "lam_b")]),
+    ])
+    cols = _data(spec, synth.gen_c2(n=60_000, seed=52), "f32")
+    theta = np.array(synth.param_values(spec)) * 1.003
+    for grad in (True, False):
+        ds = goo.Dataset.from_spec(ctx, spec, cols)
+        model = goo.Model(ctx, spec)
+        ref = om.TreeModel(spec)
+        if grad:
+            nll, g = model.nll_grad(ds, theta, "f32")
+            rnll, rg = ref.nll_grad(cols, theta)
+            assert np.max(np.abs(g - rg)) <= TOL_GRAD["f32"] * np.max(np.abs(rg))
+        else:
+            nll, rnll = model.nll(ds, theta, "f32"), ref.nll(cols, theta)
+        assert abs(nll - rnll) <= TOL_NLL["f32"] * abs(rnll)
+        assert model.jit_status == 2
