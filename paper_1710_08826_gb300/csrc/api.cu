@@ -3,6 +3,8 @@
 // Paper: the FitManager evaluates the final PDF on an unbinned DataSet (Fig. 1); most of the
 // time of a fit is the per-event evaluation (Sec. 1); MPI splits the events among processes
 // (Sec. 4).
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstddef>
 #include <cstring>
@@ -36,6 +38,24 @@ int check_theta(const goo_model* m, const double* theta) {
   return GOO_OK;
 }
 
+// Waits for the completion word of the mapped result record that an event kernel writes
+// (sop_events with result = scratch.result_host), then copies `n` doubles.  The host polls
+// the word for up to 2 ms, then waits on the stream, which also reports a failed launch.
+int read_result_mapped(goo_ctx* ctx, int n, double* dst) {
+  volatile double* flag = ctx->scratch.result_host + kResultFlag;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (unsigned it = 0; *flag == 0.0; ++it) {
+    if ((it & 255u) == 0 && std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(2)) {
+      GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+      if (*flag == 0.0) return set_error(GOO_ERR_STATE, "the event kernel finished without its completion word");
+      break;
+    }
+  }
+  std::atomic_thread_fence(std::memory_order_acquire);
+  std::memcpy(dst, (const double*)ctx->scratch.result_host, n * sizeof(double));
+  return GOO_OK;
+}
+
 // Reads `n` result doubles into the pinned staging area and waits for the stream.
 int read_result(goo_ctx* ctx, int n, double* dst) {
   double* stage = ctx->scratch.host_pinned + kPinnedResult;
@@ -60,14 +80,15 @@ int nll_common(goo_model* m, const goo_dataset* ds, const double* theta, int pre
   } else {
     const bool fuse = ds->n > 0 && !ds->w64 && sop_norm_in_event(m, precision, grad);
     GOO_TRY(sop_prepare(m, theta, precision, fuse));
-    GOO_TRY(sop_events(m, ds, 0, ds->n, precision, grad, 0, fuse));
+    ctx->scratch.result_host[kResultFlag] = 0.0;
+    if (ds->n > 0) GOO_TRY(sop_events(m, ds, 0, ds->n, precision, grad, 0, fuse, ctx->scratch.result_host));
     if (ds->n == 0) {
       res[0] = 0.0;
       res[1] = 0.0;
       for (int p = 0; p < P; ++p) res[2 + p] = 0.0;
       GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     } else {
-      GOO_TRY(read_result(ctx, 2 + P, res));
+      GOO_TRY(read_result_mapped(ctx, 2 + P, res));
     }
   }
   if (res[1] < 0) {
@@ -227,8 +248,9 @@ int goo_nll_partial(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t 
     const bool fuse = end > begin && !ds->w64 && sop_norm_in_event(m, precision, want_grad != 0);
     GOO_TRY(sop_prepare(m, theta, precision, fuse));
     if (end > begin) {
-      GOO_TRY(sop_events(m, ds, begin, end, precision, want_grad != 0, 1, fuse));
-      GOO_TRY(read_result(ctx, 3 + P, res));
+      ctx->scratch.result_host[kResultFlag] = 0.0;
+      GOO_TRY(sop_events(m, ds, begin, end, precision, want_grad != 0, 1, fuse, ctx->scratch.result_host));
+      GOO_TRY(read_result_mapped(ctx, 3 + P, res));
     } else {
       GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
       for (int i = 0; i < 3 + P; ++i) res[i] = 0.0;

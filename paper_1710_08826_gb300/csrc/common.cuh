@@ -64,6 +64,10 @@ constexpr int kStagedBlock = 512;
 constexpr int kBlock = 256;        // threads per block of the likelihood kernels
 constexpr int kResultDoubles = 4 + kMaxParams + 60;  // result record of one evaluation
 constexpr int kPinnedResult = 256;                   // offset of the result in host_pinned
+// Completion word after the result record: the sum-of-products event kernels set it to 1
+// once the record is written, so a host can poll a mapped record instead of synchronising
+// the stream (every result buffer holds kResultDoubles + 1 doubles).
+constexpr int kResultFlag = kResultDoubles;
 
 #ifndef __CUDACC_RTC__
 // ---------------------------------------------------------------------------------------
@@ -79,6 +83,9 @@ struct Scratch {
   double* result = nullptr;         // kResultDoubles doubles
   double* theta = nullptr;          // kMaxParams doubles
   double* host_pinned = nullptr;    // pinned staging: [0, 256) theta in, [256, 512) result out
+  // result record in mapped pinned host memory (kResultDoubles + 1 doubles, the device writes
+  // it over the host link): the sum-of-products path reads its result here without a copy
+  double* result_host = nullptr;
 };
 
 }  // namespace goo

@@ -331,7 +331,9 @@ int goo_init(int device, void* cuda_stream, goo_ctx** out) {
   Scratch& s = ctx->scratch;
   GOO_CUDA_TRY(cudaMalloc(&s.counters, 64 * sizeof(unsigned)));
   GOO_CUDA_TRY(cudaMemset(s.counters, 0, 64 * sizeof(unsigned)));
-  GOO_CUDA_TRY(cudaMalloc(&s.result, kResultDoubles * sizeof(double)));
+  GOO_CUDA_TRY(cudaMalloc(&s.result, (kResultDoubles + 1) * sizeof(double)));
+  GOO_CUDA_TRY(cudaHostAlloc(&s.result_host, (kResultDoubles + 1) * sizeof(double), cudaHostAllocMapped));
+  std::memset(s.result_host, 0, (kResultDoubles + 1) * sizeof(double));
   GOO_CUDA_TRY(cudaMalloc(&s.theta, 2 * kMaxParams * sizeof(double)));
   GOO_CUDA_TRY(cudaMallocHost(&s.host_pinned, 512 * sizeof(double)));
   int rc = ensure_partials(ctx, 65536);
@@ -355,6 +357,7 @@ int goo_finalize(goo_ctx* ctx) {
   if (s.result) cudaFree(s.result);
   if (s.theta) cudaFree(s.theta);
   if (s.host_pinned) cudaFreeHost(s.host_pinned);
+  if (s.result_host) cudaFreeHost(s.result_host);
   fold_timings(ctx);
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   if (ctx->owns_stream) cudaStreamDestroy(ctx->stream);

@@ -887,7 +887,8 @@ static EvConst<T, K, L> make_evconst(const ModelDev& h) {
 }
 
 template <typename T, int K, int L, bool GRAD>
-static int launch_event_T(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int out_mode) {
+static int launch_event_T(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int out_mode,
+                          double* result) {
   const T* wcol = sizeof(T) == 4 ? (const T*)(const void*)ds->w32 : (const T*)(const void*)ds->w64;
   goo_ctx* ctx = m->ctx;
   static int occ = 0;
@@ -904,8 +905,7 @@ static int launch_event_T(goo_model* m, const goo_dataset* ds, int64_t begin, in
     LaunchScope ls(ctx, sizeof(T) == 4 ? (GRAD ? "sop_nll_grad_f32" : "sop_nll_f32") : (GRAD ? "sop_nll_grad_f64" : "sop_nll_f64"));
     sop_event_kernel<T, K, L, GRAD><<<nb, kBlock, 0, ctx->stream>>>(m->dev, make_evconst<T, K, L>(*m->stage), cols,
                                                                    begin, end, ctx->scratch.partials,
-                                                                   ctx->scratch.counters, ctx->scratch.result, out_mode,
-                                                                   wcol);
+                                                                   ctx->scratch.counters, result, out_mode, wcol);
   }
   GOO_CUDA_TRY(cudaGetLastError());
   return GOO_OK;
@@ -947,7 +947,7 @@ static EvNorm<K, L, GRAD> make_evnorm(const ModelDev& h) {
 
 template <int K, int L, bool GRAD>
 static int launch_event2(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int out_mode,
-                         bool fused_norm) {
+                         bool fused_norm, double* result) {
   goo_ctx* ctx = m->ctx;
   constexpr int TE = 2 * kPairsPerThread * kBlock;
   const size_t smem = (size_t)kEventStages * m->host.n_obs * TE * sizeof(float);
@@ -1005,7 +1005,6 @@ static int launch_event2(goo_model* m, const goo_dataset* ds, int64_t begin, int
     EvConst<float, K, L> P = make_evconst<float, K, L>(*m->stage);
     float2* partials = ctx->scratch.partials;
     unsigned* counters = ctx->scratch.counters;
-    double* result = ctx->scratch.result;
     int fused = (int)fused_norm;
     void* args[] = {&md, &P, &N, &cols, &begin, &end, &partials, &counters, &result, &out_mode, &fused};
     GOO_CUDA_TRY(cudaLaunchKernelExC(&cfg, fn, args));
@@ -1016,23 +1015,24 @@ static int launch_event2(goo_model* m, const goo_dataset* ds, int64_t begin, int
 
 template <typename T, bool GRAD>
 static int launch_event_sel(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int out_mode,
-                            bool fused_norm) {
+                            bool fused_norm, double* result) {
   if constexpr (sizeof(T) == 4) {
     // packed pairs, except the largest shape with gradient lanes (its pair accumulators do
     // not fit in registers) and weighted datasets (the scalar kernel carries the weights)
     if (!ds->w32) {
       if (m->host.nK <= 2 && m->max_leaf <= 3)
-        return launch_event2<2, 3, GRAD>(m, ds, begin, end, out_mode, fused_norm);
-      if constexpr (!GRAD) return launch_event2<4, 4, GRAD>(m, ds, begin, end, out_mode, fused_norm);
+        return launch_event2<2, 3, GRAD>(m, ds, begin, end, out_mode, fused_norm, result);
+      if constexpr (!GRAD) return launch_event2<4, 4, GRAD>(m, ds, begin, end, out_mode, fused_norm, result);
     }
   }
   if (fused_norm) return set_error(GOO_ERR_STATE, "sop_events: in-kernel normalisation needs the pair kernel");
-  if (m->host.nK <= 2 && m->max_leaf <= 3) return launch_event_T<T, 2, 3, GRAD>(m, ds, begin, end, out_mode);
-  return launch_event_T<T, 4, 4, GRAD>(m, ds, begin, end, out_mode);
+  if (m->host.nK <= 2 && m->max_leaf <= 3) return launch_event_T<T, 2, 3, GRAD>(m, ds, begin, end, out_mode, result);
+  return launch_event_T<T, 4, 4, GRAD>(m, ds, begin, end, out_mode, result);
 }
 
 int sop_events(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int precision, bool grad, int out_mode,
-               bool norm_in_event) {
+               bool norm_in_event, double* result) {
+  if (!result) result = m->ctx->scratch.result;
   if (end <= begin) {
     // empty range: write a zero result without a kernel
     double z[3 + kMaxParams] = {0};
@@ -1040,12 +1040,12 @@ int sop_events(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, 
     return GOO_OK;
   }
   if (precision == GOO_F32) {
-    return grad ? launch_event_sel<float, true>(m, ds, begin, end, out_mode, norm_in_event)
-                : launch_event_sel<float, false>(m, ds, begin, end, out_mode, norm_in_event);
+    return grad ? launch_event_sel<float, true>(m, ds, begin, end, out_mode, norm_in_event, result)
+                : launch_event_sel<float, false>(m, ds, begin, end, out_mode, norm_in_event, result);
   }
   if (norm_in_event) return set_error(GOO_ERR_STATE, "sop_events: in-kernel normalisation is FP32 only");
-  return grad ? launch_event_sel<double, true>(m, ds, begin, end, out_mode, false)
-              : launch_event_sel<double, false>(m, ds, begin, end, out_mode, false);
+  return grad ? launch_event_sel<double, true>(m, ds, begin, end, out_mode, false, result)
+              : launch_event_sel<double, false>(m, ds, begin, end, out_mode, false, result);
 }
 
 template <typename T, int K, int L>
@@ -1097,7 +1097,7 @@ constexpr size_t kStOffModel = 0;
 constexpr size_t kStOffTheta = (sizeof(ModelDev) + 255) / 256 * 256;
 constexpr size_t kStOffCounters = kStOffTheta + 256;
 constexpr size_t kStOffResult = kStOffCounters + 256;
-constexpr size_t kStOffPartials = kStOffResult + kResultDoubles * sizeof(double);
+constexpr size_t kStOffPartials = kStOffResult + (kResultDoubles + 1 + 1) / 2 * 2 * sizeof(double);
 constexpr int kStaticMaxParams = 32;  // documented limit of goo_nll_grad_static
 constexpr size_t kStPartialsCap = (kStaticScratchBytes - kStOffPartials) / sizeof(float2);
 static_assert(kStOffPartials < kStaticScratchBytes, "static scratch too small for the model block");
