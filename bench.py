@@ -32,7 +32,7 @@ BYTES_PER_EVENT_F64 = 24
 # in "profile"): DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and, for the FP64
 # kernels, the FP64 pipe's active fraction (sm__pipe_fp64_cycles_active).  A record is used
 # only while the kernel's sources still hash to the captured value; bytes scale with events.
-_SOP_SRC = ['paper_1710_08826_gb300/csrc/tree.cu', 'paper_1710_08826_gb300/csrc/common.cuh', 'paper_1710_08826_gb300/csrc/model.cuh']
+_SOP_SRC = ['paper_1710_08826_gb300/csrc/tree.cu', 'paper_1710_08826_gb300/csrc/sop_kernels.cuh', 'paper_1710_08826_gb300/csrc/jit.cu', 'paper_1710_08826_gb300/csrc/common.cuh', 'paper_1710_08826_gb300/csrc/model.cuh']
 _COH_SRC = ['paper_1710_08826_gb300/csrc/dalitz.cu', 'paper_1710_08826_gb300/csrc/dalitz.cuh', 'paper_1710_08826_gb300/csrc/common.cuh', 'paper_1710_08826_gb300/csrc/model.cuh']
 _TD4_SRC = ['paper_1710_08826_gb300/csrc/td4.cu', 'paper_1710_08826_gb300/csrc/dalitz.cuh', 'paper_1710_08826_gb300/csrc/common.cuh', 'paper_1710_08826_gb300/csrc/model.cuh', 'paper_1710_08826_gb300/csrc/timeterms.cuh']
 _TD3_SRC = _COH_SRC + ['paper_1710_08826_gb300/csrc/timeterms.cuh']
@@ -792,7 +792,9 @@ def c5_study(goo, ctx, n_toys=4096, rate=None, plain_sample=8, n_mc=1_000_000, s
 def run_profile(args):
     """Short fixed launch sequences for ncu captures.
 
-    c2: [grid, event] x 4 FP32+grad evaluations, then one FP64 evaluation (10M events).
+    c2: 4 FP32+grad evaluations (one event kernel each: the kernel specialised for the model
+        at run time, normalising the grid itself), then one FP64 evaluation (grid kernel, then
+        the scalar event kernel), 10M events.
     c3: amplitude caches and Gram (first call), then 4 FP32+grad and 1 FP64 coherent
         evaluations on 5M events generated on the device.
     c3f: the same events with floating lineshapes: 4 FP32+grad evaluations (an MC pass and an

@@ -28,6 +28,21 @@ struct Cond<false, A, B> {
 // Opcode of leaf slot `slot` in a compile-time signature (0 when SIG holds none).
 __host__ __device__ constexpr int sig_op(unsigned long long sig, int slot) { return (int)((sig >> (4 * slot)) & 15ull); }
 
+
+// Leaves whose value carries a factor r besides exp(a) (the others have r = 1, so a
+// specialised kernel skips their products with r), and whether product k of a signature has
+// such a leaf or any leaf at all.
+__host__ __device__ constexpr bool leaf_has_r(int op) { return op == GOO_OP_POLY2 || op == GOO_OP_ARGUS; }
+__host__ __device__ constexpr bool sig_product_has_r(unsigned long long sig, int k, int L) {
+  bool any = false;
+  for (int l = 0; l < L; ++l) any = any || leaf_has_r(sig_op(sig, k * L + l));
+  return any;
+}
+__host__ __device__ constexpr bool sig_product_used(unsigned long long sig, int k, int L) {
+  bool any = false;
+  for (int l = 0; l < L; ++l) any = any || sig_op(sig, k * L + l) != 0;
+  return any;
+}
 // Number of parameters (derivative lanes) of a leaf opcode.
 __host__ __device__ constexpr int leaf_nder(int op) {
   return op == GOO_OP_GAUSS ? 2 : op == GOO_OP_EXPO ? 1 : op == GOO_OP_POLY2 ? 2 : op == GOO_OP_ARGUS ? 3 : 0;
@@ -595,12 +610,12 @@ __device__ __forceinline__ void eval_event2(const EvConst<float, K, L>& P, const
       }
       leaf_eval2<GRAD>(P.leaf[k][l], SIG != 0 ? sig_op(SIG, k * L + l) : P.leaf[k][l].op, xl[k][l], lr_, la_,
                        dk[k][l]);
-      r = mul(r, lr_);
+      if (SIG == 0 || leaf_has_r(sig_op(SIG, k * L + l))) r = mul(r, lr_);
       a = add(a, la_);
     }
     a = add(add(a, splat(off_hi[k])), splat(off_lo[k]));
     rk[k] = r;
-    const bool on = k < P.nK;
+    const bool on = SIG != 0 ? sig_product_used(SIG, k, L) : k < P.nK;
     ak[k] = make_float2((on && r.x != 0.f) ? a.x : -1e30f, (on && r.y != 0.f) ? a.y : -1e30f);
   }
   float2 M = ak[0];
@@ -609,7 +624,7 @@ __device__ __forceinline__ void eval_event2(const EvConst<float, K, L>& P, const
   float2 S = splat(0.f);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    rk[k] = mul(rk[k], pk::exp(sub(ak[k], M)));
+    rk[k] = (SIG == 0 || sig_product_has_r(SIG, k, L)) ? mul(rk[k], pk::exp(sub(ak[k], M))) : pk::exp(sub(ak[k], M));
     S = add(S, fma(splat(P.w_hi[k]), rk[k], mul(splat(P.w_lo[k]), rk[k])));
   }
   ok0 = S.x > 0.f && M.x > -1e29f;
