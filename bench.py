@@ -41,33 +41,33 @@ _TD3_SRC = _COH_SRC + ['paper_1710_08826_gb300/csrc/timeterms.cuh']
 ISSUE_PEAK = 152 * 4 * 2.07e9
 
 NCU_RECORDS = {
-    "sop_nll_grad_f32": {"bytes": 125_935_360, "events": 10_000_000, "sources": _SOP_SRC,
-                         "sha256": "903706de40bde32cb76d7456474a8c09d23988d39e4de0caad990ffbe819fea2",
+    "sop_nll_grad_f32": {"bytes": 125_870_080, "events": 10_000_000, "sources": _SOP_SRC,
+                         "sha256": "954818e6736e4c5149a820119fc88e5868aba2bfe3ffb9b0ea372c43b12ece4f",
                          "profile": "profiles/sop_event2_kernel_f32_c2_10M.md"},
-    "sop_nll_f64": {"bytes": 243_334_400, "events": 10_000_000, "fp64_pipe": 0.8631, "sources": _SOP_SRC,
-                    "sha256": "903706de40bde32cb76d7456474a8c09d23988d39e4de0caad990ffbe819fea2",
+    "sop_nll_f64": {"bytes": 243_810_560, "events": 10_000_000, "fp64_pipe": 0.8625, "sources": _SOP_SRC,
+                    "sha256": "954818e6736e4c5149a820119fc88e5868aba2bfe3ffb9b0ea372c43b12ece4f",
                     "profile": "profiles/sop_event_kernel_f64_c2_10M.md"},
-    "coh_nll_grad_f32": {"bytes": 323_768_832, "events": 5_000_000, "sources": _COH_SRC,
-                         "sha256": "4fdd73a53f82ab80d472525c791363ef014ad99c4e86ef7718bc5d08feae1355",
+    "coh_nll_grad_f32": {"bytes": 323_320_832, "events": 5_000_000, "sources": _COH_SRC,
+                         "sha256": "da0eac6817ec057e6710736663a05d6cc87b64eca728f7d685aceb7bca51cafe",
                          "profile": "profiles/coh_nll_staged_kernel_f32_c3_5M.md"},
-    "coh_nll_f64": {"bytes": 643_385_600, "events": 5_000_000, "fp64_pipe": 0.8702, "sources": _COH_SRC,
-                    "sha256": "4fdd73a53f82ab80d472525c791363ef014ad99c4e86ef7718bc5d08feae1355",
+    "coh_nll_f64": {"bytes": 643_298_304, "events": 5_000_000, "fp64_pipe": 0.8700, "sources": _COH_SRC,
+                    "sha256": "da0eac6817ec057e6710736663a05d6cc87b64eca728f7d685aceb7bca51cafe",
                     "profile": "profiles/coh_nll_kernel_f64_c3_5M.md"},
-    "coh_ls_grad_f32": {"bytes": 40_093_952, "events": 5_000_000, "warp_inst": 308_097_098, "issue_active": 0.6431,
+    "coh_ls_grad_f32": {"bytes": 40_095_232, "events": 5_000_000, "warp_inst": 313_731_049, "issue_active": 0.6453,
                         "sources": _COH_SRC,
-                        "sha256": "4fdd73a53f82ab80d472525c791363ef014ad99c4e86ef7718bc5d08feae1355",
+                        "sha256": "da0eac6817ec057e6710736663a05d6cc87b64eca728f7d685aceb7bca51cafe",
                         "profile": "profiles/coh_ls_kernel_f32_c3_floating_5M.md"},
-    "td3_nll_grad_f32": {"bytes": 523_443_968, "events": 2_000_000, "sources": _TD3_SRC,
-                         "sha256": "1908901ab0df1da1e8073e47f19bed9ab0e719bffe016c71d80a877295b9df98",
+    "td3_nll_grad_f32": {"bytes": 523_553_792, "events": 2_000_000, "sources": _TD3_SRC,
+                         "sha256": "2894fc9244fd38b785414dae802724dddda1c0ec214c61f51d4ac54c131db666",
                          "profile": "profiles/td3_nll_kernel_td3_2M.md"},
-    "td3_nll_f64": {"bytes": 979_524_864, "events": 2_000_000, "fp64_pipe": 0.8610, "sources": _TD3_SRC,
-                    "sha256": "1908901ab0df1da1e8073e47f19bed9ab0e719bffe016c71d80a877295b9df98",
+    "td3_nll_f64": {"bytes": 979_478_272, "events": 2_000_000, "fp64_pipe": 0.8609, "sources": _TD3_SRC,
+                    "sha256": "2894fc9244fd38b785414dae802724dddda1c0ec214c61f51d4ac54c131db666",
                     "profile": "profiles/td3_nll_kernel_td3_2M.md"},
-    "td4_nll_grad_f32": {"bytes": 171_436_544, "events": 2_000_000, "sources": _TD4_SRC,
-                         "sha256": "131f99b2bb238619f17851b0d69b70314103761055bee7685c518161fd1923bb",
+    "td4_nll_grad_f32": {"bytes": 171_342_592, "events": 2_000_000, "sources": _TD4_SRC,
+                         "sha256": "5ac59204f85b06e49659c61cb3d0e0f093a6b7eb231a675719fbb47ea56f6690",
                          "profile": "profiles/td4_nll_f32_kernel_c4_2M.md"},
-    "td4_nll_f64": {"bytes": 339_367_424, "events": 2_000_000, "fp64_pipe": 0.8661, "sources": _TD4_SRC,
-                    "sha256": "131f99b2bb238619f17851b0d69b70314103761055bee7685c518161fd1923bb",
+    "td4_nll_f64": {"bytes": 339_833_344, "events": 2_000_000, "fp64_pipe": 0.8662, "sources": _TD4_SRC,
+                    "sha256": "5ac59204f85b06e49659c61cb3d0e0f093a6b7eb231a675719fbb47ea56f6690",
                     "profile": "profiles/td4_nll_f64_kernel_c4_2M.md"},
 }
 
