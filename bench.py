@@ -47,21 +47,21 @@ NCU_RECORDS = {
     "sop_nll_f64": {"bytes": 243_810_560, "events": 10_000_000, "fp64_pipe": 0.8625, "sources": _SOP_SRC,
                     "sha256": "954818e6736e4c5149a820119fc88e5868aba2bfe3ffb9b0ea372c43b12ece4f",
                     "profile": "profiles/sop_event_kernel_f64_c2_10M.md"},
-    "coh_nll_grad_f32": {"bytes": 323_320_832, "events": 5_000_000, "sources": _COH_SRC,
-                         "sha256": "da0eac6817ec057e6710736663a05d6cc87b64eca728f7d685aceb7bca51cafe",
+    "coh_nll_grad_f32": {"bytes": 323_608_320, "events": 5_000_000, "sources": _COH_SRC,
+                         "sha256": "5d1c335f0745afc30f3f64c1b54e6daaf1950c18059a79005c53996f75143127",
                          "profile": "profiles/coh_nll_staged_kernel_f32_c3_5M.md"},
-    "coh_nll_f64": {"bytes": 643_298_304, "events": 5_000_000, "fp64_pipe": 0.8700, "sources": _COH_SRC,
-                    "sha256": "da0eac6817ec057e6710736663a05d6cc87b64eca728f7d685aceb7bca51cafe",
+    "coh_nll_f64": {"bytes": 643_307_520, "events": 5_000_000, "fp64_pipe": 0.8701, "sources": _COH_SRC,
+                    "sha256": "5d1c335f0745afc30f3f64c1b54e6daaf1950c18059a79005c53996f75143127",
                     "profile": "profiles/coh_nll_kernel_f64_c3_5M.md"},
-    "coh_ls_grad_f32": {"bytes": 40_095_232, "events": 5_000_000, "warp_inst": 313_731_049, "issue_active": 0.6453,
+    "coh_ls_grad_f32": {"bytes": 40_095_488, "events": 5_000_000, "warp_inst": 313_731_049, "issue_active": 0.6452,
                         "sources": _COH_SRC,
-                        "sha256": "da0eac6817ec057e6710736663a05d6cc87b64eca728f7d685aceb7bca51cafe",
+                        "sha256": "5d1c335f0745afc30f3f64c1b54e6daaf1950c18059a79005c53996f75143127",
                         "profile": "profiles/coh_ls_kernel_f32_c3_floating_5M.md"},
-    "td3_nll_grad_f32": {"bytes": 523_553_792, "events": 2_000_000, "sources": _TD3_SRC,
-                         "sha256": "2894fc9244fd38b785414dae802724dddda1c0ec214c61f51d4ac54c131db666",
+    "td3_nll_grad_f32": {"bytes": 524_196_352, "events": 2_000_000, "sources": _TD3_SRC,
+                         "sha256": "f059f4fddffe5aa006bb7a7c3f89f724f94210d7440c093e448ea6da9ebc21bc",
                          "profile": "profiles/td3_nll_kernel_td3_2M.md"},
-    "td3_nll_f64": {"bytes": 979_478_272, "events": 2_000_000, "fp64_pipe": 0.8609, "sources": _TD3_SRC,
-                    "sha256": "2894fc9244fd38b785414dae802724dddda1c0ec214c61f51d4ac54c131db666",
+    "td3_nll_f64": {"bytes": 979_988_224, "events": 2_000_000, "fp64_pipe": 0.8639, "sources": _TD3_SRC,
+                    "sha256": "f059f4fddffe5aa006bb7a7c3f89f724f94210d7440c093e448ea6da9ebc21bc",
                     "profile": "profiles/td3_nll_kernel_td3_2M.md"},
     "td4_nll_grad_f32": {"bytes": 171_342_592, "events": 2_000_000, "sources": _TD4_SRC,
                          "sha256": "5ac59204f85b06e49659c61cb3d0e0f093a6b7eb231a675719fbb47ea56f6690",

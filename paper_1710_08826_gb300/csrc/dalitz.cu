@@ -792,7 +792,7 @@ struct Td3Lanes {
 };
 
 template <typename T, bool GRAD>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, 2)
     td3_nll_kernel(const __grid_constant__ Td3Args<T> a, const void* __restrict__ cache_a,
                    const void* __restrict__ cache_b, const T* __restrict__ tcol, int64_t begin, int64_t end,
                    const double* __restrict__ grams, float2* partials, unsigned* counters, double* out, int out_mode) {
@@ -821,6 +821,24 @@ __global__ void __launch_bounds__(kBlock)
       bi = vb.y;
     }
   };
+  // FP32: all amplitude planes of the event are requested before any is used (loads
+  // predicated on the plane count rather than a loop exit, so none waits on the arithmetic of
+  // the one before), and kept for the gradient lanes
+  constexpr int NP = sizeof(T) == 4 ? (KB + 1) / 2 : 1;
+  float4 pa[NP], pb[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) pa[q] = pb[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto get = [&](int k, int64_t i, T& ar, T& ai, T& br, T& bi) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 va = pa[k / 2], vb = pb[k / 2];
+      ar = (k & 1) ? va.z : va.x;
+      ai = (k & 1) ? va.w : va.y;
+      br = (k & 1) ? vb.z : vb.x;
+      bi = (k & 1) ? vb.w : vb.y;
+    } else {
+      load(k, i, ar, ai, br, bi);
+    }
+  };
   Kahan lf32;
   double lf64 = 0.0;
   T lre[KA], lim[KA], lt[4];
@@ -832,12 +850,20 @@ __global__ void __launch_bounds__(kBlock)
   for (int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end;
        i += (int64_t)gridDim.x * blockDim.x) {
     const T t = tcol[i];
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+      for (int q = 0; q < NP; ++q)
+        if (2 * q < nbw) {
+          pa[q] = __ldg((const float4*)cache_a + (int64_t)q * n + i);
+          pb[q] = __ldg((const float4*)cache_b + (int64_t)q * n + i);
+        }
+    }
     T Ar = a.cr[KB], Ai = a.ci[KB], Br = a.cr[KB], Bi = a.ci[KB];  // the NR amplitude is 1 for both
 #pragma unroll
     for (int k = 0; k < KB; ++k) {
       if (k >= nbw) break;
       T ar, ai, br, bi;
-      load(k, i, ar, ai, br, bi);
+      get(k, i, ar, ai, br, bi);
       Ar += a.cr[k] * ar - a.ci[k] * ai;
       Ai += a.cr[k] * ai + a.ci[k] * ar;
       Br += a.cr[k] * br - a.ci[k] * bi;
@@ -865,7 +891,7 @@ __global__ void __launch_bounds__(kBlock)
       for (int k = 0; k < KB; ++k) {
         if (k >= nbw) break;
         T ar, ai, br, bi;
-        load(k, i, ar, ai, br, bi);
+        get(k, i, ar, ai, br, bi);
         const T qr = ar * VAr - ai * VAi + br * VBr - bi * VBi;  // Re(a V_A + abar V_B) / R
         const T qi = ar * VAi + ai * VAr + br * VBi + bi * VBr;
         lre[k] += qr;
