@@ -448,6 +448,15 @@ def run_ours(args):
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_extra:
+        # the fit of this configuration: every parameter free but the Argus endpoint m0 (the
+        # likelihood is not differentiable where m0 crosses an event), from shifted values
+        free = np.ones(P, bool)
+        free[[p[0] for p in spec["params"]].index("m0")] = False
+        start = theta.copy()
+        start[[0, 2]] += np.array([2e-4, 2e-3])
+        start[[1, 3, 4, 6, 7, 8, 9, 10, 11]] *= 1.03
+        line["c2_fit"] = fit_timed(model, ds, start, free, np.array([p[3] for p in spec["params"]]))
+        line["c1_1d"] = c1_measure(goo, ctx, stream, max(20, args.steps))
         line["c3_dalitz"] = c3_measure(goo, ctx, stream, max(5, args.steps // 2))
         line["c4_td4"] = c4_measure(goo, ctx, stream, max(5, args.steps // 2))
         line["td3_dalitz"] = td3_measure(goo, ctx, stream, max(5, args.steps // 2))
@@ -466,6 +475,53 @@ def run_ours(args):
 # ---------------------------------------------------------------------------------------
 # three-body amplitude workload (5M events, 1M-point MC normalisation)
 # ---------------------------------------------------------------------------------------
+def fit_timed(model, ds, start, free, steps, precision="f32"):
+    """One goo_fit from `start` (adjoint gradient, errors from the Hessian): wall time and
+    the minimiser's counts.  The model has been evaluated before, so no kernel is compiled
+    inside the timed fit."""
+    t0 = time.perf_counter()
+    th, err, info = model.fit(ds, start, free, steps, precision=precision, gradient="adjoint")
+    wall = time.perf_counter() - t0
+    return {"wall_s": wall, "precision": precision, "status": int(info["status"]), "edm": info["edm"],
+            "iterations": int(info["iterations"]), "nll_evals": int(info["nll_evals"]),
+            "grad_evals": int(info["grad_evals"]), "free_params": int(sum(bool(f) for f in free))}
+
+
+def c1_measure(goo, ctx, stream, steps):
+    """C1 (100,000 events in 1D): launch-bound evaluations and the fit wall time."""
+    import numpy as np
+    import torch
+
+    import synth
+    spec = synth.c1_spec()
+    cols = synth.gen_c1()
+    ds = goo.Dataset.from_spec(ctx, spec, cols)
+    model = goo.Model(ctx, spec)
+    theta = np.array(synth.param_values(spec))
+    n = len(cols["x"])
+    out = {"workload": f"c1_1d: {n:,} events on [0, 10], 0.3 Gauss + 0.7 Exp, 4 free parameters, analytic "
+                       "normalisation (launch-bound: the data is L2-resident)"}
+    for prec, grad in (("f32", True), ("f64", False)):
+        for _ in range(3):
+            model.nll_grad(ds, theta, prec) if grad else model.nll(ds, theta, prec)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            model.nll_grad(ds, theta, prec) if grad else model.nll(ds, theta, prec)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        out["f32_grad" if grad else "f64_plain"] = {"evals_per_s": steps / (ms * 1e-3), "us_per_eval": ms / steps * 1e3,
+                                                    "events_per_s": n * steps / (ms * 1e-3)}
+    free = np.ones(len(theta), bool)
+    scale = np.array([p[3] for p in spec["params"]])
+    out["fit_f32"] = fit_timed(model, ds, theta * 1.05, free, scale, "f32")
+    out["fit_f64"] = fit_timed(model, ds, theta * 1.05, free, scale, "f64")
+    return out
+
+
 def c3_measure(goo, ctx, stream, steps, n_events=5_000_000, n_mc=1_000_000):
     import numpy as np
     import torch
@@ -513,6 +569,11 @@ def c3_measure(goo, ctx, stream, steps, n_events=5_000_000, n_mc=1_000_000):
             "bound": "hbm" if grad else "fp64", "ncu": ncu_record(name, n_events),
             "what": ("goo_nll_grad, FP32 amplitude cache (64 B/event), adjoint gradient" if grad
                      else "goo_nll, FP64 amplitude cache (128 B/event)")}
+    free = np.array([not p[2] for p in spec["params"]])
+    scale = np.array([p[3] if p[3] > 0 else 1.0 for p in spec["params"]])
+    start = theta.copy()
+    start[free] *= 1.05
+    out["fit_f32"] = fit_timed(model, ds, start, free, scale)
     out["floating_lineshapes"] = c3_floating_measure(goo, ctx, stream, model, ds, theta, flush, steps, n_events, n_mc)
     return out
 
@@ -637,6 +698,18 @@ def c4_measure(goo, ctx, stream, steps, n_events=2_000_000, n_mc=3_000_000):
                      else "goo_nll, FP64 amplitude cache (160 B/event) + time")}
     out["parity_this_run"] = {"nll_f32": nll["f32"], "nll_f64": nll["f64"],
                               "rel": abs(nll["f32"] - nll["f64"]) / abs(nll["f64"])}
+    # coefficients and the lifetime free; x, y, sigma_t and the first coefficient fixed
+    names = synth.param_names(spec)
+    free = np.array([not p[2] for p in spec["params"]])
+    for nm in ("x", "y", "sigma_t"):
+        if nm in names:
+            free[names.index(nm)] = False
+    coef = np.array([nm.startswith(("re_", "im_")) for nm in names])
+    free[np.flatnonzero(coef & free)[:2]] = False
+    scale = np.array([p[3] if p[3] > 0 else 1.0 for p in spec["params"]])
+    start = theta.copy()
+    start[coef & free] *= 1.05
+    out["fit_f32"] = fit_timed(model, ds, start, free, scale)
     return out
 
 
