@@ -462,6 +462,11 @@ def run_ours(args):
         line["td3_dalitz"] = td3_measure(goo, ctx, stream, max(5, args.steps // 2))
         line["c5_serving"] = c5_study(goo, ctx, n_toys=args.toys)
         line["c5_serving_poisson"] = c5_study(goo, ctx, n_toys=max(64, args.toys // 4), rate=args.rate, plain_sample=0)
+        # a sweep of arrival rates below and above the served throughput
+        line["c5_rate_sweep"] = [
+            {k: v for k, v in c5_study(goo, ctx, n_toys=max(64, args.toys // 8), rate=r, plain_sample=0).items()
+             if k in ("toys", "arrival", "fits_per_s", "latency_p50_s", "latency_p99_s", "converged")}
+            for r in (250.0, 4000.0, 16000.0)]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_rate(cols, min(args.cpu_sample, n))
     if rank == 0:
@@ -475,14 +480,15 @@ def run_ours(args):
 # ---------------------------------------------------------------------------------------
 # three-body amplitude workload (5M events, 1M-point MC normalisation)
 # ---------------------------------------------------------------------------------------
-def fit_timed(model, ds, start, free, steps, precision="f32"):
-    """One goo_fit from `start` (adjoint gradient, errors from the Hessian): wall time and
-    the minimiser's counts.  The model has been evaluated before, so no kernel is compiled
-    inside the timed fit."""
+def fit_timed(model, ds, start, free, steps, precision="f32", gradient="adjoint"):
+    """One goo_fit from `start` (errors from the Hessian): wall time and the minimiser's
+    counts.  The model has been evaluated before, so no kernel is compiled inside the timed
+    fit."""
     t0 = time.perf_counter()
-    th, err, info = model.fit(ds, start, free, steps, precision=precision, gradient="adjoint")
+    th, err, info = model.fit(ds, start, free, steps, precision=precision, gradient=gradient)
     wall = time.perf_counter() - t0
-    return {"wall_s": wall, "precision": precision, "status": int(info["status"]), "edm": info["edm"],
+    return {"wall_s": wall, "precision": precision, "gradient": gradient, "status": int(info["status"]),
+            "edm": info["edm"],
             "iterations": int(info["iterations"]), "nll_evals": int(info["nll_evals"]),
             "grad_evals": int(info["grad_evals"]), "free_params": int(sum(bool(f) for f in free))}
 
@@ -519,6 +525,9 @@ def c1_measure(goo, ctx, stream, steps):
     scale = np.array([p[3] for p in spec["params"]])
     out["fit_f32"] = fit_timed(model, ds, theta * 1.05, free, scale, "f32")
     out["fit_f64"] = fit_timed(model, ds, theta * 1.05, free, scale, "f64")
+    # the configuration's own form: FP64 with the minimiser's numerical (central-difference)
+    # gradient
+    out["fit_f64_numerical_gradient"] = fit_timed(model, ds, theta * 1.05, free, scale, "f64", "fd")
     return out
 
 
