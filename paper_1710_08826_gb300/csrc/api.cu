@@ -301,6 +301,7 @@ int goo_model_set_jit(goo_model* m, int mode) {
   if (mode != 0 && mode != 1) return set_error(GOO_ERR_ARG, "goo_model_set_jit: mode=%d", mode);
   m->jit_mode = mode;
   m->jit_status = mode;
+  m->ev2_fn[0] = m->ev2_fn[1] = nullptr;
   return GOO_OK;
 }
 

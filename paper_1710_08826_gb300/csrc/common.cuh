@@ -159,6 +159,11 @@ struct LaunchScope {
   ~LaunchScope();
 };
 int grid_blocks(goo_ctx* ctx, int64_t work_items, int blocks_per_sm);
+// Resident blocks per SM of `kernel` (a __global__ function or a run-time compiled kernel
+// handle) with `block` threads and `smem` bytes of dynamic shared memory on the current
+// device, at least 1.  Cached per (kernel, device, block, smem): the occupancy query is a
+// driver call, and the launchers need its answer on every evaluation.
+int cached_occupancy(const void* kernel, int device, int block, size_t smem);
 
 #endif  // __CUDACC_RTC__
 

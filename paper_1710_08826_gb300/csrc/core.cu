@@ -9,6 +9,7 @@
 #include <cstring>
 #include <algorithm>
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -101,6 +102,36 @@ static void fold_timings(goo_ctx* ctx) {
     ctx->event_pool.push_back(p.stop);
   }
   ctx->pending.clear();
+}
+
+int cached_occupancy(const void* kernel, int device, int block, size_t smem) {
+  struct Key {
+    const void* k;
+    int dev, block;
+    size_t smem;
+    bool operator<(const Key& o) const {
+      if (k != o.k) return k < o.k;
+      if (dev != o.dev) return dev < o.dev;
+      if (block != o.block) return block < o.block;
+      return smem < o.smem;
+    }
+  };
+  static std::mutex mu;
+  static std::map<Key, int> cache;
+  const Key key{kernel, device, block, smem};
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = 1;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = n;
+  return n;
 }
 
 int grid_blocks(goo_ctx* ctx, int64_t work_items, int blocks_per_sm) {

@@ -1226,12 +1226,7 @@ static int launch_coh_staged(goo_model* m, const void* cache, const goo_dataset*
                                       (int)((size_t)kCohStages * ((KB + 1) / 2) * kCohTile * sizeof(float4))));
     configured[ctx->device] = true;
   }
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, coh_nll_staged_kernel<KB, GRAD>, kStagedBlock, smem) != cudaSuccess ||
-      occ < 1) {
-    cudaGetLastError();
-    occ = 1;
-  }
+  const int occ = cached_occupancy((const void*)coh_nll_staged_kernel<KB, GRAD>, ctx->device, kStagedBlock, smem);
   const int64_t tiles = (end + kCohTile - 1) / kCohTile - begin / kCohTile;
   const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)ctx->num_sms * occ));
   constexpr int NS = CohLanes<float, KB, GRAD>::NS;

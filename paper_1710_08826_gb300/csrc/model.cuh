@@ -119,6 +119,10 @@ struct goo_model {
   // jit_mode 1 (default) or 0; jit_status as goo_model_jit_status reports it
   int jit_mode = 1;
   int jit_status = 1;
+  // the packed-pair event kernel resolved for this model (index: gradient form) and the
+  // jit_status it came with; reset by goo_model_set_jit
+  const void* ev2_fn[2] = {nullptr, nullptr};
+  int ev2_status[2] = {0, 0};
 };
 
 namespace goo {

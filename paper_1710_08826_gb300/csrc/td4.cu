@@ -750,11 +750,7 @@ static int launch_td4_f32(goo_model* m, const void* cache, const goo_dataset* ds
                                       (int)((size_t)kTdStages * ((KB / 2) * kTdTile * sizeof(float4) + kTdTile * sizeof(float)))));
     configured[ctx->device] = true;
   }
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, td4_nll_f32_kernel<KB, GRAD>, kBlock, smem) != cudaSuccess || occ < 1) {
-    cudaGetLastError();
-    occ = 1;
-  }
+  const int occ = cached_occupancy((const void*)td4_nll_f32_kernel<KB, GRAD>, ctx->device, kBlock, smem);
   const int64_t tiles = (end + kTdTile - 1) / kTdTile - begin / kTdTile;
   const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)ctx->num_sms * occ));
   GOO_TRY(ensure_partials(ctx, (size_t)nb * TdLanes<KB, GRAD>::NS));

@@ -955,28 +955,30 @@ static int launch_event2(goo_model* m, const goo_dataset* ds, int64_t begin, int
   const size_t smem_max = (size_t)kEventStages * kMaxObs * TE * sizeof(float);
   static bool configured[kMaxDevicesEv] = {};
   if (ctx->device < 0 || ctx->device >= kMaxDevicesEv) return set_error(GOO_ERR_ARG, "device %d", ctx->device);
-  const void* fn = (const void*)sop_event2_kernel<K, L, GRAD>;
-  m->jit_status = m->jit_mode;
-  if (m->jit_mode) {
-    // the kernel specialised for this model's leaf signature (jit.cu), else the interpreter
-    unsigned long long sig = 0;
-    for (int k = 0; k < m->host.nK && k < K; ++k)
-      for (int l = 0; l < m->host.comp[k].n_leaf && l < L; ++l)
-        sig |= (unsigned long long)(m->host.leaf[k * kMaxLeaf + l].op & 15) << (4 * (k * L + l));
-    int st = 0;
-    const void* jf = jit_event2_kernel(ctx->device, K, L, GRAD, sig, smem_max, &st);
-    m->jit_status = st;
-    if (jf) fn = jf;
+  // the kernel for this model and gradient form, resolved on its first evaluation: the one
+  // specialised for the model's leaf signature (jit.cu), else the interpreter
+  const int gi = GRAD ? 1 : 0;
+  if (!m->ev2_fn[gi]) {
+    const void* fn = (const void*)sop_event2_kernel<K, L, GRAD>;
+    int st = m->jit_mode;
+    if (m->jit_mode) {
+      unsigned long long sig = 0;
+      for (int k = 0; k < m->host.nK && k < K; ++k)
+        for (int l = 0; l < m->host.comp[k].n_leaf && l < L; ++l)
+          sig |= (unsigned long long)(m->host.leaf[k * kMaxLeaf + l].op & 15) << (4 * (k * L + l));
+      const void* jf = jit_event2_kernel(ctx->device, K, L, GRAD, sig, smem_max, &st);
+      if (jf) fn = jf;
+    }
+    if (fn == (const void*)sop_event2_kernel<K, L, GRAD> && !configured[ctx->device]) {
+      GOO_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+      configured[ctx->device] = true;
+    }
+    m->ev2_fn[gi] = fn;
+    m->ev2_status[gi] = st;
   }
-  if (fn == (const void*)sop_event2_kernel<K, L, GRAD> && !configured[ctx->device]) {
-    GOO_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
-    configured[ctx->device] = true;
-  }
-  int bps = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, smem) != cudaSuccess || bps < 1) {
-    cudaGetLastError();
-    bps = 1;
-  }
+  const void* fn = m->ev2_fn[gi];
+  m->jit_status = m->ev2_status[gi];
+  const int bps = cached_occupancy(fn, ctx->device, kBlock, smem);
   const int64_t tiles = (end + TE - 1) / TE - begin / TE;
   const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)ctx->num_sms * bps));
   constexpr int NS = EventLanes<float, K, L, GRAD>::NS;
