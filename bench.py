@@ -41,7 +41,8 @@ _TD3_SRC = _COH_SRC + ['paper_1710_08826_gb300/csrc/timeterms.cuh']
 ISSUE_PEAK = 152 * 4 * 2.07e9
 
 NCU_RECORDS = {
-    "sop_nll_grad_f32": {"bytes": 125_870_080, "events": 10_000_000, "sources": _SOP_SRC,
+    "sop_nll_grad_f32": {"bytes": 125_870_080, "events": 10_000_000, "warp_inst": 29_148_206, "issue_active": 0.4747,
+                         "sources": _SOP_SRC,
                          "sha256": "954818e6736e4c5149a820119fc88e5868aba2bfe3ffb9b0ea372c43b12ece4f",
                          "profile": "profiles/sop_event2_kernel_f32_c2_10M.md"},
     "sop_nll_f64": {"bytes": 243_810_560, "events": 10_000_000, "fp64_pipe": 0.8625, "sources": _SOP_SRC,
@@ -423,6 +424,13 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel_share": {k: round(v[1] / max(sum(x[1] for x in kt_mix.values()), 1e-12), 4)
                                  for k, v in kt_mix.items()}}
+    rec = ncu_record(name, n)
+    if rec is not None and "warp_inst" in rec:
+        # the binding resource: instruction issue (one warp instruction per scheduler per
+        # cycle at the maximum SM clock); the warp-instruction count is ncu's for this kernel
+        roofline["issue"] = {"warp_inst_per_launch": rec["warp_inst"],
+                             "achieved_frac_of_issue_peak": rec["warp_inst"] / per_launch_s / ISSUE_PEAK,
+                             "ncu_issue_active": rec["issue_active"], "peak_warp_inst_per_s": ISSUE_PEAK}
 
     value = n * world * args.steps / (total_mix * 1e-3)
     e2e_value = n * world * e2e_steps / e2e_s
