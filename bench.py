@@ -43,10 +43,10 @@ ISSUE_PEAK = 152 * 4 * 2.07e9
 NCU_RECORDS = {
     "sop_nll_grad_f32": {"bytes": 125_705_216, "events": 10_000_000, "warp_inst": 29_148_206, "issue_active": 0.4810,
                          "sources": _SOP_SRC,
-                         "sha256": "ddf18cfb8bcc86bdbd7a081b65078ea0b457ef8e0a1bcf567bc18c39d5c4497e",
+                         "sha256": "2c45bfcf32e37d2536fa29711f5b3469217bf6857cd61bda67c010de091df1a3",
                          "profile": "profiles/sop_event2_kernel_f32_c2_10M.md"},
     "sop_nll_f64": {"bytes": 243_320_832, "events": 10_000_000, "fp64_pipe": 0.8625, "sources": _SOP_SRC,
-                    "sha256": "ddf18cfb8bcc86bdbd7a081b65078ea0b457ef8e0a1bcf567bc18c39d5c4497e",
+                    "sha256": "2c45bfcf32e37d2536fa29711f5b3469217bf6857cd61bda67c010de091df1a3",
                     "profile": "profiles/sop_event_kernel_f64_c2_10M.md"},
     "coh_nll_grad_f32": {"bytes": 323_661_824, "events": 5_000_000, "sources": _COH_SRC,
                          "sha256": "afaf0c87de43fa68f904658acf869e22695f30ae559465d5b02b20dbc5015241",

@@ -295,6 +295,13 @@ int goo_model_set_coefficients(goo_model* model, int form);
  * specialised kernel, -1 compilation failed and the interpreter ran instead. */
 int goo_model_set_jit(goo_model* model, int mode);
 int goo_model_jit_status(const goo_model* model);
+/* Compile the packed-pair event kernel for a K x L slot shape (K products of at most L
+ * leaves; 1 <= K, L <= 4), with or without gradient lanes, for a leaf signature (4 bits per
+ * slot k * L + l: the leaf's GOO_OP_* code, 0 for an empty slot), as goo_model_set_jit does
+ * on a model's first evaluation, without loading it: needs no GPU.  For checking NVRTC and
+ * the kernel sources on a machine before the first evaluation.  *cubin_bytes (if not NULL)
+ * receives the image size.  GOO_ERR_CUDA with NVRTC's log in goo_last_error on failure. */
+int goo_jit_check(int K, int L, int grad, unsigned long long sig, int64_t* cubin_bytes);
 
 /* ---- fitting (paper: the FitManager, Fig. 1; Minuit 2 as the default minimiser, Sec. 4) -------
  * Minimises the NLL of `model` on `ds` over the parameters with free_mask[p] != 0, starting

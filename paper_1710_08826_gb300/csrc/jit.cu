@@ -42,7 +42,10 @@ struct JitEntry {
 std::mutex g_mu;
 std::map<std::string, JitEntry> g_cache;
 
-int compile_event2(int K, int L, bool grad, unsigned long long sig, JitEntry& e) {
+// NVRTC compilation of sop_event2_kernel<K, L, grad, sig> to an sm_103a cubin: the image and
+// the kernel's lowered name.  Needs no device.
+int compile_event2_cubin(int K, int L, bool grad, unsigned long long sig, std::vector<char>& cubin,
+                         std::string& kname) {
   const char* src = "#include \"sop_kernels.cuh\"\n";
   const int nh = (int)(sizeof(kJitHeaderNames) / sizeof(kJitHeaderNames[0]));
   nvrtcProgram prog;
@@ -70,10 +73,17 @@ int compile_event2(int K, int L, bool grad, unsigned long long sig, JitEntry& e)
     nvrtcDestroyProgram(&prog);
     return set_error(GOO_ERR_CUDA, "NVRTC: no kernel image for %s", name);
   }
-  std::string kname(lowered);
-  std::vector<char> cubin(cubin_size);
+  kname = lowered;
+  cubin.resize(cubin_size);
   nvrtcGetCUBIN(prog, cubin.data());
   nvrtcDestroyProgram(&prog);
+  return GOO_OK;
+}
+
+int compile_event2(int K, int L, bool grad, unsigned long long sig, JitEntry& e) {
+  std::vector<char> cubin;
+  std::string kname;
+  GOO_TRY(compile_event2_cubin(K, L, grad, sig, cubin, kname));
   GOO_CUDA_TRY(cudaLibraryLoadData(&e.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
   GOO_CUDA_TRY(cudaLibraryGetKernel(&e.kernel, e.lib, kname.c_str()));
   return GOO_OK;
@@ -113,3 +123,14 @@ const void* jit_event2_kernel(int device, int K, int L, bool grad, unsigned long
 }
 
 }  // namespace goo
+
+extern "C" int goo_jit_check(int K, int L, int grad, unsigned long long sig, int64_t* cubin_bytes) {
+  using namespace goo;
+  if (K < 1 || K > kMaxComp || L < 1 || L > kMaxLeaf)
+    return set_error(GOO_ERR_ARG, "goo_jit_check: shape %d x %d (1..%d x 1..%d)", K, L, kMaxComp, kMaxLeaf);
+  std::vector<char> cubin;
+  std::string kname;
+  GOO_TRY(compile_event2_cubin(K, L, grad != 0, sig, cubin, kname));
+  if (cubin_bytes) *cubin_bytes = (int64_t)cubin.size();
+  return GOO_OK;
+}
