@@ -38,33 +38,6 @@ int check_theta(const goo_model* m, const double* theta) {
   return GOO_OK;
 }
 
-// Waits for the completion word of the mapped result record that an event kernel writes
-// (sop_events with result = scratch.result_host), then copies `n` doubles.  The host polls
-// the word for up to 2 ms, then waits on the stream, which also reports a failed launch.
-int read_result_mapped(goo_ctx* ctx, int n, double* dst) {
-  volatile double* flag = ctx->scratch.result_host + kResultFlag;
-  const auto t0 = std::chrono::steady_clock::now();
-  for (unsigned it = 0; *flag == 0.0; ++it) {
-    if ((it & 255u) == 0 && std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(2)) {
-      GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-      if (*flag == 0.0) return set_error(GOO_ERR_STATE, "the event kernel finished without its completion word");
-      break;
-    }
-  }
-  std::atomic_thread_fence(std::memory_order_acquire);
-  std::memcpy(dst, (const double*)ctx->scratch.result_host, n * sizeof(double));
-  return GOO_OK;
-}
-
-// Reads `n` result doubles into the pinned staging area and waits for the stream.
-int read_result(goo_ctx* ctx, int n, double* dst) {
-  double* stage = ctx->scratch.host_pinned + kPinnedResult;
-  GOO_CUDA_TRY(cudaMemcpyAsync(stage, ctx->scratch.result, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-  std::memcpy(dst, stage, n * sizeof(double));
-  return GOO_OK;
-}
-
 int nll_common(goo_model* m, const goo_dataset* ds, const double* theta, int precision, bool grad, double* nll_out,
                double* grad_out) {
   GOO_TRY(check_model_dataset(m, ds, precision));

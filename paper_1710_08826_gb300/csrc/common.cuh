@@ -86,6 +86,9 @@ struct Scratch {
   // result record in mapped pinned host memory (kResultDoubles + 1 doubles, the device writes
   // it over the host link): the sum-of-products path reads its result here without a copy
   double* result_host = nullptr;
+  // destination of the amplitude kernels' record for the evaluation in progress: `result`,
+  // or `result_host` while dalitz_nll / td4_nll run
+  double* result_out = nullptr;
 };
 
 }  // namespace goo
@@ -164,6 +167,17 @@ int grid_blocks(goo_ctx* ctx, int64_t work_items, int blocks_per_sm);
 // device, at least 1.  Cached per (kernel, device, block, smem): the occupancy query is a
 // driver call, and the launchers need its answer on every evaluation.
 int cached_occupancy(const void* kernel, int device, int block, size_t smem);
+// Waits for the completion word of the record a kernel writes to scratch.result_host (polling
+// for up to 2 ms, then waiting on the stream, which also reports a failed kernel) and copies
+// its first n doubles to dst.
+int read_result_mapped(goo_ctx* ctx, int n, double* dst);
+// For the lifetime of the guard, the amplitude kernels write their record to the mapped host
+// copy (scratch.result_out = scratch.result_host) with its completion word cleared.
+struct MappedResult {
+  goo_ctx* ctx;
+  explicit MappedResult(goo_ctx* c);
+  ~MappedResult();
+};
 
 #endif  // __CUDACC_RTC__
 
@@ -359,6 +373,14 @@ __device__ __forceinline__ void block_reduce_to_partials(ddf (&v)[NS], int nslot
 
 // After every block has written its partials: take a ticket.  True in the block that draws
 // the last one; every partial is then visible to it.  The caller resets the ticket.
+// Completion word of a result record (kResultFlag): every thread of the last block calls
+// this after its last write to `result`, so that a host polling the word sees the whole record.
+__device__ __forceinline__ void result_complete(double* result) {
+  __threadfence_system();
+  __syncthreads();
+  if (threadIdx.x == 0) *(volatile double*)(result + kResultFlag) = 1.0;
+}
+
 __device__ __forceinline__ bool last_block_ticket(unsigned* ticket, int nblocks) {
   __shared__ bool is_last;
   __threadfence();

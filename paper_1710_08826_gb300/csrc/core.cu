@@ -9,6 +9,7 @@
 #include <cstring>
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <map>
 #include <mutex>
 #include <vector>
@@ -103,6 +104,30 @@ static void fold_timings(goo_ctx* ctx) {
   }
   ctx->pending.clear();
 }
+
+// Waits for the completion word of the mapped result record that an event kernel writes
+// (sop_events with result = scratch.result_host), then copies `n` doubles.  The host polls
+// the word for up to 2 ms, then waits on the stream, which also reports a failed launch.
+int read_result_mapped(goo_ctx* ctx, int n, double* dst) {
+  volatile double* flag = ctx->scratch.result_host + kResultFlag;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (unsigned it = 0; *flag == 0.0; ++it) {
+    if ((it & 255u) == 0 && std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(2)) {
+      GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+      if (*flag == 0.0) return set_error(GOO_ERR_STATE, "the event kernel finished without its completion word");
+      break;
+    }
+  }
+  std::atomic_thread_fence(std::memory_order_acquire);
+  std::memcpy(dst, (const double*)ctx->scratch.result_host, n * sizeof(double));
+  return GOO_OK;
+}
+
+MappedResult::MappedResult(goo_ctx* c) : ctx(c) {
+  ctx->scratch.result_host[kResultFlag] = 0.0;
+  ctx->scratch.result_out = ctx->scratch.result_host;
+}
+MappedResult::~MappedResult() { ctx->scratch.result_out = ctx->scratch.result; }
 
 int cached_occupancy(const void* kernel, int device, int block, size_t smem) {
   struct Key {
@@ -365,6 +390,7 @@ int goo_init(int device, void* cuda_stream, goo_ctx** out) {
   GOO_CUDA_TRY(cudaMalloc(&s.result, (kResultDoubles + 1) * sizeof(double)));
   GOO_CUDA_TRY(cudaHostAlloc(&s.result_host, (kResultDoubles + 1) * sizeof(double), cudaHostAllocMapped));
   std::memset(s.result_host, 0, (kResultDoubles + 1) * sizeof(double));
+  s.result_out = s.result;
   GOO_CUDA_TRY(cudaMalloc(&s.theta, 2 * kMaxParams * sizeof(double)));
   GOO_CUDA_TRY(cudaMallocHost(&s.host_pinned, 512 * sizeof(double)));
   int rc = ensure_partials(ctx, 65536);

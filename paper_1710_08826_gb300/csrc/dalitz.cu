@@ -280,6 +280,7 @@ __device__ __forceinline__ void coh_finish(const CohArgs<T>& a, CohAcc<T, KB>& a
       result[2] = nb;
     }
   }
+  result_complete(result);
 }
 
 template <typename T, int KB>
@@ -706,6 +707,7 @@ __global__ void __launch_bounds__(kBlock)
       out[2] = nb;
     }
   }
+  result_complete(out);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1037,6 +1039,7 @@ __global__ void __launch_bounds__(kBlock, 2)
       out[2] = nb;
     }
   }
+  result_complete(out);
 }
 
 static int dalitz_constants(goo_model* m, const double* theta) {
@@ -1237,7 +1240,7 @@ static int launch_coh_staged(goo_model* m, const void* cache, const goo_dataset*
     LaunchScope ls(ctx, GRAD ? "coh_nll_grad_f32" : "coh_nll_f32");
     coh_nll_staged_kernel<KB, GRAD><<<nb, kStagedBlock, smem, ctx->stream>>>(a, (const float4*)cache, begin, end,
                                                                        d.gram_dev[pi], ctx->scratch.partials,
-                                                                       ctx->scratch.counters, ctx->scratch.result,
+                                                                       ctx->scratch.counters, ctx->scratch.result_out,
                                                                        out_mode);
   }
   GOO_CUDA_TRY(cudaGetLastError());
@@ -1268,7 +1271,7 @@ static int launch_coh(goo_model* m, const void* cache, const goo_dataset* ds, in
                                        : (GRAD ? "coh_nll_grad_f64" : "coh_nll_f64"));
     coh_nll_kernel<T, KB, GRAD><<<nb, kBlock, 0, ctx->stream>>>(a, cache, begin, end, d.gram_dev[pi],
                                                                 ctx->scratch.partials, ctx->scratch.counters,
-                                                                ctx->scratch.result, out_mode);
+                                                                ctx->scratch.result_out, out_mode);
   }
   GOO_CUDA_TRY(cudaGetLastError());
   return GOO_OK;
@@ -1369,10 +1372,10 @@ static int launch_ls_pair(goo_model* m, const goo_dataset* ds, int64_t begin, in
   DalitzModel& d = *m->dalitz;
   if (d.nbw <= 8) {
     GOO_TRY((launch_ls<T, 8, GRAD, true>(m, d.mc, 0, d.mc->n, theta, d.ls_mc, 0)));
-    return launch_ls<T, 8, GRAD, false>(m, ds, begin, end, theta, m->ctx->scratch.result, out_mode);
+    return launch_ls<T, 8, GRAD, false>(m, ds, begin, end, theta, m->ctx->scratch.result_out, out_mode);
   }
   GOO_TRY((launch_ls<T, 15, GRAD, true>(m, d.mc, 0, d.mc->n, theta, d.ls_mc, 0)));
-  return launch_ls<T, 15, GRAD, false>(m, ds, begin, end, theta, m->ctx->scratch.result, out_mode);
+  return launch_ls<T, 15, GRAD, false>(m, ds, begin, end, theta, m->ctx->scratch.result_out, out_mode);
 }
 
 // The three MC Gram matrices of the time-dependent three-body model (G_aa, G_bb, G_ab) in
@@ -1462,7 +1465,7 @@ static int launch_td3(goo_model* m, const goo_dataset* ds, int64_t begin, int64_
                                        : (GRAD ? "td3_nll_grad_f64" : "td3_nll_f64"));
     td3_nll_kernel<T, GRAD><<<nb, kBlock, 0, ctx->stream>>>(a, ca, cb, tcol, begin, end, d.gram3_dev[pi],
                                                             ctx->scratch.partials, ctx->scratch.counters,
-                                                            ctx->scratch.result, out_mode);
+                                                            ctx->scratch.result_out, out_mode);
   }
   GOO_CUDA_TRY(cudaGetLastError());
   return GOO_OK;
@@ -1653,6 +1656,8 @@ int dalitz_nll(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, 
                bool grad, double* out, int out_mode) {
   DalitzModel& d = *m->dalitz;
   goo_ctx* ctx = m->ctx;
+  // the record goes to the mapped host copy; the host polls its completion word
+  MappedResult mapped(ctx);
   const int P = m->n_params;
   if (ds->ncols <= d.col12 || ds->ncols <= d.col13) return set_error(GOO_ERR_ARG, "dataset lacks s12/s13 columns");
   GOO_TRY(dalitz_constants(m, theta));
@@ -1712,11 +1717,7 @@ int dalitz_nll(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, 
                   : launch_coh_sel<double, false>(m, cache, ds, begin, end, theta, out_mode, pi)));
   }
   }
-  double* stage = ctx->scratch.host_pinned + kPinnedResult;
-  GOO_CUDA_TRY(cudaMemcpyAsync(stage, ctx->scratch.result, nout * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-  std::memcpy(out, stage, nout * sizeof(double));
-  return GOO_OK;
+  return read_result_mapped(ctx, nout, out);
 }
 
 int dalitz_eval_logf(goo_model* m, const goo_dataset* ds, const double* theta, int precision, double* logf_dev) {

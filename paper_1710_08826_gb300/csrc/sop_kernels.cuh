@@ -399,10 +399,7 @@ __device__ __forceinline__ void event_finish(ddf (&v)[EventLanes<float, K, L, GR
       result[2] = nb;
     }
   }
-  // completion word: every writer's record words are visible system-wide before it
-  __threadfence_system();
-  __syncthreads();
-  if (threadIdx.x == 0) *(volatile double*)(result + kResultFlag) = 1.0;
+  result_complete(result);
 }
 
 // Resident blocks per SM the event kernel is compiled for: the FP32 form of the small shape

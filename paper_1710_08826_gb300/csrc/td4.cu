@@ -333,6 +333,7 @@ __device__ __forceinline__ void td4_finish(const Td4Args<T>& a, TdAcc<T, KB>& ac
       result[2] = nb;
     }
   }
+  result_complete(result);
 }
 
 // FP64: direct loads, one event per thread per grid-stride step.
@@ -758,7 +759,7 @@ static int launch_td4_f32(goo_model* m, const void* cache, const goo_dataset* ds
     LaunchScope ls(ctx, GRAD ? "td4_nll_grad_f32" : "td4_nll_f32");
     td4_nll_f32_kernel<KB, GRAD><<<nb, kBlock, smem, ctx->stream>>>(a, (const float4*)cache, ds->d32[5], begin, end,
                                                                    m->td4->gram_dev[0], ctx->scratch.partials,
-                                                                   ctx->scratch.counters, ctx->scratch.result, out_mode);
+                                                                   ctx->scratch.counters, ctx->scratch.result_out, out_mode);
   }
   GOO_CUDA_TRY(cudaGetLastError());
   return GOO_OK;
@@ -782,7 +783,7 @@ static int launch_td4_f64(goo_model* m, const void* cache, const goo_dataset* ds
     LaunchScope ls(ctx, GRAD ? "td4_nll_grad_f64" : "td4_nll_f64");
     td4_nll_f64_kernel<KB, GRAD><<<nb, kBlock, 0, ctx->stream>>>(a, (const double2*)cache, ds->d64[5], begin, end,
                                                                 m->td4->gram_dev[1], ctx->scratch.partials,
-                                                                ctx->scratch.counters, ctx->scratch.result, out_mode);
+                                                                ctx->scratch.counters, ctx->scratch.result_out, out_mode);
   }
   GOO_CUDA_TRY(cudaGetLastError());
   return GOO_OK;
@@ -802,6 +803,8 @@ static int td4_launch(goo_model* m, const void* cache, const goo_dataset* ds, in
 int td4_nll(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, const double* theta, int precision,
             bool grad, double* out, int out_mode) {
   goo_ctx* ctx = m->ctx;
+  // the record goes to the mapped host copy; the host polls its completion word
+  MappedResult mapped(ctx);
   const int P = m->n_params;
   if (ds->ncols < 6) return set_error(GOO_ERR_ARG, "the four-body model needs 6 dataset columns");
   GOO_TRY(td4_check_theta(m, theta));
@@ -815,11 +818,7 @@ int td4_nll(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, con
   GOO_TRY(td4_cache(m, ds, precision, &cache));
   GOO_TRY((grad ? td4_launch<true>(m, cache, ds, begin, end, theta, precision, out_mode)
                 : td4_launch<false>(m, cache, ds, begin, end, theta, precision, out_mode)));
-  double* stage = ctx->scratch.host_pinned + kPinnedResult;
-  GOO_CUDA_TRY(cudaMemcpyAsync(stage, ctx->scratch.result, nout * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-  std::memcpy(out, stage, nout * sizeof(double));
-  return GOO_OK;
+  return read_result_mapped(ctx, nout, out);
 }
 
 // N at theta from the host copy of the Gram matrix (the same formula as the kernels' last block)
