@@ -310,9 +310,14 @@ int goo_jit_check(int K, int L, int grad, unsigned long long sig, int64_t* cubin
  * backtracking line search, then (polish != 0) Newton steps on a finite-difference Hessian
  * of the gradient; errors_out (NULL or n_params doubles) receives sqrt(diag(H^-1)) for free
  * parameters and 0 for fixed ones.  The gradient is the adjoint kernel (GOO_GRAD_ADJOINT) or
- * central differences of goo_nll (GOO_GRAD_FD, the plain path).  res->status: 0 converged
- * (EDM = g^T H^-1 g / 2 < edm_tol), 1 iteration limit, 2 line-search failure.  Returns an
- * error code only for invalid arguments or a non-finite NLL at the start. */
+ * central differences of goo_nll (GOO_GRAD_FD, the plain path).  With refine != 0, an FP32
+ * fit (adjoint gradient, polish on) ends in FP64: after BFGS on FP32 evaluations, Newton steps
+ * use FP64 adjoint gradients with the finite-difference Hessian (from FP32 gradients when that
+ * Hessian is positive definite, else from FP64 ones), so that the minimum is the FP64
+ * likelihood's at a small cost; res->nll is then the FP64 NLL.  res->status: 0 converged
+ * (0 <= EDM = g^T H^-1 g / 2 < edm_tol), 1 iteration limit, 2 line-search failure, 3 the
+ * Hessian at the end is not positive definite.  Returns an error code only for invalid
+ * arguments or a non-finite NLL at the start. */
 enum { GOO_GRAD_ADJOINT = 0, GOO_GRAD_FD = 1 };
 typedef struct goo_fit_options {
   int32_t precision;  /* GOO_F64 or GOO_F32                                                 */
@@ -320,6 +325,7 @@ typedef struct goo_fit_options {
   int32_t max_iter;   /* BFGS iterations (<= 0: 500)                                        */
   int32_t polish;     /* Newton steps on the finite-difference Hessian after BFGS           */
   double edm_tol;     /* convergence threshold on EDM (<= 0: 1e-6)                          */
+  int32_t refine;     /* FP32 fits: final Newton steps on FP64 gradients (see above)        */
 } goo_fit_options;
 typedef struct goo_fit_result {
   double nll, edm, wall_ms;

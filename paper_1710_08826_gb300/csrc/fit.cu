@@ -107,6 +107,23 @@ bool solve(int n, std::vector<double>& A, std::vector<double>& b) {
   return true;
 }
 
+// Cholesky test: true when the symmetric matrix A (n x n) is positive definite.
+bool positive_definite(int n, const std::vector<double>& A) {
+  std::vector<double> L((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double d = A[j * n + j];
+    for (int k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
+    if (!(d > 0)) return false;
+    L[j * n + j] = std::sqrt(d);
+    for (int i = j + 1; i < n; ++i) {
+      double v = A[i * n + j];
+      for (int k = 0; k < j; ++k) v -= L[i * n + k] * L[j * n + k];
+      L[i * n + j] = v / L[j * n + j];
+    }
+  }
+  return true;
+}
+
 bool invert(int n, const std::vector<double>& A, std::vector<double>& inv) {
   inv.assign((size_t)n * n, 0.0);
   for (int c = 0; c < n; ++c) {
@@ -158,6 +175,7 @@ extern "C" int goo_fit(goo_model* model, const goo_dataset* ds, double* theta, c
     opt.max_iter = 500;
     opt.edm_tol = 1e-6;
     opt.polish = 1;
+    opt.refine = 1;
   }
   if (opt.max_iter <= 0) opt.max_iter = 500;
   if (!(opt.edm_tol > 0)) opt.edm_tol = 1e-6;
@@ -298,7 +316,45 @@ extern "C" int goo_fit(goo_model* model, const goo_dataset* ds, double* theta, c
       for (int b = 0; b < n; ++b) e += 0.5 * gg[a] * Hi[a * n + b] * gg[b];
     return e;
   };
-  if (n > 0 && (opt.polish || errors_out)) {
+  const bool refine = opt.refine && opt.polish && opt.precision == GOO_F32 && opt.gradient == GOO_GRAD_ADJOINT;
+  if (n > 0 && refine) {
+    // FP64 refinement of an FP32 fit: near the minimum the FP32 gradient's rounding is no
+    // longer small against the curvature of a large sample.  The Hessian comes from FP32
+    // gradients when it is positive definite, else from FP64 ones; Newton steps then use FP64
+    // gradients with that fixed Hessian, each accepted when the EDM drops.
+    bool pd = hessian(obj, x, H) && positive_definite(n, H);
+    obj.precision = GOO_F64;
+    if (!pd) pd = hessian(obj, x, H) && positive_definite(n, H);
+    if (pd && invert(n, H, Hi) && obj.value_grad(x.data(), &f, g.data())) {
+      have_h = true;
+      edm = edm_of(g);
+      std::vector<double> dx(n);
+      for (int step = 0; step < 6 && edm >= 1e-4 * opt.edm_tol; ++step) {
+        for (int a = 0; a < n; ++a) {
+          dx[a] = 0.0;
+          for (int b = 0; b < n; ++b) dx[a] -= Hi[a * n + b] * g[b];
+        }
+        bool moved = false;
+        for (double t = 1.0; t >= 0.125; t *= 0.5) {
+          for (int a = 0; a < n; ++a) xt[a] = x[a] + t * dx[a];
+          double ft;
+          if (!obj.value_grad(xt.data(), &ft, gt.data())) continue;
+          const double e = edm_of(gt);
+          if (e < edm) {
+            x = xt;
+            g = gt;
+            f = ft;
+            edm = e;
+            moved = true;
+            break;
+          }
+        }
+        if (log_level() >= 2) std::fprintf(stderr, "[goo] fit refine step=%d edm=%.3e moved=%d\n", step, edm, (int)moved);
+        if (!moved) break;
+      }
+    }
+    obj.precision = opt.precision;
+  } else if (n > 0 && (opt.polish || errors_out)) {
     for (int pass = 0; pass < (opt.polish ? 6 : 1); ++pass) {
       if (!hessian(obj, x, H)) break;
       have_h = invert(n, H, Hi);
@@ -326,7 +382,8 @@ extern "C" int goo_fit(goo_model* model, const goo_dataset* ds, double* theta, c
     }
     if (have_h && opt.polish && hessian(obj, x, H) && invert(n, H, Hi)) edm = edm_of(g);  // at the final point
   }
-  if (n > 0 && edm < opt.edm_tol) status = 0;
+  if (n > 0 && have_h && edm < 0) status = 3;  // the final Hessian is not positive definite
+  else if (n > 0 && edm < opt.edm_tol) status = 0;
   else if (status == 0) status = 1;
   obj.to_theta(x.data());
   for (int p = 0; p < obj.P; ++p) theta[p] = obj.work[p];

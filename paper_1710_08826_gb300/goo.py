@@ -38,7 +38,7 @@ class GooNormSpec(ctypes.Structure):
 
 class GooFitOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("gradient", ctypes.c_int32), ("max_iter", ctypes.c_int32),
-                ("polish", ctypes.c_int32), ("edm_tol", ctypes.c_double)]
+                ("polish", ctypes.c_int32), ("edm_tol", ctypes.c_double), ("refine", ctypes.c_int32)]
 
 
 class GooFitResult(ctypes.Structure):
@@ -497,7 +497,7 @@ class Model:
         return out
 
     def fit(self, ds, theta0, free=None, scale=None, precision="f32", gradient="adjoint", max_iter=500,
-            edm_tol=1e-6, polish=True, errors=True):
+            edm_tol=1e-6, polish=True, errors=True, refine=True):
         """Minimise the NLL (goo_fit).  Returns (theta_hat, errors, info dict)."""
         th, thp = _dbuf(np.array(theta0, dtype=np.float64, copy=True), self.n_params)
         if free is None:
@@ -507,7 +507,7 @@ class Model:
         fm = (ctypes.c_int * self.n_params)(*[int(bool(v)) for v in free])
         sc, scp = _dbuf(scale, self.n_params)
         opt = GooFitOptions(precision_code(precision), {"adjoint": 0, "fd": 1}[gradient], int(max_iter),
-                            int(bool(polish)), float(edm_tol))
+                            int(bool(polish)), float(edm_tol), int(bool(refine)))
         err = np.zeros(self.n_params)
         res = GooFitResult()
         _check(lib.goo_fit(self.handle, ds.handle, thp, fm, scp, ctypes.byref(opt),
