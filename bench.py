@@ -41,34 +41,34 @@ _TD3_SRC = _COH_SRC + ['paper_1710_08826_gb300/csrc/timeterms.cuh']
 ISSUE_PEAK = 152 * 4 * 2.07e9
 
 NCU_RECORDS = {
-    "sop_nll_grad_f32": {"bytes": 125_705_216, "events": 10_000_000, "warp_inst": 29_148_206, "issue_active": 0.4810,
+    "sop_nll_grad_f32": {"bytes": 126_027_776, "events": 10_000_000, "warp_inst": 29_148_206, "issue_active": 0.4692,
                          "sources": _SOP_SRC,
-                         "sha256": "2c45bfcf32e37d2536fa29711f5b3469217bf6857cd61bda67c010de091df1a3",
+                         "sha256": "532114ccab9a6c0fe787e7bb5a3c283973e352febfa8cca9ee69684dad089269",
                          "profile": "profiles/sop_event2_kernel_f32_c2_10M.md"},
-    "sop_nll_f64": {"bytes": 243_320_832, "events": 10_000_000, "fp64_pipe": 0.8625, "sources": _SOP_SRC,
-                    "sha256": "2c45bfcf32e37d2536fa29711f5b3469217bf6857cd61bda67c010de091df1a3",
+    "sop_nll_f64": {"bytes": 243_409_920, "events": 10_000_000, "fp64_pipe": 0.8625, "sources": _SOP_SRC,
+                    "sha256": "532114ccab9a6c0fe787e7bb5a3c283973e352febfa8cca9ee69684dad089269",
                     "profile": "profiles/sop_event_kernel_f64_c2_10M.md"},
-    "coh_nll_grad_f32": {"bytes": 323_661_824, "events": 5_000_000, "sources": _COH_SRC,
-                         "sha256": "afaf0c87de43fa68f904658acf869e22695f30ae559465d5b02b20dbc5015241",
+    "coh_nll_grad_f32": {"bytes": 323_350_784, "events": 5_000_000, "sources": _COH_SRC,
+                         "sha256": "08f310ad89453fbd7d0a57941eaa455389409c25c04cc8f25e2ca99d0c0435cf",
                          "profile": "profiles/coh_nll_staged_kernel_f32_c3_5M.md"},
-    "coh_nll_f64": {"bytes": 643_389_952, "events": 5_000_000, "fp64_pipe": 0.8702, "sources": _COH_SRC,
-                    "sha256": "afaf0c87de43fa68f904658acf869e22695f30ae559465d5b02b20dbc5015241",
+    "coh_nll_f64": {"bytes": 643_376_128, "events": 5_000_000, "fp64_pipe": 0.87, "sources": _COH_SRC,
+                    "sha256": "08f310ad89453fbd7d0a57941eaa455389409c25c04cc8f25e2ca99d0c0435cf",
                     "profile": "profiles/coh_nll_kernel_f64_c3_5M.md"},
-    "coh_ls_grad_f32": {"bytes": 40_095_232, "events": 5_000_000, "warp_inst": 313_731_049, "issue_active": 0.6449,
+    "coh_ls_grad_f32": {"bytes": 40_096_000, "events": 5_000_000, "warp_inst": 313_731_120, "issue_active": 0.6438,
                         "sources": _COH_SRC,
-                        "sha256": "afaf0c87de43fa68f904658acf869e22695f30ae559465d5b02b20dbc5015241",
+                        "sha256": "08f310ad89453fbd7d0a57941eaa455389409c25c04cc8f25e2ca99d0c0435cf",
                         "profile": "profiles/coh_ls_kernel_f32_c3_floating_5M.md"},
-    "td3_nll_grad_f32": {"bytes": 524_045_056, "events": 2_000_000, "sources": _TD3_SRC,
-                         "sha256": "43cfa83de6c2a542926f39007e476d30f1dfc6b74957b503a24edb8492849c06",
+    "td3_nll_grad_f32": {"bytes": 524_228_608, "events": 2_000_000, "sources": _TD3_SRC,
+                         "sha256": "15a1dce360c984926ea5ec34c819b480248a0a047f521fc610f49a88bdb6ef24",
                          "profile": "profiles/td3_nll_kernel_td3_2M.md"},
-    "td3_nll_f64": {"bytes": 980_048_896, "events": 2_000_000, "fp64_pipe": 0.8639, "sources": _TD3_SRC,
-                    "sha256": "43cfa83de6c2a542926f39007e476d30f1dfc6b74957b503a24edb8492849c06",
+    "td3_nll_f64": {"bytes": 979_578_880, "events": 2_000_000, "fp64_pipe": 0.8637, "sources": _TD3_SRC,
+                    "sha256": "15a1dce360c984926ea5ec34c819b480248a0a047f521fc610f49a88bdb6ef24",
                     "profile": "profiles/td3_nll_kernel_td3_2M.md"},
-    "td4_nll_grad_f32": {"bytes": 171_238_912, "events": 2_000_000, "sources": _TD4_SRC,
-                         "sha256": "205d58a0b40d18e7da02e280a41bda933b34a08e2a46c64f54baf03126e7d842",
+    "td4_nll_grad_f32": {"bytes": 171_327_232, "events": 2_000_000, "sources": _TD4_SRC,
+                         "sha256": "1ad883a60391ea71066001dbbc4b8f77bf7da4273223c8e9bd72b4e9dc9544a3",
                          "profile": "profiles/td4_nll_f32_kernel_c4_2M.md"},
-    "td4_nll_f64": {"bytes": 339_621_632, "events": 2_000_000, "fp64_pipe": 0.8663, "sources": _TD4_SRC,
-                    "sha256": "205d58a0b40d18e7da02e280a41bda933b34a08e2a46c64f54baf03126e7d842",
+    "td4_nll_f64": {"bytes": 339_682_304, "events": 2_000_000, "fp64_pipe": 0.8662, "sources": _TD4_SRC,
+                    "sha256": "1ad883a60391ea71066001dbbc4b8f77bf7da4273223c8e9bd72b4e9dc9544a3",
                     "profile": "profiles/td4_nll_f64_kernel_c4_2M.md"},
 }
 
