@@ -352,6 +352,17 @@ extern "C" int goo_fit(goo_model* model, const goo_dataset* ds, double* theta, c
         if (log_level() >= 2) std::fprintf(stderr, "[goo] fit refine step=%d edm=%.3e moved=%d\n", step, edm, (int)moved);
         if (!moved) break;
       }
+      // errors (and the final EDM) from the Hessian at the minimum: FP32 gradients when that
+      // Hessian is positive definite, else FP64 ones
+      std::vector<double> H2, Hi2;
+      obj.precision = opt.precision;
+      bool pd2 = hessian(obj, x, H2) && positive_definite(n, H2);
+      obj.precision = GOO_F64;
+      if (!pd2) pd2 = hessian(obj, x, H2) && positive_definite(n, H2);
+      if (pd2 && invert(n, H2, Hi2)) {
+        Hi = Hi2;
+        edm = edm_of(g);
+      }
     }
     obj.precision = opt.precision;
   } else if (n > 0 && (opt.polish || errors_out)) {
