@@ -319,16 +319,14 @@ extern "C" int goo_fit(goo_model* model, const goo_dataset* ds, double* theta, c
   const bool refine = opt.refine && opt.polish && opt.precision == GOO_F32 && opt.gradient == GOO_GRAD_ADJOINT;
   if (n > 0 && refine) {
     // FP64 refinement of an FP32 fit: near the minimum the FP32 gradient's rounding is no
-    // longer small against the curvature of a large sample.  The Hessian comes from FP32
-    // gradients when it is positive definite, else from FP64 ones; Newton steps then use FP64
-    // gradients with that fixed Hessian, each accepted when the EDM drops.
-    bool pd = hessian(obj, x, H) && positive_definite(n, H);
-    obj.precision = GOO_F64;
-    if (!pd) pd = hessian(obj, x, H) && positive_definite(n, H);
-    if (pd && invert(n, H, Hi) && obj.value_grad(x.data(), &f, g.data())) {
-      have_h = true;
+    // longer small against the curvature of a large sample.
+    // Newton steps with a fixed inverse Hessian on FP64 gradients, each accepted when the
+    // EDM drops; returns false if the FP64 gradient could not be evaluated at x
+    std::vector<double> dx(n);
+    auto newton = [&]() {
+      obj.precision = GOO_F64;
+      if (!obj.value_grad(x.data(), &f, g.data())) return false;
       edm = edm_of(g);
-      std::vector<double> dx(n);
       for (int step = 0; step < 6 && edm >= 1e-4 * opt.edm_tol; ++step) {
         for (int a = 0; a < n; ++a) {
           dx[a] = 0.0;
@@ -351,6 +349,27 @@ extern "C" int goo_fit(goo_model* model, const goo_dataset* ds, double* theta, c
         }
         if (log_level() >= 2) std::fprintf(stderr, "[goo] fit refine step=%d edm=%.3e moved=%d\n", step, edm, (int)moved);
         if (!moved) break;
+      }
+      return true;
+    };
+    // the Hessian from FP32 gradients when it is positive definite, else (or when the steps
+    // stall above the tolerance) from FP64 gradients
+    obj.precision = opt.precision;
+    bool pd = hessian(obj, x, H) && positive_definite(n, H) && invert(n, H, Hi);
+    bool h64 = false;
+    if (!pd) {
+      obj.precision = GOO_F64;
+      pd = hessian(obj, x, H) && positive_definite(n, H) && invert(n, H, Hi);
+      h64 = true;
+    }
+    if (pd && newton()) {
+      have_h = true;
+      if (edm >= opt.edm_tol && !h64) {
+        obj.precision = GOO_F64;
+        if (hessian(obj, x, H) && positive_definite(n, H) && invert(n, H, Hi)) {
+          h64 = true;
+          newton();
+        }
       }
       // errors (and the final EDM) from the Hessian at the minimum: FP32 gradients when that
       // Hessian is positive definite, else FP64 ones
