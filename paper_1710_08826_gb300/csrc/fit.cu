@@ -135,13 +135,15 @@ bool invert(int n, const std::vector<double>& A, std::vector<double>& inv) {
   return true;
 }
 
-// Symmetrised central-difference Hessian of the gradient in scaled coordinates.
-bool hessian(Objective& obj, const std::vector<double>& x, std::vector<double>& H) {
+// Symmetrised central-difference Hessian of the gradient in scaled coordinates, with step
+// 1e-3 or, if `steps` is given, steps[a] along coordinate a.
+bool hessian(Objective& obj, const std::vector<double>& x, std::vector<double>& H,
+             const std::vector<double>* steps = nullptr) {
   const int n = (int)x.size();
   H.assign((size_t)n * n, 0.0);
   std::vector<double> xp = x, gp(n), gm(n);
-  const double h = 1e-3;
   for (int a = 0; a < n; ++a) {
+    const double h = steps ? (*steps)[a] : 1e-3;
     double f;
     xp[a] = x[a] + h;
     if (!obj.value_grad(xp.data(), &f, gp.data())) return false;
@@ -353,9 +355,13 @@ extern "C" int goo_fit(goo_model* model, const goo_dataset* ds, double* theta, c
       return true;
     };
     // the Hessian from FP32 gradients when it is positive definite, else (or when the steps
-    // stall above the tolerance) from FP64 gradients
+    // stall above the tolerance) from FP64 gradients.  The FP32 differences step a quarter of
+    // each parameter's error as BFGS estimates it (at least 1e-3): on a large sample the error
+    // is small, and a fixed step would leave the gradient change within the FP32 rounding.
+    std::vector<double> hsteps(n);
+    for (int a = 0; a < n; ++a) hsteps[a] = std::fmax(1e-3, 0.25 * std::sqrt(std::fmax(Hinv[a * n + a], 0.0)));
     obj.precision = opt.precision;
-    bool pd = hessian(obj, x, H) && positive_definite(n, H) && invert(n, H, Hi);
+    bool pd = hessian(obj, x, H, &hsteps) && positive_definite(n, H) && invert(n, H, Hi);
     bool h64 = false;
     if (!pd) {
       obj.precision = GOO_F64;
@@ -372,10 +378,12 @@ extern "C" int goo_fit(goo_model* model, const goo_dataset* ds, double* theta, c
         }
       }
       // errors (and the final EDM) from the Hessian at the minimum: FP32 gradients when that
-      // Hessian is positive definite, else FP64 ones
+      // Hessian is positive definite (with the fixed step, else the error-scaled steps), else
+      // FP64 ones
       std::vector<double> H2, Hi2;
       obj.precision = opt.precision;
       bool pd2 = hessian(obj, x, H2) && positive_definite(n, H2);
+      if (!pd2) pd2 = hessian(obj, x, H2, &hsteps) && positive_definite(n, H2);
       obj.precision = GOO_F64;
       if (!pd2) pd2 = hessian(obj, x, H2) && positive_definite(n, H2);
       if (pd2 && invert(n, H2, Hi2)) {
