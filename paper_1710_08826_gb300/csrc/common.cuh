@@ -371,8 +371,6 @@ __device__ __forceinline__ void block_reduce_to_partials(ddf (&v)[NS], int nslot
   }
 }
 
-// After every block has written its partials: take a ticket.  True in the block that draws
-// the last one; every partial is then visible to it.  The caller resets the ticket.
 // Completion word of a result record (kResultFlag): every thread of the last block calls
 // this after its last write to `result`, so that a host polling the word sees the whole record.
 __device__ __forceinline__ void result_complete(double* result) {
@@ -381,6 +379,8 @@ __device__ __forceinline__ void result_complete(double* result) {
   if (threadIdx.x == 0) *(volatile double*)(result + kResultFlag) = 1.0;
 }
 
+// After every block has written its partials: take a ticket.  True in the block that draws
+// the last one; every partial is then visible to it.  The caller resets the ticket.
 __device__ __forceinline__ bool last_block_ticket(unsigned* ticket, int nblocks) {
   __shared__ bool is_last;
   __threadfence();
