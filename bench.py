@@ -43,32 +43,32 @@ ISSUE_PEAK = 152 * 4 * 2.07e9
 NCU_RECORDS = {
     "sop_nll_grad_f32": {"bytes": 126_027_776, "events": 10_000_000, "warp_inst": 29_148_206, "issue_active": 0.4692,
                          "sources": _SOP_SRC,
-                         "sha256": "532114ccab9a6c0fe787e7bb5a3c283973e352febfa8cca9ee69684dad089269",
+                         "sha256": "774529ae45f97a2caa51d78f986f0679f26a869c940a5b39fd5cba0470d0089a",
                          "profile": "profiles/sop_event2_kernel_f32_c2_10M.md"},
     "sop_nll_f64": {"bytes": 243_409_920, "events": 10_000_000, "fp64_pipe": 0.8625, "sources": _SOP_SRC,
-                    "sha256": "532114ccab9a6c0fe787e7bb5a3c283973e352febfa8cca9ee69684dad089269",
+                    "sha256": "774529ae45f97a2caa51d78f986f0679f26a869c940a5b39fd5cba0470d0089a",
                     "profile": "profiles/sop_event_kernel_f64_c2_10M.md"},
     "coh_nll_grad_f32": {"bytes": 323_350_784, "events": 5_000_000, "sources": _COH_SRC,
-                         "sha256": "08f310ad89453fbd7d0a57941eaa455389409c25c04cc8f25e2ca99d0c0435cf",
+                         "sha256": "d630025ad63b1bf75cd08f8b75c5dd9fa0cf90fa90f07116bc0aa3c44ed92126",
                          "profile": "profiles/coh_nll_staged_kernel_f32_c3_5M.md"},
     "coh_nll_f64": {"bytes": 643_376_128, "events": 5_000_000, "fp64_pipe": 0.87, "sources": _COH_SRC,
-                    "sha256": "08f310ad89453fbd7d0a57941eaa455389409c25c04cc8f25e2ca99d0c0435cf",
+                    "sha256": "d630025ad63b1bf75cd08f8b75c5dd9fa0cf90fa90f07116bc0aa3c44ed92126",
                     "profile": "profiles/coh_nll_kernel_f64_c3_5M.md"},
     "coh_ls_grad_f32": {"bytes": 40_096_000, "events": 5_000_000, "warp_inst": 313_731_120, "issue_active": 0.6438,
                         "sources": _COH_SRC,
-                        "sha256": "08f310ad89453fbd7d0a57941eaa455389409c25c04cc8f25e2ca99d0c0435cf",
+                        "sha256": "d630025ad63b1bf75cd08f8b75c5dd9fa0cf90fa90f07116bc0aa3c44ed92126",
                         "profile": "profiles/coh_ls_kernel_f32_c3_floating_5M.md"},
     "td3_nll_grad_f32": {"bytes": 524_228_608, "events": 2_000_000, "sources": _TD3_SRC,
-                         "sha256": "15a1dce360c984926ea5ec34c819b480248a0a047f521fc610f49a88bdb6ef24",
+                         "sha256": "3fd4b324cd55da187ae13132a503cf027b818697f28a417fb898708e2f694dd0",
                          "profile": "profiles/td3_nll_kernel_td3_2M.md"},
     "td3_nll_f64": {"bytes": 979_578_880, "events": 2_000_000, "fp64_pipe": 0.8637, "sources": _TD3_SRC,
-                    "sha256": "15a1dce360c984926ea5ec34c819b480248a0a047f521fc610f49a88bdb6ef24",
+                    "sha256": "3fd4b324cd55da187ae13132a503cf027b818697f28a417fb898708e2f694dd0",
                     "profile": "profiles/td3_nll_kernel_td3_2M.md"},
     "td4_nll_grad_f32": {"bytes": 171_327_232, "events": 2_000_000, "sources": _TD4_SRC,
-                         "sha256": "1ad883a60391ea71066001dbbc4b8f77bf7da4273223c8e9bd72b4e9dc9544a3",
+                         "sha256": "d4b7fe00f9c26703c33ae7dcdd5025d43125aba1871d08e83bd7cbe17d398041",
                          "profile": "profiles/td4_nll_f32_kernel_c4_2M.md"},
     "td4_nll_f64": {"bytes": 339_682_304, "events": 2_000_000, "fp64_pipe": 0.8662, "sources": _TD4_SRC,
-                    "sha256": "1ad883a60391ea71066001dbbc4b8f77bf7da4273223c8e9bd72b4e9dc9544a3",
+                    "sha256": "d4b7fe00f9c26703c33ae7dcdd5025d43125aba1871d08e83bd7cbe17d398041",
                     "profile": "profiles/td4_nll_f64_kernel_c4_2M.md"},
 }
 
