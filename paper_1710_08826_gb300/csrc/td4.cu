@@ -57,6 +57,7 @@ template <typename T>
 struct Td4Args {
   T cr[kTdMaxAmp], ci[kTdMaxAmp], br[kTdMaxAmp], bi[kTdMaxAmp];
   T G, x, y, s;  // 1/tau, mixing, resolution in the path's precision
+  TimeCoef<T> tc;  // the same with the moment-series coefficients (timeterms.cuh)
   T wa[kWMax];   // Weideman coefficients (constant term first)
   T wL;
   int wN, K, n_params, planes;
@@ -152,7 +153,7 @@ __global__ void td4_cache_kernel(const Td4Dev* __restrict__ tdp, Td4Cols<T> cols
 
 template <typename T>
 __device__ __forceinline__ void time_terms(const Td4Args<T>& a, T t, TimeTerms<T>& R) {
-  time_terms_g<T>(a.G, a.x, a.y, a.s, a.wa, a.wN, a.wL, t, R);
+  time_terms_g<T>(a.tc, a.wa, a.wN, a.wL, t, R);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -187,8 +188,8 @@ __device__ __forceinline__ void td4_event(const Td4Args<T>& a, const T (&ar)[KB]
   time_terms<T>(a, t, tt);
   const T AA = Ar * Ar + Ai * Ai, BB = Br * Br + Bi * Bi;
   const T ABr = Ar * Br + Ai * Bi, ABi = Ai * Br - Ar * Bi;  // A conj(B)
-  const T hp = T(0.5) * (AA + BB), hm = T(0.5) * (AA - BB);
-  const T R = hp * tt.Tch + hm * tt.Tc + ABr * tt.Tsh + ABi * tt.Ts;
+  // R = |A|^2 P + |B|^2 Q + Re(A B*) T_sh + Im(A B*) T_s with P, Q = (T_ch +- T_c)/2
+  const T R = AA * tt.P + BB * tt.Q + ABr * tt.Tsh + ABi * tt.Ts;
   if (!(R > T(0))) {
     acc.bad++;
     return;
@@ -197,8 +198,8 @@ __device__ __forceinline__ void td4_event(const Td4Args<T>& a, const T (&ar)[KB]
   else acc.lf64 += log(R);
   if constexpr (GRAD) {
     const T invR = T(1) / R;
-    // V / R, V = (T_ch + T_c) A* + (T_sh - i T_s) B*
-    const T c1 = (tt.Tch + tt.Tc) * invR, sh = tt.Tsh * invR, ss = tt.Ts * invR;
+    // V / R, V = (T_ch + T_c) A* + (T_sh - i T_s) B* = 2 P A* + (T_sh - i T_s) B*
+    const T c1 = T(2) * tt.P * invR, sh = tt.Tsh * invR, ss = tt.Ts * invR;
     const T Vr = c1 * Ar + sh * Br - ss * Bi;
     const T Vi = -c1 * Ai - sh * Bi - ss * Br;
 #pragma unroll
@@ -208,7 +209,7 @@ __device__ __forceinline__ void td4_event(const Td4Args<T>& a, const T (&ar)[KB]
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      acc.lt[j] += (hp * tt.d[j][0] + hm * tt.d[j][2] + ABr * tt.d[j][1] + ABi * tt.d[j][3]) * invR;
+      acc.lt[j] += (AA * tt.d[j][0] + BB * tt.d[j][1] + ABr * tt.d[j][2] + ABi * tt.d[j][3]) * invR;
   }
 }
 
@@ -419,12 +420,13 @@ __global__ void __launch_bounds__(kBlock, 2) td4_nll_f32_kernel(const __grid_con
 #pragma unroll
   for (int j = 0; j < 4; ++j) acc.lt[j] = 0.f;
   __syncthreads();  // barriers initialised before any thread waits on them
+  const long long wlim = tile_wait_limit(counters);
   int j = 0;
   bool failed = false;
   for (; tile_of(j) < tb1; ++j) {
     const int64_t t = tile_of(j);
     const int st = j % NST;
-    const bool ok_wait = mbar_wait(&s_bar[st], (unsigned)(j / NST) & 1u);
+    const bool ok_wait = mbar_wait(&s_bar[st], (unsigned)(j / NST) & 1u, wlim);
     if (ok_wait) {
       const float4* sb = s_tile + (size_t)st * stage_f4;
       const float* stt = (const float*)(sb + (size_t)planes * TE);
@@ -717,10 +719,11 @@ static void td4_args(const goo_model* m, const double* theta, int64_t n_total, T
     a.par_im[k] = d.par_im[k];
   }
   for (int j = 0; j < 4; ++j) a.par_t[j] = d.par_t[j];
-  a.x = (T)theta[d.par_t[0]];
-  a.y = (T)theta[d.par_t[1]];
-  a.G = (T)(1.0 / theta[d.par_t[2]]);
-  a.s = (T)theta[d.par_t[3]];
+  fill_time_coef<T>(a.tc, theta[d.par_t[0]], theta[d.par_t[1]], theta[d.par_t[2]], theta[d.par_t[3]]);
+  a.x = a.tc.x;
+  a.y = a.tc.y;
+  a.G = a.tc.G;
+  a.s = a.tc.s;
   const WeidemanTables& w = weideman();
   a.wN = sizeof(T) == 4 ? kWN32 : kWN64;
   for (int j = 0; j < a.wN; ++j) a.wa[j] = (T)(sizeof(T) == 4 ? w.a32[j] : w.a64[j]);

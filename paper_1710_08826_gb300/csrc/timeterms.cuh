@@ -2,8 +2,34 @@
 // (td4.cu: four-body; dalitz.cu: three-body): the Faddeeva function w(z) (Weideman's
 // rational approximation, J. A. C. Weideman, SIAM J. Numer. Anal. 31 (1994) 1497; host and
 // device), the convolution E(g; t, s) of e^{-g t'} (t' >= 0) with a Gaussian resolution for
-// real and complex g, and the four mixing terms T_ch, T_sh, T_c, T_s with their derivatives.
-// The formulas are stated at the top of td4.cu.
+// real and complex g, and the mixing terms with their derivatives.  The formulas are stated
+// at the top of td4.cu.
+//
+// The rate needs the four terms only through
+//   R = |A|^2 P + |B|^2 Q + Re(A B*) T_sh + Im(A B*) T_s,
+//   P = (T_ch + T_c)/2,  Q = (T_ch - T_c)/2,
+// i.e. the convolutions of e^{-G t'} [cosh(y G t') +- cos(x G t')]/2, e^{-G t'} sinh(y G t')
+// and e^{-G t'} sin(x G t').  For small mixing Q, T_sh and T_s are tiny differences of nearly
+// equal convolved exponentials (Q = O(x^2 + y^2), T_sh = O(y)): formed as such differences in
+// FP32 they keep only a few significant digits, and so do their derivatives.  Where
+// z = max(|x|, |y|) G (max(t, 0) + 6 s) is small they are therefore summed as power series in
+// the moments of the resolution-convolved exponential,
+//   M_n(t) = int_0^inf t'^n e^{-G t'} N(t - t'; 0, s) dt',
+//   u_n = G^n M_n / n!,
+//   P = sum_m a_m u_2m,  Q = sum_m b_m u_2m,  T_sh = sum_m y^(2m+1) u_(2m+1),
+//   T_s = sum_m (-1)^m x^(2m+1) u_(2m+1),
+//   a_m, b_m = (y^2m +- (-1)^m x^2m) / 2,
+// from the Taylor series of cosh and cos, with every term of one sign for t > G s^2.  The
+// moments follow from M_0 = E(G) (one erfcx) by the recurrence obtained by integrating
+// t' N(t - t') by parts,
+//   M_1 = (t - G s^2) M_0 + s^2 N(t),  M_(n+1) = (t - G s^2) M_n + n s^2 M_(n-1),
+// i.e. u_(n+1) = (G (t - G s^2) u_n + G^2 s^2 u_(n-1)) / (n + 1).  Derivatives:
+//   G d u_n / d G = n u_n - (n + 1) u_(n+1)        (d M_n / d G = -M_(n+1)),
+//   d u_n / d s = s d^2 u_n / d t^2                 (heat equation of the Gaussian)
+//              = s [G^2 (u_n - 2 u_(n-1) + u_(n-2)) + c_n],
+//   c_0 = N'(t) - G N(t), c_1 = G N(t), c_n = 0 for n >= 2 (from d M_n / d t = n M_(n-1)
+//   - G M_n + [n = 0] N(t)).  Elsewhere (large mixing) the terms come from the Faddeeva path,
+// where the differences are not small.
 #pragma once
 
 #include <cmath>
@@ -77,9 +103,58 @@ static const WeidemanTables& weideman() {
 // ---------------------------------------------------------------------------------------
 template <typename T>
 struct TimeTerms {
-  T Tch, Tsh, Tc, Ts;
-  T d[4][4];  // d[param][term], param = x, y, tau, sigma_t; term = ch, sh, c, s
+  T P, Q, Tsh, Ts;
+  T d[4][4];  // d[param][term], param = x, y, tau, sigma_t; term = P, Q, sh, s
 };
+
+// Orders of the moment series: u_0 .. u_(2K+2) (the G-derivative of u_(2K+1) needs
+// u_(2K+2)), and the largest z = max(|x|,|y|) G (max(t,0) + 6 s) at which the truncated
+// series is used.  FP32: K = 4, z <= 0.5 (first omitted term of Q below 1e-8 of Q);
+// FP64: K = 6, z <= 0.35 (below 1e-16 of Q).
+template <typename T>
+struct SeriesOrder {
+  static constexpr int K = sizeof(T) == 4 ? 4 : 6;
+  static constexpr double zmax = sizeof(T) == 4 ? 0.5 : 0.35;
+};
+
+// Per-theta constants of the decay-time terms in the path's precision: the series
+// coefficients and their derivatives, prepared on the host in FP64 from the rounded x, y.
+template <typename T>
+struct TimeCoef {
+  static constexpr int K = SeriesOrder<T>::K;
+  T G, x, y, s;
+  T zs;                        // max(|x|, |y|) G
+  T a[K + 1], b[K + 1];        // P, Q coefficients of u_2m (a_0 = 1, b_0 = 0)
+  T ysh[K + 1], xs[K + 1];     // T_sh, T_s coefficients of u_(2m+1)
+  T dax[K + 1], day[K + 1];    // d a_m / dx (= -d b_m / dx), d a_m / dy (= d b_m / dy)
+  T dshy[K + 1], dsx[K + 1];   // d ysh_m / dy, d xs_m / dx
+};
+
+#ifndef __CUDACC_RTC__
+template <typename T>
+inline void fill_time_coef(TimeCoef<T>& c, double x64, double y64, double tau, double s64) {
+  constexpr int K = TimeCoef<T>::K;
+  c.G = (T)(1.0 / tau);
+  c.x = (T)x64;
+  c.y = (T)y64;
+  c.s = (T)s64;
+  const double x = (double)c.x, y = (double)c.y, G = (double)c.G;
+  c.zs = (T)(std::fmax(std::fabs(x), std::fabs(y)) * G);
+  for (int m = 0; m <= K; ++m) {
+    const double sg = (m & 1) ? -1.0 : 1.0;
+    const double y2m = std::pow(y, 2 * m), x2m = std::pow(x, 2 * m);
+    c.a[m] = (T)(0.5 * (y2m + sg * x2m));
+    c.b[m] = (T)(0.5 * (y2m - sg * x2m));
+    c.day[m] = (T)(m > 0 ? m * std::pow(y, 2 * m - 1) : 0.0);
+    c.dax[m] = (T)(m > 0 ? sg * m * std::pow(x, 2 * m - 1) : 0.0);
+    c.ysh[m] = (T)(y2m * y);
+    c.xs[m] = (T)(sg * x2m * x);
+    c.dshy[m] = (T)((2 * m + 1) * y2m);
+    c.dsx[m] = (T)(sg * (2 * m + 1) * x2m);
+  }
+  c.b[0] = (T)0;
+}
+#endif
 
 template <typename T>
 __device__ __forceinline__ T td_erfcx(T u) {
@@ -139,41 +214,138 @@ __device__ __forceinline__ void conv_complex(T gr, T gi, T t, T s, T gauss, cons
   dsi = g2r * Ei + g2i * Er - gi * k * gauss;
 }
 
-// The four decay-time terms at the observed time t and their derivatives with respect to
-// (x, y, tau, sigma_t), for Gamma = G, mixing (x, y), resolution s.
+// The decay-time terms at the observed time t from the convolved exponentials (Faddeeva
+// path, any mixing) and their derivatives with respect to (x, y, tau, sigma_t), for
+// Gamma = G, mixing (x, y), resolution s; gauss = exp(-t^2 / 2 s^2).
 template <typename T>
-__device__ __forceinline__ void time_terms_g(T G, T x, T y, T s, const T* wa, int wN, T wL, T t, TimeTerms<T>& R) {
-  const T gauss = td_exp<T>(-t * t / (T(2) * s * s));
+__device__ __forceinline__ void time_terms_direct(T G, T x, T y, T s, const T* wa, int wN, T wL, T t, T gauss,
+                                                  TimeTerms<T>& R) {
   const T gp = G * (T(1) - y), gm = G * (T(1) + y);
   T Ep, dEgp, dEsp, Em, dEgm, dEsm;
   conv_real<T>(gp, t, s, gauss, Ep, dEgp, dEsp);
   conv_real<T>(gm, t, s, gauss, Em, dEgm, dEsm);
   T Ecr, Eci, dgr, dgi, dsr, dsi;
   conv_complex<T>(G, -G * x, t, s, gauss, wa, wN, wL, Ecr, Eci, dgr, dgi, dsr, dsi);
-  R.Tch = T(0.5) * (Ep + Em);
+  const T Tch = T(0.5) * (Ep + Em);
+  R.P = T(0.5) * (Tch + Ecr);
+  R.Q = T(0.5) * (Tch - Ecr);
   R.Tsh = T(0.5) * (Ep - Em);
-  R.Tc = Ecr;
   R.Ts = Eci;
+  // per parameter the derivatives of (T_ch, T_c) map to P, Q as the terms do
+  T dch[4], dc[4];
   // x: dgc/dx = -i G  ->  (-iG)(dgr + i dgi) = G dgi - i G dgr
-  R.d[0][0] = T(0);
-  R.d[0][1] = T(0);
-  R.d[0][2] = G * dgi;
+  dch[0] = T(0);
+  dc[0] = G * dgi;
+  R.d[0][2] = T(0);
   R.d[0][3] = -G * dgr;
   // y: dg+/dy = -G, dg-/dy = +G
-  R.d[1][0] = T(0.5) * G * (dEgm - dEgp);
-  R.d[1][1] = -T(0.5) * G * (dEgp + dEgm);
-  R.d[1][2] = T(0);
+  dch[1] = T(0.5) * G * (dEgm - dEgp);
+  dc[1] = T(0);
+  R.d[1][2] = -T(0.5) * G * (dEgp + dEgm);
   R.d[1][3] = T(0);
   // tau: dg/dtau = -g G
-  R.d[2][0] = -T(0.5) * G * (dEgp * gp + dEgm * gm);
-  R.d[2][1] = -T(0.5) * G * (dEgp * gp - dEgm * gm);
-  R.d[2][2] = -G * (dgr * G - dgi * (-G * x));  // Re((dgr + i dgi)(-gc G)), gc = (G, -G x)
+  dch[2] = -T(0.5) * G * (dEgp * gp + dEgm * gm);
+  dc[2] = -G * (dgr * G - dgi * (-G * x));  // Re((dgr + i dgi)(-gc G)), gc = (G, -G x)
+  R.d[2][2] = -T(0.5) * G * (dEgp * gp - dEgm * gm);
   R.d[2][3] = -G * (dgr * (-G * x) + dgi * G);
   // sigma_t
-  R.d[3][0] = T(0.5) * (dEsp + dEsm);
-  R.d[3][1] = T(0.5) * (dEsp - dEsm);
-  R.d[3][2] = dsr;
+  dch[3] = T(0.5) * (dEsp + dEsm);
+  dc[3] = dsr;
+  R.d[3][2] = T(0.5) * (dEsp - dEsm);
   R.d[3][3] = dsi;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    R.d[j][0] = T(0.5) * (dch[j] + dc[j]);
+    R.d[j][1] = T(0.5) * (dch[j] - dc[j]);
+  }
+}
+
+// The decay-time terms by the moment series (small mixing; see the top of this file).
+template <typename T>
+__device__ __forceinline__ void time_terms_series(const TimeCoef<T>& c, T t, T gauss, TimeTerms<T>& R) {
+  constexpr int K = TimeCoef<T>::K;
+  constexpr int NU = 2 * K + 3;
+  const T G = c.G, s = c.s;
+  const T s2 = s * s;
+  T E0, dEg_unused, dEs_unused;
+  conv_real<T>(G, t, s, gauss, E0, dEg_unused, dEs_unused);
+  const T phi = T(0.39894228040143267794) / s * gauss;  // N(t; 0, s)
+  const T v = t - G * s2;
+  const T Gv = G * v, G2s2 = G * G * s2;
+  T u[NU];
+  u[0] = E0;
+  u[1] = G * (v * E0 + s2 * phi);
+#pragma unroll
+  for (int n = 1; n < NU - 1; ++n) u[n + 1] = (Gv * u[n] + G2s2 * u[n - 1]) * T(1.0 / (n + 1));
+  // d u_n / d s (heat equation) and G d u_n / d G
+  const T G2 = G * G;
+  auto su = [&](int n) -> T {
+    const T um1 = n >= 1 ? u[n - 1] : T(0), um2 = n >= 2 ? u[n - 2] : T(0);
+    const T cn = n == 0 ? (-t / s2 - G) * phi : (n == 1 ? G * phi : T(0));
+    return s * (G2 * ((u[n] - um1) - (um1 - um2)) + cn);
+  };
+  auto gu = [&](int n) -> T { return T(n) * u[n] - T(n + 1) * u[n + 1]; };
+  T P = u[0], Q = T(0), Tsh = T(0), Ts = T(0);
+  T Px = T(0), Py = T(0), PG = gu(0), Ps = su(0), QG = T(0), Qs = T(0);
+  T Shy = T(0), ShG = T(0), Shs = T(0), Sx = T(0), SG = T(0), Ss = T(0);
+#pragma unroll
+  for (int m = 1; m <= K; ++m) {
+    const T ue = u[2 * m];
+    P += c.a[m] * ue;
+    Q += c.b[m] * ue;
+    Px += c.dax[m] * ue;
+    Py += c.day[m] * ue;
+    const T ge = gu(2 * m), se = su(2 * m);
+    PG += c.a[m] * ge;
+    QG += c.b[m] * ge;
+    Ps += c.a[m] * se;
+    Qs += c.b[m] * se;
+  }
+#pragma unroll
+  for (int m = 0; m <= K; ++m) {
+    const T uo = u[2 * m + 1];
+    Tsh += c.ysh[m] * uo;
+    Ts += c.xs[m] * uo;
+    Shy += c.dshy[m] * uo;
+    Sx += c.dsx[m] * uo;
+    const T go = gu(2 * m + 1), so = su(2 * m + 1);
+    ShG += c.ysh[m] * go;
+    SG += c.xs[m] * go;
+    Shs += c.ysh[m] * so;
+    Ss += c.xs[m] * so;
+  }
+  R.P = P;
+  R.Q = Q;
+  R.Tsh = Tsh;
+  R.Ts = Ts;
+  // x: P and Q move oppositely; T_sh does not depend on x, T_s not on y
+  R.d[0][0] = Px;
+  R.d[0][1] = -Px;
+  R.d[0][2] = T(0);
+  R.d[0][3] = Sx;
+  R.d[1][0] = Py;
+  R.d[1][1] = Py;
+  R.d[1][2] = Shy;
+  R.d[1][3] = T(0);
+  // tau: d / d tau = -G (G d / d G)
+  R.d[2][0] = -G * PG;
+  R.d[2][1] = -G * QG;
+  R.d[2][2] = -G * ShG;
+  R.d[2][3] = -G * SG;
+  R.d[3][0] = Ps;
+  R.d[3][1] = Qs;
+  R.d[3][2] = Shs;
+  R.d[3][3] = Ss;
+}
+
+// The decay-time terms at the observed time t and their derivatives: the moment series where
+// z = max(|x|, |y|) G (max(t, 0) + 6 s) is below SeriesOrder<T>::zmax, else the Faddeeva path.
+template <typename T>
+__device__ __forceinline__ void time_terms_g(const TimeCoef<T>& c, const T* wa, int wN, T wL, T t, TimeTerms<T>& R) {
+  const T gauss = td_exp<T>(-t * t / (T(2) * c.s * c.s));
+  const T z = c.zs * ((t > T(0) ? t : T(0)) + T(6) * c.s);
+  if (z < T(SeriesOrder<T>::zmax)) time_terms_series<T>(c, t, gauss, R);
+  else time_terms_direct<T>(c.G, c.x, c.y, c.s, wa, wN, wL, t, gauss, R);
 }
 
 

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 import torch
 
+import gradscale
 import synth
 from oracle import dalitz as od
 from oracle import fit as ofit
@@ -188,7 +189,14 @@ def test_floating_full_size(goo, ctx, precision):
     rnll, rg = _oracle_nll_grad_chunked(ref, d, c, theta)
     assert abs(nll - rnll) <= TOL_NLL[precision] * abs(rnll), (nll, rnll)
     scale = np.max(np.abs(rg))
-    # FP32: every event's derivative carries a few 1e-7 relative error, and 5M of them
-    # cancel to a gradient far below their summed magnitude
-    tol = 1e-6 if precision == "f64" else 2e-3
-    assert np.max(np.abs(g - rg)) <= tol * scale, (g - rg) / scale
+    err = np.abs(g - rg)
+    assert np.max(err) <= TOL_GRAD[precision] * scale, err / scale
+    if precision == "f32":
+        # per component: below the gradient of a 0.02 sigma shift of the parameter (measured
+        # worst: 0.011 sigma, for a mass whose gradient on these uniform events is ~200 sigma
+        # from zero; 5e-5 of that component).  The full-size fit gate binds the fit at 0.01 sigma.
+        idx = np.flatnonzero(np.abs(rg) > 0)
+        d64, c64 = _prep(spec, data, mc, "f64")
+        ds64, _, model64 = _upload(goo, ctx, spec, d64, c64)
+        sig = gradscale.sigmas(model64, ds64, theta, idx)
+        assert np.all(err[idx] * sig[idx] <= 0.02), err[idx] * sig[idx]

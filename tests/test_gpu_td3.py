@@ -4,6 +4,7 @@ shards, a fit, the full-size configuration) against the oracle."""
 import numpy as np
 import pytest
 
+import gradscale
 import synth
 from oracle import td3 as ot
 
@@ -158,26 +159,22 @@ def test_full_size_configuration(goo, ctx):
     for precision in ("f64", "f32"):
         d, c = _prep(spec, data, mc, precision)
         ds, _, model = _build(goo, ctx, spec, d, c)
+        if precision == "f64":
+            model64, ds64 = model, ds
         nll, g = model.nll_grad(ds, th, precision)
         amps, grams = m.amplitudes(d, th), m.grams(c, th)
         rnll, rg = m.nll_grad(d, c, th, amps=amps, grams=grams)
         assert abs(nll - rnll) <= TOL_NLL[precision] * abs(rnll), (precision, nll, rnll)
+        err = np.abs(g - rg)
+        assert np.max(err) <= TOL_GRAD[precision] * np.max(np.abs(rg)), (precision, np.max(err) / np.max(np.abs(rg)))
         if precision == "f64":
-            assert np.max(np.abs(g - rg)) <= TOL_GRAD["f64"] * np.max(np.abs(rg))
+            assert np.all(err <= TOL_GRAD["f64"] * np.abs(rg) + 1e-9 * np.max(np.abs(rg)))
         else:
-            # each event's FP32 terms carry a relative error of a few 1e-7 times the event's
-            # condition number: A = sum c_k a_k and B are sums of larger terms that cancel
-            # where the amplitudes interfere destructively, and R combines four time terms
-            # that nearly cancel where |B| exceeds |A| (T_ch - T_c is second order in x, y).
-            # Uniform phase-space events sample such regions far more often than the model.
-            R, dR = m.rate(amps, d["t"], th, derivs=True)
-            cf = m.coefficients(th)
-            A, B = amps[0] @ cf, amps[1] @ cf
-            SA, SB = np.abs(amps[0]) @ np.abs(cf), np.abs(amps[1]) @ np.abs(cf)
-            T = ot.time_terms(d["t"], *(th[i] for i in m.tp))
-            AA, BB, AB = np.abs(A) ** 2, np.abs(B) ** 2, A * B.conj()
-            kappa = (SA ** 2 + SB ** 2) / (AA + BB) + (0.5 * (AA + BB) * np.abs(T[0]) + 0.5 * np.abs(AA - BB) * np.abs(T[2])
-                                                       + np.abs(AB.real * T[1]) + np.abs(AB.imag * T[3])) / R
-            mag = np.sum(kappa[:, None] * np.abs(dR / R[:, None]), axis=0)
-            err = np.abs(g - rg)
-            assert np.all(err <= 2e-6 * mag + TOL_GRAD["f32"] * np.max(np.abs(rg))), np.max(err / mag)
+            # per component: the error of each component is below the gradient of a 0.01 sigma
+            # shift of its parameter (measured worst: 0.005 sigma; 1e-4 of the component's own
+            # value for all but one, 1.1e-4).  The residual FP32 error comes from the amplitude
+            # sums of uniform phase-space events, where A and B interfere destructively far
+            # more often than under the model; the full-size fit gate covers the fit itself.
+            idx = np.flatnonzero(np.abs(rg) > 0)
+            sig = gradscale.sigmas(model64, ds64, th, idx)
+            assert np.all(err[idx] * sig[idx] <= 0.01), err[idx] * sig[idx]

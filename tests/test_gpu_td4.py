@@ -186,12 +186,9 @@ def test_full_size_configuration(goo, ctx):
         a = m.amplitudes(d)
         rnll, rg = m.nll_grad(d, m.amplitudes(c), th, a=a)
         assert abs(nll - rnll) <= TOL_NLL[precision] * abs(rnll), (precision, nll, rnll)
-        if precision == "f64":
-            assert np.max(np.abs(g - rg)) <= TOL_GRAD["f64"] * np.max(np.abs(rg))
-        else:
-            # each per-event term d log R_i / d theta carries the FP32 evaluation's relative
-            # error (a few 1e-7 over ~30 operations); the terms of 2M events cancel heavily,
-            # so the bound scales with the sum of their magnitudes, not with the gradient
-            R, dR = m.rate(a, d["t"], th, derivs=True)
-            mag = np.sum(np.abs(dR / R[:, None]), axis=0)
-            assert np.all(np.abs(g - rg) <= 2e-6 * mag + TOL_GRAD["f32"] * np.max(np.abs(rg))), (g - rg, mag)
+        err = np.abs(g - rg)
+        assert np.max(err) <= TOL_GRAD[precision] * np.max(np.abs(rg)), (precision, np.max(err) / np.max(np.abs(rg)))
+        # every component against its own value as well (measured FP32 worst: 4e-6; the decay-time
+        # terms are summed as moment series, so no cancelling difference of convolved
+        # exponentials limits them)
+        assert np.all(err <= TOL_GRAD[precision] * np.abs(rg)), (precision, err / np.abs(rg))
