@@ -179,6 +179,27 @@ int64_t goo_launch_count(const goo_ctx* ctx);
  * and clears the table when reset != 0.  It waits for the recorded launches to finish. */
 int goo_timing_enable(goo_ctx* ctx, int on);
 int goo_timing_read(goo_ctx* ctx, int max_entries, char* names, int64_t* counts, double* total_ms, int reset);
+/* Limit of the kernels' bounded waits.  The paper describes no failure handling; this call
+ * serves the library's own failure detection.  Kernels that stage their input tiles in
+ * shared memory by bulk copies wait for each tile on an mbarrier for at most `cycles` SM
+ * clocks (0 restores the default of 2e9 clocks, about one second at 2 GHz; at most
+ * 2^32 - 1).  A wait that runs out makes the evaluation return GOO_ERR_TIMEOUT (nll = +inf)
+ * while the context stays usable; before a block exits it always waits up to the default
+ * limit for its own copies still in flight.  A very small limit therefore turns evaluations
+ * whose copies have not landed in time into GOO_ERR_TIMEOUT without a fault, which is how
+ * the timeout path is tested.  The setting applies to every later call on ctx (evaluations,
+ * fits, servers); it is ordered on ctx's stream and the call returns once it is in place.
+ * GOO_ERR_ARG for a NULL context or a limit out of range. */
+int goo_set_wait_limit(goo_ctx* ctx, int64_t cycles);
+/* Failure-detection test hook (the paper describes no failure handling).  With tile >= 0 the
+ * first block of the staged FP32 kernels of the sum-of-products and three-body models does
+ * not issue the copies of its tile number `tile` (counted in the block's own order), so the
+ * waits for that tile run out after the wait limit and the evaluation returns
+ * GOO_ERR_TIMEOUT; nothing faults, and the block drains the copies it did issue before it
+ * exits.  tile = -1 clears the hook.  Ordered on ctx's stream; applies to later calls on ctx.
+ * Set a short wait limit first (goo_set_wait_limit), or each such evaluation waits about a
+ * second.  GOO_ERR_ARG for a NULL context or tile < -1. */
+int goo_debug_withhold_tile(goo_ctx* ctx, int64_t tile);
 
 /* ---- data (paper: DataSet, Fig. 1 and Sec. 4) ------------------------------------------------
  * Upload `ncols` (1..8) structure-of-arrays columns of n_events values each, of type `dtype`
@@ -297,11 +318,12 @@ int goo_model_set_jit(goo_model* model, int mode);
 int goo_model_jit_status(const goo_model* model);
 /* Compile the packed-pair event kernel for a K x L slot shape (K products of at most L
  * leaves; 1 <= K, L <= 4), with or without gradient lanes, for a leaf signature (4 bits per
- * slot k * L + l: the leaf's GOO_OP_* code, 0 for an empty slot), as goo_model_set_jit does
- * on a model's first evaluation, without loading it: needs no GPU.  For checking NVRTC and
- * the kernel sources on a machine before the first evaluation.  *cubin_bytes (if not NULL)
- * receives the image size.  GOO_ERR_CUDA with NVRTC's log in goo_last_error on failure. */
-int goo_jit_check(int K, int L, int grad, unsigned long long sig, int64_t* cubin_bytes);
+ * slot k * L + l: the leaf's GOO_OP_* code, 0 for an empty slot) and column map (2 bits per
+ * slot: the leaf's observable), as goo_model_set_jit does on a model's first evaluation,
+ * without loading it: needs no GPU.  For checking NVRTC and the kernel sources on a machine
+ * before the first evaluation.  *cubin_bytes (if not NULL) receives the image size.
+ * GOO_ERR_CUDA with NVRTC's log in goo_last_error on failure. */
+int goo_jit_check(int K, int L, int grad, unsigned long long sig, unsigned long long cols, int64_t* cubin_bytes);
 
 /* ---- fitting (paper: the FitManager, Fig. 1; Minuit 2 as the default minimiser, Sec. 4) -------
  * Minimises the NLL of `model` on `ds` over the parameters with free_mask[p] != 0, starting
@@ -415,6 +437,18 @@ int goo_combine_partials(int n_parts, int n_params, const double* parts, double*
  * arithmetic the kernels run be checked on the CPU.  out[0] = Re w, out[1] = Im w. */
 int goo_faddeeva(double re, double im, int precision, double* out);
 
+/* ---- FMA-pipe peaks -------------------------------------------------------------------------
+ * The paper quotes advertised single- and double-precision FLOP/s of its GPUs (Table 1); this
+ * call measures them on the context's device, as the denominators of the FP64 and FP32
+ * rooflines.  One launch of num_sms x 4 blocks of 256 threads, each thread running 8
+ * independent chains of iters x 16 fused multiply-adds, timed with CUDA events on ctx's stream
+ * after one untimed launch.  kind: GOO_PEAK_F64 (fma.rn.f64), GOO_PEAK_F32 (fma.rn.f32) or
+ * GOO_PEAK_F32X2 (packed fma.rn.f32x2, two FMAs per instruction).  fma_per_s (host) receives
+ * FMAs per second (FLOP/s = 2 x that), ms_out (host, nullable) the launch's duration.
+ * GOO_ERR_ARG for a NULL pointer, an unknown kind or iters outside 1 .. 2^24. */
+enum { GOO_PEAK_F64 = 0, GOO_PEAK_F32 = 1, GOO_PEAK_F32X2 = 2 };
+int goo_peak_fma(goo_ctx* ctx, int kind, int iters, double* fma_per_s, double* ms_out);
+
 /* ---- likelihood without device allocation ------------------------------------------------
  * The paper has no counterpart to this call.  It computes the same NLL and gradient as
  * goo_nll_grad for a sum/product model, but allocates nothing: no goo_ctx, goo_dataset or
@@ -434,12 +468,14 @@ int goo_faddeeva(double re, double im, int precision, double* out);
  * All intermediate device state lives in one file-scope device array of 1 MiB, which every
  * GPU that loads the library holds until the process exits.  Maximum sizes: n_params <= 32,
  * n_obs <= 4, <= 4 products of <= 4 leaves; larger requests fail with GOO_ERR_ARG or
- * GOO_ERR_UNSUPPORTED and a message.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call reuses the same array and clears its counters
- * first; the array keeps the previous call's contents otherwise.  Calls that overlap on the
- * GPU (different streams or host threads, same device) race on the array: serialise them.
- * The call returns after the result has been copied to the host. */
+ * GOO_ERR_UNSUPPORTED and a message.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress, which allocates nothing) with the caller's current device, so the
+ * call keeps working after a cudaDeviceReset.  Every call reuses the same array and clears
+ * its counters first; the array keeps the previous call's contents otherwise.  Calls that
+ * overlap on the GPU (different streams or host threads, same device) race on the array:
+ * serialise them.  The call copies the model block in and the result out on cuda_stream and
+ * synchronises that stream before it returns.  GOO_ERR_NONPOSITIVE_PDF and
+ * GOO_ERR_TIMEOUT as for goo_nll_grad (nll_out = +inf, grad_out zeroed). */
 int goo_nll_grad_static(const goo_node* nodes, int n_nodes, int n_params, int n_obs, const double* obs_lo,
                         const double* obs_hi, const goo_norm_spec* norm, const void* const* cols_dev,
                         int precision, int64_t n_events, const double* theta, void* cuda_stream,

@@ -79,7 +79,10 @@ struct Scratch {
   // result record.  Reused by every call on the context's stream.
   float2* partials = nullptr;
   size_t partials_cap = 0;          // in float2 elements
-  unsigned* counters = nullptr;     // [0]: ticket, [1]: non-positive events, [2..]: spare
+  // [0]: ticket, [1]: non-positive events, [kStatusWord]: a device wait gave up,
+  // [kWaitLimitWord]: the tile-wait limit (goo_set_wait_limit), [kWithholdWord]: the
+  // failure-detection test hook (goo_debug_withhold_tile), [5..]: spare
+  unsigned* counters = nullptr;
   double* result = nullptr;         // kResultDoubles doubles
   double* theta = nullptr;          // kMaxParams doubles
   double* host_pinned = nullptr;    // pinned staging: [0, 256) theta in, [256, 512) result out
@@ -119,6 +122,9 @@ struct goo_ctx {
   int num_sms = 0;
   int64_t launches = 0;
   int live = 0;  // datasets, models and servers created on this context and not yet freed
+  // limit of the kernels' waits for input tiles in SM clocks (0: the default, about one
+  // second); a copy of counters[kWaitLimitWord] for the kernels that take it as an argument
+  unsigned wait_limit = 0;
   goo::Scratch scratch;
   bool timing = false;
   std::vector<goo::TimedLaunch> pending;
@@ -281,11 +287,19 @@ __device__ __forceinline__ float2 rcp(float2 x) { return make_float2(rcp(x.x), r
 // ---------------------------------------------------------------------------------------
 // Bulk asynchronous copies global -> shared (the non-tensor TMA form, cp.async.bulk) that
 // signal an mbarrier with their byte count, and waits on that barrier with a time limit.
-// A wait that exceeds kWaitCycles SM clocks (about one second) gives up and returns false;
-// the caller records GOO_ERR_TIMEOUT in the device status word (kStatusWord) and drains.
+// A wait that exceeds its limit in SM clocks gives up and returns false; the caller records
+// GOO_ERR_TIMEOUT in the device status word (kStatusWord) and drains.  The limit of the
+// waits for input tiles is the context's setting in counters[kWaitLimitWord]
+// (goo_set_wait_limit; 0 selects kWaitCycles, about one second); the waits that drain a
+// block's own copies before it exits always allow kWaitCycles, so that no block leaves
+// while a copy into its shared memory is in flight.
 // ---------------------------------------------------------------------------------------
 constexpr long long kWaitCycles = 2000000000LL;
-constexpr int kStatusWord = 2;  // counters[2]: nonzero after a device wait gave up
+constexpr int kStatusWord = 2;     // counters[2]: nonzero after a device wait gave up
+constexpr int kWaitLimitWord = 3;  // counters[3]: limit of the tile waits in SM clocks (0: kWaitCycles)
+// counters[4]: failure-detection test hook (goo_debug_withhold_tile); 1 + the index of a tile
+// whose copies the first block of the staged kernels does not issue, 0: none
+constexpr int kWithholdWord = 4;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -318,13 +332,49 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
-// Waits for the phase with the given parity to complete; false after kWaitCycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  if (mbar_try_wait(bar, parity)) return true;
+// Non-blocking probe of the phase with the given parity (test_wait never suspends the thread).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n"
+      "  .reg .pred p;\n"
+      "  mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "  selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for the phase with the given parity to complete; false after `limit` SM clocks.  The
+// default limit probes with try_wait (which may suspend the thread for a system-dependent
+// time); a shorter one (goo_set_wait_limit) probes with test_wait, so that the limit holds
+// even where try_wait would have suspended the thread for longer.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit = kWaitCycles) {
+  if (limit >= kWaitCycles) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+      if (clock64() - t0 > limit) return false;
+    return true;
+  }
   const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > kWaitCycles) return false;
+  while (!mbar_test_wait(bar, parity))
+    if (clock64() - t0 > limit) return false;
   return true;
+}
+
+// 1 + the block-local tile whose copies this block withholds (goo_debug_withhold_tile: the
+// first block only), 0: none.
+__device__ __forceinline__ unsigned withheld_tile(const unsigned* counters) {
+  return blockIdx.x == 0 ? __ldcg(counters + kWithholdWord) : 0u;
+}
+
+// The tile-wait limit of the evaluation in progress (counters[kWaitLimitWord], 0: kWaitCycles).
+__device__ __forceinline__ long long tile_wait_limit(const unsigned* counters) {
+  const unsigned w = __ldcg(counters + kWaitLimitWord);
+  return w ? (long long)w : kWaitCycles;
 }
 
 // orders this thread's earlier generic-proxy shared-memory accesses before later async-proxy

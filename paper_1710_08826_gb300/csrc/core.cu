@@ -368,6 +368,33 @@ int goo_timing_read(goo_ctx* ctx, int max_entries, char* names, int64_t* counts,
   return n;
 }
 
+int goo_set_wait_limit(goo_ctx* ctx, int64_t cycles) {
+  if (!ctx) return set_error(GOO_ERR_ARG, "goo_set_wait_limit: NULL context");
+  if (cycles < 0 || cycles > (int64_t)0xffffffffLL)
+    return set_error(GOO_ERR_ARG, "goo_set_wait_limit: %lld cycles (0 .. 2^32 - 1)", (long long)cycles);
+  GOO_CUDA_TRY(cudaSetDevice(ctx->device));
+  const unsigned w = (unsigned)cycles;
+  // ordered on the context's stream before every later evaluation; the call returns once the
+  // word is on the device, so `w` may leave scope
+  GOO_CUDA_TRY(cudaMemcpyAsync(ctx->scratch.counters + kWaitLimitWord, &w, sizeof w, cudaMemcpyHostToDevice,
+                               ctx->stream));
+  GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  ctx->wait_limit = w;
+  return GOO_OK;
+}
+
+int goo_debug_withhold_tile(goo_ctx* ctx, int64_t tile) {
+  if (!ctx) return set_error(GOO_ERR_ARG, "goo_debug_withhold_tile: NULL context");
+  if (tile < -1 || tile > (int64_t)0xfffffffeLL)
+    return set_error(GOO_ERR_ARG, "goo_debug_withhold_tile: tile %lld", (long long)tile);
+  GOO_CUDA_TRY(cudaSetDevice(ctx->device));
+  const unsigned w = (unsigned)(tile + 1);
+  GOO_CUDA_TRY(cudaMemcpyAsync(ctx->scratch.counters + kWithholdWord, &w, sizeof w, cudaMemcpyHostToDevice,
+                               ctx->stream));
+  GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return GOO_OK;
+}
+
 int goo_init(int device, void* cuda_stream, goo_ctx** out) {
   if (!out) return set_error(GOO_ERR_ARG, "goo_init: out is NULL");
   *out = nullptr;

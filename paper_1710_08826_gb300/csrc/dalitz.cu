@@ -354,9 +354,10 @@ __global__ void __launch_bounds__(kStagedBlock, 1) coh_nll_staged_kernel(const _
   auto tile_of = [&](int j) { return tb0 + blockIdx.x + (int64_t)j * gridDim.x; };
   auto full = [&](int64_t t) { return t * TE >= begin && (t + 1) * TE <= end; };
   auto buf = [&](int st, int p) { return s_amp + ((size_t)st * planes + p) * TE; };
+  const unsigned withhold = withheld_tile(counters);  // the failure-detection test hook
   auto issue = [&](int j) {
     const int64_t t = tile_of(j);
-    if (t >= tb1) return;
+    if (t >= tb1 || (withhold && j == (int)withhold - 1)) return;
     uint64_t* bar = &s_bar[j % NST];
     if (full(t)) {
       mbar_arrive_expect_tx(bar, (unsigned)(planes * TE * sizeof(float4)));
@@ -386,12 +387,13 @@ __global__ void __launch_bounds__(kStagedBlock, 1) coh_nll_staged_kernel(const _
   for (int k = 0; k < KA; ++k) G1[k] = G2[k] = pk::splat(0.f);
   unsigned bad = 0;
   __syncthreads();  // barriers initialised before any thread waits on them
+  const long long wlim = tile_wait_limit(counters);
   int j = 0;
   bool failed = false;
   for (; tile_of(j) < tb1; ++j) {
     const int64_t t = tile_of(j);
     const int st = j % NST;
-    const bool ok_wait = mbar_wait(&s_bar[st], (unsigned)(j / NST) & 1u);
+    const bool ok_wait = mbar_wait(&s_bar[st], (unsigned)(j / NST) & 1u, wlim);
     if (ok_wait) {
       const float4* sb = buf(st, 0);  // plane p of the tile at sb + p * TE
       const bool staged = full(t);
@@ -425,7 +427,8 @@ __global__ void __launch_bounds__(kStagedBlock, 1) coh_nll_staged_kernel(const _
     // copies still in flight before the block's shared memory is released
     if (threadIdx.x == 0) {
       atomicOr(counters + kStatusWord, 1u);
-      for (int jj = j; jj < j + NST && tile_of(jj) < tb1; ++jj) mbar_wait(&s_bar[jj % NST], (unsigned)(jj / NST) & 1u);
+      for (int jj = j; jj < j + NST && tile_of(jj) < tb1; ++jj)
+        if (!(withhold && jj == (int)withhold - 1)) mbar_wait(&s_bar[jj % NST], (unsigned)(jj / NST) & 1u);
     }
     __syncthreads();
   }
@@ -779,6 +782,7 @@ template <typename T>
 struct Td3Args {
   T cr[kTd3KB + 1], ci[kTd3KB + 1];  // coefficients by slot: resonances, then the NR in slot kTd3KB
   T G, x, y, s;                      // 1/tau, mixing, resolution in the path's precision
+  TimeCoef<T> tc;                    // the same with the moment-series coefficients
   T wa[kWMax];                       // Weideman coefficients
   T wL;
   int wN, nbw, K, n_params;
@@ -872,11 +876,11 @@ __global__ void __launch_bounds__(kBlock, 2)
       Bi += a.cr[k] * bi + a.ci[k] * br;
     }
     TimeTerms<T> tt;
-    time_terms_g<T>(a.G, a.x, a.y, a.s, a.wa, a.wN, a.wL, t, tt);
+    time_terms_g<T>(a.tc, a.wa, a.wN, a.wL, t, tt);
     const T AA = Ar * Ar + Ai * Ai, BB = Br * Br + Bi * Bi;
     const T ABr = Ar * Br + Ai * Bi, ABi = Ai * Br - Ar * Bi;  // A conj(B)
-    const T hp = T(0.5) * (AA + BB), hm = T(0.5) * (AA - BB);
-    const T R = hp * tt.Tch + hm * tt.Tc + ABr * tt.Tsh + ABi * tt.Ts;
+    // R = |A|^2 P + |B|^2 Q + Re(A B*) T_sh + Im(A B*) T_s with P, Q = (T_ch +- T_c)/2
+    const T R = AA * tt.P + BB * tt.Q + ABr * tt.Tsh + ABi * tt.Ts;
     if (!(R > T(0))) {
       ++bad;
       continue;
@@ -885,7 +889,7 @@ __global__ void __launch_bounds__(kBlock, 2)
     else lf64 += log(R);
     if constexpr (GRAD) {
       const T invR = T(1) / R;
-      const T cp = (tt.Tch + tt.Tc) * invR, cm = (tt.Tch - tt.Tc) * invR, sh = tt.Tsh * invR, ss = tt.Ts * invR;
+      const T cp = T(2) * tt.P * invR, cm = T(2) * tt.Q * invR, sh = tt.Tsh * invR, ss = tt.Ts * invR;
       // V_A / R = cp A* + (sh - i ss) B*,  V_B / R = cm B* + (sh + i ss) A*
       const T VAr = cp * Ar + sh * Br - ss * Bi, VAi = -cp * Ai - sh * Bi - ss * Br;
       const T VBr = cm * Br + sh * Ar + ss * Ai, VBi = -cm * Bi - sh * Ai + ss * Ar;
@@ -903,7 +907,7 @@ __global__ void __launch_bounds__(kBlock, 2)
       lim[KB] -= VAi + VBi;
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        lt[j] += (hp * tt.d[j][0] + hm * tt.d[j][2] + ABr * tt.d[j][1] + ABi * tt.d[j][3]) * invR;
+        lt[j] += (AA * tt.d[j][0] + BB * tt.d[j][1] + ABr * tt.d[j][2] + ABi * tt.d[j][3]) * invR;
     }
   }
   ddf v[NS];
@@ -1424,10 +1428,11 @@ static void fill_td3(const DalitzModel& d, const double* theta, int n_params, in
     a.par_re[k] = d.par_re[k];
     a.par_im[k] = d.par_im[k];
   }
-  a.x = (T)theta[d.par_t[0]];
-  a.y = (T)theta[d.par_t[1]];
-  a.G = (T)(1.0 / theta[d.par_t[2]]);
-  a.s = (T)theta[d.par_t[3]];
+  fill_time_coef<T>(a.tc, theta[d.par_t[0]], theta[d.par_t[1]], theta[d.par_t[2]], theta[d.par_t[3]]);
+  a.x = a.tc.x;
+  a.y = a.tc.y;
+  a.G = a.tc.G;
+  a.s = a.tc.s;
   for (int j = 0; j < 4; ++j) a.par_t[j] = d.par_t[j];
   const WeidemanTables& w = weideman();
   a.wN = sizeof(T) == 4 ? kWN32 : kWN64;

@@ -320,7 +320,9 @@ struct SrvModel {   // shared by every fit of a batch
 // sub-tiles of kSrvSub events whose amplitude planes are staged in shared memory by bulk
 // copies (every event is one 16-byte float4 per plane, so any sub-range is a legal copy),
 // kSrvStages sub-tiles ahead of the consumers.  Dynamic shared memory:
-// kSrvStages * (kSrvKB / 2) * kSrvSub float4.  status[0] is set when a copy wait gave up.
+// kSrvStages * (kSrvKB / 2) * kSrvSub float4.  status[0] is set when a copy wait gave up;
+// wait_limit bounds each wait for a sub-tile in SM clocks (the drain before exit allows
+// kWaitCycles).
 constexpr int kSrvSub = 512;
 constexpr int kSrvStages = 3;
 constexpr size_t kSrvSmem = (size_t)kSrvStages * (kSrvKB / 2) * kSrvSub * sizeof(float4);
@@ -329,7 +331,8 @@ __global__ void __launch_bounds__(kBlock, 2) srv_nll_kernel(const SrvEval* __res
                                                            const int2* __restrict__ fit_tiles, int ntiles,
                                                            int tile_events, const SrvModel* __restrict__ sm,
                                                            float2* tile_partials, unsigned* fit_ticket,
-                                                           SrvResult* results, unsigned* status) {
+                                                           SrvResult* results, unsigned* status,
+                                                           long long wait_limit) {
   __shared__ ddf s_red[(kBlock / 32) * kSrvLanes > kBlock ? (kBlock / 32) * kSrvLanes : kBlock];
   __shared__ unsigned s_bad[kBlock / 32];
   __shared__ bool s_last;
@@ -403,7 +406,7 @@ __global__ void __launch_bounds__(kBlock, 2) srv_nll_kernel(const SrvEval* __res
     unsigned bad = 0;
     for (int sub = 0; sub < nsub; ++sub, ++j) {
       const int st = j % NST;
-      const bool ok_wait = mbar_wait(&s_bar[st], (unsigned)(j / NST) & 1u);
+      const bool ok_wait = mbar_wait(&s_bar[st], (unsigned)(j / NST) & 1u, wait_limit);
       const int64_t lo = b0 + (int64_t)sub * TE;
       const int64_t left = b1 - lo;
       const int cnt = left <= 0 ? 0 : (left < TE ? (int)left : TE);
@@ -1490,7 +1493,8 @@ int goo_server_step(goo_server* s, int* n_queued, int* n_active, int* n_done) {
       LaunchScope ls(ctx, "srv_nll_grad");
       srv_nll_kernel<<<nb, kBlock, kSrvSmem, ctx->stream>>>(s->d_evals, s->d_tiles, s->d_fit_tiles, (int)s->ntiles,
                                                             s->opt.tile_events, s->d_model, s->d_tile_partials,
-                                                            s->d_tickets, s->d_results, s->d_done_count + 1);
+                                                            s->d_tickets, s->d_results, s->d_done_count + 1,
+                                                            ctx->wait_limit ? (long long)ctx->wait_limit : kWaitCycles);
     }
     GOO_CUDA_TRY(cudaGetLastError());
     {
@@ -1707,7 +1711,8 @@ int goo_nll_grad_batch(goo_model* m, int n_fits, const goo_dataset* const* ds, c
     {
       LaunchScope ls(ctx, "srv_nll_grad");
       srv_nll_kernel<<<nb, kBlock, kSrvSmem, ctx->stream>>>(d_ev, d_tiles, d_ft, (int)tiles.size(), T, d_sm, d_part, d_tk,
-                                                            d_res, d_status);
+                                                            d_res, d_status,
+                                                            ctx->wait_limit ? (long long)ctx->wait_limit : kWaitCycles);
     }
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(res.data(), d_res, sizeof(SrvResult) * n_fits, cudaMemcpyDeviceToHost, ctx->stream) ||

@@ -4,11 +4,12 @@
 // semantics and the host side).
 //
 // The packed-pair kernel takes a compile-time leaf signature SIG (4 bits per leaf slot: the
-// leaf's opcode, 0 for an empty slot).  SIG = 0 is the interpreter compiled into the
-// library, which reads each slot's opcode at run time; a nonzero SIG is instantiated at run
-// time by NVRTC for one model (jit.cu), so that every slot's dispatch folds away and only the
-// gradient lanes its leaf has are accumulated.  This header therefore compiles under nvcc and
-// under NVRTC alike.
+// leaf's opcode, 0 for an empty slot) and column map COLS (2 bits per slot: the leaf's
+// observable).  SIG = 0 is the interpreter compiled into the library, which reads each slot's
+// opcode and column at run time; a nonzero SIG is instantiated at run time by NVRTC for one
+// model (jit.cu), so that every slot's dispatch folds away, leaves on one observable share
+// one shared-memory load, and only the gradient lanes its leaf has are accumulated.  This
+// header therefore compiles under nvcc and under NVRTC alike.
 #pragma once
 
 #include "common.cuh"
@@ -812,11 +813,28 @@ __device__ __forceinline__ void pair_step(const EvConst<float, K, L>& P, const f
   }
 }
 
-// Column tiles of TE = 2 * kPairsPerThread * kBlock events (aligned to multiples of TE)
-// are staged in shared memory by bulk copies, kEventStages tiles ahead; block b takes tiles
-// tb0 + b, tb0 + b + gridDim.x, ...  Within a tile thread t takes pairs t, t + kBlock, ...
+// Leaf slot (k, l)'s observable in a compile-time column map COLS (2 bits per slot, slot
+// k * L + l), the companion of a nonzero signature SIG.
+__host__ __device__ constexpr int cols_col(unsigned long long cols, int slot) { return (int)((cols >> (2 * slot)) & 3ull); }
+
+// Work split.  The events [begin, end) are an 8-aligned core [A, B) plus a head [begin, A) and
+// a tail [B, end) of fewer than 8 events each.  Block b takes the contiguous range
+// [A + b c, A + (b + 1) c) of the core (c = the core divided by the grid, rounded up to 8
+// events), so every block has the same number of events to within one tile's worth at the
+// end of the grid; the first block also evaluates the head and the last block the tail,
+// reading them from global memory.  A block's range runs in tiles of up to TE =
+// 2 * kPairsPerThread * kBlock events (the last tile of a range is shorter; every tile starts
+// and ends on 8-event boundaries, so its bulk copies are 16-byte aligned multiples of 16
+// bytes), staged in shared memory kEventStages tiles ahead.  Within a tile thread t takes the
+// pairs t, t + kBlock, ...
+//
+// Warps consume tiles independently: each warp waits for a tile's copies on the stage's
+// mbarrier, evaluates its pairs and counts itself done with the buffer in s_done[stage]; the
+// warp that completes the count refills the buffer with the tile kEventStages ahead.  No
+// block barrier separates tiles, so a warp that is fast on one tile runs ahead on the next
+// instead of waiting for the slowest warp.
 // Dynamic shared memory: kEventStages * n_obs * TE floats.
-template <int K, int L, bool GRAD, unsigned long long SIG = 0>
+template <int K, int L, bool GRAD, unsigned long long SIG = 0, unsigned long long COLS = 0>
 __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
     sop_event2_kernel(const ModelDev* __restrict__ md, const EvConst<float, K, L> P,
                       const __grid_constant__ EvNorm<K, L, GRAD> N, Cols<float> cols, int64_t begin, int64_t end,
@@ -826,33 +844,45 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
   constexpr int PPT = kPairsPerThread;
   constexpr int TE = 2 * PPT * kBlock;
   constexpr int NST = kEventStages;
+  constexpr unsigned NWARP = kBlock / 32;
   __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
   __shared__ unsigned s_bad[kBlock / 32];
   __shared__ __align__(8) uint64_t s_bar[NST];
+  __shared__ unsigned s_done[NST];  // warps done with each stage's buffer, counted over all its tiles
+  __shared__ int s_last[NST];       // the last tile issued into each stage (-1: none)
+  __shared__ unsigned s_fail;
   __shared__ double s_term[K * L][4];
   __shared__ ddf s_raw[K * L][4];
   __shared__ float s_off[K][2];
   extern __shared__ __align__(128) float s_col[];  // [NST][nobs][TE]
   const int nobs = P.nobs;
-  const int64_t tb0 = begin / TE, tb1 = (end + TE - 1) / TE;
-  auto tile_of = [&](int j) { return tb0 + blockIdx.x + (int64_t)j * gridDim.x; };
-  auto full = [&](int64_t t) { return t * TE >= begin && (t + 1) * TE <= end; };
+  const int lane = threadIdx.x & 31;
+  const int64_t A = min(end, (begin + 7) & ~(int64_t)7);
+  const int64_t B = max(A, end & ~(int64_t)7);
+  const int64_t chunk = ((B - A) + (int64_t)gridDim.x * 8 - 1) / ((int64_t)gridDim.x * 8) * 8;
+  const int64_t r0 = min(B, A + (int64_t)blockIdx.x * chunk), r1 = min(B, r0 + chunk);
+  const int ntile = (int)((r1 - r0 + TE - 1) / TE);
+  auto tile_count = [&](int j) { return (int)min((int64_t)TE, r1 - (r0 + (int64_t)j * TE)); };
   auto buf = [&](int st, int c) { return s_col + ((size_t)st * nobs + c) * TE; };
-  // one thread stages tile j in buffer j % NST: bulk copies for a full tile, a bare arrival
-  // (completes the phase at once) for a ragged one, which its threads read from global memory
+  const unsigned withhold = withheld_tile(counters);
+  // one thread stages tile j in buffer j % NST (a withheld tile's copies are never issued, so
+  // its waits run out: the failure-detection test hook)
   auto issue = [&](int j) {
-    const int64_t t = tile_of(j);
-    if (t >= tb1) return;
-    uint64_t* bar = &s_bar[j % NST];
-    if (full(t)) {
-      mbar_arrive_expect_tx(bar, (unsigned)(nobs * TE * sizeof(float)));
-      for (int c = 0; c < nobs; ++c) bulk_load(buf(j % NST, c), cols.c[c] + t * TE, TE * sizeof(float), bar);
-    } else {
-      mbar_arrive(bar);
-    }
+    if (j >= ntile || (withhold && j == (int)withhold - 1)) return;
+    const int st = j % NST;
+    const unsigned bytes = (unsigned)tile_count(j) * (unsigned)sizeof(float);
+    const int64_t t0 = r0 + (int64_t)j * TE;
+    s_last[st] = j;
+    mbar_arrive_expect_tx(&s_bar[st], (unsigned)nobs * bytes);
+    for (int c = 0; c < nobs; ++c) bulk_load(buf(st, c), cols.c[c] + t0, bytes, &s_bar[st]);
   };
   if (threadIdx.x == 0) {
-    for (int st = 0; st < NST; ++st) mbar_init(&s_bar[st], 1);
+    for (int st = 0; st < NST; ++st) {
+      mbar_init(&s_bar[st], 1);
+      s_done[st] = 0u;
+      s_last[st] = -1;
+    }
+    s_fail = 0u;
     mbar_init_fence();
     for (int j = 0; j < NST; ++j) issue(j);
   }
@@ -877,72 +907,86 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
 #pragma unroll
       for (int q = 0; q < 3; ++q) S.A[k][l][q] = splat(0.f);
   }
-  int j = 0;
+  // column of leaf slot (k, l): compile-time in a specialised kernel
+  auto leaf_col = [&](int k, int l) { return SIG != 0 ? cols_col(COLS, k * L + l) : P.leaf[k][l].col; };
+  const long long wlim = tile_wait_limit(counters);
   bool failed = false;
-  for (; tile_of(j) < tb1; ++j) {
-    const int64_t t = tile_of(j);
+  for (int j = 0; j < ntile; ++j) {
     const int st = j % NST;
-    const bool ok_wait = mbar_wait(&s_bar[st], (unsigned)(j / NST) & 1u);
-    if (ok_wait) {
-      if (full(t)) {
-        // every event of the tile is in range: each leaf reads its own staged column (an
-        // unused leaf slot reads column 0 and is ignored)
-        int coff[K][L];
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-#pragma unroll
-          for (int l = 0; l < L; ++l) coff[k][l] = (st * nobs + P.leaf[k][l].col) * TE;
-#pragma unroll 1
-        for (int u = 0; u < PPT; ++u) {
-          const int pr = threadIdx.x + u * kBlock;
-          float2 xl[K][L];
-#pragma unroll
-          for (int k = 0; k < K; ++k)
-#pragma unroll
-            for (int l = 0; l < L; ++l) xl[k][l] = reinterpret_cast<const float2*>(s_col + coff[k][l])[pr];
-          pair_step<K, L, GRAD, SIG>(P, off_hi, off_lo, xl, true, true, S);
-        }
-      } else {
-#pragma unroll 1
-        for (int u = 0; u < PPT; ++u) {
-          const int64_t i = t * TE + 2 * (threadIdx.x + u * kBlock);
-          const bool v0 = i >= begin && i < end, v1 = i + 1 >= begin && i + 1 < end;
-          float2 x[kMaxObs];
-#pragma unroll
-          for (int c = 0; c < kMaxObs; ++c) {
-            x[c] = splat(0.f);
-            if (c < nobs) {
-              if (v0 && v1) x[c] = __ldg(reinterpret_cast<const float2*>(cols.c[c] + i));
-              else if (v0) x[c].x = cols.c[c][i];
-              else if (v1) x[c].y = cols.c[c][i + 1];
-            }
-          }
-          float2 xl[K][L];
-#pragma unroll
-          for (int k = 0; k < K; ++k)
-#pragma unroll
-            for (int l = 0; l < L; ++l) xl[k][l] = pick(P.leaf[k][l].col, x[0], x[1], x[2], x[3]);
-          if (v0 || v1) pair_step<K, L, GRAD, SIG>(P, off_hi, off_lo, xl, v0, v1, S);
-        }
-      }
-    }
-    // every thread is done with buffer st (and agrees on whether a wait gave up) before
-    // the buffer is refilled
-    if (__syncthreads_or(!ok_wait)) {
+    // the whole warp agrees on whether the tile arrived in time
+    if (!__all_sync(0xffffffffu, mbar_wait(&s_bar[st], (unsigned)(j / NST) & 1u, wlim))) {
       failed = true;
       break;
     }
-    if (threadIdx.x == 0) {
-      fence_proxy_async();  // the reads of buffer st precede the copy that overwrites it
-      issue(j + NST);
+    const int npair = tile_count(j) >> 1;
+    int coff[K][L];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int l = 0; l < L; ++l) coff[k][l] = (st * nobs + leaf_col(k, l)) * TE;
+#pragma unroll 1
+    for (int u = 0; u < PPT; ++u) {
+      const int pr = threadIdx.x + u * kBlock;
+      if (pr >= npair) break;
+      // each leaf reads its observable's staged column (an unused slot reads column 0 and is
+      // ignored)
+      float2 xl[K][L];
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int l = 0; l < L; ++l) xl[k][l] = reinterpret_cast<const float2*>(s_col + coff[k][l])[pr];
+      pair_step<K, L, GRAD, SIG>(P, off_hi, off_lo, xl, true, true, S);
+    }
+    // this warp is done with buffer st; the warp that completes the count for tile j refills
+    // it: every warp's reads of the buffer precede its count (block-scope fences around the
+    // shared atomic), and the refilling thread orders them before the asynchronous copy
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      const unsigned done = atomicAdd(&s_done[st], 1u) + 1u;
+      if (done == (unsigned)(j / NST + 1) * NWARP) {
+        __threadfence_block();
+        fence_proxy_async();
+        issue(j + NST);
+      }
     }
   }
-  if (failed) {
-    // a copy did not arrive in time: record it, then wait (again bounded) for this block's
-    // copies still in flight before the block's shared memory is released
+  // head and tail (fewer than 8 events each) from global memory: pairs at even indices
+  auto ragged = [&](int64_t lo, int64_t hi) {
+    const int64_t i = (lo & ~(int64_t)1) + 2 * (int64_t)threadIdx.x;
+    if (i >= hi) return;
+    const bool v0 = i >= lo, v1 = i + 1 < hi;
+    float2 x[kMaxObs];
+#pragma unroll
+    for (int c = 0; c < kMaxObs; ++c) {
+      x[c] = splat(0.f);
+      if (c < nobs) {
+        if (v0 && v1) x[c] = __ldg(reinterpret_cast<const float2*>(cols.c[c] + i));
+        else if (v0) x[c].x = cols.c[c][i];
+        else x[c].y = cols.c[c][i + 1];
+      }
+    }
+    float2 xl[K][L];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int l = 0; l < L; ++l) xl[k][l] = pk::pick(leaf_col(k, l), x[0], x[1], x[2], x[3]);
+    pair_step<K, L, GRAD, SIG>(P, off_hi, off_lo, xl, v0, v1, S);
+  };
+  if (!failed) {
+    if (blockIdx.x == 0 && A > begin) ragged(begin, A);
+    if (blockIdx.x == gridDim.x - 1 && end > B) ragged(B, end);
+  }
+  if (failed && lane == 0) atomicOr(&s_fail, 1u);
+  __syncthreads();
+  if (s_fail) {
+    // a copy did not arrive in time: record it, then wait (again bounded, with the default
+    // limit) for this block's copies still in flight before its shared memory is released;
+    // the copies of one stage complete in order, so the last one issued is waited for
     if (threadIdx.x == 0) {
       atomicOr(counters + kStatusWord, 1u);
-      for (int jj = j; jj < j + NST && tile_of(jj) < tb1; ++jj) mbar_wait(&s_bar[jj % NST], (unsigned)(jj / NST) & 1u);
+      for (int st = 0; st < NST; ++st)
+        if (s_last[st] >= 0) mbar_wait(&s_bar[st], (unsigned)(s_last[st] / NST) & 1u);
     }
     __syncthreads();
   }

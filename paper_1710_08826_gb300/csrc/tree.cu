@@ -962,11 +962,14 @@ static int launch_event2(goo_model* m, const goo_dataset* ds, int64_t begin, int
     const void* fn = (const void*)sop_event2_kernel<K, L, GRAD>;
     int st = m->jit_mode;
     if (m->jit_mode) {
-      unsigned long long sig = 0;
+      unsigned long long sig = 0, colmap = 0;
       for (int k = 0; k < m->host.nK && k < K; ++k)
-        for (int l = 0; l < m->host.comp[k].n_leaf && l < L; ++l)
-          sig |= (unsigned long long)(m->host.leaf[k * kMaxLeaf + l].op & 15) << (4 * (k * L + l));
-      const void* jf = jit_event2_kernel(ctx->device, K, L, GRAD, sig, smem_max, &st);
+        for (int l = 0; l < m->host.comp[k].n_leaf && l < L; ++l) {
+          const LeafDev& LD = m->host.leaf[k * kMaxLeaf + l];
+          sig |= (unsigned long long)(LD.op & 15) << (4 * (k * L + l));
+          colmap |= (unsigned long long)(LD.col & 3) << (2 * (k * L + l));
+        }
+      const void* jf = jit_event2_kernel(ctx->device, K, L, GRAD, sig, colmap, smem_max, &st);
       if (jf) fn = jf;
     }
     if (fn == (const void*)sop_event2_kernel<K, L, GRAD> && !configured[ctx->device]) {
@@ -979,7 +982,9 @@ static int launch_event2(goo_model* m, const goo_dataset* ds, int64_t begin, int
   const void* fn = m->ev2_fn[gi];
   m->jit_status = m->ev2_status[gi];
   const int bps = cached_occupancy(fn, ctx->device, kBlock, smem);
-  const int64_t tiles = (end + TE - 1) / TE - begin / TE;
+  // every block takes an equal contiguous share of the events (sop_event2_kernel), at most
+  // one tile's worth when the range is small
+  const int64_t tiles = (end - begin + TE - 1) / TE;
   const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)ctx->num_sms * bps));
   constexpr int NS = EventLanes<float, K, L, GRAD>::NS;
   GOO_TRY(ensure_partials(ctx, (size_t)nb * NS));
@@ -1095,30 +1100,26 @@ namespace goo {
 constexpr size_t kStaticScratchBytes = size_t(1) << 20;  // 1 MiB per device that loads the library
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
+// Layout of the array: the model block (theta reaches the kernels through it and through
+// their by-value constants), the counters, the result record, then the reduction partials.
 constexpr size_t kStOffModel = 0;
-constexpr size_t kStOffTheta = (sizeof(ModelDev) + 255) / 256 * 256;
-constexpr size_t kStOffCounters = kStOffTheta + 256;
+constexpr size_t kStOffCounters = (sizeof(ModelDev) + 255) / 256 * 256;
 constexpr size_t kStOffResult = kStOffCounters + 256;
 constexpr size_t kStOffPartials = kStOffResult + (kResultDoubles + 1 + 1) / 2 * 2 * sizeof(double);
 constexpr int kStaticMaxParams = 32;  // documented limit of goo_nll_grad_static
 constexpr size_t kStPartialsCap = (kStaticScratchBytes - kStOffPartials) / sizeof(float2);
 static_assert(kStOffPartials < kStaticScratchBytes, "static scratch too small for the model block");
 
-constexpr int kMaxDevices = 64;
-static unsigned char* g_static_ptr[kMaxDevices] = {nullptr};
-static int g_static_sms[kMaxDevices] = {0};
-
-// Once per device, with that device current: the device address of the scratch array.
-static int static_scratch_setup(int dev) {
-  if (g_static_ptr[dev]) return GOO_OK;
+// With the caller's device current: the device address of the scratch array and the SM
+// count.  Looked up on every call (neither query allocates), so nothing is cached across a
+// cudaDeviceReset or a new primary context, and concurrent host threads share no host state.
+static int static_scratch_lookup(int dev, unsigned char** base, int* sms) {
   void* p = nullptr;
   cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
   if (e != cudaSuccess) return set_error(GOO_ERR_CUDA, "goo_nll_grad_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-  int sms = 0;
-  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return set_error(GOO_ERR_CUDA, "goo_nll_grad_static: %s", cudaGetErrorString(e));
-  g_static_sms[dev] = sms;
-  g_static_ptr[dev] = (unsigned char*)p;
+  *base = (unsigned char*)p;
   return GOO_OK;
 }
 
@@ -1311,11 +1312,10 @@ extern "C" int goo_nll_grad_static(const goo_node* nodes, int n_nodes, int n_par
   GOO_TRY(static_plan(nodes, n_nodes, n_params, n_obs, obs_lo, obs_hi, norm, h));
   int max_leaf = 0;
   for (int k = 0; k < h.nK; ++k) max_leaf = h.comp[k].n_leaf > max_leaf ? h.comp[k].n_leaf : max_leaf;
-  int dev = 0;
+  int dev = 0, sms = 0;
   GOO_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return set_error(GOO_ERR_ARG, "goo_nll_grad_static: device %d", dev);
-  GOO_TRY(static_scratch_setup(dev));
-  unsigned char* base = g_static_ptr[dev];
+  unsigned char* base = nullptr;
+  GOO_TRY(static_scratch_lookup(dev, &base, &sms));
   cudaStream_t st = (cudaStream_t)cuda_stream;
   if (n_events == 0) {
     *nll_out = 0.0;
@@ -1327,15 +1327,20 @@ extern "C" int goo_nll_grad_static(const goo_node* nodes, int n_nodes, int n_par
   GOO_CUDA_TRY(cudaMemsetAsync(base + kStOffCounters, 0, 256, st));
   const bool small = h.nK <= 2 && max_leaf <= 3;
   if (precision == GOO_F32) {
-    GOO_TRY((small ? static_launch<float, 2, 3>(h, max_leaf, base, g_static_sms[dev], cols_dev, n_events, precision, st)
-                   : static_launch<float, 4, 4>(h, max_leaf, base, g_static_sms[dev], cols_dev, n_events, precision, st)));
+    GOO_TRY((small ? static_launch<float, 2, 3>(h, max_leaf, base, sms, cols_dev, n_events, precision, st)
+                   : static_launch<float, 4, 4>(h, max_leaf, base, sms, cols_dev, n_events, precision, st)));
   } else {
-    GOO_TRY((small ? static_launch<double, 2, 3>(h, max_leaf, base, g_static_sms[dev], cols_dev, n_events, precision, st)
-                   : static_launch<double, 4, 4>(h, max_leaf, base, g_static_sms[dev], cols_dev, n_events, precision, st)));
+    GOO_TRY((small ? static_launch<double, 2, 3>(h, max_leaf, base, sms, cols_dev, n_events, precision, st)
+                   : static_launch<double, 4, 4>(h, max_leaf, base, sms, cols_dev, n_events, precision, st)));
   }
   double res[2 + kStaticMaxParams];
   GOO_CUDA_TRY(cudaMemcpyAsync(res, base + kStOffResult, (2 + n_params) * sizeof(double), cudaMemcpyDeviceToHost, st));
   GOO_CUDA_TRY(cudaStreamSynchronize(st));
+  if (res[1] < 0) {  // a device wait gave up (the event kernel's status word)
+    *nll_out = HUGE_VAL;
+    for (int p = 0; p < n_params; ++p) grad_out[p] = 0.0;
+    return set_error(GOO_ERR_TIMEOUT, "goo_nll_grad_static: a device wait gave up; the result is invalid");
+  }
   if (res[1] > 0) {
     *nll_out = HUGE_VAL;
     for (int p = 0; p < n_params; ++p) grad_out[p] = 0.0;

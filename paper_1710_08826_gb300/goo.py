@@ -89,6 +89,9 @@ def _load():
         "goo_launch_count": (i64, [vp]),
         "goo_timing_enable": (ctypes.c_int, [vp, ctypes.c_int]),
         "goo_timing_read": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(i64), dp, ctypes.c_int]),
+        "goo_set_wait_limit": (ctypes.c_int, [vp, i64]),
+        "goo_debug_withhold_tile": (ctypes.c_int, [vp, i64]),
+        "goo_peak_fma": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, dp, dp]),
         "goo_dataset_upload": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int, i64, dp, dp,
                                               ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(i64)]),
         "goo_dataset_free": (ctypes.c_int, [vp]),
@@ -178,6 +181,24 @@ class Context:
 
     def timing(self, on=True):
         _check(lib.goo_timing_enable(self.handle, int(bool(on))))
+
+    def set_wait_limit(self, cycles=0):
+        """Limit of the kernels' waits for staged input tiles, in SM clocks (0: the default)."""
+        _check(lib.goo_set_wait_limit(self.handle, int(cycles)))
+
+    def withhold_tile(self, tile=-1):
+        """Failure-detection test hook: the first block of the staged kernels skips the copies of
+        its tile number `tile` (-1: off), so that their waits run out."""
+        _check(lib.goo_debug_withhold_tile(self.handle, int(tile)))
+
+    def peak_fma(self, kind="f64", iters=None):
+        """Measured FMA rate of one pipe ("f64", "f32", "f32x2"): (FMAs per second, launch ms)."""
+        code = {"f64": 0, "f32": 1, "f32x2": 2}[kind]
+        if iters is None:
+            iters = {"f64": 256, "f32": 8192, "f32x2": 4096}[kind]
+        rate, ms = ctypes.c_double(), ctypes.c_double()
+        _check(lib.goo_peak_fma(self.handle, code, int(iters), ctypes.byref(rate), ctypes.byref(ms)))
+        return rate.value, ms.value
 
     def kernel_times(self, reset=True):
         """{kernel name: (launches, total ms)} recorded since the last reset."""

@@ -79,6 +79,91 @@ def test_static_matches_regular_twice(goo, which, precision):
         np.testing.assert_allclose(g, ref_g, rtol=0, atol=TOL[precision] * np.abs(ref_g).max())
 
 
+def _dense_grid_spec():
+    # two leaves of one product on the same observable: the grid does not factorise, so the
+    # dense midpoint-grid kernel runs
+    return dict(
+        name="dense_grid",
+        observables=[("x", 0.0, 10.0), ("y", -1.0, 1.0)],
+        params=[("mu", 4.0, False, 0.01), ("sigma", 1.5, False, 0.01), ("lam", -0.2, False, 0.01),
+                ("a1", 0.3, False, 0.01), ("a2", 0.2, False, 0.01), ("frac", 0.4, False, 0.01)],
+        pdf=("add", ["frac"], [
+            ("prod", [("gauss", "x", "mu", "sigma"), ("expo", "x", "lam"), ("poly2", "y", "a1", "a2")]),
+            ("prod", [("expo", "x", "lam"), ("poly2", "y", "a1", "a2")]),
+        ]),
+        norm=("grid", [96, 40]),
+    )
+
+
+def _three_products_spec():
+    # three products of up to four leaves: the larger (4 x 4) kernel shape
+    return dict(
+        name="three_products",
+        observables=[("x", 0.0, 10.0), ("y", -1.0, 1.0), ("z", 0.0, 4.0)],
+        params=[("mu", 4.0, False, 0.01), ("sigma", 1.5, False, 0.01), ("lam", -0.2, False, 0.01),
+                ("a1", 0.3, False, 0.01), ("a2", 0.2, False, 0.01), ("mu_y", 0.1, False, 0.01),
+                ("sig_y", 0.4, False, 0.01), ("lam_z", -0.7, False, 0.01), ("f1", 0.3, False, 0.01),
+                ("f2", 0.25, False, 0.01)],
+        pdf=("add", ["f1", "f2"], [
+            ("prod", [("gauss", "x", "mu", "sigma"), ("gauss", "y", "mu_y", "sig_y"), ("expo", "z", "lam_z")]),
+            ("prod", [("expo", "x", "lam"), ("poly2", "y", "a1", "a2")]),
+            ("prod", [("gauss", "x", "mu", "sigma"), ("poly2", "y", "a1", "a2"), ("expo", "z", "lam_z")]),
+        ]),
+        norm=("analytic",),
+    )
+
+
+def _uniform_cols(spec, n, seed):
+    rng = np.random.default_rng(seed)
+    return {o[0]: rng.uniform(o[1], o[2], n) for o in spec["observables"]}
+
+
+@pytest.mark.parametrize("which", ["dense_grid", "three_products"])
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_static_other_model_shapes(goo, which, precision):
+    import torch
+    spec = _dense_grid_spec() if which == "dense_grid" else _three_products_spec()
+    cols = _uniform_cols(spec, 123_457, 33)
+    if precision == "f32":
+        cols = synth.round_to_f32(cols, spec)
+    theta = [p[1] for p in spec["params"]]
+    ctx = goo.Context(0)
+    ds = goo.Dataset.from_spec(ctx, spec, cols)
+    ref_nll, ref_g = goo.Model(ctx, spec).nll_grad(ds, theta, precision)
+    dt = torch.float64 if precision == "f64" else torch.float32
+    dev_cols = [torch.tensor(cols[o[0]], dtype=dt, device="cuda:0") for o in spec["observables"]]
+    tol_g = 1e-9 if precision == "f64" else 1e-4
+    for _ in range(2):
+        nll, g = _static_call(goo, spec, dev_cols, precision, theta)
+        assert abs(nll - ref_nll) <= TOL[precision] * abs(ref_nll)
+        np.testing.assert_allclose(g, ref_g, rtol=0, atol=tol_g * np.abs(ref_g).max())
+
+
+def test_static_empty_input(goo):
+    import torch
+    spec = synth.c1_spec()
+    theta = [p[1] for p in spec["params"]]
+    dev_cols = [torch.zeros(0, dtype=torch.float64, device="cuda:0")]
+    nll, g = _static_call(goo, spec, dev_cols, "f64", theta)
+    assert nll == 0.0 and np.all(g == 0.0)
+
+
+def test_static_rejects_unsupported_shapes(goo):
+    import torch
+    spec = synth.c1_spec()
+    nested = dict(spec, params=spec["params"] + [("frac2", 0.5, False, 0.01)],
+                  pdf=("add", ["frac"], [("add", ["frac2"], [("gauss", "x", "mu", "sigma"), ("expo", "x", "lam")]),
+                                         ("expo", "x", "lam")]))
+    argus = dict(name="argus_analytic", observables=[("m", 5.2, 5.3)],
+                 params=[("m0", 5.29, False, 0.0), ("c", -20.0, False, 0.0), ("p", 0.5, False, 0.0)],
+                 pdf=("argus", "m", "m0", "c", "p"), norm=("analytic",))
+    for sp, x in ((nested, 5.0), (argus, 5.25)):
+        dev_cols = [torch.full((64,), x, dtype=torch.float64, device="cuda:0")]
+        with pytest.raises(goo.GooError) as e:
+            _static_call(goo, sp, dev_cols, "f64", [p[1] for p in sp["params"]])
+        assert e.value.code == goo.GOO_ERR_UNSUPPORTED, e.value
+
+
 def test_static_rejects_oversized(goo):
     import torch
     spec = synth.c1_spec()
