@@ -401,6 +401,18 @@ int goo_server_submit(goo_server* server, int64_t n_events, uint64_t seed, const
 int goo_server_step(goo_server* server, int* n_queued, int* n_active, int* n_done);
 int goo_server_result(goo_server* server, int64_t ticket, double* theta_out, double* errors_out,
                       goo_fit_result* res);
+/* Failures of one served fit leave the others untouched (each fit's evaluation depends only on
+ * its own tiles and theta).  goo_server_submit refuses a non-finite theta_start with
+ * GOO_ERR_ARG; nothing is queued.  goo_server_cancel ends a queued or active fit between
+ * steps: a queued one leaves the queue, an active one releases its slot and its events'
+ * memory; its result is theta_start with zero errors, nll = +inf and status
+ * GOO_FIT_CANCELLED.  GOO_ERR_STATE for a finished fit, GOO_ERR_ARG for an unknown ticket.
+ * goo_server_fail_allocation is a failure-detection test hook: the admission of that queued
+ * fit fails as if its event memory could not be allocated, and the fit ends with status
+ * GOO_FIT_ALLOC_FAILED while the queue moves on (GOO_ERR_STATE unless the fit is queued). */
+enum { GOO_FIT_ALLOC_FAILED = 6, GOO_FIT_CANCELLED = 7 };
+int goo_server_cancel(goo_server* server, int64_t ticket);
+int goo_server_fail_allocation(goo_server* server, int64_t ticket);
 /* out[0..8]: evaluation rounds, evaluation ms, generation ms, candidates drawn, candidates
    accepted, largest envelope bound, arena bytes, arena bytes in use, and the candidates inside
    the region whose |S|^2 exceeded their cell's bound (non-zero: the envelope is too low there

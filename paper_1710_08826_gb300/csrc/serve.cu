@@ -28,6 +28,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <set>
 #include <vector>
 
 #include "common.cuh"
@@ -968,6 +969,7 @@ struct goo_server {
   std::vector<int> active;
   bool active_dirty = true;
   std::map<int64_t, goo::FitOut> done;
+  std::set<int64_t> fail_alloc;  // tickets whose admission fails its allocation (test hook)
   int64_t next_ticket = 1;
   int64_t rounds = 0, ntiles = 0;
   double eval_ms = 0.0, gen_ms = 0.0, gen_candidates = 0.0, gen_accepted = 0.0;
@@ -1145,11 +1147,30 @@ static void init_state(goo_server* s, int slot, SrvState& st, SrvEval& ev) {
   ev.begin = 0;
 }
 
+// A fit that ends without a minimisation (cancelled, or its allocation failed): its result
+// is the start point with zero errors, an infinite NLL and the given status.
+static void finish_unfitted(goo_server* s, int64_t ticket, const std::vector<double>& theta_start, int status) {
+  FitOut out;
+  out.theta = theta_start;
+  out.err.assign(theta_start.size(), 0.0);
+  std::memset(&out.res, 0, sizeof out.res);
+  out.res.nll = HUGE_VAL;
+  out.res.status = status;
+  s->done[ticket] = out;
+}
+
 static int admit(goo_server* s, std::vector<int>& admitted) {
   while (!s->queue.empty() && !s->free_slots.empty()) {
     Request& r = s->queue.front();
     const size_t bytes = fit_bytes(r.n, s->info.nbw);
     size_t off = 0;
+    if (s->fail_alloc.count(r.ticket)) {
+      // the test hook: this fit's allocation fails; it ends alone, the queue moves on
+      s->fail_alloc.erase(r.ticket);
+      finish_unfitted(s, r.ticket, r.theta_start, GOO_FIT_ALLOC_FAILED);
+      s->queue.pop_front();
+      continue;
+    }
     if (arena_alloc(s, bytes, &off) != GOO_OK) break;  // wait until memory frees up
     const int slot = s->free_slots.back();
     s->free_slots.pop_back();
@@ -1443,6 +1464,10 @@ int goo_server_create(goo_model* model, const double* theta_gen, const int* free
 int goo_server_submit(goo_server* s, int64_t n_events, uint64_t seed, const double* theta_start, int64_t* ticket) {
   if (!s || !ticket) return set_error(GOO_ERR_ARG, "goo_server_submit: NULL argument");
   if (n_events < 1) return set_error(GOO_ERR_ARG, "goo_server_submit: n_events=%lld", (long long)n_events);
+  if (theta_start)
+    for (int p = 0; p < s->model->n_params; ++p)
+      if (!std::isfinite(theta_start[p]))
+        return set_error(GOO_ERR_ARG, "goo_server_submit: theta_start[%d] is not finite", p);
   if (fit_bytes(n_events, s->info.nbw) > s->arena_bytes)
     return set_error(GOO_ERR_OOM, "goo_server_submit: %lld events need more than the whole arena", (long long)n_events);
   Request r;
@@ -1512,6 +1537,42 @@ int goo_server_step(goo_server* s, int* n_queued, int* n_active, int* n_done) {
   if (n_active) *n_active = (int)s->active.size();
   if (n_done) *n_done = (int)s->done.size();
   return GOO_OK;
+}
+
+int goo_server_cancel(goo_server* s, int64_t ticket) {
+  if (!s) return set_error(GOO_ERR_ARG, "goo_server_cancel: NULL server");
+  if (s->done.count(ticket)) return set_error(GOO_ERR_STATE, "goo_server_cancel: fit %lld has finished", (long long)ticket);
+  for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+    if (it->ticket != ticket) continue;
+    finish_unfitted(s, ticket, it->theta_start, GOO_FIT_CANCELLED);
+    s->queue.erase(it);
+    return GOO_OK;
+  }
+  for (size_t a = 0; a < s->active.size(); ++a) {
+    const int slot = s->active[a];
+    Slot& sl = s->slots[slot];
+    if (sl.ticket != ticket) continue;
+    // between steps no kernel of the server is in flight (each step synchronises): the slot's
+    // device state is simply no longer advanced, and its events' memory returns to the arena
+    finish_unfitted(s, ticket, sl.theta_start, GOO_FIT_CANCELLED);
+    arena_free(s, sl.off, sl.bytes);
+    sl = Slot();
+    s->free_slots.push_back(slot);
+    s->active.erase(s->active.begin() + a);
+    s->active_dirty = true;
+    return GOO_OK;
+  }
+  return set_error(GOO_ERR_ARG, "goo_server_cancel: no fit with ticket %lld", (long long)ticket);
+}
+
+int goo_server_fail_allocation(goo_server* s, int64_t ticket) {
+  if (!s) return set_error(GOO_ERR_ARG, "goo_server_fail_allocation: NULL server");
+  for (const Request& r : s->queue)
+    if (r.ticket == ticket) {
+      s->fail_alloc.insert(ticket);
+      return GOO_OK;
+    }
+  return set_error(GOO_ERR_STATE, "goo_server_fail_allocation: fit %lld is not waiting for admission", (long long)ticket);
 }
 
 int goo_server_result(goo_server* s, int64_t ticket, double* theta_out, double* errors_out, goo_fit_result* res) {

@@ -15,6 +15,7 @@ _LIB_PATH = os.path.join(_PKG, "libgoo.so")
 
 GOO_OK, GOO_ERR_ARG, GOO_ERR_RANGE, GOO_ERR_CUDA, GOO_ERR_OOM = 0, -1, -2, -3, -4
 GOO_ERR_NONPOSITIVE_PDF, GOO_ERR_TIMEOUT, GOO_ERR_STATE, GOO_ERR_UNSUPPORTED = -5, -6, -7, -8
+GOO_FIT_ALLOC_FAILED, GOO_FIT_CANCELLED = 6, 7
 GOO_F64, GOO_F32 = 0, 1
 GOO_LINESHAPE_CACHED, GOO_LINESHAPE_FLOATING = 0, 1
 GOO_COEF_CARTESIAN, GOO_COEF_POLAR = 0, 1
@@ -119,6 +120,8 @@ def _load():
                                            ctypes.POINTER(ctypes.c_int)]),
         "goo_server_result": (ctypes.c_int, [vp, i64, dp, dp, ctypes.c_void_p]),
         "goo_server_stats": (ctypes.c_int, [vp, dp]),
+        "goo_server_cancel": (ctypes.c_int, [vp, i64]),
+        "goo_server_fail_allocation": (ctypes.c_int, [vp, i64]),
         "goo_server_free": (ctypes.c_int, [vp]),
         "goo_toy_generate": (ctypes.c_int, [vp, dp, vp, ctypes.c_uint64, i64,
                                             ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
@@ -704,6 +707,14 @@ class Server:
             return None
         _check(rc)
         return th, err, {k: getattr(res, k) for k, _ in GooFitResult._fields_}
+
+    def cancel(self, ticket):
+        """End a queued or active fit; its result then has status GOO_FIT_CANCELLED."""
+        _check(lib.goo_server_cancel(self.handle, int(ticket)))
+
+    def fail_allocation(self, ticket):
+        """Test hook: the admission of this queued fit fails (status GOO_FIT_ALLOC_FAILED)."""
+        _check(lib.goo_server_fail_allocation(self.handle, int(ticket)))
 
     def stats(self):
         out = np.zeros(9)
