@@ -542,6 +542,9 @@ def run_ours(args):
         ds_stream.update(cols_pin, mapped=True)
         return model.nll_grad(ds_stream, theta, "f32")
 
+    def e2e_streamed(chunks):
+        return lambda: model.nll_grad_streamed(ds_stream, cols_pin, theta, n_chunks=chunks)
+
     e2e_steps = max(3, args.steps // 5)
 
     def e2e_time(fn):
@@ -560,6 +563,10 @@ def run_ours(args):
         return sec
 
     e2e_forms = {
+        "streamed_8": (e2e_time(e2e_streamed(8)), "goo_nll_grad_streamed, 8 chunks: the copy engine moves chunk c + 1 "
+                                                  "from the pinned float32 host columns while chunk c is range-checked "
+                                                  "and evaluated"),
+        "streamed_16": (e2e_time(e2e_streamed(16)), "goo_nll_grad_streamed, 16 chunks"),
         "update_mapped": (e2e_time(e2e_mapped), "goo_dataset_update (GOO_COPY_MAPPED: the ingest kernel reads the "
                                                 "pinned float32 host columns) + goo_nll_grad"),
         "update_copy": (e2e_time(e2e_update), "goo_dataset_update (GOO_COPY: copy engine from pinned float32 host "
@@ -568,6 +575,24 @@ def run_ours(args):
                                               "goo_dataset_free"),
     }
     ds_stream.close()
+    # the host link's copy bandwidth for the step's bytes (pinned host -> device, copy engine):
+    # the floor of any end-to-end form
+    link_src = torch.empty(n * BYTES_PER_EVENT_F32, dtype=torch.uint8).pin_memory()
+    link_dst = torch.empty_like(link_src, device="cuda")
+    for _ in range(2):
+        link_dst.copy_(link_src, non_blocking=True)
+    ls0 = torch.cuda.Event(enable_timing=True)
+    ls1 = torch.cuda.Event(enable_timing=True)
+    ls0.record(stream)
+    for _ in range(5):
+        link_dst.copy_(link_src, non_blocking=True)
+    ls1.record(stream)
+    ls1.synchronize()
+    link_ms = ls0.elapsed_time(ls1) / 5
+    host_link = {"h2d_gbs": link_src.numel() / (link_ms * 1e-3) / 1e9, "bytes": int(link_src.numel()),
+                 "floor_ms_per_step": link_ms,
+                 "what": "pinned host -> device copy of the step's column bytes (copy engine), 5 copies timed"}
+    del link_src, link_dst
     e2e_best = min(e2e_forms, key=lambda k: e2e_forms[k][0])
     e2e_s = e2e_forms[e2e_best][0]
 
@@ -624,7 +649,8 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * BYTES_PER_EVENT_F32 + 8 * P,
                 "d2h_bytes_per_step": 8 * (2 + P), "ms_per_step": e2e_s / e2e_steps * 1e3,
                 "what": e2e_forms[e2e_best][1],
-                "forms_ms_per_step": {k: v[0] / e2e_steps * 1e3 for k, v in e2e_forms.items()}},
+                "forms_ms_per_step": {k: v[0] / e2e_steps * 1e3 for k, v in e2e_forms.items()},
+                "host_link": host_link},
         "gpu_launches": launches,
         "clocks": clk,
     }
@@ -1048,6 +1074,12 @@ def c5_study(goo, ctx, n_toys=4096, rate=None, plain_sample=8, n_mc=1_000_000, s
            "rounds": int(stats["rounds"]), "generation_s": stats["gen_ms"] / 1e3,
            "generator_acceptance": stats["accepted"] / max(stats["candidates"], 1.0),
            "envelope_violations": int(stats["envelope_violations"]), "converged": int((statuses == 0).sum())}
+    # the fits that ended without EDM < tolerance: status 1 iteration limit, 2 line search found
+    # no decrease, 3 final Hessian not positive definite
+    out["not_converged"] = [{"toy": int(i), "events": int(sizes[i]), "status": int(results[i][2]["status"]),
+                             "edm": float(results[i][2]["edm"]), "iterations": int(results[i][2]["iterations"]),
+                             "nll": float(results[i][2]["nll"])}
+                            for i in range(n_toys) if results[i][2]["status"] != 0][:16]
     if plain_sample:
         # the plain form: per-fit serial FP64 with the finite-difference gradient, same toys,
         # on a sample stratified over the log-uniform event counts (the toys at the quantiles

@@ -440,6 +440,20 @@ int goo_nll_grad_batch(goo_model* model, int n_fits, const goo_dataset* const* d
  * compensated arithmetic into out (same layout); nll = out[0] + out[1]. */
 int goo_nll_partial(goo_model* model, const goo_dataset* ds, int64_t begin, int64_t end,
                     const double* theta, int precision, int want_grad, double* out);
+/* End-to-end evaluation from host memory with the transfer overlapped (paper Sec. 1: the time
+ * of a fit is the per-event evaluation; Fig. 1: a DataSet feeds the PDF).  Refills ds (an
+ * owning dataset of capacity >= n_events, as goo_dataset_update would) from n_events events
+ * of pinned float32 host columns (host_cols[c], one per dataset column) and returns the FP32
+ * NLL and adjoint gradient of a sum-of-products model at theta over them.  The events are
+ * split into n_chunks (1..64) chunks on multiples of 2048 events: the copy engine moves chunk
+ * c + 1 over the host link (on a second stream of the context) while chunk c is converted to
+ * float64, range-checked and evaluated on the context's stream, so that only the last
+ * chunk's evaluation follows the transfer.  The chunks' records are added in chunk order with
+ * compensation.  GOO_ERR_RANGE (*n_bad = count, ds left empty) if any event lies outside its
+ * observable's limits; GOO_ERR_UNSUPPORTED for amplitude models; other errors as goo_nll_grad.
+ * The call returns when the result is on the host. */
+int goo_nll_grad_streamed(goo_model* model, goo_dataset* ds, const float* const* host_cols, int64_t n_events,
+                          int n_chunks, const double* theta, double* nll_out, double* grad_out, int64_t* n_bad);
 int goo_combine_partials(int n_parts, int n_params, const double* parts, double* out);
 
 /* ---- Faddeeva function ------------------------------------------------------------------

@@ -92,7 +92,13 @@ struct Scratch {
   // destination of the amplitude kernels' record for the evaluation in progress: `result`,
   // or `result_host` while dalitz_nll / td4_nll run
   double* result_out = nullptr;
+  // goo_nll_grad_streamed: one mapped record per chunk (kStreamChunks records of
+  // kResultDoubles + 1 doubles), a second stream for the chunks' copies and an event per chunk
+  double* chunk_records = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t chunk_events[65] = {};
 };
+constexpr int kStreamChunks = 64;  // chunks of one goo_nll_grad_streamed call, at most
 
 }  // namespace goo
 
@@ -217,6 +223,23 @@ __device__ __forceinline__ ddf dd_from_double(double x) {
 
 __device__ __forceinline__ double dd_to_double(ddf a) { return (double)a.hi + (double)a.lo; }
 
+// a b in double-float: the product of the high parts split exactly by an FMA, plus the cross
+// terms; about 2^-44 relative.
+__device__ __forceinline__ ddf dd_mul(ddf a, ddf b) {
+  const float p = a.hi * b.hi;
+  return dd_make(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -p))));
+}
+
+// a / b in double-float (Dekker's division): a first quotient, the remainder a - q1 b with
+// q1 b.hi split exactly by an FMA, and a correction quotient; about 2^-44 relative.
+__device__ __forceinline__ ddf dd_div(ddf a, ddf b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const float p = q1 * b.hi;
+  const float pe = fmaf(q1, b.hi, -p);  // q1 b.hi = p + pe exactly
+  const float r = (((a.hi - p) - pe) + a.lo) - q1 * b.lo;
+  return dd_make(q1, __fdiv_rn(r, b.hi));
+}
+
 __device__ __forceinline__ ddf dd_shfl_xor(ddf a, int m) {
   return {__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
 }
@@ -225,6 +248,26 @@ __device__ __forceinline__ ddf dd_warp_sum(ddf v) {
 #pragma unroll
   for (int m = 16; m > 0; m >>= 1) v = dd_add(v, dd_shfl_xor(v, m));
   return v;
+}
+
+// Natural logarithm of a positive double-float as a double-float, in FP32 arithmetic: the
+// exponent is split off exactly, x.hi = m 2^e with m in [sqrt(1/2), sqrt(2)), so that
+// log x = e ln 2 + log m + log(1 + x.lo / x.hi) with |log m| < 0.35; logf(m) is within one
+// FP32 ulp of 0.35 (3e-8), e ln 2 is formed exactly in double-float and log(1 + r) = r to
+// below 1e-14 (|r| <= 2^-24).  About 3e-8 absolute.
+__device__ __forceinline__ ddf log_dd(ddf x) {
+  int e;
+  float m = frexpf(x.hi, &e);  // x.hi = m 2^e, m in [1/2, 1)
+  if (m < 0.70710678f) {
+    m *= 2.f;
+    e -= 1;
+  }
+  constexpr float kLn2Hi = 0.693147182464599609375f, kLn2Lo = -1.9046542999577152e-09f;
+  const float fe = (float)e;
+  const float ph = fe * kLn2Hi;
+  ddf r = dd_make(ph, fmaf(fe, kLn2Hi, -ph) + fe * kLn2Lo);
+  r = dd_add(r, {logf(m), 0.f});
+  return dd_add(r, {x.lo / x.hi, 0.f});
 }
 
 // Kahan-compensated FP32 accumulator (the per-thread NLL lane of the FP32 path).
@@ -421,10 +464,35 @@ __device__ __forceinline__ void block_reduce_to_partials(ddf (&v)[NS], int nslot
   }
 }
 
+// Block reduction of NS double-float lanes through shared memory: every thread writes its lanes
+// to buf[s * blockDim + t], then lane s is summed by G consecutive threads (G the largest
+// power of two, at most 32, with G NS <= blockDim), thread g of the group adding rows g,
+// g + G, ... in order, and the group combined by an xor tree.  The lane results of block b go
+// to partials[b * NS + s].  buf: NS * blockDim double-floats of shared memory no thread uses
+// at the call.  Fixed order, so bitwise repeatable; ends with the partials written by the
+// groups' first threads (no barrier after).
+template <int NS>
+__device__ __forceinline__ void block_reduce_transpose(const ddf (&v)[NS], float2* partials, ddf* buf) {
+  const int nt = blockDim.x, t = threadIdx.x;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) buf[s * nt + t] = v[s];
+  __syncthreads();
+  int G = 32;
+  while (G > 1 && G * NS > nt) G >>= 1;
+  const int s = t / G, g = t % G;
+  ddf acc = {0.f, 0.f};
+  if (s < NS)
+    for (int i = g; i < nt; i += G) acc = dd_add(acc, buf[s * nt + i]);
+  for (int m = G / 2; m > 0; m >>= 1) acc = dd_add(acc, dd_shfl_xor(acc, m));
+  if (s < NS && g == 0) partials[(size_t)blockIdx.x * NS + s] = make_float2(acc.hi, acc.lo);
+}
+
 // Completion word of a result record (kResultFlag): every thread of the last block calls
 // this after its last write to `result`, so that a host polling the word sees the whole record.
-__device__ __forceinline__ void result_complete(double* result) {
-  __threadfence_system();
+// Threads [0, writers) are the ones that wrote to the record; each of them fences its writes at
+// system scope (the threads of their warps fence too), then thread 0 sets the word.
+__device__ __forceinline__ void result_complete(double* result, int writers = 1 << 30) {
+  if ((int)(threadIdx.x & ~31u) < writers) __threadfence_system();
   __syncthreads();
   if (threadIdx.x == 0) *(volatile double*)(result + kResultFlag) = 1.0;
 }
@@ -443,10 +511,12 @@ __device__ __forceinline__ bool last_block_ticket(unsigned* ticket, int nblocks)
 }
 
 // Lane sums of partials[0 .. nblocks) by threads [0, nthreads) of the block (every thread of
-// the block calls it): lane s is summed by `per` consecutive threads (per a power of two),
+// the block calls it), loads in rounds of U per thread: lane s is summed by `per` consecutive
+// threads (per a power of two),
 // thread g of the group adding blocks g, g + per, ... in order; the group is combined by an
 // xor tree (and, for groups wider than a warp, by the warps in index order) into out[s]
 // (FP64).  Ends with a block barrier.
+template <int U = 16>
 __device__ __forceinline__ void reduce_partials(const float2* partials, int nslots, int nblocks, double* out,
                                                 ddf* smem, int nthreads) {
   int per = 1;
@@ -454,9 +524,8 @@ __device__ __forceinline__ void reduce_partials(const float2* partials, int nslo
   const int s = threadIdx.x / per, g = threadIdx.x % per;
   ddf acc = {0.f, 0.f};
   if (s < nslots && (int)threadIdx.x < nthreads) {
-    // rounds of sixteen independent loads in flight (the last round padded with exact zeros),
+    // rounds of U independent loads in flight (the last round padded with exact zeros),
     // added in block order: one L2 round trip per round
-    constexpr int U = 16;
     for (int b = g; b < nblocks; b += U * per) {
       float2 q[U];
 #pragma unroll

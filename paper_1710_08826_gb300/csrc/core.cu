@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "model.cuh"
 
 namespace goo {
 
@@ -442,6 +443,10 @@ int goo_finalize(goo_ctx* ctx) {
   if (s.theta) cudaFree(s.theta);
   if (s.host_pinned) cudaFreeHost(s.host_pinned);
   if (s.result_host) cudaFreeHost(s.result_host);
+  if (s.chunk_records) cudaFreeHost(s.chunk_records);
+  for (cudaEvent_t e : s.chunk_events)
+    if (e) cudaEventDestroy(e);
+  if (s.copy_stream) cudaStreamDestroy(s.copy_stream);
   fold_timings(ctx);
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   if (ctx->owns_stream) cudaStreamDestroy(ctx->stream);
@@ -550,6 +555,133 @@ int goo_dataset_update(goo_dataset* ds, const void* const* cols, int dtype, int6
                      "dataset now holds no events", nb, (long long)n_events);
   }
   ds->n = n_events;
+  return GOO_OK;
+}
+
+int goo_nll_grad_streamed(goo_model* m, goo_dataset* ds, const float* const* host_cols, int64_t n_events,
+                          int n_chunks, const double* theta, double* nll_out, double* grad_out, int64_t* n_bad) {
+  if (n_bad) *n_bad = 0;
+  if (!m || !ds || !host_cols || !theta || !nll_out) return set_error(GOO_ERR_ARG, "goo_nll_grad_streamed: NULL argument");
+  if (m->kind != 0)
+    return set_error(GOO_ERR_UNSUPPORTED, "goo_nll_grad_streamed: sum-of-product models only");
+  if (ds->ctx != m->ctx) return set_error(GOO_ERR_ARG, "goo_nll_grad_streamed: model and dataset of different contexts");
+  if (!ds->owns32 || !ds->owns64) return set_error(GOO_ERR_STATE, "goo_nll_grad_streamed: the dataset borrows its columns");
+  if (n_events < 1 || n_events > ds->capacity)
+    return set_error(GOO_ERR_ARG, "goo_nll_grad_streamed: n_events=%lld (capacity %lld)", (long long)n_events,
+                     (long long)ds->capacity);
+  if (n_chunks < 1 || n_chunks > kStreamChunks)
+    return set_error(GOO_ERR_ARG, "goo_nll_grad_streamed: n_chunks=%d (1..%d)", n_chunks, kStreamChunks);
+  if (ds->ncols < m->n_obs) return set_error(GOO_ERR_ARG, "goo_nll_grad_streamed: dataset has too few columns");
+  for (int o = 0; o < m->n_obs; ++o)
+    if (ds->lo[o] != m->lo[o] || ds->hi[o] != m->hi[o])
+      return set_error(GOO_ERR_ARG, "goo_nll_grad_streamed: observable %d limits differ from the model's", o);
+  for (int p = 0; p < m->n_params; ++p)
+    if (!std::isfinite(theta[p])) return set_error(GOO_ERR_ARG, "goo_nll_grad_streamed: theta[%d] is not finite", p);
+  goo_ctx* ctx = m->ctx;
+  GOO_CUDA_TRY(cudaSetDevice(ctx->device));
+  if (!host_mapped((const void* const*)host_cols, ds->ncols))
+    return set_error(GOO_ERR_ARG, "goo_nll_grad_streamed: the host columns must be pinned");
+  Scratch& sc = ctx->scratch;
+  if (!sc.copy_stream) GOO_CUDA_TRY(cudaStreamCreateWithFlags(&sc.copy_stream, cudaStreamNonBlocking));
+  for (cudaEvent_t& e : sc.chunk_events)
+    if (!e) GOO_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  const size_t rec = kResultDoubles + 1;
+  if (!sc.chunk_records) {
+    GOO_CUDA_TRY(cudaHostAlloc(&sc.chunk_records, (size_t)kStreamChunks * rec * sizeof(double), cudaHostAllocMapped));
+    std::memset(sc.chunk_records, 0, (size_t)kStreamChunks * rec * sizeof(double));
+  }
+  // launches in flight may still read the old events: the copies start after them
+  GOO_CUDA_TRY(cudaEventRecord(sc.chunk_events[kStreamChunks], ctx->stream));
+  GOO_CUDA_TRY(cudaStreamWaitEvent(sc.copy_stream, sc.chunk_events[kStreamChunks], 0));
+  ds->n = 0;
+  ds->epoch = next_dataset_epoch();
+  if (ds->w64) cudaFree(ds->w64);
+  if (ds->w32) cudaFree(ds->w32);
+  ds->w64 = nullptr;
+  ds->w32 = nullptr;
+  for (auto& c : ds->cache) c.key = 0;
+  const bool fuse = sop_norm_in_event(m, GOO_F32, true);
+  GOO_TRY(sop_prepare(m, theta, GOO_F32, fuse));
+  unsigned long long* bad = (unsigned long long*)(sc.counters + 8);
+  GOO_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), ctx->stream));
+  // chunk boundaries on multiples of 2048 events (whole column tiles of the event kernel)
+  const int64_t step = ((n_events + n_chunks - 1) / n_chunks + 2047) / 2048 * 2048;
+  int nc = 0;
+  const goo_dataset& dsv = *ds;
+  for (int64_t b = 0; b < n_events; b += step, ++nc) {
+    const int64_t e = std::min(n_events, b + step);
+    for (int c = 0; c < ds->ncols; ++c)
+      GOO_CUDA_TRY(cudaMemcpyAsync(ds->d32[c] + b, host_cols[c] + b, (size_t)(e - b) * sizeof(float),
+                                   cudaMemcpyHostToDevice, sc.copy_stream));
+    GOO_CUDA_TRY(cudaEventRecord(sc.chunk_events[nc], sc.copy_stream));
+    GOO_CUDA_TRY(cudaStreamWaitEvent(ctx->stream, sc.chunk_events[nc], 0));
+    // the chunk's float64 copy and range count, then its evaluation
+    IngestArgs a{};
+    a.ncols = ds->ncols;
+    a.store_src = 0;
+    bool aligned = true;
+    for (int c = 0; c < ds->ncols; ++c) {
+      a.src[c] = ds->d32[c] + b;
+      a.d64[c] = ds->d64[c] + b;
+      a.d32[c] = ds->d32[c] + b;
+      a.lo[c] = ds->lo[c];
+      a.hi[c] = ds->hi[c];
+      aligned = aligned && ((uintptr_t)a.src[c] & 15) == 0 && ((uintptr_t)a.d64[c] & 15) == 0;
+    }
+    {
+      LaunchScope ls(ctx, "ingest");
+      const int nb_ = grid_blocks(ctx, aligned ? (e - b + 3) / 4 : e - b, 8);
+      if (aligned) ingest_kernel<true, true><<<nb_, kBlock, 0, ctx->stream>>>(a, e - b, bad);
+      else ingest_kernel<true, false><<<nb_, kBlock, 0, ctx->stream>>>(a, e - b, bad);
+      GOO_CUDA_TRY(cudaGetLastError());
+    }
+    double* r = sc.chunk_records + (size_t)nc * rec;
+    r[kResultFlag] = 0.0;
+    ds->n = e;  // the event kernel reads [b, e) of the columns
+    GOO_TRY(sop_events(m, &dsv, b, e, GOO_F32, true, 1, fuse, r));
+  }
+  unsigned long long* stage = (unsigned long long*)(sc.host_pinned + kPinnedResult);
+  GOO_CUDA_TRY(cudaMemcpyAsync(stage, bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
+  GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  const unsigned long long nb = *stage;
+  if (nb) {
+    ds->n = 0;
+    *nll_out = HUGE_VAL;
+    if (n_bad) *n_bad = (int64_t)nb;
+    return set_error(GOO_ERR_RANGE, "goo_nll_grad_streamed: %llu of %lld events lie outside the observable limits; the "
+                     "dataset now holds no events", nb, (long long)n_events);
+  }
+  ds->n = n_events;
+  // the chunks' records, added in chunk order with compensation (as goo_combine_partials)
+  const int P = m->n_params;
+  std::vector<double> parts((size_t)nc * (3 + P));
+  double nbad_total = 0.0, status = 0.0;
+  for (int c = 0; c < nc; ++c) {
+    const double* r = sc.chunk_records + (size_t)c * rec;
+    if (r[kResultFlag] == 0.0) return set_error(GOO_ERR_STATE, "goo_nll_grad_streamed: chunk %d wrote no record", c);
+    if (r[2] < 0) status = -1.0;
+    else nbad_total += r[2];
+    double* q = parts.data() + (size_t)c * (3 + P);
+    q[0] = r[0];
+    q[1] = r[1];
+    q[2] = 0.0;
+    for (int p = 0; p < P; ++p) q[3 + p] = r[3 + p];
+  }
+  if (status < 0) {
+    *nll_out = HUGE_VAL;
+    return set_error(GOO_ERR_TIMEOUT, "goo_nll_grad_streamed: a device wait for event data gave up");
+  }
+  if (nbad_total > 0) {
+    *nll_out = HUGE_VAL;
+    if (grad_out)
+      for (int p = 0; p < P; ++p) grad_out[p] = 0.0;
+    return set_error(GOO_ERR_NONPOSITIVE_PDF, "goo_nll_grad_streamed: density <= 0 for %.0f events", nbad_total);
+  }
+  std::vector<double> tot(3 + P);
+  GOO_TRY(goo_combine_partials(nc, P, parts.data(), tot.data()));
+  *nll_out = tot[0] + tot[1];
+  if (grad_out)
+    for (int p = 0; p < P; ++p) grad_out[p] = tot[3 + p];
   return GOO_OK;
 }
 

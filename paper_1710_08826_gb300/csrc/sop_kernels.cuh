@@ -265,11 +265,28 @@ __device__ __forceinline__ void load_offsets(const ModelDev* __restrict__ md, T 
 
 // =======================================================================================
 // fused per-event kernel: evaluate, log, accumulate (and adjoint lanes), reduce
-// Lanes: 0 = sum log f; 1..K = C_k; then A_{k,l,j} at 1 + K + (k*L + l)*3 + j.
+// Lanes: 0 = sum log f; 1..K = C_k; then the leaf-derivative lanes A_{k,l,j}: at
+// 1 + K + (k*L + l)*3 + j in the interpreter (SIG = 0); in a kernel specialised for a leaf
+// signature only the lanes its leaves have, packed in slot order (a_lane).
 // =======================================================================================
-template <typename T, int K, int L, bool GRAD>
+// Derivative lanes of the leaves in slots [0, slot) of a signature.
+__host__ __device__ constexpr int sig_nder_before(unsigned long long sig, int slot) {
+  int n = 0;
+  for (int s = 0; s < slot; ++s) n += leaf_nder(sig_op(sig, s));
+  return n;
+}
+// Lane of derivative q of leaf slot (k, l), and whether the kernel carries it.
+template <int K, int L, unsigned long long SIG>
+__host__ __device__ constexpr int a_lane(int k, int l, int q) {
+  return SIG == 0 ? 1 + K + (k * L + l) * 3 + q : 1 + K + sig_nder_before(SIG, k * L + l) + q;
+}
+template <int K, int L, unsigned long long SIG>
+__host__ __device__ constexpr bool a_present(int k, int l, int q) {
+  return SIG == 0 || q < leaf_nder(sig_op(SIG, k * L + l));
+}
+template <typename T, int K, int L, bool GRAD, unsigned long long SIG = 0>
 struct EventLanes {
-  static constexpr int NS = GRAD ? 1 + K + K * L * 3 : 1;
+  static constexpr int NS = !GRAD ? 1 : (SIG == 0 ? 1 + K + K * L * 3 : 1 + K + sig_nder_before(SIG, K * L));
 };
 
 // Block reduction of the per-thread lanes, last-block reduction over the blocks and the
@@ -288,9 +305,8 @@ struct EvNorm {
   double dw[GRAD ? K : 1][GRAD ? kMaxParams : 1];  // d w_k / d theta_p
 };
 
-// Sources of the final combination's constants: the model block in device memory (MdFin), or
-// the kernel's by-value constants together with the normalisation terms the block computed
-// itself (ParFin; t[k L + l] = {h S, D_1 / S, D_2 / S, D_3 / S} of leaf slot (k, l)).
+// Source of the final combination's constants for the kernels that read the model block in
+// device memory (the self-normalising pair kernel has its own finish, event_finish_fused).
 struct MdFin {
   const ModelDev* __restrict__ md;
   int nK;
@@ -305,21 +321,6 @@ struct MdFin {
   __device__ double term(int, int, int) const { return 0.0; }
 };
 
-template <int K, int L, bool GRAD>
-struct ParFin {
-  const EvNorm<K, L, GRAD>* N;
-  const double (*t)[4];
-  static constexpr bool kOwnNorm = true;
-  __device__ int n_params() const { return N->n_params; }
-  __device__ double w(int k) const { return N->w[k]; }
-  __device__ double dw(int k, int p) const {
-    if constexpr (GRAD) return N->dw[k][p];
-    else return 0.0;
-  }
-  __device__ double dlogN(int, int) const { return 0.0; }
-  __device__ int par(int k, int l, int j) const { return N->par[k][l][j]; }
-  __device__ double term(int k, int l, int j) const { return t[k * L + l][1 + j]; }
-};
 
 // Block reduction, last-block reduction over the blocks and the final FP64 combination
 // (lanes -> NLL and d NLL / d theta), shared by the event kernels:
@@ -327,11 +328,11 @@ struct ParFin {
 // with dlogN_kp = sum_{l,j: par = p} t_klj for a block's own normalisation terms.  Thread p
 // takes parameter p and gathers its terms in a fixed order.  The constants are loaded before
 // the block's reduction, so that their latency overlaps it; the last block alone combines.
-template <int K, int L, bool GRAD, typename Fin>
-__device__ __forceinline__ void event_finish(ddf (&v)[EventLanes<float, K, L, GRAD>::NS], unsigned bad, const Fin& F,
-                                             int nK, float2* partials, unsigned* counters, double* result,
-                                             int out_mode, ddf* s_red, unsigned* s_bad) {
-  constexpr int NS = EventLanes<float, K, L, GRAD>::NS;
+template <int K, int L, bool GRAD, unsigned long long SIG, typename Fin>
+__device__ __forceinline__ void event_finish(ddf (&v)[EventLanes<float, K, L, GRAD, SIG>::NS], unsigned bad,
+                                             const Fin& F, int nK, float2* partials, unsigned* counters,
+                                             double* result, int out_mode, ddf* s_red, unsigned* s_bad) {
+  constexpr int NS = EventLanes<float, K, L, GRAD, SIG>::NS;
   __shared__ double s_out[NS];
   __shared__ double s_w[K];
   __shared__ int s_par[K][L][3];
@@ -359,7 +360,15 @@ __device__ __forceinline__ void event_finish(ddf (&v)[EventLanes<float, K, L, GR
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_bad[w];
     if (b) atomicAdd(counters + 1, b);
   }
-  if (!last_block_reduce(partials, NS, gridDim.x, counters, s_out, s_red)) return;
+  if (!last_block_ticket(counters, gridDim.x)) return;
+  // every other block added to these words before its ticket (and a fence): plain L2 reads,
+  // issued before the reduction so that their latency overlaps it
+  unsigned nbad = 0u, status = 0u;
+  if (threadIdx.x == 0) {
+    nbad = __ldcg(counters + 1);
+    status = __ldcg(counters + kStatusWord);
+  }
+  reduce_partials(partials, NS, gridDim.x, s_out, s_red, blockDim.x);
 
   // ---- final combination (last block, FP64) ----
   const int off = out_mode == 0 ? 2 : 3;
@@ -378,16 +387,14 @@ __device__ __forceinline__ void event_finish(ddf (&v)[EventLanes<float, K, L, GR
         for (int l = 0; l < L; ++l)
 #pragma unroll
           for (int jj = 0; jj < 3; ++jj)
-            if (s_par[k][l][jj] == p)
+            if (a_present<K, L, SIG>(k, l, jj) && s_par[k][l][jj] == p)
               gp += s_w[k] * ((Fin::kOwnNorm ? s_out[1 + k] * F.term(k, l, jj) : 0.0) -
-                              s_out[1 + K + (k * L + l) * 3 + jj]);
+                              s_out[a_lane<K, L, SIG>(k, l, jj)]);
     }
     result[off + p] = gp;
   }
   if (threadIdx.x == 0) {
-    // every other block added to these words before its ticket (and a fence): plain L2 reads
-    const unsigned nbad = __ldcg(counters + 1);
-    const unsigned status = __ldcg(counters + kStatusWord);
+    counters[0] = 0u;  // the ticket
     counters[1] = 0u;
     counters[kStatusWord] = 0u;
     // a device wait that gave up is reported as a negative event count
@@ -400,7 +407,7 @@ __device__ __forceinline__ void event_finish(ddf (&v)[EventLanes<float, K, L, GR
       result[2] = nb;
     }
   }
-  result_complete(result);
+  result_complete(result, P > 1 ? P : 1);
 }
 
 // Resident blocks per SM the event kernel is compiled for: the FP32 form of the small shape
@@ -511,7 +518,7 @@ __global__ void __launch_bounds__(kBlock, EventOcc<T, K, L>::value) sop_event_ke
               (sizeof(T) == 4) ? ddf{(float)Aacc[k][l][j], 0.f} : dd_from_double((double)Aacc[k][l][j]);
     }
   }
-  event_finish<K, L, GRAD>(v, bad, MdFin{md, nK}, nK, partials, counters, result, out_mode, s_red, s_bad);
+  event_finish<K, L, GRAD, 0>(v, bad, MdFin{md, nK}, nK, partials, counters, result, out_mode, s_red, s_bad);
 }
 
 // =======================================================================================
@@ -683,14 +690,16 @@ __device__ __forceinline__ void grid_coord(const GridDev& G, int d, int64_t idx,
 // evaluates them itself at its start instead of waiting for a normalisation kernel, from
 // by-value constants only.  Warp w takes leaf slots w, w + 8, ...; its lanes stride the bins
 // in a fixed order, accumulate in double-float (exact products by fma) and reduce by a fixed
-// shuffle tree, so every block obtains bit-identical sums.  FP64 runs only in the last step,
-// in one warp with a lane per (slot, term) and per product: GB300's FP64 pipe is 1/64 of
-// FP32, and every block pays it.  s_term[k L + l] = {h S, D_1 / S, D_2 / S, D_3 / S} stays
-// for the final combination.
+// shuffle tree, so every block obtains bit-identical sums s_raw[k L + l] = {S, D_1, D_2, D_3}
+// (D_j = sum of U d log(leaf) / d c_j).  Only the offsets -log N_k are needed before the
+// events: one lane per product forms them in FP32 arithmetic (log_dd).  The ratios D_j / S
+// that the gradient needs are formed by the last block alone (event_finish_fused), so that
+// the prologue every block pays holds no FP64 arithmetic (GB300's FP64 pipe is 1/64 of FP32
+// and its latency dominated this step).
 template <int K, int L, bool GRAD>
 __device__ __forceinline__ void fused_grid_norm(const EvConst<float, K, L>& P, const EvNorm<K, L, GRAD>& N,
-                                                ddf (*s_raw)[4], double (*s_term)[4], float (*s_off)[2],
-                                                float (&off_hi)[K], float (&off_lo)[K]) {
+                                                ddf (*s_raw)[4], float (*s_off)[2], float (&off_hi)[K],
+                                                float (&off_lo)[K]) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int sl = 0; sl < K * L; ++sl) {
@@ -717,27 +726,23 @@ __device__ __forceinline__ void fused_grid_norm(const EvConst<float, K, L>& P, c
       for (int jj = 0; jj < 4; ++jj) s_raw[sl][jj] = acc[jj];
   }
   __syncthreads();
-  if (warp == 0) {
-    for (int t = lane; t < K * L * 4; t += 32) {
-      const int sl = t >> 2, jj = t & 3;
+  if (warp == 0 && lane < K) {
+    // log N_k = log prod_l (h_l S_l) + sum_l a_l, one lane per product, the product in
+    // double-float and its logarithm in FP32 with the exponent split off exactly (log_dd):
+    // about 3e-8 absolute, i.e. 1e-8 of the NLL of ten million events, with no FP64 latency
+    // in the prologue every block pays
+    ddf prod = {1.f, 0.f}, aref = {0.f, 0.f};
+    bool any = false;
+    for (int l = 0; l < L; ++l) {
+      const int sl = lane * L + l;
       if (N.nb[sl] == 0) continue;
-      const double S = dd_to_double(s_raw[sl][0]);
-      s_term[sl][jj] = jj == 0 ? N.h64[sl] * S : dd_to_double(s_raw[sl][jj]) / S;
+      prod = dd_mul(prod, dd_mul({N.h_hi[sl], N.h_lo[sl]}, s_raw[sl][0]));
+      aref = dd_add(aref, dd_make(N.aref_hi[sl], N.aref_lo[sl]));
+      any = true;
     }
-    __syncwarp();
-    if (lane < K) {
-      double prod = 1.0, aref = 0.0;
-      for (int l = 0; l < L; ++l) {
-        const int sl = lane * L + l;
-        if (N.nb[sl] == 0) continue;
-        prod *= s_term[sl][0];
-        aref += (double)N.aref_hi[sl] + (double)N.aref_lo[sl];
-      }
-      const double logN = log(prod) + aref;
-      const float oh = (float)(-logN);
-      s_off[lane][0] = oh;
-      s_off[lane][1] = (float)(-logN - (double)oh);
-    }
+    const ddf logN = any ? dd_add(log_dd(prod), aref) : ddf{0.f, 0.f};
+    s_off[lane][0] = -logN.hi;
+    s_off[lane][1] = -logN.lo;
   }
   __syncthreads();
 #pragma unroll
@@ -745,6 +750,109 @@ __device__ __forceinline__ void fused_grid_norm(const EvConst<float, K, L>& P, c
     off_hi[k] = s_off[k][0];
     off_lo[k] = s_off[k][1];
   }
+}
+
+// Block reduction, last-block reduction over the blocks and the final FP64 combination of the
+// self-normalising pair kernel:
+//   d NLL / d theta_p = - sum_k C_k dw_kp + sum_{k,l,j: par = p} w_k (C_k D_klj / S_kl - A_klj),
+// the normalisation terms D_klj / S_kl formed here from the block's own grid sums.  Thread p
+// takes parameter p; its terms are formed independently and added by a fixed pairwise tree
+// (the combination is bound by FP64 latency, not throughput).  buf: NS * blockDim
+// double-floats of shared memory (the tile buffers, idle now) for the block reduction.
+template <int K, int L, bool GRAD, unsigned long long SIG>
+__device__ __forceinline__ void event_finish_fused(const ddf (&v)[EventLanes<float, K, L, GRAD, SIG>::NS],
+                                                   unsigned bad, const EvNorm<K, L, GRAD>& N,
+                                                   const ddf (*s_raw)[4], int nK, float2* partials,
+                                                   unsigned* counters, double* result, int out_mode, ddf* buf,
+                                                   unsigned* s_bad) {
+  constexpr int NS = EventLanes<float, K, L, GRAD, SIG>::NS;
+  constexpr int NT = GRAD ? K + K * L * 3 : 1;  // terms of one parameter's gradient
+  __shared__ double s_out[NS];
+  __shared__ double s_w[K];
+  __shared__ double s_t[K * L][3];
+  __shared__ int s_par[K][L][3];
+  __shared__ ddf s_red[kBlock / 32];
+  const int p = threadIdx.x;
+  const int P = N.n_params;
+  double dwp[GRAD ? K : 1];
+  if constexpr (GRAD) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) dwp[k] = (p < P && k < nK) ? N.dw[k][p] : 0.0;
+    for (int t = threadIdx.x; t < K * L * 3; t += blockDim.x) {
+      const int k = t / (L * 3), l = (t / 3) % L, jj = t % 3;
+      s_par[k][l][jj] = k < nK ? N.par[k][l][jj] : -1;
+    }
+    if (threadIdx.x < K) s_w[threadIdx.x] = N.w[threadIdx.x];
+  }
+  for (int m = 16; m > 0; m >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, m);
+  if ((threadIdx.x & 31) == 0) s_bad[threadIdx.x >> 5] = bad;
+  block_reduce_transpose<NS>(v, partials, buf);
+  if (threadIdx.x == 0) {
+    unsigned b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_bad[w];
+    if (b) atomicAdd(counters + 1, b);
+  }
+  if (!last_block_ticket(counters, gridDim.x)) return;
+  // every other block added to these words before its ticket (and a fence): plain L2 reads,
+  // issued before the reduction so that their latency overlaps it
+  unsigned nbad = 0u, status = 0u;
+  if (threadIdx.x == 0) {
+    nbad = __ldcg(counters + 1);
+    status = __ldcg(counters + kStatusWord);
+  }
+  if constexpr (GRAD) {
+    // the normalisation terms D_j / S of every leaf slot, from this block's grid sums (the
+    // quotient in double-float, then FP64)
+    for (int t = threadIdx.x; t < K * L * 3; t += blockDim.x) {
+      const int sl = t / 3, jj = t % 3;
+      s_t[sl][jj] = N.nb[sl] ? dd_to_double(dd_div(s_raw[sl][1 + jj], s_raw[sl][0])) : 0.0;
+    }
+  }
+  reduce_partials<24>(partials, NS, gridDim.x, s_out, s_red, blockDim.x);
+
+  // ---- final combination (last block, FP64) ----
+  const int off = out_mode == 0 ? 2 : 3;
+  if (p < P) {
+    double tm[NT];
+    if constexpr (GRAD) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) tm[k] = k < nK ? -s_out[1 + k] * dwp[k] : 0.0;
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+#pragma unroll
+          for (int jj = 0; jj < 3; ++jj) {
+            double term = 0.0;
+            if (a_present<K, L, SIG>(k, l, jj) && s_par[k][l][jj] == p)
+              term = s_w[k] * (s_out[1 + k] * s_t[k * L + l][jj] - s_out[a_lane<K, L, SIG>(k, l, jj)]);
+            tm[K + (k * L + l) * 3 + jj] = term;
+          }
+      // fixed pairwise tree over the NT terms
+#pragma unroll
+      for (int w = 1; w < NT; w *= 2)
+#pragma unroll
+        for (int i = 0; i + w < NT; i += 2 * w) tm[i] += tm[i + w];
+    } else {
+      tm[0] = 0.0;
+    }
+    result[off + p] = tm[0];
+  }
+  if (threadIdx.x == 0) {
+    counters[0] = 0u;  // the ticket
+    counters[1] = 0u;
+    counters[kStatusWord] = 0u;
+    // a device wait that gave up is reported as a negative event count
+    const double nb = status ? -1.0 : (double)nbad;
+    result[0] = -s_out[0];
+    if (out_mode == 0) {
+      result[1] = nb;
+    } else {
+      result[1] = 0.0;
+      result[2] = nb;
+    }
+  }
+  result_complete(result, P > 1 ? P : 1);
 }
 
 constexpr int kEventStages = 3;     // column tiles in flight per block (TMA bulk copies)
@@ -840,7 +948,7 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
                       const __grid_constant__ EvNorm<K, L, GRAD> N, Cols<float> cols, int64_t begin, int64_t end,
                       float2* partials, unsigned* counters, double* result, int out_mode, int fused_norm) {
   using namespace pk;
-  constexpr int NS = EventLanes<float, K, L, GRAD>::NS;
+  constexpr int NS = EventLanes<float, K, L, GRAD, SIG>::NS;
   constexpr int PPT = kPairsPerThread;
   constexpr int TE = 2 * PPT * kBlock;
   constexpr int NST = kEventStages;
@@ -851,7 +959,6 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
   __shared__ unsigned s_done[NST];  // warps done with each stage's buffer, counted over all its tiles
   __shared__ int s_last[NST];       // the last tile issued into each stage (-1: none)
   __shared__ unsigned s_fail;
-  __shared__ double s_term[K * L][4];
   __shared__ ddf s_raw[K * L][4];
   __shared__ float s_off[K][2];
   extern __shared__ __align__(128) float s_col[];  // [NST][nobs][TE]
@@ -892,7 +999,7 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
   float off_hi[K], off_lo[K];
   const int nK = P.nK;
   if (fused_norm) {
-    fused_grid_norm<K, L, GRAD>(P, N, s_raw, s_term, s_off, off_hi, off_lo);  // synchronises the block
+    fused_grid_norm<K, L, GRAD>(P, N, s_raw, s_off, off_hi, off_lo);  // synchronises the block
   } else {
     load_offsets<float, K>(md, off_hi, off_lo);
     __syncthreads();  // barriers initialised before any thread waits on them
@@ -1001,14 +1108,15 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
       for (int l = 0; l < L; ++l)
 #pragma unroll
         for (int q = 0; q < 3; ++q)
-          v[1 + K + (k * L + l) * 3 + q] = dd_add(ddf{S.A[k][l][q].x, 0.f}, ddf{S.A[k][l][q].y, 0.f});
+          if (a_present<K, L, SIG>(k, l, q))
+            v[a_lane<K, L, SIG>(k, l, q)] = dd_add(ddf{S.A[k][l][q].x, 0.f}, ddf{S.A[k][l][q].y, 0.f});
     }
   }
   if (fused_norm)
-    event_finish<K, L, GRAD>(v, S.bad, ParFin<K, L, GRAD>{&N, s_term}, nK, partials, counters, result, out_mode, s_red,
-                             s_bad);
+    event_finish_fused<K, L, GRAD, SIG>(v, S.bad, N, s_raw, nK, partials, counters, result, out_mode,
+                                        reinterpret_cast<ddf*>(s_col), s_bad);
   else
-    event_finish<K, L, GRAD>(v, S.bad, MdFin{md, nK}, nK, partials, counters, result, out_mode, s_red, s_bad);
+    event_finish<K, L, GRAD, SIG>(v, S.bad, MdFin{md, nK}, nK, partials, counters, result, out_mode, s_red, s_bad);
 }
 
 }  // namespace goo

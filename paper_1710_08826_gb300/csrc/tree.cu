@@ -950,9 +950,12 @@ static int launch_event2(goo_model* m, const goo_dataset* ds, int64_t begin, int
                          bool fused_norm, double* result) {
   goo_ctx* ctx = m->ctx;
   constexpr int TE = 2 * kPairsPerThread * kBlock;
-  const size_t smem = (size_t)kEventStages * m->host.n_obs * TE * sizeof(float);
+  // the column tiles, and room for the final block reduction (event_finish_fused), which reuses
+  // the tile buffers: every lane of every thread as a double-float
+  constexpr size_t red_bytes = (size_t)EventLanes<float, K, L, GRAD>::NS * kBlock * sizeof(ddf);
+  const size_t smem = std::max((size_t)kEventStages * m->host.n_obs * TE * sizeof(float), red_bytes);
   // room for the largest column count, so one setting serves every model on this device
-  const size_t smem_max = (size_t)kEventStages * kMaxObs * TE * sizeof(float);
+  const size_t smem_max = std::max((size_t)kEventStages * kMaxObs * TE * sizeof(float), red_bytes);
   static bool configured[kMaxDevicesEv] = {};
   if (ctx->device < 0 || ctx->device >= kMaxDevicesEv) return set_error(GOO_ERR_ARG, "device %d", ctx->device);
   // the kernel for this model and gradient form, resolved on its first evaluation: the one
@@ -991,8 +994,11 @@ static int launch_event2(goo_model* m, const goo_dataset* ds, int64_t begin, int
   Cols<float> cols{};
   for (int c = 0; c < kMaxObs; ++c) cols.c[c] = ds->d32[c < ds->ncols ? c : 0];
   {
-    // programmatic dependent launch: the kernel's blocks start (and put their first column
-    // tiles in flight) while the normalisation kernel before it finishes
+    // programmatic dependent launch after a normalisation kernel: the kernel's blocks start
+    // (and put their first column tiles in flight) while that kernel finishes.  A kernel that
+    // normalises the grid itself depends on no kernel's output but the previous evaluation's
+    // counters, which plain stream order covers: it launches without the attribute, since its
+    // in-kernel dependency wait cost microseconds per evaluation.
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nb);
     cfg.blockDim = dim3(kBlock);
@@ -1002,7 +1008,7 @@ static int launch_event2(goo_model* m, const goo_dataset* ds, int64_t begin, int
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = fused_norm ? 0 : 1;
     LaunchScope ls(ctx, GRAD ? "sop_nll_grad_f32" : "sop_nll_f32");
     EvNorm<K, L, GRAD> N;
     if (fused_norm) N = make_evnorm<K, L, GRAD>(*m->stage);

@@ -111,6 +111,8 @@ def _load():
         "goo_nll_grad": (ctypes.c_int, [vp, vp, dp, ctypes.c_int, dp, dp]),
         "goo_eval_logf": (ctypes.c_int, [vp, vp, dp, ctypes.c_int, vp]),
         "goo_nll_partial": (ctypes.c_int, [vp, vp, i64, i64, dp, ctypes.c_int, ctypes.c_int, dp]),
+        "goo_nll_grad_streamed": (ctypes.c_int, [vp, vp, ctypes.POINTER(vp), i64, ctypes.c_int, dp, dp, dp,
+                                                 ctypes.POINTER(i64)]),
         "goo_combine_partials": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, dp, dp]),
         "goo_gram": (ctypes.c_int, [vp, dp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int)]),
         "goo_server_create": (ctypes.c_int, [vp, dp, ctypes.POINTER(ctypes.c_int), dp, ctypes.POINTER(GooServerOptions),
@@ -503,6 +505,22 @@ class Model:
         g = np.zeros(self.n_params)
         _check(lib.goo_nll_grad(self.handle, ds.handle, tp, precision_code(precision), ctypes.byref(out),
                                 g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out.value, g
+
+    def nll_grad_streamed(self, ds, host_columns, theta, n_chunks=8):
+        """FP32 NLL and gradient of pinned float32 host columns (torch tensors made with
+        pin_memory()), refilling ds chunk by chunk while earlier chunks are evaluated
+        (goo_nll_grad_streamed)."""
+        t, tp = self._theta(theta)
+        ptrs = (ctypes.c_void_p * len(host_columns))(*[int(c.data_ptr()) for c in host_columns])
+        n = int(host_columns[0].numel())
+        out = ctypes.c_double()
+        g = np.zeros(self.n_params)
+        nbad = ctypes.c_int64()
+        rc = lib.goo_nll_grad_streamed(self.handle, ds.handle, ptrs, n, int(n_chunks), tp, ctypes.byref(out),
+                                       g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(nbad))
+        ds.n = int(lib.goo_dataset_size(ds.handle))
+        _check(rc)
         return out.value, g
 
     def eval_logf(self, ds, theta, precision="f64"):
