@@ -472,6 +472,16 @@ def run_ours(args):
         launches0 = ctx.launches
 
         def run(n):
+            # the interpreter's garbage collector stays off while steps are timed (its pauses
+            # are host jitter, not work of the step)
+            import gc
+            gc.disable()
+            try:
+                return run_steps(n)
+            finally:
+                gc.enable()
+
+        def run_steps(n):
             ms = []
             for _ in range(n):
                 flush.zero_()                       # L2 flush between timed steps (not timed)

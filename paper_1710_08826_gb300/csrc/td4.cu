@@ -63,6 +63,10 @@ struct Td4Args {
   int wN, K, n_params, planes;
   int par_re[kTdMaxAmp], par_im[kTdMaxAmp], par_t[4];
   int64_t n_total;  // events of the dataset (cache plane length)
+  // the normalisation at theta, formed on the host in FP64 from the cached Gram matrix
+  // (td4_norm_terms): N, log N, (dN / d Re c_k) / N, (dN / d Im c_k) / N and (dN / dx) / N,
+  // (dN / dy) / N, (tau dN / d tau) / N
+  double nrm_N, nrm_logN, nrm_ur[kTdMaxAmp], nrm_ui[kTdMaxAmp], nrm_dt[3];
 };
 
 
@@ -213,11 +217,13 @@ __device__ __forceinline__ void td4_event(const Td4Args<T>& a, const T (&ar)[KB]
   }
 }
 
-// Block and last-block reductions, then the FP64 combination with the Gram matrix.
+// Block and last-block reductions, then the FP64 combination with the normalisation terms the
+// host formed from the Gram matrix (they depend on theta and the MC sample only, not on the
+// events: an O(K^2) quadratic form, whose FP64 latency chain had been the last block's tail).
 template <typename T, int KB, bool GRAD>
 __device__ __forceinline__ void td4_finish(const Td4Args<T>& a, TdAcc<T, KB>& acc, int64_t begin, int64_t end,
-                                           const double* __restrict__ gram, float2* partials, unsigned* counters,
-                                           double* result, int out_mode, ddf* s_red, unsigned* s_bad) {
+                                           float2* partials, unsigned* counters, double* result, int out_mode,
+                                           ddf* s_red, unsigned* s_bad) {
   constexpr int NS = TdLanes<KB, GRAD>::NS;
   ddf v[NS];
   v[0] = (sizeof(T) == 4) ? acc.lf32.value() : dd_from_double(acc.lf64);
@@ -242,99 +248,46 @@ __device__ __forceinline__ void td4_finish(const Td4Args<T>& a, TdAcc<T, KB>& ac
   }
   __shared__ double s_out[NS];
   if (!last_block_ticket(counters, gridDim.x)) return;
-  // The last block: its last warp forms the normalisation, which depends on theta and the
-  // Gram matrix only, while the other threads reduce the blocks' lanes.  Lane k of that warp
-  // forms v_c = sum_l G_kl conj(c_l) and v_b likewise, the four moments <|A|^2>, <|B|^2>,
-  // <A B*> by fixed xor trees, N with the time integrals, and the normalisation parts of the
-  // gradients (d N / d theta) / N; then thread p gathers the gradient of parameter p.
-  __shared__ double s_ur[kTdMaxAmp], s_ui[kTdMaxAmp], s_dt[3];
-  __shared__ int s_pre[kTdMaxAmp], s_pim[kTdMaxAmp], s_pt[4];
-  __shared__ double s_N, s_logN;
-  const int K = a.K;
-  const int nwarp = blockDim.x >> 5;
-  if ((int)(threadIdx.x >> 5) == nwarp - 1) {
-    const int k = threadIdx.x & 31;
-    const double x = (double)a.x, y = (double)a.y, tau = 1.0 / (double)a.G;
-    const double iy = 1.0 / (1 - y * y), ix = 1.0 / (1 + x * x);
-    const double Ich = tau * iy, Ish = y * tau * iy, Ic = tau * ix, Is = x * tau * ix;
-    double vcr = 0, vci = 0, vbr = 0, vbi = 0, aa = 0, bb = 0, abr = 0, abi = 0;
-    if (k < K) {
-      for (int l = 0; l < K; ++l) {
-        const double gr = __ldg(gram + 2 * (k * K + l)), gi = __ldg(gram + 2 * (k * K + l) + 1);
-        const double clr = (double)a.cr[l], cli = (double)a.ci[l], blr = (double)a.br[l], bli = (double)a.bi[l];
-        vcr += gr * clr + gi * cli;  // G_kl conj(c_l)
-        vci += gi * clr - gr * cli;
-        vbr += gr * blr + gi * bli;
-        vbi += gi * blr - gr * bli;
-      }
-      const double ckr = (double)a.cr[k], cki = (double)a.ci[k], bkr = (double)a.br[k], bki = (double)a.bi[k];
-      aa = ckr * vcr - cki * vci;  // Re(c_k v_c)
-      bb = bkr * vbr - bki * vbi;
-      abr = ckr * vbr - cki * vbi;  // c_k v_b (sum over k = <A B*>)
-      abi = ckr * vbi + cki * vbr;
-    }
-    for (int m = 16; m > 0; m >>= 1) {
-      aa += __shfl_xor_sync(0xffffffffu, aa, m);
-      bb += __shfl_xor_sync(0xffffffffu, bb, m);
-      abr += __shfl_xor_sync(0xffffffffu, abr, m);
-      abi += __shfl_xor_sync(0xffffffffu, abi, m);
-    }
-    const double N = 0.5 * (aa + bb) * Ich + 0.5 * (aa - bb) * Ic + abr * Ish + abi * Is;
-    const double invN = 1.0 / N;
-    if (k < K) {
-      // dN/dRe c_k = Re((I_ch + I_c) v_c + (I_sh - i I_s) v_b), dN/dIm c_k = -Im(same)
-      s_ur[k] = ((Ich + Ic) * vcr + Ish * vbr + Is * vbi) * invN;
-      s_ui[k] = ((Ich + Ic) * vci + Ish * vbi - Is * vbr) * invN;
-      s_pre[k] = a.par_re[k];
-      s_pim[k] = a.par_im[k];
-    }
-    if (k < 4) s_pt[k] = a.par_t[k];
-    if (k == 0) {
-      s_N = N;
-      s_logN = log(N);
-      const double ix2 = ix * ix, iy2 = iy * iy;
-      const double dxc = -2 * x * tau * ix2, dxs = tau * (1 - x * x) * ix2;
-      const double dych = 2 * y * tau * iy2, dysh = tau * (1 + y * y) * iy2;
-      s_dt[0] = (0.5 * (aa - bb) * dxc + abi * dxs) * invN;  // (dN/dx) / N
-      s_dt[1] = (0.5 * (aa + bb) * dych + abr * dysh) * invN;
-      s_dt[2] = (0.5 * (aa + bb) * iy + 0.5 * (aa - bb) * ix + abr * y * iy + abi * x * ix) * invN;  // tau dN/dtau / N
-    }
+  // every other block added to these words before its ticket (and a fence): plain L2 reads,
+  // issued before the reduction so that their latency overlaps it
+  unsigned nbad = 0u, status = 0u;
+  if (threadIdx.x == 0) {
+    nbad = __ldcg(counters + 1);
+    status = __ldcg(counters + kStatusWord);
   }
-  reduce_partials(partials, NS, gridDim.x, s_out, s_red, blockDim.x - 32);
+  reduce_partials(partials, NS, gridDim.x, s_out, s_red, blockDim.x);
   const double nev = (double)(end - begin);
+  const int K = a.K;
   const int P = a.n_params;
   const int off = out_mode == 0 ? 2 : 3;
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
     double g = 0.0;
     if (GRAD) {
       for (int k = 0; k < K; ++k) {
-        if (s_pre[k] == p) g += -s_out[1 + 2 * k] + nev * s_ur[k];
-        if (s_pim[k] == p) g += -s_out[2 + 2 * k] - nev * s_ui[k];
+        if (a.par_re[k] == p) g += -s_out[1 + 2 * k] + nev * a.nrm_ur[k];
+        if (a.par_im[k] == p) g += -s_out[2 + 2 * k] - nev * a.nrm_ui[k];
       }
       const int o = 1 + 2 * KB;
       for (int j = 0; j < 4; ++j)
-        if (s_pt[j] == p) g += -s_out[o + j] + (j < 3 ? nev * s_dt[j] : 0.0);
+        if (a.par_t[j] == p) g += -s_out[o + j] + (j < 3 ? nev * a.nrm_dt[j] : 0.0);
     }
     result[off + p] = g;
   }
   if (threadIdx.x == 0) {
-    // every other block added to these words before its ticket (and a fence): plain L2 reads
-    const unsigned nbad = __ldcg(counters + 1);
-    const unsigned status = __ldcg(counters + kStatusWord);
     counters[1] = 0u;
     counters[kStatusWord] = 0u;
     *counters = 0u;  // the ticket
     const double nb = status ? -1.0 : (double)nbad;  // a wait that gave up: negative count
-    result[0] = -s_out[0] + nev * s_logN;
+    result[0] = -s_out[0] + nev * a.nrm_logN;
     if (out_mode == 0) {
       result[1] = nb;
-      result[2 + P] = s_N;
+      result[2 + P] = a.nrm_N;
     } else {
       result[1] = 0.0;
       result[2] = nb;
     }
   }
-  result_complete(result);
+  result_complete(result, P > 1 ? P : 1);
 }
 
 // FP64: direct loads, one event per thread per grid-stride step.
@@ -342,9 +295,8 @@ template <int KB, bool GRAD>
 __global__ void __launch_bounds__(kBlock, 2) td4_nll_f64_kernel(const __grid_constant__ Td4Args<double> a,
                                                                 const double2* __restrict__ cache,
                                                                 const double* __restrict__ tcol, int64_t begin,
-                                                                int64_t end, const double* __restrict__ gram,
-                                                                float2* partials, unsigned* counters, double* result,
-                                                                int out_mode) {
+                                                                int64_t end, float2* partials, unsigned* counters,
+                                                                double* result, int out_mode) {
   constexpr int NS = TdLanes<KB, GRAD>::NS;
   __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
   __shared__ unsigned s_bad[kBlock / 32];
@@ -367,7 +319,7 @@ __global__ void __launch_bounds__(kBlock, 2) td4_nll_f64_kernel(const __grid_con
     }
     td4_event<double, KB, GRAD>(a, ar, ai, tcol[i], acc);
   }
-  td4_finish<double, KB, GRAD>(a, acc, begin, end, gram, partials, counters, result, out_mode, s_red, s_bad);
+  td4_finish<double, KB, GRAD>(a, acc, begin, end, partials, counters, result, out_mode, s_red, s_bad);
 }
 
 // FP32: tiles of kTdTile events (aligned to multiples of kTdTile) of every amplitude plane
@@ -381,9 +333,8 @@ template <int KB, bool GRAD>
 __global__ void __launch_bounds__(kBlock, 2) td4_nll_f32_kernel(const __grid_constant__ Td4Args<float> a,
                                                                 const float4* __restrict__ cache,
                                                                 const float* __restrict__ tcol, int64_t begin,
-                                                                int64_t end, const double* __restrict__ gram,
-                                                                float2* partials, unsigned* counters, double* result,
-                                                                int out_mode) {
+                                                                int64_t end, float2* partials, unsigned* counters,
+                                                                double* result, int out_mode) {
   constexpr int NS = TdLanes<KB, GRAD>::NS;
   constexpr int TE = kTdTile, NST = kTdStages;
   __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
@@ -466,7 +417,7 @@ __global__ void __launch_bounds__(kBlock, 2) td4_nll_f32_kernel(const __grid_con
     }
     __syncthreads();
   }
-  td4_finish<float, KB, GRAD>(a, acc, begin, end, gram, partials, counters, result, out_mode, s_red, s_bad);
+  td4_finish<float, KB, GRAD>(a, acc, begin, end, partials, counters, result, out_mode, s_red, s_bad);
 }
 
 // per-event log f = log R - log N (goo_eval_logf)
@@ -730,6 +681,54 @@ static void td4_args(const goo_model* m, const double* theta, int64_t n_total, T
   a.wL = (T)(sizeof(T) == 4 ? w.L32 : w.L64);
 }
 
+// The normalisation at theta from the host copy of the Gram matrix (td4_ensure_gram keeps it
+// current), in FP64 and at the precision-rounded parameters the kernel uses:
+//   v_c = G conj(c), v_b = G conj(b),  <|A|^2> = Re c.v_c, <|B|^2> = Re b.v_b, <A B*> = c.v_b,
+//   N = <|A|^2+|B|^2>/2 I_ch + <|A|^2-|B|^2>/2 I_c + Re<AB*> I_sh + Im<AB*> I_s,
+//   dN / d Re c_k = Re((I_ch + I_c) v_c,k + (I_sh - i I_s) v_b,k), dN / d Im c_k = -Im(same),
+// with the time integrals' derivatives for x, y and tau.
+template <typename T>
+static void td4_norm_terms(const goo_model* m, int precision, Td4Args<T>& a) {
+  const Td4Model& d = *m->td4;
+  const int pi = precision == GOO_F32 ? 0 : 1;
+  const int K = d.K;
+  const double x = (double)a.x, y = (double)a.y, tau = 1.0 / (double)a.G;
+  const double iy = 1.0 / (1 - y * y), ix = 1.0 / (1 + x * x);
+  const double Ich = tau * iy, Ish = y * tau * iy, Ic = tau * ix, Is = x * tau * ix;
+  double vcr[kTdMaxAmp], vci[kTdMaxAmp], vbr[kTdMaxAmp], vbi[kTdMaxAmp];
+  double aa = 0, bb = 0, abr = 0, abi = 0;
+  for (int k = 0; k < K; ++k) {
+    vcr[k] = vci[k] = vbr[k] = vbi[k] = 0.0;
+    for (int l = 0; l < K; ++l) {
+      const double gr = d.gram_host[pi][2 * (k * K + l)], gi = d.gram_host[pi][2 * (k * K + l) + 1];
+      const double clr = (double)a.cr[l], cli = (double)a.ci[l], blr = (double)a.br[l], bli = (double)a.bi[l];
+      vcr[k] += gr * clr + gi * cli;  // G_kl conj(c_l)
+      vci[k] += gi * clr - gr * cli;
+      vbr[k] += gr * blr + gi * bli;
+      vbi[k] += gi * blr - gr * bli;
+    }
+    const double ckr = (double)a.cr[k], cki = (double)a.ci[k], bkr = (double)a.br[k], bki = (double)a.bi[k];
+    aa += ckr * vcr[k] - cki * vci[k];  // Re(c_k v_c,k)
+    bb += bkr * vbr[k] - bki * vbi[k];
+    abr += ckr * vbr[k] - cki * vbi[k];  // c_k v_b,k (summed: <A B*>)
+    abi += ckr * vbi[k] + cki * vbr[k];
+  }
+  const double N = 0.5 * (aa + bb) * Ich + 0.5 * (aa - bb) * Ic + abr * Ish + abi * Is;
+  const double invN = 1.0 / N;
+  for (int k = 0; k < K; ++k) {
+    a.nrm_ur[k] = ((Ich + Ic) * vcr[k] + Ish * vbr[k] + Is * vbi[k]) * invN;
+    a.nrm_ui[k] = ((Ich + Ic) * vci[k] + Ish * vbi[k] - Is * vbr[k]) * invN;
+  }
+  a.nrm_N = N;
+  a.nrm_logN = std::log(N);
+  const double ix2 = ix * ix, iy2 = iy * iy;
+  const double dxc = -2 * x * tau * ix2, dxs = tau * (1 - x * x) * ix2;
+  const double dych = 2 * y * tau * iy2, dysh = tau * (1 + y * y) * iy2;
+  a.nrm_dt[0] = (0.5 * (aa - bb) * dxc + abi * dxs) * invN;  // (dN/dx) / N
+  a.nrm_dt[1] = (0.5 * (aa + bb) * dych + abr * dysh) * invN;
+  a.nrm_dt[2] = (0.5 * (aa + bb) * iy + 0.5 * (aa - bb) * ix + abr * y * iy + abi * x * ix) * invN;  // tau dN/dtau / N
+}
+
 static int td4_check_theta(const goo_model* m, const double* theta) {
   const Td4Model& d = *m->td4;
   const double x = theta[d.par_t[0]], y = theta[d.par_t[1]], tau = theta[d.par_t[2]], s = theta[d.par_t[3]];
@@ -746,6 +745,7 @@ static int launch_td4_f32(goo_model* m, const void* cache, const goo_dataset* ds
   goo_ctx* ctx = m->ctx;
   Td4Args<float> a;
   td4_args<float>(m, theta, ds->n, a);
+  td4_norm_terms<float>(m, GOO_F32, a);
   const size_t smem = (size_t)kTdStages * ((size_t)a.planes * kTdTile * sizeof(float4) + kTdTile * sizeof(float));
   static bool configured[kMaxDevicesTd] = {};
   if (ctx->device < 0 || ctx->device >= kMaxDevicesTd) return set_error(GOO_ERR_ARG, "device %d", ctx->device);
@@ -761,8 +761,8 @@ static int launch_td4_f32(goo_model* m, const void* cache, const goo_dataset* ds
   {
     LaunchScope ls(ctx, GRAD ? "td4_nll_grad_f32" : "td4_nll_f32");
     td4_nll_f32_kernel<KB, GRAD><<<nb, kBlock, smem, ctx->stream>>>(a, (const float4*)cache, ds->d32[5], begin, end,
-                                                                   m->td4->gram_dev[0], ctx->scratch.partials,
-                                                                   ctx->scratch.counters, ctx->scratch.result_out, out_mode);
+                                                                   ctx->scratch.partials, ctx->scratch.counters,
+                                                                   ctx->scratch.result_out, out_mode);
   }
   GOO_CUDA_TRY(cudaGetLastError());
   return GOO_OK;
@@ -774,6 +774,7 @@ static int launch_td4_f64(goo_model* m, const void* cache, const goo_dataset* ds
   goo_ctx* ctx = m->ctx;
   Td4Args<double> a;
   td4_args<double>(m, theta, ds->n, a);
+  td4_norm_terms<double>(m, GOO_F64, a);
   static int occ = 0;
   if (occ == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, td4_nll_f64_kernel<KB, GRAD>, kBlock, 0) != cudaSuccess ||
                    occ < 1)) {
@@ -785,8 +786,8 @@ static int launch_td4_f64(goo_model* m, const void* cache, const goo_dataset* ds
   {
     LaunchScope ls(ctx, GRAD ? "td4_nll_grad_f64" : "td4_nll_f64");
     td4_nll_f64_kernel<KB, GRAD><<<nb, kBlock, 0, ctx->stream>>>(a, (const double2*)cache, ds->d64[5], begin, end,
-                                                                m->td4->gram_dev[1], ctx->scratch.partials,
-                                                                ctx->scratch.counters, ctx->scratch.result_out, out_mode);
+                                                                ctx->scratch.partials, ctx->scratch.counters,
+                                                                ctx->scratch.result_out, out_mode);
   }
   GOO_CUDA_TRY(cudaGetLastError());
   return GOO_OK;
