@@ -123,6 +123,9 @@ struct CohArgs {
   int64_t n_total;             // events of the dataset (cache plane length)
   int polar;                   // the coefficient parameters are (r, phi): c = r e^{i phi}
   double jc[kMaxAmp], js[kMaxAmp], jr[kMaxAmp];  // cos phi, sin phi, r per amplitude (polar)
+  // the normalisation at theta, formed on the host in FP64 from the cached Gram matrix
+  // (coh_norm_terms): N, log N and 2 v_k / N with v_k = sum_l G_kl conj(c_l)
+  double nrm_N, nrm_logN, nrm_vr[kMaxAmp], nrm_vi[kMaxAmp];
 };
 
 // A gradient over (Re c, Im c) of amplitude k mapped to its parameters (FP64): unchanged, or
@@ -181,12 +184,14 @@ __device__ __forceinline__ void coh_event(const T (&cr)[KB + 1], const T (&ci)[K
   }
 }
 
-// Block and last-block reductions of the lanes, then the FP64 combination with the Gram
-// matrix at the coefficients the kernel used.
+// Block and last-block reductions of the lanes, then the FP64 combination with the
+// normalisation terms the host formed from the Gram matrix at the coefficients the kernel used
+// (they depend on theta and the MC sample only: an O(K^2) quadratic form that would otherwise
+// be an FP64 latency chain on the last block).
 template <typename T, int KB, bool GRAD>
 __device__ __forceinline__ void coh_finish(const CohArgs<T>& a, CohAcc<T, KB>& acc, int64_t begin, int64_t end,
-                                           const double* __restrict__ gram, float2* partials, unsigned* counters,
-                                           double* result, int out_mode, ddf* s_red, unsigned* s_bad) {
+                                           float2* partials, unsigned* counters, double* result, int out_mode,
+                                           ddf* s_red, unsigned* s_bad) {
   constexpr int NS = CohLanes<T, KB, GRAD>::NS;
   constexpr int KA = KB + 1;
   ddf v[NS];
@@ -209,78 +214,49 @@ __device__ __forceinline__ void coh_finish(const CohArgs<T>& a, CohAcc<T, KB>& a
   }
   __shared__ double s_out[NS];
   if (!last_block_ticket(counters, gridDim.x)) return;
-  // The last block: its last warp forms the normalisation, which depends on theta and the
-  // Gram matrix only, while the other threads reduce the blocks' lanes.  Lane k of that warp
-  // forms v_k = sum_l G_kl conj(c_l), N = sum_k Re(c_k v_k) by a fixed xor tree, and the
-  // normalisation parts of the coefficient gradients, 2 v_k / N; then thread p gathers the
-  // gradient of parameter p (parameters may be shared) in a fixed order.
-  __shared__ double s_vr[kMaxAmp], s_vi[kMaxAmp];
-  __shared__ int s_pre[kMaxAmp], s_pim[kMaxAmp];
-  __shared__ double s_N, s_logN;
-  const int K = a.K;
-  const int nwarp = blockDim.x >> 5;
-  if ((int)(threadIdx.x >> 5) == nwarp - 1) {
-    const int k = threadIdx.x & 31;
-    double vr = 0.0, vi = 0.0, Nk = 0.0;
-    if (k < K) {
-      for (int l = 0; l < K; ++l) {
-        const double gr = __ldg(gram + 2 * (k * K + l)), gi = __ldg(gram + 2 * (k * K + l) + 1);
-        const double clr = (double)a.cr[l], cli = (double)a.ci[l];
-        vr += gr * clr + gi * cli;  // v_k = sum_l G_kl conj(c_l)
-        vi += gi * clr - gr * cli;
-      }
-      Nk = (double)a.cr[k] * vr - (double)a.ci[k] * vi;  // Re(c_k v_k)
-    }
-    double N = Nk;
-    for (int m = 16; m > 0; m >>= 1) N += __shfl_xor_sync(0xffffffffu, N, m);
-    const double invN = 1.0 / N;
-    if (k < K) {
-      s_vr[k] = 2.0 * vr * invN;
-      s_vi[k] = 2.0 * vi * invN;
-      s_pre[k] = a.par_re[k];
-      s_pim[k] = a.par_im[k];
-    }
-    if (k == 0) {
-      s_N = N;
-      s_logN = log(N);
-    }
+  // every other block added to these words before its ticket (and a fence): plain L2 reads,
+  // issued before the reduction so that their latency overlaps it
+  unsigned nbad = 0u, status = 0u;
+  if (threadIdx.x == 0) {
+    nbad = __ldcg(counters + 1);
+    status = __ldcg(counters + kStatusWord);
   }
-  reduce_partials(partials, NS, gridDim.x, s_out, s_red, blockDim.x - 32);
+  reduce_partials(partials, NS, gridDim.x, s_out, s_red, blockDim.x);
   const double nev = (double)(end - begin);
+  const int K = a.K;
   const int P = a.n_params;
   const int off = out_mode == 0 ? 2 : 3;
+  // thread p gathers the gradient of parameter p (parameters may be shared) in a fixed order
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
     double g = 0.0;
     if (GRAD)
       for (int k = 0; k < K; ++k) {
         const int slot = (k < a.nbw) ? k : KB;  // NR lives in the last slot
-        double gre = -2.0 * s_out[1 + 2 * slot] + nev * s_vr[k], gim = 2.0 * s_out[2 + 2 * slot] - nev * s_vi[k];
+        double gre = -2.0 * s_out[1 + 2 * slot] + nev * a.nrm_vr[k];
+        double gim = 2.0 * s_out[2 + 2 * slot] - nev * a.nrm_vi[k];
         coef_chain(a.polar, a.jc[k], a.js[k], a.jr[k], gre, gim);
-        if (s_pre[k] == p) g += gre;
-        if (s_pim[k] == p) g += gim;
+        if (a.par_re[k] == p) g += gre;
+        if (a.par_im[k] == p) g += gim;
       }
     result[off + p] = g;
   }
   if (threadIdx.x == 0) {
-    // every other block added to these words before its ticket (and a fence): plain L2 reads
-    const unsigned nbad = __ldcg(counters + 1);
-    const unsigned status = __ldcg(counters + kStatusWord);
     counters[1] = 0u;
     counters[kStatusWord] = 0u;
     *counters = 0u;  // the ticket
-    const double nll = -s_out[0] + nev * s_logN;
+    const double nll = -s_out[0] + nev * a.nrm_logN;
     // a device wait that gave up is reported as a negative event count
     const double nb = status ? -1.0 : (double)nbad;
     result[0] = nll;
     if (out_mode == 0) {
       result[1] = nb;
-      result[2 + P] = s_N;
+      result[2 + P] = a.nrm_N;
     } else {
       result[1] = 0.0;
       result[2] = nb;
     }
   }
-  result_complete(result);
+  result_complete(result, P > 1 ? P : 1);
 }
 
 template <typename T, int KB>
@@ -298,9 +274,8 @@ __device__ __forceinline__ void coh_coeffs(const CohArgs<T>& a, T (&cr)[KB + 1],
 // Direct form (one event per thread per grid-stride step); the FP64 path uses it.
 template <typename T, int KB, bool GRAD>
 __global__ void __launch_bounds__(kBlock, 2) coh_nll_kernel(const __grid_constant__ CohArgs<T> a, const void* cache_v,
-                                                            int64_t begin, int64_t end, const double* __restrict__ gram,
-                                                            float2* partials, unsigned* counters, double* result,
-                                                            int out_mode) {
+                                                            int64_t begin, int64_t end, float2* partials,
+                                                            unsigned* counters, double* result, int out_mode) {
   constexpr int NS = CohLanes<T, KB, GRAD>::NS;
   constexpr int KA = KB + 1;  // BW slots + NR slot
   __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
@@ -322,7 +297,7 @@ __global__ void __launch_bounds__(kBlock, 2) coh_nll_kernel(const __grid_constan
     ai[KB] = T(0);
     coh_event<T, KB, GRAD>(cr, ci, ar, ai, acc);
   }
-  coh_finish<T, KB, GRAD>(a, acc, begin, end, gram, partials, counters, result, out_mode, s_red, s_bad);
+  coh_finish<T, KB, GRAD>(a, acc, begin, end, partials, counters, result, out_mode, s_red, s_bad);
 }
 
 // FP32 form with the amplitude-cache tiles staged in shared memory.  A tile holds
@@ -336,9 +311,8 @@ constexpr int kCohStages = 3;
 template <int KB, bool GRAD>
 __global__ void __launch_bounds__(kStagedBlock, 1) coh_nll_staged_kernel(const __grid_constant__ CohArgs<float> a,
                                                                    const float4* __restrict__ cache, int64_t begin,
-                                                                   int64_t end, const double* __restrict__ gram,
-                                                                   float2* partials, unsigned* counters, double* result,
-                                                                   int out_mode) {
+                                                                   int64_t end, float2* partials, unsigned* counters,
+                                                                   double* result, int out_mode) {
   constexpr int NS = CohLanes<float, KB, GRAD>::NS;
   constexpr int KA = KB + 1;
   constexpr int TE = kCohTile;
@@ -440,7 +414,7 @@ __global__ void __launch_bounds__(kStagedBlock, 1) coh_nll_staged_kernel(const _
     acc.gre[k] = G1[k].x - G2[k].y;
     acc.gim[k] = G1[k].y + G2[k].x;
   }
-  coh_finish<float, KB, GRAD>(a, acc, begin, end, gram, partials, counters, result, out_mode, s_red, s_bad);
+  coh_finish<float, KB, GRAD>(a, acc, begin, end, partials, counters, result, out_mode, s_red, s_bad);
 }
 
 // per-event log f = log|S|^2 - log N
@@ -790,6 +764,10 @@ struct Td3Args {
   int64_t n_total;                   // events of the dataset (cache plane length)
   int polar;                         // the coefficient parameters are (r, phi)
   double jc[kMaxAmp], js[kMaxAmp], jr[kMaxAmp];  // cos phi, sin phi, r per amplitude (polar)
+  // the normalisation at theta, formed on the host in FP64 from the cached Gram matrices
+  // (td3_norm_terms): N, log N, (dN / d Re c_k) / N, (dN / d Im c_k) / N (tree order) and
+  // (dN / dx) / N, (dN / dy) / N, (tau dN / d tau) / N
+  double nrm_N, nrm_logN, nrm_re[kMaxAmp], nrm_im[kMaxAmp], nrm_dt[3];
 };
 
 template <bool GRAD>
@@ -801,7 +779,7 @@ template <typename T, bool GRAD>
 __global__ void __launch_bounds__(kBlock, 2)
     td3_nll_kernel(const __grid_constant__ Td3Args<T> a, const void* __restrict__ cache_a,
                    const void* __restrict__ cache_b, const T* __restrict__ tcol, int64_t begin, int64_t end,
-                   const double* __restrict__ grams, float2* partials, unsigned* counters, double* out, int out_mode) {
+                   float2* partials, unsigned* counters, double* out, int out_mode) {
   constexpr int KB = kTd3KB, KA = KB + 1;
   constexpr int NS = Td3Lanes<GRAD>::NS;
   __shared__ ddf s_red[(kBlock / 32) * NS > kBlock ? (kBlock / 32) * NS : kBlock];
@@ -931,82 +909,17 @@ __global__ void __launch_bounds__(kBlock, 2)
     if (b) atomicAdd(counters + 1, b);
   }
   if (!last_block_ticket(counters, gridDim.x)) return;
-  // The last block: its last warp forms the normalisation from the three Gram matrices
-  // (lane kk: amplitude kk in tree order) while the other threads reduce the lanes.
-  __shared__ double s_nre[kMaxAmp], s_nim[kMaxAmp], s_dt[3];
-  __shared__ int s_pre[kMaxAmp], s_pim[kMaxAmp], s_slot[kMaxAmp];
-  __shared__ double s_N, s_logN;
-  const int K = a.K;
-  if ((int)(threadIdx.x >> 5) == (int)(blockDim.x >> 5) - 1) {
-    const int kk = threadIdx.x & 31;
-    const double x = (double)a.x, y = (double)a.y, tau = 1.0 / (double)a.G;
-    const double iy = 1.0 / (1 - y * y), ix = 1.0 / (1 + x * x);
-    const double Ich = tau * iy, Ish = y * tau * iy, Ic = tau * ix, Is = x * tau * ix;
-    const double* Gaa = grams;
-    const double* Gbb = grams + 2 * K * K;
-    const double* Gab = grams + 4 * K * K;
-    auto coef = [&](int j, double& r, double& im) {
-      const int sl = j < nbw ? j : KB;
-      r = (double)a.cr[sl];
-      im = (double)a.ci[sl];
-    };
-    double var = 0, vai = 0, vbr = 0, vbi = 0, ur = 0, ui = 0, wr = 0, wi = 0, PA = 0, PB = 0, Xr = 0, Xi = 0;
-    if (kk < K) {
-      for (int l = 0; l < K; ++l) {
-        double clr, cli;
-        coef(l, clr, cli);
-        const double ar_ = Gaa[2 * (kk * K + l)], ai_ = Gaa[2 * (kk * K + l) + 1];
-        const double br_ = Gbb[2 * (kk * K + l)], bi_ = Gbb[2 * (kk * K + l) + 1];
-        const double xr_ = Gab[2 * (kk * K + l)], xi_ = Gab[2 * (kk * K + l) + 1];
-        const double yr_ = Gab[2 * (l * K + kk)], yi_ = Gab[2 * (l * K + kk) + 1];
-        var += ar_ * clr + ai_ * cli;  // G_aa[kk][l] conj(c_l)
-        vai += ai_ * clr - ar_ * cli;
-        vbr += br_ * clr + bi_ * cli;
-        vbi += bi_ * clr - br_ * cli;
-        ur += xr_ * clr + xi_ * cli;   // G_ab[kk][l] conj(c_l)
-        ui += xi_ * clr - xr_ * cli;
-        wr += clr * yr_ - cli * yi_;   // c_l G_ab[l][kk]
-        wi += clr * yi_ + cli * yr_;
-      }
-      double ckr, cki;
-      coef(kk, ckr, cki);
-      PA = ckr * var - cki * vai;  // Re(c_kk v_a)
-      PB = ckr * vbr - cki * vbi;
-      Xr = ckr * ur - cki * ui;    // c_kk u
-      Xi = ckr * ui + cki * ur;
-    }
-    for (int m = 16; m > 0; m >>= 1) {
-      PA += __shfl_xor_sync(0xffffffffu, PA, m);
-      PB += __shfl_xor_sync(0xffffffffu, PB, m);
-      Xr += __shfl_xor_sync(0xffffffffu, Xr, m);
-      Xi += __shfl_xor_sync(0xffffffffu, Xi, m);
-    }
-    const double N = 0.5 * (PA + PB) * Ich + 0.5 * (PA - PB) * Ic + Xr * Ish + Xi * Is;
-    const double invN = 1.0 / N;
-    if (kk < K) {
-      // d<|A|^2>/dRe c = 2 Re v_a, /dIm c = -2 Im v_a;  dX/dRe c = u + w, dX/dIm c = i (u - w)
-      const double dre = 0.5 * (2 * var + 2 * vbr) * Ich + 0.5 * (2 * var - 2 * vbr) * Ic + (ur + wr) * Ish +
-                         (ui + wi) * Is;
-      const double dim = 0.5 * (-2 * vai - 2 * vbi) * Ich + 0.5 * (-2 * vai + 2 * vbi) * Ic - (ui - wi) * Ish +
-                         (ur - wr) * Is;
-      s_nre[kk] = dre * invN;
-      s_nim[kk] = dim * invN;
-      s_pre[kk] = a.par_re[kk];
-      s_pim[kk] = a.par_im[kk];
-      s_slot[kk] = kk < nbw ? kk : KB;
-    }
-    if (kk == 0) {
-      s_N = N;
-      s_logN = log(N);
-      const double ix2 = ix * ix, iy2 = iy * iy;
-      const double dxc = -2 * x * tau * ix2, dxs = tau * (1 - x * x) * ix2;
-      const double dych = 2 * y * tau * iy2, dysh = tau * (1 + y * y) * iy2;
-      s_dt[0] = (0.5 * (PA - PB) * dxc + Xi * dxs) * invN;
-      s_dt[1] = (0.5 * (PA + PB) * dych + Xr * dysh) * invN;
-      s_dt[2] = (0.5 * (PA + PB) * iy + 0.5 * (PA - PB) * ix + Xr * y * iy + Xi * x * ix) * invN;
-    }
+  // The last block reduces the lanes and combines them with the normalisation terms the host
+  // formed from the three Gram matrices (they depend on theta and the MC sample only).
+  // Every other block added to the counter words before its ticket (and a fence): plain L2
+  // reads, issued before the reduction so that their latency overlaps it.
+  unsigned nbad = 0u, status = 0u;
+  if (threadIdx.x == 0) {
+    nbad = __ldcg(counters + 1);
+    status = __ldcg(counters + kStatusWord);
   }
-  reduce_partials(partials, NS, gridDim.x, s_out, s_red, blockDim.x - 32);
+  reduce_partials(partials, NS, gridDim.x, s_out, s_red, blockDim.x);
+  const int K = a.K;
   const double nev = (double)(end - begin);
   const int P = a.n_params;
   const int off = out_mode == 0 ? 2 : 3;
@@ -1014,36 +927,33 @@ __global__ void __launch_bounds__(kBlock, 2)
     double g = 0.0;
     if (GRAD) {
       for (int kk = 0; kk < K; ++kk) {
-        const int sl = s_slot[kk];
-        double gre = -s_out[1 + 2 * sl] + nev * s_nre[kk], gim = -s_out[2 + 2 * sl] + nev * s_nim[kk];
+        const int sl = kk < nbw ? kk : KB;
+        double gre = -s_out[1 + 2 * sl] + nev * a.nrm_re[kk], gim = -s_out[2 + 2 * sl] + nev * a.nrm_im[kk];
         coef_chain(a.polar, a.jc[kk], a.js[kk], a.jr[kk], gre, gim);
-        if (s_pre[kk] == p) g += gre;
-        if (s_pim[kk] == p) g += gim;
+        if (a.par_re[kk] == p) g += gre;
+        if (a.par_im[kk] == p) g += gim;
       }
       const int o = 1 + 2 * KA;
       for (int j = 0; j < 4; ++j)
-        if (a.par_t[j] == p) g += -s_out[o + j] + (j < 3 ? nev * s_dt[j] : 0.0);
+        if (a.par_t[j] == p) g += -s_out[o + j] + (j < 3 ? nev * a.nrm_dt[j] : 0.0);
     }
     out[off + p] = g;
   }
   if (threadIdx.x == 0) {
-    // every other block added to these words before its ticket (and a fence): plain L2 reads
-    const unsigned nbad = __ldcg(counters + 1);
-    const unsigned status = __ldcg(counters + kStatusWord);
     counters[1] = 0u;
     counters[kStatusWord] = 0u;
     *counters = 0u;  // the ticket
     const double nb = status ? -1.0 : (double)nbad;  // a device wait that gave up: negative count
-    out[0] = -s_out[0] + nev * s_logN;
+    out[0] = -s_out[0] + nev * a.nrm_logN;
     if (out_mode == 0) {
       out[1] = nb;
-      out[2 + P] = s_N;
+      out[2 + P] = a.nrm_N;
     } else {
       out[1] = 0.0;
       out[2] = nb;
     }
   }
-  result_complete(out);
+  result_complete(out, P > 1 ? P : 1);
 }
 
 static int dalitz_constants(goo_model* m, const double* theta) {
@@ -1217,6 +1127,33 @@ static void fill_args(const DalitzModel& d, const double* theta, int n_params, i
   fill_jacobian(d, theta, a);
 }
 
+// The normalisation at theta from the host copy of the Gram matrix (ensure_gram keeps it
+// current), in FP64 at the precision-rounded coefficients the kernel uses:
+//   v_k = sum_l G_kl conj(c_l),  N = sum_k Re(c_k v_k),  dN / d Re c_k = 2 Re v_k,
+//   dN / d Im c_k = -2 Im v_k.
+template <typename T>
+static void coh_norm_terms(const DalitzModel& d, const double* G, CohArgs<T>& a) {
+  const int K = d.K;
+  double vr[kMaxAmp], vi[kMaxAmp], N = 0.0;
+  for (int k = 0; k < K; ++k) {
+    vr[k] = vi[k] = 0.0;
+    for (int l = 0; l < K; ++l) {
+      const double gr = G[2 * (k * K + l)], gi = G[2 * (k * K + l) + 1];
+      const double clr = (double)a.cr[l], cli = (double)a.ci[l];
+      vr[k] += gr * clr + gi * cli;
+      vi[k] += gi * clr - gr * cli;
+    }
+    N += (double)a.cr[k] * vr[k] - (double)a.ci[k] * vi[k];
+  }
+  const double invN = 1.0 / N;
+  for (int k = 0; k < K; ++k) {
+    a.nrm_vr[k] = 2.0 * vr[k] * invN;
+    a.nrm_vi[k] = 2.0 * vi[k] * invN;
+  }
+  a.nrm_N = N;
+  a.nrm_logN = std::log(N);
+}
+
 constexpr int kMaxDevicesCoh = 64;
 
 template <int KB, bool GRAD>
@@ -1240,12 +1177,12 @@ static int launch_coh_staged(goo_model* m, const void* cache, const goo_dataset*
   GOO_TRY(ensure_partials(ctx, (size_t)nb * NS));
   CohArgs<float> a;
   fill_args<float>(d, theta, m->n_params, ds->n, a);
+  coh_norm_terms<float>(d, d.gram_host[pi], a);
   {
     LaunchScope ls(ctx, GRAD ? "coh_nll_grad_f32" : "coh_nll_f32");
     coh_nll_staged_kernel<KB, GRAD><<<nb, kStagedBlock, smem, ctx->stream>>>(a, (const float4*)cache, begin, end,
-                                                                       d.gram_dev[pi], ctx->scratch.partials,
-                                                                       ctx->scratch.counters, ctx->scratch.result_out,
-                                                                       out_mode);
+                                                                       ctx->scratch.partials, ctx->scratch.counters,
+                                                                       ctx->scratch.result_out, out_mode);
   }
   GOO_CUDA_TRY(cudaGetLastError());
   return GOO_OK;
@@ -1270,12 +1207,13 @@ static int launch_coh(goo_model* m, const void* cache, const goo_dataset* ds, in
   GOO_TRY(ensure_partials(ctx, (size_t)nb * NS));
   CohArgs<T> a;
   fill_args<T>(d, theta, m->n_params, ds->n, a);
+  coh_norm_terms<T>(d, d.gram_host[pi], a);
   {
     LaunchScope ls(ctx, sizeof(T) == 4 ? (GRAD ? "coh_nll_grad_f32" : "coh_nll_f32")
                                        : (GRAD ? "coh_nll_grad_f64" : "coh_nll_f64"));
-    coh_nll_kernel<T, KB, GRAD><<<nb, kBlock, 0, ctx->stream>>>(a, cache, begin, end, d.gram_dev[pi],
-                                                                ctx->scratch.partials, ctx->scratch.counters,
-                                                                ctx->scratch.result_out, out_mode);
+    coh_nll_kernel<T, KB, GRAD><<<nb, kBlock, 0, ctx->stream>>>(a, cache, begin, end, ctx->scratch.partials,
+                                                                ctx->scratch.counters, ctx->scratch.result_out,
+                                                                out_mode);
   }
   GOO_CUDA_TRY(cudaGetLastError());
   return GOO_OK;
@@ -1445,6 +1383,75 @@ static void fill_td3(const DalitzModel& d, const double* theta, int n_params, in
   fill_jacobian(d, theta, a);
 }
 
+// The normalisation at theta from the host copies of the three Gram matrices G_aa, G_bb, G_ab
+// (ensure_td_grams keeps them current), in FP64 at the precision-rounded parameters the kernel
+// uses.  With v_a = G_aa conj(c), v_b = G_bb conj(c), u = G_ab conj(c), w = c^T G_ab:
+//   <|A|^2> = Re c.v_a, <|B|^2> = Re c.v_b, <A B*> = c.u,
+//   N = (<|A|^2> + <|B|^2>)/2 I_ch + (<|A|^2> - <|B|^2>)/2 I_c + Re<AB*> I_sh + Im<AB*> I_s,
+//   d<|A|^2> / d Re c_k = 2 Re v_a,k, / d Im c_k = -2 Im v_a,k;
+//   d<AB*> / d Re c_k = u_k + w_k, / d Im c_k = i (u_k - w_k);
+// and the time integrals' derivatives for x, y and tau.
+template <typename T>
+static void td3_norm_terms(const DalitzModel& d, const double* G, Td3Args<T>& a) {
+  const int K = d.K;
+  const double* Gaa = G;
+  const double* Gbb = G + 2 * K * K;
+  const double* Gab = G + 4 * K * K;
+  auto cf = [&](int j, double& r, double& im) {
+    const int sl = j < d.nbw ? j : kTd3KB;
+    r = (double)a.cr[sl];
+    im = (double)a.ci[sl];
+  };
+  const double x = (double)a.x, y = (double)a.y, tau = 1.0 / (double)a.G;
+  const double iy = 1.0 / (1 - y * y), ix = 1.0 / (1 + x * x);
+  const double Ich = tau * iy, Ish = y * tau * iy, Ic = tau * ix, Is = x * tau * ix;
+  double var[kMaxAmp], vai[kMaxAmp], vbr[kMaxAmp], vbi[kMaxAmp], ur[kMaxAmp], ui[kMaxAmp], wr[kMaxAmp], wi[kMaxAmp];
+  double PA = 0, PB = 0, Xr = 0, Xi = 0;
+  for (int k = 0; k < K; ++k) {
+    var[k] = vai[k] = vbr[k] = vbi[k] = ur[k] = ui[k] = wr[k] = wi[k] = 0.0;
+    for (int l = 0; l < K; ++l) {
+      double clr, cli;
+      cf(l, clr, cli);
+      const double ar_ = Gaa[2 * (k * K + l)], ai_ = Gaa[2 * (k * K + l) + 1];
+      const double br_ = Gbb[2 * (k * K + l)], bi_ = Gbb[2 * (k * K + l) + 1];
+      const double xr_ = Gab[2 * (k * K + l)], xi_ = Gab[2 * (k * K + l) + 1];
+      const double yr_ = Gab[2 * (l * K + k)], yi_ = Gab[2 * (l * K + k) + 1];
+      var[k] += ar_ * clr + ai_ * cli;  // G_aa[k][l] conj(c_l)
+      vai[k] += ai_ * clr - ar_ * cli;
+      vbr[k] += br_ * clr + bi_ * cli;
+      vbi[k] += bi_ * clr - br_ * cli;
+      ur[k] += xr_ * clr + xi_ * cli;  // G_ab[k][l] conj(c_l)
+      ui[k] += xi_ * clr - xr_ * cli;
+      wr[k] += clr * yr_ - cli * yi_;  // c_l G_ab[l][k]
+      wi[k] += clr * yi_ + cli * yr_;
+    }
+    double ckr, cki;
+    cf(k, ckr, cki);
+    PA += ckr * var[k] - cki * vai[k];  // Re(c_k v_a,k)
+    PB += ckr * vbr[k] - cki * vbi[k];
+    Xr += ckr * ur[k] - cki * ui[k];  // c_k u_k (summed: <A B*>)
+    Xi += ckr * ui[k] + cki * ur[k];
+  }
+  const double N = 0.5 * (PA + PB) * Ich + 0.5 * (PA - PB) * Ic + Xr * Ish + Xi * Is;
+  const double invN = 1.0 / N;
+  for (int k = 0; k < K; ++k) {
+    const double dre = 0.5 * (2 * var[k] + 2 * vbr[k]) * Ich + 0.5 * (2 * var[k] - 2 * vbr[k]) * Ic +
+                       (ur[k] + wr[k]) * Ish + (ui[k] + wi[k]) * Is;
+    const double dim = 0.5 * (-2 * vai[k] - 2 * vbi[k]) * Ich + 0.5 * (-2 * vai[k] + 2 * vbi[k]) * Ic -
+                       (ui[k] - wi[k]) * Ish + (ur[k] - wr[k]) * Is;
+    a.nrm_re[k] = dre * invN;
+    a.nrm_im[k] = dim * invN;
+  }
+  a.nrm_N = N;
+  a.nrm_logN = std::log(N);
+  const double ix2 = ix * ix, iy2 = iy * iy;
+  const double dxc = -2 * x * tau * ix2, dxs = tau * (1 - x * x) * ix2;
+  const double dych = 2 * y * tau * iy2, dysh = tau * (1 + y * y) * iy2;
+  a.nrm_dt[0] = (0.5 * (PA - PB) * dxc + Xi * dxs) * invN;
+  a.nrm_dt[1] = (0.5 * (PA + PB) * dych + Xr * dysh) * invN;
+  a.nrm_dt[2] = (0.5 * (PA + PB) * iy + 0.5 * (PA - PB) * ix + Xr * y * iy + Xi * x * ix) * invN;
+}
+
 template <typename T, bool GRAD>
 static int launch_td3(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, const double* theta,
                       const void* ca, const void* cb, int out_mode) {
@@ -1464,13 +1471,14 @@ static int launch_td3(goo_model* m, const goo_dataset* ds, int64_t begin, int64_
   GOO_TRY(ensure_partials(ctx, (size_t)nb * NS));
   Td3Args<T> a;
   fill_td3<T>(d, theta, m->n_params, ds->n, a);
+  td3_norm_terms<T>(d, d.gram3_host[pi], a);
   const T* tcol = sizeof(T) == 4 ? (const T*)ds->d32[d.col_t] : (const T*)ds->d64[d.col_t];
   {
     LaunchScope ls(ctx, sizeof(T) == 4 ? (GRAD ? "td3_nll_grad_f32" : "td3_nll_f32")
                                        : (GRAD ? "td3_nll_grad_f64" : "td3_nll_f64"));
-    td3_nll_kernel<T, GRAD><<<nb, kBlock, 0, ctx->stream>>>(a, ca, cb, tcol, begin, end, d.gram3_dev[pi],
-                                                            ctx->scratch.partials, ctx->scratch.counters,
-                                                            ctx->scratch.result_out, out_mode);
+    td3_nll_kernel<T, GRAD><<<nb, kBlock, 0, ctx->stream>>>(a, ca, cb, tcol, begin, end, ctx->scratch.partials,
+                                                            ctx->scratch.counters, ctx->scratch.result_out,
+                                                            out_mode);
   }
   GOO_CUDA_TRY(cudaGetLastError());
   return GOO_OK;

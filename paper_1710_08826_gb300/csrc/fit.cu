@@ -23,6 +23,8 @@ namespace goo {
 
 namespace {
 
+constexpr int kFitRestarts = 3;  // returns from the Newton phase to the quasi-Newton phase
+
 struct Objective {
   goo_model* model;
   const goo_dataset* ds;
@@ -212,106 +214,9 @@ extern "C" int goo_fit(goo_model* model, const goo_dataset* ds, double* theta, c
   int it = 0;
   double edm = 0.0, best_edm = HUGE_VAL;
   int stale = 0;
-  for (; it < opt.max_iter && n > 0; ++it) {
-    for (int a = 0; a < n; ++a) {
-      double v = 0.0;
-      for (int b = 0; b < n; ++b) v -= Hinv[a * n + b] * g[b];
-      d[a] = v;
-    }
-    double gd = 0.0;
-    for (int a = 0; a < n; ++a) gd += g[a] * d[a];
-    if (!(gd < 0)) {  // not a descent direction: restart from steepest descent
-      for (int a = 0; a < n * n; ++a) Hinv[a] = 0.0;
-      for (int a = 0; a < n; ++a) {
-        Hinv[a * n + a] = 1.0;
-        d[a] = -g[a];
-      }
-      gd = 0.0;
-      for (int a = 0; a < n; ++a) gd += g[a] * d[a];
-    }
-    edm = -0.5 * gd;
-    if (edm < opt.edm_tol) {
-      status = 0;
-      break;
-    }
-    // Near the minimum the change of the NLL over a step is smaller than its rounding
-    // noise and the line search stops making progress: hand over to the Newton phase,
-    // which uses gradients only.
-    if (edm < 0.5 * best_edm) {
-      best_edm = edm;
-      stale = 0;
-    } else if (++stale >= 10 && opt.polish) {
-      break;
-    }
-    // backtracking line search on sufficient decrease.  The NLL carries rounding noise
-    // (FP32 per-event arithmetic: ~sqrt(N) 1e-7 |log f|), so the decrease test allows a
-    // tolerance proportional to |NLL|; convergence itself is decided by the EDM, which uses
-    // the (smooth) gradient.
-    const double ftol = (obj.precision == GOO_F32 ? 1e-9 : 1e-12) * std::fabs(f);
-    double alpha = 1.0, ft = 0.0;
-    bool ok = false;
-    for (int ls = 0; ls < 60; ++ls) {
-      for (int a = 0; a < n; ++a) xt[a] = x[a] + alpha * d[a];
-      bool good = obj.gradient == GOO_GRAD_ADJOINT ? obj.value_grad(xt.data(), &ft, gt.data()) : obj.value(xt.data(), &ft);
-      if (good && ft <= f + 1e-4 * alpha * gd + ftol) {
-        ok = true;
-        break;
-      }
-      // quadratic interpolation of the step, kept within [0.1, 0.5] of the last one
-      double next = 0.5 * alpha;
-      if (good) {
-        const double denom = 2.0 * (ft - f - alpha * gd);
-        if (denom > 0) next = -gd * alpha * alpha / denom;
-      }
-      alpha = std::fmin(0.5 * alpha, std::fmax(0.1 * alpha, next));
-    }
-    if (!ok) {
-      status = 2;
-      break;
-    }
-    if (obj.gradient != GOO_GRAD_ADJOINT && !obj.value_grad(xt.data(), &ft, gt.data())) {
-      status = 2;
-      break;
-    }
-    double sy = 0.0, yy = 0.0, ss = 0.0;
-    for (int a = 0; a < n; ++a) {
-      s[a] = xt[a] - x[a];
-      y[a] = gt[a] - g[a];
-      sy += s[a] * y[a];
-      yy += y[a] * y[a];
-      ss += s[a] * s[a];
-    }
-    if (it == 0 && sy > 0 && yy > 0) {  // scale the initial inverse Hessian (N&W eq. 6.20)
-      const double gam = sy / yy;
-      for (int a = 0; a < n * n; ++a) Hinv[a] *= gam;
-    }
-    if (sy > 1e-12 * std::sqrt(yy * ss)) {  // curvature condition; otherwise skip the update
-      // H <- (I - rho s y^T) H (I - rho y s^T) + rho s s^T
-      const double rho = 1.0 / sy;
-      for (int a = 0; a < n; ++a) {
-        double v = 0.0;
-        for (int b = 0; b < n; ++b) v += Hinv[a * n + b] * y[b];
-        Hy[a] = v;
-      }
-      double yHy = 0.0;
-      for (int a = 0; a < n; ++a) yHy += y[a] * Hy[a];
-      for (int a = 0; a < n; ++a)
-        for (int b = 0; b < n; ++b)
-          Hinv[a * n + b] += -rho * (Hy[a] * s[b] + s[a] * Hy[b]) + (rho * rho * yHy + rho) * s[a] * s[b];
-    }
-    if (log_level() >= 2)
-      std::fprintf(stderr, "[goo] fit it=%d f=%.10f edm=%.3e alpha=%.3e sy=%.3e\n", it, ft, edm, alpha, sy);
-    x = xt;
-    g = gt;
-    f = ft;
-  }
-  if (log_level() >= 2) std::fprintf(stderr, "[goo] fit bfgs done it=%d status=%d edm=%.3e\n", it, status, edm);
-  // Newton phase and errors from the finite-difference Hessian of the gradient.  A Newton
-  // step is accepted when it lowers the EDM computed from the gradient at the new point (the
-  // gradient is smooth where the NLL value carries rounding noise); a rejected step is
-  // halved up to three times.
+  // Newton phase state: the finite-difference Hessian of the gradient and its inverse
   std::vector<double> H, Hi;
-  bool have_h = false;
+  bool have_h = false, h_indefinite = false;
   auto edm_of = [&](const std::vector<double>& gg) {
     double e = 0.0;
     for (int a = 0; a < n; ++a)
@@ -319,108 +224,236 @@ extern "C" int goo_fit(goo_model* model, const goo_dataset* ds, double* theta, c
     return e;
   };
   const bool refine = opt.refine && opt.polish && opt.precision == GOO_F32 && opt.gradient == GOO_GRAD_ADJOINT;
-  if (n > 0 && refine) {
-    // FP64 refinement of an FP32 fit: near the minimum the FP32 gradient's rounding is no
-    // longer small against the curvature of a large sample.
-    // Newton steps with a fixed inverse Hessian on FP64 gradients, each accepted when the
-    // EDM drops; returns false if the FP64 gradient could not be evaluated at x
-    std::vector<double> dx(n);
-    auto newton = [&]() {
-      obj.precision = GOO_F64;
-      if (!obj.value_grad(x.data(), &f, g.data())) return false;
-      edm = edm_of(g);
-      for (int step = 0; step < 6 && edm >= 1e-4 * opt.edm_tol; ++step) {
+  // The quasi-Newton phase, then the Newton phase; when the latter ends short of the
+  // tolerance or on an indefinite Hessian, the quasi-Newton phase starts again from the
+  // current point with that Hessian's inverse (or, if it is indefinite, the inverse of its
+  // diagonal magnitudes), at most kFitRestarts times.  On small samples the likelihood can be
+  // far from quadratic where the quasi-Newton phase stops, and its curvature estimate poor.
+  for (int restart = 0;; ++restart) {
+    for (; it < opt.max_iter && n > 0; ++it) {
+      for (int a = 0; a < n; ++a) {
+        double v = 0.0;
+        for (int b = 0; b < n; ++b) v -= Hinv[a * n + b] * g[b];
+        d[a] = v;
+      }
+      double gd = 0.0;
+      for (int a = 0; a < n; ++a) gd += g[a] * d[a];
+      if (!(gd < 0)) {  // not a descent direction: restart from steepest descent
+        for (int a = 0; a < n * n; ++a) Hinv[a] = 0.0;
         for (int a = 0; a < n; ++a) {
-          dx[a] = 0.0;
-          for (int b = 0; b < n; ++b) dx[a] -= Hi[a * n + b] * g[b];
+          Hinv[a * n + a] = 1.0;
+          d[a] = -g[a];
         }
+        gd = 0.0;
+        for (int a = 0; a < n; ++a) gd += g[a] * d[a];
+      }
+      edm = -0.5 * gd;
+      if (edm < opt.edm_tol) {
+        status = 0;
+        break;
+      }
+      // Near the minimum the change of the NLL over a step is smaller than its rounding
+      // noise and the line search stops making progress: hand over to the Newton phase,
+      // which uses gradients only.
+      if (edm < 0.5 * best_edm) {
+        best_edm = edm;
+        stale = 0;
+      } else if (++stale >= 10 && opt.polish) {
+        break;
+      }
+      // backtracking line search on sufficient decrease.  The NLL carries rounding noise
+      // (FP32 per-event arithmetic: ~sqrt(N) 1e-7 |log f|), so the decrease test allows a
+      // tolerance proportional to |NLL|; convergence itself is decided by the EDM, which uses
+      // the (smooth) gradient.
+      const double ftol = (obj.precision == GOO_F32 ? 1e-9 : 1e-12) * std::fabs(f);
+      double alpha = 1.0, ft = 0.0;
+      bool ok = false;
+      for (int ls = 0; ls < 60; ++ls) {
+        for (int a = 0; a < n; ++a) xt[a] = x[a] + alpha * d[a];
+        bool good = obj.gradient == GOO_GRAD_ADJOINT ? obj.value_grad(xt.data(), &ft, gt.data()) : obj.value(xt.data(), &ft);
+        if (good && ft <= f + 1e-4 * alpha * gd + ftol) {
+          ok = true;
+          break;
+        }
+        // quadratic interpolation of the step, kept within [0.1, 0.5] of the last one
+        double next = 0.5 * alpha;
+        if (good) {
+          const double denom = 2.0 * (ft - f - alpha * gd);
+          if (denom > 0) next = -gd * alpha * alpha / denom;
+        }
+        alpha = std::fmin(0.5 * alpha, std::fmax(0.1 * alpha, next));
+      }
+      if (!ok) {
+        status = 2;
+        break;
+      }
+      if (obj.gradient != GOO_GRAD_ADJOINT && !obj.value_grad(xt.data(), &ft, gt.data())) {
+        status = 2;
+        break;
+      }
+      double sy = 0.0, yy = 0.0, ss = 0.0;
+      for (int a = 0; a < n; ++a) {
+        s[a] = xt[a] - x[a];
+        y[a] = gt[a] - g[a];
+        sy += s[a] * y[a];
+        yy += y[a] * y[a];
+        ss += s[a] * s[a];
+      }
+      if (it == 0 && sy > 0 && yy > 0) {  // scale the initial inverse Hessian (N&W eq. 6.20)
+        const double gam = sy / yy;
+        for (int a = 0; a < n * n; ++a) Hinv[a] *= gam;
+      }
+      if (sy > 1e-12 * std::sqrt(yy * ss)) {  // curvature condition; otherwise skip the update
+        // H <- (I - rho s y^T) H (I - rho y s^T) + rho s s^T
+        const double rho = 1.0 / sy;
+        for (int a = 0; a < n; ++a) {
+          double v = 0.0;
+          for (int b = 0; b < n; ++b) v += Hinv[a * n + b] * y[b];
+          Hy[a] = v;
+        }
+        double yHy = 0.0;
+        for (int a = 0; a < n; ++a) yHy += y[a] * Hy[a];
+        for (int a = 0; a < n; ++a)
+          for (int b = 0; b < n; ++b)
+            Hinv[a * n + b] += -rho * (Hy[a] * s[b] + s[a] * Hy[b]) + (rho * rho * yHy + rho) * s[a] * s[b];
+      }
+      if (log_level() >= 2)
+        std::fprintf(stderr, "[goo] fit it=%d f=%.10f edm=%.3e alpha=%.3e sy=%.3e\n", it, ft, edm, alpha, sy);
+      x = xt;
+      g = gt;
+      f = ft;
+    }
+    if (log_level() >= 2) std::fprintf(stderr, "[goo] fit bfgs done it=%d status=%d edm=%.3e\n", it, status, edm);
+    // Newton phase and errors from the finite-difference Hessian of the gradient.  A Newton
+    // step is accepted when it lowers the EDM computed from the gradient at the new point (the
+    // gradient is smooth where the NLL value carries rounding noise); a rejected step is
+    // halved up to three times.
+    if (n > 0 && refine) {
+      // FP64 refinement of an FP32 fit: near the minimum the FP32 gradient's rounding is no
+      // longer small against the curvature of a large sample.
+      // Newton steps with a fixed inverse Hessian on FP64 gradients, each accepted when the
+      // EDM drops; returns false if the FP64 gradient could not be evaluated at x
+      std::vector<double> dx(n);
+      auto newton = [&]() {
+        obj.precision = GOO_F64;
+        if (!obj.value_grad(x.data(), &f, g.data())) return false;
+        edm = edm_of(g);
+        for (int step = 0; step < 6 && edm >= 1e-4 * opt.edm_tol; ++step) {
+          for (int a = 0; a < n; ++a) {
+            dx[a] = 0.0;
+            for (int b = 0; b < n; ++b) dx[a] -= Hi[a * n + b] * g[b];
+          }
+          bool moved = false;
+          for (double t = 1.0; t >= 0.125; t *= 0.5) {
+            for (int a = 0; a < n; ++a) xt[a] = x[a] + t * dx[a];
+            double ft;
+            if (!obj.value_grad(xt.data(), &ft, gt.data())) continue;
+            const double e = edm_of(gt);
+            if (e < edm) {
+              x = xt;
+              g = gt;
+              f = ft;
+              edm = e;
+              moved = true;
+              break;
+            }
+          }
+          if (log_level() >= 2) std::fprintf(stderr, "[goo] fit refine step=%d edm=%.3e moved=%d\n", step, edm, (int)moved);
+          if (!moved) break;
+        }
+        return true;
+      };
+      // the Hessian from FP32 gradients when it is positive definite, else (or when the steps
+      // stall above the tolerance) from FP64 gradients.  The FP32 differences step a quarter of
+      // each parameter's error as BFGS estimates it (at least 1e-3): on a large sample the error
+      // is small, and a fixed step would leave the gradient change within the FP32 rounding.
+      std::vector<double> hsteps(n);
+      for (int a = 0; a < n; ++a) hsteps[a] = std::fmax(1e-3, 0.25 * std::sqrt(std::fmax(Hinv[a * n + a], 0.0)));
+      obj.precision = opt.precision;
+      bool pd = hessian(obj, x, H, &hsteps) && positive_definite(n, H) && invert(n, H, Hi);
+      bool h64 = false;
+      if (!pd) {
+        obj.precision = GOO_F64;
+        pd = hessian(obj, x, H) && positive_definite(n, H) && invert(n, H, Hi);
+        h64 = true;
+      }
+      if (pd && newton()) {
+        have_h = true;
+        if (edm >= opt.edm_tol && !h64) {
+          obj.precision = GOO_F64;
+          if (hessian(obj, x, H) && positive_definite(n, H) && invert(n, H, Hi)) {
+            h64 = true;
+            newton();
+          }
+        }
+        // errors (and the final EDM) from the Hessian at the minimum: FP32 gradients when that
+        // Hessian is positive definite (with the fixed step, else the error-scaled steps), else
+        // FP64 ones
+        std::vector<double> H2, Hi2;
+        obj.precision = opt.precision;
+        bool pd2 = hessian(obj, x, H2) && positive_definite(n, H2);
+        if (!pd2) pd2 = hessian(obj, x, H2, &hsteps) && positive_definite(n, H2);
+        obj.precision = GOO_F64;
+        if (!pd2) pd2 = hessian(obj, x, H2) && positive_definite(n, H2);
+        if (pd2 && invert(n, H2, Hi2)) {
+          Hi = Hi2;
+          edm = edm_of(g);
+        }
+      }
+      obj.precision = opt.precision;
+      break;  // no restarts in the refinement
+    }
+    if (!(n > 0 && (opt.polish || errors_out))) break;
+    {
+      bool indefinite = false;
+      for (int pass = 0; pass < (opt.polish ? 6 : 1); ++pass) {
+        if (!hessian(obj, x, H)) break;
+        have_h = invert(n, H, Hi);
+        if (!have_h) break;
+        edm = edm_of(g);
+        if (!opt.polish || (edm >= 0 && edm < 1e-4 * opt.edm_tol)) break;
+        if (!positive_definite(n, H)) {  // a Newton step could head for a saddle: restart instead
+          indefinite = true;
+          break;
+        }
+        std::vector<double> dx(n, 0.0);
+        for (int a = 0; a < n; ++a)
+          for (int b = 0; b < n; ++b) dx[a] -= Hi[a * n + b] * g[b];
         bool moved = false;
         for (double t = 1.0; t >= 0.125; t *= 0.5) {
           for (int a = 0; a < n; ++a) xt[a] = x[a] + t * dx[a];
           double ft;
           if (!obj.value_grad(xt.data(), &ft, gt.data())) continue;
-          const double e = edm_of(gt);
-          if (e < edm) {
+          if (edm_of(gt) < edm) {
             x = xt;
             g = gt;
             f = ft;
-            edm = e;
             moved = true;
             break;
           }
         }
-        if (log_level() >= 2) std::fprintf(stderr, "[goo] fit refine step=%d edm=%.3e moved=%d\n", step, edm, (int)moved);
+        if (log_level() >= 2) std::fprintf(stderr, "[goo] fit newton pass=%d edm=%.3e moved=%d\n", pass, edm, (int)moved);
         if (!moved) break;
       }
-      return true;
-    };
-    // the Hessian from FP32 gradients when it is positive definite, else (or when the steps
-    // stall above the tolerance) from FP64 gradients.  The FP32 differences step a quarter of
-    // each parameter's error as BFGS estimates it (at least 1e-3): on a large sample the error
-    // is small, and a fixed step would leave the gradient change within the FP32 rounding.
-    std::vector<double> hsteps(n);
-    for (int a = 0; a < n; ++a) hsteps[a] = std::fmax(1e-3, 0.25 * std::sqrt(std::fmax(Hinv[a * n + a], 0.0)));
-    obj.precision = opt.precision;
-    bool pd = hessian(obj, x, H, &hsteps) && positive_definite(n, H) && invert(n, H, Hi);
-    bool h64 = false;
-    if (!pd) {
-      obj.precision = GOO_F64;
-      pd = hessian(obj, x, H) && positive_definite(n, H) && invert(n, H, Hi);
-      h64 = true;
-    }
-    if (pd && newton()) {
-      have_h = true;
-      if (edm >= opt.edm_tol && !h64) {
-        obj.precision = GOO_F64;
-        if (hessian(obj, x, H) && positive_definite(n, H) && invert(n, H, Hi)) {
-          h64 = true;
-          newton();
-        }
+      if (have_h && opt.polish && !indefinite && hessian(obj, x, H) && invert(n, H, Hi)) edm = edm_of(g);  // at the final point
+      const bool pd = H.size() == (size_t)n * n && positive_definite(n, H);
+      if (opt.polish) h_indefinite = have_h && !pd;
+      if (!opt.polish || restart >= kFitRestarts || H.size() != (size_t)n * n || (pd && edm >= 0 && edm < opt.edm_tol))
+        break;
+      if (log_level() >= 2) std::fprintf(stderr, "[goo] fit restart=%d edm=%.3e pd=%d\n", restart + 1, edm, (int)pd);
+      if (pd && have_h) {
+        Hinv = Hi;
+      } else {
+        for (int a = 0; a < n * n; ++a) Hinv[a] = 0.0;
+        for (int a = 0; a < n; ++a) Hinv[a * n + a] = 1.0 / std::fmax(std::fabs(H[a * n + a]), 1e-12);
       }
-      // errors (and the final EDM) from the Hessian at the minimum: FP32 gradients when that
-      // Hessian is positive definite (with the fixed step, else the error-scaled steps), else
-      // FP64 ones
-      std::vector<double> H2, Hi2;
-      obj.precision = opt.precision;
-      bool pd2 = hessian(obj, x, H2) && positive_definite(n, H2);
-      if (!pd2) pd2 = hessian(obj, x, H2, &hsteps) && positive_definite(n, H2);
-      obj.precision = GOO_F64;
-      if (!pd2) pd2 = hessian(obj, x, H2) && positive_definite(n, H2);
-      if (pd2 && invert(n, H2, Hi2)) {
-        Hi = Hi2;
-        edm = edm_of(g);
-      }
+      best_edm = HUGE_VAL;
+      stale = 0;
+      status = 1;
+      if (it >= opt.max_iter) break;  // no quasi-Newton iterations left
     }
-    obj.precision = opt.precision;
-  } else if (n > 0 && (opt.polish || errors_out)) {
-    for (int pass = 0; pass < (opt.polish ? 6 : 1); ++pass) {
-      if (!hessian(obj, x, H)) break;
-      have_h = invert(n, H, Hi);
-      if (!have_h) break;
-      edm = edm_of(g);
-      if (!opt.polish || edm < 1e-4 * opt.edm_tol) break;
-      std::vector<double> dx(n, 0.0);
-      for (int a = 0; a < n; ++a)
-        for (int b = 0; b < n; ++b) dx[a] -= Hi[a * n + b] * g[b];
-      bool moved = false;
-      for (double t = 1.0; t >= 0.125; t *= 0.5) {
-        for (int a = 0; a < n; ++a) xt[a] = x[a] + t * dx[a];
-        double ft;
-        if (!obj.value_grad(xt.data(), &ft, gt.data())) continue;
-        if (edm_of(gt) < edm) {
-          x = xt;
-          g = gt;
-          f = ft;
-          moved = true;
-          break;
-        }
-      }
-      if (log_level() >= 2) std::fprintf(stderr, "[goo] fit newton pass=%d edm=%.3e moved=%d\n", pass, edm, (int)moved);
-      if (!moved) break;
-    }
-    if (have_h && opt.polish && hessian(obj, x, H) && invert(n, H, Hi)) edm = edm_of(g);  // at the final point
   }
-  if (n > 0 && have_h && edm < 0) status = 3;  // the final Hessian is not positive definite
+  if (n > 0 && have_h && (edm < 0 || h_indefinite)) status = 3;  // the final Hessian is not positive definite
   else if (n > 0 && edm < opt.edm_tol) status = 0;
   else if (status == 0) status = 1;
   obj.to_theta(x.data());

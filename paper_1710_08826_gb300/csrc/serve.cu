@@ -547,7 +547,7 @@ enum SrvPhase { PH_FREE = 0, PH_START = 1, PH_LINE = 2, PH_HESS = 3, PH_NEWTON =
 struct SrvState {
   int phase, P, it, ls, hj, newton, status, evals;
   double f, ft, alpha, gd, edm, best_edm, ftol_rel;
-  int stale, pad;
+  int stale, restarts;
   double x[kSrvMaxP], g[kSrvMaxP], d[kSrvMaxP], xt[kSrvMaxP], gt[kSrvMaxP];
   double Hi[kSrvMaxP * kSrvMaxP];   // BFGS inverse Hessian, then inverse FD Hessian
   double Hf[kSrvMaxP * kSrvMaxP];   // FD Hessian under construction
@@ -614,6 +614,24 @@ __device__ bool srv_invert(double* A, double* inv, int n) {
   return true;
 }
 
+// Cholesky factorisation of a copy of the symmetric n x n matrix A: true if every pivot is
+// positive (A positive definite).
+__device__ bool srv_positive_definite(const double* A, int n) {
+  double L[kSrvMaxP * kSrvMaxP];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double v = A[i * n + j];
+      for (int k = 0; k < j; ++k) v -= L[i * n + k] * L[j * n + k];
+      if (i == j) {
+        if (!(v > 0)) return false;
+        L[i * n + i] = sqrt(v);
+      } else {
+        L[i * n + j] = v / L[j * n + j];
+      }
+    }
+  return true;
+}
+
 __device__ double srv_edm(const SrvState& s, const double* g) {
   double e = 0.0;
   for (int a = 0; a < s.P; ++a)
@@ -622,6 +640,7 @@ __device__ double srv_edm(const SrvState& s, const double* g) {
 }
 
 constexpr double kHessStep = 1e-3;  // finite-difference step in units of the parameter scale
+constexpr int kSrvRestarts = 3;     // returns from the Newton phase to the quasi-Newton phase
 
 __device__ void srv_begin_hessian(SrvState& s, const SrvParams& sp, SrvEval& e) {
   s.phase = PH_HESS;
@@ -670,6 +689,26 @@ __device__ void srv_propose(SrvState& s, const SrvParams& sp, SrvEval& e) {
   for (int a = 0; a < P; ++a) xt[a] = s.x[a] + s.alpha * s.d[a];
   srv_set_trial(s, sp, e, xt);
   s.phase = PH_LINE;
+}
+
+// Back to the quasi-Newton phase from the current point, its inverse Hessian the inverse of
+// the finite-difference Hessian where that is positive definite, else the inverse of its
+// diagonal magnitudes.  Used when the Newton phase finds the Hessian indefinite or its steps
+// stall (a step that does not lower the EDM, or four steps short of the tolerance): on small
+// samples the likelihood can be far from quadratic where the quasi-Newton phase stopped, its
+// curvature estimate having put the EDM under the tolerance too early.
+__device__ void srv_restart(SrvState& s, const SrvParams& sp, SrvEval& e, bool pd) {
+  const int P = s.P;
+  if (!pd)
+    for (int a = 0; a < P; ++a)
+      for (int b = 0; b < P; ++b)
+        s.Hi[a * P + b] = (a == b) ? 1.0 / fmax(fabs(s.Hf[a * P + a]), 1e-12) : 0.0;
+  s.restarts++;
+  s.newton = 0;
+  s.best_edm = HUGE_VAL;
+  s.stale = 0;
+  s.status = 0;
+  srv_propose(s, sp, e);
 }
 
 __global__ void srv_bfgs_kernel(SrvState* states, SrvEval* evals, const SrvResult* results, const SrvParams* spp,
@@ -792,7 +831,12 @@ __global__ void srv_bfgs_kernel(SrvState* states, SrvEval* evals, const SrvResul
         }
       double A[kSrvMaxP * kSrvMaxP];
       for (int a = 0; a < P * P; ++a) A[a] = s.Hf[a];
+      const bool pd = srv_positive_definite(s.Hf, P);
       if (!srv_invert(A, s.Hi, P)) {
+        if (s.restarts < kSrvRestarts) {
+          srv_restart(s, sp, e, false);
+          break;
+        }
         s.status = 4;
         s.phase = PH_DONE;
         break;
@@ -802,8 +846,17 @@ __global__ void srv_bfgs_kernel(SrvState* states, SrvEval* evals, const SrvResul
         const double v = s.Hi[a * P + a];
         s.err[a] = v > 0 ? sqrt(v) * sp.scale[a] : NAN;
       }
-      if (s.edm < sp.edm_tol || s.newton >= 4) {
-        s.status = (s.edm < sp.edm_tol) ? 0 : 1;
+      if (s.edm < sp.edm_tol && pd) {
+        s.status = 0;
+        s.phase = PH_DONE;
+        break;
+      }
+      if (s.restarts < kSrvRestarts && (!pd || s.newton >= 4)) {
+        srv_restart(s, sp, e, pd);
+        break;
+      }
+      if (s.edm < sp.edm_tol || s.newton >= 4 || !pd) {
+        s.status = !pd ? 3 : (s.edm < sp.edm_tol) ? 0 : 1;
         s.phase = PH_DONE;
         break;
       }
@@ -835,6 +888,8 @@ __global__ void srv_bfgs_kernel(SrvState* states, SrvEval* evals, const SrvResul
         double xt[kSrvMaxP];
         for (int a = 0; a < P; ++a) xt[a] = s.x[a] + s.alpha * s.d[a];
         srv_set_trial(s, sp, e, xt);
+      } else if (s.restarts < kSrvRestarts) {
+        srv_restart(s, sp, e, true);  // the Newton phase was entered with a positive-definite Hessian
       } else {
         s.status = 1;
         s.phase = PH_DONE;
