@@ -41,35 +41,36 @@ _TD3_SRC = _COH_SRC + ['paper_1710_08826_gb300/csrc/timeterms.cuh']
 ISSUE_PEAK = 152 * 4 * 2.07e9
 
 NCU_RECORDS = {
-    "sop_nll_grad_f32": {"bytes": 126_027_776, "events": 10_000_000, "warp_inst": 29_148_206, "issue_active": 0.4692,
-                         "sources": _SOP_SRC,
-                         "sha256": "774529ae45f97a2caa51d78f986f0679f26a869c940a5b39fd5cba0470d0089a",
-                         "profile": "profiles/sop_event2_kernel_f32_c2_10M.md"},
-    "sop_nll_f64": {"bytes": 243_409_920, "events": 10_000_000, "fp64_pipe": 0.8625, "sources": _SOP_SRC,
-                    "sha256": "774529ae45f97a2caa51d78f986f0679f26a869c940a5b39fd5cba0470d0089a",
-                    "profile": "profiles/sop_event_kernel_f64_c2_10M.md"},
-    "coh_nll_grad_f32": {"bytes": 323_350_784, "events": 5_000_000, "sources": _COH_SRC,
-                         "sha256": "d630025ad63b1bf75cd08f8b75c5dd9fa0cf90fa90f07116bc0aa3c44ed92126",
-                         "profile": "profiles/coh_nll_staged_kernel_f32_c3_5M.md"},
-    "coh_nll_f64": {"bytes": 643_376_128, "events": 5_000_000, "fp64_pipe": 0.87, "sources": _COH_SRC,
-                    "sha256": "d630025ad63b1bf75cd08f8b75c5dd9fa0cf90fa90f07116bc0aa3c44ed92126",
-                    "profile": "profiles/coh_nll_kernel_f64_c3_5M.md"},
-    "coh_ls_grad_f32": {"bytes": 40_096_000, "events": 5_000_000, "warp_inst": 313_731_120, "issue_active": 0.6438,
-                        "sources": _COH_SRC,
-                        "sha256": "d630025ad63b1bf75cd08f8b75c5dd9fa0cf90fa90f07116bc0aa3c44ed92126",
-                        "profile": "profiles/coh_ls_kernel_f32_c3_floating_5M.md"},
-    "td3_nll_grad_f32": {"bytes": 524_228_608, "events": 2_000_000, "sources": _TD3_SRC,
-                         "sha256": "3fd4b324cd55da187ae13132a503cf027b818697f28a417fb898708e2f694dd0",
-                         "profile": "profiles/td3_nll_kernel_td3_2M.md"},
-    "td3_nll_f64": {"bytes": 979_578_880, "events": 2_000_000, "fp64_pipe": 0.8637, "sources": _TD3_SRC,
-                    "sha256": "3fd4b324cd55da187ae13132a503cf027b818697f28a417fb898708e2f694dd0",
-                    "profile": "profiles/td3_nll_kernel_td3_2M.md"},
-    "td4_nll_grad_f32": {"bytes": 171_327_232, "events": 2_000_000, "sources": _TD4_SRC,
-                         "sha256": "d4b7fe00f9c26703c33ae7dcdd5025d43125aba1871d08e83bd7cbe17d398041",
-                         "profile": "profiles/td4_nll_f32_kernel_c4_2M.md"},
-    "td4_nll_f64": {"bytes": 339_682_304, "events": 2_000_000, "fp64_pipe": 0.8662, "sources": _TD4_SRC,
-                    "sha256": "d4b7fe00f9c26703c33ae7dcdd5025d43125aba1871d08e83bd7cbe17d398041",
-                    "profile": "profiles/td4_nll_f64_kernel_c4_2M.md"},
+    "sop_nll_grad_f32": {"bytes": 125_557_760, "events": 10_000_000, "duration_ns": 55872, "warp_inst": 26_261_938, "issue_active": 0.4822,
+        "sources": _SOP_SRC, "sha256": "25d6802fce0adacc336fbafd30d882f18e43b1bd7eff1bc7407d51e0bfe3a3c7",
+        "profile": "profiles/sop_event2_kernel_f32_c2_10M.md"},
+    "sop_nll_f64": {"bytes": 243_042_816, "events": 10_000_000, "duration_ns": 2503616, "fp64_pipe": 0.8625, "fp64_ops": {"dfma": 649_995_818, "dadd": 340_076_104, "dmul": 259_998_770},
+        "sources": _SOP_SRC, "sha256": "25d6802fce0adacc336fbafd30d882f18e43b1bd7eff1bc7407d51e0bfe3a3c7",
+        "profile": "profiles/sop_event_kernel_f64_c2_10M.md"},
+    "coh_nll_grad_f32": {"bytes": 323_033_856, "events": 5_000_000, "duration_ns": 63840, "warp_inst": 30_973_750, "issue_active": 0.4608,
+        "sources": _COH_SRC, "sha256": "44de0bf6ca446d02ea5320c8459f10e11da1e54aac21e956a9277241b762bca7",
+        "profile": "profiles/coh_nll_staged_kernel_f32_c3_5M.md"},
+    "coh_nll_f64": {"bytes": 643_046_400, "events": 5_000_000, "duration_ns": 774336, "fp64_pipe": 0.8700, "fp64_ops": {"dfma": 165_155_649, "dadd": 135_077_825, "dmul": 105_000_000},
+        "sources": _COH_SRC, "sha256": "44de0bf6ca446d02ea5320c8459f10e11da1e54aac21e956a9277241b762bca7",
+        "profile": "profiles/coh_nll_kernel_f64_c3_5M.md"},
+    "coh_ls_mc_f32": {"bytes": 8_068_608, "events": 1_000_000, "duration_ns": 91648, "warp_inst": 65_044_091, "issue_active": 0.6340,
+        "sources": _COH_SRC, "sha256": "44de0bf6ca446d02ea5320c8459f10e11da1e54aac21e956a9277241b762bca7",
+        "profile": "profiles/coh_ls_kernel_f32_c3_floating_5M.md"},
+    "coh_ls_grad_f32": {"bytes": 40_095_744, "events": 5_000_000, "duration_ns": 421792, "warp_inst": 313_731_120, "issue_active": 0.6443,
+        "sources": _COH_SRC, "sha256": "44de0bf6ca446d02ea5320c8459f10e11da1e54aac21e956a9277241b762bca7",
+        "profile": "profiles/coh_ls_kernel_f32_c3_floating_5M.md"},
+    "td3_nll_grad_f32": {"bytes": 523_854_848, "events": 2_000_000, "duration_ns": 137152, "warp_inst": 71_326_620, "issue_active": 0.5432,
+        "sources": _TD3_SRC, "sha256": "6141299a22322a973a71749f03539f67262e2e1dabca0d35315b8c929a196f3f",
+        "profile": "profiles/td3_nll_kernel_td3_2M.md"},
+    "td3_nll_f64": {"bytes": 979_082_240, "events": 2_000_000, "duration_ns": 1611488, "fp64_pipe": 0.8524, "fp64_ops": {"dfma": 391_298_265, "dadd": 152_090_307, "dmul": 214_414_797},
+        "sources": _TD3_SRC, "sha256": "6141299a22322a973a71749f03539f67262e2e1dabca0d35315b8c929a196f3f",
+        "profile": "profiles/td3_nll_kernel_td3_2M.md"},
+    "td4_nll_grad_f32": {"bytes": 171_076_352, "events": 2_000_000, "duration_ns": 74272, "warp_inst": 50_891_205, "issue_active": 0.6650,
+        "sources": _TD4_SRC, "sha256": "e75012745e4fd8298ff111bc229eeed002f221cb0c6402bed4714ad6f38e6afc",
+        "profile": "profiles/td4_nll_f32_kernel_c4_2M.md"},
+    "td4_nll_f64": {"bytes": 339_331_072, "events": 2_000_000, "duration_ns": 1387424, "fp64_pipe": 0.8560, "fp64_ops": {"dfma": 351_287_209, "dadd": 112_088_842, "dmul": 178_181_349},
+        "sources": _TD4_SRC, "sha256": "e75012745e4fd8298ff111bc229eeed002f221cb0c6402bed4714ad6f38e6afc",
+        "profile": "profiles/td4_nll_f64_kernel_c4_2M.md"},
 }
 
 
@@ -106,10 +107,14 @@ def fp64_roofline(kernel, n_events, kernel_ms, fma64_per_s):
     ops = rec["fp64_ops"]
     scale = n_events / rec["events"]
     flops = (2.0 * ops["dfma"] + ops["dadd"] + ops["dmul"]) * scale
+    insts = (ops["dfma"] + ops["dadd"] + ops["dmul"]) * scale
     achieved = flops / (kernel_ms * 1e-3)
     peak = 2.0 * fma64_per_s
+    # a DADD or DMUL takes an FP64 issue slot as a DFMA does but counts one operation: the
+    # instruction rate against the FMA rate says how full the pipe's arithmetic slots are
     return {"bound": "fp64", "flops_per_launch": flops, "achieved_flops": achieved, "peak_flops": peak,
-            "flops_frac": achieved / peak, "fp64_pipe_active": rec.get("fp64_pipe"),
+            "flops_frac": achieved / peak, "fp64_inst_frac": insts / (kernel_ms * 1e-3) / fma64_per_s,
+            "fp64_pipe_active": rec.get("fp64_pipe"),
             "counts_per_launch": {k: v * scale for k, v in ops.items()},
             "peak_source": "goo_peak_fma (fma.rn.f64 chains on every SM), measured in this run",
             "profile": rec["profile"]}

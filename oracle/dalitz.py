@@ -196,14 +196,6 @@ class DalitzModel:
             A = self.amplitude_matrix(mc_cols, theta)
             return (A.T @ A.conj()) / A.shape[0]
 
-    def fit_fractions(self, mc_cols, theta):
-        with torch.no_grad():
-            th = torch.as_tensor(theta, dtype=torch.float64)
-            G = self.gram(mc_cols, th)
-            c = self.coefficients(th)
-            tot = (c @ G @ c.conj()).real
-            return [float((c[k] * c[k].conj() * G[k, k]).real / tot) for k in range(len(c))]
-
 
 def max_intensity_scan(model, theta, n=400):
     """Largest |S|^2 over an n x n grid of the physical region (for accept--reject envelopes)."""

@@ -35,12 +35,3 @@ def philox4x64(counter, key, rounds=10):
         c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
     return c0, c1, c2, c3
 
-
-def uniform53(word):
-    return (int(word) >> 11) * (1.0 / (1 << 53))
-
-
-def toy_uniforms(seed, j):
-    """(u12, u13, u_accept) for candidate j of the toy with this seed."""
-    w = philox4x64((j, 0, 0, 0), (seed, TOY_KEY1))
-    return uniform53(w[0]), uniform53(w[1]), uniform53(w[2])
