@@ -500,8 +500,10 @@ int goo_peak_fma(goo_ctx* ctx, int kind, int iters, double* fma_per_s, double* m
  * its counters first; the array keeps the previous call's contents otherwise.  Calls that
  * overlap on the GPU (different streams or host threads, same device) race on the array:
  * serialise them.  The call copies the model block in and the result out on cuda_stream and
- * synchronises that stream before it returns.  GOO_ERR_NONPOSITIVE_PDF and
- * GOO_ERR_TIMEOUT as for goo_nll_grad (nll_out = +inf, grad_out zeroed). */
+ * synchronises that stream before it returns, so it cannot be captured in a CUDA graph (both
+ * the copies from pageable host memory and the synchronisation are refused during a stream
+ * capture).  GOO_ERR_NONPOSITIVE_PDF and GOO_ERR_TIMEOUT as for goo_nll_grad (nll_out = +inf,
+ * grad_out zeroed). */
 int goo_nll_grad_static(const goo_node* nodes, int n_nodes, int n_params, int n_obs, const double* obs_lo,
                         const double* obs_hi, const goo_norm_spec* norm, const void* const* cols_dev,
                         int precision, int64_t n_events, const double* theta, void* cuda_stream,
