@@ -250,6 +250,26 @@ __device__ __forceinline__ ddf dd_warp_sum(ddf v) {
   return v;
 }
 
+// Warp sums of four double-float values at once by an exchanging butterfly: at the first two
+// levels each lane keeps half of its quantities and sends the other half, so a lane performs
+// six additions instead of twenty.  Afterwards lanes 8q .. 8q + 7 hold the sum of a[q]
+// (q = 0..3).  Fixed order, so bitwise repeatable.
+__device__ __forceinline__ ddf dd_warp_sum4(const ddf (&a)[4]) {
+  const int lane = threadIdx.x & 31;
+  const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0;
+  // level 16: the lower half keeps quantities 0 and 1, the upper half 2 and 3
+  ddf k0 = h16 ? a[2] : a[0], k1 = h16 ? a[3] : a[1];
+  const ddf s0 = h16 ? a[0] : a[2], s1 = h16 ? a[1] : a[3];
+  k0 = dd_add(k0, dd_shfl_xor(s0, 16));
+  k1 = dd_add(k1, dd_shfl_xor(s1, 16));
+  // level 8: lanes with bit 3 clear keep the first of the two
+  ddf k = h8 ? k1 : k0;
+  k = dd_add(k, dd_shfl_xor(h8 ? k0 : k1, 8));
+#pragma unroll
+  for (int m = 4; m > 0; m >>= 1) k = dd_add(k, dd_shfl_xor(k, m));
+  return k;
+}
+
 // Natural logarithm of a positive double-float as a double-float, in FP32 arithmetic: the
 // exponent is split off exactly, x.hi = m 2^e with m in [sqrt(1/2), sqrt(2)), so that
 // log x = e ln 2 + log m + log(1 + x.lo / x.hi) with |log m| < 0.35; logf(m) is within one

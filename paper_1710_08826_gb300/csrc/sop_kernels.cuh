@@ -688,42 +688,66 @@ __device__ __forceinline__ void grid_coord(const GridDev& G, int d, int64_t idx,
 // its own observable, log N_k = sum_l [log(h_l S_l) + a_l] with one 1-D midpoint sum S_l per
 // leaf (as grid_sep_kernel computes it), a few hundred leaf evaluations in all; every block
 // evaluates them itself at its start instead of waiting for a normalisation kernel, from
-// by-value constants only.  Warp w takes leaf slots w, w + 8, ...; its lanes stride the bins
-// in a fixed order, accumulate in double-float (exact products by fma) and reduce by a fixed
-// shuffle tree, so every block obtains bit-identical sums s_raw[k L + l] = {S, D_1, D_2, D_3}
-// (D_j = sum of U d log(leaf) / d c_j).  Only the offsets -log N_k are needed before the
+// by-value constants only.  Leaf slot sl goes to warp 7 - sl mod 8 (warp 0 issues the block's
+// first tile copies meanwhile); its lanes take the bins in a fixed order, kGridIlp at a time
+// evaluated independently and added in bin order, accumulate in double-float (exact products by fma) and reduce by a fixed
+// exchanging butterfly, so every block obtains bit-identical sums s_raw[k L + l] =
+// {S, D_1, D_2, D_3} (D_j = sum of U d log(leaf) / d c_j).  Only the offsets -log N_k are needed before the
 // events: one lane per product forms them in FP32 arithmetic (log_dd).  The ratios D_j / S
 // that the gradient needs are formed by the last block alone (event_finish_fused), so that
 // the prologue every block pays holds no FP64 arithmetic (GB300's FP64 pipe is 1/64 of FP32
 // and its latency dominated this step).
+// Bins of one leaf evaluated independently per step of the prologue's loop (their latencies
+// overlap; the sums still run in bin order).
+constexpr int kGridIlp = 4;
+
 template <int K, int L, bool GRAD>
 __device__ __forceinline__ void fused_grid_norm(const EvConst<float, K, L>& P, const EvNorm<K, L, GRAD>& N,
                                                 ddf (*s_raw)[4], float (*s_off)[2], float (&off_hi)[K],
                                                 float (&off_lo)[K]) {
+  constexpr int NW = kBlock / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // one copy of the loop for every warp (a run-time slot index; the slot's constants are
+  // selected from the parameter bank), so that the warps share its instructions
+#pragma unroll 1
+  for (int sl = NW - 1 - warp; sl < K * L; sl += NW) {
+    const int nb = N.nb[sl];
+    if (nb == 0) continue;
+    LeafReg<float> lr = P.leaf[0][0];
 #pragma unroll
-  for (int sl = 0; sl < K * L; ++sl) {
-    if (sl % (kBlock / 32) != warp || N.nb[sl] == 0) continue;  // uniform over the warp
-    const LeafReg<float>& lr = P.leaf[sl / L][sl % L];
+    for (int t = 1; t < K * L; ++t)
+      if (t == sl) lr = P.leaf[t / L][t % L];
     const float aref = N.aref_hi[sl], aref_lo = N.aref_lo[sl];
+    const float lo_hi = N.lo_hi[sl], lo_lo = N.lo_lo[sl], h_hi = N.h_hi[sl], h_lo = N.h_lo[sl];
     ddf acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    for (int i = lane; i < N.nb[sl]; i += 32) {
-      float x, xlo, r, a, dl[3];
-      grid_coord_f(N.lo_hi[sl], N.lo_lo[sl], N.h_hi[sl], N.h_lo[sl], i, x, xlo);
-      leaf_eval<true, true>(lr, x, r, a, dl, xlo);
-      const float U = r * expf((a - aref) - aref_lo);
-      acc[0] = dd_add(acc[0], ddf{U, 0.f});
+    for (int i0 = 0; i0 < nb; i0 += 32 * kGridIlp) {
+      float U[kGridIlp], D[kGridIlp][3];
 #pragma unroll
-      for (int jj = 0; jj < 3; ++jj) {
-        const float pr = U * dl[jj];
-        acc[1 + jj] = dd_add(acc[1 + jj], ddf{pr, fmaf(U, dl[jj], -pr)});
+      for (int u = 0; u < kGridIlp; ++u) {
+        const int i = i0 + 32 * u + lane;
+        U[u] = D[u][0] = D[u][1] = D[u][2] = 0.f;
+        if (i < nb) {
+          float x, xlo, r, a, dl[3];
+          grid_coord_f(lo_hi, lo_lo, h_hi, h_lo, i, x, xlo);
+          leaf_eval<true, true>(lr, x, r, a, dl, xlo);
+          U[u] = r * expf((a - aref) - aref_lo);
+#pragma unroll
+          for (int jj = 0; jj < 3; ++jj) D[u][jj] = dl[jj];
+        }
+      }
+      // in bin order (an absent bin adds an exact zero)
+#pragma unroll
+      for (int u = 0; u < kGridIlp; ++u) {
+        acc[0] = dd_add(acc[0], ddf{U[u], 0.f});
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+          const float pr = U[u] * D[u][jj];
+          acc[1 + jj] = dd_add(acc[1 + jj], ddf{pr, fmaf(U[u], D[u][jj], -pr)});
+        }
       }
     }
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) acc[jj] = dd_warp_sum(acc[jj]);
-    if (lane == 0)
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) s_raw[sl][jj] = acc[jj];
+    const ddf tot = dd_warp_sum4(acc);
+    if ((lane & 7) == 0) s_raw[sl][lane >> 3] = tot;
   }
   __syncthreads();
   if (warp == 0 && lane < K) {
@@ -983,15 +1007,30 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
     mbar_arrive_expect_tx(&s_bar[st], (unsigned)nobs * bytes);
     for (int c = 0; c < nobs; ++c) bulk_load(buf(st, c), cols.c[c] + t0, bytes, &s_bar[st]);
   };
-  if (threadIdx.x == 0) {
-    for (int st = 0; st < NST; ++st) {
-      mbar_init(&s_bar[st], 1);
-      s_done[st] = 0u;
-      s_last[st] = -1;
+  if (threadIdx.x < 32) {
+    // warp 0 stages the first NST tiles: lane 0 initialises the barriers and posts each
+    // stage's expected bytes, then the lanes issue one column copy each
+    if (lane == 0) {
+      for (int st = 0; st < NST; ++st) {
+        mbar_init(&s_bar[st], 1);
+        s_done[st] = 0u;
+        s_last[st] = -1;
+      }
+      s_fail = 0u;
+      mbar_init_fence();
+      for (int j = 0; j < NST && j < ntile; ++j) {
+        if (withhold && j == (int)withhold - 1) continue;
+        s_last[j] = j;
+        mbar_arrive_expect_tx(&s_bar[j], (unsigned)nobs * (unsigned)tile_count(j) * (unsigned)sizeof(float));
+      }
     }
-    s_fail = 0u;
-    mbar_init_fence();
-    for (int j = 0; j < NST; ++j) issue(j);
+    __syncwarp();
+    for (int q = lane; q < NST * nobs; q += 32) {
+      const int j = q / nobs, c = q % nobs;
+      if (j < ntile && !(withhold && j == (int)withhold - 1))
+        bulk_load(buf(j, c), cols.c[c] + r0 + (int64_t)j * TE, (unsigned)tile_count(j) * (unsigned)sizeof(float),
+                  &s_bar[j]);
+    }
   }
   // the column copies above read only the dataset; the normalisation written by the
   // previous kernel in the stream is read after this point
