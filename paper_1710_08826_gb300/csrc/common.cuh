@@ -533,7 +533,8 @@ __device__ __forceinline__ bool last_block_ticket(unsigned* ticket, int nblocks)
 // Lane sums of partials[0 .. nblocks) by threads [0, nthreads) of the block (every thread of
 // the block calls it), loads in rounds of U per thread: lane s is summed by `per` consecutive
 // threads (per a power of two),
-// thread g of the group adding blocks g, g + per, ... in order; the group is combined by an
+// thread g of the group adding blocks g, g + per, ... (each round of U by a pairwise tree,
+// the rounds in order); the group is combined by an
 // xor tree (and, for groups wider than a warp, by the warps in index order) into out[s]
 // (FP64).  Ends with a block barrier.
 template <int U = 16>
@@ -544,17 +545,22 @@ __device__ __forceinline__ void reduce_partials(const float2* partials, int nslo
   const int s = threadIdx.x / per, g = threadIdx.x % per;
   ddf acc = {0.f, 0.f};
   if (s < nslots && (int)threadIdx.x < nthreads) {
-    // rounds of U independent loads in flight (the last round padded with exact zeros),
-    // added in block order: one L2 round trip per round
+    // rounds of U independent loads in flight (the last round padded with exact zeros), each
+    // round added by a fixed pairwise tree (log2 U dependent additions, not U): one L2 round
+    // trip per round
     for (int b = g; b < nblocks; b += U * per) {
-      float2 q[U];
+      ddf q[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int bb = b + u * per;
-        q[u] = bb < nblocks ? __ldcg(partials + (size_t)bb * nslots + s) : make_float2(0.f, 0.f);
+        const float2 v = bb < nblocks ? __ldcg(partials + (size_t)bb * nslots + s) : make_float2(0.f, 0.f);
+        q[u] = ddf{v.x, v.y};
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) acc = dd_add(acc, {q[u].x, q[u].y});
+      for (int w = 1; w < U; w *= 2)
+#pragma unroll
+        for (int i = 0; i + w < U; i += 2 * w) q[i] = dd_add(q[i], q[i + w]);
+      acc = dd_add(acc, q[0]);
     }
   }
   const int wper = per < 32 ? per : 32;
