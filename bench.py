@@ -560,6 +560,12 @@ def run_ours(args):
     def e2e_streamed(chunks):
         return lambda: model.nll_grad_streamed(ds_stream, cols_pin, theta, n_chunks=chunks)
 
+    # the columns stay in pinned host memory; every evaluation reads them over the host link
+    ds_host = goo.Dataset(ctx, cols_pin, lo, hi, dtype="f32", borrow_host=True)
+
+    def e2e_borrow_host():
+        return model.nll_grad(ds_host, theta, "f32")
+
     e2e_steps = max(3, args.steps // 5)
 
     def e2e_time(fn):
@@ -578,6 +584,9 @@ def run_ours(args):
         return sec
 
     e2e_forms = {
+        "borrow_host": (e2e_time(e2e_borrow_host), "GOO_BORROW_HOST dataset: the event kernel reads the pinned float32 "
+                                                   "host columns over the host link itself (no copy, no ingest pass; "
+                                                   "range-checked in the kernel) + goo_nll_grad"),
         "streamed_8": (e2e_time(e2e_streamed(8)), "goo_nll_grad_streamed, 8 chunks: the copy engine moves chunk c + 1 "
                                                   "from the pinned float32 host columns while chunk c is range-checked "
                                                   "and evaluated"),
@@ -590,6 +599,7 @@ def run_ours(args):
                                               "goo_dataset_free"),
     }
     ds_stream.close()
+    ds_host.close()
     # the host link's copy bandwidth for the step's bytes (pinned host -> device, copy engine):
     # the floor of any end-to-end form
     link_src = torch.empty(n * BYTES_PER_EVENT_F32, dtype=torch.uint8).pin_memory()

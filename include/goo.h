@@ -70,9 +70,12 @@ enum {
 enum {
   GOO_COPY = 0,         /* cols are host pointers; the library copies them                 */
   GOO_BORROW_DEVICE = 1, /* cols are device pointers that must outlive the dataset        */
-  GOO_COPY_MAPPED = 2   /* cols are pinned host pointers (cudaHostAlloc / registered); the
+  GOO_COPY_MAPPED = 2,  /* cols are pinned host pointers (cudaHostAlloc / registered); the
                            ingest kernel reads them over the host link itself, with no
                            separate copy-engine transfer                                   */
+  GOO_BORROW_HOST = 3   /* cols are pinned, device-mapped float32 host arrays kept by
+                           reference: nothing is copied, every evaluation reads them over the
+                           host link and range-checks them (see goo_dataset_upload)        */
 };
 
 /* ---- model nodes --------------------------------------------------------------------- */
@@ -211,7 +214,19 @@ int goo_debug_withhold_tile(goo_ctx* ctx, int64_t tile);
  * dataset is created, and *n_bad (if not NULL) receives the number of offending events.
  * The device keeps both a float64 and a float32 copy of every column, written by one fused
  * conversion and range-check pass.  GOO_COPY_MAPPED fails with GOO_ERR_ARG unless every
- * column is pinned host memory. */
+ * column is pinned host memory.
+ *
+ * GOO_BORROW_HOST (dtype GOO_F32 only) keeps pinned, device-mapped host columns by reference
+ * (16-byte aligned; they must outlive the dataset) and copies nothing: the caller may rewrite
+ * their contents between evaluations (with no evaluation in flight).  Every FP32 evaluation of
+ * a sum-of-product model reads the events over the host link inside its event kernel, the
+ * transfer overlapped with the arithmetic, and checks each event against the limits: an
+ * evaluation that meets events outside them (or NaN) fails with GOO_ERR_RANGE.  The upload
+ * itself checks nothing.  Such a dataset serves goo_nll / goo_nll_grad / goo_nll_partial in
+ * GOO_F32 with sum-of-product models of at most 2 products of 3 leaves (or, without the
+ * gradient, 4 of 4) and no weights; anything else (FP64 evaluation, amplitude models,
+ * goo_dataset_update, goo_dataset_set_weights, goo_dataset_column in GOO_F64) fails with
+ * GOO_ERR_UNSUPPORTED or GOO_ERR_STATE. */
 int goo_dataset_upload(goo_ctx* ctx, int ncols, const void* const* cols, int dtype,
                        int64_t n_events, const double* lo, const double* hi, int flags,
                        goo_dataset** out, int64_t* n_bad);

@@ -22,6 +22,10 @@ int check_model_dataset(const goo_model* m, const goo_dataset* ds, int precision
   if (precision != GOO_F64 && precision != GOO_F32) return set_error(GOO_ERR_ARG, "precision=%d", precision);
   if (ds->w64 && m->kind != 0)
     return set_error(GOO_ERR_UNSUPPORTED, "per-event weights are supported by sum-of-product models only");
+  if (ds->host_borrowed && (m->kind != 0 || precision != GOO_F32))
+    return set_error(GOO_ERR_UNSUPPORTED,
+                     "a GOO_BORROW_HOST dataset (float32 columns in host memory) serves FP32 evaluations of "
+                     "sum-of-product models only");
   if (ds->ncols < m->n_obs)
     return set_error(GOO_ERR_ARG, "dataset has %d columns, model uses %d observables", ds->ncols, m->n_obs);
   for (int o = 0; o < m->n_obs; ++o)
@@ -63,6 +67,12 @@ int nll_common(goo_model* m, const goo_dataset* ds, const double* theta, int pre
     } else {
       GOO_TRY(read_result_mapped(ctx, 2 + P, res));
     }
+  }
+  if (res[1] <= -2) {
+    *nll_out = HUGE_VAL;
+    if (grad_out)
+      for (int p = 0; p < P; ++p) grad_out[p] = 0.0;
+    return set_error(GOO_ERR_RANGE, "%.0f events lie outside the observable limits", -res[1] - 2);
   }
   if (res[1] < 0) {
     *nll_out = HUGE_VAL;
@@ -133,6 +143,8 @@ int goo_model_build(goo_ctx* ctx, const goo_node* nodes, int n_nodes, int n_para
 
 int goo_model_set_norm(goo_model* m, const goo_norm_spec* spec) {
   if (!m || !spec) return set_error(GOO_ERR_ARG, "goo_model_set_norm: NULL argument");
+  if (spec->kind == GOO_NORM_MC && spec->mc && spec->mc->host_borrowed)
+    return set_error(GOO_ERR_UNSUPPORTED, "goo_model_set_norm: the MC sample cannot be a GOO_BORROW_HOST dataset");
   GOO_CUDA_TRY(cudaSetDevice(m->ctx->device));
   if (m->kind == 2) return td4_set_norm(m, spec);
   return m->kind == 1 ? dalitz_set_norm(m, spec) : sop_set_norm(m, spec);
@@ -188,6 +200,7 @@ int goo_eval_logf(goo_model* m, const goo_dataset* ds, const double* theta, int 
   GOO_TRY(check_model_dataset(m, ds, precision));
   GOO_TRY(check_theta(m, theta));
   if (!logf_dev && ds->n > 0) return set_error(GOO_ERR_ARG, "goo_eval_logf: logf_dev is NULL");
+  if (ds->host_borrowed) return set_error(GOO_ERR_UNSUPPORTED, "goo_eval_logf: GOO_BORROW_HOST dataset");
   GOO_CUDA_TRY(cudaSetDevice(m->ctx->device));
   if (m->kind == 1) {
     GOO_TRY(dalitz_eval_logf(m, ds, theta, precision, logf_dev));
@@ -234,6 +247,11 @@ int goo_nll_partial(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t 
   out[1] = res[1];
   out[2] = (double)(end - begin);
   for (int p = 0; p < P; ++p) out[3 + p] = want_grad ? res[3 + p] : 0.0;
+  if (nbad <= -2) {
+    out[0] = HUGE_VAL;
+    return set_error(GOO_ERR_RANGE, "%.0f events in [%lld, %lld) lie outside the observable limits", -nbad - 2,
+                     (long long)begin, (long long)end);
+  }
   if (nbad < 0) {
     out[0] = HUGE_VAL;
     return set_error(GOO_ERR_TIMEOUT, "a device wait for event data gave up in [%lld, %lld)", (long long)begin,
@@ -274,7 +292,7 @@ int goo_model_set_jit(goo_model* m, int mode) {
   if (mode != 0 && mode != 1) return set_error(GOO_ERR_ARG, "goo_model_set_jit: mode=%d", mode);
   m->jit_mode = mode;
   m->jit_status = mode;
-  m->ev2_fn[0] = m->ev2_fn[1] = nullptr;
+  m->ev2_fn[0] = m->ev2_fn[1] = m->ev2_fn[2] = m->ev2_fn[3] = nullptr;
   return GOO_OK;
 }
 

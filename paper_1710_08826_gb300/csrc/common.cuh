@@ -152,6 +152,9 @@ struct goo_dataset {
   // per-event weights (null: every event weighs 1), set by goo_dataset_set_weights
   double* w64 = nullptr;
   float* w32 = nullptr;
+  // GOO_BORROW_HOST: d32 are device-mapped pinned host columns, read by every evaluation over
+  // the host link and range-checked there; no d64
+  bool host_borrowed = false;
   double lo[goo::kMaxCols] = {};
   double hi[goo::kMaxCols] = {};
   // amplitude caches attached to this dataset, [0]: float32, [1]: float64, [2], [3]: the
@@ -363,6 +366,9 @@ constexpr int kWaitLimitWord = 3;  // counters[3]: limit of the tile waits in SM
 // counters[4]: failure-detection test hook (goo_debug_withhold_tile); 1 + the index of a tile
 // whose copies the first block of the staged kernels does not issue, 0: none
 constexpr int kWithholdWord = 4;
+// counters[5]: events outside the observable limits met by an evaluation that reads its events
+// from host memory (GOO_BORROW_HOST); reported as result[nb] = -(2 + count)
+constexpr int kRangeWord = 5;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 

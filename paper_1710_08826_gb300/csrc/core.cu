@@ -473,17 +473,49 @@ int goo_dataset_upload(goo_ctx* ctx, int ncols, const void* const* cols, int dty
   if (ncols < 1 || ncols > kMaxCols) return set_error(GOO_ERR_ARG, "goo_dataset_upload: ncols=%d (1..%d)", ncols, kMaxCols);
   if (n_events < 0) return set_error(GOO_ERR_ARG, "goo_dataset_upload: n_events=%lld", (long long)n_events);
   if (dtype != GOO_F64 && dtype != GOO_F32) return set_error(GOO_ERR_ARG, "goo_dataset_upload: dtype=%d", dtype);
-  if (flags != GOO_COPY && flags != GOO_BORROW_DEVICE && flags != GOO_COPY_MAPPED)
+  if (flags != GOO_COPY && flags != GOO_BORROW_DEVICE && flags != GOO_COPY_MAPPED && flags != GOO_BORROW_HOST)
     return set_error(GOO_ERR_ARG, "goo_dataset_upload: flags=%d", flags);
+  if (flags == GOO_BORROW_HOST && dtype != GOO_F32)
+    return set_error(GOO_ERR_ARG, "goo_dataset_upload: GOO_BORROW_HOST takes float32 columns (GOO_F32)");
   for (int c = 0; c < ncols; ++c) {
     if (!(lo[c] < hi[c])) return set_error(GOO_ERR_ARG, "goo_dataset_upload: column %d has lo >= hi", c);
     if (n_events > 0 && !cols[c]) return set_error(GOO_ERR_ARG, "goo_dataset_upload: column %d is NULL", c);
-    if (flags == GOO_BORROW_DEVICE && ((uintptr_t)cols[c] & 15))
+    if ((flags == GOO_BORROW_DEVICE || flags == GOO_BORROW_HOST) && ((uintptr_t)cols[c] & 15))
       return set_error(GOO_ERR_ARG, "goo_dataset_upload: borrowed column %d is not 16-byte aligned", c);
   }
   GOO_CUDA_TRY(cudaSetDevice(ctx->device));
-  if (flags == GOO_COPY_MAPPED && n_events > 0 && !host_mapped(cols, ncols))
-    return set_error(GOO_ERR_ARG, "goo_dataset_upload: GOO_COPY_MAPPED needs pinned host columns");
+  if ((flags == GOO_COPY_MAPPED || flags == GOO_BORROW_HOST) && n_events > 0 && !host_mapped(cols, ncols))
+    return set_error(GOO_ERR_ARG, "goo_dataset_upload: %s needs pinned host columns",
+                     flags == GOO_COPY_MAPPED ? "GOO_COPY_MAPPED" : "GOO_BORROW_HOST");
+  if (flags == GOO_BORROW_HOST) {
+    // the columns stay in host memory; evaluations read them through their device mapping
+    goo_dataset* ds = new goo_dataset();
+    ds->ctx = ctx;
+    ds->n = n_events;
+    ds->capacity = n_events;
+    ds->epoch = next_dataset_epoch();
+    ds->ncols = ncols;
+    ds->owns64 = ds->owns32 = false;
+    ds->host_borrowed = true;
+    for (int c = 0; c < ncols; ++c) {
+      ds->lo[c] = lo[c];
+      ds->hi[c] = hi[c];
+      void* dp = nullptr;
+      if (n_events > 0 && cudaHostGetDevicePointer(&dp, const_cast<void*>(cols[c]), 0) != cudaSuccess) {
+        cudaGetLastError();
+        delete ds;
+        return set_error(GOO_ERR_ARG, "goo_dataset_upload: column %d has no device mapping", c);
+      }
+      if ((uintptr_t)dp & 15) {
+        delete ds;
+        return set_error(GOO_ERR_ARG, "goo_dataset_upload: the device mapping of column %d is not 16-byte aligned", c);
+      }
+      ds->d32[c] = (float*)dp;
+    }
+    ctx->live++;
+    *out = ds;
+    return GOO_OK;
+  }
   goo_dataset* ds = new goo_dataset();
   ds->ctx = ctx;
   ds->n = n_events;
@@ -526,7 +558,9 @@ int goo_dataset_update(goo_dataset* ds, const void* const* cols, int dtype, int6
                        int64_t* n_bad) {
   if (n_bad) *n_bad = 0;
   if (!ds || !cols) return set_error(GOO_ERR_ARG, "goo_dataset_update: NULL argument");
-  if (!ds->owns32 || !ds->owns64) return set_error(GOO_ERR_STATE, "goo_dataset_update: the dataset borrows its columns");
+  if (!ds->owns32 || !ds->owns64)
+    return set_error(GOO_ERR_STATE, "goo_dataset_update: the dataset borrows its columns%s",
+                     ds->host_borrowed ? " (GOO_BORROW_HOST: rewrite the host columns instead)" : "");
   if (n_events < 0 || n_events > ds->capacity)
     return set_error(GOO_ERR_ARG, "goo_dataset_update: n_events=%lld (capacity %lld)", (long long)n_events,
                      (long long)ds->capacity);
@@ -702,6 +736,8 @@ int64_t goo_dataset_size(const goo_dataset* ds) { return ds ? ds->n : -1; }
 // since a launch in flight may read the old arrays.
 int goo_dataset_set_weights(goo_dataset* ds, const double* w) {
   if (!ds) return set_error(GOO_ERR_ARG, "goo_dataset_set_weights: NULL dataset");
+  if (ds->host_borrowed)
+    return set_error(GOO_ERR_UNSUPPORTED, "goo_dataset_set_weights: a GOO_BORROW_HOST dataset takes no weights");
   const int64_t n = ds->n;
   std::vector<float> w32;
   if (w) {

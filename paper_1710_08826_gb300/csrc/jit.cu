@@ -42,9 +42,9 @@ struct JitEntry {
 std::mutex g_mu;
 std::map<std::string, JitEntry> g_cache;
 
-// NVRTC compilation of sop_event2_kernel<K, L, grad, sig, cols> to an sm_103a cubin: the
-// image and the kernel's lowered name.  Needs no device.
-int compile_event2_cubin(int K, int L, bool grad, unsigned long long sig, unsigned long long cols,
+// NVRTC compilation of sop_event2_kernel<K, L, grad, sig, cols, direct> to an sm_103a cubin:
+// the image and the kernel's lowered name.  Needs no device.
+int compile_event2_cubin(int K, int L, bool grad, unsigned long long sig, unsigned long long cols, bool direct,
                          std::vector<char>& cubin, std::string& kname) {
   const char* src = "#include \"sop_kernels.cuh\"\n";
   const int nh = (int)(sizeof(kJitHeaderNames) / sizeof(kJitHeaderNames[0]));
@@ -52,8 +52,8 @@ int compile_event2_cubin(int K, int L, bool grad, unsigned long long sig, unsign
   if (nvrtcCreateProgram(&prog, src, "goo_event2_jit.cu", nh, kJitHeaderSources, kJitHeaderNames) != NVRTC_SUCCESS)
     return set_error(GOO_ERR_CUDA, "NVRTC: cannot create the program");
   char name[192];
-  std::snprintf(name, sizeof name, "goo::sop_event2_kernel<%d, %d, %s, 0x%llxull, 0x%llxull>", K, L,
-                grad ? "true" : "false", sig, cols);
+  std::snprintf(name, sizeof name, "goo::sop_event2_kernel<%d, %d, %s, 0x%llxull, 0x%llxull, %s>", K, L,
+                grad ? "true" : "false", sig, cols, direct ? "true" : "false");
   nvrtcAddNameExpression(prog, name);
   const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device", "-lineinfo", "-I" GOO_CUDA_INCLUDE,
                         "-I" GOO_CUDA_INCLUDE "/cccl"};
@@ -80,10 +80,11 @@ int compile_event2_cubin(int K, int L, bool grad, unsigned long long sig, unsign
   return GOO_OK;
 }
 
-int compile_event2(int K, int L, bool grad, unsigned long long sig, unsigned long long cols, JitEntry& e) {
+int compile_event2(int K, int L, bool grad, unsigned long long sig, unsigned long long cols, bool direct,
+                   JitEntry& e) {
   std::vector<char> cubin;
   std::string kname;
-  GOO_TRY(compile_event2_cubin(K, L, grad, sig, cols, cubin, kname));
+  GOO_TRY(compile_event2_cubin(K, L, grad, sig, cols, direct, cubin, kname));
   GOO_CUDA_TRY(cudaLibraryLoadData(&e.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
   GOO_CUDA_TRY(cudaLibraryGetKernel(&e.kernel, e.lib, kname.c_str()));
   return GOO_OK;
@@ -92,13 +93,13 @@ int compile_event2(int K, int L, bool grad, unsigned long long sig, unsigned lon
 }  // namespace
 
 const void* jit_event2_kernel(int device, int K, int L, bool grad, unsigned long long sig, unsigned long long cols,
-                              size_t max_smem, int* status) {
+                              bool direct, size_t max_smem, int* status) {
   char key[112];
-  std::snprintf(key, sizeof key, "%d:%d:%d:%llx:%llx", K, L, (int)grad, sig, cols);
+  std::snprintf(key, sizeof key, "%d:%d:%d:%llx:%llx:%d", K, L, (int)grad, sig, cols, (int)direct);
   std::lock_guard<std::mutex> lock(g_mu);
   JitEntry& e = g_cache[key];
   if (e.state == 0) {
-    const int rc = compile_event2(K, L, grad, sig, cols, e);
+    const int rc = compile_event2(K, L, grad, sig, cols, direct, e);
     e.state = rc == GOO_OK ? 1 : -1;
     if (rc != GOO_OK) {
       cudaGetLastError();
@@ -131,7 +132,7 @@ extern "C" int goo_jit_check(int K, int L, int grad, unsigned long long sig, uns
     return set_error(GOO_ERR_ARG, "goo_jit_check: shape %d x %d (1..%d x 1..%d)", K, L, kMaxComp, kMaxLeaf);
   std::vector<char> cubin;
   std::string kname;
-  GOO_TRY(compile_event2_cubin(K, L, grad != 0, sig, cols, cubin, kname));
+  GOO_TRY(compile_event2_cubin(K, L, grad != 0, sig, cols, false, cubin, kname));
   if (cubin_bytes) *cubin_bytes = (int64_t)cubin.size();
   return GOO_OK;
 }

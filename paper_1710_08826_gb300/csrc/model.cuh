@@ -121,8 +121,10 @@ struct goo_model {
   int jit_status = 1;
   // the packed-pair event kernel resolved for this model (index: gradient form) and the
   // jit_status it came with; reset by goo_model_set_jit
-  const void* ev2_fn[2] = {nullptr, nullptr};
-  int ev2_status[2] = {0, 0};
+  // the pair kernel per gradient form (index gi) and column source (+2: host columns read
+  // directly), resolved on first use
+  const void* ev2_fn[4] = {nullptr, nullptr, nullptr, nullptr};
+  int ev2_status[4] = {0, 0, 0, 0};
 };
 
 namespace goo {

@@ -1731,9 +1731,9 @@ int goo_nll_grad_batch(goo_model* m, int n_fits, const goo_dataset* const* ds, c
   if (precision != GOO_F32) return set_error(GOO_ERR_UNSUPPORTED, "goo_nll_grad_batch: the batched path is FP32");
   if (n_fits == 0) return GOO_OK;
   for (int f = 0; f < n_fits; ++f)
-    if (!ds[f] || ds[f]->w64)
+    if (!ds[f] || ds[f]->w64 || ds[f]->host_borrowed)
       return set_error(ds[f] ? GOO_ERR_UNSUPPORTED : GOO_ERR_ARG, "goo_nll_grad_batch: dataset %d is %s", f,
-                       ds[f] ? "weighted" : "NULL");
+                       !ds[f] ? "NULL" : ds[f]->w64 ? "weighted" : "in host memory (GOO_BORROW_HOST)");
   goo_ctx* ctx = m->ctx;
   GOO_CUDA_TRY(cudaSetDevice(ctx->device));
   const int P = m->n_params;

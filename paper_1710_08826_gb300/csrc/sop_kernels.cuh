@@ -52,6 +52,10 @@ __host__ __device__ constexpr int leaf_nder(int op) {
 template <typename T>
 struct Cols {
   const T* c[kMaxObs];
+  // for the pair kernel's direct form (a GOO_BORROW_HOST dataset: c are device-mapped host
+  // columns, read straight into registers): the float limits that admit exactly the values
+  // inside the double limits
+  float lo[kMaxObs], hi[kMaxObs];
 };
 
 template <typename T>
@@ -363,10 +367,11 @@ __device__ __forceinline__ void event_finish(ddf (&v)[EventLanes<float, K, L, GR
   if (!last_block_ticket(counters, gridDim.x)) return;
   // every other block added to these words before its ticket (and a fence): plain L2 reads,
   // issued before the reduction so that their latency overlaps it
-  unsigned nbad = 0u, status = 0u;
+  unsigned nbad = 0u, status = 0u, nrange = 0u;
   if (threadIdx.x == 0) {
     nbad = __ldcg(counters + 1);
     status = __ldcg(counters + kStatusWord);
+    nrange = __ldcg(counters + kRangeWord);
   }
   reduce_partials(partials, NS, gridDim.x, s_out, s_red, blockDim.x);
 
@@ -397,8 +402,10 @@ __device__ __forceinline__ void event_finish(ddf (&v)[EventLanes<float, K, L, GR
     counters[0] = 0u;  // the ticket
     counters[1] = 0u;
     counters[kStatusWord] = 0u;
-    // a device wait that gave up is reported as a negative event count
-    const double nb = status ? -1.0 : (double)nbad;
+    counters[kRangeWord] = 0u;
+    // a device wait that gave up is reported as -1, events outside the observable limits
+    // (direct reads of host columns) as -(2 + their count)
+    const double nb = nrange ? -2.0 - (double)nrange : status ? -1.0 : (double)nbad;
     result[0] = -s_out[0];
     if (out_mode == 0) {
       result[1] = nb;
@@ -819,10 +826,11 @@ __device__ __forceinline__ void event_finish_fused(const ddf (&v)[EventLanes<flo
   if (!last_block_ticket(counters, gridDim.x)) return;
   // every other block added to these words before its ticket (and a fence): plain L2 reads,
   // issued before the reduction so that their latency overlaps it
-  unsigned nbad = 0u, status = 0u;
+  unsigned nbad = 0u, status = 0u, nrange = 0u;
   if (threadIdx.x == 0) {
     nbad = __ldcg(counters + 1);
     status = __ldcg(counters + kStatusWord);
+    nrange = __ldcg(counters + kRangeWord);
   }
   if constexpr (GRAD) {
     // the normalisation terms D_j / S of every leaf slot, from this block's grid sums (the
@@ -866,8 +874,10 @@ __device__ __forceinline__ void event_finish_fused(const ddf (&v)[EventLanes<flo
     counters[0] = 0u;  // the ticket
     counters[1] = 0u;
     counters[kStatusWord] = 0u;
-    // a device wait that gave up is reported as a negative event count
-    const double nb = status ? -1.0 : (double)nbad;
+    counters[kRangeWord] = 0u;
+    // a device wait that gave up is reported as -1, events outside the observable limits
+    // (direct reads of host columns) as -(2 + their count)
+    const double nb = nrange ? -2.0 - (double)nrange : status ? -1.0 : (double)nbad;
     result[0] = -s_out[0];
     if (out_mode == 0) {
       result[1] = nb;
@@ -966,7 +976,7 @@ __host__ __device__ constexpr int cols_col(unsigned long long cols, int slot) { 
 // block barrier separates tiles, so a warp that is fast on one tile runs ahead on the next
 // instead of waiting for the slowest warp.
 // Dynamic shared memory: kEventStages * n_obs * TE floats.
-template <int K, int L, bool GRAD, unsigned long long SIG = 0, unsigned long long COLS = 0>
+template <int K, int L, bool GRAD, unsigned long long SIG = 0, unsigned long long COLS = 0, bool DIRECT = false>
 __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
     sop_event2_kernel(const ModelDev* __restrict__ md, const EvConst<float, K, L> P,
                       const __grid_constant__ EvNorm<K, L, GRAD> N, Cols<float> cols, int64_t begin, int64_t end,
@@ -1007,9 +1017,14 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
     mbar_arrive_expect_tx(&s_bar[st], (unsigned)nobs * bytes);
     for (int c = 0; c < nobs; ++c) bulk_load(buf(st, c), cols.c[c] + t0, bytes, &s_bar[st]);
   };
+  // DIRECT (a GOO_BORROW_HOST dataset): the columns are read straight from host memory, so
+  // no copies are staged; a separate instantiation, so that the staged kernel carries none of
+  // its code
+  constexpr bool direct = DIRECT;
   if (threadIdx.x < 32) {
     // warp 0 stages the first NST tiles: lane 0 initialises the barriers and posts each
-    // stage's expected bytes, then the lanes issue one column copy each
+    // stage's expected bytes, then the lanes issue one column copy each (none when the
+    // columns are read directly)
     if (lane == 0) {
       for (int st = 0; st < NST; ++st) {
         mbar_init(&s_bar[st], 1);
@@ -1018,14 +1033,14 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
       }
       s_fail = 0u;
       mbar_init_fence();
-      for (int j = 0; j < NST && j < ntile; ++j) {
+      for (int j = 0; j < NST && j < ntile && !direct; ++j) {
         if (withhold && j == (int)withhold - 1) continue;
         s_last[j] = j;
         mbar_arrive_expect_tx(&s_bar[j], (unsigned)nobs * (unsigned)tile_count(j) * (unsigned)sizeof(float));
       }
     }
     __syncwarp();
-    for (int q = lane; q < NST * nobs; q += 32) {
+    for (int q = lane; q < NST * nobs && !direct; q += 32) {
       const int j = q / nobs, c = q % nobs;
       if (j < ntile && !(withhold && j == (int)withhold - 1))
         bulk_load(buf(j, c), cols.c[c] + r0 + (int64_t)j * TE, (unsigned)tile_count(j) * (unsigned)sizeof(float),
@@ -1057,10 +1072,41 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
   auto leaf_col = [&](int k, int l) { return SIG != 0 ? cols_col(COLS, k * L + l) : P.leaf[k][l].col; };
   const long long wlim = tile_wait_limit(counters);
   bool failed = false;
+  unsigned nout = 0;  // events outside the observable limits (direct reads)
+  auto in_range = [&](float v, int c) { return v >= cols.lo[c] && v <= cols.hi[c]; };  // false for NaN
   for (int j = 0; j < ntile; ++j) {
     const int st = j % NST;
-    // the whole warp agrees on whether the tile arrived in time
-    if (!__all_sync(0xffffffffu, mbar_wait(&s_bar[st], (unsigned)(j / NST) & 1u, wlim))) {
+    if (direct) {
+      // this thread's pairs of tile j straight from the host columns (over the host link),
+      // every load issued before any is used, into its own slots of the stage buffer, which
+      // no other thread reads: the evaluation below is the staged path's, unchanged
+      const int npair_d = tile_count(j) >> 1;
+      const int64_t t0 = r0 + (int64_t)j * TE;
+      float2 xd[PPT][kMaxObs];
+#pragma unroll
+      for (int u = 0; u < PPT; ++u) {
+        const int pr = threadIdx.x + u * kBlock;
+#pragma unroll
+        for (int c = 0; c < kMaxObs; ++c)
+          xd[u][c] = (pr < npair_d && c < nobs) ? reinterpret_cast<const float2*>(cols.c[c] + t0)[pr]
+                                                : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < PPT; ++u) {
+        const int pr = threadIdx.x + u * kBlock;
+        if (pr >= npair_d) continue;
+        bool ok0 = true, ok1 = true;
+#pragma unroll
+        for (int c = 0; c < kMaxObs; ++c) {
+          if (c >= nobs) continue;
+          ok0 = ok0 && in_range(xd[u][c].x, c);
+          ok1 = ok1 && in_range(xd[u][c].y, c);
+          reinterpret_cast<float2*>(buf(st, c))[pr] = xd[u][c];
+        }
+        nout += (ok0 ? 0u : 1u) + (ok1 ? 0u : 1u);
+      }
+    } else if (!__all_sync(0xffffffffu, mbar_wait(&s_bar[st], (unsigned)(j / NST) & 1u, wlim))) {
+      // the whole warp agrees on whether the tile arrived in time
       failed = true;
       break;
     }
@@ -1087,7 +1133,7 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
     // it: every warp's reads of the buffer precede its count (block-scope fences around the
     // shared atomic), and the refilling thread orders them before the asynchronous copy
     __syncwarp();
-    if (lane == 0) {
+    if (lane == 0 && !direct) {
       __threadfence_block();
       const unsigned done = atomicAdd(&s_done[st], 1u) + 1u;
       if (done == (unsigned)(j / NST + 1) * NWARP) {
@@ -1103,15 +1149,20 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
     if (i >= hi) return;
     const bool v0 = i >= lo, v1 = i + 1 < hi;
     float2 x[kMaxObs];
+    bool ok0 = true, ok1 = true;
 #pragma unroll
     for (int c = 0; c < kMaxObs; ++c) {
       x[c] = splat(0.f);
       if (c < nobs) {
-        if (v0 && v1) x[c] = __ldg(reinterpret_cast<const float2*>(cols.c[c] + i));
+        // plain loads: the columns may be host memory (direct reads)
+        if (v0 && v1) x[c] = *reinterpret_cast<const float2*>(cols.c[c] + i);
         else if (v0) x[c].x = cols.c[c][i];
         else x[c].y = cols.c[c][i + 1];
+        ok0 = ok0 && in_range(x[c].x, c);
+        ok1 = ok1 && in_range(x[c].y, c);
       }
     }
+    if (direct) nout += (v0 && !ok0 ? 1u : 0u) + (v1 && !ok1 ? 1u : 0u);
     float2 xl[K][L];
 #pragma unroll
     for (int k = 0; k < K; ++k)
@@ -1124,6 +1175,11 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
     if (blockIdx.x == gridDim.x - 1 && end > B) ragged(B, end);
   }
   if (failed && lane == 0) atomicOr(&s_fail, 1u);
+  if (direct) {
+    // events outside the limits: counted before the ticket, reported by the last block
+    for (int m = 16; m > 0; m >>= 1) nout += __shfl_xor_sync(0xffffffffu, nout, m);
+    if (lane == 0 && nout) atomicAdd(counters + kRangeWord, nout);
+  }
   __syncthreads();
   if (s_fail) {
     // a copy did not arrive in time: record it, then wait (again bounded, with the default

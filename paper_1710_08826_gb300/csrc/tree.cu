@@ -956,13 +956,17 @@ static int launch_event2(goo_model* m, const goo_dataset* ds, int64_t begin, int
   const size_t smem = std::max((size_t)kEventStages * m->host.n_obs * TE * sizeof(float), red_bytes);
   // room for the largest column count, so one setting serves every model on this device
   const size_t smem_max = std::max((size_t)kEventStages * kMaxObs * TE * sizeof(float), red_bytes);
-  static bool configured[kMaxDevicesEv] = {};
+  static bool configured[kMaxDevicesEv][2] = {};
   if (ctx->device < 0 || ctx->device >= kMaxDevicesEv) return set_error(GOO_ERR_ARG, "device %d", ctx->device);
-  // the kernel for this model and gradient form, resolved on its first evaluation: the one
-  // specialised for the model's leaf signature (jit.cu), else the interpreter
-  const int gi = GRAD ? 1 : 0;
+  // the kernel for this model, gradient form and column source, resolved on its first
+  // evaluation: the one specialised for the model's leaf signature (jit.cu), else the
+  // interpreter; host columns (GOO_BORROW_HOST) take the direct-read instantiation
+  const bool direct = ds->host_borrowed;
+  const int gi = (GRAD ? 1 : 0) + (direct ? 2 : 0);
   if (!m->ev2_fn[gi]) {
-    const void* fn = (const void*)sop_event2_kernel<K, L, GRAD>;
+    const void* interp = direct ? (const void*)sop_event2_kernel<K, L, GRAD, 0, 0, true>
+                                : (const void*)sop_event2_kernel<K, L, GRAD>;
+    const void* fn = interp;
     int st = m->jit_mode;
     if (m->jit_mode) {
       unsigned long long sig = 0, colmap = 0;
@@ -972,12 +976,12 @@ static int launch_event2(goo_model* m, const goo_dataset* ds, int64_t begin, int
           sig |= (unsigned long long)(LD.op & 15) << (4 * (k * L + l));
           colmap |= (unsigned long long)(LD.col & 3) << (2 * (k * L + l));
         }
-      const void* jf = jit_event2_kernel(ctx->device, K, L, GRAD, sig, colmap, smem_max, &st);
+      const void* jf = jit_event2_kernel(ctx->device, K, L, GRAD, sig, colmap, direct, smem_max, &st);
       if (jf) fn = jf;
     }
-    if (fn == (const void*)sop_event2_kernel<K, L, GRAD> && !configured[ctx->device]) {
+    if (fn == interp && !configured[ctx->device][direct ? 1 : 0]) {
       GOO_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
-      configured[ctx->device] = true;
+      configured[ctx->device][direct ? 1 : 0] = true;
     }
     m->ev2_fn[gi] = fn;
     m->ev2_status[gi] = st;
@@ -993,6 +997,17 @@ static int launch_event2(goo_model* m, const goo_dataset* ds, int64_t begin, int
   GOO_TRY(ensure_partials(ctx, (size_t)nb * NS));
   Cols<float> cols{};
   for (int c = 0; c < kMaxObs; ++c) cols.c[c] = ds->d32[c < ds->ncols ? c : 0];
+  if (ds->host_borrowed) {
+    // read over the host link by the kernel itself, each value checked against the float
+    // limits that admit exactly the float values inside the double limits
+    for (int c = 0; c < kMaxObs && c < ds->ncols; ++c) {
+      float lo = (float)ds->lo[c], hi = (float)ds->hi[c];
+      if ((double)lo < ds->lo[c]) lo = std::nextafter(lo, HUGE_VALF);
+      if ((double)hi > ds->hi[c]) hi = std::nextafter(hi, -HUGE_VALF);
+      cols.lo[c] = lo;
+      cols.hi[c] = hi;
+    }
+  }
   {
     // programmatic dependent launch after a normalisation kernel: the kernel's blocks start
     // (and put their first column tiles in flight) while that kernel finishes.  A kernel that
@@ -1038,6 +1053,9 @@ static int launch_event_sel(goo_model* m, const goo_dataset* ds, int64_t begin, 
       if constexpr (!GRAD) return launch_event2<4, 4, GRAD>(m, ds, begin, end, out_mode, fused_norm, result);
     }
   }
+  if (ds->host_borrowed)
+    return set_error(GOO_ERR_UNSUPPORTED, "a GOO_BORROW_HOST dataset is read by the packed-pair FP32 kernel only "
+                                          "(at most 2 products of 3 leaves with the gradient, 4 of 4 without)");
   if (fused_norm) return set_error(GOO_ERR_STATE, "sop_events: in-kernel normalisation needs the pair kernel");
   if (m->host.nK <= 2 && m->max_leaf <= 3) return launch_event_T<T, 2, 3, GRAD>(m, ds, begin, end, out_mode, result);
   return launch_event_T<T, 4, 4, GRAD>(m, ds, begin, end, out_mode, result);

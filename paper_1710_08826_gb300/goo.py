@@ -19,7 +19,7 @@ GOO_FIT_ALLOC_FAILED, GOO_FIT_CANCELLED = 6, 7
 GOO_F64, GOO_F32 = 0, 1
 GOO_LINESHAPE_CACHED, GOO_LINESHAPE_FLOATING = 0, 1
 GOO_COEF_CARTESIAN, GOO_COEF_POLAR = 0, 1
-GOO_COPY, GOO_BORROW_DEVICE, GOO_COPY_MAPPED = 0, 1, 2
+GOO_COPY, GOO_BORROW_DEVICE, GOO_COPY_MAPPED, GOO_BORROW_HOST = 0, 1, 2, 3
 OP = dict(gauss=1, expo=2, poly2=3, argus=4, prod=10, add=11, bw=20, nr=21, coherent=22, td4=23, amp4=24, td3=25)
 ANG = dict(SS=0, VS0=1, SV0=2, VV0=3, VVpar=4, VVperp=5, TS0=6, TV0=7)
 NORM = dict(analytic=0, grid=1, mc=2)
@@ -235,16 +235,20 @@ class Context:
 class Dataset:
     """Structure-of-arrays event columns on the device (goo_dataset_upload)."""
 
-    def __init__(self, ctx, columns, lo, hi, dtype="f64", mapped=False):
-        """columns: host arrays (copied), CUDA tensors (borrowed), or with mapped=True pinned
-        host tensors / arrays that the ingest kernel reads directly (GOO_COPY_MAPPED)."""
+    def __init__(self, ctx, columns, lo, hi, dtype="f64", mapped=False, borrow_host=False):
+        """columns: host arrays (copied), CUDA tensors (borrowed), with mapped=True pinned
+        host tensors / arrays that the ingest kernel reads directly (GOO_COPY_MAPPED), or with
+        borrow_host=True pinned float32 host tensors kept by reference and read over the host
+        link by every evaluation (GOO_BORROW_HOST)."""
         self.ctx = ctx
         cols = list(columns)
         ncols = len(cols)
         dt = precision_code(dtype)
         self._keep = []
         ptrs = (ctypes.c_void_p * ncols)()
-        flags = GOO_COPY_MAPPED if mapped else GOO_COPY
+        if borrow_host and (mapped or dt != GOO_F32):
+            raise ValueError("borrow_host takes float32 columns (dtype='f32') and excludes mapped")
+        flags = GOO_BORROW_HOST if borrow_host else GOO_COPY_MAPPED if mapped else GOO_COPY
         n = None
         for i, c in enumerate(cols):
             if hasattr(c, "is_cuda") and c.is_cuda:
@@ -274,7 +278,7 @@ class Dataset:
                                     ctypes.byref(nbad))
         self.n_bad = int(nbad.value)
         _check(rc)
-        if flags != GOO_BORROW_DEVICE:
+        if flags not in (GOO_BORROW_DEVICE, GOO_BORROW_HOST):
             self._keep = []
         self.handle = h
         self.dtype = dtype
