@@ -41,35 +41,35 @@ _TD3_SRC = _COH_SRC + ['paper_1710_08826_gb300/csrc/timeterms.cuh']
 ISSUE_PEAK = 152 * 4 * 2.07e9
 
 NCU_RECORDS = {
-    "sop_nll_grad_f32": {"bytes": 125_557_760, "events": 10_000_000, "duration_ns": 55872, "warp_inst": 26_261_938, "issue_active": 0.4822,
-        "sources": _SOP_SRC, "sha256": "25d6802fce0adacc336fbafd30d882f18e43b1bd7eff1bc7407d51e0bfe3a3c7",
+    "sop_nll_grad_f32": {"bytes": 127_931_904, "events": 10_000_000, "duration_ns": 48928, "warp_inst": 26_078_326, "issue_active": 0.5435,
+        "sources": _SOP_SRC, "sha256": "1053be640239c11c7d88489f41db6db6bf781699a66b244f19327ee80ac76443",
         "profile": "profiles/sop_event2_kernel_f32_c2_10M.md"},
-    "sop_nll_f64": {"bytes": 243_042_816, "events": 10_000_000, "duration_ns": 2503616, "fp64_pipe": 0.8625, "fp64_ops": {"dfma": 649_995_818, "dadd": 340_076_104, "dmul": 259_998_770},
-        "sources": _SOP_SRC, "sha256": "25d6802fce0adacc336fbafd30d882f18e43b1bd7eff1bc7407d51e0bfe3a3c7",
+    "sop_nll_f64": {"bytes": 242_742_528, "events": 10_000_000, "duration_ns": 2504448, "fp64_pipe": 0.8624, "fp64_ops": {"dfma": 649_995_818, "dadd": 340_076_105, "dmul": 259_998_770},
+        "sources": _SOP_SRC, "sha256": "1053be640239c11c7d88489f41db6db6bf781699a66b244f19327ee80ac76443",
         "profile": "profiles/sop_event_kernel_f64_c2_10M.md"},
-    "coh_nll_grad_f32": {"bytes": 323_033_856, "events": 5_000_000, "duration_ns": 63840, "warp_inst": 30_973_750, "issue_active": 0.4608,
-        "sources": _COH_SRC, "sha256": "44de0bf6ca446d02ea5320c8459f10e11da1e54aac21e956a9277241b762bca7",
+    "coh_nll_grad_f32": {"bytes": 323_043_328, "events": 5_000_000, "duration_ns": 63680, "warp_inst": 30_973_750, "issue_active": 0.4606,
+        "sources": _COH_SRC, "sha256": "f0d6e196cc8aa2a6b505f428804b3e4db0aa6aa6551b35f778406746dca2b036",
         "profile": "profiles/coh_nll_staged_kernel_f32_c3_5M.md"},
-    "coh_nll_f64": {"bytes": 643_046_400, "events": 5_000_000, "duration_ns": 774336, "fp64_pipe": 0.8700, "fp64_ops": {"dfma": 165_155_649, "dadd": 135_077_825, "dmul": 105_000_000},
-        "sources": _COH_SRC, "sha256": "44de0bf6ca446d02ea5320c8459f10e11da1e54aac21e956a9277241b762bca7",
+    "coh_nll_f64": {"bytes": 643_054_848, "events": 5_000_000, "duration_ns": 773888, "fp64_pipe": 0.8701, "fp64_ops": {"dfma": 165_155_649, "dadd": 135_077_825, "dmul": 105_000_000},
+        "sources": _COH_SRC, "sha256": "f0d6e196cc8aa2a6b505f428804b3e4db0aa6aa6551b35f778406746dca2b036",
         "profile": "profiles/coh_nll_kernel_f64_c3_5M.md"},
-    "coh_ls_mc_f32": {"bytes": 8_068_608, "events": 1_000_000, "duration_ns": 91648, "warp_inst": 65_044_091, "issue_active": 0.6340,
-        "sources": _COH_SRC, "sha256": "44de0bf6ca446d02ea5320c8459f10e11da1e54aac21e956a9277241b762bca7",
+    "coh_ls_mc_f32": {"bytes": 8_068_352, "events": 1_000_000, "duration_ns": 91744, "warp_inst": 65_106_262, "issue_active": 0.6317,
+        "sources": _COH_SRC, "sha256": "f0d6e196cc8aa2a6b505f428804b3e4db0aa6aa6551b35f778406746dca2b036",
         "profile": "profiles/coh_ls_kernel_f32_c3_floating_5M.md"},
-    "coh_ls_grad_f32": {"bytes": 40_095_744, "events": 5_000_000, "duration_ns": 421792, "warp_inst": 313_731_120, "issue_active": 0.6443,
-        "sources": _COH_SRC, "sha256": "44de0bf6ca446d02ea5320c8459f10e11da1e54aac21e956a9277241b762bca7",
+    "coh_ls_grad_f32": {"bytes": 40_095_744, "events": 5_000_000, "duration_ns": 423104, "warp_inst": 313_731_120, "issue_active": 0.6429,
+        "sources": _COH_SRC, "sha256": "f0d6e196cc8aa2a6b505f428804b3e4db0aa6aa6551b35f778406746dca2b036",
         "profile": "profiles/coh_ls_kernel_f32_c3_floating_5M.md"},
-    "td3_nll_grad_f32": {"bytes": 523_854_848, "events": 2_000_000, "duration_ns": 137152, "warp_inst": 71_326_620, "issue_active": 0.5432,
-        "sources": _TD3_SRC, "sha256": "6141299a22322a973a71749f03539f67262e2e1dabca0d35315b8c929a196f3f",
+    "td3_nll_grad_f32": {"bytes": 523_827_712, "events": 2_000_000, "duration_ns": 138144, "warp_inst": 71_377_692, "issue_active": 0.5413,
+        "sources": _TD3_SRC, "sha256": "91cfbc43f3e3e573540c20890f69c314a1690267d2eefe105eb75e167e8c9883",
         "profile": "profiles/td3_nll_kernel_td3_2M.md"},
-    "td3_nll_f64": {"bytes": 979_082_240, "events": 2_000_000, "duration_ns": 1611488, "fp64_pipe": 0.8524, "fp64_ops": {"dfma": 391_298_265, "dadd": 152_090_307, "dmul": 214_414_797},
-        "sources": _TD3_SRC, "sha256": "6141299a22322a973a71749f03539f67262e2e1dabca0d35315b8c929a196f3f",
+    "td3_nll_f64": {"bytes": 979_146_240, "events": 2_000_000, "duration_ns": 1611968, "fp64_pipe": 0.8524, "fp64_ops": {"dfma": 391_298_265, "dadd": 152_090_307, "dmul": 214_414_797},
+        "sources": _TD3_SRC, "sha256": "91cfbc43f3e3e573540c20890f69c314a1690267d2eefe105eb75e167e8c9883",
         "profile": "profiles/td3_nll_kernel_td3_2M.md"},
-    "td4_nll_grad_f32": {"bytes": 171_076_352, "events": 2_000_000, "duration_ns": 74272, "warp_inst": 50_891_205, "issue_active": 0.6650,
-        "sources": _TD4_SRC, "sha256": "e75012745e4fd8298ff111bc229eeed002f221cb0c6402bed4714ad6f38e6afc",
+    "td4_nll_grad_f32": {"bytes": 171_071_744, "events": 2_000_000, "duration_ns": 74528, "warp_inst": 50_891_205, "issue_active": 0.6670,
+        "sources": _TD4_SRC, "sha256": "89a23f1bf14a2f8e55c56d8a65caf0784be88c2bad503c7ed423a12bf2f7f701",
         "profile": "profiles/td4_nll_f32_kernel_c4_2M.md"},
-    "td4_nll_f64": {"bytes": 339_331_072, "events": 2_000_000, "duration_ns": 1387424, "fp64_pipe": 0.8560, "fp64_ops": {"dfma": 351_287_209, "dadd": 112_088_842, "dmul": 178_181_349},
-        "sources": _TD4_SRC, "sha256": "e75012745e4fd8298ff111bc229eeed002f221cb0c6402bed4714ad6f38e6afc",
+    "td4_nll_f64": {"bytes": 339_160_320, "events": 2_000_000, "duration_ns": 1384672, "fp64_pipe": 0.8560, "fp64_ops": {"dfma": 351_287_209, "dadd": 112_088_842, "dmul": 178_181_349},
+        "sources": _TD4_SRC, "sha256": "89a23f1bf14a2f8e55c56d8a65caf0784be88c2bad503c7ed423a12bf2f7f701",
         "profile": "profiles/td4_nll_f64_kernel_c4_2M.md"},
 }
 
