@@ -1088,12 +1088,10 @@ def c5_study(goo, ctx, n_toys=4096, rate=None, plain_sample=8, n_mc=1_000_000, s
         rounds += 1
         if d != last_done:
             now = time.perf_counter() - t0
-            for tk in list(pending):
-                r = server.result(tk)
-                if r is not None:
-                    i = pending.pop(tk)
-                    finish[i] = now
-                    results[i] = r
+            for tk in server.finished():
+                i = pending.pop(tk)
+                finish[i] = now
+                results[i] = server.result(tk)
             last_done = d
         if nxt == n_toys and q == 0 and a == 0:
             break

@@ -416,6 +416,14 @@ int goo_server_submit(goo_server* server, int64_t n_events, uint64_t seed, const
 int goo_server_step(goo_server* server, int* n_queued, int* n_active, int* n_done);
 int goo_server_result(goo_server* server, int64_t ticket, double* theta_out, double* errors_out,
                       goo_fit_result* res);
+/* The tickets of fits that finished (converged, failed, cancelled or refused admission) since
+ * the previous call, oldest first: up to `cap` of them are written to tickets[0..*n) and
+ * removed from the list; the rest wait for the next call (*n == cap: call again).  A study
+ * of many toy fits (Sec. 5, toy MC studies) collects results this way instead
+ * of asking for every outstanding ticket after each step.  The results stay available to
+ * goo_server_result.  GOO_ERR_ARG for a NULL server or n, cap < 0, or cap > 0 with NULL
+ * tickets. */
+int goo_server_finished(goo_server* server, int64_t* tickets, int cap, int* n);
 /* Failures of one served fit leave the others untouched (each fit's evaluation depends only on
  * its own tiles and theta).  goo_server_submit refuses a non-finite theta_start with
  * GOO_ERR_ARG; nothing is queued.  goo_server_cancel ends a queued or active fit between

@@ -1024,6 +1024,7 @@ struct goo_server {
   std::vector<int> active;
   bool active_dirty = true;
   std::map<int64_t, goo::FitOut> done;
+  std::deque<int64_t> finished;  // tickets that entered `done` and were not yet drained
   std::set<int64_t> fail_alloc;  // tickets whose admission fails its allocation (test hook)
   int64_t next_ticket = 1;
   int64_t rounds = 0, ntiles = 0;
@@ -1212,6 +1213,7 @@ static void finish_unfitted(goo_server* s, int64_t ticket, const std::vector<dou
   out.res.nll = HUGE_VAL;
   out.res.status = status;
   s->done[ticket] = out;
+  s->finished.push_back(ticket);
 }
 
 static int admit(goo_server* s, std::vector<int>& admitted) {
@@ -1310,6 +1312,7 @@ static int retire(goo_server* s) {
     out.res.grad_evals = st[i].evals;
     out.res.status = st[i].status;
     s->done[sl.ticket] = out;
+    s->finished.push_back(sl.ticket);
     arena_free(s, sl.off, sl.bytes);
     sl = Slot();
     s->free_slots.push_back(slot);
@@ -1638,6 +1641,17 @@ int goo_server_result(goo_server* s, int64_t ticket, double* theta_out, double* 
   if (theta_out) std::memcpy(theta_out, f.theta.data(), f.theta.size() * sizeof(double));
   if (errors_out) std::memcpy(errors_out, f.err.data(), f.err.size() * sizeof(double));
   if (res) *res = f.res;
+  return GOO_OK;
+}
+
+int goo_server_finished(goo_server* s, int64_t* tickets, int cap, int* n) {
+  if (!s || !n || cap < 0 || (cap > 0 && !tickets)) return set_error(GOO_ERR_ARG, "goo_server_finished: bad arguments");
+  int k = 0;
+  while (k < cap && !s->finished.empty()) {
+    tickets[k++] = s->finished.front();
+    s->finished.pop_front();
+  }
+  *n = k;
   return GOO_OK;
 }
 

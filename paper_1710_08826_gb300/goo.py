@@ -122,6 +122,7 @@ def _load():
                                            ctypes.POINTER(ctypes.c_int)]),
         "goo_server_result": (ctypes.c_int, [vp, i64, dp, dp, ctypes.c_void_p]),
         "goo_server_stats": (ctypes.c_int, [vp, dp]),
+        "goo_server_finished": (ctypes.c_int, [vp, ctypes.POINTER(i64), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "goo_server_cancel": (ctypes.c_int, [vp, i64]),
         "goo_server_fail_allocation": (ctypes.c_int, [vp, i64]),
         "goo_server_free": (ctypes.c_int, [vp]),
@@ -729,6 +730,17 @@ class Server:
             return None
         _check(rc)
         return th, err, {k: getattr(res, k) for k, _ in GooFitResult._fields_}
+
+    def finished(self, cap=1024):
+        """Tickets of the fits that finished since the previous call, oldest first."""
+        buf = (ctypes.c_int64 * cap)()
+        out = []
+        while True:
+            k = ctypes.c_int()
+            _check(lib.goo_server_finished(self.handle, buf, cap, ctypes.byref(k)))
+            out.extend(buf[:k.value])
+            if k.value < cap:
+                return out
 
     def cancel(self, ticket):
         """End a queued or active fit; its result then has status GOO_FIT_CANCELLED."""

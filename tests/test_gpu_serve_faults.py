@@ -5,7 +5,8 @@ server finishes bit for bit as it does in a server without the failure.
   * a fit cancelled while it waits for admission, and one cancelled while it is active,
     end with status GOO_FIT_CANCELLED, releasing their slot and event memory;
   * a fit whose admission fails its allocation (the server's test hook) ends with status
-    GOO_FIT_ALLOC_FAILED and the queue moves on.
+    GOO_FIT_ALLOC_FAILED and the queue moves on;
+  * the finished-ticket list reports every one of these fits exactly once.
 No GPU fault is involved: the failures are made on the host between steps.
 """
 import numpy as np
@@ -43,11 +44,17 @@ def setup(goo):
     return ctx, spec, model, theta, env, start
 
 
-def _run(server, tickets, max_rounds=5000, between=None):
+def _run(server, tickets, max_rounds=5000, between=None, drained=None):
     for r in range(max_rounds):
         if between is not None:
             between(r)
         q, a, d = server.step()
+        if drained is not None:
+            # tickets drained after this step: each finished, and each drained once
+            for t in server.finished(cap=2):
+                assert server.result(t) is not None and t not in drained
+                drained.append(t)
+            assert len(drained) == d
         if q == 0 and a == 0:
             break
     return {t: server.result(t) for t in tickets}
@@ -86,8 +93,12 @@ def test_failures_stay_with_their_fit(goo, setup):
             server.cancel(t_active_cancel)
             state["cancelled"] = True
 
-    res = _run(server, list(tickets.values()) + [t_active_cancel, t_queued_cancel, t_alloc_fail], between=between)
+    drained = []
+    everyone = list(tickets.values()) + [t_active_cancel, t_queued_cancel, t_alloc_fail]
+    res = _run(server, everyone, between=between, drained=drained)
     assert state["cancelled"]
+    # the finished list holds every fit once, failed ones included, and is empty afterwards
+    assert sorted(drained) == sorted(everyone) and server.finished() == []
     assert res[t_active_cancel][2]["status"] == goo.GOO_FIT_CANCELLED
     assert res[t_queued_cancel][2]["status"] == goo.GOO_FIT_CANCELLED
     assert res[t_alloc_fail][2]["status"] == goo.GOO_FIT_ALLOC_FAILED
