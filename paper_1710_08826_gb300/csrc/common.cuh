@@ -275,6 +275,11 @@ __device__ __forceinline__ ddf dd_warp_sum4(const ddf (&a)[4]) {
 
 // Natural logarithm of a positive double-float as a double-float, in FP32 arithmetic: the
 // exponent is split off exactly, x.hi = m 2^e with m in [sqrt(1/2), sqrt(2)), so that
+// ln 2 and log2(e) as double-floats (high part: the float nearest; low part: the float
+// nearest the remainder)
+constexpr float kLn2Hi = 0.693147182464599609375f, kLn2Lo = -1.9046542999577152e-09f;
+constexpr float kLog2eHi = 1.44269502162933349609375f, kLog2eLo = 1.925963033500011e-08f;
+
 // log x = e ln 2 + log m + log(1 + x.lo / x.hi) with |log m| < 0.35; logf(m) is within one
 // FP32 ulp of 0.35 (3e-8), e ln 2 is formed exactly in double-float and log(1 + r) = r to
 // below 1e-14 (|r| <= 2^-24).  About 3e-8 absolute.
@@ -285,7 +290,6 @@ __device__ __forceinline__ ddf log_dd(ddf x) {
     m *= 2.f;
     e -= 1;
   }
-  constexpr float kLn2Hi = 0.693147182464599609375f, kLn2Lo = -1.9046542999577152e-09f;
   const float fe = (float)e;
   const float ph = fe * kLn2Hi;
   ddf r = dd_make(ph, fmaf(fe, kLn2Hi, -ph) + fe * kLn2Lo);

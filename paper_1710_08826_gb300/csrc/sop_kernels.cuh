@@ -93,6 +93,9 @@ struct EvConst {
   LeafReg<T> leaf[K][L];
   T w_hi[K], w_lo[K];   // w_k (FP64 path: w_hi only)
   int nK, nobs;
+  // the pair kernel's exponents are in base 2: the rate of an exponential leaf and the slope
+  // of an Argus leaf times log2(e), rounded once from the float constants above
+  float b2[K][L];
 };
 
 // Value r * exp(a) of one leaf at x (+ xlo, the low part of a double-float coordinate when
@@ -543,38 +546,55 @@ __device__ __forceinline__ float2 pick(int col, float2 x0, float2 x1, float2 x2,
 }
 }  // namespace pk
 
-// Two events of one leaf: r * exp(a) per lane and, if GRAD, d log(leaf) / d par_j.
-template <bool GRAD>
+// Two events of one leaf, in the pair kernel's base-2 form: the value is r * 2^a2 per lane;
+// the leaf adds its a2 to `a` (the product's running exponent) and returns r and, if GRAD, the
+// raw derivative terms whose weighted sums the lanes collect.  A lane's sum becomes
+// sum_events c_k d log(leaf) / d par_j after one constant factor per lane (pair_lane_scale):
+//   Gauss    a2 = -z^2 / (2 ln 2), z = (x - mu) / sigma; raw (z, z^2), factor 1 / sigma;
+//   Exp      a2 = (lambda log2 e) x;                      raw x;
+//   Poly2    r = 1 + c_0 x + c_1 x^2;                      raw (x / r, x^2 / r), or with
+//            PQ (the product's only Poly2: its lanes are weighted by c_k / r instead of c_k,
+//            which needs no reciprocal) raw (x, x^2);
+//   Argus    u = 1 - x^2 / m0^2, r = x, a2 = (xi log2 e) u + p log2 u;
+//            raw (d/dm0 of the natural exponent, u, log2 u), factors (1, 1, ln 2).
 // `op` is the slot's opcode: L.op in the interpreter, a compile-time constant in a
 // specialised kernel (the switch then folds to one case).
-__device__ __forceinline__ void leaf_eval2(const LeafReg<float>& L, int op, float2 x, float2& r, float2& a, float2* d) {
+template <bool GRAD, bool PQ = false>
+__device__ __forceinline__ void leaf_eval2(const LeafReg<float>& L, float b2, int op, float2 x, float2& r, float2& a,
+                                           float2* d) {
   using namespace pk;
   const float* c = L.c;
+  constexpr float kHalfLog2e = -0.72134752f;  // -1 / (2 ln 2)
   d[0] = d[1] = d[2] = splat(0.f);
   switch (op) {
     case GOO_OP_GAUSS: {
       const float2 z = mul(sub(sub(x, splat(c[0])), splat(c[1])), splat(c[2]));
       const float2 zz = mul(z, z);
       r = splat(1.f);
-      a = mul(splat(-0.5f), zz);
+      a = fma(zz, splat(kHalfLog2e), a);
       if (GRAD) {
-        d[0] = mul(z, splat(c[2]));
-        d[1] = mul(zz, splat(c[2]));
+        d[0] = z;
+        d[1] = zz;
       }
       break;
     }
     case GOO_OP_EXPO:
       r = splat(1.f);
-      a = mul(splat(c[0]), x);
+      a = fma(splat(b2), x, a);
       if (GRAD) d[0] = x;
       break;
     case GOO_OP_POLY2: {
       r = fma(x, fma(splat(c[1]), x, splat(c[0])), splat(1.f));
-      a = splat(0.f);
       if (GRAD) {
-        const float2 ir = rcp(r);
-        d[0] = mul(x, ir);
-        d[1] = mul(mul(x, x), ir);
+        const float2 xx = mul(x, x);
+        if (PQ) {
+          d[0] = x;
+          d[1] = xx;
+        } else {
+          const float2 ir = rcp(r);
+          d[0] = mul(x, ir);
+          d[1] = mul(xx, ir);
+        }
       }
       break;
     }
@@ -583,36 +603,53 @@ __device__ __forceinline__ void leaf_eval2(const LeafReg<float>& L, int op, floa
       // a lane with u <= 0 has value 0 (r = 0); u is replaced by 1 there to keep it finite
       const bool p0 = u.x > 0.f, p1 = u.y > 0.f;
       const float2 us = make_float2(p0 ? u.x : 1.f, p1 ? u.y : 1.f);
-      const float2 lu = pk::log(us);
+      const float2 lu2 = make_float2(lg2(us.x), lg2(us.y));
       r = make_float2(p0 ? x.x : 0.f, p1 ? x.y : 0.f);
-      a = fma(splat(c[4]), lu, mul(splat(c[3]), us));
+      a = fma(splat(c[4]), lu2, fma(splat(b2), us, a));
       if (GRAD) {
         d[0] = mul(mul(splat(c[5]), sub(splat(1.f), us)), fma(splat(c[4]), rcp(us), splat(c[3])));
         d[1] = us;
-        d[2] = lu;
+        d[2] = lu2;
       }
       break;
     }
     default:
       r = splat(1.f);
-      a = splat(0.f);
   }
 }
 
-// Two events: log f per lane, ok per lane (f > 0) and, if GRAD, c_k and the leaf derivatives.
-// xl[k][l] holds the observable of leaf l of product k.
+// Leaf slot (k, l) of a signature is a Poly2 leaf that is the only one in its product: the
+// pair kernel weights its lanes by c_k / r (see leaf_eval2).
+__host__ __device__ constexpr bool sig_poly_q(unsigned long long sig, int k, int l, int L) {
+  int n = 0;
+  for (int t = 0; t < L; ++t) n += sig_op(sig, k * L + t) == GOO_OP_POLY2 ? 1 : 0;
+  return sig != 0 && n == 1 && sig_op(sig, k * L + l) == GOO_OP_POLY2;
+}
+__host__ __device__ constexpr bool sig_product_poly_q(unsigned long long sig, int k, int L) {
+  bool any = false;
+  for (int l = 0; l < L; ++l) any = any || sig_poly_q(sig, k, l, L);
+  return any;
+}
+
+// Two events: log2 f per lane, ok per lane (f > 0) and, if GRAD, c_k, q_k = c_k / r of the
+// product's PQ Poly2 leaf (sig_poly_q) and the leaves' raw derivative terms.  xl[k][l] holds
+// the observable of leaf l of product k; off_hi + off_lo = -log2 N_k.
 template <int K, int L, bool GRAD, unsigned long long SIG = 0>
 __device__ __forceinline__ void eval_event2(const EvConst<float, K, L>& P, const float (&off_hi)[K],
                                             const float (&off_lo)[K], const float2 (&xl)[K][L], float2& logf,
-                                            bool& ok0, bool& ok1, float2 (&ck)[K], float2 (&dk)[K][L][3]) {
+                                            bool& ok0, bool& ok1, float2 (&ck)[K], float2 (&qk)[K],
+                                            float2 (&dk)[K][L][3]) {
   using namespace pk;
-  float2 rk[K], ak[K];
+  float2 rk[K], ak[K], rq[K], rp[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    float2 r = splat(1.f), a = splat(0.f);
+    // the exponent starts at the offset's high part; r is the product of the leaves' factors,
+    // rq the same without the PQ Poly2 leaf's, rp that leaf's alone
+    float2 r = splat(1.f), a = splat(off_hi[k]);
+    rq[k] = rp[k] = splat(1.f);
 #pragma unroll
     for (int l = 0; l < L; ++l) {
-      float2 lr_, la_;
+      float2 lr_;
       if constexpr (SIG != 0) {
         constexpr int op_unused = 0;
         if (sig_op(SIG, k * L + l) == op_unused) {  // an empty slot: r = 1, a = 0
@@ -620,12 +657,17 @@ __device__ __forceinline__ void eval_event2(const EvConst<float, K, L>& P, const
           continue;
         }
       }
-      leaf_eval2<GRAD>(P.leaf[k][l], SIG != 0 ? sig_op(SIG, k * L + l) : P.leaf[k][l].op, xl[k][l], lr_, la_,
-                       dk[k][l]);
-      if (SIG == 0 || leaf_has_r(sig_op(SIG, k * L + l))) r = mul(r, lr_);
-      a = add(a, la_);
+      const int op = SIG != 0 ? sig_op(SIG, k * L + l) : P.leaf[k][l].op;
+      if (sig_poly_q(SIG, k, l, L)) {
+        leaf_eval2<GRAD, true>(P.leaf[k][l], P.b2[k][l], op, xl[k][l], lr_, a, dk[k][l]);
+        rp[k] = lr_;
+      } else {
+        leaf_eval2<GRAD, false>(P.leaf[k][l], P.b2[k][l], op, xl[k][l], lr_, a, dk[k][l]);
+        if (SIG == 0 || leaf_has_r(op)) rq[k] = mul(rq[k], lr_);
+      }
     }
-    a = add(add(a, splat(off_hi[k])), splat(off_lo[k]));
+    r = sig_product_poly_q(SIG, k, L) ? mul(rq[k], rp[k]) : rq[k];
+    a = add(a, splat(off_lo[k]));
     rk[k] = r;
     const bool on = SIG != 0 ? sig_product_used(SIG, k, L) : k < P.nK;
     ak[k] = make_float2((on && r.x != 0.f) ? a.x : -1e30f, (on && r.y != 0.f) ? a.y : -1e30f);
@@ -636,16 +678,26 @@ __device__ __forceinline__ void eval_event2(const EvConst<float, K, L>& P, const
   float2 S = splat(0.f);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    rk[k] = (SIG == 0 || sig_product_has_r(SIG, k, L)) ? mul(rk[k], pk::exp(sub(ak[k], M))) : pk::exp(sub(ak[k], M));
+    const float2 t = sub(ak[k], M);
+    const float2 e = make_float2(ex2(t.x), ex2(t.y));
+    if (SIG == 0 || sig_product_has_r(SIG, k, L)) {
+      rq[k] = mul(rq[k], e);  // the product's value without its PQ factor
+      rk[k] = sig_product_poly_q(SIG, k, L) ? mul(rq[k], rp[k]) : rq[k];
+    } else {
+      rk[k] = e;
+    }
     S = add(S, fma(splat(P.w_hi[k]), rk[k], mul(splat(P.w_lo[k]), rk[k])));
   }
   ok0 = S.x > 0.f && M.x > -1e29f;
   ok1 = S.y > 0.f && M.y > -1e29f;
-  logf = add(M, pk::log(make_float2(ok0 ? S.x : 1.f, ok1 ? S.y : 1.f)));
+  logf = add(M, make_float2(lg2(ok0 ? S.x : 1.f), lg2(ok1 ? S.y : 1.f)));
   if constexpr (GRAD) {
     const float2 invS = rcp(S);
 #pragma unroll
-    for (int k = 0; k < K; ++k) ck[k] = mul(rk[k], invS);
+    for (int k = 0; k < K; ++k) {
+      ck[k] = mul(rk[k], invS);
+      qk[k] = sig_product_poly_q(SIG, k, L) ? mul(rq[k], invS) : ck[k];
+    }
   }
 }
 
@@ -911,9 +963,9 @@ template <int K, int L, bool GRAD, unsigned long long SIG = 0>
 __device__ __forceinline__ void pair_step(const EvConst<float, K, L>& P, const float (&off_hi)[K],
                                           const float (&off_lo)[K], const float2 (&xl)[K][L], bool v0, bool v1,
                                           PairAcc<K, L>& S) {
-  float2 logf, ck[K], dk[K][L][3];
+  float2 logf, ck[K], qk[K], dk[K][L][3];
   bool ok0, ok1;
-  eval_event2<K, L, GRAD, SIG>(P, off_hi, off_lo, xl, logf, ok0, ok1, ck, dk);
+  eval_event2<K, L, GRAD, SIG>(P, off_hi, off_lo, xl, logf, ok0, ok1, ck, qk, dk);
   const bool m0 = v0 && ok0, m1 = v1 && ok1;
   S.bad += (unsigned)(v0 && !ok0) + (unsigned)(v1 && !ok1);
   if (m0 && m1) {
@@ -927,7 +979,7 @@ __device__ __forceinline__ void pair_step(const EvConst<float, K, L>& P, const f
 #pragma unroll
           for (int q = 0; q < 3; ++q)
             if (SIG == 0 || q < leaf_nder(sig_op(SIG, k * L + l)))  // a specialised kernel skips absent lanes
-              S.A[k][l][q] = pk::fma(ck[k], dk[k][l][q], S.A[k][l][q]);
+              S.A[k][l][q] = pk::fma(sig_poly_q(SIG, k, l, L) ? qk[k] : ck[k], dk[k][l][q], S.A[k][l][q]);
       }
     }
   } else {
@@ -940,6 +992,7 @@ __device__ __forceinline__ void pair_step(const EvConst<float, K, L>& P, const f
 #pragma unroll
         for (int k = 0; k < K; ++k) {
           const float c = lane ? ck[k].y : ck[k].x;
+          const float cq = lane ? qk[k].y : qk[k].x;
           (lane ? S.C[k].y : S.C[k].x) += c;
 #pragma unroll
           for (int l = 0; l < L; ++l)
@@ -947,7 +1000,7 @@ __device__ __forceinline__ void pair_step(const EvConst<float, K, L>& P, const f
             for (int q = 0; q < 3; ++q) {
               if (SIG != 0 && q >= leaf_nder(sig_op(SIG, k * L + l))) continue;
               float& A = lane ? S.A[k][l][q].y : S.A[k][l][q].x;
-              A = fmaf(c, lane ? dk[k][l][q].y : dk[k][l][q].x, A);
+              A = fmaf(sig_poly_q(SIG, k, l, L) ? cq : c, lane ? dk[k][l][q].y : dk[k][l][q].x, A);
             }
         }
       }
@@ -1057,6 +1110,13 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
   } else {
     load_offsets<float, K>(md, off_hi, off_lo);
     __syncthreads();  // barriers initialised before any thread waits on them
+  }
+  // the pair evaluation's exponents are in base 2: -log2 N_k = -log N_k log2(e), in double-float
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const ddf o = dd_mul(ddf{off_hi[k], off_lo[k]}, ddf{kLog2eHi, kLog2eLo});
+    off_hi[k] = o.hi;
+    off_lo[k] = o.lo;
   }
   PairAcc<K, L> S;
   S.bad = 0;
@@ -1192,9 +1252,10 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
     }
     __syncthreads();
   }
-  // lanes: the two Kahan sums as one double-float, the gradient lanes as the lane sums
+  // lanes: the two Kahan sums as one double-float (log2 f, turned into natural logarithms),
+  // the gradient lanes as the lane sums, each times its constant factor (leaf_eval2)
   ddf v[NS];
-  v[0] = dd_add(dd_make(S.lf.s.x, -S.lf.c.x), dd_make(S.lf.s.y, -S.lf.c.y));
+  v[0] = dd_mul(dd_add(dd_make(S.lf.s.x, -S.lf.c.x), dd_make(S.lf.s.y, -S.lf.c.y)), ddf{kLn2Hi, kLn2Lo});
   if constexpr (GRAD) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -1203,8 +1264,13 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
       for (int l = 0; l < L; ++l)
 #pragma unroll
         for (int q = 0; q < 3; ++q)
-          if (a_present<K, L, SIG>(k, l, q))
-            v[a_lane<K, L, SIG>(k, l, q)] = dd_add(ddf{S.A[k][l][q].x, 0.f}, ddf{S.A[k][l][q].y, 0.f});
+          if (a_present<K, L, SIG>(k, l, q)) {
+            const int op = SIG != 0 ? sig_op(SIG, k * L + l) : P.leaf[k][l].op;
+            ddf t = dd_add(ddf{S.A[k][l][q].x, 0.f}, ddf{S.A[k][l][q].y, 0.f});
+            if (op == GOO_OP_GAUSS && q < 2) t = dd_mul(t, ddf{P.leaf[k][l].c[2], 0.f});
+            if (op == GOO_OP_ARGUS && q == 2) t = dd_mul(t, ddf{kLn2Hi, kLn2Lo});
+            v[a_lane<K, L, SIG>(k, l, q)] = t;
+          }
     }
   }
   if (fused_norm)

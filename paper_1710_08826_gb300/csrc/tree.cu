@@ -881,6 +881,10 @@ static EvConst<T, K, L> make_evconst(const ModelDev& h) {
       R.op = LD.op;
       R.col = LD.col;
       for (int j = 0; j < 6; ++j) R.c[j] = (sizeof(T) == 4) ? (T)LD.f[j] : (T)LD.d[j];
+      // base-2 rates of the pair kernel, from the float constants the other leaves' terms use
+      constexpr double kLog2e = 1.4426950408889634074;
+      if (LD.op == GOO_OP_EXPO) P.b2[k][l] = (float)((double)LD.f[0] * kLog2e);
+      if (LD.op == GOO_OP_ARGUS) P.b2[k][l] = (float)((double)LD.f[3] * kLog2e);
     }
   }
   return P;

@@ -81,7 +81,9 @@ def _load():
         raise ImportError(f"{_LIB_PATH} is missing: build it with "
                           "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
     lib = ctypes.CDLL(_LIB_PATH)
-    vp, dp, i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64
+    # double* arguments are declared void*: they take ctypes pointers, byref() and arrays as
+    # before, and also a numpy array's address as a plain int (the per-evaluation calls)
+    vp, dp, i64 = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64
     sig = {
         "goo_init": (ctypes.c_int, [ctypes.c_int, vp, ctypes.POINTER(vp)]),
         "goo_finalize": (ctypes.c_int, [vp]),
@@ -165,11 +167,14 @@ def _dbuf(values, n=None):
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+_PRECISION = {"f64": GOO_F64, "fp64": GOO_F64, "float64": GOO_F64,
+              "f32": GOO_F32, "fp32": GOO_F32, "float32": GOO_F32, "mixed": GOO_F32}
+
+
 def precision_code(precision):
     if precision in (GOO_F64, GOO_F32):
         return precision
-    return {"f64": GOO_F64, "fp64": GOO_F64, "float64": GOO_F64,
-            "f32": GOO_F32, "fp32": GOO_F32, "float32": GOO_F32, "mixed": GOO_F32}[precision]
+    return _PRECISION[precision]
 
 
 class Context:
@@ -466,6 +471,14 @@ class Model:
         _check(lib.goo_model_build(ctx.handle, nodes, nn, self.n_params, len(spec["observables"]), lo_p, hi_p,
                                    ctypes.byref(h)))
         self.handle = h
+        # per-model argument and result buffers of the evaluation calls, with their addresses
+        # taken once (a Model is used from one thread at a time)
+        self._tb = np.zeros(self.n_params)
+        self._ob = np.zeros(3 + self.n_params)
+        self._gb = np.zeros(self.n_params)
+        self._nb = ctypes.c_double()
+        self._tb_a, self._ob_a, self._gb_a = self._tb.ctypes.data, self._ob.ctypes.data, self._gb.ctypes.data
+        self._nb_ref = ctypes.byref(self._nb)
         self.mc = mc
         self.set_norm(norm or spec["norm"], mc)
         if spec.get("coef") == "polar":   # (magnitude, phase) coefficient parameters
@@ -491,6 +504,13 @@ class Model:
     def _theta(self, theta):
         return _dbuf(theta, self.n_params)
 
+    def _theta_addr(self, theta):
+        # theta copied into the model's buffer; its address
+        if len(theta) != self.n_params:
+            raise ValueError(f"expected {self.n_params} values, got {len(theta)}")
+        self._tb[:] = theta
+        return self._tb_a
+
     def normalise(self, theta, precision="f64"):
         t, tp = self._theta(theta)
         out = np.zeros(max(self.n_components, 1))
@@ -499,18 +519,14 @@ class Model:
         return out
 
     def nll(self, ds, theta, precision="f64"):
-        t, tp = self._theta(theta)
-        out = ctypes.c_double()
-        _check(lib.goo_nll(self.handle, ds.handle, tp, precision_code(precision), ctypes.byref(out)))
-        return out.value
+        tp = self._theta_addr(theta)
+        _check(lib.goo_nll(self.handle, ds.handle, tp, precision_code(precision), self._nb_ref))
+        return self._nb.value
 
     def nll_grad(self, ds, theta, precision="f64"):
-        t, tp = self._theta(theta)
-        out = ctypes.c_double()
-        g = np.zeros(self.n_params)
-        _check(lib.goo_nll_grad(self.handle, ds.handle, tp, precision_code(precision), ctypes.byref(out),
-                                g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
-        return out.value, g
+        tp = self._theta_addr(theta)
+        _check(lib.goo_nll_grad(self.handle, ds.handle, tp, precision_code(precision), self._nb_ref, self._gb_a))
+        return self._nb.value, self._gb.copy()
 
     def nll_grad_streamed(self, ds, host_columns, theta, n_chunks=8):
         """FP32 NLL and gradient of pinned float32 host columns (torch tensors made with
@@ -537,11 +553,10 @@ class Model:
         return out
 
     def nll_partial(self, ds, begin, end, theta, precision="f64", want_grad=True):
-        t, tp = self._theta(theta)
-        out = np.zeros(3 + self.n_params)
+        tp = self._theta_addr(theta)
         _check(lib.goo_nll_partial(self.handle, ds.handle, int(begin), int(end), tp, precision_code(precision),
-                                   int(bool(want_grad)), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
-        return out
+                                   int(bool(want_grad)), self._ob_a))
+        return self._ob.copy()
 
     def fit(self, ds, theta0, free=None, scale=None, precision="f32", gradient="adjoint", max_iter=500,
             edm_tol=1e-6, polish=True, errors=True, refine=True):
