@@ -556,7 +556,7 @@ __device__ __forceinline__ float2 pick(int col, float2 x0, float2 x1, float2 x2,
 //            PQ (the product's only Poly2: its lanes are weighted by c_k / r instead of c_k,
 //            which needs no reciprocal) raw (x, x^2);
 //   Argus    u = 1 - x^2 / m0^2, r = x, a2 = (xi log2 e) u + p log2 u;
-//            raw (d/dm0 of the natural exponent, u, log2 u), factors (1, 1, ln 2).
+//            raw ((1 - u)(p / u + xi), u, log2 u), factors (2 / m0, 1, ln 2).
 // `op` is the slot's opcode: L.op in the interpreter, a compile-time constant in a
 // specialised kernel (the switch then folds to one case).
 template <bool GRAD, bool PQ = false>
@@ -607,7 +607,7 @@ __device__ __forceinline__ void leaf_eval2(const LeafReg<float>& L, float b2, in
       r = make_float2(p0 ? x.x : 0.f, p1 ? x.y : 0.f);
       a = fma(splat(c[4]), lu2, fma(splat(b2), us, a));
       if (GRAD) {
-        d[0] = mul(mul(splat(c[5]), sub(splat(1.f), us)), fma(splat(c[4]), rcp(us), splat(c[3])));
+        d[0] = mul(sub(splat(1.f), us), fma(splat(c[4]), rcp(us), splat(c[3])));
         d[1] = us;
         d[2] = lu2;
       }
@@ -686,11 +686,13 @@ __device__ __forceinline__ void eval_event2(const EvConst<float, K, L>& P, const
     } else {
       rk[k] = e;
     }
-    S = add(S, fma(splat(P.w_hi[k]), rk[k], mul(splat(P.w_lo[k]), rk[k])));
+    S = fma(splat(P.w_hi[k]), rk[k], fma(splat(P.w_lo[k]), rk[k], S));
   }
-  ok0 = S.x > 0.f && M.x > -1e29f;
-  ok1 = S.y > 0.f && M.y > -1e29f;
-  logf = add(M, make_float2(lg2(ok0 ? S.x : 1.f), lg2(ok1 ? S.y : 1.f)));
+  // S > 0 also excludes an event where no product is present (M = -1e30): every product then
+  // has r = 0 or w = 0.  The logarithm of a lane with S <= 0 is not used.
+  ok0 = S.x > 0.f;
+  ok1 = S.y > 0.f;
+  logf = add(M, make_float2(lg2(S.x), lg2(S.y)));
   if constexpr (GRAD) {
     const float2 invS = rcp(S);
 #pragma unroll
@@ -952,7 +954,8 @@ struct EventOcc2 {
 // Per-thread accumulators of the pair kernel.
 template <int K, int L>
 struct PairAcc {
-  Kahan2 lf;
+  Kahan2 lf;   // compensated sum of the tiles' subtotals of log2 f
+  float2 lt;   // this tile's subtotal (at most kPairsPerThread pairs, plain FP32)
   float2 C[K];
   float2 A[K][L][3];
   unsigned bad;
@@ -969,7 +972,7 @@ __device__ __forceinline__ void pair_step(const EvConst<float, K, L>& P, const f
   const bool m0 = v0 && ok0, m1 = v1 && ok1;
   S.bad += (unsigned)(v0 && !ok0) + (unsigned)(v1 && !ok1);
   if (m0 && m1) {
-    S.lf.add(logf);
+    S.lt = pk::add(S.lt, logf);
     if constexpr (GRAD) {
 #pragma unroll
       for (int k = 0; k < K; ++k) {
@@ -987,7 +990,7 @@ __device__ __forceinline__ void pair_step(const EvConst<float, K, L>& P, const f
 #pragma unroll
     for (int lane = 0; lane < 2; ++lane) {
       if (!(lane ? m1 : m0)) continue;
-      S.lf.add_lane(lane, lane ? logf.y : logf.x);
+      (lane ? S.lt.y : S.lt.x) += lane ? logf.y : logf.x;
       if constexpr (GRAD) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -1120,6 +1123,7 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
   }
   PairAcc<K, L> S;
   S.bad = 0;
+  S.lt = splat(0.f);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     S.C[k] = splat(0.f);
@@ -1189,6 +1193,8 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
         for (int l = 0; l < L; ++l) xl[k][l] = reinterpret_cast<const float2*>(s_col + coff[k][l])[pr];
       pair_step<K, L, GRAD, SIG>(P, off_hi, off_lo, xl, true, true, S);
     }
+    S.lf.add(S.lt);
+    S.lt = splat(0.f);
     // this warp is done with buffer st; the warp that completes the count for tile j refills
     // it: every warp's reads of the buffer precede its count (block-scope fences around the
     // shared atomic), and the refilling thread orders them before the asynchronous copy
@@ -1233,6 +1239,7 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
   if (!failed) {
     if (blockIdx.x == 0 && A > begin) ragged(begin, A);
     if (blockIdx.x == gridDim.x - 1 && end > B) ragged(B, end);
+    S.lf.add(S.lt);
   }
   if (failed && lane == 0) atomicOr(&s_fail, 1u);
   if (direct) {
@@ -1268,6 +1275,7 @@ __global__ void __launch_bounds__(kBlock, EventOcc2<K, L, GRAD>::value)
             const int op = SIG != 0 ? sig_op(SIG, k * L + l) : P.leaf[k][l].op;
             ddf t = dd_add(ddf{S.A[k][l][q].x, 0.f}, ddf{S.A[k][l][q].y, 0.f});
             if (op == GOO_OP_GAUSS && q < 2) t = dd_mul(t, ddf{P.leaf[k][l].c[2], 0.f});
+            if (op == GOO_OP_ARGUS && q == 0) t = dd_mul(t, ddf{P.leaf[k][l].c[5], 0.f});
             if (op == GOO_OP_ARGUS && q == 2) t = dd_mul(t, ddf{kLn2Hi, kLn2Lo});
             v[a_lane<K, L, SIG>(k, l, q)] = t;
           }
