@@ -57,7 +57,7 @@ int nll_common(goo_model* m, const goo_dataset* ds, const double* theta, int pre
   } else {
     const bool fuse = ds->n > 0 && !ds->w64 && sop_norm_in_event(m, precision, grad);
     GOO_TRY(sop_prepare(m, theta, precision, fuse));
-    ctx->scratch.result_host[kResultFlag] = 0.0;
+    arm_result_mapped(ctx);
     if (ds->n > 0) GOO_TRY(sop_events(m, ds, 0, ds->n, precision, grad, 0, fuse, ctx->scratch.result_host));
     if (ds->n == 0) {
       res[0] = 0.0;
@@ -234,7 +234,7 @@ int goo_nll_partial(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t 
     const bool fuse = end > begin && !ds->w64 && sop_norm_in_event(m, precision, want_grad != 0);
     GOO_TRY(sop_prepare(m, theta, precision, fuse));
     if (end > begin) {
-      ctx->scratch.result_host[kResultFlag] = 0.0;
+      arm_result_mapped(ctx);
       GOO_TRY(sop_events(m, ds, begin, end, precision, want_grad != 0, 1, fuse, ctx->scratch.result_host));
       GOO_TRY(read_result_mapped(ctx, 3 + P, res));
     } else {

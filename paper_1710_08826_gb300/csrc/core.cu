@@ -106,16 +106,28 @@ static void fold_timings(goo_ctx* ctx) {
   ctx->pending.clear();
 }
 
-// Waits for the completion word of the mapped result record that an event kernel writes
-// (sop_events with result = scratch.result_host), then copies `n` doubles.  The host polls
-// the word for up to 2 ms, then waits on the stream, which also reports a failed launch.
+// Waits until the first `n` fields of the mapped result record that a kernel writes (armed
+// with kResultSentinel before its launch) all hold values, then copies them.  Each field is
+// one aligned 8-byte store of the kernel, so a field read without the sentinel is final.  The
+// host polls for up to 2 ms, then waits on the stream, which also reports a failed launch.
+void arm_result_mapped(goo_ctx* ctx) {
+  volatile unsigned long long* rec = reinterpret_cast<volatile unsigned long long*>(ctx->scratch.result_host);
+  for (int i = 0; i < kResultDoubles; ++i) rec[i] = kResultSentinel;
+  ctx->scratch.result_host[kResultFlag] = 0.0;
+}
+
 int read_result_mapped(goo_ctx* ctx, int n, double* dst) {
-  volatile double* flag = ctx->scratch.result_host + kResultFlag;
+  volatile unsigned long long* rec = reinterpret_cast<volatile unsigned long long*>(ctx->scratch.result_host);
   const auto t0 = std::chrono::steady_clock::now();
-  for (unsigned it = 0; *flag == 0.0; ++it) {
+  int i = 0;
+  for (unsigned it = 0;; ++it) {
+    while (i < n && rec[i] != kResultSentinel) ++i;
+    if (i == n) break;
     if ((it & 255u) == 0 && std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(2)) {
       GOO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-      if (*flag == 0.0) return set_error(GOO_ERR_STATE, "the event kernel finished without its completion word");
+      for (i = 0; i < n; ++i)
+        if (rec[i] == kResultSentinel)
+          return set_error(GOO_ERR_STATE, "the kernel finished without writing field %d of its result record", i);
       break;
     }
   }
@@ -125,7 +137,7 @@ int read_result_mapped(goo_ctx* ctx, int n, double* dst) {
 }
 
 MappedResult::MappedResult(goo_ctx* c) : ctx(c) {
-  ctx->scratch.result_host[kResultFlag] = 0.0;
+  arm_result_mapped(ctx);
   ctx->scratch.result_out = ctx->scratch.result_host;
 }
 MappedResult::~MappedResult() { ctx->scratch.result_out = ctx->scratch.result; }
