@@ -468,7 +468,8 @@ int goo_nll_partial(goo_model* model, const goo_dataset* ds, int64_t begin, int6
  * owning dataset of capacity >= n_events, as goo_dataset_update would) from n_events events
  * of pinned float32 host columns (host_cols[c], one per dataset column) and returns the FP32
  * NLL and adjoint gradient of a sum-of-products model at theta over them.  The events are
- * split into n_chunks (1..64) chunks on multiples of 2048 events: the copy engine moves chunk
+ * split into n_chunks (1..64) chunks on multiples of 3072 events (the event kernel's column
+ * tile): the copy engine moves chunk
  * c + 1 over the host link (on a second stream of the context) while chunk c is converted to
  * float64, range-checked and evaluated on the context's stream, so that only the last
  * chunk's evaluation follows the transfer.  The chunks' records are added in chunk order with

@@ -62,6 +62,10 @@ constexpr int kMaxSlots = 64;      // reduction lanes of one kernel
 // the compute-bound staged kernels keep two 256-thread blocks, which measured faster).
 constexpr int kStagedBlock = 512;
 constexpr int kBlock = 256;        // threads per block of the likelihood kernels
+// the pair kernel of the sum-of-products models: column tiles in flight per block (bulk
+// copies) and event pairs per thread per tile (a tile: 2 * 6 * 256 = 3072 events)
+constexpr int kEventStages = 2;
+constexpr int kPairsPerThread = 6;
 constexpr int kResultDoubles = 4 + kMaxParams + 60;  // result record of one evaluation
 constexpr int kPinnedResult = 256;                   // offset of the result in host_pinned
 // Completion word after the result record: the kernels set it to 1 once the record is

@@ -650,8 +650,9 @@ int goo_nll_grad_streamed(goo_model* m, goo_dataset* ds, const float* const* hos
   GOO_TRY(sop_prepare(m, theta, GOO_F32, fuse));
   unsigned long long* bad = (unsigned long long*)(sc.counters + 8);
   GOO_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), ctx->stream));
-  // chunk boundaries on multiples of 2048 events (whole column tiles of the event kernel)
-  const int64_t step = ((n_events + n_chunks - 1) / n_chunks + 2047) / 2048 * 2048;
+  // chunk boundaries on multiples of the event kernel's column tile
+  constexpr int64_t kTile = 2 * kPairsPerThread * kBlock;
+  const int64_t step = ((n_events + n_chunks - 1) / n_chunks + kTile - 1) / kTile * kTile;
   int nc = 0;
   const goo_dataset& dsv = *ds;
   for (int64_t b = 0; b < n_events; b += step, ++nc) {

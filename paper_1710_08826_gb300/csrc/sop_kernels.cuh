@@ -943,9 +943,6 @@ __device__ __forceinline__ void event_finish_fused(const ddf (&v)[EventLanes<flo
   result_complete(result, P > 1 ? P : 1);
 }
 
-constexpr int kEventStages = 3;     // column tiles in flight per block (TMA bulk copies)
-constexpr int kPairsPerThread = 4;  // event pairs per thread per tile
-
 template <int K, int L, bool GRAD>
 struct EventOcc2 {
   static constexpr int value = (K * L <= 6 && !GRAD) ? 3 : 2;
