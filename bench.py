@@ -41,35 +41,35 @@ _TD3_SRC = _COH_SRC + ['paper_1710_08826_gb300/csrc/timeterms.cuh']
 ISSUE_PEAK = 152 * 4 * 2.07e9
 
 NCU_RECORDS = {
-    "sop_nll_grad_f32": {"bytes": 127_931_904, "events": 10_000_000, "duration_ns": 48928, "warp_inst": 26_078_326, "issue_active": 0.5435,
-        "sources": _SOP_SRC, "sha256": "1053be640239c11c7d88489f41db6db6bf781699a66b244f19327ee80ac76443",
+    "sop_nll_grad_f32": {"bytes": 127_851_008, "events": 10_000_000, "duration_ns": 40864, "warp_inst": 21_770_696, "issue_active": 0.5403,
+        "sources": _SOP_SRC, "sha256": "b5b7bee304cebaa2d5d679f5cec5fc4a6d297363bec0540e3fc50d0c8ea7b181",
         "profile": "profiles/sop_event2_kernel_f32_c2_10M.md"},
-    "sop_nll_f64": {"bytes": 242_742_528, "events": 10_000_000, "duration_ns": 2504448, "fp64_pipe": 0.8624, "fp64_ops": {"dfma": 649_995_818, "dadd": 340_076_105, "dmul": 259_998_770},
-        "sources": _SOP_SRC, "sha256": "1053be640239c11c7d88489f41db6db6bf781699a66b244f19327ee80ac76443",
+    "sop_nll_f64": {"bytes": 243_686_912, "events": 10_000_000, "duration_ns": 2504160, "fp64_pipe": 0.8625, "fp64_ops": {"dfma": 649_995_818, "dadd": 340_076_105, "dmul": 259_998_770},
+        "sources": _SOP_SRC, "sha256": "b5b7bee304cebaa2d5d679f5cec5fc4a6d297363bec0540e3fc50d0c8ea7b181",
         "profile": "profiles/sop_event_kernel_f64_c2_10M.md"},
-    "coh_nll_grad_f32": {"bytes": 323_043_328, "events": 5_000_000, "duration_ns": 63680, "warp_inst": 30_973_750, "issue_active": 0.4606,
-        "sources": _COH_SRC, "sha256": "f0d6e196cc8aa2a6b505f428804b3e4db0aa6aa6551b35f778406746dca2b036",
+    "coh_nll_grad_f32": {"bytes": 323_078_912, "events": 5_000_000, "duration_ns": 62912, "warp_inst": 30_962_164, "issue_active": 0.4583,
+        "sources": _COH_SRC, "sha256": "8edfd511a31452ddc160812c27fbac6848ccab01e9671266116c75514580e8d5",
         "profile": "profiles/coh_nll_staged_kernel_f32_c3_5M.md"},
-    "coh_nll_f64": {"bytes": 643_054_848, "events": 5_000_000, "duration_ns": 773888, "fp64_pipe": 0.8701, "fp64_ops": {"dfma": 165_155_649, "dadd": 135_077_825, "dmul": 105_000_000},
-        "sources": _COH_SRC, "sha256": "f0d6e196cc8aa2a6b505f428804b3e4db0aa6aa6551b35f778406746dca2b036",
+    "coh_nll_f64": {"bytes": 643_060_224, "events": 5_000_000, "duration_ns": 773056, "fp64_pipe": 0.8699, "fp64_ops": {"dfma": 165_155_649, "dadd": 135_077_825, "dmul": 105_000_000},
+        "sources": _COH_SRC, "sha256": "8edfd511a31452ddc160812c27fbac6848ccab01e9671266116c75514580e8d5",
         "profile": "profiles/coh_nll_kernel_f64_c3_5M.md"},
-    "coh_ls_mc_f32": {"bytes": 8_068_352, "events": 1_000_000, "duration_ns": 91744, "warp_inst": 65_106_262, "issue_active": 0.6317,
-        "sources": _COH_SRC, "sha256": "f0d6e196cc8aa2a6b505f428804b3e4db0aa6aa6551b35f778406746dca2b036",
+    "coh_ls_mc_f32": {"bytes": 8_068_608, "events": 1_000_000, "duration_ns": 91424, "warp_inst": 65_097_718, "issue_active": 0.6327,
+        "sources": _COH_SRC, "sha256": "8edfd511a31452ddc160812c27fbac6848ccab01e9671266116c75514580e8d5",
         "profile": "profiles/coh_ls_kernel_f32_c3_floating_5M.md"},
-    "coh_ls_grad_f32": {"bytes": 40_095_744, "events": 5_000_000, "duration_ns": 423104, "warp_inst": 313_731_120, "issue_active": 0.6429,
-        "sources": _COH_SRC, "sha256": "f0d6e196cc8aa2a6b505f428804b3e4db0aa6aa6551b35f778406746dca2b036",
+    "coh_ls_grad_f32": {"bytes": 40_095_744, "events": 5_000_000, "duration_ns": 423008, "warp_inst": 313_878_490, "issue_active": 0.6404,
+        "sources": _COH_SRC, "sha256": "8edfd511a31452ddc160812c27fbac6848ccab01e9671266116c75514580e8d5",
         "profile": "profiles/coh_ls_kernel_f32_c3_floating_5M.md"},
-    "td3_nll_grad_f32": {"bytes": 523_827_712, "events": 2_000_000, "duration_ns": 138144, "warp_inst": 71_377_692, "issue_active": 0.5413,
-        "sources": _TD3_SRC, "sha256": "91cfbc43f3e3e573540c20890f69c314a1690267d2eefe105eb75e167e8c9883",
+    "td3_nll_grad_f32": {"bytes": 523_528_960, "events": 2_000_000, "duration_ns": 134208, "warp_inst": 71_383_984, "issue_active": 0.5488,
+        "sources": _TD3_SRC, "sha256": "9206daba8ca1202a1f75b606b6e9dcc70e0e3ff508acad2bd8eb7302e4691577",
         "profile": "profiles/td3_nll_kernel_td3_2M.md"},
-    "td3_nll_f64": {"bytes": 979_146_240, "events": 2_000_000, "duration_ns": 1611968, "fp64_pipe": 0.8524, "fp64_ops": {"dfma": 391_298_265, "dadd": 152_090_307, "dmul": 214_414_797},
-        "sources": _TD3_SRC, "sha256": "91cfbc43f3e3e573540c20890f69c314a1690267d2eefe105eb75e167e8c9883",
+    "td3_nll_f64": {"bytes": 979_147_776, "events": 2_000_000, "duration_ns": 1610336, "fp64_pipe": 0.8524, "fp64_ops": {"dfma": 391_298_265, "dadd": 152_090_307, "dmul": 214_414_797},
+        "sources": _TD3_SRC, "sha256": "9206daba8ca1202a1f75b606b6e9dcc70e0e3ff508acad2bd8eb7302e4691577",
         "profile": "profiles/td3_nll_kernel_td3_2M.md"},
-    "td4_nll_grad_f32": {"bytes": 171_071_744, "events": 2_000_000, "duration_ns": 74528, "warp_inst": 50_891_205, "issue_active": 0.6670,
-        "sources": _TD4_SRC, "sha256": "89a23f1bf14a2f8e55c56d8a65caf0784be88c2bad503c7ed423a12bf2f7f701",
+    "td4_nll_grad_f32": {"bytes": 170_844_416, "events": 2_000_000, "duration_ns": 73376, "warp_inst": 50_880_472, "issue_active": 0.6616,
+        "sources": _TD4_SRC, "sha256": "a18cdcbcba932856f50d1c7c169e18e127688fc7059da025d03fe68b40246db1",
         "profile": "profiles/td4_nll_f32_kernel_c4_2M.md"},
-    "td4_nll_f64": {"bytes": 339_160_320, "events": 2_000_000, "duration_ns": 1384672, "fp64_pipe": 0.8560, "fp64_ops": {"dfma": 351_287_209, "dadd": 112_088_842, "dmul": 178_181_349},
-        "sources": _TD4_SRC, "sha256": "89a23f1bf14a2f8e55c56d8a65caf0784be88c2bad503c7ed423a12bf2f7f701",
+    "td4_nll_f64": {"bytes": 339_123_712, "events": 2_000_000, "duration_ns": 1383968, "fp64_pipe": 0.8559, "fp64_ops": {"dfma": 351_287_209, "dadd": 112_088_842, "dmul": 178_181_349},
+        "sources": _TD4_SRC, "sha256": "a18cdcbcba932856f50d1c7c169e18e127688fc7059da025d03fe68b40246db1",
         "profile": "profiles/td4_nll_f64_kernel_c4_2M.md"},
 }
 
