@@ -217,6 +217,50 @@ __device__ __forceinline__ void td4_event(const Td4Args<T>& a, const T (&ar)[KB]
   }
 }
 
+// The FP32 form of td4_event in the staged kernel.  The amplitudes come as (re, im) pairs
+// straight from the float4 planes, and A = sum c_k a_k is formed from two packed sums,
+// (sum cr_k re_k, sum cr_k im_k) and (sum ci_k re_k, sum ci_k im_k), B likewise: four packed
+// FMAs per amplitude instead of eight scalar ones.  log2 R is accumulated (td4_finish scales
+// the FP32 sum by ln 2 once per thread) and 1/R is the hardware reciprocal.
+template <int KB, bool GRAD>
+__device__ __forceinline__ void td4_event_f32(const Td4Args<float>& a, const float2 (&am)[KB], float t,
+                                              TdAcc<float, KB>& acc) {
+  using namespace pk;
+  float2 P1 = splat(0.f), P2 = splat(0.f), Q1 = splat(0.f), Q2 = splat(0.f);
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    P1 = fma(splat(a.cr[k]), am[k], P1);
+    P2 = fma(splat(a.ci[k]), am[k], P2);
+    Q1 = fma(splat(a.br[k]), am[k], Q1);
+    Q2 = fma(splat(a.bi[k]), am[k], Q2);
+  }
+  const float Ar = P1.x - P2.y, Ai = P1.y + P2.x, Br = Q1.x - Q2.y, Bi = Q1.y + Q2.x;
+  TimeTerms<float> tt;
+  time_terms<float>(a, t, tt);
+  const float AA = Ar * Ar + Ai * Ai, BB = Br * Br + Bi * Bi;
+  const float ABr = Ar * Br + Ai * Bi, ABi = Ai * Br - Ar * Bi;  // A conj(B)
+  const float R = AA * tt.P + BB * tt.Q + ABr * tt.Tsh + ABi * tt.Ts;
+  if (!(R > 0.f)) {
+    acc.bad++;
+    return;
+  }
+  acc.lf32.add(lg2(R));
+  if constexpr (GRAD) {
+    const float invR = rcp(R);
+    const float c1 = 2.f * tt.P * invR, sh = tt.Tsh * invR, ss = tt.Ts * invR;
+    const float Vr = c1 * Ar + sh * Br - ss * Bi;
+    const float Vi = -c1 * Ai - sh * Bi - ss * Br;
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      acc.lre[k] += am[k].x * Vr - am[k].y * Vi;     // Re(a_k V) / R
+      acc.lim[k] += -(am[k].x * Vi + am[k].y * Vr);  // -Im(a_k V) / R
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      acc.lt[j] += (AA * tt.d[j][0] + BB * tt.d[j][1] + ABr * tt.d[j][2] + ABi * tt.d[j][3]) * invR;
+  }
+}
+
 // Block and last-block reductions, then the FP64 combination with the normalisation terms the
 // host formed from the Gram matrix (they depend on theta and the MC sample only, not on the
 // events: an O(K^2) quadratic form, whose FP64 latency chain had been the last block's tail).
@@ -226,7 +270,8 @@ __device__ __forceinline__ void td4_finish(const Td4Args<T>& a, TdAcc<T, KB>& ac
                                            ddf* s_red, unsigned* s_bad) {
   constexpr int NS = TdLanes<KB, GRAD>::NS;
   ddf v[NS];
-  v[0] = (sizeof(T) == 4) ? acc.lf32.value() : dd_from_double(acc.lf64);
+  // the FP32 kernel sums log2 R (td4_event_f32)
+  v[0] = (sizeof(T) == 4) ? dd_mul(acc.lf32.value(), ddf{kLn2Hi, kLn2Lo}) : dd_from_double(acc.lf64);
   if constexpr (GRAD) {
 #pragma unroll
     for (int k = 0; k < KB; ++k) {
@@ -385,18 +430,16 @@ __global__ void __launch_bounds__(kBlock, 2) td4_nll_f32_kernel(const __grid_con
       for (int e = threadIdx.x; e < TE; e += blockDim.x) {
         const int64_t i = t * TE + e;
         if (!staged && (i < begin || i >= end)) continue;
-        float ar[KB], ai[KB];
+        float2 am[KB];
 #pragma unroll
         for (int p = 0; p < KB / 2; ++p) {
           float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
           if (p < planes) v = staged ? sb[(size_t)p * TE + e] : __ldg(cache + (int64_t)p * n + i);
-          ar[2 * p] = v.x;
-          ai[2 * p] = v.y;
-          ar[2 * p + 1] = v.z;
-          ai[2 * p + 1] = v.w;
+          am[2 * p] = make_float2(v.x, v.y);
+          am[2 * p + 1] = make_float2(v.z, v.w);
         }
         const float tv = staged ? stt[e] : __ldg(tcol + i);
-        td4_event<float, KB, GRAD>(a, ar, ai, tv, acc);
+        td4_event_f32<KB, GRAD>(a, am, tv, acc);
       }
     }
     if (__syncthreads_or(!ok_wait)) {
