@@ -843,15 +843,37 @@ __global__ void __launch_bounds__(kBlock, 2)
         }
     }
     T Ar = a.cr[KB], Ai = a.ci[KB], Br = a.cr[KB], Bi = a.ci[KB];  // the NR amplitude is 1 for both
+    if constexpr (sizeof(T) == 4) {
+      // FP32: the sums as packed (re, im) FMAs on the planes' halves, (sum cr_k a_k) and
+      // (sum ci_k a_k) per cache, combined once: four packed FMAs per amplitude, not eight
+      using namespace pk;
+      float2 P1 = make_float2(Ar, Ai), P2 = splat(0.f), Q1 = make_float2(Br, Bi), Q2 = splat(0.f);
 #pragma unroll
-    for (int k = 0; k < KB; ++k) {
-      if (k >= nbw) break;
-      T ar, ai, br, bi;
-      get(k, i, ar, ai, br, bi);
-      Ar += a.cr[k] * ar - a.ci[k] * ai;
-      Ai += a.cr[k] * ai + a.ci[k] * ar;
-      Br += a.cr[k] * br - a.ci[k] * bi;
-      Bi += a.cr[k] * bi + a.ci[k] * br;
+      for (int k = 0; k < KB; ++k) {
+        if (k >= nbw) break;
+        const float4 va = pa[k / 2], vb = pb[k / 2];
+        const float2 ak = (k & 1) ? make_float2(va.z, va.w) : make_float2(va.x, va.y);
+        const float2 bk = (k & 1) ? make_float2(vb.z, vb.w) : make_float2(vb.x, vb.y);
+        P1 = fma(splat(a.cr[k]), ak, P1);
+        P2 = fma(splat(a.ci[k]), ak, P2);
+        Q1 = fma(splat(a.cr[k]), bk, Q1);
+        Q2 = fma(splat(a.ci[k]), bk, Q2);
+      }
+      Ar = P1.x - P2.y;
+      Ai = P1.y + P2.x;
+      Br = Q1.x - Q2.y;
+      Bi = Q1.y + Q2.x;
+    } else {
+#pragma unroll
+      for (int k = 0; k < KB; ++k) {
+        if (k >= nbw) break;
+        T ar, ai, br, bi;
+        get(k, i, ar, ai, br, bi);
+        Ar += a.cr[k] * ar - a.ci[k] * ai;
+        Ai += a.cr[k] * ai + a.ci[k] * ar;
+        Br += a.cr[k] * br - a.ci[k] * bi;
+        Bi += a.cr[k] * bi + a.ci[k] * br;
+      }
     }
     TimeTerms<T> tt;
     time_terms_g<T>(a.tc, a.wa, a.wN, a.wL, t, tt);
@@ -863,10 +885,12 @@ __global__ void __launch_bounds__(kBlock, 2)
       ++bad;
       continue;
     }
-    if constexpr (sizeof(T) == 4) lf32.add(logf(R));
+    if constexpr (sizeof(T) == 4) lf32.add(pk::lg2(R));  // log2 R, scaled by ln 2 at the end
     else lf64 += log(R);
     if constexpr (GRAD) {
-      const T invR = T(1) / R;
+      T invR;
+      if constexpr (sizeof(T) == 4) invR = pk::rcp(R);
+      else invR = T(1) / R;
       const T cp = T(2) * tt.P * invR, cm = T(2) * tt.Q * invR, sh = tt.Tsh * invR, ss = tt.Ts * invR;
       // V_A / R = cp A* + (sh - i ss) B*,  V_B / R = cm B* + (sh + i ss) A*
       const T VAr = cp * Ar + sh * Br - ss * Bi, VAi = -cp * Ai - sh * Bi - ss * Br;
@@ -889,7 +913,7 @@ __global__ void __launch_bounds__(kBlock, 2)
     }
   }
   ddf v[NS];
-  v[0] = (sizeof(T) == 4) ? lf32.value() : dd_from_double(lf64);
+  v[0] = (sizeof(T) == 4) ? dd_mul(lf32.value(), ddf{kLn2Hi, kLn2Lo}) : dd_from_double(lf64);
   if constexpr (GRAD) {
 #pragma unroll
     for (int k = 0; k < KA; ++k) {
