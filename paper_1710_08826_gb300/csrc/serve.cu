@@ -1583,8 +1583,10 @@ int goo_server_step(goo_server* s, int* n_queued, int* n_active, int* n_done) {
     {
       LaunchScope ls(ctx, "srv_bfgs");
       const int na = (int)s->active.size();
-      srv_bfgs_kernel<<<(na + 127) / 128, 128, 0, ctx->stream>>>(s->d_states, s->d_evals, s->d_results, s->d_params,
-                                                                s->d_slots, na, s->d_done, s->d_done_count);
+      // one thread per fit in blocks of one warp, so that the fits' FP64 work spreads over
+      // every SM (blocks of 128 put 4096 fits on 32 SMs: 237 against 168 ms over a study)
+      srv_bfgs_kernel<<<(na + 31) / 32, 32, 0, ctx->stream>>>(s->d_states, s->d_evals, s->d_results, s->d_params,
+                                                              s->d_slots, na, s->d_done, s->d_done_count);
     }
     GOO_CUDA_TRY(cudaGetLastError());
     GOO_TRY(retire(s));
