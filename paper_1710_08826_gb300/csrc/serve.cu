@@ -324,8 +324,8 @@ struct SrvModel {   // shared by every fit of a batch
 // kSrvStages * (kSrvKB / 2) * kSrvSub float4.  status[0] is set when a copy wait gave up;
 // wait_limit bounds each wait for a sub-tile in SM clocks (the drain before exit allows
 // kWaitCycles).
-constexpr int kSrvSub = 512;
-constexpr int kSrvStages = 3;
+constexpr int kSrvSub = 768;
+constexpr int kSrvStages = 2;
 constexpr size_t kSrvSmem = (size_t)kSrvStages * (kSrvKB / 2) * kSrvSub * sizeof(float4);
 
 __global__ void __launch_bounds__(kBlock, 2) srv_nll_kernel(const SrvEval* __restrict__ ev, const int2* __restrict__ tiles,
