@@ -191,14 +191,14 @@ int grid_blocks(goo_ctx* ctx, int64_t work_items, int blocks_per_sm);
 // device, at least 1.  Cached per (kernel, device, block, smem): the occupancy query is a
 // driver call, and the launchers need its answer on every evaluation.
 int cached_occupancy(const void* kernel, int device, int block, size_t smem);
-// Waits for the completion word of the record a kernel writes to scratch.result_host (polling
-// for up to 2 ms, then waiting on the stream, which also reports a failed kernel) and copies
-// its first n doubles to dst.
+// Waits until the first n fields of the record a kernel writes to scratch.result_host no
+// longer hold kResultSentinel (polling for up to 2 ms, then waiting on the stream, which also
+// reports a failed kernel) and copies them to dst.
 int read_result_mapped(goo_ctx* ctx, int n, double* dst);
 // Fills the mapped record with kResultSentinel before a launch that writes to it.
 void arm_result_mapped(goo_ctx* ctx);
 // For the lifetime of the guard, the amplitude kernels write their record to the mapped host
-// copy (scratch.result_out = scratch.result_host) with its completion word cleared.
+// copy (scratch.result_out = scratch.result_host), armed with kResultSentinel.
 struct MappedResult {
   goo_ctx* ctx;
   explicit MappedResult(goo_ctx* c);

@@ -1693,7 +1693,7 @@ int dalitz_nll(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, 
                bool grad, double* out, int out_mode) {
   DalitzModel& d = *m->dalitz;
   goo_ctx* ctx = m->ctx;
-  // the record goes to the mapped host copy; the host polls its completion word
+  // the record goes to the mapped host copy; the host polls its fields
   MappedResult mapped(ctx);
   const int P = m->n_params;
   if (ds->ncols <= d.col12 || ds->ncols <= d.col13) return set_error(GOO_ERR_ARG, "dataset lacks s12/s13 columns");

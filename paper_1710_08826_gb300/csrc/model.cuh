@@ -67,7 +67,8 @@ int sop_prepare(goo_model* m, const double* theta_host, int precision, bool norm
 bool sop_norm_in_event(const goo_model* m, int precision, bool grad);
 void host_prep(ModelDev& h, const double* theta, int precision);
 // result: the record's destination (kResultDoubles + 1 doubles; null: the context's device
-// scratch record); the kernel sets its completion word (kResultFlag) last.
+// scratch record); the kernel writes each field once and sets its completion word
+// (kResultFlag) last.
 int sop_events(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, int precision, bool grad,
                int out_mode, bool norm_in_event = false, double* result = nullptr);
 int sop_eval_logf(goo_model* m, const goo_dataset* ds, int precision, double* logf_dev);

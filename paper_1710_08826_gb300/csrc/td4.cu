@@ -850,7 +850,7 @@ static int td4_launch(goo_model* m, const void* cache, const goo_dataset* ds, in
 int td4_nll(goo_model* m, const goo_dataset* ds, int64_t begin, int64_t end, const double* theta, int precision,
             bool grad, double* out, int out_mode) {
   goo_ctx* ctx = m->ctx;
-  // the record goes to the mapped host copy; the host polls its completion word
+  // the record goes to the mapped host copy; the host polls its fields
   MappedResult mapped(ctx);
   const int P = m->n_params;
   if (ds->ncols < 6) return set_error(GOO_ERR_ARG, "the four-body model needs 6 dataset columns");
