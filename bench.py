@@ -42,34 +42,34 @@ ISSUE_PEAK = 152 * 4 * 2.07e9
 
 NCU_RECORDS = {
     "sop_nll_grad_f32": {"bytes": 127_851_008, "events": 10_000_000, "duration_ns": 40864, "warp_inst": 21_770_696, "issue_active": 0.5403,
-        "sources": _SOP_SRC, "sha256": "b5b7bee304cebaa2d5d679f5cec5fc4a6d297363bec0540e3fc50d0c8ea7b181",
+        "sources": _SOP_SRC, "sha256": "3ed4cb035de0e77ce807ec05cf23e45860e2fa58293ff1d46daf6e3a119b7d9d",
         "profile": "profiles/sop_event2_kernel_f32_c2_10M.md"},
     "sop_nll_f64": {"bytes": 243_686_912, "events": 10_000_000, "duration_ns": 2504160, "fp64_pipe": 0.8625, "fp64_ops": {"dfma": 649_995_818, "dadd": 340_076_105, "dmul": 259_998_770},
-        "sources": _SOP_SRC, "sha256": "b5b7bee304cebaa2d5d679f5cec5fc4a6d297363bec0540e3fc50d0c8ea7b181",
+        "sources": _SOP_SRC, "sha256": "3ed4cb035de0e77ce807ec05cf23e45860e2fa58293ff1d46daf6e3a119b7d9d",
         "profile": "profiles/sop_event_kernel_f64_c2_10M.md"},
     "coh_nll_grad_f32": {"bytes": 323_078_912, "events": 5_000_000, "duration_ns": 62912, "warp_inst": 30_962_164, "issue_active": 0.4583,
-        "sources": _COH_SRC, "sha256": "c84cf966502aec13ce0c524e92e548982a92dfb0b432c76af543f40255265126",
+        "sources": _COH_SRC, "sha256": "7080f40dfc6a6e2bdf5bfb0c301cff74d36163f03e14d1a2d4bda521471645fa",
         "profile": "profiles/coh_nll_staged_kernel_f32_c3_5M.md"},
     "coh_nll_f64": {"bytes": 643_060_224, "events": 5_000_000, "duration_ns": 773056, "fp64_pipe": 0.8699, "fp64_ops": {"dfma": 165_155_649, "dadd": 135_077_825, "dmul": 105_000_000},
-        "sources": _COH_SRC, "sha256": "c84cf966502aec13ce0c524e92e548982a92dfb0b432c76af543f40255265126",
+        "sources": _COH_SRC, "sha256": "7080f40dfc6a6e2bdf5bfb0c301cff74d36163f03e14d1a2d4bda521471645fa",
         "profile": "profiles/coh_nll_kernel_f64_c3_5M.md"},
     "coh_ls_mc_f32": {"bytes": 8_068_608, "events": 1_000_000, "duration_ns": 91424, "warp_inst": 65_097_718, "issue_active": 0.6327,
-        "sources": _COH_SRC, "sha256": "c84cf966502aec13ce0c524e92e548982a92dfb0b432c76af543f40255265126",
+        "sources": _COH_SRC, "sha256": "7080f40dfc6a6e2bdf5bfb0c301cff74d36163f03e14d1a2d4bda521471645fa",
         "profile": "profiles/coh_ls_kernel_f32_c3_floating_5M.md"},
     "coh_ls_grad_f32": {"bytes": 40_095_744, "events": 5_000_000, "duration_ns": 423008, "warp_inst": 313_878_490, "issue_active": 0.6404,
-        "sources": _COH_SRC, "sha256": "c84cf966502aec13ce0c524e92e548982a92dfb0b432c76af543f40255265126",
+        "sources": _COH_SRC, "sha256": "7080f40dfc6a6e2bdf5bfb0c301cff74d36163f03e14d1a2d4bda521471645fa",
         "profile": "profiles/coh_ls_kernel_f32_c3_floating_5M.md"},
     "td3_nll_grad_f32": {"bytes": 523_908_096, "events": 2_000_000, "duration_ns": 126304, "warp_inst": 61_771_144, "issue_active": 0.5046,
-        "sources": _TD3_SRC, "sha256": "4cc3f14c365a42c6224f0a1d26f9567ff03bc65c6612ade6e1ff6601fee48966",
+        "sources": _TD3_SRC, "sha256": "2ee96edbae409b131c3760732bed2b634ebb13ae77fddcb3b50e4b06945639be",
         "profile": "profiles/td3_nll_kernel_td3_2M.md"},
     "td3_nll_f64": {"bytes": 979_147_776, "events": 2_000_000, "duration_ns": 1610336, "fp64_pipe": 0.8524, "fp64_ops": {"dfma": 391_298_265, "dadd": 152_090_307, "dmul": 214_414_797},
-        "sources": _TD3_SRC, "sha256": "4cc3f14c365a42c6224f0a1d26f9567ff03bc65c6612ade6e1ff6601fee48966",
+        "sources": _TD3_SRC, "sha256": "2ee96edbae409b131c3760732bed2b634ebb13ae77fddcb3b50e4b06945639be",
         "profile": "profiles/td3_nll_kernel_td3_2M.md"},
     "td4_nll_grad_f32": {"bytes": 171_075_840, "events": 2_000_000, "duration_ns": 67168, "warp_inst": 43_957_564, "issue_active": 0.6400,
-        "sources": _TD4_SRC, "sha256": "75adf0700eed8eb2b6697754c1587462d883f8d8d06be004f82a6f16854f9848",
+        "sources": _TD4_SRC, "sha256": "8ef7e0a2b5defacd2d941f6a3e45433b34b953e864ad1b87436c32e31963df11",
         "profile": "profiles/td4_nll_f32_kernel_c4_2M.md"},
     "td4_nll_f64": {"bytes": 339_123_712, "events": 2_000_000, "duration_ns": 1383968, "fp64_pipe": 0.8559, "fp64_ops": {"dfma": 351_287_209, "dadd": 112_088_842, "dmul": 178_181_349},
-        "sources": _TD4_SRC, "sha256": "75adf0700eed8eb2b6697754c1587462d883f8d8d06be004f82a6f16854f9848",
+        "sources": _TD4_SRC, "sha256": "8ef7e0a2b5defacd2d941f6a3e45433b34b953e864ad1b87436c32e31963df11",
         "profile": "profiles/td4_nll_f64_kernel_c4_2M.md"},
 }
 
