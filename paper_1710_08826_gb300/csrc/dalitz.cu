@@ -1379,7 +1379,8 @@ static int ensure_td_grams(goo_model* m, int precision) {
 }
 
 template <typename T>
-static void fill_td3(const DalitzModel& d, const double* theta, int n_params, int64_t n_total, Td3Args<T>& a) {
+static void fill_td3(const DalitzModel& d, const double* theta, int n_params, int64_t n_total, Td3Args<T>& a,
+                     double t_hi) {
   std::memset(&a, 0, sizeof a);
   for (int k = 0; k < d.K; ++k) {
     const int sl = k < d.nbw ? k : kTd3KB;
@@ -1390,7 +1391,7 @@ static void fill_td3(const DalitzModel& d, const double* theta, int n_params, in
     a.par_re[k] = d.par_re[k];
     a.par_im[k] = d.par_im[k];
   }
-  fill_time_coef<T>(a.tc, theta[d.par_t[0]], theta[d.par_t[1]], theta[d.par_t[2]], theta[d.par_t[3]]);
+  fill_time_coef<T>(a.tc, theta[d.par_t[0]], theta[d.par_t[1]], theta[d.par_t[2]], theta[d.par_t[3]], t_hi);
   a.x = a.tc.x;
   a.y = a.tc.y;
   a.G = a.tc.G;
@@ -1494,7 +1495,7 @@ static int launch_td3(goo_model* m, const goo_dataset* ds, int64_t begin, int64_
   constexpr int NS = Td3Lanes<GRAD>::NS;
   GOO_TRY(ensure_partials(ctx, (size_t)nb * NS));
   Td3Args<T> a;
-  fill_td3<T>(d, theta, m->n_params, ds->n, a);
+  fill_td3<T>(d, theta, m->n_params, ds->n, a, m->hi[d.col_t]);
   td3_norm_terms<T>(d, d.gram3_host[pi], a);
   const T* tcol = sizeof(T) == 4 ? (const T*)ds->d32[d.col_t] : (const T*)ds->d64[d.col_t];
   {

@@ -713,7 +713,7 @@ static void td4_args(const goo_model* m, const double* theta, int64_t n_total, T
     a.par_im[k] = d.par_im[k];
   }
   for (int j = 0; j < 4; ++j) a.par_t[j] = d.par_t[j];
-  fill_time_coef<T>(a.tc, theta[d.par_t[0]], theta[d.par_t[1]], theta[d.par_t[2]], theta[d.par_t[3]]);
+  fill_time_coef<T>(a.tc, theta[d.par_t[0]], theta[d.par_t[1]], theta[d.par_t[2]], theta[d.par_t[3]], m->hi[5]);
   a.x = a.tc.x;
   a.y = a.tc.y;
   a.G = a.tc.G;

@@ -128,11 +128,18 @@ struct TimeCoef {
   T ysh[K + 1], xs[K + 1];     // T_sh, T_s coefficients of u_(2m+1)
   T dax[K + 1], day[K + 1];    // d a_m / dx (= -d b_m / dx), d a_m / dy (= d b_m / dy)
   T dshy[K + 1], dsx[K + 1];   // d ysh_m / dy, d xs_m / dx
+  // the order in use, K - 1 or K, and the largest z at which it meets the truncation
+  // criterion: K - 1 when that covers every event the dataset's time range admits
+  int ku;
+  T zmax_ku;
 };
 
 #ifndef __CUDACC_RTC__
+// t_hi: the upper limit of the observed time (events above it take the Faddeeva path where
+// the order in use does not cover them, so it decides the speed, not the result).
 template <typename T>
-inline void fill_time_coef(TimeCoef<T>& c, double x64, double y64, double tau, double s64) {
+inline void fill_time_coef(TimeCoef<T>& c, double x64, double y64, double tau, double s64,
+                           double t_hi = HUGE_VAL) {
   constexpr int K = TimeCoef<T>::K;
   c.G = (T)(1.0 / tau);
   c.x = (T)x64;
@@ -153,6 +160,14 @@ inline void fill_time_coef(TimeCoef<T>& c, double x64, double y64, double tau, d
     c.dsx[m] = (T)(sg * (2 * m + 1) * x2m);
   }
   c.b[0] = (T)0;
+  // the first omitted term against the leading one is about z^(2k) 2 / (2k + 2)! at order k;
+  // order K - 1 meets the bound that order K meets at SeriesOrder<T>::zmax up to zk1
+  auto ratio = [](double z, int k) { return std::pow(z, 2.0 * k) * 2.0 / std::tgamma(2.0 * k + 3.0); };
+  const double eps = ratio(SeriesOrder<T>::zmax, K);
+  const double zk1 = std::pow(eps * std::tgamma(2.0 * (K - 1) + 3.0) / 2.0, 1.0 / (2.0 * (K - 1)));
+  const double zdata = (double)c.zs * (std::fmax(t_hi, 0.0) + 6.0 * (double)c.s);
+  c.ku = zdata < zk1 ? K - 1 : K;
+  c.zmax_ku = (T)(zdata < zk1 ? zk1 : SeriesOrder<T>::zmax);
 }
 #endif
 
@@ -260,10 +275,11 @@ __device__ __forceinline__ void time_terms_direct(T G, T x, T y, T s, const T* w
   }
 }
 
-// The decay-time terms by the moment series (small mixing; see the top of this file).
-template <typename T>
+// The decay-time terms by the moment series of order KU (small mixing; see the top of this
+// file).
+template <typename T, int KU>
 __device__ __forceinline__ void time_terms_series(const TimeCoef<T>& c, T t, T gauss, TimeTerms<T>& R) {
-  constexpr int K = TimeCoef<T>::K;
+  constexpr int K = KU;
   constexpr int NU = 2 * K + 3;
   const T G = c.G, s = c.s;
   const T s2 = s * s;
@@ -338,14 +354,20 @@ __device__ __forceinline__ void time_terms_series(const TimeCoef<T>& c, T t, T g
   R.d[3][3] = Ss;
 }
 
-// The decay-time terms at the observed time t and their derivatives: the moment series where
-// z = max(|x|, |y|) G (max(t, 0) + 6 s) is below SeriesOrder<T>::zmax, else the Faddeeva path.
+// The decay-time terms at the observed time t and their derivatives: the moment series of the
+// order in use where z = max(|x|, |y|) G (max(t, 0) + 6 s) is below its limit (c.zmax_ku),
+// else the Faddeeva path.
 template <typename T>
 __device__ __forceinline__ void time_terms_g(const TimeCoef<T>& c, const T* wa, int wN, T wL, T t, TimeTerms<T>& R) {
   const T gauss = td_exp<T>(-t * t / (T(2) * c.s * c.s));
   const T z = c.zs * ((t > T(0) ? t : T(0)) + T(6) * c.s);
-  if (z < T(SeriesOrder<T>::zmax)) time_terms_series<T>(c, t, gauss, R);
-  else time_terms_direct<T>(c.G, c.x, c.y, c.s, wa, wN, wL, t, gauss, R);
+  if (z < c.zmax_ku) {
+    // the same order for every event of a launch (a uniform branch)
+    if (c.ku == TimeCoef<T>::K) time_terms_series<T, TimeCoef<T>::K>(c, t, gauss, R);
+    else time_terms_series<T, TimeCoef<T>::K - 1>(c, t, gauss, R);
+  } else {
+    time_terms_direct<T>(c.G, c.x, c.y, c.s, wa, wN, wL, t, gauss, R);
+  }
 }
 
 
