@@ -42,34 +42,34 @@ ISSUE_PEAK = 152 * 4 * 2.07e9
 
 NCU_RECORDS = {
     "sop_nll_grad_f32": {"bytes": 127_851_008, "events": 10_000_000, "duration_ns": 40864, "warp_inst": 21_770_696, "issue_active": 0.5403,
-        "sources": _SOP_SRC, "sha256": "3ed4cb035de0e77ce807ec05cf23e45860e2fa58293ff1d46daf6e3a119b7d9d",
+        "sources": _SOP_SRC, "sha256": "510948a29bee9a77654bc84a7a3df5014e9aba8eb1fb4f7f3c6495b38be33291",
         "profile": "profiles/sop_event2_kernel_f32_c2_10M.md"},
     "sop_nll_f64": {"bytes": 243_686_912, "events": 10_000_000, "duration_ns": 2504160, "fp64_pipe": 0.8625, "fp64_ops": {"dfma": 649_995_818, "dadd": 340_076_105, "dmul": 259_998_770},
-        "sources": _SOP_SRC, "sha256": "3ed4cb035de0e77ce807ec05cf23e45860e2fa58293ff1d46daf6e3a119b7d9d",
+        "sources": _SOP_SRC, "sha256": "510948a29bee9a77654bc84a7a3df5014e9aba8eb1fb4f7f3c6495b38be33291",
         "profile": "profiles/sop_event_kernel_f64_c2_10M.md"},
     "coh_nll_grad_f32": {"bytes": 323_078_912, "events": 5_000_000, "duration_ns": 62912, "warp_inst": 30_962_164, "issue_active": 0.4583,
-        "sources": _COH_SRC, "sha256": "727e6672a16f240bc96718670a3498029d73be4323f1aa9006246eba6c929550",
+        "sources": _COH_SRC, "sha256": "e6dd74780f809bce3110cf47365aa77f11795ed20f00040bf6bdb22689ec5c10",
         "profile": "profiles/coh_nll_staged_kernel_f32_c3_5M.md"},
     "coh_nll_f64": {"bytes": 643_060_224, "events": 5_000_000, "duration_ns": 773056, "fp64_pipe": 0.8699, "fp64_ops": {"dfma": 165_155_649, "dadd": 135_077_825, "dmul": 105_000_000},
-        "sources": _COH_SRC, "sha256": "727e6672a16f240bc96718670a3498029d73be4323f1aa9006246eba6c929550",
+        "sources": _COH_SRC, "sha256": "e6dd74780f809bce3110cf47365aa77f11795ed20f00040bf6bdb22689ec5c10",
         "profile": "profiles/coh_nll_kernel_f64_c3_5M.md"},
     "coh_ls_mc_f32": {"bytes": 8_068_608, "events": 1_000_000, "duration_ns": 91424, "warp_inst": 65_097_718, "issue_active": 0.6327,
-        "sources": _COH_SRC, "sha256": "727e6672a16f240bc96718670a3498029d73be4323f1aa9006246eba6c929550",
+        "sources": _COH_SRC, "sha256": "e6dd74780f809bce3110cf47365aa77f11795ed20f00040bf6bdb22689ec5c10",
         "profile": "profiles/coh_ls_kernel_f32_c3_floating_5M.md"},
     "coh_ls_grad_f32": {"bytes": 40_095_744, "events": 5_000_000, "duration_ns": 423008, "warp_inst": 313_878_490, "issue_active": 0.6404,
-        "sources": _COH_SRC, "sha256": "727e6672a16f240bc96718670a3498029d73be4323f1aa9006246eba6c929550",
+        "sources": _COH_SRC, "sha256": "e6dd74780f809bce3110cf47365aa77f11795ed20f00040bf6bdb22689ec5c10",
         "profile": "profiles/coh_ls_kernel_f32_c3_floating_5M.md"},
     "td3_nll_grad_f32": {"bytes": 523_831_552, "events": 2_000_000, "duration_ns": 123872, "warp_inst": 58_927_749, "issue_active": 0.4974,
-        "sources": _TD3_SRC, "sha256": "bece7c67e2ae70c4ad42f8aaa2dba570a48be5d3873cb78f727e19880a316330",
+        "sources": _TD3_SRC, "sha256": "e48af6bcb92115b4614cbcddd96cc88e067ad2ef2ac5fa5789b7c49f36a2754f",
         "profile": "profiles/td3_nll_kernel_td3_2M.md"},
     "td3_nll_f64": {"bytes": 978_785_280, "events": 2_000_000, "duration_ns": 1571456, "fp64_pipe": 0.8519, "fp64_ops": {"dfma": 379_298_265, "dadd": 152_090_307, "dmul": 204_597_360},
-        "sources": _TD3_SRC, "sha256": "bece7c67e2ae70c4ad42f8aaa2dba570a48be5d3873cb78f727e19880a316330",
+        "sources": _TD3_SRC, "sha256": "e48af6bcb92115b4614cbcddd96cc88e067ad2ef2ac5fa5789b7c49f36a2754f",
         "profile": "profiles/td3_nll_kernel_td3_2M.md"},
     "td4_nll_grad_f32": {"bytes": 171_529_216, "events": 2_000_000, "duration_ns": 66208, "warp_inst": 42_200_954, "issue_active": 0.6162,
-        "sources": _TD4_SRC, "sha256": "a02c9b359b83bc32236f13bd93ef79ba05a0fec7819f9958941490eb91a00d1d",
+        "sources": _TD4_SRC, "sha256": "7a3a5863cd246c56e893370aafe76a743a995a6210e8660c4a7e3574007c88ba",
         "profile": "profiles/td4_nll_f32_kernel_c4_2M.md"},
     "td4_nll_f64": {"bytes": 339_599_872, "events": 2_000_000, "duration_ns": 1338752, "fp64_pipe": 0.8552, "fp64_ops": {"dfma": 339_287_209, "dadd": 112_088_842, "dmul": 164_520_152},
-        "sources": _TD4_SRC, "sha256": "a02c9b359b83bc32236f13bd93ef79ba05a0fec7819f9958941490eb91a00d1d",
+        "sources": _TD4_SRC, "sha256": "7a3a5863cd246c56e893370aafe76a743a995a6210e8660c4a7e3574007c88ba",
         "profile": "profiles/td4_nll_f64_kernel_c4_2M.md"},
 }
 

@@ -353,15 +353,7 @@ __device__ __forceinline__ float rcp(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-constexpr float kLog2e = 1.4426950408889634f;  // 1 / ln 2
 constexpr float kLn2 = 0.6931471805599453f;
-__device__ __forceinline__ float2 exp(float2 x) {  // e^x per lane
-  const float2 t = mul(x, splat(kLog2e));
-  return make_float2(ex2(t.x), ex2(t.y));
-}
-__device__ __forceinline__ float2 log(float2 x) {  // natural log per lane
-  return mul(make_float2(lg2(x.x), lg2(x.y)), splat(kLn2));
-}
 __device__ __forceinline__ float2 rcp(float2 x) { return make_float2(rcp(x.x), rcp(x.y)); }
 }  // namespace pk
 

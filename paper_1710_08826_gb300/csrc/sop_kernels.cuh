@@ -712,14 +712,6 @@ struct Kahan2 {
     c = pk::sub(pk::sub(t, s), y);
     s = t;
   }
-  __device__ __forceinline__ void add_lane(int lane, float x) {
-    float& sl = lane ? s.y : s.x;
-    float& cl = lane ? c.y : c.x;
-    const float y = x - cl;
-    const float t = sl + y;
-    cl = (t - sl) - y;
-    sl = t;
-  }
 };
 
 
