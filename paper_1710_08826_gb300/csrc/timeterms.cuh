@@ -132,6 +132,7 @@ struct TimeCoef {
   // criterion: K - 1 when that covers every event the dataset's time range admits
   int ku;
   T zmax_ku;
+  T is2, is2h;  // 1 / s^2 and 1 / (2 s^2), so that no event divides by them
 };
 
 #ifndef __CUDACC_RTC__
@@ -147,6 +148,8 @@ inline void fill_time_coef(TimeCoef<T>& c, double x64, double y64, double tau, d
   c.s = (T)s64;
   const double x = (double)c.x, y = (double)c.y, G = (double)c.G;
   c.zs = (T)(std::fmax(std::fabs(x), std::fabs(y)) * G);
+  c.is2 = (T)(1.0 / ((double)c.s * (double)c.s));
+  c.is2h = (T)(0.5 / ((double)c.s * (double)c.s));
   for (int m = 0; m <= K; ++m) {
     const double sg = (m & 1) ? -1.0 : 1.0;
     const double y2m = std::pow(y, 2 * m), x2m = std::pow(x, 2 * m);
@@ -297,7 +300,7 @@ __device__ __forceinline__ void time_terms_series(const TimeCoef<T>& c, T t, T g
   const T G2 = G * G;
   auto su = [&](int n) -> T {
     const T um1 = n >= 1 ? u[n - 1] : T(0), um2 = n >= 2 ? u[n - 2] : T(0);
-    const T cn = n == 0 ? (-t / s2 - G) * phi : (n == 1 ? G * phi : T(0));
+    const T cn = n == 0 ? (-t * c.is2 - G) * phi : (n == 1 ? G * phi : T(0));
     return s * (G2 * ((u[n] - um1) - (um1 - um2)) + cn);
   };
   auto gu = [&](int n) -> T { return T(n) * u[n] - T(n + 1) * u[n + 1]; };
@@ -359,7 +362,7 @@ __device__ __forceinline__ void time_terms_series(const TimeCoef<T>& c, T t, T g
 // else the Faddeeva path.
 template <typename T>
 __device__ __forceinline__ void time_terms_g(const TimeCoef<T>& c, const T* wa, int wN, T wL, T t, TimeTerms<T>& R) {
-  const T gauss = td_exp<T>(-t * t / (T(2) * c.s * c.s));
+  const T gauss = td_exp<T>(-t * t * c.is2h);
   const T z = c.zs * ((t > T(0) ? t : T(0)) + T(6) * c.s);
   if (z < c.zmax_ku) {
     // the same order for every event of a launch (a uniform branch)
