@@ -59,17 +59,17 @@ NCU_RECORDS = {
     "coh_ls_grad_f32": {"bytes": 40_095_744, "events": 5_000_000, "duration_ns": 423008, "warp_inst": 313_878_490, "issue_active": 0.6404,
         "sources": _COH_SRC, "sha256": "e6dd74780f809bce3110cf47365aa77f11795ed20f00040bf6bdb22689ec5c10",
         "profile": "profiles/coh_ls_kernel_f32_c3_floating_5M.md"},
-    "td3_nll_grad_f32": {"bytes": 523_831_552, "events": 2_000_000, "duration_ns": 123872, "warp_inst": 58_927_749, "issue_active": 0.4974,
-        "sources": _TD3_SRC, "sha256": "e48af6bcb92115b4614cbcddd96cc88e067ad2ef2ac5fa5789b7c49f36a2754f",
+    "td3_nll_grad_f32": {"bytes": 523_792_384, "events": 2_000_000, "duration_ns": 123872, "warp_inst": 57_684_324, "issue_active": 0.4858,
+        "sources": _TD3_SRC, "sha256": "6ed9dd3bdcc23857eee61afd5ccf6fea65229ed5889dce989198cfbc3c23a7cc",
         "profile": "profiles/td3_nll_kernel_td3_2M.md"},
-    "td3_nll_f64": {"bytes": 978_785_280, "events": 2_000_000, "duration_ns": 1571456, "fp64_pipe": 0.8519, "fp64_ops": {"dfma": 379_298_265, "dadd": 152_090_307, "dmul": 204_597_360},
-        "sources": _TD3_SRC, "sha256": "e48af6bcb92115b4614cbcddd96cc88e067ad2ef2ac5fa5789b7c49f36a2754f",
+    "td3_nll_f64": {"bytes": 979_099_392, "events": 2_000_000, "duration_ns": 1546976, "fp64_pipe": 0.8508, "fp64_ops": {"dfma": 365_298_265, "dadd": 152_012_483, "dmul": 204_519_536},
+        "sources": _TD3_SRC, "sha256": "6ed9dd3bdcc23857eee61afd5ccf6fea65229ed5889dce989198cfbc3c23a7cc",
         "profile": "profiles/td3_nll_kernel_td3_2M.md"},
-    "td4_nll_grad_f32": {"bytes": 171_529_216, "events": 2_000_000, "duration_ns": 66208, "warp_inst": 42_200_954, "issue_active": 0.6162,
-        "sources": _TD4_SRC, "sha256": "7a3a5863cd246c56e893370aafe76a743a995a6210e8660c4a7e3574007c88ba",
+    "td4_nll_grad_f32": {"bytes": 170_933_248, "events": 2_000_000, "duration_ns": 65632, "warp_inst": 40_895_064, "issue_active": 0.6042,
+        "sources": _TD4_SRC, "sha256": "898395f56ed8fefb846f9ef3fb08867f16fcc8eb6ff15e61bc5de84b41a27fd9",
         "profile": "profiles/td4_nll_f32_kernel_c4_2M.md"},
-    "td4_nll_f64": {"bytes": 339_599_872, "events": 2_000_000, "duration_ns": 1338752, "fp64_pipe": 0.8552, "fp64_ops": {"dfma": 339_287_209, "dadd": 112_088_842, "dmul": 164_520_152},
-        "sources": _TD4_SRC, "sha256": "7a3a5863cd246c56e893370aafe76a743a995a6210e8660c4a7e3574007c88ba",
+    "td4_nll_f64": {"bytes": 339_106_816, "events": 2_000_000, "duration_ns": 1312992, "fp64_pipe": 0.8540, "fp64_ops": {"dfma": 325_287_209, "dadd": 112_011_018, "dmul": 164_442_328},
+        "sources": _TD4_SRC, "sha256": "898395f56ed8fefb846f9ef3fb08867f16fcc8eb6ff15e61bc5de84b41a27fd9",
         "profile": "profiles/td4_nll_f64_kernel_c4_2M.md"},
 }
 
